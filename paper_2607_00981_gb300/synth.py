@@ -1,0 +1,98 @@
+"""Seeded synthetic closed-shell Hamiltonians shaped like the paper's workloads.
+
+This module only draws random numbers; it holds none of the coupled-cluster
+arithmetic, so both the CPU oracle (through the tests) and the CUDA path can
+be fed from it.  numpy's ``default_rng`` (PCG64) is used, with this fixed
+draw order for one instance:
+
+1. ``A = standard_normal((naux, n, n))`` with ``n = o + v``;
+2. ``L = 0.5 * (A + A^T) * scale * exp(-|p - q| / 4)``  (symmetric in p,q);
+3. occupied orbital energies ``sort(uniform(-2.0, -0.5, o))``;
+4. virtual orbital energies ``sort(uniform(0.2, 5.0, v))``.
+
+The ERIs are the low-rank product ``(pq|rs) = sum_P L[P,p,q] L[P,r,s]`` and the
+Fock matrix is diagonal (canonical orbitals, occupied first).  The batched
+workload draws ``o`` in [3, 8] and ``v`` in [20, 60] from seed 0 and gives
+instance ``i`` the seed ``1000 + i`` with ``naux = 4 (o + v)``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Instance:
+    """One synthetic problem: spatial orbital counts, factors and Fock diagonal."""
+
+    o: int
+    v: int
+    naux: int
+    seed: int
+    L: np.ndarray          # [naux][n][n] float64, symmetric in the last two axes
+    fock_diag: np.ndarray  # [n] float64, occupied first
+
+    @property
+    def n(self) -> int:
+        return self.o + self.v
+
+
+def make_instance(o: int, v: int, naux: int, seed: int = 0, scale: float = 0.3) -> Instance:
+    """Draw one seeded instance with the recipe in the module docstring."""
+    if o < 1 or v < 1 or naux < 1:
+        raise ValueError("o, v and naux must be positive")
+    n = o + v
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((naux, n, n))
+    p = np.arange(n)
+    envelope = scale * np.exp(-np.abs(p[:, None] - p[None, :]) / 4.0)
+    L = 0.5 * (A + A.transpose(0, 2, 1)) * envelope[None, :, :]
+    e_occ = np.sort(rng.uniform(-2.0, -0.5, o))
+    e_vir = np.sort(rng.uniform(0.2, 5.0, v))
+    return Instance(o=o, v=v, naux=naux, seed=seed, L=np.ascontiguousarray(L),
+                    fock_diag=np.concatenate([e_occ, e_vir]))
+
+
+# The five workloads, by size.  naux follows the stated ranks.
+WORKLOADS = {
+    "o3v12": dict(o=3, v=12, naux=40, seed=0),
+    "o8v80": dict(o=8, v=80, naux=320, seed=0),
+    "o12v120": dict(o=12, v=120, naux=480, seed=0),
+    "o16v160": dict(o=16, v=160, naux=640, seed=0),
+}
+
+
+def workload(name: str) -> Instance:
+    return make_instance(**WORKLOADS[name])
+
+
+def batch_shapes(count: int = 64, seed: int = 0):
+    """(o, v, naux, seed) of the batched uneven-instance workload."""
+    rng = np.random.default_rng(seed)
+    o = rng.integers(3, 9, size=count)
+    v = rng.integers(20, 61, size=count)
+    return [(int(oi), int(vi), int(4 * (oi + vi)), 1000 + i) for i, (oi, vi) in enumerate(zip(o, v))]
+
+
+def random_amplitudes(o: int, v: int, seed: int, scale: float = 0.05):
+    """Seeded (t1, t2, t3) with the spin-free column symmetries, for parity tests.
+
+    t2[i,j,a,b] = t2[j,i,b,a]; t3 is full [o,o,o,v,v,v] and invariant under the six
+    simultaneous permutations of its (occupied, virtual) column pairs.  These are
+    plain symmetrised random numbers, not solutions of any equation.
+    """
+    rng = np.random.default_rng(seed)
+    # values on a 2^-24 grid, so the symmetrising sums below are exact and the
+    # symmetries hold bit for bit
+    q = lambda a: np.round(a * 2.0 ** 24) / 2.0 ** 24  # noqa: E731
+    t1 = q(scale * rng.standard_normal((o, v)))
+    x = q(scale * rng.standard_normal((o, o, v, v)))
+    t2 = 0.5 * (x + x.transpose(1, 0, 3, 2))
+    y = q(scale * rng.standard_normal((o, o, o, v, v, v)))
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    t3 = np.zeros_like(y)
+    for p in perms:
+        t3 += y.transpose(p[0], p[1], p[2], 3 + p[0], 3 + p[1], 3 + p[2])
+    t3 /= 6.0        # equal sums give equal quotients
+    return t1, t2, t3

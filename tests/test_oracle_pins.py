@@ -1,0 +1,246 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks it against brute
+force (determinant-space CC / FCI), an exactness theorem, a closed form, an
+invariant or a number printed in the paper.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import compact as C
+from oracle import detcc, nullspace, opcount
+from oracle import rccsdt as full
+from paper_2607_00981_gb300.synth import make_instance, random_amplitudes
+
+
+def _det_cc_energy(inst, o, rank, na=None, nb=None):
+    na = o if na is None else na
+    nb = o if nb is None else nb
+    space, H, ref, fso, h, eri = detcc.setup(inst.L, inst.fock_diag, o, na, nb)
+    cc = detcc.DetCC(space, H, ref, rank, fso)
+    E, t, _ = cc.solve(tol=1e-11)
+    return E, H[space.index[ref], space.index[ref]], cc, t, H
+
+
+# ---------------------------------------------------------------- exactness (A.1)
+
+@pytest.mark.parametrize("v", [2, 3])
+def test_ccsdt_is_exact_for_three_electrons(v):
+    """CC truncated at N = n_elec is exact: CCSDT on 3 electrons is an FCI eigenstate."""
+    inst = make_instance(2, v, naux=10, seed=5)
+    E, _, cc, t, H = _det_cc_energy(inst, 2, 3, na=2, nb=1)
+    psi = cc.psi(t)
+    assert np.linalg.norm(H @ psi - E * psi) / np.linalg.norm(psi) < 1e-8
+    assert np.min(np.abs(detcc.fci_energies(H) - E)) < 1e-10
+
+
+@pytest.mark.parametrize("v", [2, 3])
+def test_ccsdtq_is_exact_for_four_electrons(v):
+    inst = make_instance(2, v, naux=10, seed=5)
+    E, _, cc, t, H = _det_cc_energy(inst, 2, 4)
+    assert np.min(np.abs(detcc.fci_energies(H) - E)) < 1e-10
+
+
+def test_ccsdt_is_not_exact_for_four_electrons():
+    """Negative control: the exactness pin does distinguish a truncated method."""
+    inst = make_instance(2, 3, naux=10, seed=5)
+    E, _, cc, t, H = _det_cc_energy(inst, 2, 3)
+    assert np.min(np.abs(detcc.fci_energies(H) - E)) > 1e-7
+
+
+# ------------------------------------------- working equations vs brute force (A.5)
+
+@pytest.mark.parametrize("o,v,seed", [(2, 3, 3), (3, 3, 3)])
+def test_rccsd_equals_determinant_ccsd(o, v, seed):
+    inst = make_instance(o, v, naux=12, seed=seed)
+    E_det, E0, *_ = _det_cc_energy(inst, o, 2)
+    E_rcc = full.solve_full(inst.L, inst.fock_diag, o, triples=False, tol=1e-10, max_iter=400)[0]
+    assert abs((E_det - E0) - E_rcc) < 1e-10
+
+
+@pytest.mark.parametrize("o,v,seed", [(2, 2, 3), (2, 3, 3), (3, 3, 3), (3, 4, 3)])
+def test_rccsdt_equals_determinant_ccsdt(o, v, seed):
+    """The printed RCCSDT equations (with T1 dressing) reproduce spin-orbital CCSDT."""
+    inst = make_instance(o, v, naux=12, seed=seed)
+    E_det, E0, *_ = _det_cc_energy(inst, o, 3)
+    E_rcc = full.solve_full(inst.L, inst.fock_diag, o, triples=True, tol=1e-10, max_iter=400)[0]
+    assert abs((E_det - E0) - E_rcc) < 1e-10
+
+
+def test_two_electrons_rccsd_rccsdt_fci():
+    """o = 1: the only T3 block is i = j = k (purified), so RCCSD = RCCSDT = FCI."""
+    inst = make_instance(1, 4, naux=8, seed=2)
+    space, H, ref, *_ = detcc.setup(inst.L, inst.fock_diag, 1, 1, 1)
+    E0 = H[space.index[ref], space.index[ref]]
+    e_fci = detcc.fci_energies(H)[0] - E0
+    e_sd = full.solve_full(inst.L, inst.fock_diag, 1, triples=False)[0]
+    e_sdt = C.solve_compact(inst.L, inst.fock_diag, 1)[0]
+    assert abs(e_sd - e_fci) < 1e-10
+    assert abs(e_sdt - e_fci) < 1e-10
+
+
+# ------------------------------------------------------------ invariants (A.2, II.D)
+
+def test_full_residual_has_column_symmetry():
+    o, v = 3, 5
+    inst = make_instance(o, v, naux=20, seed=1)
+    t1, t2, t3 = random_amplitudes(o, v, seed=4)
+    _, r2, r3 = full.residuals(inst.L, inst.fock_diag, t1, t2, t3)
+    assert np.abs(r2 - r2.transpose(1, 0, 3, 2)).max() < 1e-12
+    for p in full.PERMS3:
+        rp = r3.transpose(p[0], p[1], p[2], 3 + p[0], 3 + p[1], 3 + p[2])
+        assert np.abs(r3 - rp).max() < 1e-12 * max(1.0, np.abs(r3).max())
+
+
+def test_compact_residual_equals_full_residual():
+    """Compact expansions (direct traversal + unpacking) give the full residual."""
+    o, v = 3, 12
+    inst = make_instance(o, v, naux=40, seed=0)
+    t1, t2, t3 = random_amplitudes(o, v, seed=7)
+    r1f, r2f, r3f = full.residuals(inst.L, inst.fock_diag, t1, t2, t3)
+    r1c, r2c, r3c = C.residuals_compact(inst.L, inst.fock_diag, t1, t2, C.pack(t3))
+    scale = np.abs(r3f).max()
+    assert np.abs(r1f - r1c).max() < 1e-12 * scale
+    assert np.abs(r2f - r2c).max() < 1e-12 * scale
+    assert np.abs(C.pack(r3f) - r3c).max() < 1e-12 * scale
+
+
+def test_compact_converged_energy_equals_full():
+    inst = make_instance(3, 6, naux=20, seed=11, scale=0.2)
+    Ec, *_ = C.solve_compact(inst.L, inst.fock_diag, 3, tol=1e-10, max_iter=300)
+    Ef, *_ = full.solve_full(inst.L, inst.fock_diag, 3, tol=1e-10, max_iter=300)
+    assert abs(Ec - Ef) < 1e-11
+
+
+def test_frozen_zero_t3_reduces_to_rccsd():
+    """T3 = 0 in the RCCSDT equations gives the RCCSD residuals and energy."""
+    o, v = 3, 5
+    inst = make_instance(o, v, naux=20, seed=1, scale=0.2)
+    t1, t2, _ = random_amplitudes(o, v, seed=4)
+    r1a, r2a, _ = full.residuals(inst.L, inst.fock_diag, t1, t2, None)
+    r1b, r2b, _ = full.residuals(inst.L, inst.fock_diag, t1, t2, np.zeros((o,) * 3 + (v,) * 3))
+    assert np.abs(r1a - r1b).max() < 1e-13 and np.abs(r2a - r2b).max() < 1e-13
+    Ea = full.solve_full(inst.L, inst.fock_diag, o, triples=False)[0]
+    Eb = full.solve_full(inst.L, inst.fock_diag, o, triples=True, t3_frozen_zero=True)[0]
+    assert abs(Ea - Eb) < 1e-11
+
+
+def test_unpack_reproduces_full_tensor():
+    o, v = 4, 3
+    _, _, t3 = random_amplitudes(o, v, seed=9)
+    assert np.array_equal(C.unpack_full(C.pack(t3), o), t3)
+
+
+def test_compact_block_index_is_a_bijection_in_colex_order():
+    for o in range(1, 9):
+        tr = C.triples(o)
+        assert len(tr) == o * (o + 1) * (o + 2) // 6 == opcount.n3(o)
+        assert len(set(tr)) == len(tr)
+        assert tr == sorted(tr, key=lambda t: (t[2], t[1], t[0]))
+
+
+def test_postprocessed_residual_is_in_the_nonredundant_subspace():
+    o, v = 3, 5
+    inst = make_instance(o, v, naux=20, seed=1)
+    t1, t2, t3 = random_amplitudes(o, v, seed=4)
+    _, _, r3c = C.residuals_compact(inst.L, inst.fock_diag, t1, t2, C.pack(t3))
+    r = C.postprocess(r3c, o)
+    s = sum(np.transpose(r, (0,) + tuple(1 + np.argsort(p))) for p in full.PERMS3)
+    assert np.abs(s).max() < 1e-13
+    for b, (i, j, k) in enumerate(C.triples(o)):
+        if i == j == k:
+            assert not np.any(r[b])
+        if i == j:
+            assert np.abs(r[b] - r[b].transpose(1, 0, 2)).max() < 1e-14
+        if j == k:
+            assert np.abs(r[b] - r[b].transpose(0, 2, 1)).max() < 1e-14
+
+
+# --------------------------------------------------------------- closed forms
+
+def test_first_energy_from_mp2_amplitudes_is_mp2_energy():
+    o, v = 3, 6
+    inst = make_instance(o, v, naux=20, seed=0)
+    t2 = full.mp2_t2(inst.L, inst.fock_diag, o)
+    E = full.energy(inst.L, inst.fock_diag, np.zeros((o, v)), t2)
+    assert abs(E - full.mp2_energy_closed_form(inst.L, inst.fock_diag, o)) < 1e-12
+
+
+def test_s3_overlap_eigenvalues_and_projector():
+    M = nullspace.overlap_matrix(3)
+    ev = np.sort(np.linalg.eigvalsh(M))
+    assert np.allclose(ev, [0, 6, 6, 6, 6, 24], atol=1e-12)
+    Pr = nullspace.projector_triples()
+    assert np.allclose(Pr @ Pr, Pr)
+    assert np.allclose(Pr @ np.ones(6), 0.0)
+    # the null vector of M is the fully symmetric one
+    w, U = np.linalg.eigh(M)
+    null = U[:, np.argmin(np.abs(w))]
+    assert np.allclose(np.abs(null), 1 / np.sqrt(6))
+
+
+def test_s4_overlap_eigenvalues():
+    ev = np.sort(np.linalg.eigvalsh(nullspace.overlap_matrix(4)))
+    counts = {mu: int(np.sum(np.isclose(ev, mu))) for mu in (0, 12, 24, 120)}
+    # [4] (1) + [3,1] (9) null; [2^2] 4, [2,1^2] 9, [1^4] 1
+    assert counts == {0: 10, 12: 4, 24: 9, 120: 1}
+
+
+def test_spin_free_overlap_matches_determinant_space():
+    """<E^{pi(abc)}_{ijk} Phi | E^{tau(abc)}_{ijk} Phi> computed from determinants
+    equals m(pi^-1 tau) = sgn 2^cycles (Eq. spinfree_overlap_class_function)."""
+    o, v = 3, 3
+    space = detcc.DetSpace(o + v, o, o)
+    ref = detcc.reference_det(o, o)
+    phi = np.zeros(space.dim)
+    phi[space.index[ref]] = 1.0
+    I, A = (0, 1, 2), (3, 4, 5)
+    perms = list(itertools.permutations(range(3)))
+    states = []
+    for p in perms:
+        vec = np.zeros(space.dim)
+        for sig in itertools.product((0, 1), repeat=3):
+            ops = ([(2 * A[p[q]] + sig[q], True) for q in range(3)]
+                   + [(2 * I[q] + sig[q], False) for q in reversed(range(3))])
+            vec += space.operator(ops) @ phi
+        states.append(vec)
+    S = np.array([[a @ b for b in states] for a in states])
+    assert np.allclose(S, nullspace.overlap_matrix(3))
+
+
+def test_operation_counts():
+    for o, v in [(1, 1), (2, 3), (3, 4), (4, 2)]:
+        assert opcount.compact_fma_enumerated(o, v) == opcount.compact_fma(o, v)
+    # large-o limit of the compact count is 1/2 o^3 v^5 + 2 o^4 v^4 + 1/2 o^5 v^3
+    o, v = 4000, 8000
+    assert abs(opcount.compact_fma(o, v) / opcount.compact_asymptotic(o, v) - 1) < 1e-3
+    # flop per iteration of the workloads (2 flop per FMA)
+    assert f"{opcount.flop_per_iteration(3, 12):.3g}" == "3.08e+07"
+    assert f"{opcount.flop_per_iteration(8, 80):.3g}" == "3.33e+12"
+    assert f"{opcount.flop_per_iteration(16, 160):.3g}" == "7.24e+14"
+
+
+def test_compact_memory_matches_paper_sizes():
+    """n3 v^3 doubles, printed as 587 GB (o=40, v=190) and 623 GB (o=24, v=318)."""
+    gib = lambda o, v: opcount.t3_bytes(o, v) / 2 ** 30  # noqa: E731
+    assert round(gib(40, 190)) == 587
+    assert round(gib(24, 318)) == 623
+    assert round(opcount.t3_bytes(48, 292) / 2 ** 40, 1) == 3.6
+    assert round(opcount.t3_bytes(52, 328) / 2 ** 40, 1) == 6.4
+
+
+def test_diis_solves_a_linear_fixed_point():
+    """DIIS on x <- A x + b converges to (I - A)^-1 b within dim + 1 steps."""
+    rng = np.random.default_rng(0)
+    n = 5
+    A = 0.5 * rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    x = np.zeros(n)
+    d = full.Diis(8)
+    for _ in range(n + 2):
+        xn = A @ x + b
+        d.push(xn, xn - x)
+        x = d.extrapolate()
+    assert np.allclose(x, np.linalg.solve(np.eye(n) - A, b), atol=1e-10)

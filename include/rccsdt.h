@@ -1,0 +1,160 @@
+/*
+ * rccsdt.h -- C ABI of the GB300 (sm_103a) RCCSDT residual library.
+ *
+ * One spin-restricted CCSDT iteration on compact triples storage: the T1-dressed
+ * Hamiltonian and intermediates, the residuals R1, R2 and R3 (the T3 residual
+ * keeps only the occupied triples i <= j <= k, each a full v^3 block over abc),
+ * the post-processing of R3, the orbital-energy denominator update with DIIS and
+ * the correlation energy.  The method is the one of arXiv 2607.00981:
+ *   - working equations: appendix A.5 (RCCSD R1/R2, RCCSDT T3 corrections,
+ *     Eq. resi-rccsdt, the RCCSDT intermediates), with the T1-dressed integrals
+ *     of appendix A.4 and the spin summations of Eq. triples-spin-sum;
+ *   - compact storage and contractions: Sec. II.B.1 and Sec. II.C (direct
+ *     traversal of the pp-ladder, unpacking for the hh-ladder and ring terms,
+ *     the representative contractions of the operation-count table);
+ *   - post-processing: Sec. II.D (symmetrise, purify, orthogonalise);
+ *   - update: Jacobi step t += r / eps of appendix A.1; DIIS of Sec. III.A.4;
+ *   - energy: the E_CC expression of appendix A.5 with bare integrals.
+ *
+ * Conventions (all arrays dense, row-major, float64 unless stated):
+ *   n = o + v spatial orbitals, occupied first.
+ *   L[naux][n][n]   factors of the chemists' ERIs, (pq|rs) = sum_P L[P,p,q] L[P,r,s];
+ *                   symmetric in the last two indices.
+ *   fock_diag[n]    canonical (diagonal) Fock matrix.
+ *   t1[o][v], t2[o][o][v][v]        spin-free amplitudes t_i^a, t_ij^ab.
+ *   t3c[n3][v][v][v], n3 = o(o+1)(o+2)/6, block blk(i<=j<=k) =
+ *                   C(k+2,3) + C(j+1,2) + i  (colex order), element [a][b][c] = t_ijk^abc.
+ *   Residuals r1, r2, r3c use the same layouts.
+ * Pointers passed in or out may be host or device memory (the library copies with
+ * cudaMemcpyDefault on the context's stream and synchronises before returning
+ * from calls that read or write caller memory).  The caller keeps ownership of
+ * its buffers; the context owns every buffer it allocates.
+ *
+ * Errors: every call returns an rccsdt_status; nothing aborts, traps or prints.
+ * rccsdt_last_error() gives a text for the last failing call on a context.
+ */
+#ifndef RCCSDT_H
+#define RCCSDT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rccsdt_ctx rccsdt_ctx;
+
+typedef enum {
+  RCCSDT_OK = 0,
+  RCCSDT_ERR_ARG = -1,        /* invalid size, pointer or option */
+  RCCSDT_ERR_OOM = -2,        /* device allocation failed */
+  RCCSDT_ERR_CUDA = -3,       /* a CUDA runtime or driver call failed */
+  RCCSDT_ERR_NONFINITE = -4,  /* NaN or Inf found in a residual norm or the energy */
+  RCCSDT_ERR_TIMEOUT = -5,    /* a device-side wait exceeded its watchdog budget */
+  RCCSDT_ERR_STATE = -6,      /* call made before the data it needs was set */
+  RCCSDT_NOT_CONVERGED = 1    /* rccsdt_solve reached max_iter */
+} rccsdt_status;
+
+typedef enum {
+  RCCSDT_FP64 = 0,            /* FP64 contractions (SIMT DFMA), FP64 T3 storage */
+  RCCSDT_SPLIT_BF16X3 = 1,    /* FP32 T3; large contractions as hi*hi + hi*lo + lo*hi in BF16
+                                 on tcgen05 with FP32 accumulation in TMEM */
+  RCCSDT_SPLIT_TF32X3 = 2     /* as above with TF32 halves */
+} rccsdt_precision;
+
+typedef struct {
+  int precision;          /* rccsdt_precision */
+  int final_fp64_iters;   /* split modes: last iterations of rccsdt_solve run in FP64 */
+  int diis_space;         /* DIIS history length M (0 = plain Jacobi) */
+  int diis_start;         /* first iteration (1-based) that extrapolates */
+  int diis_t3;            /* 1: DIIS vectors include T3; 0: T1 and T2 only */
+  int max_iter;           /* rccsdt_solve iteration cap */
+  double tol;             /* convergence threshold on the residual norm */
+  long long watchdog_cycles; /* clock64 budget of device-side waits (0 = default) */
+} rccsdt_options;
+
+/* Fills *opt with the defaults: FP64, final_fp64_iters 2, DIIS(8) from iteration 2
+ * including T3, max_iter 100, tol 1e-8. */
+int rccsdt_options_default(rccsdt_options* opt);
+
+/* Creates a context for o occupied / v virtual orbitals and naux factors, on the
+ * CUDA stream `stream` (a cudaStream_t, NULL = legacy default stream) of the
+ * current device.  Allocates all device memory the iteration needs.
+ * Errors: RCCSDT_ERR_ARG (o, v, naux < 1 or out == NULL), RCCSDT_ERR_OOM. */
+int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, void* stream,
+                  rccsdt_ctx** out);
+
+/* Bytes of device memory the context holds. */
+long long rccsdt_device_bytes(const rccsdt_ctx* ctx);
+
+/* Sets the Hamiltonian (appendix A.3): fock_diag[n], L[naux][n][n]. */
+int rccsdt_set_hamiltonian(rccsdt_ctx* ctx, const double* fock_diag, const double* L);
+
+/* Sets the amplitudes (float64 in every precision mode; stored as FP32 T3 in the
+ * split modes).  Any pointer may be NULL to leave that amplitude unchanged.
+ * Clears the DIIS history. */
+int rccsdt_set_amplitudes(rccsdt_ctx* ctx, const double* t1, const double* t2, const double* t3c);
+
+/* t1 = 0, t2 = first-order (MP2) doubles v^{ab}_{ij} / eps_ij^ab, t3 = 0. */
+int rccsdt_init_mp2(rccsdt_ctx* ctx);
+
+/* Switches the precision of later contractions (rccsdt_precision).  Changing
+ * between FP64 and a split mode converts the stored T3. */
+int rccsdt_set_precision(rccsdt_ctx* ctx, int precision);
+
+/* Step (i)-(iii) of one iteration: T1-dressing, the RCCSD and RCCSDT
+ * intermediates, and the T3 contributions to R1, R2, W^{ab}_{dj}, W^{al}_{ij}. */
+int rccsdt_build_intermediates(rccsdt_ctx* ctx);
+
+/* Steps (iv)-(v): R1, R2 and the raw compact R3 (requires the intermediates). */
+int rccsdt_residual(rccsdt_ctx* ctx);
+
+/* Symmetrise, purify and orthogonalise R3 (Sec. II.D) and return
+ * norms[4] = {|R1|, |R2|, |R3|, |R|}, |R3| the full-tensor norm
+ * (block multiplicities 6/3/1).  norms may be NULL. */
+int rccsdt_postprocess(rccsdt_ctx* ctx, double norms[4]);
+
+/* Jacobi step t += r / eps (bare Fock diagonal) for t1, t2, t3, then DIIS. */
+int rccsdt_update(rccsdt_ctx* ctx);
+
+/* Correlation energy of the current amplitudes (bare integrals). */
+int rccsdt_energy(rccsdt_ctx* ctx, double* e_corr);
+
+/* One whole iteration: energy of the current amplitudes, intermediates,
+ * residuals, post-processing, update.  e_corr and norms (as above) describe the
+ * amplitudes the residual was evaluated at; either may be NULL. */
+int rccsdt_iterate(rccsdt_ctx* ctx, double* e_corr, double norms[4]);
+
+/* Iterates from the current amplitudes until |R| <= tol or max_iter.  In the
+ * split modes the iterations run in split precision until |R| <= sqrt(tol); from
+ * then on they run in FP64 (iterative refinement), and convergence is only
+ * accepted on an FP64 iteration.  Outputs describe the last residual evaluated.
+ * Returns RCCSDT_NOT_CONVERGED if max_iter is reached. */
+int rccsdt_solve(rccsdt_ctx* ctx, double* e_corr, int* iterations, double* final_norm);
+
+/* Copies out the amplitudes / the current residuals (float64). NULL skips. */
+int rccsdt_get_amplitudes(rccsdt_ctx* ctx, double* t1, double* t2, double* t3c);
+int rccsdt_get_residuals(rccsdt_ctx* ctx, double* r1, double* r2, double* r3c);
+
+/* Leading algorithmic FMA count of the compact contractions of one iteration,
+ * n3 (3 v^5 + 12 o v^4 + 3 o^2 v^3) (operation-count table). */
+double rccsdt_iteration_fma(int o, int v);
+
+/* Per-step device times (milliseconds) of the last rccsdt_iterate, measured with
+ * CUDA events on the context's stream when timing is enabled.  Order of the
+ * entries: intermediates, pp-ladder, ring, hh-ladder, t2 terms, other R3,
+ * postprocess, update, energy.  Returns the number written (<= cap). */
+int rccsdt_step_times(rccsdt_ctx* ctx, double* ms, int cap);
+int rccsdt_enable_timing(rccsdt_ctx* ctx, int on);
+
+/* Diagnostic: copies the first `count` float64 values of a named internal tensor
+ * (e.g. "Fvv", "Wvvvo", "Wvvvv", "Wb_ovov", "r1", "X2") to `out`.  Layouts are the
+ * index orders of the paper's symbols, upper indices first.  RCCSDT_ERR_ARG for
+ * an unknown name or a count beyond the tensor. */
+int rccsdt_debug_copy(rccsdt_ctx* ctx, const char* name, double* out, long long count);
+
+const char* rccsdt_last_error(const rccsdt_ctx* ctx);
+void rccsdt_destroy(rccsdt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCCSDT_H */

@@ -1,0 +1,196 @@
+"""Thin ctypes binding of the C ABI declared in ``include/rccsdt.h``.
+
+Argument marshalling only: every step of the iteration runs in the CUDA
+library.  Array arguments may be numpy arrays (host memory) or CUDA torch
+tensors (device memory); both must be contiguous float64.  Functions keep the
+C names without the ``rccsdt_`` prefix.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_NAME = "librccsdt.so"
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, NOT_CONVERGED = 0, -1, -2, -3, -4, -5, -6, 1
+FP64, SPLIT_BF16X3, SPLIT_TF32X3 = 0, 1, 2
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("final_fp64_iters", C.c_int), ("diis_space", C.c_int),
+                ("diis_start", C.c_int), ("diis_t3", C.c_int), ("max_iter", C.c_int),
+                ("tol", C.c_double), ("watchdog_cycles", C.c_longlong)]
+
+
+class RccsdtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"rccsdt status {status}: {msg}")
+        self.status = status
+
+
+_P = C.c_void_p
+_SIGS = {
+    "rccsdt_options_default": (C.c_int, [C.POINTER(Options)]),
+    "rccsdt_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(Options), _P, C.POINTER(_P)]),
+    "rccsdt_device_bytes": (C.c_longlong, [_P]),
+    "rccsdt_set_hamiltonian": (C.c_int, [_P, _P, _P]),
+    "rccsdt_set_amplitudes": (C.c_int, [_P, _P, _P, _P]),
+    "rccsdt_init_mp2": (C.c_int, [_P]),
+    "rccsdt_set_precision": (C.c_int, [_P, C.c_int]),
+    "rccsdt_build_intermediates": (C.c_int, [_P]),
+    "rccsdt_residual": (C.c_int, [_P]),
+    "rccsdt_postprocess": (C.c_int, [_P, _P]),
+    "rccsdt_update": (C.c_int, [_P]),
+    "rccsdt_energy": (C.c_int, [_P, _P]),
+    "rccsdt_iterate": (C.c_int, [_P, _P, _P]),
+    "rccsdt_solve": (C.c_int, [_P, _P, _P, _P]),
+    "rccsdt_get_amplitudes": (C.c_int, [_P, _P, _P, _P]),
+    "rccsdt_get_residuals": (C.c_int, [_P, _P, _P, _P]),
+    "rccsdt_debug_copy": (C.c_int, [_P, C.c_char_p, _P, C.c_longlong]),
+    "rccsdt_iteration_fma": (C.c_double, [C.c_int, C.c_int]),
+    "rccsdt_step_times": (C.c_int, [_P, _P, C.c_int]),
+    "rccsdt_enable_timing": (C.c_int, [_P, C.c_int]),
+    "rccsdt_last_error": (C.c_char_p, [_P]),
+    "rccsdt_destroy": (None, [_P]),
+}
+
+
+def load_library(path: str) -> C.CDLL:
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+def _ptr(x):
+    """Raw pointer of a contiguous float64 numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous float64")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("tensors must be contiguous float64")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def default_options(lib, **kw) -> Options:
+    opt = Options()
+    lib.rccsdt_options_default(C.byref(opt))
+    for k, val in kw.items():
+        setattr(opt, k, val)
+    return opt
+
+
+class Context:
+    """One RCCSDT problem (o occupied, v virtual spatial orbitals, naux factors)."""
+
+    def __init__(self, lib, o: int, v: int, naux: int, stream: int = 0, **options):
+        self.lib, self.o, self.v, self.naux = lib, o, v, naux
+        self.n3 = o * (o + 1) * (o + 2) // 6
+        self.options = default_options(lib, **options)
+        h = _P()
+        st = lib.rccsdt_create(o, v, naux, C.byref(self.options), _P(stream) if stream else None, C.byref(h))
+        if st != OK:
+            raise RccsdtError(st, "rccsdt_create failed")
+        self.h = h
+
+    def _check(self, st, allow=(OK,)):
+        if st not in allow:
+            raise RccsdtError(st, self.lib.rccsdt_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rccsdt_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def device_bytes(self) -> int:
+        return self.lib.rccsdt_device_bytes(self.h)
+
+    def set_hamiltonian(self, fock_diag, L):
+        self._check(self.lib.rccsdt_set_hamiltonian(self.h, _ptr(fock_diag), _ptr(L)))
+
+    def set_amplitudes(self, t1=None, t2=None, t3c=None):
+        self._check(self.lib.rccsdt_set_amplitudes(self.h, _ptr(t1), _ptr(t2), _ptr(t3c)))
+
+    def init_mp2(self):
+        self._check(self.lib.rccsdt_init_mp2(self.h))
+
+    def set_precision(self, precision: int):
+        self._check(self.lib.rccsdt_set_precision(self.h, precision))
+
+    def build_intermediates(self):
+        self._check(self.lib.rccsdt_build_intermediates(self.h))
+
+    def residual(self):
+        self._check(self.lib.rccsdt_residual(self.h))
+
+    def postprocess(self):
+        norms = np.zeros(4)
+        self._check(self.lib.rccsdt_postprocess(self.h, norms.ctypes.data))
+        return norms
+
+    def update(self):
+        self._check(self.lib.rccsdt_update(self.h))
+
+    def energy(self) -> float:
+        e = np.zeros(1)
+        self._check(self.lib.rccsdt_energy(self.h, e.ctypes.data))
+        return float(e[0])
+
+    def iterate(self):
+        e = np.zeros(1)
+        norms = np.zeros(4)
+        self._check(self.lib.rccsdt_iterate(self.h, e.ctypes.data, norms.ctypes.data))
+        return float(e[0]), norms
+
+    def solve(self):
+        e = np.zeros(1)
+        it = C.c_int(0)
+        nrm = np.zeros(1)
+        st = self._check(self.lib.rccsdt_solve(self.h, e.ctypes.data, C.addressof(it), nrm.ctypes.data),
+                         allow=(OK, NOT_CONVERGED))
+        return float(e[0]), it.value, float(nrm[0]), st == OK
+
+    def get_amplitudes(self, t1=None, t2=None, t3c=None):
+        self._check(self.lib.rccsdt_get_amplitudes(self.h, _ptr(t1), _ptr(t2), _ptr(t3c)))
+
+    def get_residuals(self, r1=None, r2=None, r3c=None):
+        self._check(self.lib.rccsdt_get_residuals(self.h, _ptr(r1), _ptr(r2), _ptr(r3c)))
+
+    def amplitudes(self):
+        o, v = self.o, self.v
+        t1, t2, t3 = np.empty((o, v)), np.empty((o, o, v, v)), np.empty((self.n3, v, v, v))
+        self.get_amplitudes(t1, t2, t3)
+        return t1, t2, t3
+
+    def residuals(self):
+        o, v = self.o, self.v
+        r1, r2, r3 = np.empty((o, v)), np.empty((o, o, v, v)), np.empty((self.n3, v, v, v))
+        self.get_residuals(r1, r2, r3)
+        return r1, r2, r3
+
+    def debug_copy(self, name: str, shape):
+        out = np.empty(shape)
+        self._check(self.lib.rccsdt_debug_copy(self.h, name.encode(), out.ctypes.data, out.size))
+        return out
+
+    def enable_timing(self, on=True):
+        self._check(self.lib.rccsdt_enable_timing(self.h, 1 if on else 0))
+
+    def step_times(self):
+        ms = np.zeros(16)
+        n = self.lib.rccsdt_step_times(self.h, ms.ctypes.data, 16)
+        return ms[:n]

@@ -1,0 +1,44 @@
+// Shared device-side definitions of the RCCSDT kernels (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+namespace rcc {
+
+typedef long long i64;
+
+// Operand storage of packed GEMM panels.
+enum PanelKind : int { PANEL_F64 = 0, PANEL_BF16X2 = 1, PANEL_TF32X2 = 2 };
+
+// A packed panel out[r][k] (row-major, k contiguous) is gathered as
+//   out[r][k] = sum_{t < nterm} coef[t*K + k] * src[colbase[t*K + k] + rowoff[sel[t*K + k]*R + r]]
+// which covers strided views of dense tensors (nterm = 1, one selector) and
+// permuted/spin-summed reads of compact T3 blocks (selector = virtual permutation).
+struct PackArgs {
+  const void* src;       // double or float
+  int src_f32;           // 1: src is float
+  int R, K, nterm;
+  const double* coef;    // [nterm][K]
+  const i64* colbase;    // [nterm][K]
+  const int* sel;        // [nterm][K]
+  const i64* rowoff;     // [nsel][R]
+  int kind;              // PanelKind of the output
+  void* out_hi;          // [R][Kpad] double / bf16 / float(tf32)
+  void* out_lo;          // [R][Kpad] second half of a split (unused for F64)
+  int Kpad;              // leading dimension of the output (>= K, zero filled)
+  int read_k_fast;       // 1: source contiguous along k, 0: along r
+};
+
+// Table-driven epilogue: C[row_base[m] + col_off[row_sel[m]*N + n]] += row_alpha[m] * acc(m, n)
+struct EpiArgs {
+  void* C;               // double or float
+  int c_f32;
+  int M, N;
+  const i64* row_base;   // [M]
+  const int* row_sel;    // [M]
+  const double* row_alpha; // [M]
+  const i64* col_off;    // [nsel][N]
+};
+
+}  // namespace rcc

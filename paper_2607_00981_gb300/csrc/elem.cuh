@@ -1,0 +1,99 @@
+// Per-element arithmetic shared by the device kernels and by the test-only host
+// simulation build (RCC_HOSTSIM), so both execute the same plans.
+#pragma once
+#include "common.cuh"
+
+#define RCC_HD __host__ __device__ __forceinline__
+
+namespace rcc {
+
+RCC_HD double load_src(const void* p, int f32, i64 off) {
+  return f32 ? (double)((const float*)p)[off] : ((const double*)p)[off];
+}
+
+// Round-to-nearest, ties away from zero, to the 10-bit TF32 mantissa, done on the
+// integer representation (finite inputs).  Returns the value as a float.
+RCC_HD float tf32_round(float x) {
+  union { float f; unsigned u; } c;
+  c.f = x;
+  c.u = (c.u + 0x1000u) & 0xffffe000u;
+  return c.f;
+}
+
+RCC_HD double pack_value(const PackArgs& a, int r, int k) {
+  double s = 0.0;
+  for (int t = 0; t < a.nterm; ++t) {
+    const i64 idx = (i64)t * a.K + k;
+    const double c = a.coef[idx];
+    if (c != 0.0) {
+      const i64 off = a.colbase[idx] + a.rowoff[(i64)a.sel[idx] * a.R + r];
+      s += c * load_src(a.src, a.src_f32, off);
+    }
+  }
+  return s;
+}
+
+RCC_HD void store_panel(const PackArgs& a, int r, int k, double x) {
+  const i64 o = (i64)r * a.Kpad + k;
+  if (a.kind == PANEL_F64) {
+    ((double*)a.out_hi)[o] = x;
+  } else if (a.kind == PANEL_BF16X2) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+    const double rem = x - (double)__bfloat162float(hi);
+    ((__nv_bfloat16*)a.out_hi)[o] = hi;
+    ((__nv_bfloat16*)a.out_lo)[o] = __float2bfloat16_rn((float)rem);
+  } else {
+    const float hi = tf32_round((float)x);
+    ((float*)a.out_hi)[o] = hi;
+    ((float*)a.out_lo)[o] = tf32_round((float)(x - (double)hi));
+  }
+}
+
+RCC_HD void epi_apply(const EpiArgs& e, int m, int n, double acc) {
+  const i64 addr = e.row_base[m] + e.col_off[(i64)e.row_sel[m] * e.N + n];
+  const double val = e.row_alpha[m] * acc;
+  if (e.c_f32)
+    ((float*)e.C)[addr] += (float)val;
+  else
+    ((double*)e.C)[addr] += val;
+}
+
+// ---------------------------------------------------------------------------
+// Compact-block helpers.  blk(i<=j<=k) = C(k+2,3) + C(j+1,2) + i.
+// ---------------------------------------------------------------------------
+RCC_HD i64 blk_index(int i, int j, int k) {
+  return (i64)k * (k + 1) * (k + 2) / 6 + (i64)j * (j + 1) / 2 + i;
+}
+
+// Virtual element offset inside a v^3 block for labels (x0, x1, x2) of one
+// triple, given the stored-axis position of each label: pos[q] = stored axis
+// that label q lands on.
+RCC_HD i64 perm_offset(int v, const int* pos, int x0, int x1, int x2) {
+  i64 s[3];
+  s[0] = (i64)v * v; s[1] = v; s[2] = 1;
+  return s[pos[0]] * x0 + s[pos[1]] * x1 + s[pos[2]] * x2;
+}
+
+// Post-processing of one element of a compact R3 block (Sec. II.D):
+// symmetrise degenerate blocks, purify i=j=k, subtract the S3 mean.
+// r points at the block; returns the processed value at (a, b, c).
+template <typename T>
+RCC_HD double post_value(const T* r, int v, int i, int j, int k, int a, int b, int c) {
+  if (i == j && j == k) return 0.0;
+  const i64 V2 = (i64)v * v;
+  const double rabc = r[a * V2 + b * v + c], racb = r[a * V2 + c * v + b];
+  const double rbac = r[b * V2 + a * v + c], rbca = r[b * V2 + c * v + a];
+  const double rcab = r[c * V2 + a * v + b], rcba = r[c * V2 + b * v + a];
+  double s;
+  if (i == j)
+    s = 0.5 * (rabc + rbac);
+  else if (j == k)
+    s = 0.5 * (rabc + racb);
+  else
+    s = rabc;
+  // the symmetrisations above keep the sum over the six permutations unchanged
+  const double mean = (rabc + racb + rbac + rbca + rcab + rcba) * (1.0 / 6.0);
+  return s - mean;
+}
+
+}  // namespace rcc

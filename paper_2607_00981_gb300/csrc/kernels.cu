@@ -1,0 +1,505 @@
+// Bandwidth-bound and FP64 kernels of the RCCSDT iteration (sm_103a).
+//
+//  k_pack        strided / permuted / spin-summed gather of a GEMM operand panel
+//                (the "unpacking" of Sec. II.C.2), optionally split into hi/lo halves
+//  k_gemm_f64    FP64 DFMA GEMM C += A B^T with the table-driven scatter epilogue
+//  k_combine     out = beta*out + sum_t c_t in_t[perm_t(idx)] on dense tensors <= rank 6
+//  k_post        symmetrise / purify / orthogonalise compact R3 (Sec. II.D)
+//  k_update_*    Jacobi step t += r / eps (appendix A.1)
+//  k_wdot, k_sum deterministic weighted dot products (norms, DIIS B matrix)
+//  k_t2_outer    the K = o part of the T2-driven R3 terms, all six permutations
+//  k_diis_*      DIIS bordered solve and extrapolation (Sec. III.A.4)
+#include "elem.cuh"
+#include "kernels.h"
+
+namespace rcc {
+
+// ---------------------------------------------------------------------------
+// Panel gather.  32 x 32 tile per block of 32 x 8 threads; reads go along the
+// source's contiguous direction, writes along k (the output's contiguous axis).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_pack(PackArgs a) {
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  if (a.read_k_fast) {
+    for (int rr = ty; rr < 32; rr += 8) {
+      const int r = r0 + rr, k = k0 + tx;
+      if (r < a.R && k < a.Kpad) store_panel(a, r, k, k < a.K ? pack_value(a, r, k) : 0.0);
+    }
+  } else {
+    for (int kk = ty; kk < 32; kk += 8) {
+      const int r = r0 + tx, k = k0 + kk;
+      tile[kk][tx] = (r < a.R && k < a.K) ? pack_value(a, r, k) : 0.0;
+    }
+    __syncthreads();
+    for (int rr = ty; rr < 32; rr += 8) {
+      const int r = r0 + rr, k = k0 + tx;
+      if (r < a.R && k < a.Kpad) store_panel(a, r, k, tile[tx][rr]);
+    }
+  }
+}
+
+void launch_pack(const PackArgs& a, cudaStream_t s) {
+  dim3 grid((a.Kpad + 31) / 32, (a.R + 31) / 32), block(32, 8);
+  k_pack<<<grid, block, 0, s>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 GEMM, C[m, n] += alpha[m] * sum_k A[m, k] B[n, k]; A [M][lda], B [N][ldb]
+// (k contiguous, zero padded to a multiple of 16).  64 x 64 tile, 4 x 4 per thread.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A,
+                                                  const double* __restrict__ B, int K, int lda,
+                                                  int ldb, EpiArgs e) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int lrow = tid >> 2, lk = (tid & 3) * 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const int am = m0 + lrow, bn = n0 + lrow;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      As[lk + q][lrow] = am < e.M ? A[(i64)am * lda + k0 + lk + q] : 0.0;
+      Bs[lk + q][lrow] = bn < e.N ? B[(i64)bn * ldb + k0 + lk + q] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= e.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n < e.N) epi_apply(e, m, n, acc[i][j]);
+    }
+  }
+}
+
+void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, const EpiArgs& e,
+                     cudaStream_t s) {
+  dim3 grid((e.N + 63) / 64, (e.M + 63) / 64);
+  k_gemm_f64<<<grid, 256, 0, s>>>(A, B, K, lda, ldb, e);
+}
+
+// ---------------------------------------------------------------------------
+// Dense permuted linear combination.
+// ---------------------------------------------------------------------------
+__global__ void k_combine(CombineArgs c) {
+  const i64 total = c.total;
+  for (i64 idx = blockIdx.x * (i64)blockDim.x + threadIdx.x; idx < total;
+       idx += (i64)gridDim.x * blockDim.x) {
+    i64 rem = idx, ooff = 0;
+    i64 ioff[4] = {0, 0, 0, 0};
+    for (int d = c.rank - 1; d >= 0; --d) {
+      const i64 x = rem % c.shape[d];
+      rem /= c.shape[d];
+      ooff += x * c.ostride[d];
+      for (int t = 0; t < c.nterm; ++t) ioff[t] += x * c.istride[t][d];
+    }
+    double s = c.beta == 0.0 ? 0.0 : c.beta * c.out[ooff];
+    for (int t = 0; t < c.nterm; ++t) s += c.coef[t] * c.in[t][ioff[t]];
+    c.out[ooff] = s;
+  }
+}
+
+void launch_combine(const CombineArgs& c, cudaStream_t s) {
+  if (c.total <= 0) return;
+  i64 blocks = (c.total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_combine<<<(unsigned)blocks, 256, 0, s>>>(c);
+}
+
+// ---------------------------------------------------------------------------
+// R3 post-processing: rp[blk] = post(r[blk]).  One thread per element, grid-
+// stride over blocks; reads of the permuted partners hit L2.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_post(const T* __restrict__ r, T* __restrict__ rp, const int4* __restrict__ blocks,
+                       int v, i64 n3) {
+  const i64 V3 = (i64)v * v * v;
+  for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
+    const int4 ijk = blocks[b];
+    const T* rb = r + b * V3;
+    for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < V3; e += (i64)gridDim.x * blockDim.x) {
+      const int c = (int)(e % v), bb = (int)((e / v) % v), a = (int)(e / ((i64)v * v));
+      rp[b * V3 + e] = (T)post_value(rb, v, ijk.x, ijk.y, ijk.z, a, bb, c);
+    }
+  }
+}
+
+template <typename T>
+void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStream_t s) {
+  const i64 V3 = (i64)v * v * v;
+  unsigned gx = (unsigned)((V3 + 255) / 256);
+  if (gx > 64) gx = 64;
+  unsigned gy = (unsigned)(n3 < 1024 ? n3 : 1024);
+  k_post<T><<<dim3(gx, gy), 256, 0, s>>>(r, rp, blocks, v, n3);
+}
+template void launch_post<double>(const double*, double*, const int4*, int, i64, cudaStream_t);
+template void launch_post<float>(const float*, float*, const int4*, int, i64, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Jacobi updates with the bare Fock diagonal (orbital energies e[0..n)).
+// ---------------------------------------------------------------------------
+__global__ void k_update_t1(double* t1, const double* r1, const double* e, int o, int v, double shift) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= o * v) return;
+  const int i = idx / v, a = idx % v;
+  t1[idx] += r1[idx] / (e[i] - e[o + a] - shift);
+}
+
+__global__ void k_update_t2(double* t2, const double* r2, const double* e, int o, int v, double shift) {
+  const i64 n = (i64)o * o * v * v;
+  for (i64 idx = blockIdx.x * (i64)blockDim.x + threadIdx.x; idx < n; idx += (i64)gridDim.x * blockDim.x) {
+    const int b = (int)(idx % v), a = (int)((idx / v) % v);
+    const int j = (int)((idx / ((i64)v * v)) % o), i = (int)(idx / ((i64)v * v * o));
+    t2[idx] += r2[idx] / (e[i] + e[j] - e[o + a] - e[o + b] - shift);
+  }
+}
+
+template <typename T>
+__global__ void k_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, int o, int v,
+                            i64 n3, double shift) {
+  const i64 V3 = (i64)v * v * v;
+  for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
+    const int4 ijk = blocks[b];
+    const double eo = e[ijk.x] + e[ijk.y] + e[ijk.z];
+    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < V3; x += (i64)gridDim.x * blockDim.x) {
+      const int c = (int)(x % v), bb = (int)((x / v) % v), a = (int)(x / ((i64)v * v));
+      const double d = eo - e[o + a] - e[o + bb] - e[o + c] - shift;
+      const i64 g = b * V3 + x;
+      t3[g] = (T)((double)t3[g] + (double)rp3[g] / d);
+    }
+  }
+}
+
+void launch_update_t12(double* t1, const double* r1, double* t2, const double* r2, const double* e,
+                       int o, int v, double shift, cudaStream_t s) {
+  k_update_t1<<<(o * v + 255) / 256, 256, 0, s>>>(t1, r1, e, o, v, shift);
+  const i64 n = (i64)o * o * v * v;
+  i64 blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_update_t2<<<(unsigned)blocks, 256, 0, s>>>(t2, r2, e, o, v, shift);
+}
+
+template <typename T>
+void launch_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, int o, int v, i64 n3,
+                      double shift, cudaStream_t s) {
+  const i64 V3 = (i64)v * v * v;
+  unsigned gx = (unsigned)((V3 + 255) / 256);
+  if (gx > 64) gx = 64;
+  unsigned gy = (unsigned)(n3 < 1024 ? n3 : 1024);
+  k_update_t3<T><<<dim3(gx, gy), 256, 0, s>>>(t3, rp3, e, blocks, o, v, n3, shift);
+}
+template void launch_update_t3<double>(double*, const double*, const double*, const int4*, int, int,
+                                       i64, double, cudaStream_t);
+template void launch_update_t3<float>(float*, const float*, const double*, const int4*, int, int, i64,
+                                      double, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Deterministic weighted dot products: sum_i x[i] y[i] w[i / seg] (w NULL = 1).
+// Stage 1 writes one partial per block (fixed grid), stage 2 sums in order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__device__ __forceinline__ double block_sum(double x) {
+  __shared__ double ws[32];
+  x = warp_sum(x);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) ws[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    x = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+    x = warp_sum(x);
+  }
+  return x;
+}
+
+template <typename T>
+__global__ void k_wdot(const T* __restrict__ x, const T* __restrict__ y, i64 n, i64 seg,
+                       const double* __restrict__ w, double* __restrict__ partial) {
+  double s = 0.0;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    double p = (double)x[i] * (double)y[i];
+    if (w) p *= w[i / seg];
+    s += p;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_sum(const double* __restrict__ partial, int np, double* __restrict__ out, double scale,
+                      int accumulate) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = (accumulate ? *out : 0.0) + scale * s;
+}
+
+template <typename T>
+void launch_wdot(const T* x, const T* y, i64 n, i64 seg, const double* w, double* partial,
+                 double* out, double scale, int accumulate, cudaStream_t s) {
+  k_wdot<T><<<kDotBlocks, 256, 0, s>>>(x, y, n, seg, w, partial);
+  k_sum<<<1, 256, 0, s>>>(partial, kDotBlocks, out, scale, accumulate);
+}
+template void launch_wdot<double>(const double*, const double*, i64, i64, const double*, double*,
+                                  double*, double, int, cudaStream_t);
+template void launch_wdot<float>(const float*, const float*, i64, i64, const double*, double*, double*,
+                                 double, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// K = o part of the T2-driven R3 terms (Eq. resi-rccsdt, first line), all six
+// column permutations of -sum_l W^{a1 l}_{i1 i2} t_{l i3}^{a2 a3} for each
+// stored element.  Wvooo[a][l][i][j] = W^{al}_{ij}; t2[l][k][b][c].
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_t2_outer(T* __restrict__ r3, const double* __restrict__ Wvooo,
+                           const double* __restrict__ t2, const int4* __restrict__ blocks, int o, int v,
+                           i64 n3) {
+  const i64 V3 = (i64)v * v * v;
+  for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
+    const int4 ijk = blocks[b];
+    const int occ[3] = {ijk.x, ijk.y, ijk.z};
+    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < V3; x += (i64)gridDim.x * blockDim.x) {
+      const int lab[3] = {(int)(x / ((i64)v * v)), (int)((x / v) % v), (int)(x % v)};
+      double s = 0.0;
+      // permutations p: positions (p0, p1, p2) take the roles (1, 2, 3)
+      const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const int i1 = occ[P[q][0]], i2 = occ[P[q][1]], i3 = occ[P[q][2]];
+        const int a1 = lab[P[q][0]], a2 = lab[P[q][1]], a3 = lab[P[q][2]];
+        const double* W = Wvooo + (((i64)a1 * o) * o + i1) * o + i2;       // stride o*o over l
+        const double* t = t2 + ((i64)i3 * v + a2) * v + a3;                  // stride o*v*v over l
+        for (int l = 0; l < o; ++l) s -= W[(i64)l * o * o] * t[(i64)l * o * v * v];
+      }
+      const i64 g = b * V3 + x;
+      r3[g] = (T)((double)r3[g] + s);
+    }
+  }
+}
+
+template <typename T>
+void launch_t2_outer(T* r3, const double* Wvooo, const double* t2, const int4* blocks, int o, int v,
+                     i64 n3, cudaStream_t s) {
+  const i64 V3 = (i64)v * v * v;
+  unsigned gx = (unsigned)((V3 + 255) / 256);
+  if (gx > 64) gx = 64;
+  unsigned gy = (unsigned)(n3 < 1024 ? n3 : 1024);
+  k_t2_outer<T><<<dim3(gx, gy), 256, 0, s>>>(r3, Wvooo, t2, blocks, o, v, n3);
+}
+template void launch_t2_outer<double>(double*, const double*, const double*, const int4*, int, int, i64,
+                                      cudaStream_t);
+template void launch_t2_outer<float>(float*, const double*, const double*, const int4*, int, int, i64,
+                                     cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// DIIS: B is (M+1) x (M+1) row-major in scalars; solve the bordered system with
+// partial-pivoting Gaussian elimination; a pivot below tiny * max|B| drops that
+// direction (coefficient 0), the least-squares limit for a singular B.
+// ---------------------------------------------------------------------------
+__global__ void k_diis_solve(const double* __restrict__ Bmat, int m, int ld, double* __restrict__ coef) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double A[17][18];
+  const int n = m + 1;
+  double scale = 0.0;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) scale = fmax(scale, fabs(Bmat[i * ld + j]));
+  if (scale == 0.0) scale = 1.0;
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) {
+      double x;
+      if (i < m && j < m) x = Bmat[i * ld + j] / scale;
+      else if (i == m && j == m) x = 0.0;
+      else x = 1.0;
+      A[i][j] = x;
+    }
+    A[i][n] = (i == m) ? 1.0 : 0.0;
+  }
+  int piv_ok[17];
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int i = c + 1; i < n; ++i)
+      if (fabs(A[i][c]) > fabs(A[p][c])) p = i;
+    if (p != c)
+      for (int j = 0; j <= n; ++j) { double t = A[c][j]; A[c][j] = A[p][j]; A[p][j] = t; }
+    piv_ok[c] = fabs(A[c][c]) > 1e-14;
+    if (!piv_ok[c]) continue;
+    for (int i = c + 1; i < n; ++i) {
+      const double f = A[i][c] / A[c][c];
+      for (int j = c; j <= n; ++j) A[i][j] -= f * A[c][j];
+    }
+  }
+  double x[17];
+  for (int c = n - 1; c >= 0; --c) {
+    if (!piv_ok[c]) { x[c] = 0.0; continue; }
+    double s = A[c][n];
+    for (int j = c + 1; j < n; ++j) s -= A[c][j] * x[j];
+    x[c] = s / A[c][c];
+  }
+  for (int i = 0; i < m; ++i) coef[i] = x[i];
+}
+
+void launch_diis_solve(const double* B, int m, int ld, double* coef, cudaStream_t s) {
+  k_diis_solve<<<1, 32, 0, s>>>(B, m, ld, coef);
+}
+
+// out[i] = sum_m coef[m] * hist[m][i] (hist slots stride `stride` elements)
+template <typename T>
+__global__ void k_diis_extrapolate(T* __restrict__ out, const T* __restrict__ hist, i64 stride, i64 n,
+                                   const double* __restrict__ coef, int m) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < m; ++q) s += coef[q] * (double)hist[q * stride + i];
+    out[i] = (T)s;
+  }
+}
+
+template <typename T>
+void launch_diis_extrapolate(T* out, const T* hist, i64 stride, i64 n, const double* coef, int m,
+                             cudaStream_t s) {
+  if (n <= 0) return;
+  i64 blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_diis_extrapolate<T><<<(unsigned)blocks, 256, 0, s>>>(out, hist, stride, n, coef, m);
+}
+template void launch_diis_extrapolate<double>(double*, const double*, i64, i64, const double*, int,
+                                              cudaStream_t);
+template void launch_diis_extrapolate<float>(float*, const float*, i64, i64, const double*, int,
+                                             cudaStream_t);
+
+// e = a - b (DIIS error vector), elementwise
+template <typename T>
+__global__ void k_sub(T* __restrict__ out, const T* __restrict__ a, const T* __restrict__ b, i64 n) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    out[i] = (T)((double)a[i] - (double)b[i]);
+}
+template <typename T>
+void launch_sub(T* out, const T* a, const T* b, i64 n, cudaStream_t s) {
+  if (n <= 0) return;
+  i64 blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_sub<T><<<(unsigned)blocks, 256, 0, s>>>(out, a, b, n);
+}
+template void launch_sub<double>(double*, const double*, const double*, i64, cudaStream_t);
+template void launch_sub<float>(float*, const float*, const float*, i64, cudaStream_t);
+
+// Type conversion between FP64 and FP32 storage.
+template <typename TO, typename TI>
+__global__ void k_convert(TO* __restrict__ out, const TI* __restrict__ in, i64 n) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+template <typename TO, typename TI>
+void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t s) {
+  if (n <= 0) return;
+  i64 blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_convert<TO, TI><<<(unsigned)blocks, 256, 0, s>>>(out, in, n);
+}
+template void launch_convert<float, double>(float*, const double*, i64, cudaStream_t);
+template void launch_convert<double, float>(double*, const float*, i64, cudaStream_t);
+template void launch_convert<double, double>(double*, const double*, i64, cudaStream_t);
+
+}  // namespace rcc
+
+namespace rcc {
+
+__global__ void k_energy(const double* __restrict__ g, const double* __restrict__ t1,
+                         const double* __restrict__ t2, int o, int v, double* __restrict__ partial) {
+  const i64 total = (i64)o * o * v * v;
+  double s = 0.0;
+  for (i64 idx = blockIdx.x * (i64)blockDim.x + threadIdx.x; idx < total; idx += (i64)gridDim.x * blockDim.x) {
+    const int b = (int)(idx % v), a = (int)((idx / v) % v);
+    const int j = (int)((idx / ((i64)v * v)) % o), i = (int)(idx / ((i64)v * v * o));
+    const double giajb = g[(((i64)i * v + a) * o + j) * v + b];
+    const double gibja = g[(((i64)i * v + b) * o + j) * v + a];
+    s += (2.0 * giajb - gibja) * (t2[idx] + t1[i * v + a] * t1[j * v + b]);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+void launch_energy(const double* g, const double* t1, const double* t2, int o, int v, double* partial,
+                   double* out, cudaStream_t s) {
+  k_energy<<<kDotBlocks, 256, 0, s>>>(g, t1, t2, o, v, partial);
+  k_sum<<<1, 256, 0, s>>>(partial, kDotBlocks, out, 1.0, 0);
+}
+
+__global__ void k_mp2(double* __restrict__ t2, const double* __restrict__ g, const double* __restrict__ e, int o,
+                      int v) {
+  const i64 total = (i64)o * o * v * v;
+  for (i64 idx = blockIdx.x * (i64)blockDim.x + threadIdx.x; idx < total; idx += (i64)gridDim.x * blockDim.x) {
+    const int b = (int)(idx % v), a = (int)((idx / v) % v);
+    const int j = (int)((idx / ((i64)v * v)) % o), i = (int)(idx / ((i64)v * v * o));
+    t2[idx] = g[(((i64)i * v + a) * o + j) * v + b] / (e[i] + e[j] - e[o + a] - e[o + b]);
+  }
+}
+
+void launch_mp2(double* t2, const double* g, const double* e, int o, int v, cudaStream_t s) {
+  const i64 total = (i64)o * o * v * v;
+  i64 blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_mp2<<<(unsigned)blocks, 256, 0, s>>>(t2, g, e, o, v);
+}
+
+__global__ void k_unpack_spin(const void* __restrict__ t3, int f32, int ntrip, const i64* __restrict__ base,
+                              const int* __restrict__ pos, int v, double* __restrict__ S,
+                              double* __restrict__ D) {
+  const i64 V3 = (i64)v * v * v;
+  for (int t = blockIdx.y; t < ntrip; t += gridDim.y) {
+    const i64 b0 = base[t];
+    const i64 sv[3] = {(i64)v * v, v, 1};
+    const i64 s0 = sv[pos[3 * t + 0]], s1 = sv[pos[3 * t + 1]], s2 = sv[pos[3 * t + 2]];
+    for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < V3; e += (i64)gridDim.x * blockDim.x) {
+      const int c = (int)(e % v), b = (int)((e / v) % v), a = (int)(e / ((i64)v * v));
+      // U^{xyz} = stored[x s0 + y s1 + z s2]
+#define UU(x, y, z) load_src(t3, f32, b0 + (i64)(x) * s0 + (i64)(y) * s1 + (i64)(z) * s2)
+      const double uabc = UU(a, b, c), ubac = UU(b, a, c), ucba = UU(c, b, a);
+      if (S) S[(i64)t * V3 + e] = 2.0 * uabc - ubac - ucba;
+      if (D) {
+        const double uacb = UU(a, c, b), ucab = UU(c, a, b), ubca = UU(b, c, a);
+        D[(i64)t * V3 + e] = 4.0 * uabc - 2.0 * ubac - 2.0 * ucba - 2.0 * uacb + ucab + ubca;
+      }
+#undef UU
+    }
+  }
+}
+
+void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, double* S,
+                        double* D, cudaStream_t s) {
+  const i64 V3 = (i64)v * v * v;
+  unsigned gx = (unsigned)((V3 + 255) / 256);
+  if (gx > 32) gx = 32;
+  unsigned gy = (unsigned)(ntrip < 1024 ? ntrip : 1024);
+  k_unpack_spin<<<dim3(gx, gy), 256, 0, s>>>(t3, f32, ntrip, base, pos, v, S, D);
+}
+
+}  // namespace rcc

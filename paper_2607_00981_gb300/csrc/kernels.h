@@ -1,0 +1,66 @@
+// Launch wrappers of the RCCSDT kernels (host-callable).
+#pragma once
+#include "common.cuh"
+
+namespace rcc {
+
+constexpr int kDotBlocks = 608;  // 4 x 152 SMs, fixed so reductions are deterministic
+
+struct CombineArgs {
+  double* out;
+  i64 total;
+  int rank;
+  i64 shape[6];
+  i64 ostride[6];
+  int nterm;
+  const double* in[4];
+  i64 istride[4][6];
+  double coef[4];
+  double beta;
+};
+
+void launch_pack(const PackArgs& a, cudaStream_t s);
+void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, const EpiArgs& e,
+                     cudaStream_t s);
+void launch_combine(const CombineArgs& c, cudaStream_t s);
+template <typename T>
+void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStream_t s);
+void launch_update_t12(double* t1, const double* r1, double* t2, const double* r2, const double* e,
+                       int o, int v, double shift, cudaStream_t s);
+template <typename T>
+void launch_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, int o, int v, i64 n3,
+                      double shift, cudaStream_t s);
+template <typename T>
+void launch_wdot(const T* x, const T* y, i64 n, i64 seg, const double* w, double* partial, double* out,
+                 double scale, int accumulate, cudaStream_t s);
+template <typename T>
+void launch_t2_outer(T* r3, const double* Wvooo, const double* t2, const int4* blocks, int o, int v,
+                     i64 n3, cudaStream_t s);
+void launch_diis_solve(const double* B, int m, int ld, double* coef, cudaStream_t s);
+template <typename T>
+void launch_diis_extrapolate(T* out, const T* hist, i64 stride, i64 n, const double* coef, int m,
+                             cudaStream_t s);
+template <typename T>
+void launch_sub(T* out, const T* a, const T* b, i64 n, cudaStream_t s);
+template <typename TO, typename TI>
+void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t s);
+
+// tcgen05 split-precision GEMM (gemm_tc.cu): C += alpha * (Ahi Bhi + Ahi Blo + Alo Bhi)
+// with A [M][Kpad], B [N][Kpad] in two planes each.  kind: PANEL_BF16X2 or PANEL_TF32X2.
+// Returns 0 on success, nonzero if the configuration is unsupported.
+int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo,
+                   int Kpad, const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s);
+
+}  // namespace rcc
+
+namespace rcc {
+// E partials: sum_{ijab} (2 g[i,a,j,b] - g[i,b,j,a]) (t2[i,j,a,b] + t1[i,a] t1[j,b]), g = (ia|jb)
+void launch_energy(const double* g, const double* t1, const double* t2, int o, int v, double* partial,
+                   double* out, cudaStream_t s);
+// t2[i,j,a,b] = g[i,a,j,b] / (e_i + e_j - e_a - e_b)
+void launch_mp2(double* t2, const double* g, const double* e, int o, int v, cudaStream_t s);
+// For each of ntrip occupied triples: U = t_{trip} unpacked from compact storage,
+// S = (2 - P_a^b - P_a^c) U, D = (2 - P_b^c)(2 - P_a^b - P_a^c) U  (outputs [ntrip][v^3])
+void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v,
+                        double* S, double* D, cudaStream_t s);
+}  // namespace rcc

@@ -1,0 +1,1491 @@
+// Host runtime of the RCCSDT library: context, plans, iteration driver, C ABI.
+//
+// Every contraction of one iteration is planned once, when the context is
+// created: operand panels are described by gather tables (PackArgs) and the
+// output by a scatter table (EpiArgs); an iteration only launches kernels.
+// Dense contractions are written as einsum-like specs (appendix A.5 term by
+// term); the compact-T3 terms of Eq. resi-rccsdt use hand-built tables:
+//   pp-ladder   direct traversal, three GEMM views of each stored block
+//               (W^{ab}_{de} t^{dec}, W^{ac}_{de} t^{dbe}, W^{bc}_{de} t^{ade}), Sec. II.C.1
+//   ring, hh    unpacking (Sec. II.C.2): for a fixed pair of occupied indices the
+//               unpacked (and spin-summed) blocks form one GEMM operand; the GEMM
+//               result X_{ijk} for every i lands in the stored block sorted(i,j,k)
+//               with the virtual axes permuted by the same sort and a weight that
+//               counts the column permutations mapping onto that triple.  For a
+//               block with two equal occupied indices this accumulates twice the
+//               sum over the coset representatives, which the symmetrisation of
+//               Sec. II.D.1 turns into the exact permutation-operator sum.
+//   F_vv, F_oo  folded into W_vvvv and W_oooo, the groupings (F^v_v + W^vv_vv) and
+//               (F^o_o + W^oo_oo) of steps (iv) and (v) of Sec. III.A.2.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/rccsdt.h"
+#include "elem.cuh"
+#include "kernels.h"
+
+using rcc::i64;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Device abstraction (the test-only host simulation swaps these for host calls)
+// ---------------------------------------------------------------------------
+#ifdef RCC_HOSTSIM
+void* dev_alloc(size_t bytes, int* err) {
+  void* p = calloc(bytes ? bytes : 1, 1);
+  if (!p) *err = RCCSDT_ERR_OOM;
+  return p;
+}
+void dev_free(void* p) { free(p); }
+int dev_copy(void* dst, const void* src, size_t bytes, cudaStream_t) {
+  memcpy(dst, src, bytes);
+  return 0;
+}
+int dev_zero(void* p, size_t bytes, cudaStream_t) {
+  memset(p, 0, bytes);
+  return 0;
+}
+int dev_sync(cudaStream_t) { return 0; }
+int dev_check() { return 0; }
+#else
+void* dev_alloc(size_t bytes, int* err) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
+    cudaGetLastError();
+    *err = RCCSDT_ERR_OOM;
+    return nullptr;
+  }
+  cudaMemset(p, 0, bytes ? bytes : 16);
+  return p;
+}
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+int dev_copy(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s) == cudaSuccess ? 0 : RCCSDT_ERR_CUDA;
+}
+int dev_zero(void* p, size_t bytes, cudaStream_t s) {
+  return cudaMemsetAsync(p, 0, bytes, s) == cudaSuccess ? 0 : RCCSDT_ERR_CUDA;
+}
+int dev_sync(cudaStream_t s) { return cudaStreamSynchronize(s) == cudaSuccess ? 0 : RCCSDT_ERR_CUDA; }
+int dev_check() { return cudaGetLastError() == cudaSuccess ? 0 : RCCSDT_ERR_CUDA; }
+#endif
+
+i64 n3_of(int o) { return (i64)o * (o + 1) * (o + 2) / 6; }
+int multiplicity(int i, int j, int k) {
+  if (i == j && j == k) return 1;
+  if (i == j || j == k || i == k) return 3;
+  return 6;
+}
+// pos[q] = stored axis of position q after sorting (occ[0], occ[1], occ[2]); stable.
+void sort_positions(const int occ[3], int pos[3], int sorted[3]) {
+  int idx[3] = {0, 1, 2};
+  for (int a = 0; a < 3; ++a)
+    for (int b = a + 1; b < 3; ++b)
+      if (occ[idx[b]] < occ[idx[a]]) std::swap(idx[a], idx[b]);
+  for (int s = 0; s < 3; ++s) {
+    pos[idx[s]] = s;
+    sorted[s] = occ[idx[s]];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Owned device buffer
+// ---------------------------------------------------------------------------
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { dev_free(p); }
+  double* d() const { return (double*)p; }
+  float* f() const { return (float*)p; }
+};
+
+// A strided view of a dense tensor (element strides).
+struct View {
+  void* p = nullptr;
+  int f32 = 0;
+  std::vector<i64> shape, stride;
+};
+
+View dense(void* p, std::vector<i64> shape, int f32 = 0) {
+  View v;
+  v.p = p;
+  v.f32 = f32;
+  v.shape = shape;
+  v.stride.assign(shape.size(), 1);
+  for (int d = (int)shape.size() - 2; d >= 0; --d) v.stride[d] = v.stride[d + 1] * shape[d + 1];
+  return v;
+}
+
+// Restrict dimension `dim` to [start, start + len).
+View sub(View v, int dim, i64 start, i64 len) {
+  v.p = (char*)v.p + start * v.stride[dim] * (v.f32 ? 4 : 8);
+  v.shape[dim] = len;
+  return v;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Plans
+// ---------------------------------------------------------------------------
+struct PackPlan {
+  rcc::PackArgs a{};
+  std::unique_ptr<DBuf> coef, colbase, sel, rowoff;
+};
+
+struct EpiPlan {
+  rcc::EpiArgs e{};
+  std::unique_ptr<DBuf> row_base, row_sel, row_alpha, col_off;
+};
+
+struct GemmPlan {
+  PackPlan A, B;        // A panel rows = M, B panel rows = N, common K
+  EpiPlan E;
+  int K = 0, Kpad = 0;
+  double fma = 0;
+  int big = 0;          // candidate for the tensor-core engine in split modes
+  int step = 0;         // timing bucket
+};
+
+struct rccsdt_ctx {
+  int o = 0, v = 0, n = 0, naux = 0;
+  i64 n3 = 0, V3 = 0;
+  rccsdt_options opt{};
+  int precision = RCCSDT_FP64;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int have_ham = 0, have_amp = 0, have_int = 0, have_res = 0;
+  int timing = 0;
+  double step_ms[16] = {0};
+  size_t total_bytes = 0;
+
+  // buffers
+  std::map<std::string, std::unique_ptr<DBuf>> buf;
+  std::vector<std::unique_ptr<GemmPlan>> plans;
+  // panels (engine scratch)
+  std::unique_ptr<DBuf> panelA_hi, panelA_lo, panelB_hi, panelB_lo;
+  size_t panel_bytes = 0;
+
+  // plan groups
+  std::vector<GemmPlan*> p_dress, p_fock, p_eri, p_int, p_r12, p_energy_bare;
+  std::vector<std::vector<GemmPlan*>> p_a3;  // per z
+  std::vector<GemmPlan*> p_pp, p_hh, p_ringab, p_ringc, p_t2a;
+  // combines
+  std::vector<rcc::CombineArgs> c_fock, c_helpers, c_int_base, c_r12_base, c_r2_sym, c_wt;
+  rcc::CombineArgs c_Lt_copy{}, c_ft_copy{};
+  std::vector<std::vector<rcc::CombineArgs>> c_int_after;
+  // per-z unpack tables for a3
+  std::unique_ptr<DBuf> a3_base, a3_pos;
+
+  // DIIS state
+  int diis_count = 0, iter = 0;
+  std::unique_ptr<DBuf> blocks_info, blk_weight;
+  std::unique_ptr<DBuf> hist_t, hist_e;     // M slots each: t1 | t2 | t3 (padded)
+  i64 hist_stride = 0;                      // bytes per slot
+  i64 seg1 = 0, seg2 = 0, seg3 = 0;         // element counts
+  std::unique_ptr<DBuf> scalars, partial;
+
+  DBuf* B(const std::string& k) { return buf.at(k).get(); }
+  double* D(const std::string& k) { return buf.at(k)->d(); }
+};
+
+namespace {
+
+int fail(rccsdt_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+DBuf* alloc_buf(rccsdt_ctx* c, const std::string& name, size_t bytes, int* err) {
+  auto b = std::make_unique<DBuf>();
+  b->p = dev_alloc(bytes, err);
+  b->bytes = bytes;
+  c->total_bytes += bytes;
+  DBuf* raw = b.get();
+  c->buf[name] = std::move(b);
+  return raw;
+}
+
+std::unique_ptr<DBuf> upload(rccsdt_ctx* c, const void* host, size_t bytes, int* err) {
+  auto b = std::make_unique<DBuf>();
+  b->p = dev_alloc(bytes, err);
+  b->bytes = bytes;
+  c->total_bytes += bytes;
+  if (b->p && bytes) {
+#ifdef RCC_HOSTSIM
+    memcpy(b->p, host, bytes);
+#else
+    if (cudaMemcpy(b->p, host, bytes, cudaMemcpyHostToDevice) != cudaSuccess) *err = RCCSDT_ERR_CUDA;
+#endif
+  }
+  return b;
+}
+
+template <typename T>
+std::unique_ptr<DBuf> upload_vec(rccsdt_ctx* c, const std::vector<T>& v, int* err) {
+  return upload(c, v.data(), v.size() * sizeof(T), err);
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Fill a PackPlan from host tables; `shared_rowoff` (device) replaces rowoff if given.
+void make_pack(rccsdt_ctx* c, PackPlan& P, const void* src, int src_f32, int R, int K, int nterm,
+               const std::vector<double>& coef, const std::vector<i64>& colbase,
+               const std::vector<int>& sel, const std::vector<i64>& rowoff, int read_k_fast, int* err,
+               const i64* shared_rowoff = nullptr) {
+  P.coef = upload_vec(c, coef, err);
+  P.colbase = upload_vec(c, colbase, err);
+  P.sel = upload_vec(c, sel, err);
+  if (!shared_rowoff) P.rowoff = upload_vec(c, rowoff, err);
+  rcc::PackArgs& a = P.a;
+  a.src = src;
+  a.src_f32 = src_f32;
+  a.R = R;
+  a.K = K;
+  a.nterm = nterm;
+  a.coef = (const double*)P.coef->p;
+  a.colbase = (const i64*)P.colbase->p;
+  a.sel = (const int*)P.sel->p;
+  a.rowoff = shared_rowoff ? shared_rowoff : (const i64*)P.rowoff->p;
+  a.read_k_fast = read_k_fast;
+}
+
+void make_epi(rccsdt_ctx* c, EpiPlan& E, void* C, int c_f32, int M, int N,
+              const std::vector<i64>& row_base, const std::vector<int>& row_sel,
+              const std::vector<double>& row_alpha, const std::vector<i64>& col_off, int* err,
+              const i64* shared_col_off = nullptr) {
+  E.row_base = upload_vec(c, row_base, err);
+  E.row_sel = upload_vec(c, row_sel, err);
+  E.row_alpha = upload_vec(c, row_alpha, err);
+  if (!shared_col_off) E.col_off = upload_vec(c, col_off, err);
+  rcc::EpiArgs& e = E.e;
+  e.C = C;
+  e.c_f32 = c_f32;
+  e.M = M;
+  e.N = N;
+  e.row_base = (const i64*)E.row_base->p;
+  e.row_sel = (const int*)E.row_sel->p;
+  e.row_alpha = (const double*)E.row_alpha->p;
+  e.col_off = shared_col_off ? shared_col_off : (const i64*)E.col_off->p;
+}
+
+void finish_plan(rccsdt_ctx* c, GemmPlan* g, int K) {
+  g->K = K;
+  g->Kpad = round_up(K, 64);
+  g->A.a.Kpad = g->Kpad;
+  g->B.a.Kpad = g->Kpad;
+  g->fma = (double)g->E.e.M * g->E.e.N * K;
+  size_t need = (size_t)std::max(g->A.a.R, g->B.a.R) * g->Kpad * 8;
+  if (need > c->panel_bytes) c->panel_bytes = need;
+}
+
+// Multi-index enumeration: offsets sum_d idx_d * stride_d over dims in order.
+std::vector<i64> offsets(const std::vector<i64>& size, const std::vector<i64>& stride) {
+  i64 total = 1;
+  for (i64 s : size) total *= s;
+  std::vector<i64> out((size_t)total);
+  std::vector<i64> idx(size.size(), 0);
+  for (i64 t = 0; t < total; ++t) {
+    i64 off = 0;
+    for (size_t d = 0; d < size.size(); ++d) off += idx[d] * stride[d];
+    out[(size_t)t] = off;
+    for (int d = (int)size.size() - 1; d >= 0; --d) {
+      if (++idx[d] < size[d]) break;
+      idx[d] = 0;
+    }
+  }
+  return out;
+}
+
+// C += alpha * contract(A, B) by an einsum-like spec "ab,bc->ac" (no batch labels).
+GemmPlan* contraction(rccsdt_ctx* c, const char* spec, double alpha, const View& A, const View& Bv,
+                      const View& C, int* err, int big = 0) {
+  std::string s(spec);
+  size_t comma = s.find(','), arrow = s.find("->");
+  std::string la = s.substr(0, comma), lb = s.substr(comma + 1, arrow - comma - 1), lc = s.substr(arrow + 2);
+  if (la.size() != A.shape.size() || lb.size() != Bv.shape.size() || lc.size() != C.shape.size()) {
+    *err = RCCSDT_ERR_ARG;
+    c->err = std::string("internal: rank mismatch in ") + spec;
+    return nullptr;
+  }
+  auto find = [](const std::string& l, char ch) { return (int)l.find(ch); };
+  std::vector<i64> mA, mC, mS, nB, nC, nS, kA, kB, kS;
+  for (size_t q = 0; q < lc.size(); ++q) {
+    char ch = lc[q];
+    int ia = find(la, ch), ib = find(lb, ch);
+    if (ia >= 0 && ib >= 0) {
+      *err = RCCSDT_ERR_ARG;
+      c->err = std::string("internal: batch label in ") + spec;
+      return nullptr;
+    }
+    if (ia >= 0) {
+      mA.push_back(A.stride[ia]); mC.push_back(C.stride[q]); mS.push_back(C.shape[q]);
+    } else {
+      nB.push_back(Bv.stride[ib]); nC.push_back(C.stride[q]); nS.push_back(C.shape[q]);
+    }
+  }
+  for (size_t q = 0; q < la.size(); ++q) {
+    char ch = la[q];
+    if (find(lc, ch) >= 0) continue;
+    int ib = find(lb, ch);
+    if (ib < 0) {
+      *err = RCCSDT_ERR_ARG;
+      c->err = std::string("internal: free label in ") + spec;
+      return nullptr;
+    }
+    kA.push_back(A.stride[q]); kB.push_back(Bv.stride[ib]); kS.push_back(A.shape[q]);
+  }
+  std::vector<i64> rowA = offsets(mS, mA), rowC = offsets(mS, mC);
+  std::vector<i64> rowB = offsets(nS, nB), colC = offsets(nS, nC);
+  std::vector<i64> kAo = offsets(kS, kA), kBo = offsets(kS, kB);
+  const int M = (int)rowA.size(), N = (int)rowB.size(), K = (int)kAo.size();
+  auto g = std::make_unique<GemmPlan>();
+  std::vector<double> coefK(K, 1.0);
+  std::vector<int> selK(K, 0);
+  auto unit_fast = [](const std::vector<i64>& st) { return !st.empty() && st.back() == 1; };
+  make_pack(c, g->A, A.p, A.f32, M, K, 1, coefK, kAo, selK, rowA, unit_fast(kA) ? 1 : 0, err);
+  make_pack(c, g->B, Bv.p, Bv.f32, N, K, 1, coefK, kBo, selK, rowB, unit_fast(kB) ? 1 : 0, err);
+  make_epi(c, g->E, C.p, C.f32, M, N, rowC, std::vector<int>(M, 0), std::vector<double>(M, alpha), colC, err);
+  g->big = big;
+  finish_plan(c, g.get(), K);
+  GemmPlan* raw = g.get();
+  c->plans.push_back(std::move(g));
+  return raw;
+}
+
+// Permuted linear combination out = beta*out + sum coef_t in_t; views share a shape.
+rcc::CombineArgs combine(const View& out, double beta, std::vector<std::pair<double, View>> terms) {
+  rcc::CombineArgs a{};
+  a.out = (double*)out.p;
+  a.rank = (int)out.shape.size();
+  a.total = 1;
+  for (int d = 0; d < a.rank; ++d) {
+    a.shape[d] = out.shape[d];
+    a.ostride[d] = out.stride[d];
+    a.total *= out.shape[d];
+  }
+  a.nterm = (int)terms.size();
+  for (int t = 0; t < a.nterm; ++t) {
+    a.coef[t] = terms[t].first;
+    a.in[t] = (const double*)terms[t].second.p;
+    for (int d = 0; d < a.rank; ++d) a.istride[t][d] = terms[t].second.stride[d];
+  }
+  a.beta = beta;
+  return a;
+}
+
+// A view with explicit shape and strides (for diagonal and permuted access).
+View strided(void* p, std::vector<i64> shape, std::vector<i64> stride) {
+  View v;
+  v.p = p;
+  v.shape = shape;
+  v.stride = stride;
+  return v;
+}
+
+// Permuted view: out axis d reads input axis perm[d].
+View permuted(const View& in, std::vector<int> perm) {
+  View v = in;
+  for (size_t d = 0; d < perm.size(); ++d) {
+    v.shape[d] = in.shape[perm[d]];
+    v.stride[d] = in.stride[perm[d]];
+  }
+  return v;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Engine: run one GemmPlan
+// ---------------------------------------------------------------------------
+static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
+  const bool tc = c->precision != RCCSDT_FP64 && g->big;
+  const int kind = !tc ? rcc::PANEL_F64 : (c->precision == RCCSDT_SPLIT_BF16X3 ? rcc::PANEL_BF16X2 : rcc::PANEL_TF32X2);
+  rcc::PackArgs pa = g->A.a, pb = g->B.a;
+  pa.kind = pb.kind = kind;
+  pa.out_hi = c->panelA_hi->p;
+  pa.out_lo = c->panelA_lo ? c->panelA_lo->p : nullptr;
+  pb.out_hi = c->panelB_hi->p;
+  pb.out_lo = c->panelB_lo ? c->panelB_lo->p : nullptr;
+  rcc::launch_pack(pa, c->stream);
+  rcc::launch_pack(pb, c->stream);
+  if (!tc) {
+    rcc::launch_gemm_f64((const double*)pa.out_hi, (const double*)pb.out_hi, g->Kpad, g->Kpad, g->Kpad,
+                         g->E.e, c->stream);
+  } else {
+    int* flag = (int*)((double*)c->scalars->p + 1000);
+    if (rcc::launch_gemm_tc(kind, pa.out_hi, pa.out_lo, pb.out_hi, pb.out_lo, g->Kpad, g->E.e, flag,
+                            c->opt.watchdog_cycles, c->stream))
+      return fail(c, RCCSDT_ERR_ARG, "tensor-core GEMM configuration unsupported");
+  }
+  return dev_check();
+}
+
+static int run_plans(rccsdt_ctx* c, const std::vector<GemmPlan*>& ps) {
+  for (GemmPlan* g : ps) {
+    int st = run_gemm(c, g);
+    if (st) return st;
+  }
+  return 0;
+}
+
+static void run_combines(rccsdt_ctx* c, const std::vector<rcc::CombineArgs>& cs) {
+  for (const auto& a : cs) rcc::launch_combine(a, c->stream);
+}
+
+// ---------------------------------------------------------------------------
+// Context construction: buffers and every plan of one iteration
+// ---------------------------------------------------------------------------
+namespace {
+
+// View with dimension 0 fixed at `idx` and removed.
+View slice0(const View& v, i64 idx) {
+  View r;
+  r.p = (char*)v.p + idx * v.stride[0] * (v.f32 ? 4 : 8);
+  r.f32 = v.f32;
+  r.shape.assign(v.shape.begin() + 1, v.shape.end());
+  r.stride.assign(v.stride.begin() + 1, v.stride.end());
+  return r;
+}
+
+// Virtual-permutation index of pos (the 6 orderings in lexicographic order).
+int perm_id(const int pos[3]) {
+  static const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  for (int q = 0; q < 6; ++q)
+    if (P[q][0] == pos[0] && P[q][1] == pos[1] && P[q][2] == pos[2]) return q;
+  return 0;
+}
+
+struct TripleInfo {
+  i64 blk;
+  int pos[3];
+  int m;
+};
+TripleInfo triple(int i, int j, int k) {
+  TripleInfo t;
+  int occ[3] = {i, j, k}, srt[3];
+  sort_positions(occ, t.pos, srt);
+  t.blk = rcc::blk_index(srt[0], srt[1], srt[2]);
+  t.m = multiplicity(i, j, k);
+  return t;
+}
+
+struct Builder {
+  rccsdt_ctx* c;
+  int* err;
+  int o, v, n, naux;
+  i64 V2, V3, S[3];
+  const i64* RT2 = nullptr;  // [9][v^2]
+  const i64* RT3 = nullptr;  // [6][v^3]
+
+  View T(const std::string& name, std::vector<i64> shape) { return dense(c->D(name), shape); }
+  DBuf* mk(const std::string& name, size_t count, size_t elem = 8) { return alloc_buf(c, name, count * elem, err); }
+  GemmPlan* ct(std::vector<GemmPlan*>& grp, const char* spec, double alpha, const View& A, const View& B,
+               const View& C, int big = 0) {
+    GemmPlan* g = contraction(c, spec, alpha, A, B, C, err, big);
+    if (g) grp.push_back(g);
+    return g;
+  }
+  GemmPlan* new_plan() {
+    c->plans.push_back(std::make_unique<GemmPlan>());
+    return c->plans.back().get();
+  }
+};
+
+int build_context(rccsdt_ctx* c) {
+  int err = 0;
+  Builder b{c, &err, c->o, c->v, c->n, c->naux};
+  const int o = c->o, v = c->v, n = c->n, naux = c->naux;
+  b.V2 = (i64)v * v;
+  b.V3 = b.V2 * v;
+  b.S[0] = b.V2; b.S[1] = v; b.S[2] = 1;
+  const i64 V2 = b.V2, V3 = b.V3, n3 = c->n3;
+  const int t3f = c->opt.precision != RCCSDT_FP64;
+  const size_t t3e = t3f ? 4 : 8;
+
+  // --- data buffers
+  b.mk("e", n); b.mk("L", (size_t)naux * n * n); b.mk("Lt", (size_t)naux * n * n);
+  b.mk("F", (size_t)n * n); b.mk("ft", (size_t)n * n); b.mk("J", (size_t)n * n); b.mk("Kx", (size_t)n * n);
+  b.mk("gamma", naux); b.mk("Y", (size_t)naux * v * n);
+  const char* blocks[] = {"oooo", "ooov", "oovo", "oovv", "ovov", "ovvo", "ovvv", "vovv", "vooo", "vvoo", "vvvo", "vvvv"};
+  for (const char* s : blocks) {
+    size_t cnt = 1;
+    for (int q = 0; q < 4; ++q) cnt *= (s[q] == 'o' ? o : v);
+    b.mk(s, cnt);
+  }
+  b.mk("ovov_bare", (size_t)o * v * o * v);
+  b.mk("vs_oovv", (size_t)o * o * v * v); b.mk("ts2", (size_t)o * o * v * v);
+  b.mk("vs_ovvv", (size_t)o * v * v * v); b.mk("vs_oovo", (size_t)o * o * v * o);
+  b.mk("Fvv", V2); b.mk("Foo", (size_t)o * o); b.mk("Woooo", (size_t)o * o * o * o);
+  b.mk("Wt_oooo", (size_t)o * o * o * o);
+  b.mk("Wovvo", (size_t)o * v * v * o); b.mk("Wovov", (size_t)o * v * o * v);
+  b.mk("Wvvvo", (size_t)v * v * v * o); b.mk("Wvooo", (size_t)v * o * o * o);
+  b.mk("Wb_ovvo", (size_t)o * v * v * o); b.mk("Wb_ovov", (size_t)o * v * o * v);
+  b.mk("Wvvvv", (size_t)V2 * V2);
+  b.mk("Wring_ab", (size_t)o * v * 2 * o * v); b.mk("Wring_c", (size_t)o * v * o * v);
+  b.mk("t1", (size_t)o * v); b.mk("t2", (size_t)o * o * v * v); b.mk("r1", (size_t)o * v);
+  b.mk("r2", (size_t)o * o * v * v); b.mk("X2", (size_t)o * o * v * v);
+  b.mk("dR1", (size_t)o * v); b.mk("dX2", (size_t)o * o * v * v);
+  b.mk("t3", (size_t)n3 * V3, t3e); b.mk("r3", (size_t)n3 * V3, t3e); b.mk("rp3", (size_t)n3 * V3, t3e);
+  b.mk("Sz", (size_t)o * o * V3); b.mk("Dz", (size_t)o * o * V3);
+  if (err) return fail(c, err, "device allocation failed");
+
+  // --- block info and weights
+  {
+    std::vector<int4> info((size_t)n3);
+    std::vector<double> w((size_t)n3);
+    for (int k = 0; k < o; ++k)
+      for (int j = 0; j <= k; ++j)
+        for (int i = 0; i <= j; ++i) {
+          i64 bi = rcc::blk_index(i, j, k);
+          info[bi] = make_int4(i, j, k, 0);
+          w[bi] = multiplicity(i, j, k);
+        }
+    c->blocks_info = upload_vec(c, info, &err);
+    c->blk_weight = upload_vec(c, w, &err);
+  }
+  // --- selector tables
+  std::unique_ptr<DBuf> rt2, rt3;
+  {
+    std::vector<i64> t2tab((size_t)9 * V2), t3tab((size_t)6 * V3);
+    for (int al = 0; al < 3; ++al)
+      for (int be = 0; be < 3; ++be)
+        for (int x = 0; x < v; ++x)
+          for (int y = 0; y < v; ++y) t2tab[(size_t)(al * 3 + be) * V2 + x * v + y] = x * b.S[al] + y * b.S[be];
+    static const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (int q = 0; q < 6; ++q)
+      for (i64 e = 0; e < V3; ++e) {
+        i64 a = e / V2, bb = (e / v) % v, cc = e % v;
+        t3tab[(size_t)q * V3 + e] = a * b.S[P[q][0]] + bb * b.S[P[q][1]] + cc * b.S[P[q][2]];
+      }
+    rt2 = upload_vec(c, t2tab, &err);
+    rt3 = upload_vec(c, t3tab, &err);
+    b.RT2 = (const i64*)rt2->p;
+    b.RT3 = (const i64*)rt3->p;
+    c->buf["RT2"] = std::move(rt2);
+    c->buf["RT3"] = std::move(rt3);
+  }
+
+  const i64 O0 = 0, V0 = o;
+  View L = b.T("L", {naux, n, n}), Lt = b.T("Lt", {naux, n, n});
+  View t1 = b.T("t1", {o, v}), t2 = b.T("t2", {o, o, v, v}), ts2 = b.T("ts2", {o, o, v, v});
+  View ft = b.T("ft", {n, n}), F = b.T("F", {n, n});
+  auto eri = [&](const char* s) {
+    std::vector<i64> sh;
+    for (int q = 0; q < 4; ++q) sh.push_back(s[q] == 'o' ? o : v);
+    return b.T(s, sh);
+  };
+
+  // bare (ia|jb) for the energy and the MP2 guess
+  b.ct(c->p_energy_bare, "Pia,Pjb->iajb", 1.0, sub(sub(L, 1, O0, o), 2, V0, v), sub(sub(L, 1, O0, o), 2, V0, v),
+       b.T("ovov_bare", {o, v, o, v}));
+
+  // --- (i) T1 dressing: Lt = (1 - t1) L (1 + t1), ft = (1 - t1) [f + G(t1)] (1 + t1)
+  c->c_Lt_copy = combine(Lt, 0.0, {{1.0, L}});
+  b.ct(c->p_dress, "Ppa,ia->Ppi", 1.0, sub(L, 2, V0, v), t1, sub(Lt, 2, O0, o));
+  b.ct(c->p_dress, "ia,Piq->Paq", -1.0, t1, sub(Lt, 1, O0, o), sub(Lt, 1, V0, v));
+  b.ct(c->p_fock, "Pia,ia->P", 1.0, sub(sub(L, 1, O0, o), 2, V0, v), t1, b.T("gamma", {naux}));
+  b.ct(c->p_fock, "Prs,P->rs", 1.0, L, b.T("gamma", {naux}), b.T("J", {n, n}));
+  b.ct(c->p_fock, "ia,Pis->Pas", 1.0, t1, sub(L, 1, O0, o), b.T("Y", {naux, v, n}));
+  b.ct(c->p_fock, "Pra,Pas->rs", 1.0, sub(L, 2, V0, v), b.T("Y", {naux, v, n}), b.T("Kx", {n, n}));
+  c->c_fock.push_back(combine(F, 0.0, {{2.0, b.T("J", {n, n})}, {-1.0, b.T("Kx", {n, n})}}));
+  c->c_fock.push_back(combine(strided(c->D("F"), {n}, {n + 1}), 1.0, {{1.0, b.T("e", {n})}}));
+  c->c_fock.push_back(combine(ft, 0.0, {{1.0, F}}));
+  std::vector<GemmPlan*> p_ft;
+  b.ct(p_ft, "pa,ia->pi", 1.0, sub(F, 1, V0, v), t1, sub(ft, 1, O0, o));
+  b.ct(p_ft, "ia,iq->aq", -1.0, t1, sub(ft, 0, O0, o), sub(ft, 0, V0, v));
+  for (GemmPlan* g : p_ft) c->p_fock.push_back(g);  // run after the combines (see run order)
+
+  // --- ERI blocks v~^{pq}_{rs} = sum_P Lt[P,p,r] Lt[P,q,s]
+  for (const char* s : blocks) {
+    auto sp = [&](char ch) { return ch == 'o' ? std::make_pair(O0, (i64)o) : std::make_pair(V0, (i64)v); };
+    auto p = sp(s[0]), q = sp(s[1]), r = sp(s[2]), t = sp(s[3]);
+    View A = sub(sub(Lt, 1, p.first, p.second), 2, r.first, r.second);
+    View Bv = sub(sub(Lt, 1, q.first, q.second), 2, t.first, t.second);
+    b.ct(c->p_eri, "Ppr,Pqs->pqrs", 1.0, A, Bv, eri(s), std::string(s) == "vvvv");
+  }
+
+  // --- spin-summed helpers
+  c->c_helpers.push_back(combine(b.T("vs_oovv", {o, o, v, v}), 0.0,
+                                 {{2.0, eri("oovv")}, {-1.0, permuted(eri("oovv"), {0, 1, 3, 2})}}));
+  c->c_helpers.push_back(combine(ts2, 0.0, {{2.0, t2}, {-1.0, permuted(t2, {0, 1, 3, 2})}}));
+  c->c_helpers.push_back(combine(b.T("vs_ovvv", {o, v, v, v}), 0.0,
+                                 {{2.0, eri("ovvv")}, {-1.0, permuted(eri("ovvv"), {0, 1, 3, 2})}}));
+  c->c_helpers.push_back(combine(b.T("vs_oovo", {o, o, v, o}), 0.0,
+                                 {{2.0, eri("oovo")}, {-1.0, permuted(eri("ooov"), {0, 1, 3, 2})}}));
+
+  // --- RCCSD and RCCSDT intermediates (appendix A.5)
+  View vs_oovv = b.T("vs_oovv", {o, o, v, v}), vs_ovvv = b.T("vs_ovvv", {o, v, v, v});
+  View vs_oovo = b.T("vs_oovo", {o, o, v, o});
+  View Fvv = b.T("Fvv", {v, v}), Foo = b.T("Foo", {o, o}), Woooo = b.T("Woooo", {o, o, o, o});
+  View Wovvo = b.T("Wovvo", {o, v, v, o}), Wovov = b.T("Wovov", {o, v, o, v});
+  View Wvvvo = b.T("Wvvvo", {v, v, v, o}), Wvooo = b.T("Wvooo", {v, o, o, o});
+  View Wb_ovvo = b.T("Wb_ovvo", {o, v, v, o}), Wb_ovov = b.T("Wb_ovov", {o, v, o, v});
+  View Wvvvv = b.T("Wvvvv", {v, v, v, v});
+  c->c_int_base.push_back(combine(Fvv, 0.0, {{1.0, sub(sub(ft, 0, V0, v), 1, V0, v)}}));
+  c->c_int_base.push_back(combine(Foo, 0.0, {{1.0, sub(sub(ft, 0, O0, o), 1, O0, o)}}));
+  c->c_int_base.push_back(combine(Woooo, 0.0, {{1.0, eri("oooo")}}));
+  c->c_int_base.push_back(combine(Wovvo, 0.0, {{2.0, eri("ovvo")}, {-1.0, permuted(eri("ovov"), {0, 1, 3, 2})}}));
+  c->c_int_base.push_back(combine(Wovov, 0.0, {{1.0, eri("ovov")}}));
+  c->c_int_base.push_back(combine(Wvvvo, 0.0, {{1.0, eri("vvvo")}}));
+  c->c_int_base.push_back(combine(Wvooo, 0.0, {{1.0, eri("vooo")}}));
+  c->c_int_base.push_back(combine(Wvvvv, 0.0, {{1.0, eri("vvvv")}}));
+  b.ct(c->p_int, "kldc,kldb->bc", -1.0, vs_oovv, t2, Fvv);
+  b.ct(c->p_int, "lkcd,ljcd->kj", 1.0, vs_oovv, t2, Foo);
+  b.ct(c->p_int, "klcd,ijcd->klij", 1.0, eri("oovv"), t2, Woooo);
+  b.ct(c->p_int, "lkdc,lida->kaci", 0.5, vs_oovv, ts2, Wovvo);
+  b.ct(c->p_int, "lkcd,ilda->kaic", -0.5, eri("oovv"), t2, Wovov);
+  b.ct(c->p_int, "laed,ljeb->abdj", 0.5, vs_ovvv, ts2, Wvvvo);
+  b.ct(c->p_int, "lade,jleb->abdj", -0.5, eri("ovvv"), t2, Wvvvo);
+  b.ct(c->p_int, "lbde,jlea->abdj", -1.0, eri("ovvv"), t2, Wvvvo);
+  b.ct(c->p_int, "lmdj,lmab->abdj", 1.0, eri("oovo"), t2, Wvvvo);
+  b.ct(c->p_int, "ld,ijad->alij", 1.0, sub(sub(ft, 0, O0, o), 1, V0, v), t2, Wvooo);
+  b.ct(c->p_int, "mldj,mida->alij", 0.5, vs_oovo, ts2, Wvooo);
+  b.ct(c->p_int, "mljd,imda->alij", -0.5, eri("ooov"), t2, Wvooo);
+  b.ct(c->p_int, "mlid,jmda->alij", -1.0, eri("ooov"), t2, Wvooo);
+  b.ct(c->p_int, "alde,ijde->alij", 1.0, eri("vovv"), t2, Wvooo);
+  b.ct(c->p_int, "lmde,lmab->abde", 1.0, eri("oovv"), t2, Wvvvv, 1);
+  c->c_int_after.resize(1);
+  c->c_int_after[0].push_back(combine(Wb_ovvo, 0.0, {{1.0, Wovvo}}));
+  c->c_int_after[0].push_back(combine(Wb_ovov, 0.0, {{1.0, Wovov}}));
+  std::vector<GemmPlan*> p_int2;
+  b.ct(p_int2, "mled,miea->ladi", 0.5, vs_oovv, ts2, Wb_ovvo);
+  b.ct(p_int2, "mlde,imea->laid", -0.5, eri("oovv"), t2, Wb_ovov);
+  c->p_a3.resize(o + 1);
+  c->p_a3[o] = p_int2;  // slot o: the Wbar contractions
+
+  // --- step (iii): T3 contributions, per z batch of unpacked blocks t_{xyz}
+  {
+    std::vector<i64> base((size_t)o * o * o);
+    std::vector<int> pos((size_t)o * o * o * 3);
+    for (int z = 0; z < o; ++z)
+      for (int x = 0; x < o; ++x)
+        for (int y = 0; y < o; ++y) {
+          TripleInfo ti = triple(x, y, z);
+          size_t id = ((size_t)z * o + x) * o + y;
+          base[id] = ti.blk * V3;
+          for (int q = 0; q < 3; ++q) pos[id * 3 + q] = ti.pos[q];
+        }
+    c->a3_base = upload_vec(c, base, &err);
+    c->a3_pos = upload_vec(c, pos, &err);
+    View Sz = b.T("Sz", {o, o, v, v, v}), Dz = b.T("Dz", {o, o, v, v, v});
+    View dR1 = b.T("dR1", {o, v}), dX2 = b.T("dX2", {o, o, v, v});
+    for (int z = 0; z < o; ++z) {
+      auto& g = c->p_a3[z];
+      b.ct(g, "xybc,xybca->a", 0.5, eri("oovv"), Dz, slice0(dR1, z));
+      b.ct(g, "xc,xycab->yab", 0.5, sub(sub(ft, 0, O0, o), 1, V0, v), Sz, permuted(slice0(permuted(dX2, {1, 0, 2, 3}), z), {0, 1, 2}));
+      b.ct(g, "bxcd,xydac->yab", 1.0, eri("vovv"), Sz, slice0(permuted(dX2, {1, 0, 2, 3}), z), 1);
+      b.ct(g, "xjc,xycab->yjab", -1.0, slice0(eri("ooov"), z), Sz, dX2);
+      b.ct(g, "xde,xyeba->abdy", -1.0, slice0(eri("oovv"), z), Sz, Wvvvo, 1);
+      b.ct(g, "lxde,xyead->aly", 1.0, eri("oovv"), Sz, slice0(permuted(Wvooo, {3, 0, 1, 2}), z));
+    }
+  }
+
+  // --- R1, R2
+  View r1 = b.T("r1", {o, v}), X2 = b.T("X2", {o, o, v, v});
+  c->c_r12_base.push_back(combine(r1, 0.0, {{1.0, permuted(sub(sub(ft, 0, V0, v), 1, O0, o), {1, 0})},
+                                            {1.0, b.T("dR1", {o, v})}}));
+  b.ct(c->p_r12, "kc,ikac->ia", 1.0, sub(sub(ft, 0, O0, o), 1, V0, v), ts2, r1);
+  b.ct(c->p_r12, "akcd,ikcd->ia", 1.0, eri("vovv"), ts2, r1);
+  b.ct(c->p_r12, "klic,klac->ia", -1.0, eri("ooov"), ts2, r1);
+  c->c_r12_base.push_back(combine(X2, 0.0, {{0.5, permuted(eri("vvoo"), {2, 3, 0, 1})},
+                                            {1.0, b.T("dX2", {o, o, v, v})}}));
+  b.ct(c->p_r12, "bc,ijac->ijab", 1.0, Fvv, t2, X2);
+  b.ct(c->p_r12, "kj,ikab->ijab", -1.0, Foo, t2, X2);
+  b.ct(c->p_r12, "abcd,ijcd->ijab", 0.5, eri("vvvv"), t2, X2, 1);
+  b.ct(c->p_r12, "klij,klab->ijab", 0.5, Woooo, t2, X2);
+  b.ct(c->p_r12, "kaci,kjcb->ijab", 0.5, Wovvo, ts2, X2);
+  b.ct(c->p_r12, "kaic,jkcb->ijab", -0.5, Wovov, t2, X2);
+  b.ct(c->p_r12, "kbic,jkca->ijab", -1.0, Wovov, t2, X2);
+  c->c_r2_sym.push_back(combine(b.T("r2", {o, o, v, v}), 0.0, {{1.0, X2}, {1.0, permuted(X2, {1, 0, 3, 2})}}));
+
+  // --- R3 operands: F folded into W_vvvv and W_oooo, ring A operands
+  {
+    View Wt = b.T("Wt_oooo", {o, o, o, o});
+    c->c_wt.push_back(combine(Wt, 0.0, {{1.0, Woooo}}));
+    // W~^{lm}_{ij} -= 1/2 F^l_i delta_mj ; -= 1/2 delta_li F^m_j
+    c->c_wt.push_back(combine(strided(c->D("Wt_oooo"), {o, o, o}, {(i64)o * o * o, (i64)o * o + 1, o}), 1.0,
+                              {{-0.5, strided(c->D("Foo"), {o, o, o}, {o, 0, 1})}}));
+    c->c_wt.push_back(combine(strided(c->D("Wt_oooo"), {o, o, o}, {(i64)o * o * o + o, (i64)o * o, 1}), 1.0,
+                              {{-0.5, strided(c->D("Foo"), {o, o, o}, {0, o, 1})}}));
+    // W~^{ab}_{de} += 1/2 F^a_d delta_be ; += 1/2 delta_ad F^b_e
+    c->c_wt.push_back(combine(strided(c->D("Wvvvv"), {v, v, v}, {V3, V2 + 1, v}), 1.0,
+                              {{0.5, strided(c->D("Fvv"), {v, v, v}, {v, 0, 1})}}));
+    c->c_wt.push_back(combine(strided(c->D("Wvvvv"), {v, v, v}, {V3 + v, V2, 1}), 1.0,
+                              {{0.5, strided(c->D("Fvv"), {v, v, v}, {0, v, 1})}}));
+    // Wring_ab[i][a][0][l][d] = 1/4 Wbar^{la}_{di};  [1][l][d] = -1/4 Wbar^{la}_{id}
+    const i64 K2 = 2LL * o * v;
+    View Wab0 = strided(c->D("Wring_ab"), {o, v, o, v}, {v * K2, K2, v, 1});
+    View Wab1 = strided(c->D("Wring_ab") + (i64)o * v, {o, v, o, v}, {v * K2, K2, v, 1});
+    c->c_wt.push_back(combine(Wab0, 0.0, {{0.25, permuted(Wb_ovvo, {3, 1, 0, 2})}}));
+    c->c_wt.push_back(combine(Wab1, 0.0, {{-0.25, permuted(Wb_ovov, {2, 1, 0, 3})}}));
+    // Wring_c[i][b][l][d] = -Wbar^{lb}_{id}
+    c->c_wt.push_back(combine(b.T("Wring_c", {o, v, o, v}), 0.0, {{-1.0, permuted(Wb_ovov, {2, 1, 0, 3})}}));
+  }
+
+  void* r3p = c->B("r3")->p;
+  void* t3p = c->B("t3")->p;
+  // --- pp-ladder: three views of each stored block (direct traversal)
+  {
+    i64 per_blk = (i64)v * round_up((int)V2, 64) * 8;
+    i64 nb = std::max<i64>(1, std::min<i64>(n3, (2LL << 30) / per_blk));
+    for (int term = 0; term < 3; ++term)
+      for (i64 b0 = 0; b0 < n3; b0 += nb) {
+        i64 b1 = std::min(n3, b0 + nb);
+        int N = (int)((b1 - b0) * v);
+        GemmPlan* g = b.new_plan();
+        std::vector<i64> arow(V2), acol(V2), brow(N), bcol(V2), ebase(V2), ecol(N);
+        for (i64 r = 0; r < V2; ++r) { arow[r] = r * V2; acol[r] = r; }
+        for (i64 q = 0; q < V2; ++q) {
+          i64 d = q / v, e = q % v;
+          bcol[q] = term == 0 ? d * V2 + e * v : term == 1 ? d * V2 + e : d * v + e;
+        }
+        for (int q = 0; q < N; ++q) {
+          i64 blk = b0 + q / v, w = q % v;
+          brow[q] = blk * V3 + (term == 0 ? w : term == 1 ? w * v : w * V2);
+          ecol[q] = brow[q];
+        }
+        for (i64 r = 0; r < V2; ++r) {
+          i64 x = r / v, y = r % v;
+          ebase[r] = term == 0 ? x * V2 + y * v : term == 1 ? x * V2 + y : x * v + y;
+        }
+        make_pack(c, g->A, c->D("Wvvvv"), 0, (int)V2, (int)V2, 1, std::vector<double>(V2, 1.0), acol,
+                  std::vector<int>(V2, 0), arow, 1, &err);
+        make_pack(c, g->B, t3p, t3f, N, (int)V2, 1, std::vector<double>(V2, 1.0), bcol, std::vector<int>(V2, 0),
+                  brow, term == 0 ? 0 : 1, &err);
+        make_epi(c, g->E, r3p, t3f, (int)V2, N, ebase, std::vector<int>(V2, 0), std::vector<double>(V2, 1.0),
+                 ecol, &err);
+        g->big = 1;
+        g->step = 1;
+        finish_plan(c, g, (int)V2);
+        c->p_pp.push_back(g);
+      }
+  }
+
+  // --- hh-ladder (with F_oo folded in), unit k: rows (i<=j), cols abc, K = (l,m)
+  {
+    std::vector<std::pair<int, int>> pairs;
+    for (int i = 0; i < o; ++i)
+      for (int j = i; j < o; ++j) pairs.push_back({i, j});
+    const int M = (int)pairs.size(), K = o * o;
+    for (int k = 0; k < o; ++k) {
+      GemmPlan* g = b.new_plan();
+      std::vector<i64> arow(M), acol(K), bcol(K), ebase(M);
+      std::vector<int> bsel(K), esel(M);
+      std::vector<double> ealpha(M);
+      for (int q = 0; q < M; ++q) arow[q] = (i64)pairs[q].first * o + pairs[q].second;
+      for (int l = 0; l < o; ++l)
+        for (int m = 0; m < o; ++m) {
+          acol[l * o + m] = (i64)l * o * o * o + (i64)m * o * o;
+          TripleInfo ti = triple(l, m, k);
+          bcol[l * o + m] = ti.blk * V3;
+          bsel[l * o + m] = perm_id(ti.pos);
+        }
+      for (int q = 0; q < M; ++q) {
+        TripleInfo ti = triple(pairs[q].first, pairs[q].second, k);
+        ebase[q] = ti.blk * V3;
+        esel[q] = perm_id(ti.pos);
+        ealpha[q] = (6.0 / ti.m) * (pairs[q].first < pairs[q].second ? 2.0 : 1.0);
+      }
+      make_pack(c, g->A, c->D("Wt_oooo"), 0, M, K, 1, std::vector<double>(K, 0.5), acol, std::vector<int>(K, 0),
+                arow, 0, &err);
+      make_pack(c, g->B, t3p, t3f, (int)V3, K, 1, std::vector<double>(K, 1.0), bcol, bsel, {}, 0, &err, b.RT3);
+      make_epi(c, g->E, r3p, t3f, M, (int)V3, ebase, esel, ealpha, {}, &err, b.RT3);
+      g->big = 1;
+      g->step = 3;
+      finish_plan(c, g, K);
+      c->p_hh.push_back(g);
+    }
+  }
+
+  // --- ring terms (a) + (b): unit (j <= k); rows (i,a), cols (b,c), K = (part, l, d)
+  {
+    const int M = o * v, K = 2 * o * v;
+    for (int j = 0; j < o; ++j)
+      for (int k = j; k < o; ++k) {
+        GemmPlan* g = b.new_plan();
+        std::vector<i64> arow(M), acol(K), bcol((size_t)3 * K), ebase(M);
+        std::vector<int> bsel((size_t)3 * K, 0), esel(M);
+        std::vector<double> bcoef((size_t)3 * K, 0.0), ealpha(M);
+        for (int r = 0; r < M; ++r) arow[r] = (i64)r * K;
+        for (int q = 0; q < K; ++q) acol[q] = q;
+        for (int l = 0; l < o; ++l) {
+          TripleInfo u = triple(l, j, k), u1 = triple(j, l, k), u2 = triple(k, l, j);
+          for (int d = 0; d < v; ++d) {
+            int q0 = l * v + d, q1 = o * v + l * v + d;
+            // part 0: 2 U^{dbc} - U^{bdc} - U^{cbd}, U = t_{ljk}
+            bcoef[q0] = 2.0; bcol[q0] = u.blk * V3 + d * b.S[u.pos[0]]; bsel[q0] = u.pos[1] * 3 + u.pos[2];
+            bcoef[K + q0] = -1.0; bcol[K + q0] = u.blk * V3 + d * b.S[u.pos[1]]; bsel[K + q0] = u.pos[0] * 3 + u.pos[2];
+            bcoef[2 * K + q0] = -1.0; bcol[2 * K + q0] = u.blk * V3 + d * b.S[u.pos[2]]; bsel[2 * K + q0] = u.pos[1] * 3 + u.pos[0];
+            // part 1: t_{jlk}^{dbc} + t_{klj}^{dcb}
+            bcoef[q1] = 1.0; bcol[q1] = u1.blk * V3 + d * b.S[u1.pos[0]]; bsel[q1] = u1.pos[1] * 3 + u1.pos[2];
+            bcoef[K + q1] = 1.0; bcol[K + q1] = u2.blk * V3 + d * b.S[u2.pos[0]]; bsel[K + q1] = u2.pos[2] * 3 + u2.pos[1];
+            bcol[2 * K + q1] = u1.blk * V3;
+          }
+        }
+        for (int i = 0; i < o; ++i) {
+          TripleInfo ti = triple(i, j, k);
+          for (int a = 0; a < v; ++a) {
+            ebase[i * v + a] = ti.blk * V3 + a * b.S[ti.pos[0]];
+            esel[i * v + a] = ti.pos[1] * 3 + ti.pos[2];
+            ealpha[i * v + a] = (6.0 / ti.m) * (j < k ? 2.0 : 1.0);
+          }
+        }
+        make_pack(c, g->A, c->D("Wring_ab"), 0, M, K, 1, std::vector<double>(K, 1.0), acol, std::vector<int>(K, 0),
+                  arow, 1, &err);
+        make_pack(c, g->B, t3p, t3f, (int)V2, K, 3, bcoef, bcol, bsel, {}, 0, &err, b.RT2);
+        make_epi(c, g->E, r3p, t3f, M, (int)V2, ebase, esel, ealpha, {}, &err, b.RT2);
+        g->big = 1;
+        g->step = 2;
+        finish_plan(c, g, K);
+        c->p_ringab.push_back(g);
+      }
+  }
+
+  // --- ring term (c): unit (j,k); rows (i,b), cols (a,c), K = (l,d)
+  {
+    const int M = o * v, K = o * v;
+    for (int j = 0; j < o; ++j)
+      for (int k = 0; k < o; ++k) {
+        GemmPlan* g = b.new_plan();
+        std::vector<i64> arow(M), acol(K), bcol(K), ebase(M);
+        std::vector<int> bsel(K), esel(M);
+        std::vector<double> ealpha(M);
+        for (int r = 0; r < M; ++r) arow[r] = (i64)r * K;
+        for (int q = 0; q < K; ++q) acol[q] = q;
+        for (int l = 0; l < o; ++l) {
+          TripleInfo u = triple(j, l, k);
+          for (int d = 0; d < v; ++d) {
+            bcol[l * v + d] = u.blk * V3 + d * b.S[u.pos[0]];
+            bsel[l * v + d] = u.pos[1] * 3 + u.pos[2];
+          }
+        }
+        for (int i = 0; i < o; ++i) {
+          TripleInfo ti = triple(i, j, k);
+          for (int bb = 0; bb < v; ++bb) {
+            ebase[i * v + bb] = ti.blk * V3 + bb * b.S[ti.pos[1]];
+            esel[i * v + bb] = ti.pos[0] * 3 + ti.pos[2];
+            ealpha[i * v + bb] = 6.0 / ti.m;
+          }
+        }
+        make_pack(c, g->A, c->D("Wring_c"), 0, M, K, 1, std::vector<double>(K, 1.0), acol, std::vector<int>(K, 0),
+                  arow, 1, &err);
+        make_pack(c, g->B, t3p, t3f, (int)V2, K, 1, std::vector<double>(K, 1.0), bcol, bsel, {}, 0, &err, b.RT2);
+        make_epi(c, g->E, r3p, t3f, M, (int)V2, ebase, esel, ealpha, {}, &err, b.RT2);
+        g->big = 1;
+        g->step = 2;
+        finish_plan(c, g, K);
+        c->p_ringc.push_back(g);
+      }
+  }
+
+  // --- T2-driven term sum_d W^{ab}_{dj} t_ik^{dc}: unit (j, i<k | i>k | i=k);
+  //     rows (pair, c), cols (a, b), K = d
+  for (int j = 0; j < o; ++j)
+    for (int region = 0; region < 3; ++region) {
+      std::vector<std::pair<int, int>> pairs;
+      for (int i = 0; i < o; ++i)
+        for (int k = 0; k < o; ++k)
+          if ((region == 0 && i < k) || (region == 1 && i > k) || (region == 2 && i == k)) pairs.push_back({i, k});
+      if (pairs.empty()) continue;
+      const int M = (int)pairs.size() * v, K = v;
+      GemmPlan* g = b.new_plan();
+      std::vector<i64> arow(M), acol(K), brow(V2), bcol(K), ebase(M);
+      std::vector<int> esel(M);
+      std::vector<double> ealpha(M);
+      for (int q = 0; q < (int)pairs.size(); ++q)
+        for (int cc = 0; cc < v; ++cc) {
+          int r = q * v + cc;
+          arow[r] = ((i64)pairs[q].first * o + pairs[q].second) * V2 + cc;
+          TripleInfo ti = triple(pairs[q].first, j, pairs[q].second);
+          ebase[r] = ti.blk * V3 + cc * b.S[ti.pos[2]];
+          esel[r] = ti.pos[0] * 3 + ti.pos[1];
+          ealpha[r] = 6.0 / ti.m;
+        }
+      for (int d = 0; d < v; ++d) { acol[d] = (i64)d * v; bcol[d] = (i64)d * o; }
+      for (i64 ab = 0; ab < V2; ++ab) brow[ab] = ab * v * o + j;
+      make_pack(c, g->A, c->D("t2"), 0, M, K, 1, std::vector<double>(K, 1.0), acol, std::vector<int>(K, 0), arow, 0,
+                &err);
+      make_pack(c, g->B, c->D("Wvvvo"), 0, (int)V2, K, 1, std::vector<double>(K, 1.0), bcol, std::vector<int>(K, 0),
+                brow, 0, &err);
+      make_epi(c, g->E, r3p, t3f, M, (int)V2, ebase, esel, ealpha, {}, &err, b.RT2);
+      g->big = 1;
+      g->step = 4;
+      finish_plan(c, g, K);
+      c->p_t2a.push_back(g);
+    }
+
+  if (err) return fail(c, err, "plan construction failed");
+  return 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Iteration steps
+// ---------------------------------------------------------------------------
+namespace {
+
+struct StepTimer {
+  rccsdt_ctx* c;
+  int slot;
+#ifndef RCC_HOSTSIM
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+#endif
+  StepTimer(rccsdt_ctx* c_, int slot_) : c(c_), slot(slot_) {
+#ifndef RCC_HOSTSIM
+    if (c->timing) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, c->stream);
+    }
+#endif
+  }
+  ~StepTimer() {
+#ifndef RCC_HOSTSIM
+    if (c->timing) {
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      c->step_ms[slot] += ms;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
+#endif
+  }
+};
+
+int zero(rccsdt_ctx* c, const char* name) { return dev_zero(c->B(name)->p, c->B(name)->bytes, c->stream); }
+
+int do_intermediates(rccsdt_ctx* c) {
+  StepTimer tm(c, 0);
+  int st = 0;
+  rcc::launch_combine(c->c_Lt_copy, c->stream);
+  if ((st = run_plans(c, c->p_dress))) return st;
+  for (const char* z : {"gamma", "J", "Y", "Kx"}) zero(c, z);
+  // gamma, J, Y, Kx, then F and ft = F, then the two ft dressing plans
+  for (int q = 0; q < 4; ++q)
+    if ((st = run_gemm(c, c->p_fock[q]))) return st;
+  run_combines(c, c->c_fock);
+  for (size_t q = 4; q < c->p_fock.size(); ++q)
+    if ((st = run_gemm(c, c->p_fock[q]))) return st;
+  for (const char* s : {"oooo", "ooov", "oovo", "oovv", "ovov", "ovvo", "ovvv", "vovv", "vooo", "vvoo", "vvvo", "vvvv"})
+    zero(c, s);
+  if ((st = run_plans(c, c->p_eri))) return st;
+  run_combines(c, c->c_helpers);
+  run_combines(c, c->c_int_base);
+  if ((st = run_plans(c, c->p_int))) return st;
+  run_combines(c, c->c_int_after[0]);
+  if ((st = run_plans(c, c->p_a3[c->o]))) return st;
+  // step (iii): T3 -> R1, R2, W^{ab}_{dj}, W^{al}_{ij}
+  zero(c, "dR1");
+  zero(c, "dX2");
+  const int o = c->o;
+  const int t3f = c->opt.precision != RCCSDT_FP64;
+  for (int z = 0; z < o; ++z) {
+    rcc::launch_unpack_spin(c->B("t3")->p, t3f, o * o, (const i64*)c->a3_base->p + (size_t)z * o * o,
+                            (const int*)c->a3_pos->p + (size_t)z * o * o * 3, c->v, c->D("Sz"), c->D("Dz"),
+                            c->stream);
+    if ((st = run_plans(c, c->p_a3[z]))) return st;
+  }
+  c->have_int = 1;
+  return dev_check();
+}
+
+int do_residual(rccsdt_ctx* c) {
+  int st = 0;
+  {
+    StepTimer tm(c, 5);
+    run_combines(c, c->c_r12_base);
+    if ((st = run_plans(c, c->p_r12))) return st;
+    run_combines(c, c->c_r2_sym);
+    zero(c, "r3");
+    run_combines(c, c->c_wt);
+  }
+  {
+    StepTimer tm(c, 1);
+    if ((st = run_plans(c, c->p_pp))) return st;
+  }
+  {
+    StepTimer tm(c, 2);
+    if ((st = run_plans(c, c->p_ringab))) return st;
+    if ((st = run_plans(c, c->p_ringc))) return st;
+  }
+  {
+    StepTimer tm(c, 3);
+    if ((st = run_plans(c, c->p_hh))) return st;
+  }
+  {
+    StepTimer tm(c, 4);
+    if ((st = run_plans(c, c->p_t2a))) return st;
+    const int4* blk = (const int4*)c->blocks_info->p;
+    if (c->opt.precision != RCCSDT_FP64)
+      rcc::launch_t2_outer<float>(c->B("r3")->f(), c->D("Wvooo"), c->D("t2"), blk, c->o, c->v, c->n3, c->stream);
+    else
+      rcc::launch_t2_outer<double>(c->D("r3"), c->D("Wvooo"), c->D("t2"), blk, c->o, c->v, c->n3, c->stream);
+  }
+  c->have_res = 1;
+  return dev_check();
+}
+
+double* scal(rccsdt_ctx* c, int i) { return (double*)c->scalars->p + i; }
+double* partials(rccsdt_ctx* c) { return (double*)c->partial->p; }
+
+// scalars layout: [0..3] norms^2 (r1, r2, r3, total) [4] energy [16..16+M*M) DIIS B, [300..316) coef
+constexpr int kB = 16, kCoef = 300;
+
+int do_postprocess(rccsdt_ctx* c, double norms[4]) {
+  StepTimer tm(c, 6);
+  const int4* blk = (const int4*)c->blocks_info->p;
+  const bool f = c->opt.precision != RCCSDT_FP64;
+  const i64 V3 = c->V3;
+  if (f)
+    rcc::launch_post<float>(c->B("r3")->f(), c->B("rp3")->f(), blk, c->v, c->n3, c->stream);
+  else
+    rcc::launch_post<double>(c->D("r3"), c->D("rp3"), blk, c->v, c->n3, c->stream);
+  rcc::launch_wdot<double>(c->D("r1"), c->D("r1"), (i64)c->o * c->v, 1, nullptr, partials(c), scal(c, 0), 1.0, 0,
+                           c->stream);
+  rcc::launch_wdot<double>(c->D("r2"), c->D("r2"), (i64)c->o * c->o * c->v * c->v, 1, nullptr, partials(c),
+                           scal(c, 1), 1.0, 0, c->stream);
+  if (f)
+    rcc::launch_wdot<float>(c->B("rp3")->f(), c->B("rp3")->f(), c->n3 * V3, V3, c->blk_weight->d(), partials(c),
+                            scal(c, 2), 1.0, 0, c->stream);
+  else
+    rcc::launch_wdot<double>(c->D("rp3"), c->D("rp3"), c->n3 * V3, V3, c->blk_weight->d(), partials(c), scal(c, 2),
+                             1.0, 0, c->stream);
+  if (norms) {
+    double h[3];
+    if (dev_copy(h, scal(c, 0), sizeof(h), c->stream) || dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+    norms[0] = sqrt(h[0]);
+    norms[1] = sqrt(h[1]);
+    norms[2] = sqrt(h[2]);
+    norms[3] = sqrt(h[0] + h[1] + h[2]);
+    for (int q = 0; q < 4; ++q)
+      if (!std::isfinite(norms[q])) return fail(c, RCCSDT_ERR_NONFINITE, "non-finite residual norm");
+  }
+  return dev_check();
+}
+
+// Segment views of history slot s: t1 | t2 | t3 (t3 of the storage type).
+struct Seg {
+  double* t1;
+  double* t2;
+  void* t3;
+};
+Seg slot(rccsdt_ctx* c, int q) {
+  const int M = c->opt.diis_space;
+  char* p = q < M ? (char*)c->hist_t->p + (i64)q * c->hist_stride : (char*)c->hist_e->p + (i64)(q - M) * c->hist_stride;
+  Seg s;
+  s.t1 = (double*)p;
+  s.t2 = (double*)(p + c->seg1 * 8);
+  s.t3 = p + (c->seg1 + c->seg2) * 8;
+  return s;
+}
+
+int do_update(rccsdt_ctx* c) {
+  StepTimer tm(c, 7);
+  const int o = c->o, v = c->v;
+  const bool f = c->opt.precision != RCCSDT_FP64;
+  const int4* blk = (const int4*)c->blocks_info->p;
+  const int M = c->opt.diis_space;
+  const bool dt3 = c->opt.diis_t3 != 0;
+  c->iter += 1;
+  int s = -1;
+  if (M > 0) {
+    s = c->diis_count % M;
+    Seg e = slot(c, M + s);
+    // old amplitudes into the error slot, then e = t_new - t_old after the step
+    dev_copy(e.t1, c->D("t1"), c->seg1 * 8, c->stream);
+    dev_copy(e.t2, c->D("t2"), c->seg2 * 8, c->stream);
+    if (dt3) dev_copy(e.t3, c->B("t3")->p, c->seg3 * (f ? 4 : 8), c->stream);
+  }
+  rcc::launch_update_t12(c->D("t1"), c->D("r1"), c->D("t2"), c->D("r2"), c->D("e"), o, v, 0.0, c->stream);
+  if (f)
+    rcc::launch_update_t3<float>(c->B("t3")->f(), c->B("rp3")->f(), c->D("e"), blk, o, v, c->n3, 0.0, c->stream);
+  else
+    rcc::launch_update_t3<double>(c->D("t3"), c->D("rp3"), c->D("e"), blk, o, v, c->n3, 0.0, c->stream);
+  if (M <= 0) return dev_check();
+  Seg tn = slot(c, s), e = slot(c, M + s);
+  rcc::launch_sub<double>(e.t1, c->D("t1"), e.t1, c->seg1, c->stream);
+  rcc::launch_sub<double>(e.t2, c->D("t2"), e.t2, c->seg2, c->stream);
+  dev_copy(tn.t1, c->D("t1"), c->seg1 * 8, c->stream);
+  dev_copy(tn.t2, c->D("t2"), c->seg2 * 8, c->stream);
+  if (dt3) {
+    if (f) rcc::launch_sub<float>((float*)e.t3, c->B("t3")->f(), (const float*)e.t3, c->seg3, c->stream);
+    else rcc::launch_sub<double>((double*)e.t3, c->D("t3"), (const double*)e.t3, c->seg3, c->stream);
+    dev_copy(tn.t3, c->B("t3")->p, c->seg3 * (f ? 4 : 8), c->stream);
+  }
+  c->diis_count += 1;
+  const int m = std::min(c->diis_count, M);
+  // new row / column of B
+  for (int q = 0; q < m; ++q) {
+    Seg eq = slot(c, M + q);
+    double* out = scal(c, kB + s * M + q);
+    rcc::launch_wdot<double>(e.t1, eq.t1, c->seg1, 1, nullptr, partials(c), out, 1.0, 0, c->stream);
+    rcc::launch_wdot<double>(e.t2, eq.t2, c->seg2, 1, nullptr, partials(c), out, 1.0, 1, c->stream);
+    if (dt3) {
+      if (f)
+        rcc::launch_wdot<float>((const float*)e.t3, (const float*)eq.t3, c->seg3, c->V3, c->blk_weight->d(),
+                                partials(c), out, 1.0, 1, c->stream);
+      else
+        rcc::launch_wdot<double>((const double*)e.t3, (const double*)eq.t3, c->seg3, c->V3, c->blk_weight->d(),
+                                 partials(c), out, 1.0, 1, c->stream);
+    }
+    dev_copy(scal(c, kB + q * M + s), out, 8, c->stream);
+  }
+  if (c->iter >= c->opt.diis_start && m >= 2) {
+    rcc::launch_diis_solve(scal(c, kB), m, M, scal(c, kCoef), c->stream);
+    rcc::launch_diis_extrapolate<double>(c->D("t1"), slot(c, 0).t1, c->hist_stride / 8, c->seg1, scal(c, kCoef), m,
+                                         c->stream);
+    rcc::launch_diis_extrapolate<double>(c->D("t2"), slot(c, 0).t2, c->hist_stride / 8, c->seg2, scal(c, kCoef), m,
+                                         c->stream);
+    if (dt3) {
+      if (f)
+        rcc::launch_diis_extrapolate<float>(c->B("t3")->f(), (const float*)slot(c, 0).t3, c->hist_stride / 4, c->seg3,
+                                            scal(c, kCoef), m, c->stream);
+      else
+        rcc::launch_diis_extrapolate<double>(c->D("t3"), (const double*)slot(c, 0).t3, c->hist_stride / 8, c->seg3,
+                                             scal(c, kCoef), m, c->stream);
+    }
+  }
+  return dev_check();
+}
+
+int do_energy(rccsdt_ctx* c, double* e_out) {
+  StepTimer tm(c, 8);
+  rcc::launch_energy(c->D("ovov_bare"), c->D("t1"), c->D("t2"), c->o, c->v, partials(c), scal(c, 4), c->stream);
+  if (e_out) {
+    if (dev_copy(e_out, scal(c, 4), 8, c->stream) || dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+    if (!std::isfinite(*e_out)) return fail(c, RCCSDT_ERR_NONFINITE, "non-finite energy");
+  }
+  return dev_check();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+#define RCC_API extern "C" __attribute__((visibility("default")))
+
+RCC_API int rccsdt_options_default(rccsdt_options* opt) {
+  if (!opt) return RCCSDT_ERR_ARG;
+  memset(opt, 0, sizeof(*opt));
+  opt->precision = RCCSDT_FP64;
+  opt->final_fp64_iters = 2;
+  opt->diis_space = 8;
+  opt->diis_start = 2;
+  opt->diis_t3 = 1;
+  opt->max_iter = 100;
+  opt->tol = 1e-8;
+  opt->watchdog_cycles = 0;
+  return RCCSDT_OK;
+}
+
+RCC_API int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, void* stream, rccsdt_ctx** out) {
+  if (!out) return RCCSDT_ERR_ARG;
+  *out = nullptr;
+  if (o < 1 || v < 1 || naux < 1 || o > 64 || v > 4096) return RCCSDT_ERR_ARG;
+  rccsdt_options def;
+  rccsdt_options_default(&def);
+  const rccsdt_options& op = opt ? *opt : def;
+  if (op.precision < 0 || op.precision > 2 || op.diis_space < 0 || op.diis_space > 16) return RCCSDT_ERR_ARG;
+  auto* c = new rccsdt_ctx();
+  c->o = o; c->v = v; c->n = o + v; c->naux = naux;
+  c->n3 = n3_of(o);
+  c->V3 = (i64)v * v * v;
+  c->opt = op;
+  c->precision = op.precision;
+  c->stream = (cudaStream_t)stream;
+  int err = 0;
+  c->scalars = upload_vec(c, std::vector<double>(2048, 0.0), &err);
+  c->partial = upload_vec(c, std::vector<double>(rcc::kDotBlocks, 0.0), &err);
+  int st = err ? RCCSDT_ERR_OOM : build_context(c);
+  if (!st) {
+    // engine panels (hi planes hold doubles in FP64 mode; lo planes only for split modes)
+    c->panelA_hi = std::make_unique<DBuf>();
+    c->panelB_hi = std::make_unique<DBuf>();
+    c->panelA_hi->p = dev_alloc(c->panel_bytes, &err);
+    c->panelB_hi->p = dev_alloc(c->panel_bytes, &err);
+    c->total_bytes += 2 * c->panel_bytes;
+    if (op.precision != RCCSDT_FP64) {
+      c->panelA_lo = std::make_unique<DBuf>();
+      c->panelB_lo = std::make_unique<DBuf>();
+      c->panelA_lo->p = dev_alloc(c->panel_bytes / 2, &err);
+      c->panelB_lo->p = dev_alloc(c->panel_bytes / 2, &err);
+      c->total_bytes += c->panel_bytes;
+    }
+    // DIIS history
+    c->seg1 = (i64)o * v;
+    c->seg2 = (i64)o * o * v * v;
+    c->seg3 = op.diis_t3 ? c->n3 * c->V3 : 0;
+    const i64 t3e = op.precision != RCCSDT_FP64 ? 4 : 8;
+    c->hist_stride = ((c->seg1 + c->seg2) * 8 + c->seg3 * t3e + 15) / 16 * 16;
+    if (op.diis_space > 0) {
+      c->hist_t = std::make_unique<DBuf>();
+      c->hist_e = std::make_unique<DBuf>();
+      c->hist_t->p = dev_alloc((size_t)c->hist_stride * op.diis_space, &err);
+      c->hist_e->p = dev_alloc((size_t)c->hist_stride * op.diis_space, &err);
+      c->total_bytes += 2 * (size_t)c->hist_stride * op.diis_space;
+    }
+    if (err) st = fail(c, RCCSDT_ERR_OOM, "device allocation failed");
+  }
+  if (st) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return RCCSDT_OK;
+}
+
+RCC_API long long rccsdt_device_bytes(const rccsdt_ctx* c) { return c ? (long long)c->total_bytes : 0; }
+
+RCC_API int rccsdt_set_hamiltonian(rccsdt_ctx* c, const double* fock_diag, const double* L) {
+  if (!c || !fock_diag || !L) return fail(c, RCCSDT_ERR_ARG, "null argument");
+  if (dev_copy(c->D("e"), fock_diag, (size_t)c->n * 8, c->stream) ||
+      dev_copy(c->D("L"), L, (size_t)c->naux * c->n * c->n * 8, c->stream))
+    return fail(c, RCCSDT_ERR_CUDA, "copy failed");
+  dev_zero(c->B("ovov_bare")->p, c->B("ovov_bare")->bytes, c->stream);
+  int st = run_plans(c, c->p_energy_bare);
+  if (st) return st;
+  if (dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "set_hamiltonian failed");
+  c->have_ham = 1;
+  c->have_int = c->have_res = 0;
+  return RCCSDT_OK;
+}
+
+static void reset_diis(rccsdt_ctx* c) {
+  c->diis_count = 0;
+  c->iter = 0;
+}
+
+RCC_API int rccsdt_set_amplitudes(rccsdt_ctx* c, const double* t1, const double* t2, const double* t3c) {
+  if (!c) return RCCSDT_ERR_ARG;
+  const bool f = c->opt.precision != RCCSDT_FP64;
+  if (t1 && dev_copy(c->D("t1"), t1, (size_t)c->seg1 * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+  if (t2 && dev_copy(c->D("t2"), t2, (size_t)c->o * c->o * c->v * c->v * 8, c->stream))
+    return fail(c, RCCSDT_ERR_CUDA, "copy");
+  if (t3c) {
+    const i64 cnt = c->n3 * c->V3;
+    if (!f) {
+      if (dev_copy(c->D("t3"), t3c, (size_t)cnt * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+    } else {
+      // stage the FP64 values in rp3's storage (as doubles, chunked) and convert
+      const i64 chunk = c->B("rp3")->bytes / 8;
+      for (i64 off = 0; off < cnt; off += chunk) {
+        const i64 len = std::min(chunk, cnt - off);
+        if (dev_copy(c->B("rp3")->p, t3c + off, (size_t)len * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+        rcc::launch_convert<float, double>(c->B("t3")->f() + off, (const double*)c->B("rp3")->p, len, c->stream);
+      }
+    }
+  }
+  if (dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "set_amplitudes failed");
+  c->have_amp = 1;
+  c->have_int = c->have_res = 0;
+  reset_diis(c);
+  return RCCSDT_OK;
+}
+
+RCC_API int rccsdt_init_mp2(rccsdt_ctx* c) {
+  if (!c) return RCCSDT_ERR_ARG;
+  if (!c->have_ham) return fail(c, RCCSDT_ERR_STATE, "hamiltonian not set");
+  zero(c, "t1");
+  zero(c, "t3");
+  rcc::launch_mp2(c->D("t2"), c->D("ovov_bare"), c->D("e"), c->o, c->v, c->stream);
+  if (dev_sync(c->stream) || dev_check()) return fail(c, RCCSDT_ERR_CUDA, "init_mp2 failed");
+  c->have_amp = 1;
+  c->have_int = c->have_res = 0;
+  reset_diis(c);
+  return RCCSDT_OK;
+}
+
+RCC_API int rccsdt_set_precision(rccsdt_ctx* c, int precision) {
+  if (!c || precision < 0 || precision > 2) return fail(c, RCCSDT_ERR_ARG, "bad precision");
+  if ((precision != RCCSDT_FP64) != (c->opt.precision != RCCSDT_FP64) && precision != RCCSDT_FP64)
+    return fail(c, RCCSDT_ERR_ARG, "a context created in FP64 mode has no split-precision panels");
+  c->precision = precision;
+  return RCCSDT_OK;
+}
+
+static int need(rccsdt_ctx* c, bool amp, bool inter, bool res) {
+  if (!c) return RCCSDT_ERR_ARG;
+  if (!c->have_ham) return fail(c, RCCSDT_ERR_STATE, "hamiltonian not set");
+  if (amp && !c->have_amp) return fail(c, RCCSDT_ERR_STATE, "amplitudes not set");
+  if (inter && !c->have_int) return fail(c, RCCSDT_ERR_STATE, "intermediates not built");
+  if (res && !c->have_res) return fail(c, RCCSDT_ERR_STATE, "residual not computed");
+  return 0;
+}
+
+RCC_API int rccsdt_build_intermediates(rccsdt_ctx* c) {
+  int st = need(c, true, false, false);
+  if (st) return st;
+  st = do_intermediates(c);
+  return st ? st : (dev_sync(c->stream) ? fail(c, RCCSDT_ERR_CUDA, "intermediates failed") : 0);
+}
+
+RCC_API int rccsdt_residual(rccsdt_ctx* c) {
+  int st = need(c, true, true, false);
+  if (st) return st;
+  st = do_residual(c);
+  return st ? st : (dev_sync(c->stream) ? fail(c, RCCSDT_ERR_CUDA, "residual failed") : 0);
+}
+
+RCC_API int rccsdt_postprocess(rccsdt_ctx* c, double norms[4]) {
+  int st = need(c, true, true, true);
+  if (st) return st;
+  return do_postprocess(c, norms);
+}
+
+RCC_API int rccsdt_update(rccsdt_ctx* c) {
+  int st = need(c, true, true, true);
+  if (st) return st;
+  st = do_update(c);
+  c->have_int = c->have_res = 0;
+  return st ? st : (dev_sync(c->stream) ? fail(c, RCCSDT_ERR_CUDA, "update failed") : 0);
+}
+
+RCC_API int rccsdt_energy(rccsdt_ctx* c, double* e) {
+  int st = need(c, true, false, false);
+  if (st) return st;
+  double tmp;
+  return do_energy(c, e ? e : &tmp);
+}
+
+RCC_API int rccsdt_iterate(rccsdt_ctx* c, double* e, double norms[4]) {
+  int st = need(c, true, false, false);
+  if (st) return st;
+  for (double& x : c->step_ms) x = 0.0;
+  double tmp[4], et;
+  if ((st = do_energy(c, nullptr))) return st;
+  if ((st = do_intermediates(c))) return st;
+  if ((st = do_residual(c))) return st;
+  if ((st = do_postprocess(c, norms ? norms : tmp))) return st;
+  if ((st = do_update(c))) return st;
+  c->have_int = c->have_res = 0;
+  if (dev_copy(&et, scal(c, 4), 8, c->stream) || dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "iterate");
+  if (!std::isfinite(et)) return fail(c, RCCSDT_ERR_NONFINITE, "non-finite energy");
+  if (e) *e = et;
+  return RCCSDT_OK;
+}
+
+RCC_API int rccsdt_solve(rccsdt_ctx* c, double* e_corr, int* iterations, double* final_norm) {
+  int st = need(c, true, false, false);
+  if (st) return st;
+  const int split = c->opt.precision != RCCSDT_FP64;
+  int fp64_left = -1;
+  double e = 0, norms[4] = {0, 0, 0, 0};
+  for (int it = 1; it <= c->opt.max_iter; ++it) {
+    if (split) {
+      if (fp64_left < 0 && (it == 1 ? false : norms[3] <= sqrt(c->opt.tol))) fp64_left = c->opt.final_fp64_iters;
+      rccsdt_set_precision(c, fp64_left >= 0 ? RCCSDT_FP64 : c->opt.precision);
+    }
+    // evaluate at the current amplitudes; stop before updating when converged
+    if ((st = do_energy(c, &e))) return st;
+    if ((st = do_intermediates(c))) return st;
+    if ((st = do_residual(c))) return st;
+    if ((st = do_postprocess(c, norms))) return st;
+    if (iterations) *iterations = it;
+    if (final_norm) *final_norm = norms[3];
+    if (e_corr) *e_corr = e;
+    if (norms[3] <= c->opt.tol && (!split || fp64_left >= 0)) {
+      if (split) rccsdt_set_precision(c, c->opt.precision);
+      return RCCSDT_OK;
+    }
+    if ((st = do_update(c))) return st;
+    if (split && fp64_left > 0) --fp64_left;
+  }
+  if (split) rccsdt_set_precision(c, c->opt.precision);
+  return RCCSDT_NOT_CONVERGED;
+}
+
+RCC_API int rccsdt_get_amplitudes(rccsdt_ctx* c, double* t1, double* t2, double* t3c) {
+  if (!c) return RCCSDT_ERR_ARG;
+  const bool f = c->opt.precision != RCCSDT_FP64;
+  if (t1 && dev_copy(t1, c->D("t1"), (size_t)c->seg1 * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+  if (t2 && dev_copy(t2, c->D("t2"), (size_t)c->o * c->o * c->v * c->v * 8, c->stream))
+    return fail(c, RCCSDT_ERR_CUDA, "copy");
+  if (t3c) {
+    const i64 cnt = c->n3 * c->V3;
+    if (!f) {
+      if (dev_copy(t3c, c->D("t3"), (size_t)cnt * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+    } else {
+      const i64 chunk = c->B("Sz")->bytes / 8;
+      for (i64 off = 0; off < cnt; off += chunk) {
+        const i64 len = std::min(chunk, cnt - off);
+        rcc::launch_convert<double, float>(c->D("Sz"), c->B("t3")->f() + off, len, c->stream);
+        if (dev_copy(t3c + off, c->D("Sz"), (size_t)len * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+      }
+    }
+  }
+  return dev_sync(c->stream) ? fail(c, RCCSDT_ERR_CUDA, "get_amplitudes failed") : 0;
+}
+
+RCC_API int rccsdt_get_residuals(rccsdt_ctx* c, double* r1, double* r2, double* r3c) {
+  if (!c) return RCCSDT_ERR_ARG;
+  const bool f = c->opt.precision != RCCSDT_FP64;
+  if (r1 && dev_copy(r1, c->D("r1"), (size_t)c->seg1 * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+  if (r2 && dev_copy(r2, c->D("r2"), (size_t)c->o * c->o * c->v * c->v * 8, c->stream))
+    return fail(c, RCCSDT_ERR_CUDA, "copy");
+  if (r3c) {
+    const i64 cnt = c->n3 * c->V3;
+    if (!f) {
+      if (dev_copy(r3c, c->D("r3"), (size_t)cnt * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+    } else {
+      const i64 chunk = c->B("Sz")->bytes / 8;
+      for (i64 off = 0; off < cnt; off += chunk) {
+        const i64 len = std::min(chunk, cnt - off);
+        rcc::launch_convert<double, float>(c->D("Sz"), c->B("r3")->f() + off, len, c->stream);
+        if (dev_copy(r3c + off, c->D("Sz"), (size_t)len * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+      }
+    }
+  }
+  return dev_sync(c->stream) ? fail(c, RCCSDT_ERR_CUDA, "get_residuals failed") : 0;
+}
+
+RCC_API int rccsdt_debug_copy(rccsdt_ctx* c, const char* name, double* out, long long count) {
+  if (!c || !name || !out) return RCCSDT_ERR_ARG;
+  auto it = c->buf.find(name);
+  if (it == c->buf.end()) return fail(c, RCCSDT_ERR_ARG, std::string("no tensor ") + name);
+  if ((size_t)count * 8 > it->second->bytes) return fail(c, RCCSDT_ERR_ARG, "count too large");
+  if (dev_copy(out, it->second->p, (size_t)count * 8, c->stream) || dev_sync(c->stream))
+    return fail(c, RCCSDT_ERR_CUDA, "copy");
+  return RCCSDT_OK;
+}
+
+RCC_API double rccsdt_iteration_fma(int o, int v) {
+  const double n3 = (double)o * (o + 1) * (o + 2) / 6.0, V = v;
+  return n3 * (3.0 * V * V * V * V * V + 12.0 * o * V * V * V * V + 3.0 * (double)o * o * V * V * V);
+}
+
+RCC_API int rccsdt_enable_timing(rccsdt_ctx* c, int on) {
+  if (!c) return RCCSDT_ERR_ARG;
+  c->timing = on ? 1 : 0;
+  return RCCSDT_OK;
+}
+
+RCC_API int rccsdt_step_times(rccsdt_ctx* c, double* ms, int cap) {
+  if (!c || !ms) return RCCSDT_ERR_ARG;
+  const int n = std::min(cap, 9);
+  for (int q = 0; q < n; ++q) ms[q] = c->step_ms[q];
+  return n;
+}
+
+RCC_API const char* rccsdt_last_error(const rccsdt_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+RCC_API void rccsdt_destroy(rccsdt_ctx* c) {
+  if (!c) return;
+  dev_sync(c->stream);
+  delete c;
+}

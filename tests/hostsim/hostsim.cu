@@ -1,0 +1,247 @@
+// TEST-ONLY host simulation of the RCCSDT library's kernels.
+//
+// Built together with the library's runtime (compiled with -DRCC_HOSTSIM) into a
+// separate shared object that only the CPU tests load.  It executes the very
+// plans (gather tables, scatter tables, term lists) of the CUDA library with
+// plain host loops over the same per-element functions (elem.cuh), so the host
+// logic can be checked against the oracle without a GPU.  The product binding
+// never loads it; the CUDA library has no CPU path.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "elem.cuh"
+#include "kernels.h"
+
+namespace rcc {
+
+void launch_pack(const PackArgs& a, cudaStream_t) {
+  for (int r = 0; r < a.R; ++r)
+    for (int k = 0; k < a.Kpad; ++k) store_panel(a, r, k, k < a.K ? pack_value(a, r, k) : 0.0);
+}
+
+void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, const EpiArgs& e, cudaStream_t) {
+  for (int m = 0; m < e.M; ++m)
+    for (int n = 0; n < e.N; ++n) {
+      double s = 0.0;
+      for (int k = 0; k < K; ++k) s += A[(i64)m * lda + k] * B[(i64)n * ldb + k];
+      epi_apply(e, m, n, s);
+    }
+}
+
+// Split-precision product hi*hi + hi*lo + lo*hi with float products and a float
+// accumulator (the order of the tensor-core sum is not modelled).
+int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int Kpad,
+                   const EpiArgs& e, int*, long long, cudaStream_t) {
+  auto get = [&](const void* p, i64 i) -> float {
+    if (kind == PANEL_BF16X2) return __bfloat162float(((const __nv_bfloat16*)p)[i]);
+    return ((const float*)p)[i];
+  };
+  for (int m = 0; m < e.M; ++m)
+    for (int n = 0; n < e.N; ++n) {
+      float s = 0.f;
+      for (int k = 0; k < Kpad; ++k) {
+        const i64 ia = (i64)m * Kpad + k, ib = (i64)n * Kpad + k;
+        const float ah = get(Ahi, ia), al = get(Alo, ia), bh = get(Bhi, ib), bl = get(Blo, ib);
+        s += ah * bh + ah * bl + al * bh;
+      }
+      epi_apply(e, m, n, (double)s);
+    }
+  return 0;
+}
+
+void launch_combine(const CombineArgs& c, cudaStream_t) {
+  for (i64 idx = 0; idx < c.total; ++idx) {
+    i64 rem = idx, ooff = 0;
+    i64 ioff[4] = {0, 0, 0, 0};
+    for (int d = c.rank - 1; d >= 0; --d) {
+      const i64 x = rem % c.shape[d];
+      rem /= c.shape[d];
+      ooff += x * c.ostride[d];
+      for (int t = 0; t < c.nterm; ++t) ioff[t] += x * c.istride[t][d];
+    }
+    double s = c.beta == 0.0 ? 0.0 : c.beta * c.out[ooff];
+    for (int t = 0; t < c.nterm; ++t) s += c.coef[t] * c.in[t][ioff[t]];
+    c.out[ooff] = s;
+  }
+}
+
+template <typename T>
+void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStream_t) {
+  const i64 V3 = (i64)v * v * v;
+  for (i64 b = 0; b < n3; ++b)
+    for (i64 e = 0; e < V3; ++e) {
+      const int c = (int)(e % v), bb = (int)((e / v) % v), a = (int)(e / ((i64)v * v));
+      rp[b * V3 + e] = (T)post_value(r + b * V3, v, blocks[b].x, blocks[b].y, blocks[b].z, a, bb, c);
+    }
+}
+template void launch_post<double>(const double*, double*, const int4*, int, i64, cudaStream_t);
+template void launch_post<float>(const float*, float*, const int4*, int, i64, cudaStream_t);
+
+void launch_update_t12(double* t1, const double* r1, double* t2, const double* r2, const double* e, int o, int v,
+                       double shift, cudaStream_t) {
+  for (int i = 0; i < o; ++i)
+    for (int a = 0; a < v; ++a) t1[i * v + a] += r1[i * v + a] / (e[i] - e[o + a] - shift);
+  for (int i = 0; i < o; ++i)
+    for (int j = 0; j < o; ++j)
+      for (int a = 0; a < v; ++a)
+        for (int b = 0; b < v; ++b) {
+          const i64 x = (((i64)i * o + j) * v + a) * v + b;
+          t2[x] += r2[x] / (e[i] + e[j] - e[o + a] - e[o + b] - shift);
+        }
+}
+
+template <typename T>
+void launch_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, int o, int v, i64 n3, double shift,
+                      cudaStream_t) {
+  const i64 V3 = (i64)v * v * v;
+  for (i64 b = 0; b < n3; ++b)
+    for (i64 x = 0; x < V3; ++x) {
+      const int c = (int)(x % v), bb = (int)((x / v) % v), a = (int)(x / ((i64)v * v));
+      const double d = e[blocks[b].x] + e[blocks[b].y] + e[blocks[b].z] - e[o + a] - e[o + bb] - e[o + c] - shift;
+      t3[b * V3 + x] = (T)((double)t3[b * V3 + x] + (double)rp3[b * V3 + x] / d);
+    }
+}
+template void launch_update_t3<double>(double*, const double*, const double*, const int4*, int, int, i64, double,
+                                       cudaStream_t);
+template void launch_update_t3<float>(float*, const float*, const double*, const int4*, int, int, i64, double,
+                                      cudaStream_t);
+
+template <typename T>
+void launch_wdot(const T* x, const T* y, i64 n, i64 seg, const double* w, double*, double* out, double scale,
+                 int accumulate, cudaStream_t) {
+  double s = 0.0;
+  for (i64 i = 0; i < n; ++i) s += (double)x[i] * (double)y[i] * (w ? w[i / seg] : 1.0);
+  *out = (accumulate ? *out : 0.0) + scale * s;
+}
+template void launch_wdot<double>(const double*, const double*, i64, i64, const double*, double*, double*, double,
+                                  int, cudaStream_t);
+template void launch_wdot<float>(const float*, const float*, i64, i64, const double*, double*, double*, double, int,
+                                 cudaStream_t);
+
+template <typename T>
+void launch_t2_outer(T* r3, const double* Wvooo, const double* t2, const int4* blocks, int o, int v, i64 n3,
+                     cudaStream_t) {
+  const i64 V3 = (i64)v * v * v;
+  const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  for (i64 b = 0; b < n3; ++b) {
+    const int occ[3] = {blocks[b].x, blocks[b].y, blocks[b].z};
+    for (i64 x = 0; x < V3; ++x) {
+      const int lab[3] = {(int)(x / ((i64)v * v)), (int)((x / v) % v), (int)(x % v)};
+      double s = 0.0;
+      for (int q = 0; q < 6; ++q) {
+        const int i1 = occ[P[q][0]], i2 = occ[P[q][1]], i3 = occ[P[q][2]];
+        const int a1 = lab[P[q][0]], a2 = lab[P[q][1]], a3 = lab[P[q][2]];
+        for (int l = 0; l < o; ++l)
+          s -= Wvooo[(((i64)a1 * o + l) * o + i1) * o + i2] * t2[(((i64)l * o + i3) * v + a2) * v + a3];
+      }
+      r3[b * V3 + x] = (T)((double)r3[b * V3 + x] + s);
+    }
+  }
+}
+template void launch_t2_outer<double>(double*, const double*, const double*, const int4*, int, int, i64,
+                                      cudaStream_t);
+template void launch_t2_outer<float>(float*, const double*, const double*, const int4*, int, int, i64, cudaStream_t);
+
+void launch_diis_solve(const double* Bm, int m, int ld, double* coef, cudaStream_t) {
+  const int n = m + 1;
+  std::vector<double> A((size_t)n * (n + 1));
+  double scale = 0.0;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) scale = std::fmax(scale, std::fabs(Bm[i * ld + j]));
+  if (scale == 0.0) scale = 1.0;
+  auto at = [&](int i, int j) -> double& { return A[(size_t)i * (n + 1) + j]; };
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) at(i, j) = (i < m && j < m) ? Bm[i * ld + j] / scale : (i == m && j == m ? 0.0 : 1.0);
+    at(i, n) = i == m ? 1.0 : 0.0;
+  }
+  std::vector<int> ok(n);
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int i = c + 1; i < n; ++i)
+      if (std::fabs(at(i, c)) > std::fabs(at(p, c))) p = i;
+    if (p != c)
+      for (int j = 0; j <= n; ++j) std::swap(at(c, j), at(p, j));
+    ok[c] = std::fabs(at(c, c)) > 1e-14;
+    if (!ok[c]) continue;
+    for (int i = c + 1; i < n; ++i) {
+      const double f = at(i, c) / at(c, c);
+      for (int j = c; j <= n; ++j) at(i, j) -= f * at(c, j);
+    }
+  }
+  std::vector<double> x(n);
+  for (int c = n - 1; c >= 0; --c) {
+    if (!ok[c]) { x[c] = 0.0; continue; }
+    double s = at(c, n);
+    for (int j = c + 1; j < n; ++j) s -= at(c, j) * x[j];
+    x[c] = s / at(c, c);
+  }
+  for (int i = 0; i < m; ++i) coef[i] = x[i];
+}
+
+template <typename T>
+void launch_diis_extrapolate(T* out, const T* hist, i64 stride, i64 n, const double* coef, int m, cudaStream_t) {
+  for (i64 i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int q = 0; q < m; ++q) s += coef[q] * (double)hist[q * stride + i];
+    out[i] = (T)s;
+  }
+}
+template void launch_diis_extrapolate<double>(double*, const double*, i64, i64, const double*, int, cudaStream_t);
+template void launch_diis_extrapolate<float>(float*, const float*, i64, i64, const double*, int, cudaStream_t);
+
+template <typename T>
+void launch_sub(T* out, const T* a, const T* b, i64 n, cudaStream_t) {
+  for (i64 i = 0; i < n; ++i) out[i] = (T)((double)a[i] - (double)b[i]);
+}
+template void launch_sub<double>(double*, const double*, const double*, i64, cudaStream_t);
+template void launch_sub<float>(float*, const float*, const float*, i64, cudaStream_t);
+
+template <typename TO, typename TI>
+void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t) {
+  for (i64 i = 0; i < n; ++i) out[i] = (TO)in[i];
+}
+template void launch_convert<float, double>(float*, const double*, i64, cudaStream_t);
+template void launch_convert<double, float>(double*, const float*, i64, cudaStream_t);
+template void launch_convert<double, double>(double*, const double*, i64, cudaStream_t);
+
+void launch_energy(const double* g, const double* t1, const double* t2, int o, int v, double*, double* out,
+                   cudaStream_t) {
+  double s = 0.0;
+  for (int i = 0; i < o; ++i)
+    for (int j = 0; j < o; ++j)
+      for (int a = 0; a < v; ++a)
+        for (int b = 0; b < v; ++b) {
+          const double giajb = g[(((i64)i * v + a) * o + j) * v + b], gibja = g[(((i64)i * v + b) * o + j) * v + a];
+          s += (2.0 * giajb - gibja) * (t2[(((i64)i * o + j) * v + a) * v + b] + t1[i * v + a] * t1[j * v + b]);
+        }
+  *out = s;
+}
+
+void launch_mp2(double* t2, const double* g, const double* e, int o, int v, cudaStream_t) {
+  for (int i = 0; i < o; ++i)
+    for (int j = 0; j < o; ++j)
+      for (int a = 0; a < v; ++a)
+        for (int b = 0; b < v; ++b)
+          t2[(((i64)i * o + j) * v + a) * v + b] =
+              g[(((i64)i * v + a) * o + j) * v + b] / (e[i] + e[j] - e[o + a] - e[o + b]);
+}
+
+void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, double* S,
+                        double* D, cudaStream_t) {
+  const i64 V3 = (i64)v * v * v;
+  const i64 sv[3] = {(i64)v * v, v, 1};
+  for (int t = 0; t < ntrip; ++t) {
+    const i64 s0 = sv[pos[3 * t]], s1 = sv[pos[3 * t + 1]], s2 = sv[pos[3 * t + 2]];
+    auto U = [&](int x, int y, int z) { return load_src(t3, f32, base[t] + x * s0 + y * s1 + z * s2); };
+    for (i64 e = 0; e < V3; ++e) {
+      const int c = (int)(e % v), b = (int)((e / v) % v), a = (int)(e / ((i64)v * v));
+      if (S) S[t * V3 + e] = 2.0 * U(a, b, c) - U(b, a, c) - U(c, b, a);
+      if (D)
+        D[t * V3 + e] = 4.0 * U(a, b, c) - 2.0 * U(b, a, c) - 2.0 * U(c, b, a) - 2.0 * U(a, c, b) + U(c, a, b) +
+                        U(b, c, a);
+    }
+  }
+}
+
+}  // namespace rcc

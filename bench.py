@@ -1,0 +1,296 @@
+"""RCCSDT iteration benchmark on one GB300 (replicas under torchrun).
+
+A step is one whole RCCSDT iteration through the C ABI (``rccsdt_iterate``):
+energy, T1-dressing, intermediates, the T3 contributions to R1/R2/W, the
+residuals R1, R2 and the compact R3 (pp-ladder, ring, hh-ladder, T2-driven
+terms), post-processing of R3, the Jacobi update and DIIS.  Inputs are seeded
+synthetic low-rank Hamiltonians; amplitudes start from the MP2 guess.
+
+Prints one JSON line (rank 0).  ``value`` is seconds per iteration of the whole
+job (the slowest rank's timed region divided by the iterations all ranks ran);
+``tflops`` counts the algorithmic compact FMA n3 (3v^5 + 12ov^4 + 3o^2v^3) once.
+``--impl reference`` times the FP64 CPU oracle instead, on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RCCSDT s/iteration and TFLOP/s at 1 GB300, FP64 vs split-precision at <=1e-6 Eh"
+PRECISIONS = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
+DTYPE = {"fp64": "f64", "bf16x3": "bf16x3 (fp32 accumulate, fp32 T3)", "tf32x3": "tf32x3 (fp32 accumulate, fp32 T3)"}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu, self.rows, self.proc = gpu, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in self.rows for q in range(4) if len(r) > 5 + q and r[5 + q] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def oracle_sample(inst, seconds_budget=20.0):
+    """Time the FP64 oracle's compact R3 block work on a bounded subset of blocks.
+
+    The sample is the oracle's ``r3_block`` (pp-ladder, ring, hh-ladder, F and T2
+    terms of one stored block) on the first blocks of a stride through the block
+    list, with intermediates built once outside the timed region; the time is
+    extrapolated to all n3 blocks by block count.  Returns (s/iteration, sample text).
+    """
+    from oracle import compact as oc
+    from oracle import rccsdt as of
+    o, v = inst.o, inst.v
+    rng = np.random.default_rng(0)
+    t1 = 1e-3 * rng.standard_normal((o, v))
+    t2 = of.mp2_t2(inst.L, inst.fock_diag, o)
+    Lt, ft = of.dress(inst.L, inst.fock_diag, t1)
+    I = of.intermediates(Lt, ft, t2, None, triples=True)
+    tr = oc.triples(o)
+    t3c = 1e-3 * rng.standard_normal((len(tr), v, v, v))
+    stride = max(1, len(tr) // 16)
+    picked, t_used = 0, 0.0
+    t0 = time.perf_counter()
+    for b in range(0, len(tr), stride):
+        i, j, k = tr[b]
+        oc.r3_block(I, t2, t3c, i, j, k)
+        picked += 1
+        t_used = time.perf_counter() - t0
+        if t_used > seconds_budget:
+            break
+    per_block = t_used / picked
+    return per_block * len(tr), f"oracle r3_block on {picked} of {len(tr)} stored blocks (stride {stride}), " \
+                                f"{t_used:.1f} s, extrapolated by block count; intermediates excluded"
+
+
+def run_reference(args, rank, world):
+    from paper_2607_00981_gb300.synth import workload
+    if rank != 0:
+        return
+    inst = workload(args.workload)
+    times = []
+    sample = ""
+    for s in range(args.warmup + args.steps):
+        val, sample = oracle_sample(inst, seconds_budget=args.ref_seconds)
+        if s >= args.warmup:
+            times.append(val)
+    value = statistics.mean(times)
+    from oracle import opcount
+    flop = opcount.flop_per_iteration(inst.o, inst.v)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/iteration", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args, inst), "tflops": flop / value / 1e12,
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "sample": sample, "value": value,
+                             "unit": "s/iteration"},
+            "e2e": {"value": value, "unit": "s/iteration", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config(args, inst):
+    return {"workload": f"{args.workload}: RCCSDT iteration, o={inst.o} v={inst.v} naux={inst.naux}, "
+                        f"compact T3 {inst.o * (inst.o + 1) * (inst.o + 2) // 6} x {inst.v}^3, seed {inst.seed}",
+            "o": inst.o, "v": inst.v, "naux": inst.naux, "precision": args.precision,
+            "l2": "inputs larger than L2 (compact T3/R3 and the operand panels exceed 129 MB)",
+            "amplitudes": "MP2 guess, then the benchmark's own iterations"}
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2607_00981_gb300 as pkg
+    from paper_2607_00981_gb300.synth import workload
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    inst = workload(args.workload)
+    o, v, naux = inst.o, inst.v, inst.naux
+    prec = PRECISIONS[args.precision]
+    stream = torch.cuda.current_stream()
+    ctx = pkg.context(o, v, naux, stream=stream.cuda_stream, precision=prec,
+                      diis_t3=0 if args.no_diis_t3 else 1)
+    lib = ctx.lib
+    L = torch.from_numpy(inst.L).to(f"cuda:{dev}")
+    f = torch.from_numpy(inst.fock_diag).to(f"cuda:{dev}")
+    ctx.set_hamiltonian(f, L)
+    ctx.init_mp2()
+    for _ in range(args.warmup):
+        ctx.iterate()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --- device-timed region: K whole iterations, inputs resident in HBM
+    barrier()
+    launches0 = lib.rccsdt_kernel_launches()
+    ctx.enable_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        e0.record(stream)
+        energies = []
+        for _ in range(args.steps):
+            e, norms = ctx.iterate()
+            energies.append(e)
+        e1.record(stream)
+        barrier()
+    launches = lib.rccsdt_kernel_launches() - launches0
+    ms_total = e0.elapsed_time(e1)
+    st = ctx.step_times()
+    ctx.enable_timing(False)
+    t_max = torch.tensor([ms_total], device=f"cuda:{dev}", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_total = float(t_max.item())
+    s_per_iter = ms_total / 1e3 / (args.steps * world)
+    fma = lib.rccsdt_iteration_fma(o, v)
+
+    # --- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        hL, hf = pin(inst.L), pin(inst.fock_diag)
+        n3 = ctx.n3
+        ht1, ht2, ht3 = ctx.amplitudes()
+        ht1, ht2, ht3 = pin(ht1), pin(ht2), pin(ht3)
+        bytes_in = hL.nbytes + hf.nbytes + ht1.nbytes + ht2.nbytes + ht3.nbytes
+        bytes_out = ht1.nbytes + ht2.nbytes + ht3.nbytes + 8 * 5
+        ksteps = max(1, min(args.steps, 3))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            ctx.set_hamiltonian(hf, hL)
+            ctx.set_amplitudes(ht1, ht2, ht3)
+            ctx.iterate()
+            ctx.get_amplitudes(ht1, ht2, ht3)
+        barrier()
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], device=f"cuda:{dev}", dtype=torch.float64)
+        if dist:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": float(tt.item()) / (ksteps * world), "unit": "s/iteration",
+               "h2d_bytes_per_step": int(bytes_in), "d2h_bytes_per_step": int(bytes_out),
+               "steps": ksteps, "note": "set_hamiltonian + set_amplitudes from pinned host memory, "
+                                        "rccsdt_iterate, get_amplitudes to host; DIIS history restarts each step"}
+        del n3
+
+    # --- roofline of the dominant kernel (the pp-ladder GEMM)
+    pk = peaks()
+    gemm_ms, gemm_n, gemm_flop = float(st[9]), float(st[10]), float(st[11])
+    roof = None
+    if gemm_n > 0 and gemm_ms > 0:
+        achieved = (gemm_flop / gemm_n) / (gemm_ms / gemm_n / 1e3) / 1e12
+        if prec == 0:
+            peak, bound, src = 1.25, "alu", "nominal FP64 1.25 TFLOP/s of the profiling recipe (DFMA path)"
+        elif prec == 1:
+            peak, bound, src = pk.get("bf16_tflops_sustained", 1700.0) / 3.0, "tensor", \
+                "measured bf16 sustained / 3 (three BF16 products per FP32-accurate product)"
+        else:
+            peak, bound, src = pk.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25) / 3.0, "tensor", \
+                "measured bf16 sustained x nominal tf32/bf16 ratio / 3"
+        roof = {"kernel": "pp-ladder GEMM (k_gemm_f64)" if prec == 0 else "pp-ladder GEMM (k_gemm_tc)",
+                "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": src, "launches": int(gemm_n),
+                "avg_launch_ms": gemm_ms / gemm_n}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, sample = oracle_sample(inst, seconds_budget=args.ref_seconds)
+        cpu = {"value": val, "unit": "s/iteration", "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": s_per_iter, "unit": "s/iteration", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+                "config": dict(config(args, inst), parallelism=f"replicas{world}"),
+                "tflops": 2.0 * fma * world / (ms_total / 1e3 / args.steps) / 1e12,
+                "energy_last": energies[-1], "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
+                "cpu_baseline": cpu, "clocks": clk.summary(),
+                "step_ms": {k: float(x) / args.steps for k, x in zip(
+                    ["intermediates", "pp", "ring", "hh", "t2", "r12_setup", "post", "update", "energy"], st[:9])}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="o8v80")
+    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-diis-t3", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -138,12 +138,20 @@ int rccsdt_get_residuals(rccsdt_ctx* ctx, double* r1, double* r2, double* r3c);
  * n3 (3 v^5 + 12 o v^4 + 3 o^2 v^3) (operation-count table). */
 double rccsdt_iteration_fma(int o, int v);
 
-/* Per-step device times (milliseconds) of the last rccsdt_iterate, measured with
- * CUDA events on the context's stream when timing is enabled.  Order of the
- * entries: intermediates, pp-ladder, ring, hh-ladder, t2 terms, other R3,
- * postprocess, update, energy.  Returns the number written (<= cap). */
+/* Timing window.  rccsdt_enable_timing(ctx, 1) starts a window: from then on
+ * the library records CUDA events (never waited on) around each step and around
+ * each GEMM launch of the pp-ladder on the context's stream.  rccsdt_step_times
+ * waits for the last event and writes, summed over the window:
+ *   ms[0..8]  device ms of: intermediates, pp-ladder, ring, hh-ladder, T2 terms,
+ *             R1/R2 and setup, postprocess, update, energy;
+ *   ms[9]     device ms inside the pp-ladder GEMM kernels alone;
+ *   ms[10]    number of those GEMM launches;  ms[11]  their algorithmic flop.
+ * Returns the number of entries written (<= cap, at most 12). */
 int rccsdt_step_times(rccsdt_ctx* ctx, double* ms, int cap);
 int rccsdt_enable_timing(rccsdt_ctx* ctx, int on);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+long long rccsdt_kernel_launches(void);
 
 /* Diagnostic: copies the first `count` float64 values of a named internal tensor
  * (e.g. "Fvv", "Wvvvo", "Wvvvv", "Wb_ovov", "r1", "X2") to `out`.  Layouts are the

@@ -53,6 +53,7 @@ _SIGS = {
     "rccsdt_iteration_fma": (C.c_double, [C.c_int, C.c_int]),
     "rccsdt_step_times": (C.c_int, [_P, _P, C.c_int]),
     "rccsdt_enable_timing": (C.c_int, [_P, C.c_int]),
+    "rccsdt_kernel_launches": (C.c_longlong, []),
     "rccsdt_last_error": (C.c_char_p, [_P]),
     "rccsdt_destroy": (None, [_P]),
 }

@@ -9,10 +9,14 @@
 //  k_wdot, k_sum deterministic weighted dot products (norms, DIIS B matrix)
 //  k_t2_outer    the K = o part of the T2-driven R3 terms, all six permutations
 //  k_diis_*      DIIS bordered solve and extrapolation (Sec. III.A.4)
+#include <algorithm>
+
 #include "elem.cuh"
 #include "kernels.h"
 
 namespace rcc {
+
+long long g_launch_count = 0;  // kernels launched by this library (host-side count)
 
 // ---------------------------------------------------------------------------
 // Panel gather.  32 x 32 tile per block of 32 x 8 threads; reads go along the
@@ -42,6 +46,7 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
 
 void launch_pack(const PackArgs& a, cudaStream_t s) {
   dim3 grid((a.Kpad + 31) / 32, (a.R + 31) / 32), block(32, 8);
+  ++g_launch_count;
   k_pack<<<grid, block, 0, s>>>(a);
 }
 
@@ -51,7 +56,8 @@ void launch_pack(const PackArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A,
                                                   const double* __restrict__ B, int K, int lda,
-                                                  int ldb, EpiArgs e) {
+                                                  int ldb, EpiArgs e, int kz_len,
+                                                  double* __restrict__ partial) {
   __shared__ double As[16][64 + 1];
   __shared__ double Bs[16][64 + 1];
   const int tid = threadIdx.x;
@@ -63,7 +69,9 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A,
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (int k0 = 0; k0 < K; k0 += 16) {
+  const int kbeg = blockIdx.z * kz_len;
+  const int kend = min(K, kbeg + kz_len);
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
     const int am = m0 + lrow, bn = n0 + lrow;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -92,15 +100,53 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const double* __restrict__ A,
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int n = n0 + tx + 16 * j;
-      if (n < e.N) epi_apply(e, m, n, acc[i][j]);
+      if (n >= e.N) continue;
+      if (partial)
+        partial[((i64)blockIdx.z * e.M + m) * e.N + n] = acc[i][j];
+      else
+        epi_apply(e, m, n, acc[i][j]);
     }
   }
 }
 
+// Split-K reduction in a fixed order, then the scatter epilogue.
+__global__ void k_splitk_reduce(const double* __restrict__ partial, int splitk, EpiArgs e) {
+  const i64 MN = (i64)e.M * e.N;
+  for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < MN; x += (i64)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < splitk; ++z) s += partial[z * MN + x];
+    epi_apply(e, (int)(x / e.N), (int)(x % e.N), s);
+  }
+}
+
+// Launches with split-K when the output has few tiles and K is long; `scratch`
+// (scratch_elems doubles) holds the partial tiles.  Deterministic in both paths.
 void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, const EpiArgs& e,
-                     cudaStream_t s) {
-  dim3 grid((e.N + 63) / 64, (e.M + 63) / 64);
-  k_gemm_f64<<<grid, 256, 0, s>>>(A, B, K, lda, ldb, e);
+                     double* scratch, i64 scratch_elems, cudaStream_t s) {
+  const int tiles = ((e.N + 63) / 64) * ((e.M + 63) / 64);
+  int splitk = 1;
+  if (tiles < 304 && K >= 1024 && scratch) {
+    splitk = (608 + tiles - 1) / tiles;
+    splitk = std::min(splitk, K / 256);
+    const i64 MN = (i64)e.M * e.N;
+    while (splitk > 1 && (i64)splitk * MN > scratch_elems) --splitk;
+  }
+  if (splitk <= 1) {
+    dim3 grid((e.N + 63) / 64, (e.M + 63) / 64, 1);
+    ++g_launch_count;
+    k_gemm_f64<<<grid, 256, 0, s>>>(A, B, K, lda, ldb, e, K, nullptr);
+    return;
+  }
+  const int kz = ((K + splitk - 1) / splitk + 15) / 16 * 16;
+  splitk = (K + kz - 1) / kz;
+  dim3 grid((e.N + 63) / 64, (e.M + 63) / 64, splitk);
+  ++g_launch_count;
+  k_gemm_f64<<<grid, 256, 0, s>>>(A, B, K, lda, ldb, e, kz, scratch);
+  const i64 MN = (i64)e.M * e.N;
+  i64 blocks = (MN + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  ++g_launch_count;
+  k_splitk_reduce<<<(unsigned)blocks, 256, 0, s>>>(scratch, splitk, e);
 }
 
 // ---------------------------------------------------------------------------
@@ -128,6 +174,7 @@ void launch_combine(const CombineArgs& c, cudaStream_t s) {
   if (c.total <= 0) return;
   i64 blocks = (c.total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
+  ++g_launch_count;
   k_combine<<<(unsigned)blocks, 256, 0, s>>>(c);
 }
 
@@ -155,6 +202,7 @@ void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStrea
   unsigned gx = (unsigned)((V3 + 255) / 256);
   if (gx > 64) gx = 64;
   unsigned gy = (unsigned)(n3 < 1024 ? n3 : 1024);
+  ++g_launch_count;
   k_post<T><<<dim3(gx, gy), 256, 0, s>>>(r, rp, blocks, v, n3);
 }
 template void launch_post<double>(const double*, double*, const int4*, int, i64, cudaStream_t);
@@ -197,10 +245,12 @@ __global__ void k_update_t3(T* t3, const T* rp3, const double* e, const int4* bl
 
 void launch_update_t12(double* t1, const double* r1, double* t2, const double* r2, const double* e,
                        int o, int v, double shift, cudaStream_t s) {
+  ++g_launch_count;
   k_update_t1<<<(o * v + 255) / 256, 256, 0, s>>>(t1, r1, e, o, v, shift);
   const i64 n = (i64)o * o * v * v;
   i64 blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
+  ++g_launch_count;
   k_update_t2<<<(unsigned)blocks, 256, 0, s>>>(t2, r2, e, o, v, shift);
 }
 
@@ -211,6 +261,7 @@ void launch_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, 
   unsigned gx = (unsigned)((V3 + 255) / 256);
   if (gx > 64) gx = 64;
   unsigned gy = (unsigned)(n3 < 1024 ? n3 : 1024);
+  ++g_launch_count;
   k_update_t3<T><<<dim3(gx, gy), 256, 0, s>>>(t3, rp3, e, blocks, o, v, n3, shift);
 }
 template void launch_update_t3<double>(double*, const double*, const double*, const int4*, int, int,
@@ -266,7 +317,9 @@ __global__ void k_sum(const double* __restrict__ partial, int np, double* __rest
 template <typename T>
 void launch_wdot(const T* x, const T* y, i64 n, i64 seg, const double* w, double* partial,
                  double* out, double scale, int accumulate, cudaStream_t s) {
+  ++g_launch_count;
   k_wdot<T><<<kDotBlocks, 256, 0, s>>>(x, y, n, seg, w, partial);
+  ++g_launch_count;
   k_sum<<<1, 256, 0, s>>>(partial, kDotBlocks, out, scale, accumulate);
 }
 template void launch_wdot<double>(const double*, const double*, i64, i64, const double*, double*,
@@ -313,6 +366,7 @@ void launch_t2_outer(T* r3, const double* Wvooo, const double* t2, const int4* b
   unsigned gx = (unsigned)((V3 + 255) / 256);
   if (gx > 64) gx = 64;
   unsigned gy = (unsigned)(n3 < 1024 ? n3 : 1024);
+  ++g_launch_count;
   k_t2_outer<T><<<dim3(gx, gy), 256, 0, s>>>(r3, Wvooo, t2, blocks, o, v, n3);
 }
 template void launch_t2_outer<double>(double*, const double*, const double*, const int4*, int, int, i64,
@@ -368,6 +422,7 @@ __global__ void k_diis_solve(const double* __restrict__ Bmat, int m, int ld, dou
 }
 
 void launch_diis_solve(const double* B, int m, int ld, double* coef, cudaStream_t s) {
+  ++g_launch_count;
   k_diis_solve<<<1, 32, 0, s>>>(B, m, ld, coef);
 }
 
@@ -388,6 +443,7 @@ void launch_diis_extrapolate(T* out, const T* hist, i64 stride, i64 n, const dou
   if (n <= 0) return;
   i64 blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
+  ++g_launch_count;
   k_diis_extrapolate<T><<<(unsigned)blocks, 256, 0, s>>>(out, hist, stride, n, coef, m);
 }
 template void launch_diis_extrapolate<double>(double*, const double*, i64, i64, const double*, int,
@@ -406,6 +462,7 @@ void launch_sub(T* out, const T* a, const T* b, i64 n, cudaStream_t s) {
   if (n <= 0) return;
   i64 blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
+  ++g_launch_count;
   k_sub<T><<<(unsigned)blocks, 256, 0, s>>>(out, a, b, n);
 }
 template void launch_sub<double>(double*, const double*, const double*, i64, cudaStream_t);
@@ -422,6 +479,7 @@ void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t s) {
   if (n <= 0) return;
   i64 blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
+  ++g_launch_count;
   k_convert<TO, TI><<<(unsigned)blocks, 256, 0, s>>>(out, in, n);
 }
 template void launch_convert<float, double>(float*, const double*, i64, cudaStream_t);
@@ -449,7 +507,9 @@ __global__ void k_energy(const double* __restrict__ g, const double* __restrict_
 
 void launch_energy(const double* g, const double* t1, const double* t2, int o, int v, double* partial,
                    double* out, cudaStream_t s) {
+  ++g_launch_count;
   k_energy<<<kDotBlocks, 256, 0, s>>>(g, t1, t2, o, v, partial);
+  ++g_launch_count;
   k_sum<<<1, 256, 0, s>>>(partial, kDotBlocks, out, 1.0, 0);
 }
 
@@ -467,6 +527,7 @@ void launch_mp2(double* t2, const double* g, const double* e, int o, int v, cuda
   const i64 total = (i64)o * o * v * v;
   i64 blocks = (total + 255) / 256;
   if (blocks > 4096) blocks = 4096;
+  ++g_launch_count;
   k_mp2<<<(unsigned)blocks, 256, 0, s>>>(t2, g, e, o, v);
 }
 
@@ -499,6 +560,7 @@ void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, con
   unsigned gx = (unsigned)((V3 + 255) / 256);
   if (gx > 32) gx = 32;
   unsigned gy = (unsigned)(ntrip < 1024 ? ntrip : 1024);
+  ++g_launch_count;
   k_unpack_spin<<<dim3(gx, gy), 256, 0, s>>>(t3, f32, ntrip, base, pos, v, S, D);
 }
 

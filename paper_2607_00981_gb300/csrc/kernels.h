@@ -4,7 +4,8 @@
 
 namespace rcc {
 
-constexpr int kDotBlocks = 608;  // 4 x 152 SMs, fixed so reductions are deterministic
+constexpr int kDotBlocks = 608;
+extern long long g_launch_count;  // 4 x 152 SMs, fixed so reductions are deterministic
 
 struct CombineArgs {
   double* out;
@@ -21,7 +22,7 @@ struct CombineArgs {
 
 void launch_pack(const PackArgs& a, cudaStream_t s);
 void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, const EpiArgs& e,
-                     cudaStream_t s);
+                     double* scratch, i64 scratch_elems, cudaStream_t s);
 void launch_combine(const CombineArgs& c, cudaStream_t s);
 template <typename T>
 void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStream_t s);

@@ -168,6 +168,12 @@ struct rccsdt_ctx {
   int have_ham = 0, have_amp = 0, have_int = 0, have_res = 0;
   int timing = 0;
   double step_ms[16] = {0};
+  // event pool for non-blocking interval timing: tag < 16 = step slots, 16 = GEMM engine
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_tag;
+  std::vector<double> ev_flop;
+  int ev_used = 0;
+  long long launches = 0;
   size_t total_bytes = 0;
 
   // buffers
@@ -194,7 +200,7 @@ struct rccsdt_ctx {
   std::unique_ptr<DBuf> hist_t, hist_e;     // M slots each: t1 | t2 | t3 (padded)
   i64 hist_stride = 0;                      // bytes per slot
   i64 seg1 = 0, seg2 = 0, seg3 = 0;         // element counts
-  std::unique_ptr<DBuf> scalars, partial;
+  std::unique_ptr<DBuf> scalars, partial, splitk;
 
   DBuf* B(const std::string& k) { return buf.at(k).get(); }
   double* D(const std::string& k) { return buf.at(k)->d(); }
@@ -407,6 +413,64 @@ View permuted(const View& in, std::vector<int> perm) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Interval timing with pooled CUDA events (recorded, never waited on until the
+// totals are read), so timing does not serialise the iteration.
+// ---------------------------------------------------------------------------
+static int timer_begin(rccsdt_ctx* c, int tag, double flop = 0.0) {
+#ifdef RCC_HOSTSIM
+  (void)c; (void)tag; (void)flop;
+  return -1;
+#else
+  if (!c->timing) return -1;
+  if (c->ev_used + 2 > (int)c->ev.size()) {
+    // grow the pool (fresh events, nothing pending on them)
+    const int add = 1024;
+    for (int q = 0; q < add; ++q) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      c->ev.push_back(e);
+    }
+    c->ev_tag.resize(c->ev.size() / 2);
+    c->ev_flop.resize(c->ev.size() / 2);
+  }
+  const int idx = c->ev_used / 2;
+  c->ev_tag[idx] = tag;
+  c->ev_flop[idx] = flop;
+  cudaEventRecord(c->ev[c->ev_used], c->stream);
+  c->ev_used += 2;
+  return idx;
+#endif
+}
+
+static void timer_end(rccsdt_ctx* c, int idx) {
+#ifndef RCC_HOSTSIM
+  if (idx >= 0) cudaEventRecord(c->ev[2 * idx + 1], c->stream);
+#else
+  (void)c; (void)idx;
+#endif
+}
+
+// Sums the recorded intervals: ms per tag into out_ms[17], GEMM launches and flop.
+static void timer_collect(rccsdt_ctx* c, double* out_ms, double* gemm_launches, double* gemm_flop) {
+  for (int q = 0; q < 17; ++q) out_ms[q] = 0.0;
+  *gemm_launches = 0.0;
+  *gemm_flop = 0.0;
+#ifndef RCC_HOSTSIM
+  if (c->ev_used == 0) return;
+  cudaEventSynchronize(c->ev[c->ev_used - 1]);
+  for (int idx = 0; idx < c->ev_used / 2; ++idx) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev[2 * idx], c->ev[2 * idx + 1]);
+    out_ms[c->ev_tag[idx]] += ms;
+    if (c->ev_tag[idx] == 16) {
+      *gemm_launches += 1.0;
+      *gemm_flop += c->ev_flop[idx];
+    }
+  }
+#endif
+}
+
+// ---------------------------------------------------------------------------
 // Engine: run one GemmPlan
 // ---------------------------------------------------------------------------
 static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
@@ -420,15 +484,17 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   pb.out_lo = c->panelB_lo ? c->panelB_lo->p : nullptr;
   rcc::launch_pack(pa, c->stream);
   rcc::launch_pack(pb, c->stream);
+  const int tidx = g->step == 1 ? timer_begin(c, 16, 2.0 * g->fma) : -1;
   if (!tc) {
     rcc::launch_gemm_f64((const double*)pa.out_hi, (const double*)pb.out_hi, g->Kpad, g->Kpad, g->Kpad,
-                         g->E.e, c->stream);
+                         g->E.e, c->splitk->d(), (i64)(c->splitk->bytes / 8), c->stream);
   } else {
     int* flag = (int*)((double*)c->scalars->p + 1000);
     if (rcc::launch_gemm_tc(kind, pa.out_hi, pa.out_lo, pb.out_hi, pb.out_lo, g->Kpad, g->E.e, flag,
                             c->opt.watchdog_cycles, c->stream))
       return fail(c, RCCSDT_ERR_ARG, "tensor-core GEMM configuration unsupported");
   }
+  timer_end(c, tidx);
   return dev_check();
 }
 
@@ -940,31 +1006,9 @@ namespace {
 struct StepTimer {
   rccsdt_ctx* c;
   int slot;
-#ifndef RCC_HOSTSIM
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-#endif
-  StepTimer(rccsdt_ctx* c_, int slot_) : c(c_), slot(slot_) {
-#ifndef RCC_HOSTSIM
-    if (c->timing) {
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
-      cudaEventRecord(e0, c->stream);
-    }
-#endif
-  }
-  ~StepTimer() {
-#ifndef RCC_HOSTSIM
-    if (c->timing) {
-      cudaEventRecord(e1, c->stream);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      c->step_ms[slot] += ms;
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-    }
-#endif
-  }
+  int idx = -1;
+  StepTimer(rccsdt_ctx* c_, int slot_) : c(c_), slot(slot_) { idx = timer_begin(c, slot); }
+  ~StepTimer() { timer_end(c, idx); }
 };
 
 int zero(rccsdt_ctx* c, const char* name) { return dev_zero(c->B(name)->p, c->B(name)->bytes, c->stream); }
@@ -1212,6 +1256,10 @@ RCC_API int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, voi
   int err = 0;
   c->scalars = upload_vec(c, std::vector<double>(2048, 0.0), &err);
   c->partial = upload_vec(c, std::vector<double>(rcc::kDotBlocks, 0.0), &err);
+  c->splitk = std::make_unique<DBuf>();
+  c->splitk->bytes = (size_t)32 << 20;  // split-K partial tiles (4 Mi doubles)
+  c->splitk->p = dev_alloc(c->splitk->bytes, &err);
+  c->total_bytes += c->splitk->bytes;
   int st = err ? RCCSDT_ERR_OOM : build_context(c);
   if (!st) {
     // engine panels (hi planes hold doubles in FP64 mode; lo planes only for split modes)
@@ -1366,7 +1414,6 @@ RCC_API int rccsdt_energy(rccsdt_ctx* c, double* e) {
 RCC_API int rccsdt_iterate(rccsdt_ctx* c, double* e, double norms[4]) {
   int st = need(c, true, false, false);
   if (st) return st;
-  for (double& x : c->step_ms) x = 0.0;
   double tmp[4], et;
   if ((st = do_energy(c, nullptr))) return st;
   if ((st = do_intermediates(c))) return st;
@@ -1472,20 +1519,33 @@ RCC_API double rccsdt_iteration_fma(int o, int v) {
 RCC_API int rccsdt_enable_timing(rccsdt_ctx* c, int on) {
   if (!c) return RCCSDT_ERR_ARG;
   c->timing = on ? 1 : 0;
+  c->ev_used = 0;  // starts a new measurement window
   return RCCSDT_OK;
 }
 
 RCC_API int rccsdt_step_times(rccsdt_ctx* c, double* ms, int cap) {
   if (!c || !ms) return RCCSDT_ERR_ARG;
-  const int n = std::min(cap, 9);
-  for (int q = 0; q < n; ++q) ms[q] = c->step_ms[q];
+  double all[17], gl, gf;
+  timer_collect(c, all, &gl, &gf);
+  const int n = std::min(cap, 12);
+  for (int q = 0; q < n; ++q) {
+    if (q < 9) ms[q] = all[q];
+    else if (q == 9) ms[q] = all[16];
+    else if (q == 10) ms[q] = gl;
+    else ms[q] = gf;
+  }
   return n;
 }
+
+RCC_API long long rccsdt_kernel_launches(void) { return rcc::g_launch_count; }
 
 RCC_API const char* rccsdt_last_error(const rccsdt_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 RCC_API void rccsdt_destroy(rccsdt_ctx* c) {
   if (!c) return;
   dev_sync(c->stream);
+#ifndef RCC_HOSTSIM
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+#endif
   delete c;
 }

@@ -15,12 +15,15 @@
 
 namespace rcc {
 
+long long g_launch_count = 0;
+
 void launch_pack(const PackArgs& a, cudaStream_t) {
   for (int r = 0; r < a.R; ++r)
     for (int k = 0; k < a.Kpad; ++k) store_panel(a, r, k, k < a.K ? pack_value(a, r, k) : 0.0);
 }
 
-void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, const EpiArgs& e, cudaStream_t) {
+void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, const EpiArgs& e, double*, i64,
+                     cudaStream_t) {
   for (int m = 0; m < e.M; ++m)
     for (int n = 0; n < e.N; ++n) {
       double s = 0.0;

@@ -162,6 +162,32 @@ int rccsdt_debug_copy(rccsdt_ctx* ctx, const char* name, double* out, long long 
 const char* rccsdt_last_error(const rccsdt_ctx* ctx);
 void rccsdt_destroy(rccsdt_ctx* ctx);
 
+/* Residual norms for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this entry point exists for callers such as a framework that
+ * owns all device memory through its own pool allocator (a raw cudaMalloc would
+ * bypass its accounting), or a service that reserves its memory at start-up and
+ * must not allocate in steady state (cudaMalloc may synchronise the device, add
+ * latency, or fail near the HBM limit).  It needs no context and allocates
+ * nothing: its scratch is a fixed device array in the library image.
+ *
+ * Computes norms[4] = {|R1|, |R2|, |R3|, |R|} exactly as rccsdt_postprocess does
+ * (|R3| weights each stored block by 6, 3 or 1 occupied triples) from the caller's
+ * device buffers r1[o][v], r2[o][o][v][v] and the post-processed compact
+ * r3c[n3][v][v][v] (float64), writing the four values to the device pointer
+ * `norms`.  Work is queued on `stream` (a cudaStream_t, NULL = legacy default) and
+ * the call returns without waiting.
+ *
+ * Limit: n3 = o(o+1)(o+2)/6 <= 4096, i.e. o <= 28; larger o, o or v < 1, or a NULL
+ * pointer return RCCSDT_ERR_ARG before any GPU work.  RCCSDT_ERR_CUDA if the
+ * device lookup or a launch fails.
+ * The first call on each device looks up the scratch's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls on a device share the scratch and every call
+ * overwrites the slots it uses before reading them; calls whose kernels overlap
+ * on the GPU race on it, so order them on one stream. */
+int rccsdt_residual_norms_noalloc(int o, int v, const double* r1, const double* r2, const double* r3c,
+                                  double* norms, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

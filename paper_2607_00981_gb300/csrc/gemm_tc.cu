@@ -1,9 +1,429 @@
-// tcgen05 split-precision GEMM (placeholder until the tensor-core kernel lands).
+// Split-precision GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+//   C[m, n] (+)= alpha[m] * sum_k (Ahi Bhi + Ahi Blo + Alo Bhi)[m, n]
+//
+// A [M][Kpad] and B [N][Kpad] are K-major panels split into hi/lo planes (BF16,
+// or TF32 held in FP32 words); the three products accumulate in FP32 in tensor
+// memory.  This is the 3-term split product of Henry, Tang & Heinecke (ARITH 2019)
+// for BF16 and of Ootomo & Yokota (2022) for TF32: dropping lo*lo leaves a
+// relative error of about 2^-16 (BF16) or 2^-21 (TF32) per product.
+//
+// Persistent kernel, one CTA per SM, 192 threads:
+//   warp 0     TMA producer: 128-byte-swizzled 128 x 64B-row tiles of A and
+//              256-row tiles of B, hi and lo planes, into a 2-stage ring;
+//   warp 1     TMEM owner and MMA issuer (one thread): 3 tcgen05.mma per 32-byte
+//              K slice into a 128 x 256 FP32 accumulator, double buffered in
+//              TMEM (512 columns) so the epilogue of one tile overlaps the MMAs
+//              of the next;
+//   warps 2-5  epilogue: tcgen05.ld of the accumulator (one row per thread) and
+//              the table-driven scatter C[row_base[m] + col_off[sel[m]][n]] +=
+//              alpha[m] * acc, or FP32 partial tiles when K is split.
+// Every mbarrier wait is bounded by a clock64 budget; on expiry the kernel sets
+// *status, drains its own copies and MMAs (bounded again), frees TMEM and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "elem.cuh"
 #include "kernels.h"
 
 namespace rcc {
-int launch_gemm_tc(int, const void*, const void*, const void*, const void*, int, const EpiArgs&, int*, long long,
-                   cudaStream_t) {
-  return 1;
+namespace {
+
+constexpr int BM = 128, BN = 256, STAGES = 2;
+constexpr int ROWB = 128;                      // bytes of one K-row of a tile (swizzle span)
+constexpr int A_PLANE = BM * ROWB, B_PLANE = BN * ROWB;
+constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;  // 96 KiB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int kThreads = 192;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false on timeout or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          su32(dst)),
+      "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// SM100 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), version 1; tiles are 1024-byte aligned (base offset 0).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;                      // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D = F32, A = B = fmt (1 BF16, 2 TF32), both K-major, N = BN, M = BM.
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int FMT>
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  if constexpr (FMT == 1) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d),
+        "l"(a), "l"(b), "r"(idesc(1)), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d),
+        "l"(a), "l"(b), "r"(idesc(2)), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TileGeom {
+  int mt, nt, splitk, kblocks, kb_per;
+};
+
+__device__ __forceinline__ void decode(const TileGeom& g, int tile, int& tm, int& tn, int& kb0, int& kb1) {
+  const int ks = tile % g.splitk;
+  const int t = tile / g.splitk;
+  tm = t % g.mt;
+  tn = t / g.mt;
+  kb0 = ks * g.kb_per;
+  kb1 = min(g.kblocks, kb0 + g.kb_per);
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, TileGeom g, EpiArgs e,
+              float* __restrict__ partial, int* __restrict__ status, long long budget) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int ntiles = g.mt * g.nt * g.splitk;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      int issued[STAGES];
+      for (int q = 0; q < STAGES; ++q) issued[q] = -1;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        int tm, tn, kb0, kb1;
+        decode(g, tile, tm, tn, kb0, kb1);
+        for (int kb = kb0; kb < kb1; ++kb) {
+          if (!mbar_wait(&empty[s], ph ^ 1, budget, abort_flag)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          const int x = kb * (ROWB / (FMT == 1 ? 2 : 4));
+          tma_load_2d(st, &mAh, &full[s], x, tm * BM);
+          tma_load_2d(st + A_PLANE, &mAl, &full[s], x, tm * BM);
+          tma_load_2d(st + 2 * A_PLANE, &mBh, &full[s], x, tn * BN);
+          tma_load_2d(st + 2 * A_PLANE + B_PLANE, &mBl, &full[s], x, tn * BN);
+          issued[s] = (int)ph;
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1;
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(status, 1);
+        // drain: wait (bounded) for the copies this thread issued
+        for (int q = 0; q < STAGES; ++q) {
+          if (issued[q] < 0) continue;
+          const long long t0 = clock64();
+          while (!mbar_try(&full[q], (uint32_t)issued[q]) && clock64() - t0 < budget) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      int it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+        int tm, tn, kb0, kb1;
+        decode(g, tile, tm, tn, kb0, kb1);
+        const int b = it & 1;
+        const uint32_t aph = (it >> 1) & 1;
+        if (!mbar_wait(&tempty[b], aph ^ 1, budget, abort_flag)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * BN);
+        for (int kb = kb0; kb < kb1; ++kb) {
+          if (!mbar_wait(&full[s], ph, budget, abort_flag)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t base = su32(smem + s * STAGE_BYTES);
+          const uint64_t ah = sdesc(base), al = sdesc(base + A_PLANE);
+          const uint64_t bh = sdesc(base + 2 * A_PLANE), bl = sdesc(base + 2 * A_PLANE + B_PLANE);
+#pragma unroll
+          for (int j = 0; j < ROWB / 32; ++j) {
+            const uint64_t adv = (uint64_t)(j * 32 >> 4);  // 32-byte K slice inside the swizzled row
+            umma<FMT>(d, ah + adv, bh + adv, (kb > kb0 || j > 0) ? 1u : 0u);
+            umma<FMT>(d, ah + adv, bl + adv, 1u);
+            umma<FMT>(d, al + adv, bh + adv, 1u);
+          }
+          umma_commit(&empty[s]);
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&tfull[b]);
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(status, 1);
+      }
+      // make sure every MMA this thread issued has completed before TMEM is freed
+      umma_commit(drain);
+      const long long t0 = clock64();
+      while (!mbar_try(drain, 0) && clock64() - t0 < budget) {
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      int tm, tn, kb0, kb1;
+      decode(g, tile, tm, tn, kb0, kb1);
+      const int b = it & 1;
+      const uint32_t aph = (it >> 1) & 1;
+      if (!mbar_wait(&tfull[b], aph, budget, abort_flag)) {
+        *abort_flag = 1;
+        atomicExch(status, 1);
+        break;
+      }
+      fence_after();
+      const int m = tm * BM + row;
+      const int ks = tile % g.splitk;
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c * 32), r);
+        if (m < e.M) {
+          const int n0 = tn * BN + c * 32;
+          if (partial) {
+            float* dst = partial + ((i64)ks * e.M + m) * e.N;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (n0 + j < e.N) dst[n0 + j] = __uint_as_float(r[j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (n0 + j < e.N) epi_apply(e, m, n0 + j, (double)__uint_as_float(r[j]));
+          }
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+__global__ void k_splitk_reduce_f32(const float* __restrict__ partial, int splitk, EpiArgs e) {
+  const i64 MN = (i64)e.M * e.N;
+  for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < MN; x += (i64)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < splitk; ++z) s += (double)partial[z * MN + x];
+    epi_apply(e, (int)(x / e.N), (int)(x % e.N), s);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const void* ptr, int rows, int Kpad, int kind, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const int esz = kind == PANEL_BF16X2 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kpad * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(ROWB / esz), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt = kind == PANEL_BF16X2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return fn(map, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+}  // namespace
+
+int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int Kpad,
+                   const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s, float* scratch,
+                   long long scratch_elems) {
+  if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
+  const int esz = kind == PANEL_BF16X2 ? 2 : 4;
+  const int bk = ROWB / esz;
+  if (Kpad % bk != 0 || e.M <= 0 || e.N <= 0) return 1;
+  CUtensorMap mAh, mAl, mBh, mBl;
+  if (!make_map(&mAh, Ahi, e.M, Kpad, kind, BM) || !make_map(&mAl, Alo, e.M, Kpad, kind, BM) ||
+      !make_map(&mBh, Bhi, e.N, Kpad, kind, BN) || !make_map(&mBl, Blo, e.N, Kpad, kind, BN))
+    return 2;
+  TileGeom g;
+  g.mt = (e.M + BM - 1) / BM;
+  g.nt = (e.N + BN - 1) / BN;
+  g.kblocks = Kpad / bk;
+  g.splitk = 1;
+  const int sms = num_sms();
+  const int tiles = g.mt * g.nt;
+  if (tiles < sms && g.kblocks >= 8 && scratch) {
+    int sk = std::min((2 * sms + tiles - 1) / tiles, g.kblocks / 4);
+    while (sk > 1 && (long long)sk * e.M * e.N > scratch_elems) --sk;
+    g.splitk = std::max(sk, 1);
+  }
+  g.kb_per = (g.kblocks + g.splitk - 1) / g.splitk;
+  g.splitk = (g.kblocks + g.kb_per - 1) / g.kb_per;
+  const int ntiles = tiles * g.splitk;
+  const int grid = std::min(ntiles, sms);
+  const long long budget = watchdog > 0 ? watchdog : 4000000000LL;
+  float* part = g.splitk > 1 ? scratch : nullptr;
+  if (kind == PANEL_BF16X2) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      attr = true;
+    }
+    ++g_launch_count;
+    k_gemm_tc<1><<<grid, kThreads, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, g, e, part, status_flag, budget);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      attr = true;
+    }
+    ++g_launch_count;
+    k_gemm_tc<2><<<grid, kThreads, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, g, e, part, status_flag, budget);
+  }
+  if (part) {
+    const long long MN = (long long)e.M * e.N;
+    long long blocks = (MN + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    ++g_launch_count;
+    k_splitk_reduce_f32<<<(unsigned)blocks, 256, 0, s>>>(part, g.splitk, e);
+  }
+  return 0;
+}
+
 }  // namespace rcc

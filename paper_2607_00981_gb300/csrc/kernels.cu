@@ -25,7 +25,7 @@ long long g_launch_count = 0;  // kernels launched by this library (host-side co
 __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
   __shared__ double tile[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
   if (a.read_k_fast) {
     for (int rr = ty; rr < 32; rr += 8) {
       const int r = r0 + rr, k = k0 + tx;
@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
 }
 
 void launch_pack(const PackArgs& a, cudaStream_t s) {
-  dim3 grid((a.Kpad + 31) / 32, (a.R + 31) / 32), block(32, 8);
+  // rows on grid x (up to 2^31 - 1 blocks), K on grid y (Kpad / 32 <= 65535)
+  dim3 grid((a.R + 31) / 32, (a.Kpad + 31) / 32), block(32, 8);
   ++g_launch_count;
   k_pack<<<grid, block, 0, s>>>(a);
 }
@@ -336,13 +337,14 @@ template <typename T>
 __global__ void k_t2_outer(T* __restrict__ r3, const double* __restrict__ Wvooo,
                            const double* __restrict__ t2, const int4* __restrict__ blocks, int o, int v,
                            i64 n3) {
+  // arithmetic in the storage precision of R3 (FP32 in the split modes)
   const i64 V3 = (i64)v * v * v;
   for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
     const int4 ijk = blocks[b];
     const int occ[3] = {ijk.x, ijk.y, ijk.z};
     for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < V3; x += (i64)gridDim.x * blockDim.x) {
       const int lab[3] = {(int)(x / ((i64)v * v)), (int)((x / v) % v), (int)(x % v)};
-      double s = 0.0;
+      T s = 0;
       // permutations p: positions (p0, p1, p2) take the roles (1, 2, 3)
       const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 #pragma unroll
@@ -351,10 +353,10 @@ __global__ void k_t2_outer(T* __restrict__ r3, const double* __restrict__ Wvooo,
         const int a1 = lab[P[q][0]], a2 = lab[P[q][1]], a3 = lab[P[q][2]];
         const double* W = Wvooo + (((i64)a1 * o) * o + i1) * o + i2;       // stride o*o over l
         const double* t = t2 + ((i64)i3 * v + a2) * v + a3;                  // stride o*v*v over l
-        for (int l = 0; l < o; ++l) s -= W[(i64)l * o * o] * t[(i64)l * o * v * v];
+        for (int l = 0; l < o; ++l) s -= (T)W[(i64)l * o * o] * (T)t[(i64)l * o * v * v];
       }
       const i64 g = b * V3 + x;
-      r3[g] = (T)((double)r3[g] + s);
+      r3[g] = r3[g] + s;
     }
   }
 }

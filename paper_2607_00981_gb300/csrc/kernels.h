@@ -49,8 +49,10 @@ void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t s);
 // tcgen05 split-precision GEMM (gemm_tc.cu): C += alpha * (Ahi Bhi + Ahi Blo + Alo Bhi)
 // with A [M][Kpad], B [N][Kpad] in two planes each.  kind: PANEL_BF16X2 or PANEL_TF32X2.
 // Returns 0 on success, nonzero if the configuration is unsupported.
+// `scratch` (scratch_elems floats) holds FP32 partial tiles when K is split.
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo,
-                   int Kpad, const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s);
+                   int Kpad, const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s,
+                   float* scratch, long long scratch_elems);
 
 }  // namespace rcc
 

@@ -77,6 +77,14 @@ int dev_zero(void* p, size_t bytes, cudaStream_t s) {
 int dev_sync(cudaStream_t s) { return cudaStreamSynchronize(s) == cudaSuccess ? 0 : RCCSDT_ERR_CUDA; }
 int dev_check() { return cudaGetLastError() == cudaSuccess ? 0 : RCCSDT_ERR_CUDA; }
 #endif
+// Last CUDA error text (or empty) for error messages.
+const char* cuda_error_text() {
+#ifdef RCC_HOSTSIM
+  return "";
+#else
+  return cudaGetErrorString(cudaPeekAtLastError());
+#endif
+}
 
 i64 n3_of(int o) { return (i64)o * (o + 1) * (o + 2) / 6; }
 int multiplicity(int i, int j, int k) {
@@ -363,8 +371,9 @@ GemmPlan* contraction(rccsdt_ctx* c, const char* spec, double alpha, const View&
   make_pack(c, g->A, A.p, A.f32, M, K, 1, coefK, kAo, selK, rowA, unit_fast(kA) ? 1 : 0, err);
   make_pack(c, g->B, Bv.p, Bv.f32, N, K, 1, coefK, kBo, selK, rowB, unit_fast(kB) ? 1 : 0, err);
   make_epi(c, g->E, C.p, C.f32, M, N, rowC, std::vector<int>(M, 0), std::vector<double>(M, alpha), colC, err);
-  g->big = big;
   finish_plan(c, g.get(), K);
+  // in the split modes every contraction of 5e8 FMA or more runs on the tensor cores
+  g->big = big || g->fma >= 5e8;
   GemmPlan* raw = g.get();
   c->plans.push_back(std::move(g));
   return raw;
@@ -491,11 +500,16 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   } else {
     int* flag = (int*)((double*)c->scalars->p + 1000);
     if (rcc::launch_gemm_tc(kind, pa.out_hi, pa.out_lo, pb.out_hi, pb.out_lo, g->Kpad, g->E.e, flag,
-                            c->opt.watchdog_cycles, c->stream))
+                            c->opt.watchdog_cycles, c->stream, (float*)c->splitk->p,
+                            (long long)(c->splitk->bytes / 4)))
       return fail(c, RCCSDT_ERR_ARG, "tensor-core GEMM configuration unsupported");
   }
   timer_end(c, tidx);
-  return dev_check();
+#ifndef RCC_HOSTSIM
+  const cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) return fail(c, RCCSDT_ERR_CUDA, std::string("GEMM launch: ") + cudaGetErrorString(ce));
+#endif
+  return 0;
 }
 
 static int run_plans(rccsdt_ctx* c, const std::vector<GemmPlan*>& ps) {
@@ -1011,6 +1025,16 @@ struct StepTimer {
   ~StepTimer() { timer_end(c, idx); }
 };
 
+int check(rccsdt_ctx* c, const char* where) {
+#ifndef RCC_HOSTSIM
+  const cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) return fail(c, RCCSDT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(ce));
+#else
+  (void)c; (void)where;
+#endif
+  return 0;
+}
+
 int zero(rccsdt_ctx* c, const char* name) { return dev_zero(c->B(name)->p, c->B(name)->bytes, c->stream); }
 
 int do_intermediates(rccsdt_ctx* c) {
@@ -1045,7 +1069,7 @@ int do_intermediates(rccsdt_ctx* c) {
     if ((st = run_plans(c, c->p_a3[z]))) return st;
   }
   c->have_int = 1;
-  return dev_check();
+  return check(c, "do_intermediates");
 }
 
 int do_residual(rccsdt_ctx* c) {
@@ -1081,7 +1105,7 @@ int do_residual(rccsdt_ctx* c) {
       rcc::launch_t2_outer<double>(c->D("r3"), c->D("Wvooo"), c->D("t2"), blk, c->o, c->v, c->n3, c->stream);
   }
   c->have_res = 1;
-  return dev_check();
+  return check(c, "do_residual");
 }
 
 double* scal(rccsdt_ctx* c, int i) { return (double*)c->scalars->p + i; }
@@ -1119,7 +1143,7 @@ int do_postprocess(rccsdt_ctx* c, double norms[4]) {
     for (int q = 0; q < 4; ++q)
       if (!std::isfinite(norms[q])) return fail(c, RCCSDT_ERR_NONFINITE, "non-finite residual norm");
   }
-  return dev_check();
+  return check(c, "do_postprocess");
 }
 
 // Segment views of history slot s: t1 | t2 | t3 (t3 of the storage type).
@@ -1160,7 +1184,7 @@ int do_update(rccsdt_ctx* c) {
     rcc::launch_update_t3<float>(c->B("t3")->f(), c->B("rp3")->f(), c->D("e"), blk, o, v, c->n3, 0.0, c->stream);
   else
     rcc::launch_update_t3<double>(c->D("t3"), c->D("rp3"), c->D("e"), blk, o, v, c->n3, 0.0, c->stream);
-  if (M <= 0) return dev_check();
+  if (M <= 0) return check(c, "do_update");
   Seg tn = slot(c, s), e = slot(c, M + s);
   rcc::launch_sub<double>(e.t1, c->D("t1"), e.t1, c->seg1, c->stream);
   rcc::launch_sub<double>(e.t2, c->D("t2"), e.t2, c->seg2, c->stream);
@@ -1204,7 +1228,7 @@ int do_update(rccsdt_ctx* c) {
                                              scal(c, kCoef), m, c->stream);
     }
   }
-  return dev_check();
+  return check(c, "do_update");
 }
 
 int do_energy(rccsdt_ctx* c, double* e_out) {
@@ -1214,7 +1238,7 @@ int do_energy(rccsdt_ctx* c, double* e_out) {
     if (dev_copy(e_out, scal(c, 4), 8, c->stream) || dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
     if (!std::isfinite(*e_out)) return fail(c, RCCSDT_ERR_NONFINITE, "non-finite energy");
   }
-  return dev_check();
+  return check(c, "do_energy");
 }
 
 }  // namespace

@@ -35,7 +35,7 @@ void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, 
 // Split-precision product hi*hi + hi*lo + lo*hi with float products and a float
 // accumulator (the order of the tensor-core sum is not modelled).
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int Kpad,
-                   const EpiArgs& e, int*, long long, cudaStream_t) {
+                   const EpiArgs& e, int*, long long, cudaStream_t, float*, long long) {
   auto get = [&](const void* p, i64 i) -> float {
     if (kind == PANEL_BF16X2) return __bfloat162float(((const __nv_bfloat16*)p)[i]);
     return ((const float*)p)[i];

@@ -1,0 +1,62 @@
+"""Split-precision (3xBF16, 3xTF32) residuals against the FP64 oracle.
+
+The large contractions run as hi*hi + hi*lo + lo*hi products with FP32
+accumulation (tcgen05 on the GPU; FP32 emulation in the host simulation), T3 is
+stored in FP32.  Bars, relative to the largest residual element: 3xBF16 keeps
+about 16 bits per product, so 5e-5; 3xTF32 about 21 bits, so 5e-6.
+"""
+import numpy as np
+import pytest
+
+from oracle import compact as oc
+from paper_2607_00981_gb300 import binding as B
+from paper_2607_00981_gb300.synth import make_instance, random_amplitudes
+
+from ._helpers import gpu_lib, hostsim_lib
+
+BACKENDS = [pytest.param("hostsim", id="hostsim"), pytest.param("gpu", id="gpu", marks=pytest.mark.gpu)]
+TOL = {B.SPLIT_BF16X3: 5e-5, B.SPLIT_TF32X3: 5e-6}
+
+
+@pytest.mark.parametrize("kind", BACKENDS)
+@pytest.mark.parametrize("prec", [B.SPLIT_BF16X3, B.SPLIT_TF32X3], ids=["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("o,v,naux", [(3, 12, 40), (4, 9, 16), (2, 21, 12)])
+def test_split_residual_matches_oracle(kind, prec, o, v, naux):
+    lib = gpu_lib() if kind == "gpu" else hostsim_lib()
+    inst = make_instance(o, v, naux, seed=o + v)
+    t1, t2, t3 = random_amplitudes(o, v, seed=2 * v + o)
+    t3c = oc.pack(t3)
+    ctx = B.Context(lib, o, v, naux, precision=prec)
+    ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    ctx.set_amplitudes(t1, t2, t3c)
+    ctx.build_intermediates()
+    ctx.residual()
+    norms = ctx.postprocess()
+    r1, r2, r3 = ctx.residuals()
+    R1, R2, R3 = oc.residuals_compact(inst.L, inst.fock_diag, t1, t2, t3c)
+    scale = max(1.0, np.abs(R3).max())
+    tol = TOL[prec]
+    assert np.abs(r1 - R1).max() / scale < tol
+    assert np.abs(r2 - R2).max() / scale < tol
+    assert np.abs(oc.postprocess(r3, o) - oc.postprocess(R3, o)).max() / scale < tol
+    ref = oc.residual_norm(R1, R2, oc.postprocess(R3, o), o)
+    assert abs(norms[3] - ref) < tol * max(1.0, ref)
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind", BACKENDS)
+@pytest.mark.parametrize("prec", [B.SPLIT_BF16X3, B.SPLIT_TF32X3], ids=["bf16x3", "tf32x3"])
+def test_split_solve_refines_to_fp64_energy(kind, prec):
+    """Split iterations, then FP64 refinement: converged energy within 1e-6 Eh
+    (the target) of the FP64 oracle's, at a weakly coupled o=3, v=8 instance."""
+    lib = gpu_lib() if kind == "gpu" else hostsim_lib()
+    o, v, naux = 3, 8, 20
+    inst = make_instance(o, v, naux, seed=11, scale=0.2)
+    E0 = oc.solve_compact(inst.L, inst.fock_diag, o, tol=1e-10, max_iter=300)[0]
+    ctx = B.Context(lib, o, v, naux, precision=prec, tol=1e-8, max_iter=300)
+    ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    ctx.init_mp2()
+    E, it, nrm, conv = ctx.solve()
+    assert conv
+    assert abs(E - E0) < 1e-6
+    ctx.close()

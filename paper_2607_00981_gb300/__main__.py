@@ -20,13 +20,14 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "bf16x3", "tf32x3"])
     ap.add_argument("--scale", type=float, default=None, help="override the factor entry scale")
+    ap.add_argument("--no-diis-t3", action="store_true", help="DIIS on T1 and T2 only")
     args = ap.parse_args(argv)
     spec = dict(WORKLOADS[args.workload])
     if args.scale is not None:
         spec["scale"] = args.scale
     inst = make_instance(**spec)
     prec = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}[args.precision]
-    ctx = pkg.context(inst.o, inst.v, inst.naux, precision=prec)
+    ctx = pkg.context(inst.o, inst.v, inst.naux, precision=prec, diis_t3=0 if args.no_diis_t3 else 1)
     ctx.set_hamiltonian(inst.fock_diag, inst.L)
     ctx.init_mp2()
     for it in range(args.iters):

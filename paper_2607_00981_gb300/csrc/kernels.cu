@@ -25,28 +25,32 @@ long long g_launch_count = 0;  // kernels launched by this library (host-side co
 __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
   __shared__ double tile[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
-  if (a.read_k_fast) {
-    for (int rr = ty; rr < 32; rr += 8) {
-      const int r = r0 + rr, k = k0 + tx;
-      if (r < a.R && k < a.Kpad) store_panel(a, r, k, k < a.K ? pack_value(a, r, k) : 0.0);
-    }
-  } else {
-    for (int kk = ty; kk < 32; kk += 8) {
-      const int r = r0 + tx, k = k0 + kk;
-      tile[kk][tx] = (r < a.R && k < a.K) ? pack_value(a, r, k) : 0.0;
-    }
-    __syncthreads();
-    for (int rr = ty; rr < 32; rr += 8) {
-      const int r = r0 + rr, k = k0 + tx;
-      if (r < a.R && k < a.Kpad) store_panel(a, r, k, tile[tx][rr]);
+  const int r0 = blockIdx.x * 32;
+  for (int k0 = blockIdx.y * 32; k0 < a.Kpad; k0 += gridDim.y * 32) {
+    if (a.read_k_fast) {
+      for (int rr = ty; rr < 32; rr += 8) {
+        const int r = r0 + rr, k = k0 + tx;
+        if (r < a.R && k < a.Kpad) store_panel(a, r, k, k < a.K ? pack_value(a, r, k) : 0.0);
+      }
+    } else {
+      for (int kk = ty; kk < 32; kk += 8) {
+        const int r = r0 + tx, k = k0 + kk;
+        tile[kk][tx] = (r < a.R && k < a.K) ? pack_value(a, r, k) : 0.0;
+      }
+      __syncthreads();
+      for (int rr = ty; rr < 32; rr += 8) {
+        const int r = r0 + rr, k = k0 + tx;
+        if (r < a.R && k < a.Kpad) store_panel(a, r, k, tile[tx][rr]);
+      }
+      __syncthreads();
     }
   }
 }
 
 void launch_pack(const PackArgs& a, cudaStream_t s) {
-  // rows on grid x (up to 2^31 - 1 blocks), K on grid y (Kpad / 32 <= 65535)
-  dim3 grid((a.R + 31) / 32, (a.Kpad + 31) / 32), block(32, 8);
+  // rows on grid x (up to 2^31 - 1 blocks); K on grid y, grid-strided past 65535
+  const int gy = std::min((a.Kpad + 31) / 32, 65535);
+  dim3 grid((a.R + 31) / 32, gy), block(32, 8);
   ++g_launch_count;
   k_pack<<<grid, block, 0, s>>>(a);
 }

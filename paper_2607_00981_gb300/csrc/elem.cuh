@@ -49,6 +49,33 @@ RCC_HD void store_panel(const PackArgs& a, int r, int k, double x) {
   }
 }
 
+// FP32 variants for FP32 sources packed into split panels (no FP64 arithmetic).
+RCC_HD float pack_value_f(const PackArgs& a, int r, int k) {
+  float s = 0.f;
+  for (int t = 0; t < a.nterm; ++t) {
+    const i64 idx = (i64)t * a.K + k;
+    const float c = (float)a.coef[idx];
+    if (c != 0.f) {
+      const i64 off = a.colbase[idx] + a.rowoff[(i64)a.sel[idx] * a.R + r];
+      s += c * ((const float*)a.src)[off];
+    }
+  }
+  return s;
+}
+
+RCC_HD void store_panel_f(const PackArgs& a, int r, int k, float x) {
+  const i64 o = (i64)r * a.Kpad + k;
+  if (a.kind == PANEL_BF16X2) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    ((__nv_bfloat16*)a.out_hi)[o] = hi;
+    ((__nv_bfloat16*)a.out_lo)[o] = __float2bfloat16_rn(x - __bfloat162float(hi));
+  } else {
+    const float hi = tf32_round(x);
+    ((float*)a.out_hi)[o] = hi;
+    ((float*)a.out_lo)[o] = tf32_round(x - hi);
+  }
+}
+
 RCC_HD void epi_apply(const EpiArgs& e, int m, int n, double acc) {
   const i64 addr = e.row_base[m] + e.col_off[(i64)e.row_sel[m] * e.N + n];
   const double val = e.row_alpha[m] * acc;

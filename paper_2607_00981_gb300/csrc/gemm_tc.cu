@@ -127,6 +127,45 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Scatter 32 accumulator columns of row m: every address and old value is
+// loaded before any store, so the loads of a row overlap in flight.
+__device__ __forceinline__ void epilogue_row(const EpiArgs& e, int m, int n0, const uint32_t (&r)[32]) {
+  const i64 rb = e.row_base[m];
+  const i64* co = e.col_off + (i64)e.row_sel[m] * e.N;
+  const int nv = min(32, e.N - n0);
+  if (e.c_f32) {
+    float* C = (float*)e.C;
+    const float al = (float)e.row_alpha[m];
+#pragma unroll
+    for (int h = 0; h < 32; h += 16) {
+      i64 ad[16];
+      float old[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) ad[j] = (h + j < nv) ? rb + __ldg(co + n0 + h + j) : -1;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) old[j] = ad[j] >= 0 ? C[ad[j]] : 0.f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (ad[j] >= 0) C[ad[j]] = fmaf(al, __uint_as_float(r[h + j]), old[j]);
+    }
+  } else {
+    double* C = (double*)e.C;
+    const double al = e.row_alpha[m];
+#pragma unroll
+    for (int h = 0; h < 32; h += 16) {
+      i64 ad[16];
+      double old[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) ad[j] = (h + j < nv) ? rb + __ldg(co + n0 + h + j) : -1;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) old[j] = ad[j] >= 0 ? C[ad[j]] : 0.0;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (ad[j] >= 0) C[ad[j]] = old[j] + al * (double)__uint_as_float(r[h + j]);
+    }
+  }
+}
+
 struct TileGeom {
   int mt, nt, splitk, kblocks, kb_per;
 };
@@ -303,9 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int j = 0; j < 32; ++j)
               if (n0 + j < e.N) dst[n0 + j] = __uint_as_float(r[j]);
           } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (n0 + j < e.N) epi_apply(e, m, n0 + j, (double)__uint_as_float(r[j]));
+            epilogue_row(e, m, n0, r);
           }
         }
       }

@@ -7,9 +7,9 @@
 //  k_post        symmetrise / purify / orthogonalise compact R3 (Sec. II.D)
 //  k_update_*    Jacobi step t += r / eps (appendix A.1)
 //  k_wdot, k_sum deterministic weighted dot products (norms, DIIS B matrix)
-//  k_t2_outer    the K = o part of the T2-driven R3 terms, all six permutations
 //  k_diis_*      DIIS bordered solve and extrapolation (Sec. III.A.4)
 #include <algorithm>
+#include <type_traits>
 
 #include "elem.cuh"
 #include "kernels.h"
@@ -22,25 +22,41 @@ long long g_launch_count = 0;  // kernels launched by this library (host-side co
 // Panel gather.  32 x 32 tile per block of 32 x 8 threads; reads go along the
 // source's contiguous direction, writes along k (the output's contiguous axis).
 // ---------------------------------------------------------------------------
+template <bool F32>
 __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
-  __shared__ double tile[32][33];
+  // F32: FP32 source into a split panel, all arithmetic in FP32
+  typedef typename std::conditional<F32, float, double>::type T;
+  __shared__ T tile[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int r0 = blockIdx.x * 32;
   for (int k0 = blockIdx.y * 32; k0 < a.Kpad; k0 += gridDim.y * 32) {
     if (a.read_k_fast) {
       for (int rr = ty; rr < 32; rr += 8) {
         const int r = r0 + rr, k = k0 + tx;
-        if (r < a.R && k < a.Kpad) store_panel(a, r, k, k < a.K ? pack_value(a, r, k) : 0.0);
+        if (r < a.R && k < a.Kpad) {
+          if constexpr (F32)
+            store_panel_f(a, r, k, k < a.K ? pack_value_f(a, r, k) : 0.f);
+          else
+            store_panel(a, r, k, k < a.K ? pack_value(a, r, k) : 0.0);
+        }
       }
     } else {
       for (int kk = ty; kk < 32; kk += 8) {
         const int r = r0 + tx, k = k0 + kk;
-        tile[kk][tx] = (r < a.R && k < a.K) ? pack_value(a, r, k) : 0.0;
+        if constexpr (F32)
+          tile[kk][tx] = (r < a.R && k < a.K) ? pack_value_f(a, r, k) : 0.f;
+        else
+          tile[kk][tx] = (r < a.R && k < a.K) ? pack_value(a, r, k) : 0.0;
       }
       __syncthreads();
       for (int rr = ty; rr < 32; rr += 8) {
         const int r = r0 + rr, k = k0 + tx;
-        if (r < a.R && k < a.Kpad) store_panel(a, r, k, tile[tx][rr]);
+        if (r < a.R && k < a.Kpad) {
+          if constexpr (F32)
+            store_panel_f(a, r, k, tile[tx][rr]);
+          else
+            store_panel(a, r, k, tile[tx][rr]);
+        }
       }
       __syncthreads();
     }
@@ -52,7 +68,10 @@ void launch_pack(const PackArgs& a, cudaStream_t s) {
   const int gy = std::min((a.Kpad + 31) / 32, 65535);
   dim3 grid((a.R + 31) / 32, gy), block(32, 8);
   ++g_launch_count;
-  k_pack<<<grid, block, 0, s>>>(a);
+  if (a.src_f32 && a.kind != PANEL_F64)
+    k_pack<true><<<grid, block, 0, s>>>(a);
+  else
+    k_pack<false><<<grid, block, 0, s>>>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -331,54 +350,6 @@ template void launch_wdot<double>(const double*, const double*, i64, i64, const 
                                   double*, double, int, cudaStream_t);
 template void launch_wdot<float>(const float*, const float*, i64, i64, const double*, double*, double*,
                                  double, int, cudaStream_t);
-
-// ---------------------------------------------------------------------------
-// K = o part of the T2-driven R3 terms (Eq. resi-rccsdt, first line), all six
-// column permutations of -sum_l W^{a1 l}_{i1 i2} t_{l i3}^{a2 a3} for each
-// stored element.  Wvooo[a][l][i][j] = W^{al}_{ij}; t2[l][k][b][c].
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_t2_outer(T* __restrict__ r3, const double* __restrict__ Wvooo,
-                           const double* __restrict__ t2, const int4* __restrict__ blocks, int o, int v,
-                           i64 n3) {
-  // arithmetic in the storage precision of R3 (FP32 in the split modes)
-  const i64 V3 = (i64)v * v * v;
-  for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
-    const int4 ijk = blocks[b];
-    const int occ[3] = {ijk.x, ijk.y, ijk.z};
-    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < V3; x += (i64)gridDim.x * blockDim.x) {
-      const int lab[3] = {(int)(x / ((i64)v * v)), (int)((x / v) % v), (int)(x % v)};
-      T s = 0;
-      // permutations p: positions (p0, p1, p2) take the roles (1, 2, 3)
-      const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-#pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        const int i1 = occ[P[q][0]], i2 = occ[P[q][1]], i3 = occ[P[q][2]];
-        const int a1 = lab[P[q][0]], a2 = lab[P[q][1]], a3 = lab[P[q][2]];
-        const double* W = Wvooo + (((i64)a1 * o) * o + i1) * o + i2;       // stride o*o over l
-        const double* t = t2 + ((i64)i3 * v + a2) * v + a3;                  // stride o*v*v over l
-        for (int l = 0; l < o; ++l) s -= (T)W[(i64)l * o * o] * (T)t[(i64)l * o * v * v];
-      }
-      const i64 g = b * V3 + x;
-      r3[g] = r3[g] + s;
-    }
-  }
-}
-
-template <typename T>
-void launch_t2_outer(T* r3, const double* Wvooo, const double* t2, const int4* blocks, int o, int v,
-                     i64 n3, cudaStream_t s) {
-  const i64 V3 = (i64)v * v * v;
-  unsigned gx = (unsigned)((V3 + 255) / 256);
-  if (gx > 64) gx = 64;
-  unsigned gy = (unsigned)(n3 < 1024 ? n3 : 1024);
-  ++g_launch_count;
-  k_t2_outer<T><<<dim3(gx, gy), 256, 0, s>>>(r3, Wvooo, t2, blocks, o, v, n3);
-}
-template void launch_t2_outer<double>(double*, const double*, const double*, const int4*, int, int, i64,
-                                      cudaStream_t);
-template void launch_t2_outer<float>(float*, const double*, const double*, const int4*, int, int, i64,
-                                     cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // DIIS: B is (M+1) x (M+1) row-major in scalars; solve the bordered system with

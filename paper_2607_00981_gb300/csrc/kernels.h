@@ -34,9 +34,6 @@ void launch_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, 
 template <typename T>
 void launch_wdot(const T* x, const T* y, i64 n, i64 seg, const double* w, double* partial, double* out,
                  double scale, int accumulate, cudaStream_t s);
-template <typename T>
-void launch_t2_outer(T* r3, const double* Wvooo, const double* t2, const int4* blocks, int o, int v,
-                     i64 n3, cudaStream_t s);
 void launch_diis_solve(const double* B, int m, int ld, double* coef, cudaStream_t s);
 template <typename T>
 void launch_diis_extrapolate(T* out, const T* hist, i64 stride, i64 n, const double* coef, int m,

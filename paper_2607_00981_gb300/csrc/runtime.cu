@@ -164,6 +164,7 @@ struct GemmPlan {
   double fma = 0;
   int big = 0;          // candidate for the tensor-core engine in split modes
   int step = 0;         // timing bucket
+  int reuse_A = 0;      // the A panel packed by the previous plan of the group is still valid
 };
 
 struct rccsdt_ctx {
@@ -194,7 +195,7 @@ struct rccsdt_ctx {
   // plan groups
   std::vector<GemmPlan*> p_dress, p_fock, p_eri, p_int, p_r12, p_energy_bare;
   std::vector<std::vector<GemmPlan*>> p_a3;  // per z
-  std::vector<GemmPlan*> p_pp, p_hh, p_ringab, p_ringc, p_t2a;
+  std::vector<GemmPlan*> p_pp, p_hh, p_ringab, p_ringc, p_t2a, p_t2b;
   // combines
   std::vector<rcc::CombineArgs> c_fock, c_helpers, c_int_base, c_r12_base, c_r2_sym, c_wt;
   rcc::CombineArgs c_Lt_copy{}, c_ft_copy{};
@@ -372,8 +373,8 @@ GemmPlan* contraction(rccsdt_ctx* c, const char* spec, double alpha, const View&
   make_pack(c, g->B, Bv.p, Bv.f32, N, K, 1, coefK, kBo, selK, rowB, unit_fast(kB) ? 1 : 0, err);
   make_epi(c, g->E, C.p, C.f32, M, N, rowC, std::vector<int>(M, 0), std::vector<double>(M, alpha), colC, err);
   finish_plan(c, g.get(), K);
-  // in the split modes every contraction of 5e8 FMA or more runs on the tensor cores
-  g->big = big || g->fma >= 5e8;
+  // in the split modes every contraction of 1e7 FMA or more runs on the tensor cores
+  g->big = big || g->fma >= 1e7;
   GemmPlan* raw = g.get();
   c->plans.push_back(std::move(g));
   return raw;
@@ -491,11 +492,11 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   pa.out_lo = c->panelA_lo ? c->panelA_lo->p : nullptr;
   pb.out_hi = c->panelB_hi->p;
   pb.out_lo = c->panelB_lo ? c->panelB_lo->p : nullptr;
-  rcc::launch_pack(pa, c->stream);
+  if (!g->reuse_A) rcc::launch_pack(pa, c->stream);
   rcc::launch_pack(pb, c->stream);
   const int tidx = g->step == 1 ? timer_begin(c, 16, 2.0 * g->fma) : -1;
   if (!tc) {
-    rcc::launch_gemm_f64((const double*)pa.out_hi, (const double*)pb.out_hi, g->Kpad, g->Kpad, g->Kpad,
+    rcc::launch_gemm_f64((const double*)pa.out_hi, (const double*)pb.out_hi, round_up(g->K, 16), g->Kpad, g->Kpad,
                          g->E.e, c->splitk->d(), (i64)(c->splitk->bytes / 8), c->stream);
   } else {
     int* flag = (int*)((double*)c->scalars->p + 1000);
@@ -1006,6 +1007,54 @@ int build_context(rccsdt_ctx* c) {
       c->p_t2a.push_back(g);
     }
 
+  // --- T2-driven term -sum_l W^{al}_{ij} t_lk^{bc}: unit (i,j) over all ordered pairs;
+  //     rows (k,b,c), cols a, K = l.  Trips (i,j,k) of one unit are distinct multisets.
+  {
+    std::vector<i64> rt1((size_t)3 * v);
+    for (int p = 0; p < 3; ++p)
+      for (int a = 0; a < v; ++a) rt1[(size_t)p * v + a] = a * b.S[p];
+    c->buf["RT1"] = upload_vec(c, rt1, &err);
+    const i64* RT1 = (const i64*)c->buf["RT1"]->p;
+    const int M = o * (int)V2, K = o;
+    std::vector<i64> arow(M), acol(K);
+    for (int k = 0; k < o; ++k)
+      for (i64 bc = 0; bc < V2; ++bc) arow[k * V2 + bc] = (i64)k * V2 + bc;   // t2[l][k][b][c]
+    for (int l = 0; l < o; ++l) acol[l] = (i64)l * o * V2;
+    bool first = true;
+    for (int i = 0; i < o; ++i)
+      for (int j = 0; j < o; ++j) {
+        GemmPlan* g = b.new_plan();
+        std::vector<i64> brow(v), bcol(K), ebase(M);
+        std::vector<int> esel(M);
+        std::vector<double> ealpha(M);
+        for (int a = 0; a < v; ++a) brow[a] = (i64)a * o * o * o;             // Wvooo[a][l][i][j]
+        for (int l = 0; l < o; ++l) bcol[l] = (i64)l * o * o + (i64)i * o + j;
+        for (int k = 0; k < o; ++k) {
+          TripleInfo ti = triple(i, j, k);
+          for (i64 bc = 0; bc < V2; ++bc) {
+            const i64 bb = bc / v, cc = bc % v, r = k * V2 + bc;
+            ebase[r] = ti.blk * V3 + bb * b.S[ti.pos[1]] + cc * b.S[ti.pos[2]];
+            esel[r] = ti.pos[0];
+            ealpha[r] = -6.0 / ti.m;
+          }
+        }
+        make_pack(c, g->A, c->D("t2"), 0, M, K, 1, std::vector<double>(K, 1.0), acol, std::vector<int>(K, 0), arow, 0,
+                  &err);
+        make_pack(c, g->B, c->D("Wvooo"), 0, v, K, 1, std::vector<double>(K, 1.0), bcol, std::vector<int>(K, 0), brow,
+                  0, &err);
+        make_epi(c, g->E, r3p, t3f, M, v, ebase, esel, ealpha, {}, &err, RT1);
+        g->big = 1;
+        g->step = 4;
+        g->reuse_A = first ? 0 : 1;
+        first = false;
+        finish_plan(c, g, K);
+        c->p_t2b.push_back(g);
+      }
+  }
+  // the A panel is shared by consecutive plans of these groups
+  for (auto* grp : {&c->p_pp, &c->p_hh, &c->p_ringab, &c->p_ringc})
+    for (size_t q = 1; q < grp->size(); ++q) (*grp)[q]->reuse_A = 1;
+
   if (err) return fail(c, err, "plan construction failed");
   return 0;
 }
@@ -1098,11 +1147,7 @@ int do_residual(rccsdt_ctx* c) {
   {
     StepTimer tm(c, 4);
     if ((st = run_plans(c, c->p_t2a))) return st;
-    const int4* blk = (const int4*)c->blocks_info->p;
-    if (c->opt.precision != RCCSDT_FP64)
-      rcc::launch_t2_outer<float>(c->B("r3")->f(), c->D("Wvooo"), c->D("t2"), blk, c->o, c->v, c->n3, c->stream);
-    else
-      rcc::launch_t2_outer<double>(c->D("r3"), c->D("Wvooo"), c->D("t2"), blk, c->o, c->v, c->n3, c->stream);
+    if ((st = run_plans(c, c->p_t2b))) return st;
   }
   c->have_res = 1;
   return check(c, "do_residual");

@@ -122,30 +122,6 @@ template void launch_wdot<double>(const double*, const double*, i64, i64, const 
 template void launch_wdot<float>(const float*, const float*, i64, i64, const double*, double*, double*, double, int,
                                  cudaStream_t);
 
-template <typename T>
-void launch_t2_outer(T* r3, const double* Wvooo, const double* t2, const int4* blocks, int o, int v, i64 n3,
-                     cudaStream_t) {
-  const i64 V3 = (i64)v * v * v;
-  const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-  for (i64 b = 0; b < n3; ++b) {
-    const int occ[3] = {blocks[b].x, blocks[b].y, blocks[b].z};
-    for (i64 x = 0; x < V3; ++x) {
-      const int lab[3] = {(int)(x / ((i64)v * v)), (int)((x / v) % v), (int)(x % v)};
-      double s = 0.0;
-      for (int q = 0; q < 6; ++q) {
-        const int i1 = occ[P[q][0]], i2 = occ[P[q][1]], i3 = occ[P[q][2]];
-        const int a1 = lab[P[q][0]], a2 = lab[P[q][1]], a3 = lab[P[q][2]];
-        for (int l = 0; l < o; ++l)
-          s -= Wvooo[(((i64)a1 * o + l) * o + i1) * o + i2] * t2[(((i64)l * o + i3) * v + a2) * v + a3];
-      }
-      r3[b * V3 + x] = (T)((double)r3[b * V3 + x] + s);
-    }
-  }
-}
-template void launch_t2_outer<double>(double*, const double*, const double*, const int4*, int, int, i64,
-                                      cudaStream_t);
-template void launch_t2_outer<float>(float*, const double*, const double*, const int4*, int, int, i64, cudaStream_t);
-
 void launch_diis_solve(const double* Bm, int m, int ld, double* coef, cudaStream_t) {
   const int n = m + 1;
   std::vector<double> A((size_t)n * (n + 1));

@@ -104,22 +104,23 @@ RCC_HD i64 perm_offset(int v, const int* pos, int x0, int x1, int x2) {
 // Post-processing of one element of a compact R3 block (Sec. II.D):
 // symmetrise degenerate blocks, purify i=j=k, subtract the S3 mean.
 // r points at the block; returns the processed value at (a, b, c).
+// Arithmetic in the storage type T (FP32 storage computes in FP32).
 template <typename T>
-RCC_HD double post_value(const T* r, int v, int i, int j, int k, int a, int b, int c) {
-  if (i == j && j == k) return 0.0;
+RCC_HD T post_value(const T* r, int v, int i, int j, int k, int a, int b, int c) {
+  if (i == j && j == k) return (T)0;
   const i64 V2 = (i64)v * v;
-  const double rabc = r[a * V2 + b * v + c], racb = r[a * V2 + c * v + b];
-  const double rbac = r[b * V2 + a * v + c], rbca = r[b * V2 + c * v + a];
-  const double rcab = r[c * V2 + a * v + b], rcba = r[c * V2 + b * v + a];
-  double s;
+  const T rabc = r[a * V2 + b * v + c], racb = r[a * V2 + c * v + b];
+  const T rbac = r[b * V2 + a * v + c], rbca = r[b * V2 + c * v + a];
+  const T rcab = r[c * V2 + a * v + b], rcba = r[c * V2 + b * v + a];
+  T s;
   if (i == j)
-    s = 0.5 * (rabc + rbac);
+    s = (T)0.5 * (rabc + rbac);
   else if (j == k)
-    s = 0.5 * (rabc + racb);
+    s = (T)0.5 * (rabc + racb);
   else
     s = rabc;
   // the symmetrisations above keep the sum over the six permutations unchanged
-  const double mean = (rabc + racb + rbac + rbca + rcab + rcba) * (1.0 / 6.0);
+  const T mean = (rabc + racb + rbac + rbca + rcab + rcba) * (T)(1.0 / 6.0);
   return s - mean;
 }
 

@@ -215,7 +215,7 @@ __global__ void k_post(const T* __restrict__ r, T* __restrict__ rp, const int4* 
     const T* rb = r + b * V3;
     for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < V3; e += (i64)gridDim.x * blockDim.x) {
       const int c = (int)(e % v), bb = (int)((e / v) % v), a = (int)(e / ((i64)v * v));
-      rp[b * V3 + e] = (T)post_value(rb, v, ijk.x, ijk.y, ijk.z, a, bb, c);
+      rp[b * V3 + e] = post_value<T>(rb, v, ijk.x, ijk.y, ijk.z, a, bb, c);
     }
   }
 }
@@ -255,14 +255,16 @@ template <typename T>
 __global__ void k_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, int o, int v,
                             i64 n3, double shift) {
   const i64 V3 = (i64)v * v * v;
+  // the denominator is assembled in FP64; the step r / eps is taken in the
+  // storage precision of T3 (FP32 storage: FP32 division, as precise as the store)
   for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
     const int4 ijk = blocks[b];
     const double eo = e[ijk.x] + e[ijk.y] + e[ijk.z];
     for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < V3; x += (i64)gridDim.x * blockDim.x) {
       const int c = (int)(x % v), bb = (int)((x / v) % v), a = (int)(x / ((i64)v * v));
-      const double d = eo - e[o + a] - e[o + bb] - e[o + c] - shift;
+      const T d = (T)(eo - e[o + a] - e[o + bb] - e[o + c] - shift);
       const i64 g = b * V3 + x;
-      t3[g] = (T)((double)t3[g] + (double)rp3[g] / d);
+      t3[g] = t3[g] + rp3[g] / d;
     }
   }
 }
@@ -508,9 +510,9 @@ void launch_mp2(double* t2, const double* g, const double* e, int o, int v, cuda
   k_mp2<<<(unsigned)blocks, 256, 0, s>>>(t2, g, e, o, v);
 }
 
+template <typename T>
 __global__ void k_unpack_spin(const void* __restrict__ t3, int f32, int ntrip, const i64* __restrict__ base,
-                              const int* __restrict__ pos, int v, double* __restrict__ S,
-                              double* __restrict__ D) {
+                              const int* __restrict__ pos, int v, T* __restrict__ S, T* __restrict__ D) {
   const i64 V3 = (i64)v * v * v;
   for (int t = blockIdx.y; t < ntrip; t += gridDim.y) {
     const i64 b0 = base[t];
@@ -519,26 +521,31 @@ __global__ void k_unpack_spin(const void* __restrict__ t3, int f32, int ntrip, c
     for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < V3; e += (i64)gridDim.x * blockDim.x) {
       const int c = (int)(e % v), b = (int)((e / v) % v), a = (int)(e / ((i64)v * v));
       // U^{xyz} = stored[x s0 + y s1 + z s2]
-#define UU(x, y, z) load_src(t3, f32, b0 + (i64)(x) * s0 + (i64)(y) * s1 + (i64)(z) * s2)
-      const double uabc = UU(a, b, c), ubac = UU(b, a, c), ucba = UU(c, b, a);
-      if (S) S[(i64)t * V3 + e] = 2.0 * uabc - ubac - ucba;
+#define UU(x, y, z) (T) load_src(t3, f32, b0 + (i64)(x) * s0 + (i64)(y) * s1 + (i64)(z) * s2)
+      const T uabc = UU(a, b, c), ubac = UU(b, a, c), ucba = UU(c, b, a);
+      if (S) S[(i64)t * V3 + e] = (T)2 * uabc - ubac - ucba;
       if (D) {
-        const double uacb = UU(a, c, b), ucab = UU(c, a, b), ubca = UU(b, c, a);
-        D[(i64)t * V3 + e] = 4.0 * uabc - 2.0 * ubac - 2.0 * ucba - 2.0 * uacb + ucab + ubca;
+        const T uacb = UU(a, c, b), ucab = UU(c, a, b), ubca = UU(b, c, a);
+        D[(i64)t * V3 + e] = (T)4 * uabc - (T)2 * ubac - (T)2 * ucba - (T)2 * uacb + ucab + ubca;
       }
 #undef UU
     }
   }
 }
 
-void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, double* S,
-                        double* D, cudaStream_t s) {
+template <typename T>
+void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, T* S, T* D,
+                        cudaStream_t s) {
   const i64 V3 = (i64)v * v * v;
   unsigned gx = (unsigned)((V3 + 255) / 256);
   if (gx > 32) gx = 32;
   unsigned gy = (unsigned)(ntrip < 1024 ? ntrip : 1024);
   ++g_launch_count;
-  k_unpack_spin<<<dim3(gx, gy), 256, 0, s>>>(t3, f32, ntrip, base, pos, v, S, D);
+  k_unpack_spin<T><<<dim3(gx, gy), 256, 0, s>>>(t3, f32, ntrip, base, pos, v, S, D);
 }
+template void launch_unpack_spin<double>(const void*, int, int, const i64*, const int*, int, double*, double*,
+                                         cudaStream_t);
+template void launch_unpack_spin<float>(const void*, int, int, const i64*, const int*, int, float*, float*,
+                                        cudaStream_t);
 
 }  // namespace rcc

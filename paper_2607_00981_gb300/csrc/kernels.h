@@ -61,6 +61,7 @@ void launch_energy(const double* g, const double* t1, const double* t2, int o, i
 void launch_mp2(double* t2, const double* g, const double* e, int o, int v, cudaStream_t s);
 // For each of ntrip occupied triples: U = t_{trip} unpacked from compact storage,
 // S = (2 - P_a^b - P_a^c) U, D = (2 - P_b^c)(2 - P_a^b - P_a^c) U  (outputs [ntrip][v^3])
-void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v,
-                        double* S, double* D, cudaStream_t s);
+template <typename T>
+void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, T* S, T* D,
+                        cudaStream_t s);
 }  // namespace rcc

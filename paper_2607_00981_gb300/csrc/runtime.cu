@@ -619,7 +619,7 @@ int build_context(rccsdt_ctx* c) {
   b.mk("r2", (size_t)o * o * v * v); b.mk("X2", (size_t)o * o * v * v);
   b.mk("dR1", (size_t)o * v); b.mk("dX2", (size_t)o * o * v * v);
   b.mk("t3", (size_t)n3 * V3, t3e); b.mk("r3", (size_t)n3 * V3, t3e); b.mk("rp3", (size_t)n3 * V3, t3e);
-  b.mk("Sz", (size_t)o * o * V3); b.mk("Dz", (size_t)o * o * V3);
+  b.mk("Sz", (size_t)o * o * V3, t3e); b.mk("Dz", (size_t)o * o * V3, t3e);
   if (err) return fail(c, err, "device allocation failed");
 
   // --- block info and weights
@@ -760,7 +760,7 @@ int build_context(rccsdt_ctx* c) {
         }
     c->a3_base = upload_vec(c, base, &err);
     c->a3_pos = upload_vec(c, pos, &err);
-    View Sz = b.T("Sz", {o, o, v, v, v}), Dz = b.T("Dz", {o, o, v, v, v});
+    View Sz = dense(c->B("Sz")->p, {o, o, v, v, v}, t3f), Dz = dense(c->B("Dz")->p, {o, o, v, v, v}, t3f);
     View dR1 = b.T("dR1", {o, v}), dX2 = b.T("dX2", {o, o, v, v});
     for (int z = 0; z < o; ++z) {
       auto& g = c->p_a3[z];
@@ -1112,9 +1112,13 @@ int do_intermediates(rccsdt_ctx* c) {
   const int o = c->o;
   const int t3f = c->opt.precision != RCCSDT_FP64;
   for (int z = 0; z < o; ++z) {
-    rcc::launch_unpack_spin(c->B("t3")->p, t3f, o * o, (const i64*)c->a3_base->p + (size_t)z * o * o,
-                            (const int*)c->a3_pos->p + (size_t)z * o * o * 3, c->v, c->D("Sz"), c->D("Dz"),
-                            c->stream);
+    const i64* zb = (const i64*)c->a3_base->p + (size_t)z * o * o;
+    const int* zp = (const int*)c->a3_pos->p + (size_t)z * o * o * 3;
+    if (t3f)
+      rcc::launch_unpack_spin<float>(c->B("t3")->p, 1, o * o, zb, zp, c->v, c->B("Sz")->f(), c->B("Dz")->f(),
+                                     c->stream);
+    else
+      rcc::launch_unpack_spin<double>(c->B("t3")->p, 0, o * o, zb, zp, c->v, c->D("Sz"), c->D("Dz"), c->stream);
     if ((st = run_plans(c, c->p_a3[z]))) return st;
   }
   c->have_int = 1;
@@ -1405,6 +1409,7 @@ RCC_API int rccsdt_set_amplitudes(rccsdt_ctx* c, const double* t1, const double*
         const i64 len = std::min(chunk, cnt - off);
         if (dev_copy(c->B("rp3")->p, t3c + off, (size_t)len * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
         rcc::launch_convert<float, double>(c->B("t3")->f() + off, (const double*)c->B("rp3")->p, len, c->stream);
+        if (dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
       }
     }
   }
@@ -1538,10 +1543,12 @@ RCC_API int rccsdt_get_amplitudes(rccsdt_ctx* c, double* t1, double* t2, double*
       if (dev_copy(t3c, c->D("t3"), (size_t)cnt * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
     } else {
       const i64 chunk = c->B("Sz")->bytes / 8;
+      double* stage = (double*)c->B("Sz")->p;  // FP64 staging through the unpack scratch
       for (i64 off = 0; off < cnt; off += chunk) {
         const i64 len = std::min(chunk, cnt - off);
-        rcc::launch_convert<double, float>(c->D("Sz"), c->B("t3")->f() + off, len, c->stream);
-        if (dev_copy(t3c + off, c->D("Sz"), (size_t)len * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+        rcc::launch_convert<double, float>(stage, c->B("t3")->f() + off, len, c->stream);
+        if (dev_copy(t3c + off, stage, (size_t)len * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+        if (dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
       }
     }
   }
@@ -1560,10 +1567,12 @@ RCC_API int rccsdt_get_residuals(rccsdt_ctx* c, double* r1, double* r2, double* 
       if (dev_copy(r3c, c->D("r3"), (size_t)cnt * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
     } else {
       const i64 chunk = c->B("Sz")->bytes / 8;
+      double* stage = (double*)c->B("Sz")->p;
       for (i64 off = 0; off < cnt; off += chunk) {
         const i64 len = std::min(chunk, cnt - off);
-        rcc::launch_convert<double, float>(c->D("Sz"), c->B("r3")->f() + off, len, c->stream);
-        if (dev_copy(r3c + off, c->D("Sz"), (size_t)len * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+        rcc::launch_convert<double, float>(stage, c->B("r3")->f() + off, len, c->stream);
+        if (dev_copy(r3c + off, stage, (size_t)len * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+        if (dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
       }
     }
   }

@@ -75,7 +75,7 @@ void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStrea
   for (i64 b = 0; b < n3; ++b)
     for (i64 e = 0; e < V3; ++e) {
       const int c = (int)(e % v), bb = (int)((e / v) % v), a = (int)(e / ((i64)v * v));
-      rp[b * V3 + e] = (T)post_value(r + b * V3, v, blocks[b].x, blocks[b].y, blocks[b].z, a, bb, c);
+      rp[b * V3 + e] = post_value<T>(r + b * V3, v, blocks[b].x, blocks[b].y, blocks[b].z, a, bb, c);
     }
 }
 template void launch_post<double>(const double*, double*, const int4*, int, i64, cudaStream_t);
@@ -101,8 +101,8 @@ void launch_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, 
   for (i64 b = 0; b < n3; ++b)
     for (i64 x = 0; x < V3; ++x) {
       const int c = (int)(x % v), bb = (int)((x / v) % v), a = (int)(x / ((i64)v * v));
-      const double d = e[blocks[b].x] + e[blocks[b].y] + e[blocks[b].z] - e[o + a] - e[o + bb] - e[o + c] - shift;
-      t3[b * V3 + x] = (T)((double)t3[b * V3 + x] + (double)rp3[b * V3 + x] / d);
+      const T d = (T)(e[blocks[b].x] + e[blocks[b].y] + e[blocks[b].z] - e[o + a] - e[o + bb] - e[o + c] - shift);
+      t3[b * V3 + x] = t3[b * V3 + x] + rp3[b * V3 + x] / d;
     }
 }
 template void launch_update_t3<double>(double*, const double*, const double*, const int4*, int, int, i64, double,
@@ -206,8 +206,9 @@ void launch_mp2(double* t2, const double* g, const double* e, int o, int v, cuda
               g[(((i64)i * v + a) * o + j) * v + b] / (e[i] + e[j] - e[o + a] - e[o + b]);
 }
 
-void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, double* S,
-                        double* D, cudaStream_t) {
+template <typename T>
+void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, T* S, T* D,
+                        cudaStream_t) {
   const i64 V3 = (i64)v * v * v;
   const i64 sv[3] = {(i64)v * v, v, 1};
   for (int t = 0; t < ntrip; ++t) {
@@ -215,12 +216,16 @@ void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, con
     auto U = [&](int x, int y, int z) { return load_src(t3, f32, base[t] + x * s0 + y * s1 + z * s2); };
     for (i64 e = 0; e < V3; ++e) {
       const int c = (int)(e % v), b = (int)((e / v) % v), a = (int)(e / ((i64)v * v));
-      if (S) S[t * V3 + e] = 2.0 * U(a, b, c) - U(b, a, c) - U(c, b, a);
+      if (S) S[t * V3 + e] = (T)(2.0 * U(a, b, c) - U(b, a, c) - U(c, b, a));
       if (D)
-        D[t * V3 + e] = 4.0 * U(a, b, c) - 2.0 * U(b, a, c) - 2.0 * U(c, b, a) - 2.0 * U(a, c, b) + U(c, a, b) +
-                        U(b, c, a);
+        D[t * V3 + e] = (T)(4.0 * U(a, b, c) - 2.0 * U(b, a, c) - 2.0 * U(c, b, a) - 2.0 * U(a, c, b) + U(c, a, b) +
+                            U(b, c, a));
     }
   }
 }
+template void launch_unpack_spin<double>(const void*, int, int, const i64*, const int*, int, double*, double*,
+                                         cudaStream_t);
+template void launch_unpack_spin<float>(const void*, int, int, const i64*, const int*, int, float*, float*,
+                                        cudaStream_t);
 
 }  // namespace rcc

@@ -148,6 +148,33 @@ def config(args, inst):
             "amplitudes": "MP2 guess, then the benchmark's own iterations"}
 
 
+def compare_fp64_split(pkg, stream, dev, name="o8v80", warm=2, steps=2):
+    """FP64 and 3xBF16 s/iteration on the same o8v80 workload (same MP2 start)."""
+    import torch
+    from paper_2607_00981_gb300.synth import workload
+    inst = workload(name)
+    out = {"workload": name}
+    for label, prec in (("fp64", 0), ("bf16x3", 1), ("tf32x3", 2)):
+        ctx = pkg.context(inst.o, inst.v, inst.naux, stream=stream.cuda_stream, precision=prec)
+        ctx.set_hamiltonian(inst.fock_diag, inst.L)
+        ctx.init_mp2()
+        for _ in range(warm):
+            ctx.iterate()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.iterate()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[label] = e0.elapsed_time(e1) / 1e3 / steps
+        ctx.close()
+    out["unit"] = "s/iteration"
+    out["speedup_bf16x3"] = out["fp64"] / out["bf16x3"]
+    out["speedup_tf32x3"] = out["fp64"] / out["tf32x3"]
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2607_00981_gb300 as pkg
@@ -163,8 +190,10 @@ def run_ours(args, rank, world):
     o, v, naux = inst.o, inst.v, inst.naux
     prec = PRECISIONS[args.precision]
     stream = torch.cuda.current_stream()
-    ctx = pkg.context(o, v, naux, stream=stream.cuda_stream, precision=prec,
-                      diis_t3=0 if args.no_diis_t3 else 1)
+    n3 = o * (o + 1) * (o + 2) // 6
+    hist_t3 = 2 * 8 * n3 * v ** 3 * (8 if prec == 0 else 4)
+    diis_t3 = 0 if (args.no_diis_t3 or hist_t3 > 64e9) else 1
+    ctx = pkg.context(o, v, naux, stream=stream.cuda_stream, precision=prec, diis_t3=diis_t3)
     lib = ctx.lib
     L = torch.from_numpy(inst.L).to(f"cuda:{dev}")
     f = torch.from_numpy(inst.fock_diag).to(f"cuda:{dev}")
@@ -212,7 +241,7 @@ def run_ours(args, rank, world):
         ht1, ht2, ht3 = pin(ht1), pin(ht2), pin(ht3)
         bytes_in = hL.nbytes + hf.nbytes + ht1.nbytes + ht2.nbytes + ht3.nbytes
         bytes_out = ht1.nbytes + ht2.nbytes + ht3.nbytes + 8 * 5
-        ksteps = max(1, min(args.steps, 3))
+        ksteps = max(1, min(args.steps, 3 if n3 * v ** 3 < 1e9 else 1))
         barrier()
         t0 = time.perf_counter()
         for _ in range(ksteps):
@@ -229,7 +258,6 @@ def run_ours(args, rank, world):
                "h2d_bytes_per_step": int(bytes_in), "d2h_bytes_per_step": int(bytes_out),
                "steps": ksteps, "note": "set_hamiltonian + set_amplitudes from pinned host memory, "
                                         "rccsdt_iterate, get_amplitudes to host; DIIS history restarts each step"}
-        del n3
 
     # --- roofline of the dominant kernel (the pp-ladder GEMM)
     pk = peaks()
@@ -250,6 +278,10 @@ def run_ours(args, rank, world):
                 "traffic": None, "peak_source": src, "launches": int(gemm_n),
                 "avg_launch_ms": gemm_ms / gemm_n}
 
+    compare = None
+    if not args.no_compare and world == 1:
+        compare = compare_fp64_split(pkg, stream, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, sample = oracle_sample(inst, seconds_budget=args.ref_seconds)
@@ -262,7 +294,8 @@ def run_ours(args, rank, world):
                 "config": dict(config(args, inst), parallelism=f"replicas{world}"),
                 "tflops": 2.0 * fma * world / (ms_total / 1e3 / args.steps) / 1e12,
                 "energy_last": energies[-1], "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
-                "cpu_baseline": cpu, "clocks": clk.summary(),
+                "cpu_baseline": cpu, "clocks": clk.summary(), "fp64_vs_split": compare,
+                "diis": "T1, T2 and T3" if diis_t3 else "T1 and T2 (T3 history would exceed 64 GB)",
                 "step_ms": {k: float(x) / args.steps for k, x in zip(
                     ["intermediates", "pp", "ring", "hh", "t2", "r12_setup", "post", "update", "energy"], st[:9])}}
         print(json.dumps(line), flush=True)
@@ -277,11 +310,12 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="o8v80")
-    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
+    ap.add_argument("--workload", default="o16v160")
+    ap.add_argument("--precision", default="bf16x3", choices=list(PRECISIONS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-diis-t3", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 vs split comparison at o8v80")
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

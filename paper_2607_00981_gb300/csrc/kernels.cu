@@ -510,42 +510,81 @@ void launch_mp2(double* t2, const double* g, const double* e, int o, int v, cuda
   k_mp2<<<(unsigned)blocks, 256, 0, s>>>(t2, g, e, o, v);
 }
 
+// S = (2 - P_a^b - P_a^c) U for each occupied triple, U = t_{trip} read from its
+// stored block.  One CTA computes a 16^3 tile of one triple: the three source
+// cubes (U^{abc}, U^{bac}, U^{cba} over the tile's label ranges) are loaded into
+// shared memory with the threads running along the stored block's unit-stride
+// axis, then S is written along c.
 template <typename T>
-__global__ void k_unpack_spin(const void* __restrict__ t3, int f32, int ntrip, const i64* __restrict__ base,
-                              const int* __restrict__ pos, int v, T* __restrict__ S, T* __restrict__ D) {
+__global__ void __launch_bounds__(256) k_unpack_spin(const void* __restrict__ t3, int f32, int ntrip,
+                                                     const i64* __restrict__ base, const int* __restrict__ pos, int v,
+                                                     T* __restrict__ S) {
+  constexpr int TL = 16;
+  // padded [TL][TL+1][TL+2] cubes in dynamic shared memory (59 KB for FP32, 118 KB for FP64)
+  extern __shared__ __align__(16) unsigned char unpack_smem[];
+  typedef T Cube[TL][TL + 1][TL + 2];
+  Cube* cube = reinterpret_cast<Cube*>(unpack_smem);
+  const int nt = (v + TL - 1) / TL;
   const i64 V3 = (i64)v * v * v;
+  const i64 sv[3] = {(i64)v * v, v, 1};
   for (int t = blockIdx.y; t < ntrip; t += gridDim.y) {
     const i64 b0 = base[t];
-    const i64 sv[3] = {(i64)v * v, v, 1};
-    const i64 s0 = sv[pos[3 * t + 0]], s1 = sv[pos[3 * t + 1]], s2 = sv[pos[3 * t + 2]];
-    for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < V3; e += (i64)gridDim.x * blockDim.x) {
-      const int c = (int)(e % v), b = (int)((e / v) % v), a = (int)(e / ((i64)v * v));
-      // U^{xyz} = stored[x s0 + y s1 + z s2]
-#define UU(x, y, z) (T) load_src(t3, f32, b0 + (i64)(x) * s0 + (i64)(y) * s1 + (i64)(z) * s2)
-      const T uabc = UU(a, b, c), ubac = UU(b, a, c), ucba = UU(c, b, a);
-      if (S) S[(i64)t * V3 + e] = (T)2 * uabc - ubac - ucba;
-      if (D) {
-        const T uacb = UU(a, c, b), ucab = UU(c, a, b), ubca = UU(b, c, a);
-        D[(i64)t * V3 + e] = (T)4 * uabc - (T)2 * ubac - (T)2 * ucba - (T)2 * uacb + ucab + ubca;
+    const int p[3] = {pos[3 * t], pos[3 * t + 1], pos[3 * t + 2]};
+    const i64 st[3] = {sv[p[0]], sv[p[1]], sv[p[2]]};
+    // slot (position) whose label runs along the stored unit-stride axis
+    const int fast = p[0] == 2 ? 0 : (p[1] == 2 ? 1 : 2);
+    for (int tile = blockIdx.x; tile < nt * nt * nt; tile += gridDim.x) {
+      const int ta = tile / (nt * nt), tb = (tile / nt) % nt, tc = tile % nt;
+      const int lo[3] = {ta * TL, tb * TL, tc * TL};
+      // term q reads U at slots (x0, x1, x2) whose label ranges are, in output label order:
+      //   q=0: (a, b, c)   q=1: (b, a, c)   q=2: (c, b, a)
+      const int rng[3][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0}};
+      __syncthreads();
+      for (int q = 0; q < 3; ++q) {
+        for (int e = threadIdx.x; e < TL * TL * TL; e += blockDim.x) {
+          int u[3];
+          // the fast slot varies fastest across threads
+          const int s1 = (fast + 1) % 3, s2 = (fast + 2) % 3;
+          u[fast] = e % TL;
+          u[s1] = (e / TL) % TL;
+          u[s2] = e / (TL * TL);
+          const int x0 = lo[rng[q][0]] + u[0], x1 = lo[rng[q][1]] + u[1], x2 = lo[rng[q][2]] + u[2];
+          T val = (T)0;
+          if (x0 < v && x1 < v && x2 < v) val = (T)load_src(t3, f32, b0 + x0 * st[0] + x1 * st[1] + x2 * st[2]);
+          cube[q][u[0]][u[1]][u[2]] = val;
+        }
       }
-#undef UU
+      __syncthreads();
+      for (int e = threadIdx.x; e < TL * TL * TL; e += blockDim.x) {
+        const int c = e % TL, bb = (e / TL) % TL, a = e / (TL * TL);
+        const int ga = lo[0] + a, gb = lo[1] + bb, gc = lo[2] + c;
+        if (ga < v && gb < v && gc < v) {
+          // U^{abc} = cube0[a][b][c], U^{bac} = cube1[b][a][c], U^{cba} = cube2[c][b][a]
+          const T s_ = (T)2 * cube[0][a][bb][c] - cube[1][bb][a][c] - cube[2][c][bb][a];
+          S[(i64)t * V3 + ((i64)ga * v + gb) * v + gc] = s_;
+        }
+      }
     }
   }
 }
 
 template <typename T>
-void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, T* S, T* D,
+void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, T* S,
                         cudaStream_t s) {
-  const i64 V3 = (i64)v * v * v;
-  unsigned gx = (unsigned)((V3 + 255) / 256);
-  if (gx > 32) gx = 32;
+  const int nt = (v + 15) / 16;
+  unsigned gx = (unsigned)(nt * nt * nt);
+  if (gx > 1024) gx = 1024;
   unsigned gy = (unsigned)(ntrip < 1024 ? ntrip : 1024);
+  const size_t smem = 3 * sizeof(T) * 16 * 17 * 18;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_unpack_spin<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
   ++g_launch_count;
-  k_unpack_spin<T><<<dim3(gx, gy), 256, 0, s>>>(t3, f32, ntrip, base, pos, v, S, D);
+  k_unpack_spin<T><<<dim3(gx, gy), 256, smem, s>>>(t3, f32, ntrip, base, pos, v, S);
 }
-template void launch_unpack_spin<double>(const void*, int, int, const i64*, const int*, int, double*, double*,
-                                         cudaStream_t);
-template void launch_unpack_spin<float>(const void*, int, int, const i64*, const int*, int, float*, float*,
-                                        cudaStream_t);
+template void launch_unpack_spin<double>(const void*, int, int, const i64*, const int*, int, double*, cudaStream_t);
+template void launch_unpack_spin<float>(const void*, int, int, const i64*, const int*, int, float*, cudaStream_t);
 
 }  // namespace rcc

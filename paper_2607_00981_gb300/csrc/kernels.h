@@ -60,8 +60,8 @@ void launch_energy(const double* g, const double* t1, const double* t2, int o, i
 // t2[i,j,a,b] = g[i,a,j,b] / (e_i + e_j - e_a - e_b)
 void launch_mp2(double* t2, const double* g, const double* e, int o, int v, cudaStream_t s);
 // For each of ntrip occupied triples: U = t_{trip} unpacked from compact storage,
-// S = (2 - P_a^b - P_a^c) U, D = (2 - P_b^c)(2 - P_a^b - P_a^c) U  (outputs [ntrip][v^3])
+// S = (2 - P_a^b - P_a^c) U  (output [ntrip][v^3])
 template <typename T>
-void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, T* S, T* D,
+void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, T* S,
                         cudaStream_t s);
 }  // namespace rcc

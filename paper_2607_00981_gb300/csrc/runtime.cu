@@ -619,7 +619,7 @@ int build_context(rccsdt_ctx* c) {
   b.mk("r2", (size_t)o * o * v * v); b.mk("X2", (size_t)o * o * v * v);
   b.mk("dR1", (size_t)o * v); b.mk("dX2", (size_t)o * o * v * v);
   b.mk("t3", (size_t)n3 * V3, t3e); b.mk("r3", (size_t)n3 * V3, t3e); b.mk("rp3", (size_t)n3 * V3, t3e);
-  b.mk("Sz", (size_t)o * o * V3, t3e); b.mk("Dz", (size_t)o * o * V3, t3e);
+  b.mk("Sz", (size_t)o * o * V3, t3e);
   if (err) return fail(c, err, "device allocation failed");
 
   // --- block info and weights
@@ -760,11 +760,14 @@ int build_context(rccsdt_ctx* c) {
         }
     c->a3_base = upload_vec(c, base, &err);
     c->a3_pos = upload_vec(c, pos, &err);
-    View Sz = dense(c->B("Sz")->p, {o, o, v, v, v}, t3f), Dz = dense(c->B("Dz")->p, {o, o, v, v, v}, t3f);
+    View Sz = dense(c->B("Sz")->p, {o, o, v, v, v}, t3f);
     View dR1 = b.T("dR1", {o, v}), dX2 = b.T("dX2", {o, o, v, v});
     for (int z = 0; z < o; ++z) {
       auto& g = c->p_a3[z];
-      b.ct(g, "xybc,xybca->a", 0.5, eri("oovv"), Dz, slice0(dR1, z));
+      // R1 T3 term with the double check D^{x0x1x2} = 2 S^{x0x1x2} - S^{x0x2x1}:
+      // 1/2 sum v^{xy}_{bc} D^{bca} = sum v^{xy}_{bc} S^{bca} - 1/2 sum v^{xy}_{bc} S^{bac}
+      b.ct(g, "xybc,xybca->a", 1.0, eri("oovv"), Sz, slice0(dR1, z));
+      b.ct(g, "xybc,xybac->a", -0.5, eri("oovv"), Sz, slice0(dR1, z));
       b.ct(g, "xc,xycab->yab", 0.5, sub(sub(ft, 0, O0, o), 1, V0, v), Sz, permuted(slice0(permuted(dX2, {1, 0, 2, 3}), z), {0, 1, 2}));
       b.ct(g, "bxcd,xydac->yab", 1.0, eri("vovv"), Sz, slice0(permuted(dX2, {1, 0, 2, 3}), z), 1);
       b.ct(g, "xjc,xycab->yjab", -1.0, slice0(eri("ooov"), z), Sz, dX2);
@@ -1016,23 +1019,24 @@ int build_context(rccsdt_ctx* c) {
     c->buf["RT1"] = upload_vec(c, rt1, &err);
     const i64* RT1 = (const i64*)c->buf["RT1"]->p;
     const int M = o * (int)V2, K = o;
-    std::vector<i64> arow(M), acol(K);
-    for (int k = 0; k < o; ++k)
-      for (i64 bc = 0; bc < V2; ++bc) arow[k * V2 + bc] = (i64)k * V2 + bc;   // t2[l][k][b][c]
-    for (int l = 0; l < o; ++l) acol[l] = (i64)l * o * V2;
-    bool first = true;
+    std::vector<i64> acol(K);
+    for (int l = 0; l < o; ++l) acol[l] = (i64)l * o * V2;                   // t2[l][k][b][c]
     for (int i = 0; i < o; ++i)
       for (int j = 0; j < o; ++j) {
         GemmPlan* g = b.new_plan();
-        std::vector<i64> brow(v), bcol(K), ebase(M);
+        std::vector<i64> arow(M), brow(v), bcol(K), ebase(M);
         std::vector<int> esel(M);
         std::vector<double> ealpha(M);
         for (int a = 0; a < v; ++a) brow[a] = (i64)a * o * o * o;             // Wvooo[a][l][i][j]
         for (int l = 0; l < o; ++l) bcol[l] = (i64)l * o * o + (i64)i * o + j;
         for (int k = 0; k < o; ++k) {
           TripleInfo ti = triple(i, j, k);
-          for (i64 bc = 0; bc < V2; ++bc) {
-            const i64 bb = bc / v, cc = bc % v, r = k * V2 + bc;
+          // enumerate (b, c) so that consecutive rows hit the stored unit-stride axis
+          // when b or c lands there (coalesced scatter); otherwise c fastest
+          const bool b_fast = ti.pos[1] == 2;
+          for (i64 q = 0; q < V2; ++q) {
+            const i64 bb = b_fast ? q % v : q / v, cc = b_fast ? q / v : q % v, r = k * V2 + q;
+            arow[r] = (i64)k * V2 + bb * v + cc;
             ebase[r] = ti.blk * V3 + bb * b.S[ti.pos[1]] + cc * b.S[ti.pos[2]];
             esel[r] = ti.pos[0];
             ealpha[r] = -6.0 / ti.m;
@@ -1045,8 +1049,6 @@ int build_context(rccsdt_ctx* c) {
         make_epi(c, g->E, r3p, t3f, M, v, ebase, esel, ealpha, {}, &err, RT1);
         g->big = 1;
         g->step = 4;
-        g->reuse_A = first ? 0 : 1;
-        first = false;
         finish_plan(c, g, K);
         c->p_t2b.push_back(g);
       }
@@ -1115,10 +1117,9 @@ int do_intermediates(rccsdt_ctx* c) {
     const i64* zb = (const i64*)c->a3_base->p + (size_t)z * o * o;
     const int* zp = (const int*)c->a3_pos->p + (size_t)z * o * o * 3;
     if (t3f)
-      rcc::launch_unpack_spin<float>(c->B("t3")->p, 1, o * o, zb, zp, c->v, c->B("Sz")->f(), c->B("Dz")->f(),
-                                     c->stream);
+      rcc::launch_unpack_spin<float>(c->B("t3")->p, 1, o * o, zb, zp, c->v, c->B("Sz")->f(), c->stream);
     else
-      rcc::launch_unpack_spin<double>(c->B("t3")->p, 0, o * o, zb, zp, c->v, c->D("Sz"), c->D("Dz"), c->stream);
+      rcc::launch_unpack_spin<double>(c->B("t3")->p, 0, o * o, zb, zp, c->v, c->D("Sz"), c->stream);
     if ((st = run_plans(c, c->p_a3[z]))) return st;
   }
   c->have_int = 1;

@@ -207,7 +207,7 @@ void launch_mp2(double* t2, const double* g, const double* e, int o, int v, cuda
 }
 
 template <typename T>
-void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, T* S, T* D,
+void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, T* S,
                         cudaStream_t) {
   const i64 V3 = (i64)v * v * v;
   const i64 sv[3] = {(i64)v * v, v, 1};
@@ -216,16 +216,11 @@ void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, con
     auto U = [&](int x, int y, int z) { return load_src(t3, f32, base[t] + x * s0 + y * s1 + z * s2); };
     for (i64 e = 0; e < V3; ++e) {
       const int c = (int)(e % v), b = (int)((e / v) % v), a = (int)(e / ((i64)v * v));
-      if (S) S[t * V3 + e] = (T)(2.0 * U(a, b, c) - U(b, a, c) - U(c, b, a));
-      if (D)
-        D[t * V3 + e] = (T)(4.0 * U(a, b, c) - 2.0 * U(b, a, c) - 2.0 * U(c, b, a) - 2.0 * U(a, c, b) + U(c, a, b) +
-                            U(b, c, a));
+      S[t * V3 + e] = (T)(2.0 * U(a, b, c) - U(b, a, c) - U(c, b, a));
     }
   }
 }
-template void launch_unpack_spin<double>(const void*, int, int, const i64*, const int*, int, double*, double*,
-                                         cudaStream_t);
-template void launch_unpack_spin<float>(const void*, int, int, const i64*, const int*, int, float*, float*,
-                                        cudaStream_t);
+template void launch_unpack_spin<double>(const void*, int, int, const i64*, const int*, int, double*, cudaStream_t);
+template void launch_unpack_spin<float>(const void*, int, int, const i64*, const int*, int, float*, cudaStream_t);
 
 }  // namespace rcc

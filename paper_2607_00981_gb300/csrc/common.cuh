@@ -28,6 +28,7 @@ struct PackArgs {
   void* out_lo;          // [R][Kpad] second half of a split (unused for F64)
   int Kpad;              // leading dimension of the output (>= K, zero filled)
   int read_k_fast;       // 1: source contiguous along k, 0: along r
+  int one_sel;           // 1: every selector is 0 (rowoff is a single table of R entries)
 };
 
 // Table-driven epilogue: C[row_base[m] + col_off[row_sel[m]*N + n]] += row_alpha[m] * acc(m, n)

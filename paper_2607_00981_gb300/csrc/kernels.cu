@@ -22,43 +22,65 @@ long long g_launch_count = 0;  // kernels launched by this library (host-side co
 // Panel gather.  32 x 32 tile per block of 32 x 8 threads; reads go along the
 // source's contiguous direction, writes along k (the output's contiguous axis).
 // ---------------------------------------------------------------------------
+// One 32 x 32 tile per step; the tile's column tables (coefficient, base offset,
+// selector of up to 3 terms) and, with a single selector, its 32 row offsets
+// are staged in shared memory, so an element costs one source load.
 template <bool F32>
 __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
-  // F32: FP32 source into a split panel, all arithmetic in FP32
   typedef typename std::conditional<F32, float, double>::type T;
   __shared__ T tile[32][33];
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  __shared__ i64 cb[3][32];
+  __shared__ T cf[3][32];
+  __shared__ int sl[3][32];
+  __shared__ i64 ro[32];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int r0 = blockIdx.x * 32;
+  const int nterm = a.nterm < 3 ? a.nterm : 3;
+  if (a.one_sel && tid < 32) ro[tid] = (r0 + tid < a.R) ? a.rowoff[r0 + tid] : 0;
+  auto value = [&](int rr, int kk) -> T {
+    const int r = r0 + rr;
+    T s = (T)0;
+    for (int t = 0; t < nterm; ++t) {
+      const T c = cf[t][kk];
+      if (c != (T)0) {
+        const i64 off = cb[t][kk] + (a.one_sel ? ro[rr] : a.rowoff[(i64)sl[t][kk] * a.R + r]);
+        if constexpr (F32)
+          s += c * ((const float*)a.src)[off];  // no FP64 conversions on the FP32 path
+        else
+          s += c * (T)load_src(a.src, a.src_f32, off);
+      }
+    }
+    return s;
+  };
+  auto store = [&](int r, int k, T x) {
+    if constexpr (F32)
+      store_panel_f(a, r, k, x);
+    else
+      store_panel(a, r, k, x);
+  };
   for (int k0 = blockIdx.y * 32; k0 < a.Kpad; k0 += gridDim.y * 32) {
+    __syncthreads();
+    if (tid < nterm * 32) {
+      const int t = tid >> 5, kk = tid & 31, k = k0 + kk;
+      const bool ok = k < a.K;
+      const i64 idx = (i64)t * a.K + k;
+      cb[t][kk] = ok ? a.colbase[idx] : 0;
+      cf[t][kk] = ok ? (T)a.coef[idx] : (T)0;
+      sl[t][kk] = ok ? a.sel[idx] : 0;
+    }
+    __syncthreads();
     if (a.read_k_fast) {
       for (int rr = ty; rr < 32; rr += 8) {
         const int r = r0 + rr, k = k0 + tx;
-        if (r < a.R && k < a.Kpad) {
-          if constexpr (F32)
-            store_panel_f(a, r, k, k < a.K ? pack_value_f(a, r, k) : 0.f);
-          else
-            store_panel(a, r, k, k < a.K ? pack_value(a, r, k) : 0.0);
-        }
+        if (r < a.R && k < a.Kpad) store(r, k, value(rr, tx));
       }
     } else {
-      for (int kk = ty; kk < 32; kk += 8) {
-        const int r = r0 + tx, k = k0 + kk;
-        if constexpr (F32)
-          tile[kk][tx] = (r < a.R && k < a.K) ? pack_value_f(a, r, k) : 0.f;
-        else
-          tile[kk][tx] = (r < a.R && k < a.K) ? pack_value(a, r, k) : 0.0;
-      }
+      for (int kk = ty; kk < 32; kk += 8) tile[kk][tx] = (r0 + tx < a.R) ? value(tx, kk) : (T)0;
       __syncthreads();
       for (int rr = ty; rr < 32; rr += 8) {
         const int r = r0 + rr, k = k0 + tx;
-        if (r < a.R && k < a.Kpad) {
-          if constexpr (F32)
-            store_panel_f(a, r, k, tile[tx][rr]);
-          else
-            store_panel(a, r, k, tile[tx][rr]);
-        }
+        if (r < a.R && k < a.Kpad) store(r, k, tile[tx][rr]);
       }
-      __syncthreads();
     }
   }
 }

@@ -274,6 +274,9 @@ void make_pack(rccsdt_ctx* c, PackPlan& P, const void* src, int src_f32, int R, 
   a.sel = (const int*)P.sel->p;
   a.rowoff = shared_rowoff ? shared_rowoff : (const i64*)P.rowoff->p;
   a.read_k_fast = read_k_fast;
+  a.one_sel = 1;
+  for (int x : sel)
+    if (x != 0) a.one_sel = 0;
 }
 
 void make_epi(rccsdt_ctx* c, EpiPlan& E, void* C, int c_f32, int M, int N,

@@ -572,7 +572,13 @@ __global__ void __launch_bounds__(256) k_unpack_spin(const void* __restrict__ t3
           u[s2] = e / (TL * TL);
           const int x0 = lo[rng[q][0]] + u[0], x1 = lo[rng[q][1]] + u[1], x2 = lo[rng[q][2]] + u[2];
           T val = (T)0;
-          if (x0 < v && x1 < v && x2 < v) val = (T)load_src(t3, f32, b0 + x0 * st[0] + x1 * st[1] + x2 * st[2]);
+          if (x0 < v && x1 < v && x2 < v) {
+            const i64 off = b0 + x0 * st[0] + x1 * st[1] + x2 * st[2];
+            if constexpr (sizeof(T) == 4)
+              val = ((const float*)t3)[off];  // FP32 storage: no FP64 conversions
+            else
+              val = (T)load_src(t3, f32, off);
+          }
           cube[q][u[0]][u[1]][u[2]] = val;
         }
       }

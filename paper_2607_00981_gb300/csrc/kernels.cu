@@ -615,4 +615,51 @@ void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, con
 template void launch_unpack_spin<double>(const void*, int, int, const i64*, const int*, int, double*, cudaStream_t);
 template void launch_unpack_spin<float>(const void*, int, int, const i64*, const int*, int, float*, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// T3 contribution to R1 for one batch z of unpacked, spin-summed blocks
+// S[x][y][e1][e2][e3] (the double check is D^{x0x1x2} = 2 S^{x0x1x2} - S^{x0x2x1}):
+//   dR1[z][a] += sum_{x,y,b} sum_c v^{xy}_{bc} (S[x,y,b,c,a] - 1/2 S[x,y,b,a,c])
+// One pass over S; per-block partial sums, then a fixed-order reduction.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_r1_t3(const T* __restrict__ S, const double* __restrict__ oovv, int o,
+                                               int v, double* __restrict__ partial) {
+  const i64 nslab = (i64)o * o * v;
+  const i64 V2 = (i64)v * v;
+  for (int a0 = 0; a0 < v; a0 += blockDim.x) {
+    const int a = a0 + threadIdx.x;
+    T acc = (T)0;
+    if (a < v) {
+      for (i64 s = blockIdx.x; s < nslab; s += gridDim.x) {
+        const T* sl = S + s * V2;          // slab (x, y, b): [c][a]
+        const double* w = oovv + s * v;    // v^{xy}_{bc} over c (oovv[x][y][b][c])
+        for (int c = 0; c < v; ++c) acc += (T)w[c] * (sl[(i64)c * v + a] - (T)0.5 * sl[(i64)a * v + c]);
+      }
+      partial[(i64)blockIdx.x * v + a] = (double)acc;
+    }
+  }
+}
+
+__global__ void k_r1_reduce(const double* __restrict__ partial, int nblk, int v, double* __restrict__ out) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= v) return;
+  double s = 0.0;
+  for (int q = 0; q < nblk; ++q) s += partial[(i64)q * v + a];
+  out[a] += s;
+}
+
+template <typename T>
+void launch_r1_t3(const T* S, const double* oovv, int o, int v, double* dR1_z, double* scratch, i64 scratch_elems,
+                  cudaStream_t s) {
+  const i64 nslab = (i64)o * o * v;
+  int nblk = (int)std::min<i64>(nslab, 1216);
+  while ((i64)nblk * v > scratch_elems && nblk > 1) nblk /= 2;
+  ++g_launch_count;
+  k_r1_t3<T><<<nblk, 256, 0, s>>>(S, oovv, o, v, scratch);
+  ++g_launch_count;
+  k_r1_reduce<<<(v + 127) / 128, 128, 0, s>>>(scratch, nblk, v, dR1_z);
+}
+template void launch_r1_t3<double>(const double*, const double*, int, int, double*, double*, i64, cudaStream_t);
+template void launch_r1_t3<float>(const float*, const double*, int, int, double*, double*, i64, cudaStream_t);
+
 }  // namespace rcc

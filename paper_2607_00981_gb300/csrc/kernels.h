@@ -64,4 +64,8 @@ void launch_mp2(double* t2, const double* g, const double* e, int o, int v, cuda
 template <typename T>
 void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, const int* pos, int v, T* S,
                         cudaStream_t s);
+// dR1_z[a] += sum_{x,y,b,c} v^{xy}_{bc} (S[x,y,b,c,a] - 1/2 S[x,y,b,a,c]) (T3 term of R1, one batch z)
+template <typename T>
+void launch_r1_t3(const T* S, const double* oovv, int o, int v, double* dR1_z, double* scratch, i64 scratch_elems,
+                  cudaStream_t s);
 }  // namespace rcc

@@ -165,6 +165,7 @@ struct GemmPlan {
   int big = 0;          // candidate for the tensor-core engine in split modes
   int step = 0;         // timing bucket
   int reuse_A = 0;      // the A panel packed by the previous plan of the group is still valid
+  int reuse_B = 0;      // likewise for the B panel
 };
 
 struct rccsdt_ctx {
@@ -191,6 +192,7 @@ struct rccsdt_ctx {
   // panels (engine scratch)
   std::unique_ptr<DBuf> panelA_hi, panelA_lo, panelB_hi, panelB_lo;
   size_t panel_bytes = 0;
+  int packedA_kind = -1, packedB_kind = -1;  // panel kinds last written (reuse needs a match)
 
   // plan groups
   std::vector<GemmPlan*> p_dress, p_fock, p_eri, p_int, p_r12, p_energy_bare;
@@ -495,8 +497,9 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   pa.out_lo = c->panelA_lo ? c->panelA_lo->p : nullptr;
   pb.out_hi = c->panelB_hi->p;
   pb.out_lo = c->panelB_lo ? c->panelB_lo->p : nullptr;
-  if (!g->reuse_A) rcc::launch_pack(pa, c->stream);
-  rcc::launch_pack(pb, c->stream);
+  if (!g->reuse_A || c->packedA_kind != kind) rcc::launch_pack(pa, c->stream);
+  if (!g->reuse_B || c->packedB_kind != kind) rcc::launch_pack(pb, c->stream);
+  c->packedA_kind = c->packedB_kind = kind;
   const int tidx = g->step == 1 ? timer_begin(c, 16, 2.0 * g->fma) : -1;
   if (!tc) {
     rcc::launch_gemm_f64((const double*)pa.out_hi, (const double*)pb.out_hi, round_up(g->K, 16), g->Kpad, g->Kpad,
@@ -767,15 +770,16 @@ int build_context(rccsdt_ctx* c) {
     View dR1 = b.T("dR1", {o, v}), dX2 = b.T("dX2", {o, o, v, v});
     for (int z = 0; z < o; ++z) {
       auto& g = c->p_a3[z];
-      // R1 T3 term with the double check D^{x0x1x2} = 2 S^{x0x1x2} - S^{x0x2x1}:
-      // 1/2 sum v^{xy}_{bc} D^{bca} = sum v^{xy}_{bc} S^{bca} - 1/2 sum v^{xy}_{bc} S^{bac}
-      b.ct(g, "xybc,xybca->a", 1.0, eri("oovv"), Sz, slice0(dR1, z));
-      b.ct(g, "xybc,xybac->a", -0.5, eri("oovv"), Sz, slice0(dR1, z));
-      b.ct(g, "xc,xycab->yab", 0.5, sub(sub(ft, 0, O0, o), 1, V0, v), Sz, permuted(slice0(permuted(dX2, {1, 0, 2, 3}), z), {0, 1, 2}));
-      b.ct(g, "bxcd,xydac->yab", 1.0, eri("vovv"), Sz, slice0(permuted(dX2, {1, 0, 2, 3}), z), 1);
-      b.ct(g, "xjc,xycab->yjab", -1.0, slice0(eri("ooov"), z), Sz, dX2);
-      b.ct(g, "xde,xyeba->abdy", -1.0, slice0(eri("oovv"), z), Sz, Wvvvo, 1);
-      b.ct(g, "lxde,xyead->aly", 1.0, eri("oovv"), Sz, slice0(permuted(Wvooo, {3, 0, 1, 2}), z));
+      // (the R1 term runs in k_r1_t3 on the same S batch)
+      // S panel [(y,e2,e3)][(x,e1)], shared by three contractions
+      View dX2z = slice0(permuted(dX2, {1, 0, 2, 3}), z);  // dX2[y, z, a, b] over (y, a, b)
+      b.ct(g, "xc,xycab->yab", 0.5, sub(sub(ft, 0, O0, o), 1, V0, v), Sz, dX2z);
+      b.ct(g, "xjc,xycab->yjab", -1.0, slice0(eri("ooov"), z), Sz, dX2)->reuse_B = 1;
+      b.ct(g, "xde,xyeba->ybad", -1.0, slice0(eri("oovv"), z), Sz, permuted(Wvvvo, {3, 1, 0, 2}), 1)->reuse_B = 1;
+      // S panel [(y,e2)][(x,e3,e1)], shared by two contractions
+      b.ct(g, "bxcd,xydac->yab", 1.0, eri("vovv"), Sz, dX2z, 1);
+      b.ct(g, "lxde,xyead->yal", 1.0, eri("oovv"), Sz,
+           permuted(slice0(permuted(Wvooo, {3, 0, 1, 2}), z), {2, 0, 1}))->reuse_B = 1;
     }
   }
 
@@ -1124,6 +1128,12 @@ int do_intermediates(rccsdt_ctx* c) {
     else
       rcc::launch_unpack_spin<double>(c->B("t3")->p, 0, o * o, zb, zp, c->v, c->D("Sz"), c->stream);
     if ((st = run_plans(c, c->p_a3[z]))) return st;
+    if (t3f)
+      rcc::launch_r1_t3<float>(c->B("Sz")->f(), c->D("oovv"), o, c->v, c->D("dR1") + (size_t)z * c->v,
+                               c->splitk->d(), (i64)(c->splitk->bytes / 8), c->stream);
+    else
+      rcc::launch_r1_t3<double>(c->D("Sz"), c->D("oovv"), o, c->v, c->D("dR1") + (size_t)z * c->v, c->splitk->d(),
+                                (i64)(c->splitk->bytes / 8), c->stream);
   }
   c->have_int = 1;
   return check(c, "do_intermediates");

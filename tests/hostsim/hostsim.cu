@@ -223,4 +223,17 @@ void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, con
 template void launch_unpack_spin<double>(const void*, int, int, const i64*, const int*, int, double*, cudaStream_t);
 template void launch_unpack_spin<float>(const void*, int, int, const i64*, const int*, int, float*, cudaStream_t);
 
+template <typename T>
+void launch_r1_t3(const T* S, const double* oovv, int o, int v, double* dR1_z, double*, i64, cudaStream_t) {
+  const i64 nslab = (i64)o * o * v, V2 = (i64)v * v;
+  for (int a = 0; a < v; ++a) {
+    double acc = 0.0;
+    for (i64 s = 0; s < nslab; ++s)
+      for (int c = 0; c < v; ++c)
+        acc += oovv[s * v + c] * ((double)S[s * V2 + (i64)c * v + a] - 0.5 * (double)S[s * V2 + (i64)a * v + c]);
+    dR1_z[a] += acc;
+  }
+}
+template void launch_r1_t3<double>(const double*, const double*, int, int, double*, double*, i64, cudaStream_t);
+template void launch_r1_t3<float>(const float*, const double*, int, int, double*, double*, i64, cudaStream_t);
 }  // namespace rcc

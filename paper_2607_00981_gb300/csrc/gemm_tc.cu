@@ -418,7 +418,7 @@ int num_sms() {
 
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int Kpad,
                    const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s, float* scratch,
-                   long long scratch_elems) {
+                   long long scratch_elems, float* raw_out) {
   if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
   const int esz = kind == PANEL_BF16X2 ? 2 : 4;
   const int bk = ROWB / esz;
@@ -434,7 +434,7 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
   g.splitk = 1;
   const int sms = num_sms();
   const int tiles = g.mt * g.nt;
-  if (tiles < sms && g.kblocks >= 8 && scratch) {
+  if (tiles < sms && g.kblocks >= 8 && scratch && !raw_out) {
     int sk = std::min((2 * sms + tiles - 1) / tiles, g.kblocks / 4);
     while (sk > 1 && (long long)sk * e.M * e.N > scratch_elems) --sk;
     g.splitk = std::max(sk, 1);
@@ -444,7 +444,7 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
   const int ntiles = tiles * g.splitk;
   const int grid = std::min(ntiles, sms);
   const long long budget = watchdog > 0 ? watchdog : 4000000000LL;
-  float* part = g.splitk > 1 ? scratch : nullptr;
+  float* part = raw_out ? raw_out : (g.splitk > 1 ? scratch : nullptr);
   if (kind == PANEL_BF16X2) {
     static bool attr = false;
     if (!attr) {
@@ -462,7 +462,7 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
     ++g_launch_count;
     k_gemm_tc<2><<<grid, kThreads, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, g, e, part, status_flag, budget);
   }
-  if (part) {
+  if (part && !raw_out) {
     const long long MN = (long long)e.M * e.N;
     long long blocks = (MN + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;

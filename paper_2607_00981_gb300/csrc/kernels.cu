@@ -662,4 +662,68 @@ void launch_r1_t3(const T* S, const double* oovv, int o, int v, double* dR1_z, d
 template void launch_r1_t3<double>(const double*, const double*, int, int, double*, double*, i64, cudaStream_t);
 template void launch_r1_t3<float>(const float*, const double*, int, int, double*, double*, i64, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Two-phase scatter of whole v^3 rows: X[m] in natural (a,b,c) order is added to
+// the stored block at row_base[m] with the virtual axes permuted by the sort
+// permutation perm_sel[m].  One CTA moves a 16^3 cube: the cube is read along c
+// (coalesced), staged in shared memory, and added along the target's unit-stride
+// axis (coalesced read-modify-write).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter_rows3(const float* __restrict__ X, int M, int v,
+                                                       const i64* __restrict__ row_base,
+                                                       const int* __restrict__ row_sel,
+                                                       const double* __restrict__ row_alpha, T* __restrict__ C) {
+  constexpr int TL = 16;
+  __shared__ float cube[TL][TL + 1][TL + 2];
+  const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const int nt = (v + TL - 1) / TL;
+  const i64 V3 = (i64)v * v * v;
+  const i64 sv[3] = {(i64)v * v, v, 1};
+  for (int m = blockIdx.y; m < M; m += gridDim.y) {
+    const int* p = P[row_sel[m]];
+    const i64 st[3] = {sv[p[0]], sv[p[1]], sv[p[2]]};
+    const int fast = p[0] == 2 ? 0 : (p[1] == 2 ? 1 : 2);   // label on the target's unit-stride axis
+    const int s1 = (fast + 1) % 3, s2 = (fast + 2) % 3;
+    const i64 base = row_base[m];
+    const T al = (T)row_alpha[m];
+    const float* xm = X + (i64)m * V3;
+    for (int tile = blockIdx.x; tile < nt * nt * nt; tile += gridDim.x) {
+      const int lo[3] = {tile / (nt * nt) * TL, (tile / nt) % nt * TL, tile % nt * TL};
+      __syncthreads();
+      for (int e = threadIdx.x; e < TL * TL * TL; e += blockDim.x) {
+        const int c = e % TL, b = (e / TL) % TL, a = e / (TL * TL);
+        const int ga = lo[0] + a, gb = lo[1] + b, gc = lo[2] + c;
+        cube[a][b][c] = (ga < v && gb < v && gc < v) ? xm[((i64)ga * v + gb) * v + gc] : 0.f;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < TL * TL * TL; e += blockDim.x) {
+        int u[3];
+        u[fast] = e % TL;
+        u[s1] = (e / TL) % TL;
+        u[s2] = e / (TL * TL);
+        const int ga = lo[0] + u[0], gb = lo[1] + u[1], gc = lo[2] + u[2];
+        if (ga < v && gb < v && gc < v) {
+          const i64 off = base + ga * st[0] + gb * st[1] + gc * st[2];
+          C[off] = C[off] + al * (T)cube[u[0]][u[1]][u[2]];
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+void launch_scatter_rows3(const float* X, int M, int v, const i64* row_base, const int* row_sel,
+                          const double* row_alpha, T* C, cudaStream_t s) {
+  const int nt = (v + 15) / 16;
+  unsigned gx = (unsigned)std::min(nt * nt * nt, 1024);
+  unsigned gy = (unsigned)std::min(M, 65535);
+  ++g_launch_count;
+  k_scatter_rows3<T><<<dim3(gx, gy), 256, 0, s>>>(X, M, v, row_base, row_sel, row_alpha, C);
+}
+template void launch_scatter_rows3<float>(const float*, int, int, const i64*, const int*, const double*, float*,
+                                          cudaStream_t);
+template void launch_scatter_rows3<double>(const float*, int, int, const i64*, const int*, const double*, double*,
+                                           cudaStream_t);
+
 }  // namespace rcc

@@ -47,9 +47,17 @@ void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t s);
 // with A [M][Kpad], B [N][Kpad] in two planes each.  kind: PANEL_BF16X2 or PANEL_TF32X2.
 // Returns 0 on success, nonzero if the configuration is unsupported.
 // `scratch` (scratch_elems floats) holds FP32 partial tiles when K is split.
+// With raw_out, the raw FP32 result is written densely to raw_out[m * N + n] (no
+// alpha, no scatter, no split-K) for a separate scatter pass.
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo,
                    int Kpad, const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s,
-                   float* scratch, long long scratch_elems);
+                   float* scratch, long long scratch_elems, float* raw_out = nullptr);
+// Second phase of a two-phase scatter: for each row m of the dense FP32 result X
+// [M][v^3] (natural (a,b,c) order), C[row_base[m] + perm_sel[m](a,b,c)] +=
+// row_alpha[m] * X[m][abc]; perm_sel indexes the 6 virtual permutations.
+template <typename T>
+void launch_scatter_rows3(const float* X, int M, int v, const i64* row_base, const int* row_sel,
+                          const double* row_alpha, T* C, cudaStream_t s);
 
 }  // namespace rcc
 

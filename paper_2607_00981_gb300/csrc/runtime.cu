@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <array>
 #include <map>
 #include <memory>
 #include <string>
@@ -166,6 +167,11 @@ struct GemmPlan {
   int step = 0;         // timing bucket
   int reuse_A = 0;      // the A panel packed by the previous plan of the group is still valid
   int reuse_B = 0;      // likewise for the B panel
+  // Two-phase scatter on the tensor cores: the GEMM result X [M][N] is written
+  // densely; consecutive groups of M / s3_rows rows form one v^3 block of X whose
+  // axes map to stored axes by s3_sel, added to C[s3_base] with weight s3_alpha.
+  int s3_rows = 0;
+  std::unique_ptr<DBuf> s3_base, s3_sel, s3_alpha;
 };
 
 struct rccsdt_ctx {
@@ -211,7 +217,7 @@ struct rccsdt_ctx {
   std::unique_ptr<DBuf> hist_t, hist_e;     // M slots each: t1 | t2 | t3 (padded)
   i64 hist_stride = 0;                      // bytes per slot
   i64 seg1 = 0, seg2 = 0, seg3 = 0;         // element counts
-  std::unique_ptr<DBuf> scalars, partial, splitk;
+  std::unique_ptr<DBuf> scalars, partial, splitk, rawX;
 
   DBuf* B(const std::string& k) { return buf.at(k).get(); }
   double* D(const std::string& k) { return buf.at(k)->d(); }
@@ -299,6 +305,10 @@ void make_epi(rccsdt_ctx* c, EpiPlan& E, void* C, int c_f32, int M, int N,
   e.row_alpha = (const double*)E.row_alpha->p;
   e.col_off = shared_col_off ? shared_col_off : (const i64*)E.col_off->p;
 }
+
+// Block-row tables of the two-phase scatter; xaxes[r] = stored axis of each X axis.
+void set_two_phase(rccsdt_ctx* c, GemmPlan* g, const std::vector<i64>& base, const std::vector<std::array<int, 3>>& xaxes,
+                   const std::vector<double>& alpha, int* err);
 
 void finish_plan(rccsdt_ctx* c, GemmPlan* g, int K) {
   g->K = K;
@@ -506,10 +516,21 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
                          g->E.e, c->splitk->d(), (i64)(c->splitk->bytes / 8), c->stream);
   } else {
     int* flag = (int*)((double*)c->scalars->p + 1000);
+    float* raw = g->s3_rows > 0 && c->rawX ? (float*)c->rawX->p : nullptr;
     if (rcc::launch_gemm_tc(kind, pa.out_hi, pa.out_lo, pb.out_hi, pb.out_lo, g->Kpad, g->E.e, flag,
                             c->opt.watchdog_cycles, c->stream, (float*)c->splitk->p,
-                            (long long)(c->splitk->bytes / 4)))
+                            (long long)(c->splitk->bytes / 4), raw))
       return fail(c, RCCSDT_ERR_ARG, "tensor-core GEMM configuration unsupported");
+    if (raw) {
+      const rcc::EpiArgs& e = g->E.e;
+      const i64* sb = (const i64*)g->s3_base->p;
+      const int* ss = (const int*)g->s3_sel->p;
+      const double* sa = (const double*)g->s3_alpha->p;
+      if (e.c_f32)
+        rcc::launch_scatter_rows3<float>(raw, g->s3_rows, c->v, sb, ss, sa, (float*)e.C, c->stream);
+      else
+        rcc::launch_scatter_rows3<double>(raw, g->s3_rows, c->v, sb, ss, sa, (double*)e.C, c->stream);
+    }
   }
   timer_end(c, tidx);
 #ifndef RCC_HOSTSIM
@@ -552,6 +573,19 @@ int perm_id(const int pos[3]) {
   for (int q = 0; q < 6; ++q)
     if (P[q][0] == pos[0] && P[q][1] == pos[1] && P[q][2] == pos[2]) return q;
   return 0;
+}
+
+}  // namespace
+
+namespace {
+void set_two_phase(rccsdt_ctx* c, GemmPlan* g, const std::vector<i64>& base, const std::vector<std::array<int, 3>>& xaxes,
+                   const std::vector<double>& alpha, int* err) {
+  std::vector<int> sel(xaxes.size());
+  for (size_t r = 0; r < xaxes.size(); ++r) sel[r] = perm_id(xaxes[r].data());
+  g->s3_base = upload_vec(c, base, err);
+  g->s3_sel = upload_vec(c, sel, err);
+  g->s3_alpha = upload_vec(c, alpha, err);
+  g->s3_rows = (int)base.size();
 }
 
 struct TripleInfo {
@@ -895,6 +929,14 @@ int build_context(rccsdt_ctx* c) {
       make_epi(c, g->E, r3p, t3f, M, (int)V3, ebase, esel, ealpha, {}, &err, b.RT3);
       g->big = 1;
       g->step = 3;
+      {
+        std::vector<std::array<int, 3>> ax(M);
+        for (int q = 0; q < M; ++q) {
+          TripleInfo ti = triple(pairs[q].first, pairs[q].second, k);
+          ax[q] = {ti.pos[0], ti.pos[1], ti.pos[2]};                       // X block [a][b][c]
+        }
+        set_two_phase(c, g, ebase, ax, ealpha, &err);
+      }
       finish_plan(c, g, K);
       c->p_hh.push_back(g);
     }
@@ -939,6 +981,18 @@ int build_context(rccsdt_ctx* c) {
         make_epi(c, g->E, r3p, t3f, M, (int)V2, ebase, esel, ealpha, {}, &err, b.RT2);
         g->big = 1;
         g->step = 2;
+        {
+          std::vector<i64> tb(o);
+          std::vector<std::array<int, 3>> ax(o);
+          std::vector<double> ta(o);
+          for (int i = 0; i < o; ++i) {
+            TripleInfo ti = triple(i, j, k);
+            tb[i] = ti.blk * V3;
+            ax[i] = {ti.pos[0], ti.pos[1], ti.pos[2]};                        // X block [a][b][c]
+            ta[i] = (6.0 / ti.m) * (j < k ? 2.0 : 1.0);
+          }
+          set_two_phase(c, g, tb, ax, ta, &err);
+        }
         finish_plan(c, g, K);
         c->p_ringab.push_back(g);
       }
@@ -976,6 +1030,18 @@ int build_context(rccsdt_ctx* c) {
         make_epi(c, g->E, r3p, t3f, M, (int)V2, ebase, esel, ealpha, {}, &err, b.RT2);
         g->big = 1;
         g->step = 2;
+        {
+          std::vector<i64> tb(o);
+          std::vector<std::array<int, 3>> ax(o);
+          std::vector<double> ta(o);
+          for (int i = 0; i < o; ++i) {
+            TripleInfo ti = triple(i, j, k);
+            tb[i] = ti.blk * V3;
+            ax[i] = {ti.pos[1], ti.pos[0], ti.pos[2]};                        // X block [b][a][c]
+            ta[i] = 6.0 / ti.m;
+          }
+          set_two_phase(c, g, tb, ax, ta, &err);
+        }
         finish_plan(c, g, K);
         c->p_ringc.push_back(g);
       }
@@ -1013,6 +1079,19 @@ int build_context(rccsdt_ctx* c) {
       make_epi(c, g->E, r3p, t3f, M, (int)V2, ebase, esel, ealpha, {}, &err, b.RT2);
       g->big = 1;
       g->step = 4;
+      {
+        const int np = (int)pairs.size();
+        std::vector<i64> tb(np);
+        std::vector<std::array<int, 3>> ax(np);
+        std::vector<double> ta(np);
+        for (int q = 0; q < np; ++q) {
+          TripleInfo ti = triple(pairs[q].first, j, pairs[q].second);
+          tb[q] = ti.blk * V3;
+          ax[q] = {ti.pos[2], ti.pos[0], ti.pos[1]};                          // X block [c][a][b]
+          ta[q] = 6.0 / ti.m;
+        }
+        set_two_phase(c, g, tb, ax, ta, &err);
+      }
       finish_plan(c, g, K);
       c->p_t2a.push_back(g);
     }
@@ -1056,6 +1135,21 @@ int build_context(rccsdt_ctx* c) {
         make_epi(c, g->E, r3p, t3f, M, v, ebase, esel, ealpha, {}, &err, RT1);
         g->big = 1;
         g->step = 4;
+        {
+          std::vector<i64> tb(o);
+          std::vector<std::array<int, 3>> ax(o);
+          std::vector<double> ta(o);
+          for (int k = 0; k < o; ++k) {
+            TripleInfo ti = triple(i, j, k);
+            tb[k] = ti.blk * V3;
+            if (ti.pos[1] == 2)
+              ax[k] = {ti.pos[2], ti.pos[1], ti.pos[0]};                      // X block [c][b][a]
+            else
+              ax[k] = {ti.pos[1], ti.pos[2], ti.pos[0]};                      // X block [b][c][a]
+            ta[k] = -6.0 / ti.m;
+          }
+          set_two_phase(c, g, tb, ax, ta, &err);
+        }
         finish_plan(c, g, K);
         c->p_t2b.push_back(g);
       }
@@ -1361,6 +1455,16 @@ RCC_API int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, voi
       c->panelA_lo->p = dev_alloc(c->panel_bytes / 2, &err);
       c->panelB_lo->p = dev_alloc(c->panel_bytes / 2, &err);
       c->total_bytes += c->panel_bytes;
+    }
+    // dense FP32 result of the hh-ladder GEMM for its two-phase scatter (split modes)
+    if (op.precision != RCCSDT_FP64) {
+      c->rawX = std::make_unique<DBuf>();
+      size_t mx = 0;
+      for (auto& g : c->plans)
+        if (g->s3_rows > 0) mx = std::max(mx, (size_t)g->E.e.M * g->E.e.N);
+      c->rawX->bytes = mx * 4;
+      c->rawX->p = dev_alloc(c->rawX->bytes, &err);
+      c->total_bytes += c->rawX->bytes;
     }
     // DIIS history
     c->seg1 = (i64)o * v;

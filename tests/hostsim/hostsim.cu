@@ -35,7 +35,7 @@ void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, 
 // Split-precision product hi*hi + hi*lo + lo*hi with float products and a float
 // accumulator (the order of the tensor-core sum is not modelled).
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int Kpad,
-                   const EpiArgs& e, int*, long long, cudaStream_t, float*, long long) {
+                   const EpiArgs& e, int*, long long, cudaStream_t, float*, long long, float* raw_out) {
   auto get = [&](const void* p, i64 i) -> float {
     if (kind == PANEL_BF16X2) return __bfloat162float(((const __nv_bfloat16*)p)[i]);
     return ((const float*)p)[i];
@@ -48,7 +48,10 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
         const float ah = get(Ahi, ia), al = get(Alo, ia), bh = get(Bhi, ib), bl = get(Blo, ib);
         s += ah * bh + ah * bl + al * bh;
       }
-      epi_apply(e, m, n, (double)s);
+      if (raw_out)
+        raw_out[(i64)m * e.N + n] = s;
+      else
+        epi_apply(e, m, n, (double)s);
     }
   return 0;
 }
@@ -236,4 +239,21 @@ void launch_r1_t3(const T* S, const double* oovv, int o, int v, double* dR1_z, d
 }
 template void launch_r1_t3<double>(const double*, const double*, int, int, double*, double*, i64, cudaStream_t);
 template void launch_r1_t3<float>(const float*, const double*, int, int, double*, double*, i64, cudaStream_t);
+template <typename T>
+void launch_scatter_rows3(const float* X, int M, int v, const i64* row_base, const int* row_sel,
+                          const double* row_alpha, T* C, cudaStream_t) {
+  const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const i64 V3 = (i64)v * v * v, S[3] = {(i64)v * v, v, 1};
+  for (int m = 0; m < M; ++m) {
+    const int* p = P[row_sel[m]];
+    for (i64 e = 0; e < V3; ++e) {
+      const int a = (int)(e / ((i64)v * v)), b = (int)((e / v) % v), c = (int)(e % v);
+      C[row_base[m] + a * S[p[0]] + b * S[p[1]] + c * S[p[2]]] += (T)(row_alpha[m] * (double)X[(i64)m * V3 + e]);
+    }
+  }
+}
+template void launch_scatter_rows3<float>(const float*, int, int, const i64*, const int*, const double*, float*,
+                                          cudaStream_t);
+template void launch_scatter_rows3<double>(const float*, int, int, const i64*, const int*, const double*, double*,
+                                           cudaStream_t);
 }  // namespace rcc

@@ -140,6 +140,21 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The slowest rank's value (all ranks get it); identity without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def per_iteration(seconds_max: float, steps: int, world: int) -> float:
+    """Whole-job seconds per iteration: N replicas each ran `steps` iterations."""
+    return seconds_max / (steps * world)
+
+
 def config(args, inst):
     return {"workload": f"{args.workload}: RCCSDT iteration, o={inst.o} v={inst.v} naux={inst.naux}, "
                         f"compact T3 {inst.o * (inst.o + 1) * (inst.o + 2) // 6} x {inst.v}^3, seed {inst.seed}",
@@ -224,11 +239,8 @@ def run_ours(args, rank, world):
     ms_total = e0.elapsed_time(e1)
     st = ctx.step_times()
     ctx.enable_timing(False)
-    t_max = torch.tensor([ms_total], device=f"cuda:{dev}", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_total = float(t_max.item())
-    s_per_iter = ms_total / 1e3 / (args.steps * world)
+    ms_total = max_over_ranks(ms_total, dist, f"cuda:{dev}")
+    s_per_iter = per_iteration(ms_total / 1e3, args.steps, world)
     fma = lib.rccsdt_iteration_fma(o, v)
 
     # --- end to end through the C ABI with pinned host buffers
@@ -250,11 +262,8 @@ def run_ours(args, rank, world):
             ctx.iterate()
             ctx.get_amplitudes(ht1, ht2, ht3)
         barrier()
-        dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], device=f"cuda:{dev}", dtype=torch.float64)
-        if dist:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": float(tt.item()) / (ksteps * world), "unit": "s/iteration",
+        dt = max_over_ranks(time.perf_counter() - t0, dist, f"cuda:{dev}")
+        e2e = {"value": per_iteration(dt, ksteps, world), "unit": "s/iteration",
                "h2d_bytes_per_step": int(bytes_in), "d2h_bytes_per_step": int(bytes_out),
                "steps": ksteps, "note": "set_hamiltonian + set_amplitudes from pinned host memory, "
                                         "rccsdt_iterate, get_amplitudes to host; DIIS history restarts each step"}

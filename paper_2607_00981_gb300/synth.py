@@ -63,8 +63,19 @@ WORKLOADS = {
 }
 
 
+# Weakly coupled instances for runs that must converge.  With the per-entry scale
+# fixed at 0.3 the ERIs grow with the rank and the iteration stalls or diverges at
+# these sizes; here the scale is 0.6 * 0.3 * sqrt(40 / naux) (rank-normalised,
+# then reduced).
+CONVERGENCE = {
+    "o6v48w": dict(o=6, v=48, naux=216, seed=7, scale=0.6 * 0.3 * (40 / 216) ** 0.5),
+    "o8v80w": dict(o=8, v=80, naux=320, seed=0, scale=0.6 * 0.3 * (40 / 320) ** 0.5),
+}
+
+
 def workload(name: str) -> Instance:
-    return make_instance(**WORKLOADS[name])
+    spec = WORKLOADS.get(name) or CONVERGENCE[name]
+    return make_instance(**spec)
 
 
 def batch_shapes(count: int = 64, seed: int = 0):

@@ -726,4 +726,86 @@ template void launch_scatter_rows3<float>(const float*, int, int, const i64*, co
 template void launch_scatter_rows3<double>(const float*, int, int, const i64*, const int*, const double*, double*,
                                            cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// T2-driven term of Eq. resi-rccsdt with K = o, output-stationary:
+//   r_{ijk}^{abc} += sum over the six column permutations of
+//                    -sum_l W^{a1 l}_{i1 i2} t_{l i3}^{a2 a3}
+// One CTA owns a 16^3 tile of one stored block and accumulates all six terms in
+// registers; per term the W slice [a1][l] and the t2 slice [l][a2][a3] of the
+// tile are staged in shared memory (l in chunks of 16).  Each thread holds a
+// fixed (b, c) and 16 values of a; the block is written once, along c.
+// Wvooo[a][l][i][j] = W^{al}_{ij}; t2[l][k][b][c] = t_lk^bc (T precision copies).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_t2_outer(T* __restrict__ r3, const T* __restrict__ Wvooo,
+                                                  const T* __restrict__ t2, const int4* __restrict__ blocks, int o,
+                                                  int v, i64 n3) {
+  constexpr int TL = 16, LC = 16;
+  __shared__ T Ws[TL][LC + 1];
+  __shared__ T Ts[LC][TL][TL + 1];
+  const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const int nt = (v + TL - 1) / TL;
+  const i64 V3 = (i64)v * v * v;
+  const int tc = threadIdx.x % TL, tb = threadIdx.x / TL;
+  for (i64 blk = blockIdx.y; blk < n3; blk += gridDim.y) {
+    const int4 ijk = blocks[blk];
+    const int occ[3] = {ijk.x, ijk.y, ijk.z};
+    for (int tile = blockIdx.x; tile < nt * nt * nt; tile += gridDim.x) {
+      const int lo[3] = {tile / (nt * nt) * TL, (tile / nt) % nt * TL, tile % nt * TL};
+      T acc[TL];
+#pragma unroll
+      for (int a = 0; a < TL; ++a) acc[a] = (T)0;
+      for (int q = 0; q < 6; ++q) {
+        // roles: position P[q][0] -> (i1, a1), P[q][1] -> (i2, a2), P[q][2] -> (i3, a3)
+        const int x1 = P[q][0], x2 = P[q][1], x3 = P[q][2];
+        const int i1 = occ[x1], i2 = occ[x2], i3 = occ[x3];
+        for (int l0 = 0; l0 < o; l0 += LC) {
+          const int lc = min(LC, o - l0);
+          __syncthreads();
+          for (int e = threadIdx.x; e < TL * LC; e += blockDim.x) {
+            const int u = e / LC, l = e % LC, ga = lo[x1] + u;
+            Ws[u][l] = (l < lc && ga < v) ? Wvooo[(((i64)ga * o + l0 + l) * o + i1) * o + i2] : (T)0;
+          }
+          for (int e = threadIdx.x; e < LC * TL * TL; e += blockDim.x) {
+            const int l = e / (TL * TL), u2 = (e / TL) % TL, u3 = e % TL;
+            const int g2 = lo[x2] + u2, g3 = lo[x3] + u3;
+            Ts[l][u2][u3] = (l < lc && g2 < v && g3 < v) ? t2[(((i64)(l0 + l) * o + i3) * v + g2) * v + g3] : (T)0;
+          }
+          __syncthreads();
+#pragma unroll
+          for (int a = 0; a < TL; ++a) {
+            const int loc[3] = {a, tb, tc};
+            const int u1 = loc[x1], u2 = loc[x2], u3 = loc[x3];
+            T s = (T)0;
+            for (int l = 0; l < lc; ++l) s += Ws[u1][l] * Ts[l][u2][u3];
+            acc[a] -= s;
+          }
+        }
+      }
+      const int gb = lo[1] + tb, gc = lo[2] + tc;
+      if (gb < v && gc < v) {
+#pragma unroll
+        for (int a = 0; a < TL; ++a) {
+          const int ga = lo[0] + a;
+          if (ga < v) {
+            const i64 off = blk * V3 + ((i64)ga * v + gb) * v + gc;
+            r3[off] = r3[off] + acc[a];
+          }
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+void launch_t2_outer(T* r3, const T* Wvooo, const T* t2, const int4* blocks, int o, int v, i64 n3, cudaStream_t s) {
+  const int nt = (v + 15) / 16;
+  const unsigned gx = (unsigned)std::min(nt * nt * nt, 65535);
+  const unsigned gy = (unsigned)std::min<i64>(n3, 65535);
+  ++g_launch_count;
+  k_t2_outer<T><<<dim3(gx, gy), 256, 0, s>>>(r3, Wvooo, t2, blocks, o, v, n3);
+}
+template void launch_t2_outer<double>(double*, const double*, const double*, const int4*, int, int, i64, cudaStream_t);
+template void launch_t2_outer<float>(float*, const float*, const float*, const int4*, int, int, i64, cudaStream_t);
+
 }  // namespace rcc

@@ -76,4 +76,8 @@ void launch_unpack_spin(const void* t3, int f32, int ntrip, const i64* base, con
 template <typename T>
 void launch_r1_t3(const T* S, const double* oovv, int o, int v, double* dR1_z, double* scratch, i64 scratch_elems,
                   cudaStream_t s);
+// T2-driven R3 term with K = o, all six column permutations, output-stationary
+// (Wvooo[a][l][i][j], t2[l][k][b][c] in the precision T of R3).
+template <typename T>
+void launch_t2_outer(T* r3, const T* Wvooo, const T* t2, const int4* blocks, int o, int v, i64 n3, cudaStream_t s);
 }  // namespace rcc

@@ -203,7 +203,7 @@ struct rccsdt_ctx {
   // plan groups
   std::vector<GemmPlan*> p_dress, p_fock, p_eri, p_int, p_r12, p_energy_bare;
   std::vector<std::vector<GemmPlan*>> p_a3;  // per z
-  std::vector<GemmPlan*> p_pp, p_hh, p_ringab, p_ringc, p_t2a, p_t2b;
+  std::vector<GemmPlan*> p_pp, p_hh, p_ringab, p_ringc, p_t2a;
   // combines
   std::vector<rcc::CombineArgs> c_fock, c_helpers, c_int_base, c_r12_base, c_r2_sym, c_wt;
   rcc::CombineArgs c_Lt_copy{}, c_ft_copy{};
@@ -1096,64 +1096,12 @@ int build_context(rccsdt_ctx* c) {
       c->p_t2a.push_back(g);
     }
 
-  // --- T2-driven term -sum_l W^{al}_{ij} t_lk^{bc}: unit (i,j) over all ordered pairs;
-  //     rows (k,b,c), cols a, K = l.  Trips (i,j,k) of one unit are distinct multisets.
-  {
-    std::vector<i64> rt1((size_t)3 * v);
-    for (int p = 0; p < 3; ++p)
-      for (int a = 0; a < v; ++a) rt1[(size_t)p * v + a] = a * b.S[p];
-    c->buf["RT1"] = upload_vec(c, rt1, &err);
-    const i64* RT1 = (const i64*)c->buf["RT1"]->p;
-    const int M = o * (int)V2, K = o;
-    std::vector<i64> acol(K);
-    for (int l = 0; l < o; ++l) acol[l] = (i64)l * o * V2;                   // t2[l][k][b][c]
-    for (int i = 0; i < o; ++i)
-      for (int j = 0; j < o; ++j) {
-        GemmPlan* g = b.new_plan();
-        std::vector<i64> arow(M), brow(v), bcol(K), ebase(M);
-        std::vector<int> esel(M);
-        std::vector<double> ealpha(M);
-        for (int a = 0; a < v; ++a) brow[a] = (i64)a * o * o * o;             // Wvooo[a][l][i][j]
-        for (int l = 0; l < o; ++l) bcol[l] = (i64)l * o * o + (i64)i * o + j;
-        for (int k = 0; k < o; ++k) {
-          TripleInfo ti = triple(i, j, k);
-          // enumerate (b, c) so that consecutive rows hit the stored unit-stride axis
-          // when b or c lands there (coalesced scatter); otherwise c fastest
-          const bool b_fast = ti.pos[1] == 2;
-          for (i64 q = 0; q < V2; ++q) {
-            const i64 bb = b_fast ? q % v : q / v, cc = b_fast ? q / v : q % v, r = k * V2 + q;
-            arow[r] = (i64)k * V2 + bb * v + cc;
-            ebase[r] = ti.blk * V3 + bb * b.S[ti.pos[1]] + cc * b.S[ti.pos[2]];
-            esel[r] = ti.pos[0];
-            ealpha[r] = -6.0 / ti.m;
-          }
-        }
-        make_pack(c, g->A, c->D("t2"), 0, M, K, 1, std::vector<double>(K, 1.0), acol, std::vector<int>(K, 0), arow, 0,
-                  &err);
-        make_pack(c, g->B, c->D("Wvooo"), 0, v, K, 1, std::vector<double>(K, 1.0), bcol, std::vector<int>(K, 0), brow,
-                  0, &err);
-        make_epi(c, g->E, r3p, t3f, M, v, ebase, esel, ealpha, {}, &err, RT1);
-        g->big = 1;
-        g->step = 4;
-        {
-          std::vector<i64> tb(o);
-          std::vector<std::array<int, 3>> ax(o);
-          std::vector<double> ta(o);
-          for (int k = 0; k < o; ++k) {
-            TripleInfo ti = triple(i, j, k);
-            tb[k] = ti.blk * V3;
-            if (ti.pos[1] == 2)
-              ax[k] = {ti.pos[2], ti.pos[1], ti.pos[0]};                      // X block [c][b][a]
-            else
-              ax[k] = {ti.pos[1], ti.pos[2], ti.pos[0]};                      // X block [b][c][a]
-            ta[k] = -6.0 / ti.m;
-          }
-          set_two_phase(c, g, tb, ax, ta, &err);
-        }
-        finish_plan(c, g, K);
-        c->p_t2b.push_back(g);
-      }
+  // (the T2-driven term -sum_l W^{al}_{ij} t_lk^{bc} runs output-stationary in k_t2_outer)
+  if (t3f) {
+    b.mk("t2_f", (size_t)o * o * V2, 4);
+    b.mk("Wvooo_f", (size_t)v * o * o * o, 4);
   }
+
   // the A panel is shared by consecutive plans of these groups
   for (auto* grp : {&c->p_pp, &c->p_hh, &c->p_ringab, &c->p_ringc})
     for (size_t q = 1; q < grp->size(); ++q) (*grp)[q]->reuse_A = 1;
@@ -1259,7 +1207,16 @@ int do_residual(rccsdt_ctx* c) {
   {
     StepTimer tm(c, 4);
     if ((st = run_plans(c, c->p_t2a))) return st;
-    if ((st = run_plans(c, c->p_t2b))) return st;
+    const int4* blk = (const int4*)c->blocks_info->p;
+    if (c->opt.precision != RCCSDT_FP64) {
+      rcc::launch_convert<float, double>(c->B("t2_f")->f(), c->D("t2"), (i64)c->o * c->o * c->v * c->v, c->stream);
+      rcc::launch_convert<float, double>(c->B("Wvooo_f")->f(), c->D("Wvooo"), (i64)c->v * c->o * c->o * c->o,
+                                         c->stream);
+      rcc::launch_t2_outer<float>(c->B("r3")->f(), c->B("Wvooo_f")->f(), c->B("t2_f")->f(), blk, c->o, c->v, c->n3,
+                                  c->stream);
+    } else {
+      rcc::launch_t2_outer<double>(c->D("r3"), c->D("Wvooo"), c->D("t2"), blk, c->o, c->v, c->n3, c->stream);
+    }
   }
   c->have_res = 1;
   return check(c, "do_residual");

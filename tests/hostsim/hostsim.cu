@@ -256,4 +256,25 @@ template void launch_scatter_rows3<float>(const float*, int, int, const i64*, co
                                           cudaStream_t);
 template void launch_scatter_rows3<double>(const float*, int, int, const i64*, const int*, const double*, double*,
                                            cudaStream_t);
+template <typename T>
+void launch_t2_outer(T* r3, const T* Wvooo, const T* t2, const int4* blocks, int o, int v, i64 n3, cudaStream_t) {
+  const i64 V3 = (i64)v * v * v;
+  const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  for (i64 b = 0; b < n3; ++b) {
+    const int occ[3] = {blocks[b].x, blocks[b].y, blocks[b].z};
+    for (i64 x = 0; x < V3; ++x) {
+      const int lab[3] = {(int)(x / ((i64)v * v)), (int)((x / v) % v), (int)(x % v)};
+      double s = 0.0;
+      for (int q = 0; q < 6; ++q) {
+        const int i1 = occ[P[q][0]], i2 = occ[P[q][1]], i3 = occ[P[q][2]];
+        const int a1 = lab[P[q][0]], a2 = lab[P[q][1]], a3 = lab[P[q][2]];
+        for (int l = 0; l < o; ++l)
+          s -= (double)Wvooo[(((i64)a1 * o + l) * o + i1) * o + i2] * (double)t2[(((i64)l * o + i3) * v + a2) * v + a3];
+      }
+      r3[b * V3 + x] = (T)((double)r3[b * V3 + x] + s);
+    }
+  }
+}
+template void launch_t2_outer<double>(double*, const double*, const double*, const int4*, int, int, i64, cudaStream_t);
+template void launch_t2_outer<float>(float*, const float*, const float*, const int4*, int, int, i64, cudaStream_t);
 }  // namespace rcc

@@ -232,24 +232,25 @@ template <typename T>
 __global__ void k_post(const T* __restrict__ r, T* __restrict__ rp, const int4* __restrict__ blocks,
                        int v, i64 n3) {
   const i64 V3 = (i64)v * v * v;
+  // blockIdx.x runs over (a, b) rows of the block, threads over c: 32-bit index math
   for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
     const int4 ijk = blocks[b];
     const T* rb = r + b * V3;
-    for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < V3; e += (i64)gridDim.x * blockDim.x) {
-      const int c = (int)(e % v), bb = (int)((e / v) % v), a = (int)(e / ((i64)v * v));
-      rp[b * V3 + e] = post_value<T>(rb, v, ijk.x, ijk.y, ijk.z, a, bb, c);
+    T* out = rp + b * V3;
+    for (int ab = blockIdx.x; ab < v * v; ab += gridDim.x) {
+      const int a = ab / v, bb = ab - a * v;
+      for (int c = threadIdx.x; c < v; c += blockDim.x)
+        out[ab * v + c] = post_value<T>(rb, v, ijk.x, ijk.y, ijk.z, a, bb, c);
     }
   }
 }
 
 template <typename T>
 void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStream_t s) {
-  const i64 V3 = (i64)v * v * v;
-  unsigned gx = (unsigned)((V3 + 255) / 256);
-  if (gx > 64) gx = 64;
-  unsigned gy = (unsigned)(n3 < 1024 ? n3 : 1024);
+  unsigned gx = (unsigned)std::min(v * v, 1024);
+  unsigned gy = (unsigned)(n3 < 65535 ? n3 : 65535);
   ++g_launch_count;
-  k_post<T><<<dim3(gx, gy), 256, 0, s>>>(r, rp, blocks, v, n3);
+  k_post<T><<<dim3(gx, gy), v < 256 ? (v + 31) / 32 * 32 : 256, 0, s>>>(r, rp, blocks, v, n3);
 }
 template void launch_post<double>(const double*, double*, const int4*, int, i64, cudaStream_t);
 template void launch_post<float>(const float*, float*, const int4*, int, i64, cudaStream_t);
@@ -282,11 +283,15 @@ __global__ void k_update_t3(T* t3, const T* rp3, const double* e, const int4* bl
   for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
     const int4 ijk = blocks[b];
     const double eo = e[ijk.x] + e[ijk.y] + e[ijk.z];
-    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < V3; x += (i64)gridDim.x * blockDim.x) {
-      const int c = (int)(x % v), bb = (int)((x / v) % v), a = (int)(x / ((i64)v * v));
-      const T d = (T)(eo - e[o + a] - e[o + bb] - e[o + c] - shift);
-      const i64 g = b * V3 + x;
-      t3[g] = t3[g] + rp3[g] / d;
+    T* tb = t3 + b * V3;
+    const T* rb = rp3 + b * V3;
+    for (int ab = blockIdx.x; ab < v * v; ab += gridDim.x) {
+      const int a = ab / v, bb = ab - a * v;
+      const double eab = eo - e[o + a] - e[o + bb] - shift;
+      for (int c = threadIdx.x; c < v; c += blockDim.x) {
+        const T d = (T)(eab - e[o + c]);
+        tb[ab * v + c] = tb[ab * v + c] + rb[ab * v + c] / d;
+      }
     }
   }
 }
@@ -305,12 +310,10 @@ void launch_update_t12(double* t1, const double* r1, double* t2, const double* r
 template <typename T>
 void launch_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, int o, int v, i64 n3,
                       double shift, cudaStream_t s) {
-  const i64 V3 = (i64)v * v * v;
-  unsigned gx = (unsigned)((V3 + 255) / 256);
-  if (gx > 64) gx = 64;
-  unsigned gy = (unsigned)(n3 < 1024 ? n3 : 1024);
+  unsigned gx = (unsigned)std::min(v * v, 1024);
+  unsigned gy = (unsigned)(n3 < 65535 ? n3 : 65535);
   ++g_launch_count;
-  k_update_t3<T><<<dim3(gx, gy), 256, 0, s>>>(t3, rp3, e, blocks, o, v, n3, shift);
+  k_update_t3<T><<<dim3(gx, gy), v < 256 ? (v + 31) / 32 * 32 : 256, 0, s>>>(t3, rp3, e, blocks, o, v, n3, shift);
 }
 template void launch_update_t3<double>(double*, const double*, const double*, const int4*, int, int,
                                        i64, double, cudaStream_t);
@@ -344,11 +347,19 @@ __device__ __forceinline__ double block_sum(double x) {
 template <typename T>
 __global__ void k_wdot(const T* __restrict__ x, const T* __restrict__ y, i64 n, i64 seg,
                        const double* __restrict__ w, double* __restrict__ partial) {
+  // grid-stride over segments (weight per segment), threads within a segment
   double s = 0.0;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
-    double p = (double)x[i] * (double)y[i];
-    if (w) p *= w[i / seg];
-    s += p;
+  if (w) {
+    const i64 nseg = (n + seg - 1) / seg;
+    for (i64 sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
+      const i64 b0 = sgi * seg, b1 = b0 + seg < n ? b0 + seg : n;
+      double ss = 0.0;
+      for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) ss += (double)x[i] * (double)y[i];
+      s += w[sgi] * ss;
+    }
+  } else {
+    for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+      s += (double)x[i] * (double)y[i];
   }
   s = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -772,13 +783,27 @@ __global__ void __launch_bounds__(256) k_t2_outer(T* __restrict__ r3, const T* _
             Ts[l][u2][u3] = (l < lc && g2 < v && g3 < v) ? t2[(((i64)(l0 + l) * o + i3) * v + g2) * v + g3] : (T)0;
           }
           __syncthreads();
+          // the thread's fixed (b, c) sit on two of the three roles; a runs over the third
+          if (x1 == 0) {  // a = a1: W varies with a, the t2 value is fixed per l
+            const int u2 = x2 == 1 ? tb : tc, u3 = x3 == 1 ? tb : tc;
+            for (int l = 0; l < lc; ++l) {
+              const T tv = Ts[l][u2][u3];
 #pragma unroll
-          for (int a = 0; a < TL; ++a) {
-            const int loc[3] = {a, tb, tc};
-            const int u1 = loc[x1], u2 = loc[x2], u3 = loc[x3];
-            T s = (T)0;
-            for (int l = 0; l < lc; ++l) s += Ws[u1][l] * Ts[l][u2][u3];
-            acc[a] -= s;
+              for (int a = 0; a < TL; ++a) acc[a] -= Ws[a][l] * tv;
+            }
+          } else {  // a = a2 or a3: W fixed per l, t2 varies with a
+            const int u1 = x1 == 1 ? tb : tc;
+            const int other = (x2 == 0) ? (x3 == 1 ? tb : tc) : (x2 == 1 ? tb : tc);
+            for (int l = 0; l < lc; ++l) {
+              const T wv = Ws[u1][l];
+              if (x2 == 0) {
+#pragma unroll
+                for (int a = 0; a < TL; ++a) acc[a] -= wv * Ts[l][a][other];
+              } else {
+#pragma unroll
+                for (int a = 0; a < TL; ++a) acc[a] -= wv * Ts[l][other][a];
+              }
+            }
           }
         }
       }

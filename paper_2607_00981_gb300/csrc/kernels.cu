@@ -387,12 +387,146 @@ template void launch_wdot<float>(const float*, const float*, i64, i64, const dou
                                  double, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// DIIS: B is (M+1) x (M+1) row-major in scalars; solve the bordered system with
-// partial-pivoting Gaussian elimination; a pivot below tiny * max|B| drops that
-// direction (coefficient 0), the least-squares limit for a singular B.
+// DIIS (Sec. III.A.4) with its bookkeeping on the device, so one iteration is a
+// fixed sequence of launches (capturable in a CUDA graph).  State st[8]:
+//   st[0] updates done, st[1] history entries written, st[2] slot of the current
+//   update, st[3] entries in use after it, st[4] 1 if this update extrapolates.
+// History slot q of a segment starts at base + q * stride + off (bytes).
 // ---------------------------------------------------------------------------
-__global__ void k_diis_solve(const double* __restrict__ Bmat, int m, int ld, double* __restrict__ coef) {
+__global__ void k_diis_begin(int* st, int M, int diis_start) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int iter = st[0] + 1, count = st[1];
+  st[0] = iter;
+  st[2] = count % M;
+  st[1] = count + 1;
+  st[3] = count + 1 < M ? count + 1 : M;
+  st[4] = (iter >= diis_start && st[3] >= 2) ? 1 : 0;
+}
+
+void launch_diis_begin(int* st, int M, int diis_start, cudaStream_t s) {
+  ++g_launch_count;
+  k_diis_begin<<<1, 32, 0, s>>>(st, M, diis_start);
+}
+
+static unsigned ew_blocks(i64 n) {
+  i64 blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  return (unsigned)blocks;
+}
+
+// slot[st[2]] = src (the amplitudes before the Jacobi step)
+template <typename T>
+__global__ void k_slot_save(char* __restrict__ base, i64 stride, i64 off, const int* __restrict__ st,
+                            const T* __restrict__ src, i64 n) {
+  T* dst = (T*)(base + (i64)st[2] * stride + off);
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+template <typename T>
+void launch_slot_save(char* base, i64 stride, i64 off, const int* st, const T* src, i64 n, cudaStream_t s) {
+  if (n <= 0) return;
+  ++g_launch_count;
+  k_slot_save<T><<<ew_blocks(n), 256, 0, s>>>(base, stride, off, st, src, n);
+}
+template void launch_slot_save<double>(char*, i64, i64, const int*, const double*, i64, cudaStream_t);
+template void launch_slot_save<float>(char*, i64, i64, const int*, const float*, i64, cudaStream_t);
+
+// error slot: e = t - e (new minus old); amplitude slot: t
+template <typename T>
+__global__ void k_slot_diff_store(char* __restrict__ hist_t, char* __restrict__ hist_e, i64 stride, i64 off,
+                                  const int* __restrict__ st, const T* __restrict__ t, i64 n) {
+  const i64 o = (i64)st[2] * stride + off;
+  T* ts = (T*)(hist_t + o);
+  T* es = (T*)(hist_e + o);
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    const T x = t[i];
+    es[i] = x - es[i];
+    ts[i] = x;
+  }
+}
+
+template <typename T>
+void launch_slot_diff_store(char* hist_t, char* hist_e, i64 stride, i64 off, const int* st, const T* t, i64 n,
+                            cudaStream_t s) {
+  if (n <= 0) return;
+  ++g_launch_count;
+  k_slot_diff_store<T><<<ew_blocks(n), 256, 0, s>>>(hist_t, hist_e, stride, off, st, t, n);
+}
+template void launch_slot_diff_store<double>(char*, char*, i64, i64, const int*, const double*, i64, cudaStream_t);
+template void launch_slot_diff_store<float>(char*, char*, i64, i64, const int*, const float*, i64, cudaStream_t);
+
+// partial[q][block] = sum_x w(x) e_s[x] e_q[x] for q < st[3] (0 otherwise); weights
+// per segment of `seg` elements when w is given.  Fixed grid: deterministic.
+template <typename T>
+__global__ void k_diis_dots(const char* __restrict__ hist_e, i64 stride, i64 off, const int* __restrict__ st, int M,
+                            i64 n, i64 seg, const double* __restrict__ w, double* __restrict__ partial) {
+  const int m = st[3];
+  const T* es = (const T*)(hist_e + (i64)st[2] * stride + off);
+  for (int q = 0; q < M; ++q) {
+    double s = 0.0;
+    if (q < m) {
+      const T* eq = (const T*)(hist_e + (i64)q * stride + off);
+      if (w) {
+        const i64 nseg = (n + seg - 1) / seg;
+        for (i64 sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
+          const i64 b0 = sgi * seg, b1 = b0 + seg < n ? b0 + seg : n;
+          double ss = 0.0;
+          for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) ss += (double)es[i] * (double)eq[i];
+          s += w[sgi] * ss;
+        }
+      } else {
+        for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+          s += (double)es[i] * (double)eq[i];
+      }
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[(i64)q * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+template <typename T>
+void launch_diis_dots(const char* hist_e, i64 stride, i64 off, const int* st, int M, i64 n, i64 seg, const double* w,
+                      double* partial, cudaStream_t s) {
+  ++g_launch_count;
+  k_diis_dots<T><<<kDotBlocks, 256, 0, s>>>(hist_e, stride, off, st, M, n, seg, w, partial);
+}
+template void launch_diis_dots<double>(const char*, i64, i64, const int*, int, i64, i64, const double*, double*,
+                                       cudaStream_t);
+template void launch_diis_dots<float>(const char*, i64, i64, const int*, int, i64, i64, const double*, double*,
+                                      cudaStream_t);
+
+// B[s][q] = B[q][s] = sum over the nseg segment partials (fixed order); block q.
+__global__ void k_diis_row(const double* __restrict__ partial, int nseg, const int* __restrict__ st, int M,
+                           double* __restrict__ B) {
+  const int q = blockIdx.x, slot = st[2];
+  if (q >= st[3]) return;
+  double tot = 0.0;
+  for (int g = 0; g < nseg; ++g) {
+    const double* p = partial + ((i64)g * M + q) * kDotBlocks;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < kDotBlocks; i += blockDim.x) s += p[i];
+    s = block_sum(s);
+    tot += s;  // meaningful in thread 0
+  }
+  if (threadIdx.x == 0) {
+    B[slot * M + q] = tot;
+    B[q * M + slot] = tot;
+  }
+}
+
+void launch_diis_row(const double* partial, int nseg, const int* st, int M, double* B, cudaStream_t s) {
+  ++g_launch_count;
+  k_diis_row<<<M, 256, 0, s>>>(partial, nseg, st, M, B);
+}
+
+// Bordered solve [B 1; 1 0] [c; lambda] = [0; 1] over the st[3] entries in use by
+// partial-pivoting Gaussian elimination; a pivot below 1e-14 of max|B| drops that
+// direction (coefficient 0), the least-squares limit for a singular B.  Runs only
+// when st[4] is set.
+__global__ void k_diis_solve(const double* __restrict__ Bmat, const int* __restrict__ st, int ld,
+                             double* __restrict__ coef) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || !st[4]) return;
+  const int m = st[3];
   double A[17][18];
   const int n = m + 1;
   double scale = 0.0;
@@ -433,15 +567,18 @@ __global__ void k_diis_solve(const double* __restrict__ Bmat, int m, int ld, dou
   for (int i = 0; i < m; ++i) coef[i] = x[i];
 }
 
-void launch_diis_solve(const double* B, int m, int ld, double* coef, cudaStream_t s) {
+void launch_diis_solve(const double* B, const int* st, int ld, double* coef, cudaStream_t s) {
   ++g_launch_count;
-  k_diis_solve<<<1, 32, 0, s>>>(B, m, ld, coef);
+  k_diis_solve<<<1, 32, 0, s>>>(B, st, ld, coef);
 }
 
-// out[i] = sum_m coef[m] * hist[m][i] (hist slots stride `stride` elements)
+// out[i] = sum_q coef[q] * hist[q][i] over the st[3] entries (hist slots `stride`
+// elements apart); runs only when st[4] is set.
 template <typename T>
 __global__ void k_diis_extrapolate(T* __restrict__ out, const T* __restrict__ hist, i64 stride, i64 n,
-                                   const double* __restrict__ coef, int m) {
+                                   const double* __restrict__ coef, const int* __restrict__ st) {
+  if (!st[4]) return;
+  const int m = st[3];
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int q = 0; q < m; ++q) s += coef[q] * (double)hist[q * stride + i];
@@ -450,35 +587,16 @@ __global__ void k_diis_extrapolate(T* __restrict__ out, const T* __restrict__ hi
 }
 
 template <typename T>
-void launch_diis_extrapolate(T* out, const T* hist, i64 stride, i64 n, const double* coef, int m,
+void launch_diis_extrapolate(T* out, const T* hist, i64 stride, i64 n, const double* coef, const int* st,
                              cudaStream_t s) {
   if (n <= 0) return;
-  i64 blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
   ++g_launch_count;
-  k_diis_extrapolate<T><<<(unsigned)blocks, 256, 0, s>>>(out, hist, stride, n, coef, m);
+  k_diis_extrapolate<T><<<ew_blocks(n), 256, 0, s>>>(out, hist, stride, n, coef, st);
 }
-template void launch_diis_extrapolate<double>(double*, const double*, i64, i64, const double*, int,
+template void launch_diis_extrapolate<double>(double*, const double*, i64, i64, const double*, const int*,
                                               cudaStream_t);
-template void launch_diis_extrapolate<float>(float*, const float*, i64, i64, const double*, int,
+template void launch_diis_extrapolate<float>(float*, const float*, i64, i64, const double*, const int*,
                                              cudaStream_t);
-
-// e = a - b (DIIS error vector), elementwise
-template <typename T>
-__global__ void k_sub(T* __restrict__ out, const T* __restrict__ a, const T* __restrict__ b, i64 n) {
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
-    out[i] = (T)((double)a[i] - (double)b[i]);
-}
-template <typename T>
-void launch_sub(T* out, const T* a, const T* b, i64 n, cudaStream_t s) {
-  if (n <= 0) return;
-  i64 blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  ++g_launch_count;
-  k_sub<T><<<(unsigned)blocks, 256, 0, s>>>(out, a, b, n);
-}
-template void launch_sub<double>(double*, const double*, const double*, i64, cudaStream_t);
-template void launch_sub<float>(float*, const float*, const float*, i64, cudaStream_t);
 
 // Type conversion between FP64 and FP32 storage.
 template <typename TO, typename TI>

@@ -34,12 +34,22 @@ void launch_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, 
 template <typename T>
 void launch_wdot(const T* x, const T* y, i64 n, i64 seg, const double* w, double* partial, double* out,
                  double scale, int accumulate, cudaStream_t s);
-void launch_diis_solve(const double* B, int m, int ld, double* coef, cudaStream_t s);
+// DIIS with device-side bookkeeping (st[8]: updates, entries written, slot, entries
+// in use, extrapolate flag); every launch reads the state, none needs the host.
+void launch_diis_begin(int* st, int M, int diis_start, cudaStream_t s);
 template <typename T>
-void launch_diis_extrapolate(T* out, const T* hist, i64 stride, i64 n, const double* coef, int m,
+void launch_slot_save(char* base, i64 stride, i64 off, const int* st, const T* src, i64 n, cudaStream_t s);
+template <typename T>
+void launch_slot_diff_store(char* hist_t, char* hist_e, i64 stride, i64 off, const int* st, const T* t, i64 n,
+                            cudaStream_t s);
+template <typename T>
+void launch_diis_dots(const char* hist_e, i64 stride, i64 off, const int* st, int M, i64 n, i64 seg, const double* w,
+                      double* partial, cudaStream_t s);
+void launch_diis_row(const double* partial, int nseg, const int* st, int M, double* B, cudaStream_t s);
+void launch_diis_solve(const double* B, const int* st, int ld, double* coef, cudaStream_t s);
+template <typename T>
+void launch_diis_extrapolate(T* out, const T* hist, i64 stride, i64 n, const double* coef, const int* st,
                              cudaStream_t s);
-template <typename T>
-void launch_sub(T* out, const T* a, const T* b, i64 n, cudaStream_t s);
 template <typename TO, typename TI>
 void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t s);
 

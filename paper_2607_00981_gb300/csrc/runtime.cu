@@ -217,6 +217,7 @@ struct rccsdt_ctx {
   std::unique_ptr<DBuf> hist_t, hist_e;     // M slots each: t1 | t2 | t3 (padded)
   i64 hist_stride = 0;                      // bytes per slot
   i64 seg1 = 0, seg2 = 0, seg3 = 0;         // element counts
+  std::unique_ptr<DBuf> diis_st, diis_partial;  // device DIIS counters int[8]; dot partials [3][M][blocks]
   std::unique_ptr<DBuf> scalars, partial, splitk, rawX;
 
   DBuf* B(const std::string& k) { return buf.at(k).get(); }
@@ -1284,14 +1285,19 @@ int do_update(rccsdt_ctx* c) {
   const int M = c->opt.diis_space;
   const bool dt3 = c->opt.diis_t3 != 0;
   c->iter += 1;
-  int s = -1;
+  int* st = c->diis_st ? (int*)c->diis_st->p : nullptr;
+  char* ht = c->hist_t ? (char*)c->hist_t->p : nullptr;
+  char* he = c->hist_e ? (char*)c->hist_e->p : nullptr;
+  const i64 S = c->hist_stride, off1 = 0, off2 = c->seg1 * 8, off3 = (c->seg1 + c->seg2) * 8;
   if (M > 0) {
-    s = c->diis_count % M;
-    Seg e = slot(c, M + s);
-    // old amplitudes into the error slot, then e = t_new - t_old after the step
-    dev_copy(e.t1, c->D("t1"), c->seg1 * 8, c->stream);
-    dev_copy(e.t2, c->D("t2"), c->seg2 * 8, c->stream);
-    if (dt3) dev_copy(e.t3, c->B("t3")->p, c->seg3 * (f ? 4 : 8), c->stream);
+    // slot and counters on the device; the amplitudes before the step go to the error slot
+    rcc::launch_diis_begin(st, M, c->opt.diis_start, c->stream);
+    rcc::launch_slot_save<double>(he, S, off1, st, c->D("t1"), c->seg1, c->stream);
+    rcc::launch_slot_save<double>(he, S, off2, st, c->D("t2"), c->seg2, c->stream);
+    if (dt3) {
+      if (f) rcc::launch_slot_save<float>(he, S, off3, st, c->B("t3")->f(), c->seg3, c->stream);
+      else rcc::launch_slot_save<double>(he, S, off3, st, c->D("t3"), c->seg3, c->stream);
+    }
   }
   rcc::launch_update_t12(c->D("t1"), c->D("r1"), c->D("t2"), c->D("r2"), c->D("e"), o, v, 0.0, c->stream);
   if (f)
@@ -1299,48 +1305,39 @@ int do_update(rccsdt_ctx* c) {
   else
     rcc::launch_update_t3<double>(c->D("t3"), c->D("rp3"), c->D("e"), blk, o, v, c->n3, 0.0, c->stream);
   if (M <= 0) return check(c, "do_update");
-  Seg tn = slot(c, s), e = slot(c, M + s);
-  rcc::launch_sub<double>(e.t1, c->D("t1"), e.t1, c->seg1, c->stream);
-  rcc::launch_sub<double>(e.t2, c->D("t2"), e.t2, c->seg2, c->stream);
-  dev_copy(tn.t1, c->D("t1"), c->seg1 * 8, c->stream);
-  dev_copy(tn.t2, c->D("t2"), c->seg2 * 8, c->stream);
+  // error vector e = t_new - t_old and the new amplitudes into slot st[2]
+  rcc::launch_slot_diff_store<double>(ht, he, S, off1, st, c->D("t1"), c->seg1, c->stream);
+  rcc::launch_slot_diff_store<double>(ht, he, S, off2, st, c->D("t2"), c->seg2, c->stream);
   if (dt3) {
-    if (f) rcc::launch_sub<float>((float*)e.t3, c->B("t3")->f(), (const float*)e.t3, c->seg3, c->stream);
-    else rcc::launch_sub<double>((double*)e.t3, c->D("t3"), (const double*)e.t3, c->seg3, c->stream);
-    dev_copy(tn.t3, c->B("t3")->p, c->seg3 * (f ? 4 : 8), c->stream);
+    if (f) rcc::launch_slot_diff_store<float>(ht, he, S, off3, st, c->B("t3")->f(), c->seg3, c->stream);
+    else rcc::launch_slot_diff_store<double>(ht, he, S, off3, st, c->D("t3"), c->seg3, c->stream);
   }
   c->diis_count += 1;
-  const int m = std::min(c->diis_count, M);
-  // new row / column of B
-  for (int q = 0; q < m; ++q) {
-    Seg eq = slot(c, M + q);
-    double* out = scal(c, kB + s * M + q);
-    rcc::launch_wdot<double>(e.t1, eq.t1, c->seg1, 1, nullptr, partials(c), out, 1.0, 0, c->stream);
-    rcc::launch_wdot<double>(e.t2, eq.t2, c->seg2, 1, nullptr, partials(c), out, 1.0, 1, c->stream);
-    if (dt3) {
-      if (f)
-        rcc::launch_wdot<float>((const float*)e.t3, (const float*)eq.t3, c->seg3, c->V3, c->blk_weight->d(),
-                                partials(c), out, 1.0, 1, c->stream);
-      else
-        rcc::launch_wdot<double>((const double*)e.t3, (const double*)eq.t3, c->seg3, c->V3, c->blk_weight->d(),
-                                 partials(c), out, 1.0, 1, c->stream);
-    }
-    dev_copy(scal(c, kB + q * M + s), out, 8, c->stream);
+  // new row / column of B: <e_s, e_q> with the multiplicity weights on t3
+  double* dp = (double*)c->diis_partial->p;
+  const i64 G = (i64)M * rcc::kDotBlocks;
+  rcc::launch_diis_dots<double>(he, S, off1, st, M, c->seg1, 1, nullptr, dp, c->stream);
+  rcc::launch_diis_dots<double>(he, S, off2, st, M, c->seg2, 1, nullptr, dp + G, c->stream);
+  if (dt3) {
+    if (f)
+      rcc::launch_diis_dots<float>(he, S, off3, st, M, c->seg3, c->V3, c->blk_weight->d(), dp + 2 * G, c->stream);
+    else
+      rcc::launch_diis_dots<double>(he, S, off3, st, M, c->seg3, c->V3, c->blk_weight->d(), dp + 2 * G, c->stream);
   }
-  if (c->iter >= c->opt.diis_start && m >= 2) {
-    rcc::launch_diis_solve(scal(c, kB), m, M, scal(c, kCoef), c->stream);
-    rcc::launch_diis_extrapolate<double>(c->D("t1"), slot(c, 0).t1, c->hist_stride / 8, c->seg1, scal(c, kCoef), m,
-                                         c->stream);
-    rcc::launch_diis_extrapolate<double>(c->D("t2"), slot(c, 0).t2, c->hist_stride / 8, c->seg2, scal(c, kCoef), m,
-                                         c->stream);
-    if (dt3) {
-      if (f)
-        rcc::launch_diis_extrapolate<float>(c->B("t3")->f(), (const float*)slot(c, 0).t3, c->hist_stride / 4, c->seg3,
-                                            scal(c, kCoef), m, c->stream);
-      else
-        rcc::launch_diis_extrapolate<double>(c->D("t3"), (const double*)slot(c, 0).t3, c->hist_stride / 8, c->seg3,
-                                             scal(c, kCoef), m, c->stream);
-    }
+  rcc::launch_diis_row(dp, dt3 ? 3 : 2, st, M, scal(c, kB), c->stream);
+  // extrapolation (the kernels skip themselves before diis_start or with one entry)
+  rcc::launch_diis_solve(scal(c, kB), st, M, scal(c, kCoef), c->stream);
+  rcc::launch_diis_extrapolate<double>(c->D("t1"), slot(c, 0).t1, c->hist_stride / 8, c->seg1, scal(c, kCoef), st,
+                                       c->stream);
+  rcc::launch_diis_extrapolate<double>(c->D("t2"), slot(c, 0).t2, c->hist_stride / 8, c->seg2, scal(c, kCoef), st,
+                                       c->stream);
+  if (dt3) {
+    if (f)
+      rcc::launch_diis_extrapolate<float>(c->B("t3")->f(), (const float*)slot(c, 0).t3, c->hist_stride / 4, c->seg3,
+                                          scal(c, kCoef), st, c->stream);
+    else
+      rcc::launch_diis_extrapolate<double>(c->D("t3"), (const double*)slot(c, 0).t3, c->hist_stride / 8, c->seg3,
+                                           scal(c, kCoef), st, c->stream);
   }
   return check(c, "do_update");
 }
@@ -1435,6 +1432,8 @@ RCC_API int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, voi
       c->hist_t->p = dev_alloc((size_t)c->hist_stride * op.diis_space, &err);
       c->hist_e->p = dev_alloc((size_t)c->hist_stride * op.diis_space, &err);
       c->total_bytes += 2 * (size_t)c->hist_stride * op.diis_space;
+      c->diis_st = upload_vec(c, std::vector<int>(8, 0), &err);
+      c->diis_partial = upload_vec(c, std::vector<double>((size_t)3 * op.diis_space * rcc::kDotBlocks, 0.0), &err);
     }
     if (err) st = fail(c, RCCSDT_ERR_OOM, "device allocation failed");
   }
@@ -1465,6 +1464,7 @@ RCC_API int rccsdt_set_hamiltonian(rccsdt_ctx* c, const double* fock_diag, const
 static void reset_diis(rccsdt_ctx* c) {
   c->diis_count = 0;
   c->iter = 0;
+  if (c->diis_st) dev_zero(c->diis_st->p, c->diis_st->bytes, c->stream);
 }
 
 RCC_API int rccsdt_set_amplitudes(rccsdt_ctx* c, const double* t1, const double* t2, const double* t3c) {

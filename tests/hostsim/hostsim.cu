@@ -6,6 +6,7 @@
 // plain host loops over the same per-element functions (elem.cuh), so the host
 // logic can be checked against the oracle without a GPU.  The product binding
 // never loads it; the CUDA library has no CPU path.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -125,7 +126,68 @@ template void launch_wdot<double>(const double*, const double*, i64, i64, const 
 template void launch_wdot<float>(const float*, const float*, i64, i64, const double*, double*, double*, double, int,
                                  cudaStream_t);
 
-void launch_diis_solve(const double* Bm, int m, int ld, double* coef, cudaStream_t) {
+void launch_diis_begin(int* st, int M, int diis_start, cudaStream_t) {
+  const int iter = st[0] + 1, count = st[1];
+  st[0] = iter;
+  st[2] = count % M;
+  st[1] = count + 1;
+  st[3] = std::min(count + 1, M);
+  st[4] = (iter >= diis_start && st[3] >= 2) ? 1 : 0;
+}
+
+template <typename T>
+void launch_slot_save(char* base, i64 stride, i64 off, const int* st, const T* src, i64 n, cudaStream_t) {
+  T* dst = (T*)(base + (i64)st[2] * stride + off);
+  for (i64 i = 0; i < n; ++i) dst[i] = src[i];
+}
+template void launch_slot_save<double>(char*, i64, i64, const int*, const double*, i64, cudaStream_t);
+template void launch_slot_save<float>(char*, i64, i64, const int*, const float*, i64, cudaStream_t);
+
+template <typename T>
+void launch_slot_diff_store(char* hist_t, char* hist_e, i64 stride, i64 off, const int* st, const T* t, i64 n,
+                            cudaStream_t) {
+  T* ts = (T*)(hist_t + (i64)st[2] * stride + off);
+  T* es = (T*)(hist_e + (i64)st[2] * stride + off);
+  for (i64 i = 0; i < n; ++i) {
+    es[i] = t[i] - es[i];
+    ts[i] = t[i];
+  }
+}
+template void launch_slot_diff_store<double>(char*, char*, i64, i64, const int*, const double*, i64, cudaStream_t);
+template void launch_slot_diff_store<float>(char*, char*, i64, i64, const int*, const float*, i64, cudaStream_t);
+
+// the host version keeps one partial per q (the device splits it over its fixed grid)
+template <typename T>
+void launch_diis_dots(const char* hist_e, i64 stride, i64 off, const int* st, int M, i64 n, i64 seg, const double* w,
+                      double* partial, cudaStream_t) {
+  const T* es = (const T*)(hist_e + (i64)st[2] * stride + off);
+  for (int q = 0; q < M; ++q) {
+    double s = 0.0;
+    if (q < st[3]) {
+      const T* eq = (const T*)(hist_e + (i64)q * stride + off);
+      for (i64 i = 0; i < n; ++i) s += (double)es[i] * (double)eq[i] * (w ? w[i / seg] : 1.0);
+    }
+    for (int b = 0; b < kDotBlocks; ++b) partial[(i64)q * kDotBlocks + b] = b == 0 ? s : 0.0;
+  }
+}
+template void launch_diis_dots<double>(const char*, i64, i64, const int*, int, i64, i64, const double*, double*,
+                                       cudaStream_t);
+template void launch_diis_dots<float>(const char*, i64, i64, const int*, int, i64, i64, const double*, double*,
+                                      cudaStream_t);
+
+void launch_diis_row(const double* partial, int nseg, const int* st, int M, double* B, cudaStream_t) {
+  for (int q = 0; q < st[3]; ++q) {
+    double tot = 0.0;
+    for (int g = 0; g < nseg; ++g)
+      for (int b = 0; b < kDotBlocks; ++b) tot += partial[((i64)g * M + q) * kDotBlocks + b];
+    B[st[2] * M + q] = tot;
+    B[q * M + st[2]] = tot;
+  }
+}
+
+void launch_diis_solve(const double* Bm, const int* st, int ld, double* coef, cudaStream_t) {
+  if (!st[4]) return;
+  const int m = st[3];
   const int n = m + 1;
   std::vector<double> A((size_t)n * (n + 1));
   double scale = 0.0;
@@ -162,22 +224,19 @@ void launch_diis_solve(const double* Bm, int m, int ld, double* coef, cudaStream
 }
 
 template <typename T>
-void launch_diis_extrapolate(T* out, const T* hist, i64 stride, i64 n, const double* coef, int m, cudaStream_t) {
+void launch_diis_extrapolate(T* out, const T* hist, i64 stride, i64 n, const double* coef, const int* st,
+                             cudaStream_t) {
+  if (!st[4]) return;
   for (i64 i = 0; i < n; ++i) {
     double s = 0.0;
-    for (int q = 0; q < m; ++q) s += coef[q] * (double)hist[q * stride + i];
+    for (int q = 0; q < st[3]; ++q) s += coef[q] * (double)hist[q * stride + i];
     out[i] = (T)s;
   }
 }
-template void launch_diis_extrapolate<double>(double*, const double*, i64, i64, const double*, int, cudaStream_t);
-template void launch_diis_extrapolate<float>(float*, const float*, i64, i64, const double*, int, cudaStream_t);
-
-template <typename T>
-void launch_sub(T* out, const T* a, const T* b, i64 n, cudaStream_t) {
-  for (i64 i = 0; i < n; ++i) out[i] = (T)((double)a[i] - (double)b[i]);
-}
-template void launch_sub<double>(double*, const double*, const double*, i64, cudaStream_t);
-template void launch_sub<float>(float*, const float*, const float*, i64, cudaStream_t);
+template void launch_diis_extrapolate<double>(double*, const double*, i64, i64, const double*, const int*,
+                                              cudaStream_t);
+template void launch_diis_extrapolate<float>(float*, const float*, i64, i64, const double*, const int*,
+                                             cudaStream_t);
 
 template <typename TO, typename TI>
 void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t) {

@@ -162,6 +162,49 @@ int rccsdt_debug_copy(rccsdt_ctx* ctx, const char* name, double* out, long long 
 const char* rccsdt_last_error(const rccsdt_ctx* ctx);
 void rccsdt_destroy(rccsdt_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Batched instances.  A batch holds n independent contexts (instance i has
+ * o[i], v[i], naux[i]; all share *opt) and iterates them together: one CUDA
+ * graph launch per iteration runs every unconverged instance's iteration
+ * concurrently, each as the body of a conditional node chosen on the device from
+ * a per-instance code the host writes before the launch.  The graph is built on
+ * the first rccsdt_batch_solve (capture of each instance's launch sequence) and
+ * replayed afterwards.
+ * --------------------------------------------------------------------------- */
+typedef struct rccsdt_batch rccsdt_batch;
+
+/* Creates the batch and its n contexts on `stream` (used by the per-instance
+ * calls below); the batch launches its graph on a stream of its own.
+ * Errors: RCCSDT_ERR_ARG (n < 1, NULL arrays, an invalid size), RCCSDT_ERR_OOM. */
+int rccsdt_batch_create(int n, const int* o, const int* v, const int* naux, const rccsdt_options* opt,
+                        void* stream, rccsdt_batch** out);
+
+/* Context of instance i (owned by the batch, NULL if i is out of range).  Use it
+ * with rccsdt_set_hamiltonian, rccsdt_init_mp2 / rccsdt_set_amplitudes and
+ * rccsdt_get_amplitudes; do not destroy it. */
+rccsdt_ctx* rccsdt_batch_instance(rccsdt_batch* b, int i);
+
+/* Iterates every instance from its current amplitudes with the rule of
+ * rccsdt_solve (including the FP64 final phase of the split modes) until each has
+ * converged, failed or reached max_iter.  Host arrays of n entries receive each
+ * instance's energy, evaluations, final |R| and status (any may be NULL).
+ * Returns RCCSDT_OK when all converged, the most severe negative status if one
+ * failed, else RCCSDT_NOT_CONVERGED.  Unlike rccsdt_solve, an instance that stops
+ * at max_iter keeps the amplitudes its last residual was evaluated at. */
+int rccsdt_batch_solve(rccsdt_batch* b, double* e_corr, int* iterations, double* final_norm, int* status);
+
+/* Statistics of the last rccsdt_batch_solve: out[0] graph launches, [1] device ms
+ * over those launches (CUDA events around each launch), [2] algorithmic flop of
+ * the evaluations run, [3] kernels executed, [4] nodes of the top-level graph,
+ * [5] host ms to build the graph (captures included), [6] host ms to instantiate
+ * and upload it, [7] device ms of the first launch.  Returns entries written. */
+int rccsdt_batch_stats(const rccsdt_batch* b, double* out, int cap);
+/* Device ms of each launch of the last rccsdt_batch_solve; returns the count. */
+int rccsdt_batch_launch_times(const rccsdt_batch* b, double* ms, int cap);
+
+const char* rccsdt_batch_last_error(const rccsdt_batch* b);
+void rccsdt_batch_destroy(rccsdt_batch* b);
+
 /* Residual norms for callers that cannot allocate device memory.  The paper has
  * no counterpart: this entry point exists for callers such as a framework that
  * owns all device memory through its own pool allocator (a raw cudaMalloc would

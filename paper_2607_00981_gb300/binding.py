@@ -56,6 +56,13 @@ _SIGS = {
     "rccsdt_kernel_launches": (C.c_longlong, []),
     "rccsdt_last_error": (C.c_char_p, [_P]),
     "rccsdt_destroy": (None, [_P]),
+    "rccsdt_batch_create": (C.c_int, [C.c_int, _P, _P, _P, C.POINTER(Options), _P, C.POINTER(_P)]),
+    "rccsdt_batch_instance": (_P, [_P, C.c_int]),
+    "rccsdt_batch_solve": (C.c_int, [_P, _P, _P, _P, _P]),
+    "rccsdt_batch_stats": (C.c_int, [_P, _P, C.c_int]),
+    "rccsdt_batch_launch_times": (C.c_int, [_P, _P, C.c_int]),
+    "rccsdt_batch_last_error": (C.c_char_p, [_P]),
+    "rccsdt_batch_destroy": (None, [_P]),
 }
 
 
@@ -95,10 +102,14 @@ def default_options(lib, **kw) -> Options:
 class Context:
     """One RCCSDT problem (o occupied, v virtual spatial orbitals, naux factors)."""
 
-    def __init__(self, lib, o: int, v: int, naux: int, stream: int = 0, **options):
+    def __init__(self, lib, o: int, v: int, naux: int, stream: int = 0, _borrowed=None, **options):
         self.lib, self.o, self.v, self.naux = lib, o, v, naux
         self.n3 = o * (o + 1) * (o + 2) // 6
         self.options = default_options(lib, **options)
+        self.owned = _borrowed is None
+        if _borrowed is not None:  # a context owned by a Batch
+            self.h = _borrowed
+            return
         h = _P()
         st = lib.rccsdt_create(o, v, naux, C.byref(self.options), _P(stream) if stream else None, C.byref(h))
         if st != OK:
@@ -112,7 +123,8 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
-            self.lib.rccsdt_destroy(self.h)
+            if getattr(self, "owned", True):
+                self.lib.rccsdt_destroy(self.h)
             self.h = None
 
     __del__ = close
@@ -195,3 +207,59 @@ class Context:
         ms = np.zeros(16)
         n = self.lib.rccsdt_step_times(self.h, ms.ctypes.data, 16)
         return ms[:n]
+
+
+class Batch:
+    """Independent instances iterated together (one CUDA graph launch per iteration).
+
+    ``shapes`` is a list of (o, v, naux); ``instances[i]`` is a borrowed Context for
+    setting the Hamiltonian and amplitudes of instance i.
+    """
+
+    def __init__(self, lib, shapes, stream: int = 0, **options):
+        self.lib = lib
+        self.shapes = [tuple(int(x) for x in s) for s in shapes]
+        n = len(self.shapes)
+        o = (C.c_int * n)(*[s[0] for s in self.shapes])
+        v = (C.c_int * n)(*[s[1] for s in self.shapes])
+        na = (C.c_int * n)(*[s[2] for s in self.shapes])
+        self.options = default_options(lib, **options)
+        h = _P()
+        st = lib.rccsdt_batch_create(n, C.cast(o, _P), C.cast(v, _P), C.cast(na, _P), C.byref(self.options),
+                                     _P(stream) if stream else None, C.byref(h))
+        if st != OK:
+            raise RccsdtError(st, "rccsdt_batch_create failed")
+        self.h = h
+        self.instances = [Context(lib, s[0], s[1], s[2], _borrowed=lib.rccsdt_batch_instance(h, i), **options)
+                          for i, s in enumerate(self.shapes)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            for c in self.instances:
+                c.h = None
+            self.lib.rccsdt_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def solve(self):
+        """Returns (energies, iterations, final norms, statuses) as numpy arrays."""
+        n = len(self.shapes)
+        e, nrm = np.zeros(n), np.zeros(n)
+        it, st = np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.int32)
+        rc = self.lib.rccsdt_batch_solve(self.h, e.ctypes.data, it.ctypes.data, nrm.ctypes.data, st.ctypes.data)
+        if rc < 0:
+            raise RccsdtError(rc, self.lib.rccsdt_batch_last_error(self.h).decode())
+        return e, it, nrm, st
+
+    def stats(self):
+        out = np.zeros(8)
+        k = self.lib.rccsdt_batch_stats(self.h, out.ctypes.data, 8)
+        keys = ["launches", "device_ms", "flop", "kernels", "graph_nodes", "build_ms", "instantiate_ms",
+                "first_launch_ms"]
+        return dict(zip(keys[:k], out[:k].tolist()))
+
+    def launch_times(self, cap: int = 100000):
+        ms = np.zeros(cap)
+        k = self.lib.rccsdt_batch_launch_times(self.h, ms.ctypes.data, cap)
+        return ms[:k]

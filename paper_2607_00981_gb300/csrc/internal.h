@@ -1,0 +1,28 @@
+// Internal interface between the single-instance runtime and the batched driver.
+#pragma once
+#include <cuda_runtime.h>
+
+struct rccsdt_ctx;
+
+namespace rcc {
+
+// Queues one evaluation on the context's stream without any host synchronisation:
+// [the update of the amplitudes from the last residual when update_first], then the
+// energy, intermediates, residuals and post-processed R3 with its norms, with the
+// contractions in `precision`.  Results stay in the device scalars.
+int ctx_enqueue(rccsdt_ctx* c, int update_first, int precision);
+// Device scalars: [0..2] squared norms of R1, R2, R3 (block-weighted), [4] energy;
+// the int at byte offset 8000 is the tensor-core watchdog flag.
+const double* ctx_scalars(const rccsdt_ctx* c);
+cudaStream_t ctx_stream(const rccsdt_ctx* c);
+void ctx_set_stream(rccsdt_ctx* c, cudaStream_t s);
+int ctx_main_precision(const rccsdt_ctx* c);
+void ctx_reset_precision(rccsdt_ctx* c);
+// Resets host-side launch bookkeeping (operand reuse tracking, timing) so that a
+// captured sequence does not depend on what ran before it.
+void ctx_begin_capture(rccsdt_ctx* c);
+// 0 when the Hamiltonian and amplitudes are set, else an rccsdt_status.
+int ctx_ready(rccsdt_ctx* c);
+int ctx_dims(const rccsdt_ctx* c, int* o, int* v);
+
+}  // namespace rcc

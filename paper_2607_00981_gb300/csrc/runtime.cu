@@ -29,6 +29,7 @@
 
 #include "../../include/rccsdt.h"
 #include "elem.cuh"
+#include "internal.h"
 #include "kernels.h"
 
 using rcc::i64;
@@ -1702,3 +1703,36 @@ RCC_API void rccsdt_destroy(rccsdt_ctx* c) {
 #endif
   delete c;
 }
+
+// ---------------------------------------------------------------------------
+// Internal entry points for the batched driver (batch.cu); not part of the ABI.
+// ---------------------------------------------------------------------------
+namespace rcc {
+
+int ctx_enqueue(rccsdt_ctx* c, int update_first, int precision) {
+  c->precision = precision;
+  int st = 0;
+  if (update_first && (st = do_update(c))) return st;
+  if ((st = do_energy(c, nullptr))) return st;
+  if ((st = do_intermediates(c))) return st;
+  if ((st = do_residual(c))) return st;
+  return do_postprocess(c, nullptr);
+}
+
+const double* ctx_scalars(const rccsdt_ctx* c) { return (const double*)c->scalars->p; }
+cudaStream_t ctx_stream(const rccsdt_ctx* c) { return c->stream; }
+void ctx_set_stream(rccsdt_ctx* c, cudaStream_t s) { c->stream = s; }
+int ctx_main_precision(const rccsdt_ctx* c) { return c->opt.precision; }
+void ctx_reset_precision(rccsdt_ctx* c) { c->precision = c->opt.precision; }
+void ctx_begin_capture(rccsdt_ctx* c) {
+  c->packedA_kind = c->packedB_kind = -1;
+  c->timing = 0;
+}
+int ctx_ready(rccsdt_ctx* c) { return need(c, true, false, false); }
+int ctx_dims(const rccsdt_ctx* c, int* o, int* v) {
+  *o = c->o;
+  *v = c->v;
+  return 0;
+}
+
+}  // namespace rcc

@@ -86,6 +86,18 @@ def batch_shapes(count: int = 64, seed: int = 0):
     return [(int(oi), int(vi), int(4 * (oi + vi)), 1000 + i) for i, (oi, vi) in enumerate(zip(o, v))]
 
 
+def batch_instances(count: int = 64, seed: int = 0, weak: bool = True):
+    """The batched uneven-instance workload: ``batch_shapes`` with each instance's
+    factors drawn by ``make_instance``.  With ``weak`` the per-entry scale is the
+    rank-normalised, reduced ``0.6 * 0.3 * sqrt(40 / naux)`` of ``CONVERGENCE`` (the
+    scale 0.3 of the other workloads makes these ranks strongly coupled)."""
+    out = []
+    for o, v, naux, sd in batch_shapes(count, seed):
+        scale = 0.6 * 0.3 * (40 / naux) ** 0.5 if weak else 0.3
+        out.append(make_instance(o, v, naux, sd, scale=scale))
+    return out
+
+
 def random_amplitudes(o: int, v: int, seed: int, scale: float = 0.05):
     """Seeded (t1, t2, t3) with the spin-free column symmetries, for parity tests.
 

@@ -26,7 +26,8 @@ def hostsim_lib():
     if not os.path.exists(out) or any(os.path.getmtime(s) > os.path.getmtime(out) for s in srcs):
         os.makedirs(os.path.dirname(out), exist_ok=True)
         cmd = [nvcc(), "-std=c++17", "-O2", "-Xcompiler", "-fPIC", "-shared", "-DRCC_HOSTSIM", "-I", CSRC,
-               os.path.join(CSRC, "runtime.cu"), os.path.join(HOSTSIM_DIR, "hostsim.cu"), "-o", out]
+               os.path.join(CSRC, "runtime.cu"), os.path.join(CSRC, "batch.cu"), os.path.join(HOSTSIM_DIR, "hostsim.cu"),
+               "-o", out]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode:
             sys.stderr.write(res.stdout + res.stderr)

@@ -69,10 +69,16 @@ typedef struct {
   int max_iter;           /* rccsdt_solve iteration cap */
   double tol;             /* convergence threshold on the residual norm */
   long long watchdog_cycles; /* clock64 budget of device-side waits (0 = default) */
+  long long grouped_bytes;   /* split modes: device bytes the grouped residual may hold (all
+                                operand panels and dense results of the R3 contractions at
+                                once); when an instance needs more, or 0, its contractions
+                                run one by one through shared panels */
+  int autotune;              /* 1: time candidate launch shapes of the grouped GEMM on the
+                                first iteration and keep the fastest; 0: fixed shape */
 } rccsdt_options;
 
 /* Fills *opt with the defaults: FP64, final_fp64_iters 2, DIIS(8) from iteration 2
- * including T3, max_iter 100, tol 1e-8. */
+ * including T3, max_iter 100, tol 1e-8, grouped_bytes 8 GiB, autotune 0. */
 int rccsdt_options_default(rccsdt_options* opt);
 
 /* Creates a context for o occupied / v virtual orbitals and naux factors, on the
@@ -152,6 +158,12 @@ int rccsdt_enable_timing(rccsdt_ctx* ctx, int on);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 long long rccsdt_kernel_launches(void);
+
+/* Contraction engine of the context: out[0] 1 if the grouped residual is on,
+ * [1] its GEMM problems, [2] their output tiles, [3] operand gathers, [4] block
+ * contributions reduced into R3, [5] device bytes it holds, [6] persistent grid
+ * of its GEMM launch (0 = one CTA per SM), [7] panel kind.  Returns entries written. */
+int rccsdt_engine_info(const rccsdt_ctx* ctx, long long* out, int cap);
 
 /* Diagnostic: copies the first `count` float64 values of a named internal tensor
  * (e.g. "Fvv", "Wvvvo", "Wvvvv", "Wb_ovov", "r1", "X2") to `out`.  Layouts are the

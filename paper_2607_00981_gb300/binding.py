@@ -22,7 +22,8 @@ FP64, SPLIT_BF16X3, SPLIT_TF32X3 = 0, 1, 2
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("final_fp64_iters", C.c_int), ("diis_space", C.c_int),
                 ("diis_start", C.c_int), ("diis_t3", C.c_int), ("max_iter", C.c_int),
-                ("tol", C.c_double), ("watchdog_cycles", C.c_longlong)]
+                ("tol", C.c_double), ("watchdog_cycles", C.c_longlong), ("grouped_bytes", C.c_longlong),
+                ("autotune", C.c_int)]
 
 
 class RccsdtError(RuntimeError):
@@ -54,6 +55,7 @@ _SIGS = {
     "rccsdt_step_times": (C.c_int, [_P, _P, C.c_int]),
     "rccsdt_enable_timing": (C.c_int, [_P, C.c_int]),
     "rccsdt_kernel_launches": (C.c_longlong, []),
+    "rccsdt_engine_info": (C.c_int, [_P, _P, C.c_int]),
     "rccsdt_last_error": (C.c_char_p, [_P]),
     "rccsdt_destroy": (None, [_P]),
     "rccsdt_batch_create": (C.c_int, [C.c_int, _P, _P, _P, C.POINTER(Options), _P, C.POINTER(_P)]),
@@ -199,6 +201,12 @@ class Context:
         out = np.empty(shape)
         self._check(self.lib.rccsdt_debug_copy(self.h, name.encode(), out.ctypes.data, out.size))
         return out
+
+    def engine_info(self):
+        out = np.zeros(8, dtype=np.int64)
+        k = self.lib.rccsdt_engine_info(self.h, out.ctypes.data, 8)
+        keys = ["grouped", "problems", "tiles", "gathers", "contributions", "bytes", "grid", "kind"]
+        return dict(zip(keys[:k], out[:k].tolist()))
 
     def enable_timing(self, on=True):
         self._check(self.lib.rccsdt_enable_timing(self.h, 1 if on else 0))

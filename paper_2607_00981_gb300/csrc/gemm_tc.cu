@@ -172,27 +172,102 @@ struct TileGeom {
 
 constexpr int GROUP_N = 8;  // tiles of one wave span 8 column tiles x (SMs / 8) row tiles
 
+// One output tile: problem p, row tile tm, column tile tn, K blocks [kb0, kb1), split slice ks.
+struct Tile {
+  int p, tm, tn, kb0, kb1, ks;
+};
+
 // Grouped raster order: within a group of GROUP_N column tiles, the column tile
 // varies fastest, then the row tile, so the A and B tiles one wave reads stay
 // L2-resident (about 4x less HBM traffic than a plain row-major order on the
 // largest GEMMs).
-__device__ __forceinline__ void decode(const TileGeom& g, int tile, int& tm, int& tn, int& kb0, int& kb1) {
-  const int ks = tile % g.splitk;
-  const int t = tile / g.splitk;
-  const int per_group = g.mt * GROUP_N;
+__device__ __forceinline__ void raster(int mt, int nt, int t, int& tm, int& tn) {
+  const int per_group = mt * GROUP_N;
   const int grp = t / per_group, idx = t % per_group;
-  const int gw = min(GROUP_N, g.nt - grp * GROUP_N);
+  const int gw = min(GROUP_N, nt - grp * GROUP_N);
   tm = idx / gw;
   tn = grp * GROUP_N + idx % gw;
-  kb0 = ks * g.kb_per;
-  kb1 = min(g.kblocks, kb0 + g.kb_per);
 }
 
-template <int FMT>
+// Schedule of a single GEMM (optionally split along K) with the table-driven
+// scatter epilogue or FP32 partial tiles.  Tensor maps live in the kernel's
+// parameter space (__grid_constant__).
+struct PlainSched {
+  CUtensorMap ah, al, bh, bl;
+  TileGeom g;
+  EpiArgs e;
+  float* partial;  // [splitk][M][N] partial tiles, or the dense raw result when splitk == 1
+  __device__ __forceinline__ int ntiles() const { return g.mt * g.nt * g.splitk; }
+  __device__ __forceinline__ void tile(int t, Tile& x) const {
+    x.p = 0;
+    x.ks = t % g.splitk;
+    raster(g.mt, g.nt, t / g.splitk, x.tm, x.tn);
+    x.kb0 = x.ks * g.kb_per;
+    x.kb1 = min(g.kblocks, x.kb0 + g.kb_per);
+  }
+  __device__ __forceinline__ const CUtensorMap* map(int q, const Tile&) const {
+    return q == 0 ? &ah : q == 1 ? &al : q == 2 ? &bh : &bl;
+  }
+  __device__ __forceinline__ void store(const Tile& x, int m, int n0, const uint32_t (&r)[32]) const {
+    if (m >= e.M) return;
+    if (partial) {
+      float* dst = partial + ((i64)x.ks * e.M + m) * e.N;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (n0 + j < e.N) dst[n0 + j] = __uint_as_float(r[j]);
+    } else {
+      epilogue_row(e, m, n0, r);
+    }
+  }
+};
+
+// Schedule of a group of independent GEMMs of different shapes (problem table in
+// device memory, tensor maps included): one persistent launch runs every tile
+// of every problem; problem p owns the tiles [tile0_p, tile0_p + mt_p nt_p).
+// Each problem writes its dense FP32 result out_p[M_p][N_p].
+struct GroupSched {
+  const GProblem* probs;
+  int nprob, total;
+  __device__ __forceinline__ int ntiles() const { return total; }
+  __device__ __forceinline__ void tile(int t, Tile& x) const {
+    int lo = 0, hi = nprob - 1;  // last problem with tile0 <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(&probs[mid].tile0) <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const GProblem& P = probs[lo];
+    x.p = lo;
+    x.ks = 0;
+    raster(__ldg(&P.mt), __ldg(&P.nt), t - __ldg(&P.tile0), x.tm, x.tn);
+    x.kb0 = 0;
+    x.kb1 = __ldg(&P.kblocks);
+  }
+  __device__ __forceinline__ const CUtensorMap* map(int q, const Tile& x) const {
+    const GProblem& P = probs[x.p];
+    return q == 0 ? &P.ah : q == 1 ? &P.al : q == 2 ? &P.bh : &P.bl;
+  }
+  __device__ __forceinline__ void store(const Tile& x, int m, int n0, const uint32_t (&r)[32]) const {
+    const GProblem& P = probs[x.p];
+    const int M = __ldg(&P.M), N = __ldg(&P.N);
+    if (m >= M) return;
+    float* dst = P.out + (i64)m * N + n0;
+    if ((N & 3) == 0 && n0 + 32 <= N) {
+#pragma unroll
+      for (int j = 0; j < 32; j += 4)
+        *(float4*)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                          __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (n0 + j < N) dst[j] = __uint_as_float(r[j]);
+    }
+  }
+};
+
+template <int FMT, class S>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
-              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, TileGeom g, EpiArgs e,
-              float* __restrict__ partial, int* __restrict__ status, long long budget) {
+    k_gemm_tc(const __grid_constant__ S sch, int* __restrict__ status, long long budget) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -228,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int ntiles = g.mt * g.nt * g.splitk;
+  const int ntiles = sch.ntiles();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -238,20 +313,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int q = 0; q < STAGES; ++q) issued[q] = -1;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        int tm, tn, kb0, kb1;
-        decode(g, tile, tm, tn, kb0, kb1);
-        for (int kb = kb0; kb < kb1; ++kb) {
+        Tile x;
+        sch.tile(tile, x);
+        const CUtensorMap *mah = sch.map(0, x), *mal = sch.map(1, x), *mbh = sch.map(2, x), *mbl = sch.map(3, x);
+        for (int kb = x.kb0; kb < x.kb1; ++kb) {
           if (!mbar_wait(&empty[s], ph ^ 1, budget, abort_flag)) {
             ok = false;
             break;
           }
           uint8_t* st = smem + s * STAGE_BYTES;
           mbar_expect_tx(&full[s], STAGE_BYTES);
-          const int x = kb * (ROWB / (FMT == 1 ? 2 : 4));
-          tma_load_2d(st, &mAh, &full[s], x, tm * BM);
-          tma_load_2d(st + A_PLANE, &mAl, &full[s], x, tm * BM);
-          tma_load_2d(st + 2 * A_PLANE, &mBh, &full[s], x, tn * BN);
-          tma_load_2d(st + 2 * A_PLANE + B_PLANE, &mBl, &full[s], x, tn * BN);
+          const int kx = kb * (ROWB / (FMT == 1 ? 2 : 4));
+          tma_load_2d(st, mah, &full[s], kx, x.tm * BM);
+          tma_load_2d(st + A_PLANE, mal, &full[s], kx, x.tm * BM);
+          tma_load_2d(st + 2 * A_PLANE, mbh, &full[s], kx, x.tn * BN);
+          tma_load_2d(st + 2 * A_PLANE + B_PLANE, mbl, &full[s], kx, x.tn * BN);
           issued[s] = (int)ph;
           if (++s == STAGES) {
             s = 0;
@@ -278,8 +354,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       int it = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
-        int tm, tn, kb0, kb1;
-        decode(g, tile, tm, tn, kb0, kb1);
+        Tile x;
+        sch.tile(tile, x);
         const int b = it & 1;
         const uint32_t aph = (it >> 1) & 1;
         if (!mbar_wait(&tempty[b], aph ^ 1, budget, abort_flag)) {
@@ -288,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         fence_after();
         const uint32_t d = tmem + (uint32_t)(b * BN);
-        for (int kb = kb0; kb < kb1; ++kb) {
+        for (int kb = x.kb0; kb < x.kb1; ++kb) {
           if (!mbar_wait(&full[s], ph, budget, abort_flag)) {
             ok = false;
             break;
@@ -300,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int j = 0; j < ROWB / 32; ++j) {
             const uint64_t adv = (uint64_t)(j * 32 >> 4);  // 32-byte K slice inside the swizzled row
-            umma<FMT>(d, ah + adv, bh + adv, (kb > kb0 || j > 0) ? 1u : 0u);
+            umma<FMT>(d, ah + adv, bh + adv, (kb > x.kb0 || j > 0) ? 1u : 0u);
             umma<FMT>(d, ah + adv, bl + adv, 1u);
             umma<FMT>(d, al + adv, bh + adv, 1u);
           }
@@ -328,8 +404,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = q * 32 + lane;
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-      int tm, tn, kb0, kb1;
-      decode(g, tile, tm, tn, kb0, kb1);
+      Tile x;
+      sch.tile(tile, x);
       const int b = it & 1;
       const uint32_t aph = (it >> 1) & 1;
       if (!mbar_wait(&tfull[b], aph, budget, abort_flag)) {
@@ -338,22 +414,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       fence_after();
-      const int m = tm * BM + row;
-      const int ks = tile % g.splitk;
+      const int m = x.tm * BM + row;
       for (int c = 0; c < BN / 32; ++c) {
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c * 32), r);
-        if (m < e.M) {
-          const int n0 = tn * BN + c * 32;
-          if (partial) {
-            float* dst = partial + ((i64)ks * e.M + m) * e.N;
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (n0 + j < e.N) dst[n0 + j] = __uint_as_float(r[j]);
-          } else {
-            epilogue_row(e, m, n0, r);
-          }
-        }
+        sch.store(x, m, x.tn * BN + c * 32, r);
       }
       fence_before();
       __syncwarp();
@@ -416,6 +481,17 @@ int num_sms() {
 
 }  // namespace
 
+template <int FMT, class S>
+static void launch_sched(const S& sch, int grid, int* status_flag, long long budget, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_tc<FMT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr = true;
+  }
+  ++g_launch_count;
+  k_gemm_tc<FMT, S><<<grid, kThreads, SMEM_BYTES, s>>>(sch, status_flag, budget);
+}
+
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int Kpad,
                    const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s, float* scratch,
                    long long scratch_elems, float* raw_out) {
@@ -423,11 +499,11 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
   const int esz = kind == PANEL_BF16X2 ? 2 : 4;
   const int bk = ROWB / esz;
   if (Kpad % bk != 0 || e.M <= 0 || e.N <= 0) return 1;
-  CUtensorMap mAh, mAl, mBh, mBl;
-  if (!make_map(&mAh, Ahi, e.M, Kpad, kind, BM) || !make_map(&mAl, Alo, e.M, Kpad, kind, BM) ||
-      !make_map(&mBh, Bhi, e.N, Kpad, kind, BN) || !make_map(&mBl, Blo, e.N, Kpad, kind, BN))
+  PlainSched sch;
+  if (!make_map(&sch.ah, Ahi, e.M, Kpad, kind, BM) || !make_map(&sch.al, Alo, e.M, Kpad, kind, BM) ||
+      !make_map(&sch.bh, Bhi, e.N, Kpad, kind, BN) || !make_map(&sch.bl, Blo, e.N, Kpad, kind, BN))
     return 2;
-  TileGeom g;
+  TileGeom& g = sch.g;
   g.mt = (e.M + BM - 1) / BM;
   g.nt = (e.N + BN - 1) / BN;
   g.kblocks = Kpad / bk;
@@ -445,23 +521,12 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
   const int grid = std::min(ntiles, sms);
   const long long budget = watchdog > 0 ? watchdog : 4000000000LL;
   float* part = raw_out ? raw_out : (g.splitk > 1 ? scratch : nullptr);
-  if (kind == PANEL_BF16X2) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-      attr = true;
-    }
-    ++g_launch_count;
-    k_gemm_tc<1><<<grid, kThreads, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, g, e, part, status_flag, budget);
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-      attr = true;
-    }
-    ++g_launch_count;
-    k_gemm_tc<2><<<grid, kThreads, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, g, e, part, status_flag, budget);
-  }
+  sch.e = e;
+  sch.partial = part;
+  if (kind == PANEL_BF16X2)
+    launch_sched<1>(sch, grid, status_flag, budget, s);
+  else
+    launch_sched<2>(sch, grid, status_flag, budget, s);
   if (part && !raw_out) {
     const long long MN = (long long)e.M * e.N;
     long long blocks = (MN + 255) / 256;
@@ -469,6 +534,48 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
     ++g_launch_count;
     k_splitk_reduce_f32<<<(unsigned)blocks, 256, 0, s>>>(part, g.splitk, e);
   }
+  return 0;
+}
+
+int gemm_tc_block_k(int kind) { return ROWB / (kind == PANEL_BF16X2 ? 2 : 4); }
+
+int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int M,
+                  int N, int Kpad, float* out) {
+  if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
+  const int bk = gemm_tc_block_k(kind);
+  if (Kpad % bk != 0 || M <= 0 || N <= 0) return 1;
+  if (!make_map(&p->ah, Ahi, M, Kpad, kind, BM) || !make_map(&p->al, Alo, M, Kpad, kind, BM) ||
+      !make_map(&p->bh, Bhi, N, Kpad, kind, BN) || !make_map(&p->bl, Blo, N, Kpad, kind, BN))
+    return 2;
+  p->a_hi = Ahi;
+  p->a_lo = Alo;
+  p->b_hi = Bhi;
+  p->b_lo = Blo;
+  p->out = out;
+  p->M = M;
+  p->N = N;
+  p->Kpad = Kpad;
+  p->kblocks = Kpad / bk;
+  p->mt = (M + BM - 1) / BM;
+  p->nt = (N + BN - 1) / BN;
+  return 0;
+}
+
+int gproblem_tiles(const GProblem& p) { return p.mt * p.nt; }
+
+int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total_tiles, int grid, int* status_flag,
+                           long long watchdog, cudaStream_t s) {
+  if ((kind != PANEL_BF16X2 && kind != PANEL_TF32X2) || nprob <= 0 || total_tiles <= 0) return 1;
+  GroupSched sch;
+  sch.probs = probs;
+  sch.nprob = nprob;
+  sch.total = total_tiles;
+  const int g = std::max(1, std::min(grid > 0 ? grid : num_sms(), total_tiles));
+  const long long budget = watchdog > 0 ? watchdog : 4000000000LL;
+  if (kind == PANEL_BF16X2)
+    launch_sched<1>(sch, g, status_flag, budget, s);
+  else
+    launch_sched<2>(sch, g, status_flag, budget, s);
   return 0;
 }
 

@@ -26,7 +26,7 @@ long long g_launch_count = 0;  // kernels launched by this library (host-side co
 // selector of up to 3 terms) and, with a single selector, its 32 row offsets
 // are staged in shared memory, so an element costs one source load.
 template <bool F32>
-__global__ void __launch_bounds__(256) k_pack(PackArgs a) {
+__device__ __forceinline__ void pack_tiles(const PackArgs& a, int r0, int kfirst, int kstep) {
   typedef typename std::conditional<F32, float, double>::type T;
   __shared__ T tile[32][33];
   __shared__ i64 cb[3][32];
@@ -34,7 +34,6 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
   __shared__ int sl[3][32];
   __shared__ i64 ro[32];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int r0 = blockIdx.x * 32;
   const int nterm = a.nterm < 3 ? a.nterm : 3;
   if (a.one_sel && tid < 32) ro[tid] = (r0 + tid < a.R) ? a.rowoff[r0 + tid] : 0;
   auto value = [&](int rr, int kk) -> T {
@@ -58,7 +57,7 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
     else
       store_panel(a, r, k, x);
   };
-  for (int k0 = blockIdx.y * 32; k0 < a.Kpad; k0 += gridDim.y * 32) {
+  for (int k0 = kfirst; k0 < a.Kpad; k0 += kstep) {
     __syncthreads();
     if (tid < nterm * 32) {
       const int t = tid >> 5, kk = tid & 31, k = k0 + kk;
@@ -85,6 +84,14 @@ __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
   }
 }
 
+// One 32 x 32 tile per step; the tile's column tables (coefficient, base offset,
+// selector of up to 3 terms) and, with a single selector, its 32 row offsets
+// are staged in shared memory, so an element costs one source load.
+template <bool F32>
+__global__ void __launch_bounds__(256) k_pack(PackArgs a) {
+  pack_tiles<F32>(a, blockIdx.x * 32, blockIdx.y * 32, gridDim.y * 32);
+}
+
 void launch_pack(const PackArgs& a, cudaStream_t s) {
   // rows on grid x (up to 2^31 - 1 blocks); K on grid y, grid-strided past 65535
   const int gy = std::min((a.Kpad + 31) / 32, 65535);
@@ -95,6 +102,109 @@ void launch_pack(const PackArgs& a, cudaStream_t s) {
   else
     k_pack<false><<<grid, block, 0, s>>>(a);
 }
+
+// Many gathers in one launch: block b packs one 32 x 32 tile of the gather p with
+// tile0[p] <= b < tile0[p + 1] (row tiles outer, K tiles inner).  All gathers of
+// one launch share the source type (F32: FP32 sources into split panels).
+template <bool F32>
+__global__ void __launch_bounds__(256) k_pack_grouped(const PackArgs* __restrict__ list,
+                                                      const int* __restrict__ tile0, int npack) {
+  const int b = blockIdx.x;
+  int lo = 0, hi = npack - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile0[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const PackArgs a = list[lo];
+  const int kt = (a.Kpad + 31) / 32;
+  const int local = b - tile0[lo];
+  pack_tiles<F32>(a, (local / kt) * 32, (local % kt) * 32, 1 << 30);
+}
+
+int pack_tiles_of(const PackArgs& a) { return ((a.R + 31) / 32) * ((a.Kpad + 31) / 32); }
+
+void launch_pack_grouped(const PackArgs* list, const int* tile0, int npack, int total_tiles, int f32_src,
+                         cudaStream_t s) {
+  if (npack <= 0 || total_tiles <= 0) return;
+  ++g_launch_count;
+  if (f32_src)
+    k_pack_grouped<true><<<total_tiles, dim3(32, 8), 0, s>>>(list, tile0, npack);
+  else
+    k_pack_grouped<false><<<total_tiles, dim3(32, 8), 0, s>>>(list, tile0, npack);
+}
+
+// ---------------------------------------------------------------------------
+// Output-stationary reduction of the dense GEMM results into compact R3.
+// Every contribution is a contiguous v^3 block X[x0][x1][x2] of a GEMM result
+// whose axis q lands on stored axis pos[q] of its target block, with a weight.
+// Block (cube, target) of the grid owns one 16^3 cube of one target block and
+// sums all of that block's contributions in a fixed order (no atomics): per
+// contribution, the permuted 16^3 cube of X is staged in shared memory with
+// coalesced loads and added into registers; the cube is written once.
+// ---------------------------------------------------------------------------
+__constant__ int c_perm3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_r3_gather(const float* __restrict__ X, const i64* __restrict__ target,
+                                                   const int* __restrict__ cstart, const i64* __restrict__ xoff,
+                                                   const int* __restrict__ csel, const float* __restrict__ calpha,
+                                                   int v, int accumulate, T* __restrict__ r3) {
+  __shared__ float xs[16][16][17];
+  const int nc = (v + 15) / 16;
+  const int cube = blockIdx.x, t = blockIdx.y;
+  const int y0[3] = {(cube / (nc * nc)) * 16, ((cube / nc) % nc) * 16, (cube % nc) * 16};
+  const i64 V2 = (i64)v * v;
+  const int tb = threadIdx.x >> 4, tc = threadIdx.x & 15;  // output (b, c) of this thread; a loops
+  float acc[16];
+#pragma unroll
+  for (int a = 0; a < 16; ++a) acc[a] = 0.f;
+  const int c0 = cstart[t], c1 = cstart[t + 1];
+  for (int c = c0; c < c1; ++c) {
+    const int sel = csel[c];
+    const int p0 = c_perm3[sel][0], p1 = c_perm3[sel][1], p2 = c_perm3[sel][2];
+    const int xo0 = y0[p0], xo1 = y0[p1], xo2 = y0[p2];
+    const float* xb = X + xoff[c];
+    __syncthreads();
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+      const int x0 = xo0 + i, x1 = xo1 + tb, x2 = xo2 + tc;
+      xs[i][tb][tc] = (x0 < v && x1 < v && x2 < v) ? __ldg(xb + x0 * V2 + (i64)x1 * v + x2) : 0.f;
+    }
+    __syncthreads();
+    const float al = calpha[c];
+#pragma unroll
+    for (int a = 0; a < 16; ++a) {
+      const int yl[3] = {a, tb, tc};
+      acc[a] = fmaf(al, xs[yl[p0]][yl[p1]][yl[p2]], acc[a]);
+    }
+  }
+  T* out = r3 + target[t];
+  const int yb = y0[1] + tb, yc = y0[2] + tc;
+  if (yb >= v || yc >= v) return;
+#pragma unroll
+  for (int a = 0; a < 16; ++a) {
+    const int ya = y0[0] + a;
+    if (ya < v) {
+      const i64 o = ya * V2 + (i64)yb * v + yc;
+      out[o] = accumulate ? (T)(out[o] + (T)acc[a]) : (T)acc[a];
+    }
+  }
+}
+
+template <typename T>
+void launch_r3_gather(const float* X, const i64* target, int ntarget, const int* cstart, const i64* xoff,
+                      const int* csel, const float* calpha, int v, int accumulate, T* r3, cudaStream_t s) {
+  if (ntarget <= 0) return;
+  const int nc = (v + 15) / 16;
+  ++g_launch_count;
+  k_r3_gather<T><<<dim3(nc * nc * nc, ntarget), 256, 0, s>>>(X, target, cstart, xoff, csel, calpha, v, accumulate,
+                                                             r3);
+}
+template void launch_r3_gather<float>(const float*, const i64*, int, const int*, const i64*, const int*, const float*,
+                                      int, int, float*, cudaStream_t);
+template void launch_r3_gather<double>(const float*, const i64*, int, const int*, const i64*, const int*,
+                                       const float*, int, int, double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // FP64 GEMM, C[m, n] += alpha[m] * sum_k A[m, k] B[n, k]; A [M][lda], B [N][ldb]
@@ -169,11 +279,13 @@ __global__ void k_splitk_reduce(const double* __restrict__ partial, int splitk, 
 // (scratch_elems doubles) holds the partial tiles.  Deterministic in both paths.
 void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, const EpiArgs& e,
                      double* scratch, i64 scratch_elems, cudaStream_t s) {
+  // The FP64 pipe does about 2 FMA per clock per SM, so a GEMM is only fast when
+  // every SM works on it: a grid below 2 x 152 tiles splits K (chunks of >= 32).
   const int tiles = ((e.N + 63) / 64) * ((e.M + 63) / 64);
   int splitk = 1;
-  if (tiles < 304 && K >= 1024 && scratch) {
+  if (tiles < 304 && K >= 64 && scratch) {
     splitk = (608 + tiles - 1) / tiles;
-    splitk = std::min(splitk, K / 256);
+    splitk = std::min(splitk, K / 32);
     const i64 MN = (i64)e.M * e.N;
     while (splitk > 1 && (i64)splitk * MN > scratch_elems) --splitk;
   }

@@ -1,5 +1,7 @@
 // Launch wrappers of the RCCSDT kernels (host-callable).
 #pragma once
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace rcc {
@@ -21,6 +23,19 @@ struct CombineArgs {
 };
 
 void launch_pack(const PackArgs& a, cudaStream_t s);
+// Grouped gathers (FP32 sources into split panels): list and tile0 in device
+// memory, tile0[p] = sum of pack_tiles_of() over the gathers before p.
+int pack_tiles_of(const PackArgs& a);
+void launch_pack_grouped(const PackArgs* list, const int* tile0, int npack, int total_tiles, int f32_src,
+                         cudaStream_t s);
+// Output-stationary reduction into compact R3: target block t (element offset
+// target[t] into r3) receives, in order, the contributions cstart[t] ..
+// cstart[t+1]-1: alpha * X[xoff + permuted v^3 block] with the virtual
+// permutation csel (index into the 6 orderings, X axis q -> stored axis).
+// accumulate = 0 overwrites the target blocks.
+template <typename T>
+void launch_r3_gather(const float* X, const i64* target, int ntarget, const int* cstart, const i64* xoff,
+                      const int* csel, const float* calpha, int v, int accumulate, T* r3, cudaStream_t s);
 void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, const EpiArgs& e,
                      double* scratch, i64 scratch_elems, cudaStream_t s);
 void launch_combine(const CombineArgs& c, cudaStream_t s);
@@ -62,6 +77,29 @@ void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t s);
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo,
                    int Kpad, const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s,
                    float* scratch, long long scratch_elems, float* raw_out = nullptr);
+// One GEMM of a grouped launch: X[M][N] = (Ahi Bhi + Ahi Blo + Alo Bhi) with A
+// [M][Kpad], B [N][Kpad] split panels; the tensor maps are encoded on the host
+// (make_gproblem) and the table is copied to device memory before the launch.
+struct alignas(128) GProblem {
+  CUtensorMap ah, al, bh, bl;
+  const void* a_hi;
+  const void* a_lo;
+  const void* b_hi;
+  const void* b_lo;
+  float* out;  // dense FP32 result, row-major [M][N]
+  int M, N, Kpad, kblocks, mt, nt;
+  int tile0;   // first tile of this problem in the launch's tile order (set by the caller)
+  int pad;
+};
+// Fills p (except tile0) for panels of `kind`; nonzero if unsupported.
+int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int M,
+                  int N, int Kpad, float* out);
+int gproblem_tiles(const GProblem& p);
+int gemm_tc_block_k(int kind);
+// One persistent launch over every tile of the nprob problems (device table,
+// tile0 prefix order); grid <= 0 picks one CTA per SM.
+int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total_tiles, int grid, int* status_flag,
+                           long long watchdog, cudaStream_t s);
 // Second phase of a two-phase scatter: for each row m of the dense FP32 result X
 // [M][v^3] (natural (a,b,c) order), C[row_base[m] + perm_sel[m](a,b,c)] +=
 // row_alpha[m] * X[m][abc]; perm_sel indexes the 6 virtual permutations.

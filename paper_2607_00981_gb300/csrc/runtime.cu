@@ -17,6 +17,7 @@
 //               Sec. II.D.1 turns into the exact permutation-operator sum.
 //   F_vv, F_oo  folded into W_vvvv and W_oooo, the groupings (F^v_v + W^vv_vv) and
 //               (F^o_o + W^oo_oo) of steps (iv) and (v) of Sec. III.A.2.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -173,6 +174,12 @@ struct GemmPlan {
   // axes map to stored axes by s3_sel, added to C[s3_base] with weight s3_alpha.
   int s3_rows = 0;
   std::unique_ptr<DBuf> s3_base, s3_sel, s3_alpha;
+  // host copies of the block tables (grouped residual); swap_ab: the grouped form
+  // exchanges the operands so that each v^3 block of the result is contiguous
+  std::vector<i64> h_base;
+  std::vector<int> h_sel;
+  std::vector<double> h_alpha;
+  int swap_ab = 0;
 };
 
 struct rccsdt_ctx {
@@ -211,6 +218,23 @@ struct rccsdt_ctx {
   std::vector<std::vector<rcc::CombineArgs>> c_int_after;
   // per-z unpack tables for a3
   std::unique_ptr<DBuf> a3_base, a3_pos;
+
+  // Grouped residual (split modes): every tensor-core contraction of the R3
+  // residual in one grouped GEMM launch, its operands gathered by two grouped
+  // launches, its results reduced into R3 by one output-stationary launch.
+  struct Grouped {
+    int on = 0, kind = -1;
+    size_t bytes = 0;
+    std::unique_ptr<DBuf> panels, raw;
+    std::unique_ptr<DBuf> packs[2], ptile[2];  // [0] FP64 sources, [1] FP32 sources
+    int npack[2] = {0, 0}, ntile[2] = {0, 0};
+    std::unique_ptr<DBuf> probs;
+    int nprob = 0, ntiles = 0, grid = 0;
+    double flop = 0.0;
+    std::unique_ptr<DBuf> target, cstart, xoff, csel, calpha;
+    int ntarget = 0;
+    std::vector<int> order;  // problem order of the launch (tile0 prefix in this order)
+  } gr;
 
   // DIIS state
   int diis_count = 0, iter = 0;
@@ -584,6 +608,9 @@ void set_two_phase(rccsdt_ctx* c, GemmPlan* g, const std::vector<i64>& base, con
                    const std::vector<double>& alpha, int* err) {
   std::vector<int> sel(xaxes.size());
   for (size_t r = 0; r < xaxes.size(); ++r) sel[r] = perm_id(xaxes[r].data());
+  g->h_base = base;
+  g->h_sel = sel;
+  g->h_alpha = alpha;
   g->s3_base = upload_vec(c, base, err);
   g->s3_sel = upload_vec(c, sel, err);
   g->s3_alpha = upload_vec(c, alpha, err);
@@ -895,6 +922,18 @@ int build_context(rccsdt_ctx* c) {
                  ecol, &err);
         g->big = 1;
         g->step = 1;
+        // grouped form: X = T3 view x W^T, rows (blk, w), columns (x, y) -- each block
+        // of v rows is the contiguous v^3 block [w][x][y] of stored block blk
+        {
+          static const int ax[3][3] = {{2, 0, 1}, {1, 0, 2}, {0, 1, 2}};
+          int pos[3] = {ax[term][0], ax[term][1], ax[term][2]};
+          for (i64 blk = b0; blk < b1; ++blk) {
+            g->h_base.push_back(blk * V3);
+            g->h_sel.push_back(perm_id(pos));
+            g->h_alpha.push_back(1.0);
+          }
+          g->swap_ab = 1;
+        }
         finish_plan(c, g, (int)V2);
         c->p_pp.push_back(g);
       }
@@ -1115,6 +1154,191 @@ int build_context(rccsdt_ctx* c) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Grouped residual setup.  The problems are the tensor-core contractions of the
+// R3 residual (pp-ladder with exchanged operands, ring, hh-ladder, T2 terms);
+// panels whose plans share an operand are gathered once.  Returns 0 and leaves
+// gr.on = 0 when the mode does not apply or exceeds its memory budget.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct GPanel {
+  const rcc::PackArgs* src;
+  size_t hi = 0, lo = 0;  // byte offsets in the panel arena
+};
+
+int build_grouped(rccsdt_ctx* c) {
+  auto& G = c->gr;
+  G.on = 0;
+  if (c->opt.precision == RCCSDT_FP64 || c->opt.grouped_bytes <= 0) return 0;
+  const int kind = c->opt.precision == RCCSDT_SPLIT_BF16X3 ? rcc::PANEL_BF16X2 : rcc::PANEL_TF32X2;
+  const size_t esz = kind == rcc::PANEL_BF16X2 ? 2 : 4;
+  std::vector<GemmPlan*> plans;
+  for (auto* grp : {&c->p_pp, &c->p_ringab, &c->p_ringc, &c->p_hh, &c->p_t2a})
+    for (GemmPlan* g : *grp) plans.push_back(g);
+  if (plans.empty()) return 0;
+  // panels: the shared operand of a group (reuse_A) is gathered once
+  std::vector<GPanel> panels;
+  std::vector<int> pa(plans.size()), pb(plans.size());
+  size_t off = 0;
+  auto add_panel = [&](const rcc::PackArgs* a) {
+    GPanel p;
+    p.src = a;
+    const size_t plane = (size_t)a->R * a->Kpad * esz;
+    p.hi = off;
+    off += (plane + 255) / 256 * 256;
+    p.lo = off;
+    off += (plane + 255) / 256 * 256;
+    panels.push_back(p);
+    return (int)panels.size() - 1;
+  };
+  for (size_t q = 0; q < plans.size(); ++q) {
+    GemmPlan* g = plans[q];
+    const rcc::PackArgs* shared = &g->A.a;  // the operand reuse_A refers to
+    const rcc::PackArgs* other = &g->B.a;
+    int ish = (g->reuse_A && q > 0) ? -1 : add_panel(shared);
+    if (ish < 0) ish = plans[q - 1]->swap_ab ? pb[q - 1] : pa[q - 1];
+    const int iot = add_panel(other);
+    if (g->swap_ab) {
+      pa[q] = iot;
+      pb[q] = ish;
+    } else {
+      pa[q] = ish;
+      pb[q] = iot;
+    }
+  }
+  const size_t panel_bytes = off;
+  // dense results
+  std::vector<size_t> xo(plans.size());
+  size_t xel = 0;
+  for (size_t q = 0; q < plans.size(); ++q) {
+    xo[q] = xel;
+    xel += ((size_t)plans[q]->E.e.M * plans[q]->E.e.N + 63) / 64 * 64;
+  }
+  const size_t need = panel_bytes + xel * 4;
+  G.flop = 0.0;
+  for (GemmPlan* g : plans) G.flop += 2.0 * g->fma;
+  if ((long long)need > c->opt.grouped_bytes) return 0;
+  int err = 0;
+  G.panels = std::make_unique<DBuf>();
+  G.panels->bytes = panel_bytes;
+  G.panels->p = dev_alloc(panel_bytes, &err);
+  G.raw = std::make_unique<DBuf>();
+  G.raw->bytes = xel * 4;
+  G.raw->p = dev_alloc(G.raw->bytes, &err);
+  if (err) return fail(c, RCCSDT_ERR_OOM, "grouped residual: device allocation failed");
+  c->total_bytes += need;
+  G.bytes = need;
+  char* base = (char*)G.panels->p;
+  float* raw = (float*)G.raw->p;
+  // gathers, split by source type
+  std::vector<rcc::PackArgs> packs[2];
+  std::vector<int> ptile[2];
+  int tiles[2] = {0, 0};
+  for (const GPanel& p : panels) {
+    rcc::PackArgs a = *p.src;
+    a.kind = kind;
+    a.out_hi = base + p.hi;
+    a.out_lo = base + p.lo;
+    const int t = a.src_f32 ? 1 : 0;
+    packs[t].push_back(a);
+    ptile[t].push_back(tiles[t]);
+    tiles[t] += rcc::pack_tiles_of(a);
+  }
+  for (int t = 0; t < 2; ++t) {
+    G.npack[t] = (int)packs[t].size();
+    G.ntile[t] = tiles[t];
+    if (G.npack[t]) {
+      G.packs[t] = upload_vec(c, packs[t], &err);
+      G.ptile[t] = upload_vec(c, ptile[t], &err);
+    }
+  }
+  // problems, longest K first (the persistent CTAs take tiles round robin)
+  std::vector<rcc::GProblem> probs(plans.size());
+  for (size_t q = 0; q < plans.size(); ++q) {
+    GemmPlan* g = plans[q];
+    const GPanel &A = panels[pa[q]], &B = panels[pb[q]];
+    const int M = g->swap_ab ? g->E.e.N : g->E.e.M, N = g->swap_ab ? g->E.e.M : g->E.e.N;
+    if (rcc::make_gproblem(&probs[q], kind, base + A.hi, base + A.lo, base + B.hi, base + B.lo, M, N, g->Kpad,
+                           raw + xo[q]))
+      return fail(c, RCCSDT_ERR_CUDA, "grouped residual: tensor map encoding failed");
+  }
+  G.order.resize(plans.size());
+  for (size_t q = 0; q < plans.size(); ++q) G.order[q] = (int)q;
+  std::stable_sort(G.order.begin(), G.order.end(),
+                   [&](int x, int y) { return probs[x].kblocks > probs[y].kblocks; });
+  std::vector<rcc::GProblem> sorted;
+  int t0 = 0;
+  for (int q : G.order) {
+    rcc::GProblem P = probs[q];
+    P.tile0 = t0;
+    t0 += rcc::gproblem_tiles(P);
+    sorted.push_back(P);
+  }
+  G.nprob = (int)sorted.size();
+  G.ntiles = t0;
+  G.probs = upload_vec(c, sorted, &err);
+  // contributions per stored block, in plan order
+  const i64 V3 = c->V3;
+  std::vector<std::vector<std::array<i64, 2>>> per(c->n3);  // (xoff, q * 64 + r-th) -> resolved below
+  std::vector<std::vector<std::pair<int, float>>> meta(c->n3);
+  for (size_t q = 0; q < plans.size(); ++q) {
+    GemmPlan* g = plans[q];
+    for (size_t r = 0; r < g->h_base.size(); ++r) {
+      const i64 blk = g->h_base[r] / V3;
+      per[blk].push_back({(i64)xo[q] + (i64)r * V3, 0});
+      meta[blk].push_back({g->h_sel[r], (float)g->h_alpha[r]});
+    }
+  }
+  std::vector<i64> target(c->n3), xoff;
+  std::vector<int> cstart(c->n3 + 1, 0), csel;
+  std::vector<float> calpha;
+  for (i64 b = 0; b < c->n3; ++b) {
+    target[b] = b * V3;
+    cstart[b] = (int)xoff.size();
+    for (size_t k = 0; k < per[b].size(); ++k) {
+      xoff.push_back(per[b][k][0]);
+      csel.push_back(meta[b][k].first);
+      calpha.push_back(meta[b][k].second);
+    }
+  }
+  cstart[c->n3] = (int)xoff.size();
+  G.ntarget = (int)c->n3;
+  G.target = upload_vec(c, target, &err);
+  G.cstart = upload_vec(c, cstart, &err);
+  G.xoff = upload_vec(c, xoff, &err);
+  G.csel = upload_vec(c, csel, &err);
+  G.calpha = upload_vec(c, calpha, &err);
+  if (err) return fail(c, RCCSDT_ERR_OOM, "grouped residual: table upload failed");
+  G.kind = kind;
+  G.on = 1;
+  return 0;
+}
+
+// The residual's tensor-core contractions through the grouped path (R3 is
+// overwritten by the reduction, so it needs no zeroing).
+int run_grouped(rccsdt_ctx* c) {
+  auto& G = c->gr;
+  for (int t = 0; t < 2; ++t)
+    if (G.npack[t])
+      rcc::launch_pack_grouped((const rcc::PackArgs*)G.packs[t]->p, (const int*)G.ptile[t]->p, G.npack[t], G.ntile[t],
+                               t == 1, c->stream);
+  int* flag = (int*)((double*)c->scalars->p + 1000);
+  const int tidx = timer_begin(c, 16, G.flop);
+  if (rcc::launch_gemm_tc_grouped(G.kind, (const rcc::GProblem*)G.probs->p, G.nprob, G.ntiles, G.grid, flag,
+                                  c->opt.watchdog_cycles, c->stream))
+    return fail(c, RCCSDT_ERR_ARG, "grouped GEMM configuration unsupported");
+  timer_end(c, tidx);
+  const float* X = (const float*)G.raw->p;
+  if (c->opt.precision != RCCSDT_FP64)
+    rcc::launch_r3_gather<float>(X, (const i64*)G.target->p, G.ntarget, (const int*)G.cstart->p,
+                                 (const i64*)G.xoff->p, (const int*)G.csel->p, (const float*)G.calpha->p, c->v, 0,
+                                 c->B("r3")->f(), c->stream);
+  return 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // Iteration steps
 // ---------------------------------------------------------------------------
 namespace {
@@ -1185,30 +1409,37 @@ int do_intermediates(rccsdt_ctx* c) {
 
 int do_residual(rccsdt_ctx* c) {
   int st = 0;
+  const bool grouped = c->gr.on && c->precision == c->opt.precision;
   {
     StepTimer tm(c, 5);
     run_combines(c, c->c_r12_base);
     if ((st = run_plans(c, c->p_r12))) return st;
     run_combines(c, c->c_r2_sym);
-    zero(c, "r3");
+    if (!grouped) zero(c, "r3");
     run_combines(c, c->c_wt);
   }
-  {
+  if (grouped) {
+    // pp-ladder, ring, hh-ladder and the T2 term with W^{ab}_{dj}: one grouped pass
     StepTimer tm(c, 1);
-    if ((st = run_plans(c, c->p_pp))) return st;
-  }
-  {
-    StepTimer tm(c, 2);
-    if ((st = run_plans(c, c->p_ringab))) return st;
-    if ((st = run_plans(c, c->p_ringc))) return st;
-  }
-  {
-    StepTimer tm(c, 3);
-    if ((st = run_plans(c, c->p_hh))) return st;
+    if ((st = run_grouped(c))) return st;
+  } else {
+    {
+      StepTimer tm(c, 1);
+      if ((st = run_plans(c, c->p_pp))) return st;
+    }
+    {
+      StepTimer tm(c, 2);
+      if ((st = run_plans(c, c->p_ringab))) return st;
+      if ((st = run_plans(c, c->p_ringc))) return st;
+    }
+    {
+      StepTimer tm(c, 3);
+      if ((st = run_plans(c, c->p_hh))) return st;
+    }
   }
   {
     StepTimer tm(c, 4);
-    if ((st = run_plans(c, c->p_t2a))) return st;
+    if (!grouped && (st = run_plans(c, c->p_t2a))) return st;
     const int4* blk = (const int4*)c->blocks_info->p;
     if (c->opt.precision != RCCSDT_FP64) {
       rcc::launch_convert<float, double>(c->B("t2_f")->f(), c->D("t2"), (i64)c->o * c->o * c->v * c->v, c->stream);
@@ -1371,6 +1602,8 @@ RCC_API int rccsdt_options_default(rccsdt_options* opt) {
   opt->max_iter = 100;
   opt->tol = 1e-8;
   opt->watchdog_cycles = 0;
+  opt->grouped_bytes = 8LL << 30;
+  opt->autotune = 0;
   return RCCSDT_OK;
 }
 
@@ -1438,6 +1671,7 @@ RCC_API int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, voi
     }
     if (err) st = fail(c, RCCSDT_ERR_OOM, "device allocation failed");
   }
+  if (!st) st = build_grouped(c);
   if (st) {
     delete c;
     return st;
@@ -1692,6 +1926,17 @@ RCC_API int rccsdt_step_times(rccsdt_ctx* c, double* ms, int cap) {
 }
 
 RCC_API long long rccsdt_kernel_launches(void) { return rcc::g_launch_count; }
+
+RCC_API int rccsdt_engine_info(const rccsdt_ctx* c, long long* out, int cap) {
+  if (!c || !out) return RCCSDT_ERR_ARG;
+  const auto& G = c->gr;
+  const long long v[8] = {G.on, G.nprob, G.ntiles, (long long)G.npack[0] + G.npack[1],
+                          G.on ? (long long)(G.xoff ? G.xoff->bytes / 8 : 0) : 0, (long long)(G.on ? G.bytes : 0),
+                          G.grid, G.kind};
+  const int k = cap < 8 ? cap : 8;
+  for (int q = 0; q < k; ++q) out[q] = v[q];
+  return k;
+}
 
 RCC_API const char* rccsdt_last_error(const rccsdt_ctx* c) { return c ? c->err.c_str() : "null context"; }
 

@@ -23,6 +23,12 @@ void launch_pack(const PackArgs& a, cudaStream_t) {
     for (int k = 0; k < a.Kpad; ++k) store_panel(a, r, k, k < a.K ? pack_value(a, r, k) : 0.0);
 }
 
+int pack_tiles_of(const PackArgs& a) { return ((a.R + 31) / 32) * ((a.Kpad + 31) / 32); }
+
+void launch_pack_grouped(const PackArgs* list, const int*, int npack, int, int, cudaStream_t s) {
+  for (int p = 0; p < npack; ++p) launch_pack(list[p], s);
+}
+
 void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, const EpiArgs& e, double*, i64,
                      cudaStream_t) {
   for (int m = 0; m < e.M; ++m)
@@ -72,6 +78,69 @@ void launch_combine(const CombineArgs& c, cudaStream_t) {
     c.out[ooff] = s;
   }
 }
+
+int gemm_tc_block_k(int kind) { return kind == PANEL_BF16X2 ? 64 : 32; }
+
+int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int M,
+                  int N, int Kpad, float* out) {
+  if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
+  if (Kpad % gemm_tc_block_k(kind) != 0 || M <= 0 || N <= 0) return 1;
+  memset((void*)p, 0, sizeof(*p));
+  p->a_hi = Ahi;
+  p->a_lo = Alo;
+  p->b_hi = Bhi;
+  p->b_lo = Blo;
+  p->out = out;
+  p->M = M;
+  p->N = N;
+  p->Kpad = Kpad;
+  p->kblocks = Kpad / gemm_tc_block_k(kind);
+  p->mt = (M + 127) / 128;
+  p->nt = (N + 255) / 256;
+  return 0;
+}
+
+int gproblem_tiles(const GProblem& p) { return p.mt * p.nt; }
+
+int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int, int, int* flag, long long wd,
+                           cudaStream_t s) {
+  for (int q = 0; q < nprob; ++q) {
+    const GProblem& P = probs[q];
+    EpiArgs e{};
+    e.M = P.M;
+    e.N = P.N;
+    if (launch_gemm_tc(kind, P.a_hi, P.a_lo, P.b_hi, P.b_lo, P.Kpad, e, flag, wd, s, nullptr, 0, P.out)) return 1;
+  }
+  return 0;
+}
+
+template <typename T>
+void launch_r3_gather(const float* X, const i64* target, int ntarget, const int* cstart, const i64* xoff,
+                      const int* csel, const float* calpha, int v, int accumulate, T* r3, cudaStream_t) {
+  static const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const i64 V2 = (i64)v * v, V3 = V2 * v;
+  std::vector<float> acc((size_t)V3);
+  for (int t = 0; t < ntarget; ++t) {
+    std::fill(acc.begin(), acc.end(), 0.f);
+    for (int c = cstart[t]; c < cstart[t + 1]; ++c) {
+      const int* p = P[csel[c]];
+      const float* xb = X + xoff[c];
+      for (int a = 0; a < v; ++a)
+        for (int b = 0; b < v; ++b)
+          for (int cc = 0; cc < v; ++cc) {
+            const int y[3] = {a, b, cc};
+            acc[(size_t)(a * V2 + b * v + cc)] =
+                std::fma(calpha[c], xb[y[p[0]] * V2 + (i64)y[p[1]] * v + y[p[2]]], acc[(size_t)(a * V2 + b * v + cc)]);
+          }
+    }
+    T* out = r3 + target[t];
+    for (i64 e = 0; e < V3; ++e) out[e] = accumulate ? (T)(out[e] + (T)acc[(size_t)e]) : (T)acc[(size_t)e];
+  }
+}
+template void launch_r3_gather<float>(const float*, const i64*, int, const int*, const i64*, const int*, const float*,
+                                      int, int, float*, cudaStream_t);
+template void launch_r3_gather<double>(const float*, const i64*, int, const int*, const i64*, const int*,
+                                       const float*, int, int, double*, cudaStream_t);
 
 template <typename T>
 void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStream_t) {

@@ -89,10 +89,12 @@ def test_batch_converged_energies_match_oracle(kind):
 @pytest.mark.parametrize("prec", [B.SPLIT_BF16X3, B.SPLIT_TF32X3], ids=["bf16x3", "tf32x3"])
 def test_batch_split_precision(kind, prec):
     """Split batches: the same trajectory as single split solves, FP64 final phase,
-    energies within 1e-6 Eh of the FP64 oracle."""
+    energies within 1e-6 Eh of the FP64 oracle.  (The FP64 phase of a split
+    context still stores T3 and R3 in FP32, which puts |R| <= 1e-8 in reach but
+    not much below.)"""
     lib = _lib(kind)
     insts = _instances()[:3]
-    opt = dict(tol=1e-9, max_iter=200, precision=prec)
+    opt = dict(tol=1e-8, max_iter=200, precision=prec)
     b = _batch(lib, insts, **opt)
     e, it, nrm, st = b.solve()
     assert (st == B.OK).all(), st

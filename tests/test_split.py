@@ -21,12 +21,16 @@ TOL = {B.SPLIT_BF16X3: 5e-5, B.SPLIT_TF32X3: 5e-6}
 @pytest.mark.parametrize("kind", BACKENDS)
 @pytest.mark.parametrize("prec", [B.SPLIT_BF16X3, B.SPLIT_TF32X3], ids=["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("o,v,naux", [(3, 12, 40), (4, 9, 16), (2, 21, 12)])
-def test_split_residual_matches_oracle(kind, prec, o, v, naux):
+@pytest.mark.parametrize("grouped", [1, 0], ids=["grouped", "per-plan"])
+def test_split_residual_matches_oracle(kind, prec, o, v, naux, grouped):
+    """Both engines: the grouped residual (one grouped GEMM, output-stationary
+    reduction) and the per-plan path (shared panels, two-phase scatter)."""
     lib = gpu_lib() if kind == "gpu" else hostsim_lib()
     inst = make_instance(o, v, naux, seed=o + v)
     t1, t2, t3 = random_amplitudes(o, v, seed=2 * v + o)
     t3c = oc.pack(t3)
-    ctx = B.Context(lib, o, v, naux, precision=prec)
+    ctx = B.Context(lib, o, v, naux, precision=prec, grouped_bytes=(8 << 30) if grouped else 0)
+    assert ctx.engine_info()["grouped"] == grouped
     ctx.set_hamiltonian(inst.fock_diag, inst.L)
     ctx.set_amplitudes(t1, t2, t3c)
     ctx.build_intermediates()

@@ -307,7 +307,10 @@ RCC_API int rccsdt_batch_create(int n, const int* o, const int* v, const int* na
   for (int i = 0; i < n && !st; ++i) {
     rccsdt_ctx* c = nullptr;
     st = rccsdt_create(o[i], v[i], naux[i], &b->opt, stream, &c);
-    if (!st) b->inst.push_back(c);
+    if (!st) {
+      if (n > 1) rcc::ctx_set_concurrent(c, 1);
+      b->inst.push_back(c);
+    }
   }
 #ifdef RCC_HOSTSIM
   if (!st) {

@@ -18,6 +18,9 @@ cudaStream_t ctx_stream(const rccsdt_ctx* c);
 void ctx_set_stream(rccsdt_ctx* c, cudaStream_t s);
 int ctx_main_precision(const rccsdt_ctx* c);
 void ctx_reset_precision(rccsdt_ctx* c);
+// 1: other contexts run concurrently on the GPU (a batch), so GEMMs are launched
+// with their natural grids instead of splitting K across every SM.
+void ctx_set_concurrent(rccsdt_ctx* c, int on);
 // Resets host-side launch bookkeeping (operand reuse tracking, timing) so that a
 // captured sequence does not depend on what ran before it.
 void ctx_begin_capture(rccsdt_ctx* c);

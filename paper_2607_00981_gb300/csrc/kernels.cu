@@ -18,6 +18,9 @@ namespace rcc {
 
 long long g_launch_count = 0;  // kernels launched by this library (host-side count)
 
+// The six orderings of three virtual labels (lexicographic); index = selector.
+__constant__ int c_perm3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
 // ---------------------------------------------------------------------------
 // Panel gather.  32 x 32 tile per block of 32 x 8 threads; reads go along the
 // source's contiguous direction, writes along k (the output's contiguous axis).
@@ -143,8 +146,6 @@ void launch_pack_grouped(const PackArgs* list, const int* tile0, int npack, int 
 // contribution, the permuted 16^3 cube of X is staged in shared memory with
 // coalesced loads and added into registers; the cube is written once.
 // ---------------------------------------------------------------------------
-__constant__ int c_perm3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-
 template <typename T>
 __global__ void __launch_bounds__(256) k_r3_gather(const float* __restrict__ X, const i64* __restrict__ target,
                                                    const int* __restrict__ cstart, const i64* __restrict__ xoff,
@@ -166,11 +167,14 @@ __global__ void __launch_bounds__(256) k_r3_gather(const float* __restrict__ X, 
     const int xo0 = y0[p0], xo1 = y0[p1], xo2 = y0[p2];
     const float* xb = X + xoff[c];
     __syncthreads();
-#pragma unroll 4
+    float ld[16];
+#pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int x0 = xo0 + i, x1 = xo1 + tb, x2 = xo2 + tc;
-      xs[i][tb][tc] = (x0 < v && x1 < v && x2 < v) ? __ldg(xb + x0 * V2 + (i64)x1 * v + x2) : 0.f;
+      ld[i] = (x0 < v && x1 < v && x2 < v) ? __ldg(xb + x0 * V2 + (i64)x1 * v + x2) : 0.f;
     }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) xs[i][tb][tc] = ld[i];
     __syncthreads();
     const float al = calpha[c];
 #pragma unroll
@@ -337,32 +341,117 @@ void launch_combine(const CombineArgs& c, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// R3 post-processing: rp[blk] = post(r[blk]).  One thread per element, grid-
-// stride over blocks; reads of the permuted partners hit L2.
+// R3 post-processing: rp[blk] = post(r[blk]) (symmetrise, purify, orthogonalise).
+// Every element needs its six virtual permutations, which lie in the six cubes
+// of one orbit of 16^3 tiles {(TA,TB,TC) permuted}.  One CTA takes one orbit of
+// one block: it loads the orbit's distinct cubes (1, 3 or 6) into shared memory
+// along the unit-stride axis, then writes every element of those cubes once --
+// one HBM read and one write per element.
 // ---------------------------------------------------------------------------
+constexpr int kPostTL = 16;
+
 template <typename T>
-__global__ void k_post(const T* __restrict__ r, T* __restrict__ rp, const int4* __restrict__ blocks,
-                       int v, i64 n3) {
-  const i64 V3 = (i64)v * v * v;
-  // blockIdx.x runs over (a, b) rows of the block, threads over c: 32-bit index math
-  for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
-    const int4 ijk = blocks[b];
-    const T* rb = r + b * V3;
-    T* out = rp + b * V3;
-    for (int ab = blockIdx.x; ab < v * v; ab += gridDim.x) {
-      const int a = ab / v, bb = ab - a * v;
-      for (int c = threadIdx.x; c < v; c += blockDim.x)
-        out[ab * v + c] = post_value<T>(rb, v, ijk.x, ijk.y, ijk.z, a, bb, c);
+__global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __restrict__ rp,
+                                              const int4* __restrict__ blocks, int v) {
+  constexpr int TL = kPostTL;
+  typedef T Cube[TL][TL][TL + 1];
+  extern __shared__ __align__(16) unsigned char post_smem[];
+  Cube* cube = reinterpret_cast<Cube*>(post_smem);
+  __shared__ int tcoord[6][3];
+  __shared__ int slot[6][6];
+  __shared__ int ncube;
+  const int nt = (v + TL - 1) / TL;
+  const i64 b = blockIdx.y;
+  const i64 V2 = (i64)v * v, V3 = V2 * v;
+  const int4 ijk = blocks[b];
+  // orbit index -> sorted tile triple (TA <= TB <= TC), colex like the blocks
+  if (threadIdx.x == 0) {
+    int rem = blockIdx.x, tc = 0;
+    while ((tc + 1) * (tc + 2) * (tc + 3) / 6 <= rem) ++tc;
+    rem -= tc * (tc + 1) * (tc + 2) / 6;
+    int tb = 0;
+    while ((tb + 1) * (tb + 2) / 2 <= rem) ++tb;
+    const int ta = rem - tb * (tb + 1) / 2;
+    const int T0[3] = {ta, tb, tc};
+    const int(*P)[3] = c_perm3;
+    int n = 0;
+    for (int q = 0; q < 6; ++q) {
+      const int x = T0[P[q][0]], y = T0[P[q][1]], z = T0[P[q][2]];
+      bool dup = false;
+      for (int k = 0; k < n; ++k) dup |= tcoord[k][0] == x && tcoord[k][1] == y && tcoord[k][2] == z;
+      if (!dup) {
+        tcoord[n][0] = x;
+        tcoord[n][1] = y;
+        tcoord[n][2] = z;
+        ++n;
+      }
+    }
+    // slot[k][s]: cube holding the s-th permutation of an element of cube k
+    for (int k = 0; k < n; ++k)
+      for (int q = 0; q < 6; ++q) {
+        const int x = tcoord[k][P[q][0]], y = tcoord[k][P[q][1]], z = tcoord[k][P[q][2]];
+        for (int k2 = 0; k2 < n; ++k2)
+          if (tcoord[k2][0] == x && tcoord[k2][1] == y && tcoord[k2][2] == z) slot[k][q] = k2;
+      }
+    ncube = n;
+  }
+  __syncthreads();
+  const int n = ncube;
+  const T* rb = r + b * V3;
+  const int tz = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int k = 0; k < n; ++k) {
+    const int x0 = tcoord[k][0] * TL, y0 = tcoord[k][1] * TL, z0 = tcoord[k][2] * TL;
+#pragma unroll
+    for (int x = 0; x < TL; ++x) {
+      const int gx = x0 + x, gy = y0 + ty, gz = z0 + tz;
+      cube[k][x][ty][tz] = (gx < v && gy < v && gz < v) ? rb[gx * V2 + (i64)gy * v + gz] : (T)0;
+    }
+  }
+  __syncthreads();
+  T* out = rp + b * V3;
+  const bool all_eq = ijk.x == ijk.y && ijk.y == ijk.z;
+  for (int k = 0; k < n; ++k) {
+    const int x0 = tcoord[k][0] * TL, y0 = tcoord[k][1] * TL, z0 = tcoord[k][2] * TL;
+    const int s1 = slot[k][1], s2 = slot[k][2], s3 = slot[k][3], s4 = slot[k][4], s5 = slot[k][5];
+    for (int x = 0; x < TL; ++x) {
+      const int gx = x0 + x, gy = y0 + ty, gz = z0 + tz;
+      if (gx >= v || gy >= v || gz >= v) continue;
+      // element (a,b,c) = local (x, ty, tz); the permutation (p0,p1,p2) of the labels
+      // reads local (l[p0], l[p1], l[p2]) of the cube holding that tile permutation
+      const T rabc = cube[k][x][ty][tz];
+      const T racb = cube[s1][x][tz][ty];
+      const T rbac = cube[s2][ty][x][tz];
+      const T rbca = cube[s3][ty][tz][x];
+      const T rcab = cube[s4][tz][x][ty];
+      const T rcba = cube[s5][tz][ty][x];
+      T val;
+      if (all_eq) {
+        val = (T)0;
+      } else {
+        T sym;
+        if (ijk.x == ijk.y) sym = (T)0.5 * (rabc + rbac);
+        else if (ijk.y == ijk.z) sym = (T)0.5 * (rabc + racb);
+        else sym = rabc;
+        val = sym - (rabc + racb + rbac + rbca + rcab + rcba) * (T)(1.0 / 6.0);
+      }
+      out[gx * V2 + (i64)gy * v + gz] = val;
     }
   }
 }
 
 template <typename T>
 void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStream_t s) {
-  unsigned gx = (unsigned)std::min(v * v, 1024);
-  unsigned gy = (unsigned)(n3 < 65535 ? n3 : 65535);
+  if (n3 <= 0) return;
+  const int nt = (v + kPostTL - 1) / kPostTL;
+  const unsigned norb = (unsigned)(nt * (nt + 1) * (nt + 2) / 6);
+  const size_t smem = 6 * sizeof(T) * kPostTL * kPostTL * (kPostTL + 1);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_post<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
   ++g_launch_count;
-  k_post<T><<<dim3(gx, gy), v < 256 ? (v + 31) / 32 * 32 : 256, 0, s>>>(r, rp, blocks, v, n3);
+  k_post<T><<<dim3(norb, (unsigned)n3), 256, smem, s>>>(r, rp, blocks, v);
 }
 template void launch_post<double>(const double*, double*, const int4*, int, i64, cudaStream_t);
 template void launch_post<float>(const float*, float*, const int4*, int, i64, cudaStream_t);
@@ -387,23 +476,25 @@ __global__ void k_update_t2(double* t2, const double* r2, const double* e, int o
 }
 
 template <typename T>
-__global__ void k_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, int o, int v,
-                            i64 n3, double shift) {
-  const i64 V3 = (i64)v * v * v;
-  // the denominator is assembled in FP64; the step r / eps is taken in the
+__global__ void __launch_bounds__(256) k_update_t3(T* __restrict__ t3, const T* __restrict__ rp3,
+                                                   const double* __restrict__ e, const int4* __restrict__ blocks,
+                                                   int o, int v, double shift) {
+  // block (a, blk): the slab t3[blk][a][:][:], threads 32 along c x 8 along b.
+  // The denominator is assembled in FP64; the step r / eps is taken in the
   // storage precision of T3 (FP32 storage: FP32 division, as precise as the store)
-  for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
-    const int4 ijk = blocks[b];
-    const double eo = e[ijk.x] + e[ijk.y] + e[ijk.z];
-    T* tb = t3 + b * V3;
-    const T* rb = rp3 + b * V3;
-    for (int ab = blockIdx.x; ab < v * v; ab += gridDim.x) {
-      const int a = ab / v, bb = ab - a * v;
-      const double eab = eo - e[o + a] - e[o + bb] - shift;
-      for (int c = threadIdx.x; c < v; c += blockDim.x) {
-        const T d = (T)(eab - e[o + c]);
-        tb[ab * v + c] = tb[ab * v + c] + rb[ab * v + c] / d;
-      }
+  const int a = blockIdx.x;
+  const i64 b = blockIdx.y;
+  const int4 ijk = blocks[b];
+  const double ea = e[ijk.x] + e[ijk.y] + e[ijk.z] - e[o + a] - shift;
+  const i64 V2 = (i64)v * v;
+  T* tb = t3 + (b * v + a) * V2;
+  const T* rb = rp3 + (b * v + a) * V2;
+  for (int bb = threadIdx.y; bb < v; bb += 8) {
+    const double eab = ea - e[o + bb];
+    for (int c = threadIdx.x; c < v; c += 32) {
+      const int idx = bb * v + c;
+      const T d = (T)(eab - e[o + c]);
+      tb[idx] = tb[idx] + rb[idx] / d;
     }
   }
 }
@@ -422,10 +513,9 @@ void launch_update_t12(double* t1, const double* r1, double* t2, const double* r
 template <typename T>
 void launch_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, int o, int v, i64 n3,
                       double shift, cudaStream_t s) {
-  unsigned gx = (unsigned)std::min(v * v, 1024);
-  unsigned gy = (unsigned)(n3 < 65535 ? n3 : 65535);
+  if (n3 <= 0) return;
   ++g_launch_count;
-  k_update_t3<T><<<dim3(gx, gy), v < 256 ? (v + 31) / 32 * 32 : 256, 0, s>>>(t3, rp3, e, blocks, o, v, n3, shift);
+  k_update_t3<T><<<dim3((unsigned)v, (unsigned)n3), dim3(32, 8), 0, s>>>(t3, rp3, e, blocks, o, v, shift);
 }
 template void launch_update_t3<double>(double*, const double*, const double*, const int4*, int, int,
                                        i64, double, cudaStream_t);
@@ -456,22 +546,38 @@ __device__ __forceinline__ double block_sum(double x) {
   return x;
 }
 
+// Piece p of the weighted sum: with w, segment p / P, part p % P of P equal parts
+// (P pieces per segment, so that every block of the fixed grid has work even with
+// few long segments); without w, a grid-stride slice.
+struct Pieces {
+  i64 n, seg, nseg, len;
+  int P;
+};
+__host__ __device__ inline Pieces make_pieces(i64 n, i64 seg, bool weighted, int grid) {
+  Pieces q;
+  q.n = n;
+  q.seg = weighted ? seg : n;
+  q.nseg = weighted ? (n + seg - 1) / seg : 1;
+  const i64 per = (grid + q.nseg - 1) / q.nseg;
+  q.P = (int)(per < 1 ? 1 : per);
+  q.len = (q.seg + q.P - 1) / q.P;
+  return q;
+}
+
 template <typename T>
 __global__ void k_wdot(const T* __restrict__ x, const T* __restrict__ y, i64 n, i64 seg,
                        const double* __restrict__ w, double* __restrict__ partial) {
-  // grid-stride over segments (weight per segment), threads within a segment
+  const Pieces pc = make_pieces(n, seg, w != nullptr, gridDim.x);
   double s = 0.0;
-  if (w) {
-    const i64 nseg = (n + seg - 1) / seg;
-    for (i64 sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
-      const i64 b0 = sgi * seg, b1 = b0 + seg < n ? b0 + seg : n;
-      double ss = 0.0;
-      for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) ss += (double)x[i] * (double)y[i];
-      s += w[sgi] * ss;
-    }
-  } else {
-    for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
-      s += (double)x[i] * (double)y[i];
+  for (i64 p = blockIdx.x; p < pc.nseg * pc.P; p += gridDim.x) {
+    const i64 sg = p / pc.P, part = p % pc.P;
+    const i64 b0 = sg * pc.seg + part * pc.len;
+    i64 b1 = b0 + pc.len;
+    const i64 send = sg * pc.seg + pc.seg < n ? sg * pc.seg + pc.seg : n;
+    if (b1 > send) b1 = send;
+    double ss = 0.0;
+    for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) ss += (double)x[i] * (double)y[i];
+    s += (w ? w[sg] : 1.0) * ss;
   }
   s = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -568,31 +674,41 @@ template void launch_slot_diff_store<double>(char*, char*, i64, i64, const int*,
 template void launch_slot_diff_store<float>(char*, char*, i64, i64, const int*, const float*, i64, cudaStream_t);
 
 // partial[q][block] = sum_x w(x) e_s[x] e_q[x] for q < st[3] (0 otherwise); weights
-// per segment of `seg` elements when w is given.  Fixed grid: deterministic.
+// per segment of `seg` elements when w is given.  One pass: e_s is read once and
+// every e_q once.  Fixed grid and pieces: deterministic.
 template <typename T>
 __global__ void k_diis_dots(const char* __restrict__ hist_e, i64 stride, i64 off, const int* __restrict__ st, int M,
                             i64 n, i64 seg, const double* __restrict__ w, double* __restrict__ partial) {
   const int m = st[3];
   const T* es = (const T*)(hist_e + (i64)st[2] * stride + off);
-  for (int q = 0; q < M; ++q) {
-    double s = 0.0;
-    if (q < m) {
-      const T* eq = (const T*)(hist_e + (i64)q * stride + off);
-      if (w) {
-        const i64 nseg = (n + seg - 1) / seg;
-        for (i64 sgi = blockIdx.x; sgi < nseg; sgi += gridDim.x) {
-          const i64 b0 = sgi * seg, b1 = b0 + seg < n ? b0 + seg : n;
-          double ss = 0.0;
-          for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) ss += (double)es[i] * (double)eq[i];
-          s += w[sgi] * ss;
-        }
-      } else {
-        for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
-          s += (double)es[i] * (double)eq[i];
-      }
+  const Pieces pc = make_pieces(n, seg, w != nullptr, gridDim.x);
+  double s[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) s[q] = 0.0;
+  for (i64 p = blockIdx.x; p < pc.nseg * pc.P; p += gridDim.x) {
+    const i64 sg = p / pc.P, part = p % pc.P;
+    const i64 b0 = sg * pc.seg + part * pc.len;
+    i64 b1 = b0 + pc.len;
+    const i64 send = sg * pc.seg + pc.seg < n ? sg * pc.seg + pc.seg : n;
+    if (b1 > send) b1 = send;
+    double ss[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) ss[q] = 0.0;
+    for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+      const double x = (double)es[i];
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (q < m) ss[q] += x * (double)((const T*)(hist_e + (i64)q * stride + off))[i];
     }
-    s = block_sum(s);
-    if (threadIdx.x == 0) partial[(i64)q * gridDim.x + blockIdx.x] = s;
+    const double wt = w ? w[sg] : 1.0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s[q] += wt * ss[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    if (q >= M) break;  // M is uniform over the block
+    const double t = block_sum(q < m ? s[q] : 0.0);
+    if (threadIdx.x == 0) partial[(i64)q * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -881,12 +997,13 @@ __global__ void __launch_bounds__(256) k_r1_t3(const T* __restrict__ S, const do
   }
 }
 
+// One block per a: the nblk partials are summed in a fixed order.
 __global__ void k_r1_reduce(const double* __restrict__ partial, int nblk, int v, double* __restrict__ out) {
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= v) return;
+  const int a = blockIdx.x;
   double s = 0.0;
-  for (int q = 0; q < nblk; ++q) s += partial[(i64)q * v + a];
-  out[a] += s;
+  for (int q = threadIdx.x; q < nblk; q += blockDim.x) s += partial[(i64)q * v + a];
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[a] += s;
 }
 
 template <typename T>
@@ -898,7 +1015,7 @@ void launch_r1_t3(const T* S, const double* oovv, int o, int v, double* dR1_z, d
   ++g_launch_count;
   k_r1_t3<T><<<nblk, 256, 0, s>>>(S, oovv, o, v, scratch);
   ++g_launch_count;
-  k_r1_reduce<<<(v + 127) / 128, 128, 0, s>>>(scratch, nblk, v, dR1_z);
+  k_r1_reduce<<<v, 256, 0, s>>>(scratch, nblk, v, dR1_z);
 }
 template void launch_r1_t3<double>(const double*, const double*, int, int, double*, double*, i64, cudaStream_t);
 template void launch_r1_t3<float>(const float*, const double*, int, int, double*, double*, i64, cudaStream_t);

@@ -165,7 +165,8 @@ struct GemmPlan {
   EpiPlan E;
   int K = 0, Kpad = 0;
   double fma = 0;
-  int big = 0;          // candidate for the tensor-core engine in split modes
+  int big = 0;          // large contraction (reported; every contraction runs split in split modes)
+  int f64_only = 0;     // always FP64 (the bare integrals of the energy and the MP2 guess)
   int step = 0;         // timing bucket
   int reuse_A = 0;      // the A panel packed by the previous plan of the group is still valid
   int reuse_B = 0;      // likewise for the B panel
@@ -191,6 +192,7 @@ struct rccsdt_ctx {
   std::string err;
   int have_ham = 0, have_amp = 0, have_int = 0, have_res = 0;
   int timing = 0;
+  int concurrent = 0;  // other contexts share the GPU (batch): GEMMs keep their natural grids
   double step_ms[16] = {0};
   // event pool for non-blocking interval timing: tag < 16 = step slots, 16 = GEMM engine
   std::vector<cudaEvent_t> ev;
@@ -525,7 +527,10 @@ static void timer_collect(rccsdt_ctx* c, double* out_ms, double* gemm_launches, 
 // Engine: run one GemmPlan
 // ---------------------------------------------------------------------------
 static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
-  const bool tc = c->precision != RCCSDT_FP64 && g->big;
+  // in the split modes every contraction runs as a split product on the tensor
+  // cores (FP64 throughput on this part is 2 FMA per clock per SM), except the
+  // bare integrals that define the energy
+  const bool tc = c->precision != RCCSDT_FP64 && !g->f64_only;
   const int kind = !tc ? rcc::PANEL_F64 : (c->precision == RCCSDT_SPLIT_BF16X3 ? rcc::PANEL_BF16X2 : rcc::PANEL_TF32X2);
   rcc::PackArgs pa = g->A.a, pb = g->B.a;
   pa.kind = pb.kind = kind;
@@ -539,12 +544,12 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   const int tidx = g->step == 1 ? timer_begin(c, 16, 2.0 * g->fma) : -1;
   if (!tc) {
     rcc::launch_gemm_f64((const double*)pa.out_hi, (const double*)pb.out_hi, round_up(g->K, 16), g->Kpad, g->Kpad,
-                         g->E.e, c->splitk->d(), (i64)(c->splitk->bytes / 8), c->stream);
+                         g->E.e, c->concurrent ? nullptr : c->splitk->d(), (i64)(c->splitk->bytes / 8), c->stream);
   } else {
     int* flag = (int*)((double*)c->scalars->p + 1000);
     float* raw = g->s3_rows > 0 && c->rawX ? (float*)c->rawX->p : nullptr;
     if (rcc::launch_gemm_tc(kind, pa.out_hi, pa.out_lo, pb.out_hi, pb.out_lo, g->Kpad, g->E.e, flag,
-                            c->opt.watchdog_cycles, c->stream, (float*)c->splitk->p,
+                            c->opt.watchdog_cycles, c->stream, c->concurrent ? nullptr : (float*)c->splitk->p,
                             (long long)(c->splitk->bytes / 4), raw))
       return fail(c, RCCSDT_ERR_ARG, "tensor-core GEMM configuration unsupported");
     if (raw) {
@@ -740,6 +745,7 @@ int build_context(rccsdt_ctx* c) {
   // bare (ia|jb) for the energy and the MP2 guess
   b.ct(c->p_energy_bare, "Pia,Pjb->iajb", 1.0, sub(sub(L, 1, O0, o), 2, V0, v), sub(sub(L, 1, O0, o), 2, V0, v),
        b.T("ovov_bare", {o, v, o, v}));
+  for (GemmPlan* g : c->p_energy_bare) g->f64_only = 1;
 
   // --- (i) T1 dressing: Lt = (1 - t1) L (1 + t1), ft = (1 - t1) [f + G(t1)] (1 + t1)
   c->c_Lt_copy = combine(Lt, 0.0, {{1.0, L}});
@@ -1969,6 +1975,7 @@ cudaStream_t ctx_stream(const rccsdt_ctx* c) { return c->stream; }
 void ctx_set_stream(rccsdt_ctx* c, cudaStream_t s) { c->stream = s; }
 int ctx_main_precision(const rccsdt_ctx* c) { return c->opt.precision; }
 void ctx_reset_precision(rccsdt_ctx* c) { c->precision = c->opt.precision; }
+void ctx_set_concurrent(rccsdt_ctx* c, int on) { c->concurrent = on; }
 void ctx_begin_capture(rccsdt_ctx* c) {
   c->packedA_kind = c->packedB_kind = -1;
   c->timing = 0;

@@ -58,9 +58,11 @@ def test_batch_equals_single_solves_fp64(kind):
     for q, inst in enumerate(insts):
         (e1, it1, n1, conv), t_single = _single(lib, inst, **opt)
         assert conv
+        # batched contexts keep each GEMM on its natural grid (no K split across all
+        # SMs), so sums may be ordered differently than in a lone context
         assert it[q] == it1, (q, it[q], it1)
-        assert e[q] == e1, (q, e[q], e1)            # same kernels, same order: bit for bit
-        assert nrm[q] == n1
+        assert abs(e[q] - e1) < 1e-11, (q, e[q], e1)
+        assert abs(nrm[q] - n1) < 1e-12
         # amplitudes left in the batch context: the ones the last residual was evaluated at
         t_batch = b.instances[q].amplitudes()
         assert nrm[q] <= 1e-10
@@ -100,7 +102,7 @@ def test_batch_split_precision(kind, prec):
     assert (st == B.OK).all(), st
     for q, inst in enumerate(insts):
         (e1, it1, n1, conv), _ = _single(lib, inst, **opt)
-        assert it[q] == it1 and e[q] == e1, (q, it[q], it1, e[q], e1)
+        assert it[q] == it1 and abs(e[q] - e1) < 1e-9, (q, it[q], it1, e[q], e1)
         E0 = oc.solve_compact(inst.L, inst.fock_diag, inst.o, tol=1e-10, max_iter=300)[0]
         assert abs(e[q] - E0) < 1e-6
     b.close()
@@ -122,7 +124,7 @@ def test_batch_max_iter_stops_one_instance(kind):
         if it[q] == need:
             assert st2[q] == B.NOT_CONVERGED and it2[q] == need - 1
         else:
-            assert st2[q] == B.OK and e2[q] == e[q]
+            assert st2[q] == B.OK and abs(e2[q] - e[q]) < 1e-12
     b.close()
 
 

@@ -352,31 +352,28 @@ constexpr int kPostTL = 16;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __restrict__ rp,
-                                              const int4* __restrict__ blocks, int v) {
+                                              const int4* __restrict__ blocks, int v, i64 n3) {
   constexpr int TL = kPostTL;
-  typedef T Cube[TL][TL][TL + 1];
+  // [16][17][17]: odd strides on both outer axes keep the permuted reads below 2-way bank conflicts
+  typedef T Cube[TL][TL + 1][TL + 1];
   extern __shared__ __align__(16) unsigned char post_smem[];
   Cube* cube = reinterpret_cast<Cube*>(post_smem);
   __shared__ int tcoord[6][3];
   __shared__ int slot[6][6];
   __shared__ int ncube;
-  const int nt = (v + TL - 1) / TL;
-  const i64 b = blockIdx.y;
   const i64 V2 = (i64)v * v, V3 = V2 * v;
-  const int4 ijk = blocks[b];
-  // orbit index -> sorted tile triple (TA <= TB <= TC), colex like the blocks
+  // orbit index -> sorted tile triple (TA <= TB <= TC), colex like the blocks; the
+  // orbit's distinct cubes and, per cube and label permutation, the cube holding it
   if (threadIdx.x == 0) {
     int rem = blockIdx.x, tc = 0;
     while ((tc + 1) * (tc + 2) * (tc + 3) / 6 <= rem) ++tc;
     rem -= tc * (tc + 1) * (tc + 2) / 6;
     int tb = 0;
     while ((tb + 1) * (tb + 2) / 2 <= rem) ++tb;
-    const int ta = rem - tb * (tb + 1) / 2;
-    const int T0[3] = {ta, tb, tc};
-    const int(*P)[3] = c_perm3;
+    const int T0[3] = {rem - tb * (tb + 1) / 2, tb, tc};
     int n = 0;
     for (int q = 0; q < 6; ++q) {
-      const int x = T0[P[q][0]], y = T0[P[q][1]], z = T0[P[q][2]];
+      const int x = T0[c_perm3[q][0]], y = T0[c_perm3[q][1]], z = T0[c_perm3[q][2]];
       bool dup = false;
       for (int k = 0; k < n; ++k) dup |= tcoord[k][0] == x && tcoord[k][1] == y && tcoord[k][2] == z;
       if (!dup) {
@@ -386,55 +383,65 @@ __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __rest
         ++n;
       }
     }
-    // slot[k][s]: cube holding the s-th permutation of an element of cube k
-    for (int k = 0; k < n; ++k)
-      for (int q = 0; q < 6; ++q) {
-        const int x = tcoord[k][P[q][0]], y = tcoord[k][P[q][1]], z = tcoord[k][P[q][2]];
-        for (int k2 = 0; k2 < n; ++k2)
-          if (tcoord[k2][0] == x && tcoord[k2][1] == y && tcoord[k2][2] == z) slot[k][q] = k2;
-      }
     ncube = n;
   }
   __syncthreads();
-  const int n = ncube;
-  const T* rb = r + b * V3;
-  const int tz = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  for (int k = 0; k < n; ++k) {
-    const int x0 = tcoord[k][0] * TL, y0 = tcoord[k][1] * TL, z0 = tcoord[k][2] * TL;
-#pragma unroll
-    for (int x = 0; x < TL; ++x) {
-      const int gx = x0 + x, gy = y0 + ty, gz = z0 + tz;
-      cube[k][x][ty][tz] = (gx < v && gy < v && gz < v) ? rb[gx * V2 + (i64)gy * v + gz] : (T)0;
+  if (threadIdx.x < 36) {
+    const int k = threadIdx.x / 6, q = threadIdx.x % 6;
+    if (k < ncube) {
+      const int x = tcoord[k][c_perm3[q][0]], y = tcoord[k][c_perm3[q][1]], z = tcoord[k][c_perm3[q][2]];
+      for (int k2 = 0; k2 < ncube; ++k2)
+        if (tcoord[k2][0] == x && tcoord[k2][1] == y && tcoord[k2][2] == z) slot[k][q] = k2;
     }
   }
   __syncthreads();
-  T* out = rp + b * V3;
-  const bool all_eq = ijk.x == ijk.y && ijk.y == ijk.z;
-  for (int k = 0; k < n; ++k) {
-    const int x0 = tcoord[k][0] * TL, y0 = tcoord[k][1] * TL, z0 = tcoord[k][2] * TL;
-    const int s1 = slot[k][1], s2 = slot[k][2], s3 = slot[k][3], s4 = slot[k][4], s5 = slot[k][5];
-    for (int x = 0; x < TL; ++x) {
-      const int gx = x0 + x, gy = y0 + ty, gz = z0 + tz;
-      if (gx >= v || gy >= v || gz >= v) continue;
-      // element (a,b,c) = local (x, ty, tz); the permutation (p0,p1,p2) of the labels
-      // reads local (l[p0], l[p1], l[p2]) of the cube holding that tile permutation
-      const T rabc = cube[k][x][ty][tz];
-      const T racb = cube[s1][x][tz][ty];
-      const T rbac = cube[s2][ty][x][tz];
-      const T rbca = cube[s3][ty][tz][x];
-      const T rcab = cube[s4][tz][x][ty];
-      const T rcba = cube[s5][tz][ty][x];
-      T val;
-      if (all_eq) {
-        val = (T)0;
-      } else {
-        T sym;
-        if (ijk.x == ijk.y) sym = (T)0.5 * (rabc + rbac);
-        else if (ijk.y == ijk.z) sym = (T)0.5 * (rabc + racb);
-        else sym = rabc;
-        val = sym - (rabc + racb + rbac + rbca + rcab + rcba) * (T)(1.0 / 6.0);
+  const int n = ncube;
+  const int tz = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
+    const int4 ijk = blocks[b];
+    const T* rb = r + b * V3;
+    __syncthreads();  // the previous block's cubes are consumed
+    for (int k = 0; k < n; ++k) {
+      const int x0 = tcoord[k][0] * TL, gy = tcoord[k][1] * TL + ty, gz = tcoord[k][2] * TL + tz;
+      const bool in = gy < v && gz < v;
+      const T* src = rb + (i64)gy * v + gz;
+      T ld[TL];
+#pragma unroll
+      for (int x = 0; x < TL; ++x) ld[x] = (in && x0 + x < v) ? src[(i64)(x0 + x) * V2] : (T)0;
+#pragma unroll
+      for (int x = 0; x < TL; ++x) cube[k][x][ty][tz] = ld[x];
+    }
+    __syncthreads();
+    T* out = rp + b * V3;
+    const bool all_eq = ijk.x == ijk.y && ijk.y == ijk.z;
+    for (int k = 0; k < n; ++k) {
+      const int x0 = tcoord[k][0] * TL, gy = tcoord[k][1] * TL + ty, gz = tcoord[k][2] * TL + tz;
+      if (gy >= v || gz >= v) continue;
+      const int s1 = slot[k][1], s2 = slot[k][2], s3 = slot[k][3], s4 = slot[k][4], s5 = slot[k][5];
+      T* dst = out + (i64)gy * v + gz;
+#pragma unroll 4
+      for (int x = 0; x < TL; ++x) {
+        if (x0 + x >= v) break;
+        // element (a,b,c) = local (x, ty, tz); the label permutation (p0,p1,p2) is
+        // local (l[p0], l[p1], l[p2]) of the cube holding that tile permutation
+        const T rabc = cube[k][x][ty][tz];
+        const T racb = cube[s1][x][tz][ty];
+        const T rbac = cube[s2][ty][x][tz];
+        const T rbca = cube[s3][ty][tz][x];
+        const T rcab = cube[s4][tz][x][ty];
+        const T rcba = cube[s5][tz][ty][x];
+        T val;
+        if (all_eq) {
+          val = (T)0;
+        } else {
+          T sym;
+          if (ijk.x == ijk.y) sym = (T)0.5 * (rabc + rbac);
+          else if (ijk.y == ijk.z) sym = (T)0.5 * (rabc + racb);
+          else sym = rabc;
+          val = sym - (rabc + racb + rbac + rbca + rcab + rcba) * (T)(1.0 / 6.0);
+        }
+        dst[(i64)(x0 + x) * V2] = val;
       }
-      out[gx * V2 + (i64)gy * v + gz] = val;
     }
   }
 }
@@ -443,15 +450,17 @@ template <typename T>
 void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStream_t s) {
   if (n3 <= 0) return;
   const int nt = (v + kPostTL - 1) / kPostTL;
-  const unsigned norb = (unsigned)(nt * (nt + 1) * (nt + 2) / 6);
-  const size_t smem = 6 * sizeof(T) * kPostTL * kPostTL * (kPostTL + 1);
+  const int norb = nt * (nt + 1) * (nt + 2) / 6;
+  // about 2048 CTAs; each keeps its orbit tables across the blocks it visits
+  const i64 gy = std::max<i64>(1, std::min<i64>(n3, (2048 + norb - 1) / norb));
+  const size_t smem = 6 * sizeof(T) * kPostTL * (kPostTL + 1) * (kPostTL + 1);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_post<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   ++g_launch_count;
-  k_post<T><<<dim3(norb, (unsigned)n3), 256, smem, s>>>(r, rp, blocks, v);
+  k_post<T><<<dim3((unsigned)norb, (unsigned)gy), 256, smem, s>>>(r, rp, blocks, v, n3);
 }
 template void launch_post<double>(const double*, double*, const int4*, int, i64, cudaStream_t);
 template void launch_post<float>(const float*, float*, const int4*, int, i64, cudaStream_t);
@@ -906,47 +915,66 @@ __global__ void __launch_bounds__(256) k_unpack_spin(const void* __restrict__ t3
   const int nt = (v + TL - 1) / TL;
   const i64 V3 = (i64)v * v * v;
   const i64 sv[3] = {(i64)v * v, v, 1};
+  const int lf = threadIdx.x & 15, lm = threadIdx.x >> 4;  // lane along the fast slot, row along the middle slot
   for (int t = blockIdx.y; t < ntrip; t += gridDim.y) {
     const i64 b0 = base[t];
     const int p[3] = {pos[3 * t], pos[3 * t + 1], pos[3 * t + 2]};
-    const i64 st[3] = {sv[p[0]], sv[p[1]], sv[p[2]]};
-    // slot (position) whose label runs along the stored unit-stride axis
+    const i64 st[3] = {p[0] == 0 ? sv[0] : (p[0] == 1 ? sv[1] : sv[2]), p[1] == 0 ? sv[0] : (p[1] == 1 ? sv[1] : sv[2]),
+                       p[2] == 0 ? sv[0] : (p[2] == 1 ? sv[1] : sv[2])};
+    // slot (position) whose label runs along the stored unit-stride axis, and the other two
     const int fast = p[0] == 2 ? 0 : (p[1] == 2 ? 1 : 2);
+    const int mid = (fast + 1) % 3, slow = (fast + 2) % 3;
     for (int tile = blockIdx.x; tile < nt * nt * nt; tile += gridDim.x) {
-      const int ta = tile / (nt * nt), tb = (tile / nt) % nt, tc = tile % nt;
-      const int lo[3] = {ta * TL, tb * TL, tc * TL};
+      const int lo[3] = {(tile / (nt * nt)) * TL, ((tile / nt) % nt) * TL, (tile % nt) * TL};
+      (void)sv;
       // term q reads U at slots (x0, x1, x2) whose label ranges are, in output label order:
       //   q=0: (a, b, c)   q=1: (b, a, c)   q=2: (c, b, a)
-      const int rng[3][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0}};
+      auto label = [](int q, int slot_) {
+        return q == 0 ? slot_ : (q == 1 ? (slot_ == 2 ? 2 : 1 - slot_) : 2 - slot_);
+      };
+      auto sel3 = [](int i, int x0, int x1, int x2) { return i == 0 ? x0 : (i == 1 ? x1 : x2); };
+      auto sel3l = [](int i, i64 x0, i64 x1, i64 x2) { return i == 0 ? x0 : (i == 1 ? x1 : x2); };
+      const i64 sf = sel3l(fast, st[0], st[1], st[2]), sm = sel3l(mid, st[0], st[1], st[2]),
+                ss = sel3l(slow, st[0], st[1], st[2]);
+      // shared offsets of the slots in a [TL][TL+1][TL+2] cube
+      const int cf = sel3(fast, (TL + 1) * (TL + 2), TL + 2, 1), cm = sel3(mid, (TL + 1) * (TL + 2), TL + 2, 1),
+                cs = sel3(slow, (TL + 1) * (TL + 2), TL + 2, 1);
       __syncthreads();
       for (int q = 0; q < 3; ++q) {
-        for (int e = threadIdx.x; e < TL * TL * TL; e += blockDim.x) {
-          int u[3];
-          // the fast slot varies fastest across threads
-          const int s1 = (fast + 1) % 3, s2 = (fast + 2) % 3;
-          u[fast] = e % TL;
-          u[s1] = (e / TL) % TL;
-          u[s2] = e / (TL * TL);
-          const int x0 = lo[rng[q][0]] + u[0], x1 = lo[rng[q][1]] + u[1], x2 = lo[rng[q][2]] + u[2];
+        const int xf = sel3(label(q, fast), lo[0], lo[1], lo[2]) + lf;
+        const int xm = sel3(label(q, mid), lo[0], lo[1], lo[2]) + lm;
+        const int xs0 = sel3(label(q, slow), lo[0], lo[1], lo[2]);
+        const bool in = xf < v && xm < v;
+        const i64 off0 = b0 + xf * sf + xm * sm + xs0 * ss;
+        T ld[TL];
+#pragma unroll
+        for (int u = 0; u < TL; ++u) {
           T val = (T)0;
-          if (x0 < v && x1 < v && x2 < v) {
-            const i64 off = b0 + x0 * st[0] + x1 * st[1] + x2 * st[2];
+          if (in && xs0 + u < v) {
+            const i64 off = off0 + u * ss;
             if constexpr (sizeof(T) == 4)
               val = ((const float*)t3)[off];  // FP32 storage: no FP64 conversions
             else
               val = (T)load_src(t3, f32, off);
           }
-          cube[q][u[0]][u[1]][u[2]] = val;
+          ld[u] = val;
         }
+        T* cq = &cube[q][0][0][0] + lf * cf + lm * cm;
+#pragma unroll
+        for (int u = 0; u < TL; ++u) cq[u * cs] = ld[u];
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < TL * TL * TL; e += blockDim.x) {
-        const int c = e % TL, bb = (e / TL) % TL, a = e / (TL * TL);
-        const int ga = lo[0] + a, gb = lo[1] + bb, gc = lo[2] + c;
-        if (ga < v && gb < v && gc < v) {
+      // S along c: thread (bb, c), loop a
+      const int bb = threadIdx.x >> 4, c = threadIdx.x & 15;
+      const int gb = lo[1] + bb, gc = lo[2] + c;
+      if (gb < v && gc < v) {
+        T* dst = S + (i64)t * V3 + (i64)gb * v + gc;
+#pragma unroll 4
+        for (int a = 0; a < TL; ++a) {
+          const int ga = lo[0] + a;
+          if (ga >= v) break;
           // U^{abc} = cube0[a][b][c], U^{bac} = cube1[b][a][c], U^{cba} = cube2[c][b][a]
-          const T s_ = (T)2 * cube[0][a][bb][c] - cube[1][bb][a][c] - cube[2][c][bb][a];
-          S[(i64)t * V3 + ((i64)ga * v + gb) * v + gc] = s_;
+          dst[(i64)ga * v * v] = (T)2 * cube[0][a][bb][c] - cube[1][bb][a][c] - cube[2][c][bb][a];
         }
       }
     }

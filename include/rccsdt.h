@@ -74,7 +74,8 @@ typedef struct {
                                 once); when an instance needs more, or 0, its contractions
                                 run one by one through shared panels */
   int autotune;              /* 1: time candidate launch shapes of the grouped GEMM on the
-                                first iteration and keep the fastest; 0: fixed shape */
+                                first iteration and keep the fastest; 0: fixed shape;
+                                2 + i: always candidate i (0..5) of the autotuner's list */
 } rccsdt_options;
 
 /* Fills *opt with the defaults: FP64, final_fp64_iters 2, DIIS(8) from iteration 2
@@ -162,7 +163,10 @@ long long rccsdt_kernel_launches(void);
 /* Contraction engine of the context: out[0] 1 if the grouped residual is on,
  * [1] its GEMM problems, [2] their output tiles, [3] operand gathers, [4] block
  * contributions reduced into R3, [5] device bytes it holds, [6] persistent grid
- * of its GEMM launch (0 = one CTA per SM), [7] panel kind.  Returns entries written. */
+ * of its GEMM launch (0 = one CTA per SM), [7] panel kind, [8] tile width,
+ * [9] problem order (0 longest K first, 1 plan order), [10] 1 once the autotuner
+ * has run, [11] its chosen shape's GEMM time and [12] the fixed shape's (256-wide
+ * tiles, longest K first, one CTA per SM), in microseconds.  Returns entries written. */
 int rccsdt_engine_info(const rccsdt_ctx* ctx, long long* out, int cap);
 
 /* Diagnostic: copies the first `count` float64 values of a named internal tensor

@@ -203,9 +203,10 @@ class Context:
         return out
 
     def engine_info(self):
-        out = np.zeros(8, dtype=np.int64)
-        k = self.lib.rccsdt_engine_info(self.h, out.ctypes.data, 8)
-        keys = ["grouped", "problems", "tiles", "gathers", "contributions", "bytes", "grid", "kind"]
+        out = np.zeros(13, dtype=np.int64)
+        k = self.lib.rccsdt_engine_info(self.h, out.ctypes.data, 13)
+        keys = ["grouped", "problems", "tiles", "gathers", "contributions", "bytes", "grid", "kind", "bn", "order",
+                "tuned", "tuned_us", "fixed_us"]
         return dict(zip(keys[:k], out[:k].tolist()))
 
     def enable_timing(self, on=True):

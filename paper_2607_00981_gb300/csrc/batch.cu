@@ -356,6 +356,11 @@ RCC_API int rccsdt_batch_solve(rccsdt_batch* b, double* e_corr, int* iterations,
     const int st = rcc::ctx_ready(b->inst[i]);
     if (st) return bfail(b, st, std::string("instance ") + std::to_string(i) + ": " + rccsdt_last_error(b->inst[i]));
   }
+  if (!b->built)
+    for (int i = 0; i < n; ++i) {
+      const int st = rcc::ctx_prepare(b->inst[i]);
+      if (st) return bfail(b, st, std::string("instance ") + std::to_string(i) + ": " + rccsdt_last_error(b->inst[i]));
+    }
   b->state.assign(n, InstState());
   b->launches = b->kernels = 0;
   b->device_ms = b->flop = 0.0;

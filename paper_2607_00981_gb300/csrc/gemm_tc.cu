@@ -32,12 +32,19 @@
 namespace rcc {
 namespace {
 
-constexpr int BM = 128, BN = 256, STAGES = 2;
+constexpr int BM = 128, STAGES = 2;
 constexpr int ROWB = 128;                      // bytes of one K-row of a tile (swizzle span)
-constexpr int A_PLANE = BM * ROWB, B_PLANE = BN * ROWB;
-constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;  // 96 KiB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int A_PLANE = BM * ROWB;
 constexpr int kThreads = 192;
+
+// Tile width BN (256 or 128 columns): B planes, stage and shared-memory sizes.
+template <int BN>
+struct TileCfg {
+  static constexpr int B_PLANE = BN * ROWB;
+  static constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;  // 96 KiB for BN = 256
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int TMEM_COLS = 2 * BN;                        // double-buffered accumulator
+};
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -89,22 +96,22 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 }
 
 // Instruction descriptor: D = F32, A = B = fmt (1 BF16, 2 TF32), both K-major, N = BN, M = BM.
-__host__ __device__ constexpr uint32_t idesc(uint32_t fmt) {
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, int BN) {
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-template <int FMT>
+template <int FMT, int BN>
 __device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
   if constexpr (FMT == 1) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             d),
-        "l"(a), "l"(b), "r"(idesc(1)), "r"(acc));
+        "l"(a), "l"(b), "r"(idesc(1, BN)), "r"(acc));
   } else {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             d),
-        "l"(a), "l"(b), "r"(idesc(2)), "r"(acc));
+        "l"(a), "l"(b), "r"(idesc(2, BN)), "r"(acc));
   }
 }
 
@@ -265,9 +272,11 @@ struct GroupSched {
   }
 };
 
-template <int FMT, class S>
+template <int FMT, int BN, class S>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ S sch, int* __restrict__ status, long long budget) {
+  constexpr int B_PLANE = TileCfg<BN>::B_PLANE, STAGE_BYTES = TileCfg<BN>::STAGE_BYTES;
+  constexpr int TMEM_COLS = TileCfg<BN>::TMEM_COLS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                 "r"(512)
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -376,9 +385,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int j = 0; j < ROWB / 32; ++j) {
             const uint64_t adv = (uint64_t)(j * 32 >> 4);  // 32-byte K slice inside the swizzled row
-            umma<FMT>(d, ah + adv, bh + adv, (kb > x.kb0 || j > 0) ? 1u : 0u);
-            umma<FMT>(d, ah + adv, bl + adv, 1u);
-            umma<FMT>(d, al + adv, bh + adv, 1u);
+            umma<FMT, BN>(d, ah + adv, bh + adv, (kb > x.kb0 || j > 0) ? 1u : 0u);
+            umma<FMT, BN>(d, ah + adv, bl + adv, 1u);
+            umma<FMT, BN>(d, al + adv, bh + adv, 1u);
           }
           umma_commit(&empty[s]);
           if (++s == STAGES) {
@@ -429,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   fence_after();
   if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
@@ -481,21 +490,34 @@ int num_sms() {
 
 }  // namespace
 
-template <int FMT, class S>
+template <int FMT, int BN, class S>
 static void launch_sched(const S& sch, int grid, int* status_flag, long long budget, cudaStream_t s) {
+  constexpr int SMEM = TileCfg<BN>::SMEM_BYTES;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc<FMT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<FMT, BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     attr = true;
   }
   ++g_launch_count;
-  k_gemm_tc<FMT, S><<<grid, kThreads, SMEM_BYTES, s>>>(sch, status_flag, budget);
+  k_gemm_tc<FMT, BN, S><<<grid, kThreads, SMEM, s>>>(sch, status_flag, budget);
+}
+
+template <class S>
+static void launch_any(int kind, int bn, const S& sch, int grid, int* status_flag, long long budget, cudaStream_t s) {
+  if (kind == PANEL_BF16X2) {
+    if (bn == 128) launch_sched<1, 128>(sch, grid, status_flag, budget, s);
+    else launch_sched<1, 256>(sch, grid, status_flag, budget, s);
+  } else {
+    if (bn == 128) launch_sched<2, 128>(sch, grid, status_flag, budget, s);
+    else launch_sched<2, 256>(sch, grid, status_flag, budget, s);
+  }
 }
 
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int Kpad,
                    const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s, float* scratch,
-                   long long scratch_elems, float* raw_out) {
+                   long long scratch_elems, float* raw_out, int bn) {
   if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
+  const int BN = bn == 128 ? 128 : 256;
   const int esz = kind == PANEL_BF16X2 ? 2 : 4;
   const int bk = ROWB / esz;
   if (Kpad % bk != 0 || e.M <= 0 || e.N <= 0) return 1;
@@ -523,10 +545,7 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
   float* part = raw_out ? raw_out : (g.splitk > 1 ? scratch : nullptr);
   sch.e = e;
   sch.partial = part;
-  if (kind == PANEL_BF16X2)
-    launch_sched<1>(sch, grid, status_flag, budget, s);
-  else
-    launch_sched<2>(sch, grid, status_flag, budget, s);
+  launch_any(kind, BN, sch, grid, status_flag, budget, s);
   if (part && !raw_out) {
     const long long MN = (long long)e.M * e.N;
     long long blocks = (MN + 255) / 256;
@@ -540,8 +559,9 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
 int gemm_tc_block_k(int kind) { return ROWB / (kind == PANEL_BF16X2 ? 2 : 4); }
 
 int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int M,
-                  int N, int Kpad, float* out) {
+                  int N, int Kpad, float* out, int bn) {
   if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
+  const int BN = bn == 128 ? 128 : 256;
   const int bk = gemm_tc_block_k(kind);
   if (Kpad % bk != 0 || M <= 0 || N <= 0) return 1;
   if (!make_map(&p->ah, Ahi, M, Kpad, kind, BM) || !make_map(&p->al, Alo, M, Kpad, kind, BM) ||
@@ -563,8 +583,8 @@ int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const
 
 int gproblem_tiles(const GProblem& p) { return p.mt * p.nt; }
 
-int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total_tiles, int grid, int* status_flag,
-                           long long watchdog, cudaStream_t s) {
+int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total_tiles, int grid, int bn,
+                           int* status_flag, long long watchdog, cudaStream_t s) {
   if ((kind != PANEL_BF16X2 && kind != PANEL_TF32X2) || nprob <= 0 || total_tiles <= 0) return 1;
   GroupSched sch;
   sch.probs = probs;
@@ -572,10 +592,7 @@ int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total
   sch.total = total_tiles;
   const int g = std::max(1, std::min(grid > 0 ? grid : num_sms(), total_tiles));
   const long long budget = watchdog > 0 ? watchdog : 4000000000LL;
-  if (kind == PANEL_BF16X2)
-    launch_sched<1>(sch, g, status_flag, budget, s);
-  else
-    launch_sched<2>(sch, g, status_flag, budget, s);
+  launch_any(kind, bn == 128 ? 128 : 256, sch, g, status_flag, budget, s);
   return 0;
 }
 

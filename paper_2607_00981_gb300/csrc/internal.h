@@ -26,6 +26,9 @@ void ctx_set_concurrent(rccsdt_ctx* c, int on);
 void ctx_begin_capture(rccsdt_ctx* c);
 // 0 when the Hamiltonian and amplitudes are set, else an rccsdt_status.
 int ctx_ready(rccsdt_ctx* c);
+// Runs what must not happen inside a graph capture (the grouped GEMM's autotuner,
+// on one eager evaluation) when the context asks for it; 0 otherwise.
+int ctx_prepare(rccsdt_ctx* c);
 int ctx_dims(const rccsdt_ctx* c, int* o, int* v);
 
 }  // namespace rcc

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) k_r3_gather(const float* __restrict__ X, 
                                                    const int* __restrict__ cstart, const i64* __restrict__ xoff,
                                                    const int* __restrict__ csel, const float* __restrict__ calpha,
                                                    int v, int accumulate, T* __restrict__ r3) {
-  __shared__ float xs[16][16][17];
+  __shared__ float xs[16][17][17];  // odd outer strides: permuted reads stay below 2-way conflicts
   const int nc = (v + 15) / 16;
   const int cube = blockIdx.x, t = blockIdx.y;
   const int y0[3] = {(cube / (nc * nc)) * 16, ((cube / nc) % nc) * 16, (cube % nc) * 16};
@@ -567,10 +567,31 @@ __host__ __device__ inline Pieces make_pieces(i64 n, i64 seg, bool weighted, int
   q.n = n;
   q.seg = weighted ? seg : n;
   q.nseg = weighted ? (n + seg - 1) / seg : 1;
-  const i64 per = (grid + q.nseg - 1) / q.nseg;
+  // about 16 pieces per block (balanced tail), each of at least 2048 elements
+  i64 per = (16LL * grid + q.nseg - 1) / q.nseg;
+  const i64 cap = (q.seg + 2047) / 2048;
+  if (per > cap) per = cap;
   q.P = (int)(per < 1 ? 1 : per);
   q.len = (q.seg + q.P - 1) / q.P;
   return q;
+}
+
+// sum_i x[i] y[i] over [b0, b1) by this block's threads, four loads in flight each
+template <typename T>
+__device__ __forceinline__ double dot_range(const T* __restrict__ x, const T* __restrict__ y, i64 b0, i64 b1) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const i64 step = blockDim.x;
+  i64 i = b0 + threadIdx.x;
+  for (; i + 3 * step < b1; i += 4 * step) {
+    const T x0 = x[i], x1 = x[i + step], x2 = x[i + 2 * step], x3 = x[i + 3 * step];
+    const T y0 = y[i], y1 = y[i + step], y2 = y[i + 2 * step], y3 = y[i + 3 * step];
+    s0 += (double)x0 * (double)y0;
+    s1 += (double)x1 * (double)y1;
+    s2 += (double)x2 * (double)y2;
+    s3 += (double)x3 * (double)y3;
+  }
+  for (; i < b1; i += step) s0 += (double)x[i] * (double)y[i];
+  return (s0 + s1) + (s2 + s3);
 }
 
 template <typename T>
@@ -584,9 +605,7 @@ __global__ void k_wdot(const T* __restrict__ x, const T* __restrict__ y, i64 n, 
     i64 b1 = b0 + pc.len;
     const i64 send = sg * pc.seg + pc.seg < n ? sg * pc.seg + pc.seg : n;
     if (b1 > send) b1 = send;
-    double ss = 0.0;
-    for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) ss += (double)x[i] * (double)y[i];
-    s += (w ? w[sg] : 1.0) * ss;
+    s += (w ? w[sg] : 1.0) * dot_range<T>(x, y, b0, b1);
   }
   s = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;

@@ -74,9 +74,10 @@ void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t s);
 // `scratch` (scratch_elems floats) holds FP32 partial tiles when K is split.
 // With raw_out, the raw FP32 result is written densely to raw_out[m * N + n] (no
 // alpha, no scatter, no split-K) for a separate scatter pass.
+// bn: tile width, 256 (default) or 128 columns.
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo,
                    int Kpad, const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s,
-                   float* scratch, long long scratch_elems, float* raw_out = nullptr);
+                   float* scratch, long long scratch_elems, float* raw_out = nullptr, int bn = 256);
 // One GEMM of a grouped launch: X[M][N] = (Ahi Bhi + Ahi Blo + Alo Bhi) with A
 // [M][Kpad], B [N][Kpad] split panels; the tensor maps are encoded on the host
 // (make_gproblem) and the table is copied to device memory before the launch.
@@ -93,13 +94,13 @@ struct alignas(128) GProblem {
 };
 // Fills p (except tile0) for panels of `kind`; nonzero if unsupported.
 int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int M,
-                  int N, int Kpad, float* out);
+                  int N, int Kpad, float* out, int bn = 256);
 int gproblem_tiles(const GProblem& p);
 int gemm_tc_block_k(int kind);
 // One persistent launch over every tile of the nprob problems (device table,
-// tile0 prefix order); grid <= 0 picks one CTA per SM.
-int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total_tiles, int grid, int* status_flag,
-                           long long watchdog, cudaStream_t s);
+// tile0 prefix order, tables made with the same bn); grid <= 0 picks one CTA per SM.
+int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total_tiles, int grid, int bn,
+                           int* status_flag, long long watchdog, cudaStream_t s);
 // Second phase of a two-phase scatter: for each row m of the dense FP32 result X
 // [M][v^3] (natural (a,b,c) order), C[row_base[m] + perm_sel[m](a,b,c)] +=
 // row_alpha[m] * X[m][abc]; perm_sel indexes the 6 virtual permutations.

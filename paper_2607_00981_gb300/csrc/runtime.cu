@@ -235,7 +235,15 @@ struct rccsdt_ctx {
     double flop = 0.0;
     std::unique_ptr<DBuf> target, cstart, xoff, csel, calpha;
     int ntarget = 0;
-    std::vector<int> order;  // problem order of the launch (tile0 prefix in this order)
+    // launch shape: tile width, problem order (0 longest K first, 1 plan order), grid
+    int bn = 256, ord = 0, tuned = 0;
+    double tuned_ms = 0.0, fixed_ms = 0.0;
+    struct Src {
+      const void *ahi, *alo, *bhi, *blo;
+      int M, N, Kpad;
+      float* out;
+    };
+    std::vector<Src> src;
   } gr;
 
   // DIIS state
@@ -1172,6 +1180,36 @@ struct GPanel {
   size_t hi = 0, lo = 0;  // byte offsets in the panel arena
 };
 
+// Problem table of the grouped GEMM for tile width bn and problem order ord
+// (0: longest K first -- the persistent CTAs take tiles round robin; 1: plan order).
+int grouped_table(rccsdt_ctx* c, int bn, int ord, std::unique_ptr<DBuf>* out, int* ntiles) {
+  auto& G = c->gr;
+  const size_t n = G.src.size();
+  std::vector<rcc::GProblem> probs(n);
+  for (size_t q = 0; q < n; ++q) {
+    const auto& x = G.src[q];
+    if (rcc::make_gproblem(&probs[q], G.kind, x.ahi, x.alo, x.bhi, x.blo, x.M, x.N, x.Kpad, x.out, bn))
+      return fail(c, RCCSDT_ERR_CUDA, "grouped residual: tensor map encoding failed");
+  }
+  std::vector<int> order(n);
+  for (size_t q = 0; q < n; ++q) order[q] = (int)q;
+  if (ord == 0)
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return probs[x].kblocks > probs[y].kblocks; });
+  std::vector<rcc::GProblem> sorted;
+  int t0 = 0;
+  for (int q : order) {
+    rcc::GProblem P = probs[q];
+    P.tile0 = t0;
+    t0 += rcc::gproblem_tiles(P);
+    sorted.push_back(P);
+  }
+  int err = 0;
+  *out = upload_vec(c, sorted, &err);
+  *ntiles = t0;
+  if (err) return fail(c, RCCSDT_ERR_OOM, "grouped residual: table upload failed");
+  return 0;
+}
+
 int build_grouped(rccsdt_ctx* c) {
   auto& G = c->gr;
   G.on = 0;
@@ -1258,31 +1296,24 @@ int build_grouped(rccsdt_ctx* c) {
       G.ptile[t] = upload_vec(c, ptile[t], &err);
     }
   }
-  // problems, longest K first (the persistent CTAs take tiles round robin)
-  std::vector<rcc::GProblem> probs(plans.size());
+  // problems (kept as sources so that other launch shapes can be encoded later)
   for (size_t q = 0; q < plans.size(); ++q) {
     GemmPlan* g = plans[q];
     const GPanel &A = panels[pa[q]], &B = panels[pb[q]];
-    const int M = g->swap_ab ? g->E.e.N : g->E.e.M, N = g->swap_ab ? g->E.e.M : g->E.e.N;
-    if (rcc::make_gproblem(&probs[q], kind, base + A.hi, base + A.lo, base + B.hi, base + B.lo, M, N, g->Kpad,
-                           raw + xo[q]))
-      return fail(c, RCCSDT_ERR_CUDA, "grouped residual: tensor map encoding failed");
+    rccsdt_ctx::Grouped::Src x;
+    x.ahi = base + A.hi;
+    x.alo = base + A.lo;
+    x.bhi = base + B.hi;
+    x.blo = base + B.lo;
+    x.M = g->swap_ab ? g->E.e.N : g->E.e.M;
+    x.N = g->swap_ab ? g->E.e.M : g->E.e.N;
+    x.Kpad = g->Kpad;
+    x.out = raw + xo[q];
+    G.src.push_back(x);
   }
-  G.order.resize(plans.size());
-  for (size_t q = 0; q < plans.size(); ++q) G.order[q] = (int)q;
-  std::stable_sort(G.order.begin(), G.order.end(),
-                   [&](int x, int y) { return probs[x].kblocks > probs[y].kblocks; });
-  std::vector<rcc::GProblem> sorted;
-  int t0 = 0;
-  for (int q : G.order) {
-    rcc::GProblem P = probs[q];
-    P.tile0 = t0;
-    t0 += rcc::gproblem_tiles(P);
-    sorted.push_back(P);
-  }
-  G.nprob = (int)sorted.size();
-  G.ntiles = t0;
-  G.probs = upload_vec(c, sorted, &err);
+  G.kind = kind;
+  if (int e2 = grouped_table(c, 256, 0, &G.probs, &G.ntiles)) return e2;
+  G.nprob = (int)plans.size();
   // contributions per stored block, in plan order
   const i64 V3 = c->V3;
   std::vector<std::vector<std::array<i64, 2>>> per(c->n3);  // (xoff, q * 64 + r-th) -> resolved below
@@ -1315,9 +1346,76 @@ int build_grouped(rccsdt_ctx* c) {
   G.csel = upload_vec(c, csel, &err);
   G.calpha = upload_vec(c, calpha, &err);
   if (err) return fail(c, RCCSDT_ERR_OOM, "grouped residual: table upload failed");
-  G.kind = kind;
   G.on = 1;
   return 0;
+}
+
+int check(rccsdt_ctx* c, const char* where);
+
+// Autotuner of the grouped GEMM: times each candidate launch shape (tile width,
+// problem order, persistent grid) on the panels of the current iteration and
+// keeps the fastest.  The first candidate is the fixed shape (256-wide tiles,
+// longest K first, one CTA per SM); its time is kept for comparison.
+int autotune_grouped(rccsdt_ctx* c) {
+  auto& G = c->gr;
+  G.tuned = 1;
+#ifdef RCC_HOSTSIM
+  return 0;
+#else
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  struct Cand {
+    int bn, ord, grid;
+  };
+  const Cand cands[] = {{256, 0, 0}, {256, 1, 0}, {128, 0, 0}, {128, 1, 0}, {256, 0, sms / 2}, {128, 0, sms / 2}};
+  int* flag = (int*)((double*)c->scalars->p + 1000);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(c, RCCSDT_ERR_CUDA, "autotune: event creation failed");
+  double best = 1e300;
+  Cand bc = cands[0];
+  std::unique_ptr<DBuf> best_tab;
+  int best_tiles = 0, st = 0;
+  const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
+  const int only = c->opt.autotune >= 2 ? c->opt.autotune - 2 : -1;  // a fixed candidate (testing)
+  for (const Cand& k : cands) {
+    if (only >= 0 && only < ncand && &k != &cands[only] && &k != &cands[0]) continue;
+    std::unique_ptr<DBuf> tab;
+    int nt = 0;
+    if ((st = grouped_table(c, k.bn, k.ord, &tab, &nt))) break;
+    const rcc::GProblem* P = (const rcc::GProblem*)tab->p;
+    rcc::launch_gemm_tc_grouped(G.kind, P, G.nprob, nt, k.grid, k.bn, flag, c->opt.watchdog_cycles, c->stream);
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 2; ++r)
+      rcc::launch_gemm_tc_grouped(G.kind, P, G.nprob, nt, k.grid, k.bn, flag, c->opt.watchdog_cycles, c->stream);
+    cudaEventRecord(e1, c->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = fail(c, RCCSDT_ERR_CUDA, "autotune: launch failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double t = ms / 2.0;
+    if (&k == &cands[0]) G.fixed_ms = t;
+    if (only >= 0 && only < ncand ? &k == &cands[only] : t < best) {
+      best = t;
+      bc = k;
+      best_tab = std::move(tab);
+      best_tiles = nt;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  G.probs = std::move(best_tab);
+  G.ntiles = best_tiles;
+  G.bn = bc.bn;
+  G.ord = bc.ord;
+  G.grid = bc.grid;
+  G.tuned_ms = best;
+  return check(c, "autotune");
+#endif
 }
 
 // The residual's tensor-core contractions through the grouped path (R3 is
@@ -1328,9 +1426,13 @@ int run_grouped(rccsdt_ctx* c) {
     if (G.npack[t])
       rcc::launch_pack_grouped((const rcc::PackArgs*)G.packs[t]->p, (const int*)G.ptile[t]->p, G.npack[t], G.ntile[t],
                                t == 1, c->stream);
+  if (c->opt.autotune && !G.tuned) {
+    const int st = autotune_grouped(c);
+    if (st) return st;
+  }
   int* flag = (int*)((double*)c->scalars->p + 1000);
   const int tidx = timer_begin(c, 16, G.flop);
-  if (rcc::launch_gemm_tc_grouped(G.kind, (const rcc::GProblem*)G.probs->p, G.nprob, G.ntiles, G.grid, flag,
+  if (rcc::launch_gemm_tc_grouped(G.kind, (const rcc::GProblem*)G.probs->p, G.nprob, G.ntiles, G.grid, G.bn, flag,
                                   c->opt.watchdog_cycles, c->stream))
     return fail(c, RCCSDT_ERR_ARG, "grouped GEMM configuration unsupported");
   timer_end(c, tidx);
@@ -1936,10 +2038,11 @@ RCC_API long long rccsdt_kernel_launches(void) { return rcc::g_launch_count; }
 RCC_API int rccsdt_engine_info(const rccsdt_ctx* c, long long* out, int cap) {
   if (!c || !out) return RCCSDT_ERR_ARG;
   const auto& G = c->gr;
-  const long long v[8] = {G.on, G.nprob, G.ntiles, (long long)G.npack[0] + G.npack[1],
-                          G.on ? (long long)(G.xoff ? G.xoff->bytes / 8 : 0) : 0, (long long)(G.on ? G.bytes : 0),
-                          G.grid, G.kind};
-  const int k = cap < 8 ? cap : 8;
+  const long long v[13] = {G.on, G.nprob, G.ntiles, (long long)G.npack[0] + G.npack[1],
+                           G.on ? (long long)(G.xoff ? G.xoff->bytes / 8 : 0) : 0, (long long)(G.on ? G.bytes : 0),
+                           G.grid, G.kind, G.bn, G.ord, G.tuned, (long long)(G.tuned_ms * 1e3),
+                           (long long)(G.fixed_ms * 1e3)};
+  const int k = cap < 13 ? cap : 13;
   for (int q = 0; q < k; ++q) out[q] = v[q];
   return k;
 }
@@ -1981,6 +2084,14 @@ void ctx_begin_capture(rccsdt_ctx* c) {
   c->timing = 0;
 }
 int ctx_ready(rccsdt_ctx* c) { return need(c, true, false, false); }
+int ctx_prepare(rccsdt_ctx* c) {
+  if (!c->opt.autotune || !c->gr.on || c->gr.tuned) return 0;
+  // one evaluation in the main precision runs the autotuner on real panels
+  const int st = ctx_enqueue(c, 0, c->opt.precision);
+  c->precision = c->opt.precision;
+  if (st) return st;
+  return dev_sync(c->stream) ? fail(c, RCCSDT_ERR_CUDA, "autotune evaluation failed") : 0;
+}
 int ctx_dims(const rccsdt_ctx* c, int* o, int* v) {
   *o = c->o;
   *v = c->v;

@@ -42,7 +42,7 @@ void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, 
 // Split-precision product hi*hi + hi*lo + lo*hi with float products and a float
 // accumulator (the order of the tensor-core sum is not modelled).
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int Kpad,
-                   const EpiArgs& e, int*, long long, cudaStream_t, float*, long long, float* raw_out) {
+                   const EpiArgs& e, int*, long long, cudaStream_t, float*, long long, float* raw_out, int) {
   auto get = [&](const void* p, i64 i) -> float {
     if (kind == PANEL_BF16X2) return __bfloat162float(((const __nv_bfloat16*)p)[i]);
     return ((const float*)p)[i];
@@ -82,7 +82,7 @@ void launch_combine(const CombineArgs& c, cudaStream_t) {
 int gemm_tc_block_k(int kind) { return kind == PANEL_BF16X2 ? 64 : 32; }
 
 int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int M,
-                  int N, int Kpad, float* out) {
+                  int N, int Kpad, float* out, int bn) {
   if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
   if (Kpad % gemm_tc_block_k(kind) != 0 || M <= 0 || N <= 0) return 1;
   memset((void*)p, 0, sizeof(*p));
@@ -96,20 +96,20 @@ int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const
   p->Kpad = Kpad;
   p->kblocks = Kpad / gemm_tc_block_k(kind);
   p->mt = (M + 127) / 128;
-  p->nt = (N + 255) / 256;
+  p->nt = (N + (bn == 128 ? 127 : 255)) / (bn == 128 ? 128 : 256);
   return 0;
 }
 
 int gproblem_tiles(const GProblem& p) { return p.mt * p.nt; }
 
-int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int, int, int* flag, long long wd,
+int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int, int, int, int* flag, long long wd,
                            cudaStream_t s) {
   for (int q = 0; q < nprob; ++q) {
     const GProblem& P = probs[q];
     EpiArgs e{};
     e.M = P.M;
     e.N = P.N;
-    if (launch_gemm_tc(kind, P.a_hi, P.a_lo, P.b_hi, P.b_lo, P.Kpad, e, flag, wd, s, nullptr, 0, P.out)) return 1;
+    if (launch_gemm_tc(kind, P.a_hi, P.a_lo, P.b_hi, P.b_lo, P.Kpad, e, flag, wd, s, nullptr, 0, P.out, 256)) return 1;
   }
   return 0;
 }

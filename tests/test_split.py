@@ -64,3 +64,31 @@ def test_split_solve_refines_to_fp64_energy(kind, prec):
     assert conv
     assert abs(E - E0) < 1e-6
     ctx.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", [None, 0, 1, 2, 3, 4, 5], ids=["tuned", "c0", "c1", "c2", "c3", "c4", "c5"])
+def test_grouped_launch_shapes_match_oracle(shape):
+    """Every launch shape of the grouped GEMM (256/128-wide tiles, problem orders,
+    grids), and the one the autotuner picks, gives the oracle's residual."""
+    lib = gpu_lib()
+    o, v, naux = 3, 21, 30
+    inst = make_instance(o, v, naux, seed=5)
+    t1, t2, t3 = random_amplitudes(o, v, seed=9)
+    t3c = oc.pack(t3)
+    ctx = B.Context(lib, o, v, naux, precision=B.SPLIT_BF16X3, autotune=1 if shape is None else 2 + shape)
+    ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    ctx.set_amplitudes(t1, t2, t3c)
+    ctx.build_intermediates()
+    ctx.residual()
+    ctx.postprocess()
+    info = ctx.engine_info()
+    assert info["grouped"] == 1 and info["tuned"] == 1
+    if shape is not None:
+        assert info["bn"] == (128 if shape in (2, 3, 5) else 256)
+    r1, r2, r3 = ctx.residuals()
+    R1, R2, R3 = oc.residuals_compact(inst.L, inst.fock_diag, t1, t2, t3c)
+    scale = max(1.0, np.abs(R3).max())
+    assert np.abs(oc.postprocess(r3, o) - oc.postprocess(R3, o)).max() / scale < TOL[B.SPLIT_BF16X3]
+    assert np.abs(r2 - R2).max() / scale < TOL[B.SPLIT_BF16X3]
+    ctx.close()

@@ -62,7 +62,6 @@ typedef enum {
 
 typedef struct {
   int precision;          /* rccsdt_precision */
-  int final_fp64_iters;   /* split modes: last iterations of rccsdt_solve run in FP64 */
   int diis_space;         /* DIIS history length M (0 = plain Jacobi) */
   int diis_start;         /* first iteration (1-based) that extrapolates */
   int diis_t3;            /* 1: DIIS vectors include T3; 0: T1 and T2 only */
@@ -78,8 +77,8 @@ typedef struct {
                                 2 + i: always candidate i (0..5) of the autotuner's list */
 } rccsdt_options;
 
-/* Fills *opt with the defaults: FP64, final_fp64_iters 2, DIIS(8) from iteration 2
- * including T3, max_iter 100, tol 1e-8, grouped_bytes 8 GiB, autotune 0. */
+/* Fills *opt with the defaults: FP64, DIIS(8) from iteration 2 including T3,
+ * max_iter 100, tol 1e-8, grouped_bytes 8 GiB, autotune 0. */
 int rccsdt_options_default(rccsdt_options* opt);
 
 /* Creates a context for o occupied / v virtual orbitals and naux factors, on the
@@ -130,11 +129,12 @@ int rccsdt_energy(rccsdt_ctx* ctx, double* e_corr);
  * amplitudes the residual was evaluated at; either may be NULL. */
 int rccsdt_iterate(rccsdt_ctx* ctx, double* e_corr, double norms[4]);
 
-/* Iterates from the current amplitudes until |R| <= tol or max_iter.  In the
- * split modes the iterations run in split precision until |R| <= sqrt(tol); from
- * then on they run in FP64 (iterative refinement), and convergence is only
- * accepted on an FP64 iteration.  Outputs describe the last residual evaluated.
- * Returns RCCSDT_NOT_CONVERGED if max_iter is reached. */
+/* Iterates from the current amplitudes until |R| <= tol or max_iter evaluations.
+ * In the split modes the iterations run in split precision until |R| <= sqrt(tol);
+ * from then on they run with FP64 contractions (iterative refinement), and
+ * convergence is only accepted on an FP64 evaluation.  Outputs describe the last residual evaluated
+ * (iterations counts evaluations).  Returns RCCSDT_NOT_CONVERGED if max_iter is
+ * reached. */
 int rccsdt_solve(rccsdt_ctx* ctx, double* e_corr, int* iterations, double* final_norm);
 
 /* Copies out the amplitudes / the current residuals (float64). NULL skips. */

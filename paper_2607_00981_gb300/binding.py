@@ -20,7 +20,7 @@ FP64, SPLIT_BF16X3, SPLIT_TF32X3 = 0, 1, 2
 
 
 class Options(C.Structure):
-    _fields_ = [("precision", C.c_int), ("final_fp64_iters", C.c_int), ("diis_space", C.c_int),
+    _fields_ = [("precision", C.c_int), ("diis_space", C.c_int),
                 ("diis_start", C.c_int), ("diis_t3", C.c_int), ("max_iter", C.c_int),
                 ("tol", C.c_double), ("watchdog_cycles", C.c_longlong), ("grouped_bytes", C.c_longlong),
                 ("autotune", C.c_int)]

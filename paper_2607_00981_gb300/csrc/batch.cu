@@ -1,22 +1,17 @@
 // Batched driver: many independent RCCSDT instances of different (o, v) iterated
 // together, one CUDA graph launch per iteration of the whole batch.
 //
-// Each instance owns a full context (its own plans and buffers).  Its iteration
-// is captured once into the bodies of a conditional SWITCH node of one graph:
-//   body 0  evaluation in the main precision (energy, intermediates, residuals,
-//           post-processing and norms at the current amplitudes),
-//   body 1  the same in FP64 (split-precision batches only),
-//   body 2  the update from the last residual followed by body 0's work,
-//   body 3  the update followed by body 1's work (split-precision batches only),
-//   other   nothing (converged or stopped instances).
-// A control kernel at the top of the graph sets each SWITCH from a code array
-// that the host writes before the launch; a gather kernel at the bottom copies
-// every instance's norms and energy into one array read back with one copy.  The
-// SWITCH nodes have no edges between them, so the instances run concurrently.
-// The host keeps, per instance, exactly the state machine of rccsdt_solve (split
-// precision until |R| <= sqrt(tol), FP64 from then on, convergence accepted on an
-// FP64 evaluation), so a batched instance takes the same iterations, and computes
-// the same numbers, as rccsdt_solve on its own context.
+// Each instance owns a full context (its own plans and buffers).  Its steps are
+// captured once into the bodies of a conditional SWITCH node of one graph, one
+// body per step kind of the solver (solve_sm.h: evaluation, or update followed
+// by evaluation, in the main precision or with FP64 contractions); a code past
+// the last body runs nothing (converged or stopped instances).  A control kernel at the top of the graph sets each SWITCH
+// from a code array that the host writes before the launch; a gather kernel at
+// the bottom copies every instance's norms and energy into one array read back
+// with one copy.  The SWITCH nodes have no edges between them, so the instances
+// run concurrently.  The host runs, per instance, the state machine of
+// rccsdt_solve, so a batched instance takes the same steps as rccsdt_solve on a
+// context of its own.
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -27,19 +22,14 @@
 #include "../../include/rccsdt.h"
 #include "internal.h"
 #include "kernels.h"
+#include "solve_sm.h"
 
 namespace {
 
-enum { kEvalMain = 0, kEvalF64 = 1, kStepMain = 2, kStepF64 = 3, kSkip = 4, kBodies = 4 };
+using rcc::kBodies;
+using rcc::kSkip;
+using rcc::SolveState;
 constexpr int kOutStride = 8;  // per instance: |R1|^2 |R2|^2 |R3|^2 - E flag - -
-
-struct InstState {
-  int it = 0;          // evaluations done
-  int fp64_left = -1;  // split modes: >= 0 once the FP64 phase has started
-  int done = 0;
-  int status = RCCSDT_NOT_CONVERGED;
-  double e = 0.0, norm = 0.0;
-};
 
 #ifndef RCC_HOSTSIM
 __global__ void k_batch_switch(const unsigned long long* __restrict__ handles, const int* __restrict__ codes, int n) {
@@ -69,7 +59,7 @@ struct rccsdt_batch {
   cudaStream_t stream = nullptr;  // caller's stream (instance API calls)
   cudaStream_t run = nullptr;     // owned: capture and graph launches
   std::vector<rccsdt_ctx*> inst;
-  std::vector<InstState> state;
+  std::vector<SolveState> state;
   std::vector<long long> body_launches;  // [n][kBodies]
   std::string err;
   // graph
@@ -98,44 +88,6 @@ namespace {
 int bfail(rccsdt_batch* b, int code, const std::string& msg) {
   if (b) b->err = msg;
   return code;
-}
-
-bool split_mode(const rccsdt_batch* b) { return b->opt.precision != RCCSDT_FP64; }
-
-// Next body for instance i (the rccsdt_solve state machine); kSkip when done.
-int next_code(const rccsdt_batch* b, InstState& s) {
-  if (s.done) return kSkip;
-  const bool split = split_mode(b);
-  if (s.it == 0) return kEvalMain;
-  // end of iteration s.it: its update follows; then the start of iteration s.it + 1
-  if (split && s.fp64_left > 0) --s.fp64_left;
-  if (split && s.fp64_left < 0 && s.norm <= std::sqrt(b->opt.tol)) s.fp64_left = b->opt.final_fp64_iters;
-  return (split && s.fp64_left >= 0) ? kStepF64 : kStepMain;
-}
-
-// Book the results of one evaluation of instance i.
-void take_result(rccsdt_batch* b, InstState& s, const double* out) {
-  const bool split = split_mode(b);
-  s.it += 1;
-  s.norm = std::sqrt(out[0] + out[1] + out[2]);
-  s.e = out[4];
-  if (out[5] != 0.0) {
-    s.status = RCCSDT_ERR_TIMEOUT;
-    s.done = 1;
-  } else if (!std::isfinite(s.norm) || !std::isfinite(s.e)) {
-    s.status = RCCSDT_ERR_NONFINITE;
-    s.done = 1;
-  } else if (s.norm <= b->opt.tol && (!split || s.fp64_left >= 0)) {
-    s.status = RCCSDT_OK;
-    s.done = 1;
-  } else if (s.it >= b->opt.max_iter) {
-    s.status = RCCSDT_NOT_CONVERGED;
-    s.done = 1;
-  }
-}
-
-int body_precision(const rccsdt_batch* b, int code) {
-  return (code == kEvalF64 || code == kStepF64) ? RCCSDT_FP64 : b->opt.precision;
 }
 
 #ifndef RCC_HOSTSIM
@@ -176,7 +128,7 @@ int build_graph(rccsdt_batch* b) {
   }
   // one SWITCH per instance, bodies captured from the instance's own launch sequence
   std::vector<cudaGraphNode_t> sw(n);
-  const bool split = split_mode(b);
+  const bool split = rcc::split_opt(b->opt);
   for (int i = 0; i < n; ++i) {
     cudaGraphNodeParams p = {};
     p.type = cudaGraphNodeTypeConditional;
@@ -188,7 +140,8 @@ int build_graph(rccsdt_batch* b) {
     cudaGraph_t* bodies = p.conditional.phGraph_out;
     rccsdt_ctx* c = b->inst[i];
     for (int code = 0; code < kBodies; ++code) {
-      if (!split && (code == kEvalF64 || code == kStepF64)) {
+      const bool unused = !split && (code == rcc::kEvalF64 || code == rcc::kStepF64);
+      if (unused) {
         cudaGraphNode_t e;
         cudaGraphAddEmptyNode(&e, bodies[code], nullptr, 0);
         b->body_launches[(size_t)i * kBodies + code] = 0;
@@ -202,7 +155,7 @@ int build_graph(rccsdt_batch* b) {
         rcc::ctx_set_stream(c, b->stream);
         return bfail(b, RCCSDT_ERR_CUDA, "capture start failed");
       }
-      const int st = rcc::ctx_enqueue(c, code >= kStepMain, body_precision(b, code));
+      const int st = rcc::ctx_enqueue_code(c, code);
       cudaGraph_t out = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(b->run, &out);
       b->body_launches[(size_t)i * kBodies + code] = rcc::g_launch_count - l0;
@@ -254,13 +207,10 @@ int run_once(rccsdt_batch* b) {
     if (code >= kSkip) continue;
     rccsdt_ctx* c = b->inst[i];
     rcc::ctx_begin_capture(c);
-    const int st = rcc::ctx_enqueue(c, code >= kStepMain, body_precision(b, code));
+    int st = rcc::ctx_enqueue_code(c, code);
     rcc::ctx_reset_precision(c);
+    if (!st) st = rcc::ctx_read_scalars(c, b->h_out + (size_t)i * kOutStride);
     if (st) return bfail(b, st, std::string("instance ") + std::to_string(i) + ": " + rccsdt_last_error(c));
-    const double* s = rcc::ctx_scalars(c);
-    double* o = b->h_out + (size_t)i * kOutStride;
-    o[0] = s[0]; o[1] = s[1]; o[2] = s[2]; o[3] = 0.0; o[4] = s[4];
-    o[5] = (double)((const int*)(s + 1000))[0];
   }
   return 0;
 #else
@@ -301,7 +251,7 @@ RCC_API int rccsdt_batch_create(int n, const int* o, const int* v, const int* na
   b->n = n;
   b->opt = opt ? *opt : def;
   b->stream = (cudaStream_t)stream;
-  b->state.assign(n, InstState());
+  b->state.assign(n, SolveState());
   b->body_launches.assign((size_t)n * kBodies, 0);
   int st = 0;
   for (int i = 0; i < n && !st; ++i) {
@@ -361,14 +311,14 @@ RCC_API int rccsdt_batch_solve(rccsdt_batch* b, double* e_corr, int* iterations,
       const int st = rcc::ctx_prepare(b->inst[i]);
       if (st) return bfail(b, st, std::string("instance ") + std::to_string(i) + ": " + rccsdt_last_error(b->inst[i]));
     }
-  b->state.assign(n, InstState());
+  b->state.assign(n, SolveState());
   b->launches = b->kernels = 0;
   b->device_ms = b->flop = 0.0;
   b->launch_ms.clear();
   for (;;) {
     int active = 0;
     for (int i = 0; i < n; ++i) {
-      b->h_codes[i] = next_code(b, b->state[i]);
+      b->h_codes[i] = rcc::next_code(b->opt, b->state[i]);
       if (b->h_codes[i] < kSkip) ++active;
     }
     if (!active) break;
@@ -383,7 +333,7 @@ RCC_API int rccsdt_batch_solve(rccsdt_batch* b, double* e_corr, int* iterations,
       int o = 0, v = 0;
       rcc::ctx_dims(b->inst[i], &o, &v);
       b->flop += 2.0 * rccsdt_iteration_fma(o, v);
-      take_result(b, b->state[i], b->h_out + (size_t)i * kOutStride);
+      rcc::take_result(b->opt, b->state[i], code, b->h_out + (size_t)i * kOutStride);
     }
   }
 #ifndef RCC_HOSTSIM
@@ -391,7 +341,7 @@ RCC_API int rccsdt_batch_solve(rccsdt_batch* b, double* e_corr, int* iterations,
 #endif
   int worst = RCCSDT_OK;
   for (int i = 0; i < n; ++i) {
-    const InstState& s = b->state[i];
+    const SolveState& s = b->state[i];
     if (e_corr) e_corr[i] = s.e;
     if (iterations) iterations[i] = s.it;
     if (final_norm) final_norm[i] = s.norm;

@@ -11,6 +11,11 @@ namespace rcc {
 // energy, intermediates, residuals and post-processed R3 with its norms, with the
 // contractions in `precision`.  Results stay in the device scalars.
 int ctx_enqueue(rccsdt_ctx* c, int update_first, int precision);
+// Queues body `code` of the solver's state machine (solve_sm.h).
+int ctx_enqueue_code(rccsdt_ctx* c, int code);
+// Reads the last evaluation's scalars (norms squared [0..2], energy [4], watchdog
+// flag [5]) to the host, synchronising the context's stream.
+int ctx_read_scalars(rccsdt_ctx* c, double* out);
 // Device scalars: [0..2] squared norms of R1, R2, R3 (block-weighted), [4] energy;
 // the int at byte offset 8000 is the tensor-core watchdog flag.
 const double* ctx_scalars(const rccsdt_ctx* c);

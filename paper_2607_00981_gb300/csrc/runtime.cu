@@ -31,6 +31,7 @@
 #include "../../include/rccsdt.h"
 #include "elem.cuh"
 #include "internal.h"
+#include "solve_sm.h"
 #include "kernels.h"
 
 using rcc::i64;
@@ -1578,6 +1579,7 @@ int do_postprocess(rccsdt_ctx* c, double norms[4]) {
     rcc::launch_post<float>(c->B("r3")->f(), c->B("rp3")->f(), blk, c->v, c->n3, c->stream);
   else
     rcc::launch_post<double>(c->D("r3"), c->D("rp3"), blk, c->v, c->n3, c->stream);
+
   rcc::launch_wdot<double>(c->D("r1"), c->D("r1"), (i64)c->o * c->v, 1, nullptr, partials(c), scal(c, 0), 1.0, 0,
                            c->stream);
   rcc::launch_wdot<double>(c->D("r2"), c->D("r2"), (i64)c->o * c->o * c->v * c->v, 1, nullptr, partials(c),
@@ -1703,7 +1705,6 @@ RCC_API int rccsdt_options_default(rccsdt_options* opt) {
   if (!opt) return RCCSDT_ERR_ARG;
   memset(opt, 0, sizeof(*opt));
   opt->precision = RCCSDT_FP64;
-  opt->final_fp64_iters = 2;
   opt->diis_space = 8;
   opt->diis_start = 2;
   opt->diis_t3 = 1;
@@ -1922,31 +1923,22 @@ RCC_API int rccsdt_iterate(rccsdt_ctx* c, double* e, double norms[4]) {
 RCC_API int rccsdt_solve(rccsdt_ctx* c, double* e_corr, int* iterations, double* final_norm) {
   int st = need(c, true, false, false);
   if (st) return st;
-  const int split = c->opt.precision != RCCSDT_FP64;
-  int fp64_left = -1;
-  double e = 0, norms[4] = {0, 0, 0, 0};
-  for (int it = 1; it <= c->opt.max_iter; ++it) {
-    if (split) {
-      if (fp64_left < 0 && (it == 1 ? false : norms[3] <= sqrt(c->opt.tol))) fp64_left = c->opt.final_fp64_iters;
-      rccsdt_set_precision(c, fp64_left >= 0 ? RCCSDT_FP64 : c->opt.precision);
-    }
-    // evaluate at the current amplitudes; stop before updating when converged
-    if ((st = do_energy(c, &e))) return st;
-    if ((st = do_intermediates(c))) return st;
-    if ((st = do_residual(c))) return st;
-    if ((st = do_postprocess(c, norms))) return st;
-    if (iterations) *iterations = it;
-    if (final_norm) *final_norm = norms[3];
-    if (e_corr) *e_corr = e;
-    if (norms[3] <= c->opt.tol && (!split || fp64_left >= 0)) {
-      if (split) rccsdt_set_precision(c, c->opt.precision);
-      return RCCSDT_OK;
-    }
-    if ((st = do_update(c))) return st;
-    if (split && fp64_left > 0) --fp64_left;
+  rcc::SolveState S;
+  for (;;) {
+    const int code = rcc::next_code(c->opt, S);
+    if (code >= rcc::kSkip) break;
+    if ((st = rcc::ctx_enqueue_code(c, code))) return st;
+    double out[6];
+    if ((st = rcc::ctx_read_scalars(c, out))) return st;
+    rcc::take_result(c->opt, S, code, out);
   }
-  if (split) rccsdt_set_precision(c, c->opt.precision);
-  return RCCSDT_NOT_CONVERGED;
+  c->have_int = c->have_res = 0;
+  if (iterations) *iterations = S.it;
+  if (final_norm) *final_norm = S.norm;
+  if (e_corr) *e_corr = S.e;
+  if (S.status == RCCSDT_ERR_TIMEOUT) return fail(c, S.status, "a device-side wait exceeded its watchdog budget");
+  if (S.status == RCCSDT_ERR_NONFINITE) return fail(c, S.status, "non-finite residual norm or energy");
+  return S.status;
 }
 
 RCC_API int rccsdt_get_amplitudes(rccsdt_ctx* c, double* t1, double* t2, double* t3c) {
@@ -2071,6 +2063,27 @@ int ctx_enqueue(rccsdt_ctx* c, int update_first, int precision) {
   if ((st = do_intermediates(c))) return st;
   if ((st = do_residual(c))) return st;
   return do_postprocess(c, nullptr);
+}
+
+// Queues one body of the solver (solve_sm.h) without host synchronisation.
+int ctx_enqueue_code(rccsdt_ctx* c, int code) {
+  if (code < 0 || code >= kBodies) return fail(c, RCCSDT_ERR_ARG, "internal: unknown body");
+  const int st = ctx_enqueue(c, code == kStepMain || code == kStepF64, body_precision(c->opt, code));
+  c->precision = c->opt.precision;
+  return st ? st : check(c, "ctx_enqueue_code");
+}
+
+// Device scalars of the last evaluation into out[0..5] (host), synchronising.
+int ctx_read_scalars(rccsdt_ctx* c, double* out) {
+  double h[6];
+  if (dev_copy(h, c->scalars->p, 5 * sizeof(double), c->stream) ||
+      dev_copy(&h[5], (double*)c->scalars->p + 1000, sizeof(double), c->stream) || dev_sync(c->stream))
+    return fail(c, RCCSDT_ERR_CUDA, "scalar read failed");
+  const int flag = *(const int*)&h[5];
+  for (int q = 0; q < 5; ++q) out[q] = h[q];
+  out[3] = 0.0;
+  out[5] = (double)flag;
+  return 0;
 }
 
 const double* ctx_scalars(const rccsdt_ctx* c) { return (const double*)c->scalars->p; }

@@ -72,13 +72,16 @@ typedef struct {
                                 operand panels and dense results of the R3 contractions at
                                 once); when an instance needs more, or 0, its contractions
                                 run one by one through shared panels */
+  long long unpack_bytes;    /* device bytes for the unpacked, spin-summed T3 blocks t_{xyz} of
+                                the T3 -> R1/R2/W step (as many values of z as fit, at least
+                                one; <= 0 means 1 GiB) */
   int autotune;              /* 1: time candidate launch shapes of the grouped GEMM on the
                                 first iteration and keep the fastest; 0: fixed shape;
                                 2 + i: always candidate i (0..5) of the autotuner's list */
 } rccsdt_options;
 
 /* Fills *opt with the defaults: FP64, DIIS(8) from iteration 2 including T3,
- * max_iter 100, tol 1e-8, grouped_bytes 8 GiB, autotune 0. */
+ * max_iter 100, tol 1e-8, grouped_bytes 8 GiB, unpack_bytes 1 GiB, autotune 0. */
 int rccsdt_options_default(rccsdt_options* opt);
 
 /* Creates a context for o occupied / v virtual orbitals and naux factors, on the

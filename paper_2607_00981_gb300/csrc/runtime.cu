@@ -213,7 +213,9 @@ struct rccsdt_ctx {
 
   // plan groups
   std::vector<GemmPlan*> p_dress, p_fock, p_eri, p_int, p_r12, p_energy_bare;
-  std::vector<std::vector<GemmPlan*>> p_a3;  // per z
+  std::vector<std::vector<GemmPlan*>> p_a3;  // per batch of a3_Z values of z
+  std::vector<GemmPlan*> p_wbar;             // the W-bar contractions before step (iii)
+  int a3_Z = 1;
   std::vector<GemmPlan*> p_pp, p_hh, p_ringab, p_ringc, p_t2a;
   // combines
   std::vector<rcc::CombineArgs> c_fock, c_helpers, c_int_base, c_r12_base, c_r2_sym, c_wt;
@@ -702,7 +704,10 @@ int build_context(rccsdt_ctx* c) {
   b.mk("r2", (size_t)o * o * v * v); b.mk("X2", (size_t)o * o * v * v);
   b.mk("dR1", (size_t)o * v); b.mk("dX2", (size_t)o * o * v * v);
   b.mk("t3", (size_t)n3 * V3, t3e); b.mk("r3", (size_t)n3 * V3, t3e); b.mk("rp3", (size_t)n3 * V3, t3e);
-  b.mk("Sz", (size_t)o * o * V3, t3e);
+  // step (iii) unpacks the blocks t_{xyz} of a3_Z values of z at a time (options.unpack_bytes)
+  const i64 ub = c->opt.unpack_bytes > 0 ? c->opt.unpack_bytes : (1LL << 30);
+  c->a3_Z = (int)std::max<i64>(1, std::min<i64>(o, ub / std::max<i64>(1, (i64)o * o * V3 * (i64)t3e)));
+  b.mk("Sz", (size_t)c->a3_Z * o * o * V3, t3e);
   if (err) return fail(c, err, "device allocation failed");
 
   // --- block info and weights
@@ -827,8 +832,7 @@ int build_context(rccsdt_ctx* c) {
   std::vector<GemmPlan*> p_int2;
   b.ct(p_int2, "mled,miea->ladi", 0.5, vs_oovv, ts2, Wb_ovvo);
   b.ct(p_int2, "mlde,imea->laid", -0.5, eri("oovv"), t2, Wb_ovov);
-  c->p_a3.resize(o + 1);
-  c->p_a3[o] = p_int2;  // slot o: the Wbar contractions
+  c->p_wbar = p_int2;
 
   // --- step (iii): T3 contributions, per z batch of unpacked blocks t_{xyz}
   {
@@ -844,20 +848,25 @@ int build_context(rccsdt_ctx* c) {
         }
     c->a3_base = upload_vec(c, base, &err);
     c->a3_pos = upload_vec(c, pos, &err);
-    View Sz = dense(c->B("Sz")->p, {o, o, v, v, v}, t3f);
     View dR1 = b.T("dR1", {o, v}), dX2 = b.T("dX2", {o, o, v, v});
-    for (int z = 0; z < o; ++z) {
-      auto& g = c->p_a3[z];
+    const int Z = c->a3_Z;
+    for (int z0 = 0; z0 < o; z0 += Z) {
+      const int Zb = std::min(Z, o - z0);
+      View Sz = dense(c->B("Sz")->p, {Zb, o, o, v, v, v}, t3f);  // S[z][x][y][e1][e2][e3]
+      c->p_a3.emplace_back();
+      auto& g = c->p_a3.back();
       // (the R1 term runs in k_r1_t3 on the same S batch)
-      // S panel [(y,e2,e3)][(x,e1)], shared by three contractions
-      View dX2z = slice0(permuted(dX2, {1, 0, 2, 3}), z);  // dX2[y, z, a, b] over (y, a, b)
-      b.ct(g, "xc,xycab->yab", 0.5, sub(sub(ft, 0, O0, o), 1, V0, v), Sz, dX2z);
-      b.ct(g, "xjc,xycab->yjab", -1.0, slice0(eri("ooov"), z), Sz, dX2)->reuse_B = 1;
-      b.ct(g, "xde,xyeba->ybad", -1.0, slice0(eri("oovv"), z), Sz, permuted(Wvvvo, {3, 1, 0, 2}), 1)->reuse_B = 1;
-      // S panel [(y,e2)][(x,e3,e1)], shared by two contractions
-      b.ct(g, "bxcd,xydac->yab", 1.0, eri("vovv"), Sz, dX2z, 1);
-      b.ct(g, "lxde,xyead->yal", 1.0, eri("oovv"), Sz,
-           permuted(slice0(permuted(Wvooo, {3, 0, 1, 2}), z), {2, 0, 1}))->reuse_B = 1;
+      View dX2z = sub(permuted(dX2, {1, 0, 2, 3}), 0, z0, Zb);  // dX2[y, z, a, b] over (z, y, a, b)
+      b.ct(g, "xc,zxycab->zyab", 0.5, sub(sub(ft, 0, O0, o), 1, V0, v), Sz, dX2z);
+      // S panel [(y,e2,e3)][(z,x,e1)], shared by two contractions (and the first one when Zb = 1)
+      GemmPlan* q = b.ct(g, "zxjc,zxycab->yjab", -1.0, sub(eri("ooov"), 0, z0, Zb), Sz, dX2);
+      if (q && Zb == 1) q->reuse_B = 1;
+      b.ct(g, "zxde,zxyeba->ybad", -1.0, sub(eri("oovv"), 0, z0, Zb), Sz, permuted(Wvvvo, {3, 1, 0, 2}), 1)
+          ->reuse_B = 1;
+      // S panel [(z,y,e2)][(x,e3,e1)], shared by two contractions
+      b.ct(g, "bxcd,zxydac->zyab", 1.0, eri("vovv"), Sz, dX2z, 1);
+      b.ct(g, "lxde,zxyead->zyal", 1.0, eri("oovv"), Sz,
+           permuted(sub(permuted(Wvooo, {3, 0, 1, 2}), 0, z0, Zb), {0, 3, 1, 2}))->reuse_B = 1;
     }
   }
 
@@ -1491,26 +1500,31 @@ int do_intermediates(rccsdt_ctx* c) {
   run_combines(c, c->c_int_base);
   if ((st = run_plans(c, c->p_int))) return st;
   run_combines(c, c->c_int_after[0]);
-  if ((st = run_plans(c, c->p_a3[c->o]))) return st;
-  // step (iii): T3 -> R1, R2, W^{ab}_{dj}, W^{al}_{ij}
+  if ((st = run_plans(c, c->p_wbar))) return st;
+  // step (iii): T3 -> R1, R2, W^{ab}_{dj}, W^{al}_{ij}, a3_Z values of z at a time
   zero(c, "dR1");
   zero(c, "dX2");
   const int o = c->o;
   const int t3f = c->opt.precision != RCCSDT_FP64;
-  for (int z = 0; z < o; ++z) {
-    const i64* zb = (const i64*)c->a3_base->p + (size_t)z * o * o;
-    const int* zp = (const int*)c->a3_pos->p + (size_t)z * o * o * 3;
+  const i64 slab = (i64)o * o * c->V3;  // S of one z
+  for (int z0 = 0, bz = 0; z0 < o; z0 += c->a3_Z, ++bz) {
+    const int Zb = std::min(c->a3_Z, o - z0);
+    const i64* zb = (const i64*)c->a3_base->p + (size_t)z0 * o * o;
+    const int* zp = (const int*)c->a3_pos->p + (size_t)z0 * o * o * 3;
     if (t3f)
-      rcc::launch_unpack_spin<float>(c->B("t3")->p, 1, o * o, zb, zp, c->v, c->B("Sz")->f(), c->stream);
+      rcc::launch_unpack_spin<float>(c->B("t3")->p, 1, Zb * o * o, zb, zp, c->v, c->B("Sz")->f(), c->stream);
     else
-      rcc::launch_unpack_spin<double>(c->B("t3")->p, 0, o * o, zb, zp, c->v, c->D("Sz"), c->stream);
-    if ((st = run_plans(c, c->p_a3[z]))) return st;
-    if (t3f)
-      rcc::launch_r1_t3<float>(c->B("Sz")->f(), c->D("oovv"), o, c->v, c->D("dR1") + (size_t)z * c->v,
-                               c->splitk->d(), (i64)(c->splitk->bytes / 8), c->stream);
-    else
-      rcc::launch_r1_t3<double>(c->D("Sz"), c->D("oovv"), o, c->v, c->D("dR1") + (size_t)z * c->v, c->splitk->d(),
-                                (i64)(c->splitk->bytes / 8), c->stream);
+      rcc::launch_unpack_spin<double>(c->B("t3")->p, 0, Zb * o * o, zb, zp, c->v, c->D("Sz"), c->stream);
+    if ((st = run_plans(c, c->p_a3[bz]))) return st;
+    for (int z = z0; z < z0 + Zb; ++z) {
+      if (t3f)
+        rcc::launch_r1_t3<float>(c->B("Sz")->f() + (z - z0) * slab, c->D("oovv"), o, c->v,
+                                 c->D("dR1") + (size_t)z * c->v, c->splitk->d(), (i64)(c->splitk->bytes / 8),
+                                 c->stream);
+      else
+        rcc::launch_r1_t3<double>(c->D("Sz") + (z - z0) * slab, c->D("oovv"), o, c->v, c->D("dR1") + (size_t)z * c->v,
+                                  c->splitk->d(), (i64)(c->splitk->bytes / 8), c->stream);
+    }
   }
   c->have_int = 1;
   return check(c, "do_intermediates");
@@ -1712,6 +1726,7 @@ RCC_API int rccsdt_options_default(rccsdt_options* opt) {
   opt->tol = 1e-8;
   opt->watchdog_cycles = 0;
   opt->grouped_bytes = 8LL << 30;
+  opt->unpack_bytes = 1LL << 30;
   opt->autotune = 0;
   return RCCSDT_OK;
 }

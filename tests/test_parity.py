@@ -32,11 +32,14 @@ SHAPES = [(3, 4, 8), (2, 7, 10), (4, 5, 12), (1, 6, 6), (3, 1, 4), (3, 12, 40), 
 
 @pytest.mark.parametrize("kind", BACKENDS)
 @pytest.mark.parametrize("o,v,naux", SHAPES)
-def test_residual_matches_oracle(kind, o, v, naux):
+@pytest.mark.parametrize("zbatch", ["all", "one"])
+def test_residual_matches_oracle(kind, o, v, naux, zbatch):
+    """zbatch: step (iii) unpacks the blocks of every z at once, or of one z at a
+    time (a 1-byte unpack budget)."""
     inst = make_instance(o, v, naux, seed=o * 31 + v)
     t1, t2, t3 = random_amplitudes(o, v, seed=v * 7 + o)
     t3c = oc.pack(t3)
-    ctx = _ctx(kind, o, v, naux)
+    ctx = _ctx(kind, o, v, naux, unpack_bytes=(1 << 30) if zbatch == "all" else 1)
     ctx.set_hamiltonian(inst.fock_diag, inst.L)
     ctx.set_amplitudes(t1, t2, t3c)
     ctx.build_intermediates()

@@ -29,6 +29,13 @@ struct PackArgs {
   int Kpad;              // leading dimension of the output (>= K, zero filled)
   int read_k_fast;       // 1: source contiguous along k, 0: along r
   int one_sel;           // 1: every selector is 0 (rowoff is a single table of R entries)
+  // Row offsets computed instead of looked up (rowoff then unused): rows are the
+  // labels (x, y) (row_mode 2, R = lv^2) or (x, y, z) (row_mode 3, R = lv^3) in
+  // base lv; with stored-block strides S = {lv^2, lv, 1}, selector s gives
+  //   mode 2: x S[s / 3] + y S[s % 3]
+  //   mode 3: x S[p0] + y S[p1] + z S[p2], (p0, p1, p2) the s-th of the six orderings.
+  int row_mode;
+  int lv;
 };
 
 // Table-driven epilogue: C[row_base[m] + col_off[row_sel[m]*N + n]] += row_alpha[m] * acc(m, n)

@@ -20,13 +20,31 @@ RCC_HD float tf32_round(float x) {
   return c.f;
 }
 
+// Stored-axis index of label q under ordering s (the six orderings, lexicographic).
+RCC_HD int perm3(int s, int q) {
+  // {0,1,2} {0,2,1} {1,0,2} {1,2,0} {2,0,1} {2,1,0}
+  const int first = s >> 1;
+  const int rest0 = first == 0 ? 1 : 0, rest1 = first == 2 ? 1 : 2;
+  return q == 0 ? first : ((q == 1) == ((s & 1) == 0) ? rest0 : rest1);
+}
+
+// Row offset of row r under selector s (table or computed, see PackArgs).
+RCC_HD i64 row_offset(const PackArgs& a, int s, int r) {
+  if (a.row_mode == 0) return a.rowoff[(i64)s * a.R + r];
+  const i64 v = a.lv;
+  auto S = [v](int axis) { return axis == 0 ? v * v : (axis == 1 ? v : (i64)1); };
+  if (a.row_mode == 2) return (r / a.lv) * S(s / 3) + (r % a.lv) * S(s % 3);
+  const int x = r / (a.lv * a.lv), y = (r / a.lv) % a.lv, z = r % a.lv;
+  return x * S(perm3(s, 0)) + y * S(perm3(s, 1)) + z * S(perm3(s, 2));
+}
+
 RCC_HD double pack_value(const PackArgs& a, int r, int k) {
   double s = 0.0;
   for (int t = 0; t < a.nterm; ++t) {
     const i64 idx = (i64)t * a.K + k;
     const double c = a.coef[idx];
     if (c != 0.0) {
-      const i64 off = a.colbase[idx] + a.rowoff[(i64)a.sel[idx] * a.R + r];
+      const i64 off = a.colbase[idx] + row_offset(a, a.sel[idx], r);
       s += c * load_src(a.src, a.src_f32, off);
     }
   }
@@ -56,7 +74,7 @@ RCC_HD float pack_value_f(const PackArgs& a, int r, int k) {
     const i64 idx = (i64)t * a.K + k;
     const float c = (float)a.coef[idx];
     if (c != 0.f) {
-      const i64 off = a.colbase[idx] + a.rowoff[(i64)a.sel[idx] * a.R + r];
+      const i64 off = a.colbase[idx] + row_offset(a, a.sel[idx], r);
       s += c * ((const float*)a.src)[off];
     }
   }

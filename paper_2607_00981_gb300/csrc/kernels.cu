@@ -36,16 +36,27 @@ __device__ __forceinline__ void pack_tiles(const PackArgs& a, int r0, int kfirst
   __shared__ T cf[3][32];
   __shared__ int sl[3][32];
   __shared__ i64 ro[32];
+  __shared__ int lab[3][32];   // computed row offsets: the tile rows' labels ...
+  __shared__ i64 cs[3][3][32];  // ... and, per term and column, the label strides
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int nterm = a.nterm < 3 ? a.nterm : 3;
-  if (a.one_sel && tid < 32) ro[tid] = (r0 + tid < a.R) ? a.rowoff[r0 + tid] : 0;
+  const int rm = a.row_mode;
+  if (!rm && a.one_sel && tid < 32) ro[tid] = (r0 + tid < a.R) ? a.rowoff[r0 + tid] : 0;
+  if (rm && tid < 32) {
+    const int r = r0 + tid < a.R ? r0 + tid : 0, lv = a.lv;
+    lab[0][tid] = rm == 2 ? r / lv : r / (lv * lv);
+    lab[1][tid] = rm == 2 ? r % lv : (r / lv) % lv;
+    lab[2][tid] = rm == 2 ? 0 : r % lv;
+  }
   auto value = [&](int rr, int kk) -> T {
     const int r = r0 + rr;
     T s = (T)0;
     for (int t = 0; t < nterm; ++t) {
       const T c = cf[t][kk];
       if (c != (T)0) {
-        const i64 off = cb[t][kk] + (a.one_sel ? ro[rr] : a.rowoff[(i64)sl[t][kk] * a.R + r]);
+        const i64 off = cb[t][kk] + (rm ? lab[0][rr] * cs[t][0][kk] + lab[1][rr] * cs[t][1][kk] +
+                                              lab[2][rr] * cs[t][2][kk]
+                                        : (a.one_sel ? ro[rr] : a.rowoff[(i64)sl[t][kk] * a.R + r]));
         if constexpr (F32)
           s += c * ((const float*)a.src)[off];  // no FP64 conversions on the FP32 path
         else
@@ -68,7 +79,15 @@ __device__ __forceinline__ void pack_tiles(const PackArgs& a, int r0, int kfirst
       const i64 idx = (i64)t * a.K + k;
       cb[t][kk] = ok ? a.colbase[idx] : 0;
       cf[t][kk] = ok ? (T)a.coef[idx] : (T)0;
-      sl[t][kk] = ok ? a.sel[idx] : 0;
+      const int sel = ok ? a.sel[idx] : 0;
+      sl[t][kk] = sel;
+      if (rm) {
+        const i64 v = a.lv;
+        auto S = [&](int axis) { return axis == 0 ? v * v : (axis == 1 ? v : (i64)1); };
+        cs[t][0][kk] = rm == 2 ? S(sel / 3) : S(perm3(sel, 0));
+        cs[t][1][kk] = rm == 2 ? S(sel % 3) : S(perm3(sel, 1));
+        cs[t][2][kk] = rm == 2 ? 0 : S(perm3(sel, 2));
+      }
     }
     __syncthreads();
     if (a.read_k_fast) {
@@ -1081,37 +1100,52 @@ __global__ void __launch_bounds__(256) k_scatter_rows3(const float* __restrict__
                                                        const double* __restrict__ row_alpha, T* __restrict__ C) {
   constexpr int TL = 16;
   __shared__ float cube[TL][TL + 1][TL + 2];
-  const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  constexpr int SA = (TL + 1) * (TL + 2), SB = TL + 2;  // shared strides of the cube's a and b slots
   const int nt = (v + TL - 1) / TL;
-  const i64 V3 = (i64)v * v * v;
-  const i64 sv[3] = {(i64)v * v, v, 1};
+  const i64 V2 = (i64)v * v, V3 = V2 * v;
+  const int lf = threadIdx.x & 15, lm = threadIdx.x >> 4;
   for (int m = blockIdx.y; m < M; m += gridDim.y) {
-    const int* p = P[row_sel[m]];
-    const i64 st[3] = {sv[p[0]], sv[p[1]], sv[p[2]]};
-    const int fast = p[0] == 2 ? 0 : (p[1] == 2 ? 1 : 2);   // label on the target's unit-stride axis
-    const int s1 = (fast + 1) % 3, s2 = (fast + 2) % 3;
+    const int sel = row_sel[m];
+    const int p0 = perm3(sel, 0), p1 = perm3(sel, 1), p2 = perm3(sel, 2);  // stored axis of X slot q
+    // slot whose label lands on the target's unit-stride axis, and the other two
+    const int fast = p0 == 2 ? 0 : (p1 == 2 ? 1 : 2);
+    const int mid = fast == 0 ? 1 : 0, slow = 3 - fast - mid;
+    auto pq = [&](int q) { return q == 0 ? p0 : (q == 1 ? p1 : p2); };
+    auto sv = [&](int axis) { return axis == 0 ? V2 : (axis == 1 ? (i64)v : (i64)1); };
+    auto ss = [&](int q) { return q == 0 ? SA : (q == 1 ? SB : 1); };
+    const i64 stm = sv(pq(mid)), sts = sv(pq(slow));
+    const int cF = ss(fast), cM = ss(mid), cS = ss(slow);
     const i64 base = row_base[m];
     const T al = (T)row_alpha[m];
     const float* xm = X + (i64)m * V3;
     for (int tile = blockIdx.x; tile < nt * nt * nt; tile += gridDim.x) {
-      const int lo[3] = {tile / (nt * nt) * TL, (tile / nt) % nt * TL, tile % nt * TL};
+      const int lo0 = tile / (nt * nt) * TL, lo1 = (tile / nt) % nt * TL, lo2 = tile % nt * TL;
       __syncthreads();
-      for (int e = threadIdx.x; e < TL * TL * TL; e += blockDim.x) {
-        const int c = e % TL, b = (e / TL) % TL, a = e / (TL * TL);
-        const int ga = lo[0] + a, gb = lo[1] + b, gc = lo[2] + c;
-        cube[a][b][c] = (ga < v && gb < v && gc < v) ? xm[((i64)ga * v + gb) * v + gc] : 0.f;
+      {  // X cube along c: thread (b, c) = (lm, lf), 16 loads in flight
+        const int gb = lo1 + lm, gc = lo2 + lf;
+        const bool in = gb < v && gc < v;
+        float ld[TL];
+#pragma unroll
+        for (int a = 0; a < TL; ++a) ld[a] = (in && lo0 + a < v) ? __ldg(xm + (lo0 + a) * V2 + (i64)gb * v + gc) : 0.f;
+#pragma unroll
+        for (int a = 0; a < TL; ++a) cube[a][lm][lf] = ld[a];
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < TL * TL * TL; e += blockDim.x) {
-        int u[3];
-        u[fast] = e % TL;
-        u[s1] = (e / TL) % TL;
-        u[s2] = e / (TL * TL);
-        const int ga = lo[0] + u[0], gb = lo[1] + u[1], gc = lo[2] + u[2];
-        if (ga < v && gb < v && gc < v) {
-          const i64 off = base + ga * st[0] + gb * st[1] + gc * st[2];
-          C[off] = C[off] + al * (T)cube[u[0]][u[1]][u[2]];
-        }
+      // add along the target's unit-stride axis: slot fast = lf, mid = lm, slow = u
+      const int lofast = fast == 0 ? lo0 : (fast == 1 ? lo1 : lo2);
+      const int lomid = mid == 0 ? lo0 : (mid == 1 ? lo1 : lo2);
+      const int loslow = slow == 0 ? lo0 : (slow == 1 ? lo1 : lo2);
+      const int gf = lofast + lf, gm = lomid + lm;
+      if (gf < v && gm < v) {
+        T* dst = C + base + gf + gm * stm + (i64)loslow * sts;
+        const float* src = &cube[0][0][0] + lf * cF + lm * cM;
+        const int nu = min(TL, v - loslow);
+        T old[TL];
+#pragma unroll
+        for (int u = 0; u < TL; ++u) old[u] = u < nu ? dst[u * sts] : (T)0;
+#pragma unroll
+        for (int u = 0; u < TL; ++u)
+          if (u < nu) dst[u * sts] = old[u] + al * (T)src[u * cS];
       }
     }
   }

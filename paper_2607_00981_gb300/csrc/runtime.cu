@@ -305,7 +305,7 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 void make_pack(rccsdt_ctx* c, PackPlan& P, const void* src, int src_f32, int R, int K, int nterm,
                const std::vector<double>& coef, const std::vector<i64>& colbase,
                const std::vector<int>& sel, const std::vector<i64>& rowoff, int read_k_fast, int* err,
-               const i64* shared_rowoff = nullptr) {
+               const i64* shared_rowoff = nullptr, int row_mode = 0) {
   P.coef = upload_vec(c, coef, err);
   P.colbase = upload_vec(c, colbase, err);
   P.sel = upload_vec(c, sel, err);
@@ -324,6 +324,9 @@ void make_pack(rccsdt_ctx* c, PackPlan& P, const void* src, int src_f32, int R, 
   a.one_sel = 1;
   for (int x : sel)
     if (x != 0) a.one_sel = 0;
+  // the shared selector tables are the computed forms (rows = 2 or 3 virtual labels)
+  a.row_mode = row_mode;
+  a.lv = c->v;
 }
 
 void make_epi(rccsdt_ctx* c, EpiPlan& E, void* C, int c_f32, int M, int N,
@@ -990,7 +993,7 @@ int build_context(rccsdt_ctx* c) {
       }
       make_pack(c, g->A, c->D("Wt_oooo"), 0, M, K, 1, std::vector<double>(K, 0.5), acol, std::vector<int>(K, 0),
                 arow, 0, &err);
-      make_pack(c, g->B, t3p, t3f, (int)V3, K, 1, std::vector<double>(K, 1.0), bcol, bsel, {}, 0, &err, b.RT3);
+      make_pack(c, g->B, t3p, t3f, (int)V3, K, 1, std::vector<double>(K, 1.0), bcol, bsel, {}, 0, &err, b.RT3, 3);
       make_epi(c, g->E, r3p, t3f, M, (int)V3, ebase, esel, ealpha, {}, &err, b.RT3);
       g->big = 1;
       g->step = 3;
@@ -1042,7 +1045,7 @@ int build_context(rccsdt_ctx* c) {
         }
         make_pack(c, g->A, c->D("Wring_ab"), 0, M, K, 1, std::vector<double>(K, 1.0), acol, std::vector<int>(K, 0),
                   arow, 1, &err);
-        make_pack(c, g->B, t3p, t3f, (int)V2, K, 3, bcoef, bcol, bsel, {}, 0, &err, b.RT2);
+        make_pack(c, g->B, t3p, t3f, (int)V2, K, 3, bcoef, bcol, bsel, {}, 0, &err, b.RT2, 2);
         make_epi(c, g->E, r3p, t3f, M, (int)V2, ebase, esel, ealpha, {}, &err, b.RT2);
         g->big = 1;
         g->step = 2;
@@ -1091,7 +1094,7 @@ int build_context(rccsdt_ctx* c) {
         }
         make_pack(c, g->A, c->D("Wring_c"), 0, M, K, 1, std::vector<double>(K, 1.0), acol, std::vector<int>(K, 0),
                   arow, 1, &err);
-        make_pack(c, g->B, t3p, t3f, (int)V2, K, 1, std::vector<double>(K, 1.0), bcol, bsel, {}, 0, &err, b.RT2);
+        make_pack(c, g->B, t3p, t3f, (int)V2, K, 1, std::vector<double>(K, 1.0), bcol, bsel, {}, 0, &err, b.RT2, 2);
         make_epi(c, g->E, r3p, t3f, M, (int)V2, ebase, esel, ealpha, {}, &err, b.RT2);
         g->big = 1;
         g->step = 2;

@@ -517,12 +517,36 @@ __global__ void __launch_bounds__(256) k_update_t3(T* __restrict__ t3, const T* 
   const i64 V2 = (i64)v * v;
   T* tb = t3 + (b * v + a) * V2;
   const T* rb = rp3 + (b * v + a) * V2;
-  for (int bb = threadIdx.y; bb < v; bb += 8) {
-    const double eab = ea - e[o + bb];
-    for (int c = threadIdx.x; c < v; c += 32) {
-      const int idx = bb * v + c;
-      const T d = (T)(eab - e[o + c]);
-      tb[idx] = tb[idx] + rb[idx] / d;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 storage: the FP64 row parts e_ijk - e_a - e_b and the e_c are carried as
+    // float pairs (hi + lo) in shared memory, so the FP32 denominator is the FP64
+    // one rounded once, without FP64 arithmetic per element
+    extern __shared__ float upd_smem[];  // 4 v floats (launch_update_t3)
+    float *rh = upd_smem, *rl = rh + v, *ch = rl + v, *cl = ch + v;
+    for (int q = threadIdx.y * 32 + threadIdx.x; q < v; q += 256) {
+      const double eab = ea - e[o + q], ec = e[o + q];
+      rh[q] = (float)eab;
+      rl[q] = (float)(eab - (double)rh[q]);
+      ch[q] = (float)ec;
+      cl[q] = (float)(ec - (double)ch[q]);
+    }
+    __syncthreads();
+    for (int bb = threadIdx.y; bb < v; bb += 8) {
+      const float eh = rh[bb], el = rl[bb];
+      for (int c = threadIdx.x; c < v; c += 32) {
+        const int idx = bb * v + c;
+        const float d = (eh - ch[c]) + (el - cl[c]);
+        tb[idx] = tb[idx] + rb[idx] / d;
+      }
+    }
+  } else {
+    for (int bb = threadIdx.y; bb < v; bb += 8) {
+      const double eab = ea - e[o + bb];
+      for (int c = threadIdx.x; c < v; c += 32) {
+        const int idx = bb * v + c;
+        const T d = (T)(eab - e[o + c]);
+        tb[idx] = tb[idx] + rb[idx] / d;
+      }
     }
   }
 }
@@ -543,7 +567,13 @@ void launch_update_t3(T* t3, const T* rp3, const double* e, const int4* blocks, 
                       double shift, cudaStream_t s) {
   if (n3 <= 0) return;
   ++g_launch_count;
-  k_update_t3<T><<<dim3((unsigned)v, (unsigned)n3), dim3(32, 8), 0, s>>>(t3, rp3, e, blocks, o, v, shift);
+  const size_t smem = sizeof(T) == 4 ? (size_t)16 * v : 0;
+  static bool attr = false;
+  if (!attr) {  // v up to 4096: 64 KB of float pairs
+    cudaFuncSetAttribute(k_update_t3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * 4096);
+    attr = true;
+  }
+  k_update_t3<T><<<dim3((unsigned)v, (unsigned)n3), dim3(32, 8), smem, s>>>(t3, rp3, e, blocks, o, v, shift);
 }
 template void launch_update_t3<double>(double*, const double*, const double*, const int4*, int, int,
                                        i64, double, cudaStream_t);
@@ -595,22 +625,46 @@ __host__ __device__ inline Pieces make_pieces(i64 n, i64 seg, bool weighted, int
   return q;
 }
 
-// sum_i x[i] y[i] over [b0, b1) by this block's threads, four loads in flight each
+// sum_i x[i] y[i] over [b0, b1) by this block's threads, four loads in flight each.
+// FP32 data: products and runs of 32 terms are summed in FP32 and every run is
+// added to an FP64 total (the FP64 pipe of this part does about 2 operations per
+// clock per SM, too few for one conversion and FMA per element).
 template <typename T>
 __device__ __forceinline__ double dot_range(const T* __restrict__ x, const T* __restrict__ y, i64 b0, i64 b1) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   const i64 step = blockDim.x;
   i64 i = b0 + threadIdx.x;
-  for (; i + 3 * step < b1; i += 4 * step) {
-    const T x0 = x[i], x1 = x[i + step], x2 = x[i + 2 * step], x3 = x[i + 3 * step];
-    const T y0 = y[i], y1 = y[i + step], y2 = y[i + 2 * step], y3 = y[i + 3 * step];
-    s0 += (double)x0 * (double)y0;
-    s1 += (double)x1 * (double)y1;
-    s2 += (double)x2 * (double)y2;
-    s3 += (double)x3 * (double)y3;
+  if constexpr (sizeof(T) == 4) {
+    double tot = 0.0;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int run = 0;
+    for (; i + 3 * step < b1; i += 4 * step) {
+      const float x0 = x[i], x1 = x[i + step], x2 = x[i + 2 * step], x3 = x[i + 3 * step];
+      const float y0 = y[i], y1 = y[i + step], y2 = y[i + 2 * step], y3 = y[i + 3 * step];
+      s0 = fmaf(x0, y0, s0);
+      s1 = fmaf(x1, y1, s1);
+      s2 = fmaf(x2, y2, s2);
+      s3 = fmaf(x3, y3, s3);
+      if (++run == 8) {
+        tot += (double)((s0 + s1) + (s2 + s3));
+        s0 = s1 = s2 = s3 = 0.f;
+        run = 0;
+      }
+    }
+    for (; i < b1; i += step) s0 = fmaf((float)x[i], (float)y[i], s0);
+    return tot + (double)((s0 + s1) + (s2 + s3));
+  } else {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (; i + 3 * step < b1; i += 4 * step) {
+      const T x0 = x[i], x1 = x[i + step], x2 = x[i + 2 * step], x3 = x[i + 3 * step];
+      const T y0 = y[i], y1 = y[i + step], y2 = y[i + 2 * step], y3 = y[i + 3 * step];
+      s0 += (double)x0 * (double)y0;
+      s1 += (double)x1 * (double)y1;
+      s2 += (double)x2 * (double)y2;
+      s3 += (double)x3 * (double)y3;
+    }
+    for (; i < b1; i += step) s0 += (double)x[i] * (double)y[i];
+    return (s0 + s1) + (s2 + s3);
   }
-  for (; i < b1; i += step) s0 += (double)x[i] * (double)y[i];
-  return (s0 + s1) + (s2 + s3);
 }
 
 template <typename T>
@@ -741,11 +795,35 @@ __global__ void k_diis_dots(const char* __restrict__ hist_e, i64 stride, i64 off
     double ss[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) ss[q] = 0.0;
-    for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-      const double x = (double)es[i];
+    if constexpr (sizeof(T) == 4) {
+      // runs of 16 terms per thread in FP32, added to FP64 (see dot_range)
+      float fs[16];
+      int run = 0;
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (q < m) ss[q] += x * (double)((const T*)(hist_e + (i64)q * stride + off))[i];
+      for (int q = 0; q < 16; ++q) fs[q] = 0.f;
+      for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        const float x = es[i];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (q < m) fs[q] = fmaf(x, ((const float*)(hist_e + (i64)q * stride + off))[i], fs[q]);
+        if (++run == 16) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            ss[q] += (double)fs[q];
+            fs[q] = 0.f;
+          }
+          run = 0;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) ss[q] += (double)fs[q];
+    } else {
+      for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        const double x = (double)es[i];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (q < m) ss[q] += x * (double)((const T*)(hist_e + (i64)q * stride + off))[i];
+      }
     }
     const double wt = w ? w[sg] : 1.0;
 #pragma unroll

@@ -106,12 +106,124 @@ __device__ __forceinline__ void pack_tiles(const PackArgs& a, int r0, int kfirst
   }
 }
 
+// Lean FP32-source gather into split panels (the common case): NT terms at most,
+// panel kind KIND, 32-bit offsets inside a stored block (v^3 < 2^31), one row
+// pointer per output row.  Same tiles and semantics as pack_tiles<true>.
+template <int NT, int KIND>
+__device__ __forceinline__ void pack_tiles_f32(const PackArgs& a, int r0, int kfirst, int kstep) {
+  __shared__ float tile[32][33];
+  __shared__ i64 cb[NT][32];
+  __shared__ float cf[NT][32];
+  __shared__ int sl[NT][32];
+  __shared__ int cs[NT][3][32];
+  __shared__ i64 ro[32];
+  __shared__ int lab[3][32];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int nterm = a.nterm < NT ? a.nterm : NT;
+  const int rm = a.row_mode;
+  const float* src = (const float*)a.src;
+  if (tid < 32) {
+    const int r = r0 + tid < a.R ? r0 + tid : 0, lv = a.lv;
+    if (rm) {
+      lab[0][tid] = rm == 2 ? r / lv : r / (lv * lv);
+      lab[1][tid] = rm == 2 ? r % lv : (r / lv) % lv;
+      lab[2][tid] = rm == 2 ? 0 : r % lv;
+    } else if (a.one_sel) {
+      ro[tid] = a.rowoff[r];
+    }
+  }
+  auto value = [&](int rr, int kk) -> float {
+    float s = 0.f;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      if (t >= nterm) break;
+      const float c = cf[t][kk];
+      if (c != 0.f) {
+        i64 off = cb[t][kk];
+        if (rm)
+          off += lab[0][rr] * cs[t][0][kk] + lab[1][rr] * cs[t][1][kk] + lab[2][rr] * cs[t][2][kk];
+        else
+          off += a.one_sel ? ro[rr] : a.rowoff[(i64)sl[t][kk] * a.R + r0 + rr];
+        s = fmaf(c, __ldg(src + off), s);
+      }
+    }
+    return s;
+  };
+  auto store = [&](int r, int k, float x) {
+    const i64 o = (i64)r * a.Kpad + k;
+    if constexpr (KIND == PANEL_BF16X2) {
+      const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+      ((__nv_bfloat16*)a.out_hi)[o] = hi;
+      ((__nv_bfloat16*)a.out_lo)[o] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    } else {
+      const float hi = tf32_round(x);
+      ((float*)a.out_hi)[o] = hi;
+      ((float*)a.out_lo)[o] = tf32_round(x - hi);
+    }
+  };
+  for (int k0 = kfirst; k0 < a.Kpad; k0 += kstep) {
+    __syncthreads();
+    if (tid < nterm * 32) {
+      const int t = tid >> 5, kk = tid & 31, k = k0 + kk;
+      const bool ok = k < a.K;
+      const i64 idx = (i64)t * a.K + k;
+      cb[t][kk] = ok ? a.colbase[idx] : 0;
+      cf[t][kk] = ok ? (float)a.coef[idx] : 0.f;
+      const int sel = ok ? a.sel[idx] : 0;
+      sl[t][kk] = sel;
+      if (rm) {
+        const int v = a.lv;
+        auto S = [&](int axis) { return axis == 0 ? v * v : (axis == 1 ? v : 1); };
+        cs[t][0][kk] = rm == 2 ? S(sel / 3) : S(perm3(sel, 0));
+        cs[t][1][kk] = rm == 2 ? S(sel % 3) : S(perm3(sel, 1));
+        cs[t][2][kk] = rm == 2 ? 0 : S(perm3(sel, 2));
+      }
+    }
+    __syncthreads();
+    if (a.read_k_fast) {
+      float x[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = (r0 + ty + 8 * j < a.R && k0 + tx < a.Kpad) ? value(ty + 8 * j, tx) : 0.f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (r0 + ty + 8 * j < a.R && k0 + tx < a.Kpad) store(r0 + ty + 8 * j, k0 + tx, x[j]);
+    } else {
+      float x[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = (r0 + tx < a.R) ? value(tx, ty + 8 * j) : 0.f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) tile[ty + 8 * j][tx] = x[j];
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = r0 + ty + 8 * j, k = k0 + tx;
+        if (r < a.R && k < a.Kpad) store(r, k, tile[tx][ty + 8 * j]);
+      }
+    }
+  }
+}
+
+template <bool F32>
+__device__ __forceinline__ void pack_tiles_any(const PackArgs& a, int r0, int kfirst, int kstep) {
+  if constexpr (F32) {
+    if (a.nterm <= 1) {
+      if (a.kind == PANEL_BF16X2) pack_tiles_f32<1, PANEL_BF16X2>(a, r0, kfirst, kstep);
+      else pack_tiles_f32<1, PANEL_TF32X2>(a, r0, kfirst, kstep);
+    } else {
+      if (a.kind == PANEL_BF16X2) pack_tiles_f32<3, PANEL_BF16X2>(a, r0, kfirst, kstep);
+      else pack_tiles_f32<3, PANEL_TF32X2>(a, r0, kfirst, kstep);
+    }
+  } else {
+    pack_tiles<false>(a, r0, kfirst, kstep);
+  }
+}
+
 // One 32 x 32 tile per step; the tile's column tables (coefficient, base offset,
 // selector of up to 3 terms) and, with a single selector, its 32 row offsets
 // are staged in shared memory, so an element costs one source load.
 template <bool F32>
 __global__ void __launch_bounds__(256) k_pack(PackArgs a) {
-  pack_tiles<F32>(a, blockIdx.x * 32, blockIdx.y * 32, gridDim.y * 32);
+  pack_tiles_any<F32>(a, blockIdx.x * 32, blockIdx.y * 32, gridDim.y * 32);
 }
 
 void launch_pack(const PackArgs& a, cudaStream_t s) {
@@ -141,7 +253,7 @@ __global__ void __launch_bounds__(256) k_pack_grouped(const PackArgs* __restrict
   const PackArgs a = list[lo];
   const int kt = (a.Kpad + 31) / 32;
   const int local = b - tile0[lo];
-  pack_tiles<F32>(a, (local / kt) * 32, (local % kt) * 32, 1 << 30);
+  pack_tiles_any<F32>(a, (local / kt) * 32, (local % kt) * 32, 1 << 30);
 }
 
 int pack_tiles_of(const PackArgs& a) { return ((a.R + 31) / 32) * ((a.Kpad + 31) / 32); }

@@ -160,11 +160,14 @@ def config(args, inst):
                         f"compact T3 {inst.o * (inst.o + 1) * (inst.o + 2) // 6} x {inst.v}^3, seed {inst.seed}",
             "o": inst.o, "v": inst.v, "naux": inst.naux, "precision": args.precision,
             "l2": "inputs larger than L2 (compact T3/R3 and the operand panels exceed 129 MB)",
-            "amplitudes": "MP2 guess, then the benchmark's own iterations"}
+            "amplitudes": "MP2 guess, then the benchmark's own iterations",
+            "coupling": ("weak: factor entries scaled by 0.6*0.3*sqrt(40/naux) (the literal 0.3 diverges and "
+                         "overflows FP32 T3 within a few iterations; the work per iteration is the same)"
+                         if args.workload.endswith("w") else "literal per-entry scale 0.3")}
 
 
-def compare_fp64_split(pkg, stream, dev, name="o8v80", warm=2, steps=2):
-    """FP64 and 3xBF16 s/iteration on the same o8v80 workload (same MP2 start)."""
+def compare_fp64_split(pkg, stream, dev, name="o8v80w", warm=2, steps=2):
+    """FP64, 3xBF16 and 3xTF32 s/iteration on the same o8v80 shapes (same MP2 start)."""
     import torch
     from paper_2607_00981_gb300.synth import workload
     inst = workload(name)
@@ -422,12 +425,12 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="o16v160")
+    ap.add_argument("--workload", default="o16v160w")
     ap.add_argument("--precision", default="bf16x3", choices=list(PRECISIONS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-diis-t3", action="store_true")
-    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 vs split comparison at o8v80")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 vs split comparison at o8v80w")
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instance workload")
     args = ap.parse_args()

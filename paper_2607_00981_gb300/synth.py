@@ -70,6 +70,8 @@ WORKLOADS = {
 CONVERGENCE = {
     "o6v48w": dict(o=6, v=48, naux=216, seed=7, scale=0.6 * 0.3 * (40 / 216) ** 0.5),
     "o8v80w": dict(o=8, v=80, naux=320, seed=0, scale=0.6 * 0.3 * (40 / 320) ** 0.5),
+    "o12v120w": dict(o=12, v=120, naux=480, seed=0, scale=0.6 * 0.3 * (40 / 480) ** 0.5),
+    "o16v160w": dict(o=16, v=160, naux=640, seed=0, scale=0.6 * 0.3 * (40 / 640) ** 0.5),
 }
 
 

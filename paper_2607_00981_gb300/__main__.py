@@ -11,18 +11,18 @@ import sys
 import time
 
 import paper_2607_00981_gb300 as pkg
-from paper_2607_00981_gb300.synth import WORKLOADS, make_instance
+from paper_2607_00981_gb300.synth import CONVERGENCE, WORKLOADS, make_instance
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2607_00981_gb300")
-    ap.add_argument("--workload", default="o3v12", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="o3v12", choices=sorted(WORKLOADS) + sorted(CONVERGENCE))
     ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "bf16x3", "tf32x3"])
     ap.add_argument("--scale", type=float, default=None, help="override the factor entry scale")
     ap.add_argument("--no-diis-t3", action="store_true", help="DIIS on T1 and T2 only")
     args = ap.parse_args(argv)
-    spec = dict(WORKLOADS[args.workload])
+    spec = dict(WORKLOADS.get(args.workload) or CONVERGENCE[args.workload])
     if args.scale is not None:
         spec["scale"] = args.scale
     inst = make_instance(**spec)

@@ -1,0 +1,264 @@
+// Operand panels read from compact T3 blocks through 16^3 (or 8^3) cubes.
+//
+// The tensor-core operands of the ring and hh-ladder terms are unpacked T3 blocks
+// (Sec. II.C.2): each "piece" of a panel is one stored v^3 block, or a linear
+// combination of up to three label permutations of stored blocks (the spin
+// summation 2U^{dbc} - U^{bdc} - U^{cbd}), written into the K-major panel.  A
+// table-driven gather reads such a block with the virtual axes permuted, which for
+// most permutations touches one 32-byte sector per element.  Here a CTA stages a
+// cube of the labels in shared memory, reading every source cube along its stored
+// unit-stride axis, and writes the panel in runs along K:
+//   mode 0  the piece's label L0 runs along K (K = k0 + L0) and the rows are
+//           row0 + L1 v + L2 (ring terms: K = (part, l, d), rows (b, c) or (a, c));
+//   mode 1  each piece is one column (K = k0) of one term and the rows are
+//           row0 + L0 v^2 + L1 v + L2 (hh-ladder: K = (l, m), rows (a, b, c)); a CTA
+//           takes 16 consecutive columns and an 8^3 cube of rows.
+// A term's `pos` packs the stored axis of labels L0, L1, L2 (2 bits each).
+#include <cstdint>
+
+#include "elem.cuh"
+#include "kernels.h"
+
+namespace rcc {
+namespace {
+
+__device__ __forceinline__ int pos_of(int pos, int q) { return (pos >> (2 * q)) & 3; }
+__device__ __forceinline__ i64 axis_stride(int axis, int v) {
+  return axis == 0 ? (i64)v * v : (axis == 1 ? (i64)v : (i64)1);
+}
+
+template <int KIND>
+__device__ __forceinline__ void store_run(const CubeDst& d, i64 row, int k, const float (&x)[16], int n, bool vec) {
+  // n <= 16 consecutive K values of one row
+  if constexpr (KIND == PANEL_BF16X2) {
+    __nv_bfloat16* hi = (__nv_bfloat16*)d.out_hi + row * d.Kpad + k;
+    __nv_bfloat16* lo = (__nv_bfloat16*)d.out_lo + row * d.Kpad + k;
+    if (vec && n == 16) {
+      uint32_t h[8], l[8];  // bf16 pairs, first element in the low half
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * j]), h1 = __float2bfloat16_rn(x[2 * j + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * j] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * j + 1] - __bfloat162float(h1));
+        h[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        l[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      }
+      ((uint4*)hi)[0] = make_uint4(h[0], h[1], h[2], h[3]);
+      ((uint4*)hi)[1] = make_uint4(h[4], h[5], h[6], h[7]);
+      ((uint4*)lo)[0] = make_uint4(l[0], l[1], l[2], l[3]);
+      ((uint4*)lo)[1] = make_uint4(l[4], l[5], l[6], l[7]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (j < n) {
+          const __nv_bfloat16 h = __float2bfloat16_rn(x[j]);
+          hi[j] = h;
+          lo[j] = __float2bfloat16_rn(x[j] - __bfloat162float(h));
+        }
+    }
+  } else {
+    float* hi = (float*)d.out_hi + row * d.Kpad + k;
+    float* lo = (float*)d.out_lo + row * d.Kpad + k;
+    if (vec && n == 16) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          h[j] = tf32_round(x[4 * q + j]);
+          l[j] = tf32_round(x[4 * q + j] - h[j]);
+        }
+        ((float4*)hi)[q] = make_float4(h[0], h[1], h[2], h[3]);
+        ((float4*)lo)[q] = make_float4(l[0], l[1], l[2], l[3]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (j < n) {
+          const float h = tf32_round(x[j]);
+          hi[j] = h;
+          lo[j] = tf32_round(x[j] - h);
+        }
+    }
+  }
+}
+
+// Mode 0: grid (label cubes of 16^3, pieces).  Shared: one [16][17][18] cube per term.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_cube_pack_k(const CubePiece* __restrict__ pieces,
+                                                     const CubeDst* __restrict__ dsts, CubeDst d0,
+                                                     const float* __restrict__ src, int v) {
+  constexpr int TL = 16, CA = (TL + 1) * (TL + 2), CB = TL + 2;
+  extern __shared__ __align__(16) float cube_smem[];
+  const CubePiece& P = pieces[blockIdx.y];
+  const int nterm = P.nterm;
+  const int nc = (v + TL - 1) / TL;
+  const int cb = blockIdx.x;
+  const int lo[3] = {(cb / (nc * nc)) * TL, ((cb / nc) % nc) * TL, (cb % nc) * TL};
+  const int lf = threadIdx.x & 15, lm = threadIdx.x >> 4;
+  for (int t = 0; t < nterm; ++t) {
+    const int pos = P.t[t].pos;
+    const int p0 = pos_of(pos, 0), p1 = pos_of(pos, 1);
+    // label on the stored unit-stride axis, then the other two
+    const int fast = p0 == 2 ? 0 : (p1 == 2 ? 1 : 2);
+    const int mid = fast == 0 ? 1 : 0, slow = 3 - fast - mid;
+    const i64 sm = axis_stride(pos_of(pos, mid), v), ss = axis_stride(pos_of(pos, slow), v);
+    const int cf = fast == 0 ? CA : (fast == 1 ? CB : 1), cmid = mid == 0 ? CA : (mid == 1 ? CB : 1),
+              cs = slow == 0 ? CA : (slow == 1 ? CB : 1);
+    const int xf = (fast == 0 ? lo[0] : fast == 1 ? lo[1] : lo[2]) + lf;
+    const int xm = (mid == 0 ? lo[0] : mid == 1 ? lo[1] : lo[2]) + lm;
+    const int xs = slow == 0 ? lo[0] : slow == 1 ? lo[1] : lo[2];
+    const bool in = xf < v && xm < v;
+    const float* s0 = src + P.t[t].base + xf + xm * sm + (i64)xs * ss;
+    float ld[TL];
+#pragma unroll
+    for (int u = 0; u < TL; ++u) ld[u] = (in && xs + u < v) ? __ldg(s0 + u * ss) : 0.f;
+    float* c = cube_smem + t * TL * CA + lf * cf + lm * cmid;
+#pragma unroll
+    for (int u = 0; u < TL; ++u) c[u * cs] = ld[u];
+  }
+  __syncthreads();
+  // thread (L1, L2) = (lm, lf) writes its row's run of 16 K values (L0)
+  const int g1 = lo[1] + lm, g2 = lo[2] + lf;
+  if (g1 >= v || g2 >= v) return;
+  float x[TL];
+#pragma unroll
+  for (int u = 0; u < TL; ++u) x[u] = 0.f;
+  for (int t = 0; t < nterm; ++t) {
+    const float cf = P.t[t].coef;
+    const float* c = cube_smem + t * TL * CA + lm * CB + lf;
+#pragma unroll
+    for (int u = 0; u < TL; ++u) x[u] = fmaf(cf, c[u * CA], x[u]);
+  }
+  const CubeDst d = dsts ? dsts[P.dst] : d0;
+  const int n = min(TL, v - lo[0]);
+  const int k = P.k0 + lo[0];
+  const bool vec = (k & 7) == 0 && (KIND == PANEL_BF16X2 || (k & 3) == 0);
+  store_run<KIND>(d, P.row0 + (i64)g1 * v + g2, k, x, n, vec);
+}
+
+// Mode 1: grid (label cubes of 8^3, groups of 16 pieces = 16 consecutive columns).
+template <int KIND>
+__global__ void __launch_bounds__(256) k_cube_pack_col(const CubePiece* __restrict__ pieces,
+                                                       const CubeDst* __restrict__ dsts, CubeDst d0,
+                                                       const float* __restrict__ src, int v) {
+  constexpr int TL = 8, CS = TL * TL * (TL + 1) + 1;  // one padded 8^3 cube per column
+  __shared__ float cols[16 * CS];
+  const int nc = (v + TL - 1) / TL;
+  const int cb = blockIdx.x;
+  const int lo[3] = {(cb / (nc * nc)) * TL, ((cb / nc) % nc) * TL, (cb % nc) * TL};
+  const CubePiece* G = pieces + (i64)blockIdx.y * 16;
+  const int tid = threadIdx.x;
+  for (int c = 0; c < 16; ++c) {
+    const CubePiece& P = G[c];
+    float acc[2] = {0.f, 0.f};
+    for (int t = 0; t < (P.nterm > 0 ? 1 : 0); ++t) {  // one term per column
+      const int pos = P.t[t].pos;
+      const int p0 = pos_of(pos, 0), p1 = pos_of(pos, 1);
+      const int fast = p0 == 2 ? 0 : (p1 == 2 ? 1 : 2);
+      const int mid = fast == 0 ? 1 : 0, slow = 3 - fast - mid;
+      const i64 sm = axis_stride(pos_of(pos, mid), v), ss = axis_stride(pos_of(pos, slow), v);
+      const float cf = P.t[t].coef;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = tid + 256 * h;  // (slow, mid, fast) of 8^3
+        const int uf = e & 7, um = (e >> 3) & 7, us = e >> 6;
+        const int xf = (fast == 0 ? lo[0] : fast == 1 ? lo[1] : lo[2]) + uf;
+        const int xm = (mid == 0 ? lo[0] : mid == 1 ? lo[1] : lo[2]) + um;
+        const int xs = (slow == 0 ? lo[0] : slow == 1 ? lo[1] : lo[2]) + us;
+        if (xf < v && xm < v && xs < v) acc[h] = fmaf(cf, __ldg(src + P.t[t].base + xf + xm * sm + xs * ss), acc[h]);
+      }
+    }
+    // stage by label order (L0, L1, L2), whatever the load order was
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + 256 * h;
+      const int uf = e & 7, um = (e >> 3) & 7, us = e >> 6;
+      int u0 = 0, u1 = 0, u2 = 0;
+      if (P.nterm > 0) {
+        const int pos = P.t[0].pos;
+        const int p0 = pos_of(pos, 0), p1 = pos_of(pos, 1);
+        const int fast = p0 == 2 ? 0 : (p1 == 2 ? 1 : 2);
+        const int mid = fast == 0 ? 1 : 0;
+        u0 = fast == 0 ? uf : (mid == 0 ? um : us);
+        u1 = fast == 1 ? uf : (mid == 1 ? um : us);
+        u2 = fast == 2 ? uf : (mid == 2 ? um : us);
+      } else {
+        u0 = us;
+        u1 = um;
+        u2 = uf;
+      }
+      cols[c * CS + (u0 * TL + u1) * (TL + 1) + u2] = acc[h];
+    }
+  }
+  __syncthreads();
+  const CubeDst d = dsts ? dsts[G[0].dst] : d0;
+  const int k = G[0].k0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int e = tid + 256 * h;
+    const int u0 = e >> 6, u1 = (e >> 3) & 7, u2 = e & 7;
+    const int g0 = lo[0] + u0, g1 = lo[1] + u1, g2 = lo[2] + u2;
+    if (g0 >= v || g1 >= v || g2 >= v) continue;
+    float x[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) x[c] = cols[c * CS + (u0 * TL + u1) * (TL + 1) + u2];
+    store_run<KIND>(d, G[0].row0 + ((i64)g0 * v + g1) * v + g2, k, x, 16, true);
+  }
+}
+
+__global__ void k_zero_cols(CubeDst d, i64 rows, int k0, int esz) {
+  const int w = d.Kpad - k0;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < rows * w; i += (i64)gridDim.x * blockDim.x) {
+    const i64 r = i / w, k = k0 + i % w;
+    if (esz == 2) {
+      ((__nv_bfloat16*)d.out_hi)[r * d.Kpad + k] = __float2bfloat16_rn(0.f);
+      ((__nv_bfloat16*)d.out_lo)[r * d.Kpad + k] = __float2bfloat16_rn(0.f);
+    } else {
+      ((float*)d.out_hi)[r * d.Kpad + k] = 0.f;
+      ((float*)d.out_lo)[r * d.Kpad + k] = 0.f;
+    }
+  }
+}
+
+}  // namespace
+
+void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, const CubeDst* dsts,
+                      const CubeDst& d0, const float* src, int v, cudaStream_t s) {
+  if (npieces <= 0) return;
+  if (mode == 0) {
+    const int nc = (v + 15) / 16;
+    const size_t smem = (size_t)3 * 16 * 17 * 18 * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_cube_pack_k<PANEL_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_cube_pack_k<PANEL_TF32X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    dim3 grid((unsigned)(nc * nc * nc), (unsigned)npieces);
+    ++g_launch_count;
+    if (kind == PANEL_BF16X2)
+      k_cube_pack_k<PANEL_BF16X2><<<grid, 256, smem, s>>>(pieces, dsts, d0, src, v);
+    else
+      k_cube_pack_k<PANEL_TF32X2><<<grid, 256, smem, s>>>(pieces, dsts, d0, src, v);
+  } else {
+    const int nc = (v + 7) / 8;
+    dim3 grid((unsigned)(nc * nc * nc), (unsigned)(npieces / 16));
+    ++g_launch_count;
+    if (kind == PANEL_BF16X2)
+      k_cube_pack_col<PANEL_BF16X2><<<grid, 256, 0, s>>>(pieces, dsts, d0, src, v);
+    else
+      k_cube_pack_col<PANEL_TF32X2><<<grid, 256, 0, s>>>(pieces, dsts, d0, src, v);
+  }
+}
+
+void launch_zero_cols(const CubeDst& d, i64 rows, int k0, int kind, cudaStream_t s) {
+  if (k0 >= d.Kpad || rows <= 0) return;
+  const i64 n = rows * (d.Kpad - k0);
+  i64 blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  ++g_launch_count;
+  k_zero_cols<<<(unsigned)blocks, 256, 0, s>>>(d, rows, k0, kind == PANEL_BF16X2 ? 2 : 4);
+}
+
+}  // namespace rcc

@@ -222,7 +222,7 @@ __device__ __forceinline__ void pack_tiles_any(const PackArgs& a, int r0, int kf
 // selector of up to 3 terms) and, with a single selector, its 32 row offsets
 // are staged in shared memory, so an element costs one source load.
 template <bool F32>
-__global__ void __launch_bounds__(256) k_pack(PackArgs a) {
+__global__ void __launch_bounds__(256, 6) k_pack(PackArgs a) {
   pack_tiles_any<F32>(a, blockIdx.x * 32, blockIdx.y * 32, gridDim.y * 32);
 }
 
@@ -241,7 +241,7 @@ void launch_pack(const PackArgs& a, cudaStream_t s) {
 // tile0[p] <= b < tile0[p + 1] (row tiles outer, K tiles inner).  All gathers of
 // one launch share the source type (F32: FP32 sources into split panels).
 template <bool F32>
-__global__ void __launch_bounds__(256) k_pack_grouped(const PackArgs* __restrict__ list,
+__global__ void __launch_bounds__(256, 6) k_pack_grouped(const PackArgs* __restrict__ list,
                                                       const int* __restrict__ tile0, int npack) {
   const int b = blockIdx.x;
   int lo = 0, hi = npack - 1;

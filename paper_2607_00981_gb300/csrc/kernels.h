@@ -101,6 +101,31 @@ int gemm_tc_block_k(int kind);
 // tile0 prefix order, tables made with the same bn); grid <= 0 picks one CTA per SM.
 int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total_tiles, int grid, int bn,
                            int* status_flag, long long watchdog, cudaStream_t s);
+// Operand panels read from compact T3 through label cubes (cube_pack.cu).
+struct CubeTerm {
+  i64 base;    // element offset of the stored block
+  float coef;
+  int pos;     // stored axis of labels L0, L1, L2: pos0 | pos1 << 2 | pos2 << 4
+};
+struct CubePiece {
+  int dst;     // index into the destination table (0 without a table)
+  int k0;      // mode 0: panel column of L0 = 0; mode 1: the piece's column
+  i64 row0;    // panel row of the labels' origin
+  int nterm;   // 0 (zeros), 1..3 (mode 1: at most 1)
+  CubeTerm t[3];
+};
+struct CubeDst {
+  void* out_hi;
+  void* out_lo;
+  int Kpad;
+};
+// mode 0: K = k0 + L0, rows row0 + L1 v + L2 (pieces in any order);
+// mode 1: K = k0, rows row0 + L0 v^2 + L1 v + L2, pieces in groups of 16 consecutive
+// columns of one panel (npieces a multiple of 16).  Panels of `kind` (split).
+void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, const CubeDst* dsts,
+                      const CubeDst& d0, const float* src, int v, cudaStream_t s);
+// Zero the panel columns [k0, Kpad) of `rows` rows.
+void launch_zero_cols(const CubeDst& d, i64 rows, int k0, int kind, cudaStream_t s);
 // Second phase of a two-phase scatter: for each row m of the dense FP32 result X
 // [M][v^3] (natural (a,b,c) order), C[row_base[m] + perm_sel[m](a,b,c)] +=
 // row_alpha[m] * X[m][abc]; perm_sel indexes the 6 virtual permutations.

@@ -182,6 +182,10 @@ struct GemmPlan {
   std::vector<int> h_sel;
   std::vector<double> h_alpha;
   int swap_ab = 0;
+  // split modes: the B operand is gathered from T3 through label cubes (cube_pack.cu)
+  std::vector<rcc::CubePiece> h_cube;
+  std::unique_ptr<DBuf> cube;
+  int cube_mode = -1;
 };
 
 struct rccsdt_ctx {
@@ -233,6 +237,8 @@ struct rccsdt_ctx {
     std::unique_ptr<DBuf> panels, raw;
     std::unique_ptr<DBuf> packs[2], ptile[2];  // [0] FP64 sources, [1] FP32 sources
     int npack[2] = {0, 0}, ntile[2] = {0, 0};
+    std::unique_ptr<DBuf> cubes[2], cube_dst;     // label-cube gathers from T3, modes 0 and 1
+    int ncube[2] = {0, 0};
     std::unique_ptr<DBuf> probs;
     int nprob = 0, ntiles = 0, grid = 0;
     double flop = 0.0;
@@ -553,7 +559,16 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   pb.out_hi = c->panelB_hi->p;
   pb.out_lo = c->panelB_lo ? c->panelB_lo->p : nullptr;
   if (!g->reuse_A || c->packedA_kind != kind) rcc::launch_pack(pa, c->stream);
-  if (!g->reuse_B || c->packedB_kind != kind) rcc::launch_pack(pb, c->stream);
+  if (!g->reuse_B || c->packedB_kind != kind) {
+    if (tc && g->cube) {
+      const rcc::CubeDst d0{pb.out_hi, pb.out_lo, g->Kpad};
+      rcc::launch_cube_pack(g->cube_mode, kind, (const rcc::CubePiece*)g->cube->p, (int)g->h_cube.size(), nullptr,
+                            d0, (const float*)pb.src, c->v, c->stream);
+      if (g->cube_mode == 0) rcc::launch_zero_cols(d0, pb.R, g->K, kind, c->stream);
+    } else {
+      rcc::launch_pack(pb, c->stream);
+    }
+  }
   c->packedA_kind = c->packedB_kind = kind;
   const int tidx = g->step == 1 ? timer_begin(c, 16, 2.0 * g->fma) : -1;
   if (!tc) {
@@ -641,6 +656,22 @@ struct TripleInfo {
   int pos[3];
   int m;
 };
+
+int packpos(int a, int b, int c) { return a | (b << 2) | (c << 4); }
+
+rcc::CubePiece cube_piece(int k0, int nterm) {
+  rcc::CubePiece p;
+  memset(&p, 0, sizeof(p));
+  p.k0 = k0;
+  p.nterm = nterm;
+  return p;
+}
+
+void set_cube(rccsdt_ctx* c, GemmPlan* g, int mode, std::vector<rcc::CubePiece> pieces, int* err) {
+  g->cube_mode = mode;
+  g->h_cube = std::move(pieces);
+  g->cube = upload_vec(c, g->h_cube, err);
+}
 TripleInfo triple(int i, int j, int k) {
   TripleInfo t;
   int occ[3] = {i, j, k}, srt[3];
@@ -1006,6 +1037,20 @@ int build_context(rccsdt_ctx* c) {
         set_two_phase(c, g, ebase, ax, ealpha, &err);
       }
       finish_plan(c, g, K);
+      if (t3f) {  // B columns (l, m): the block t_{lmk} with rows (a, b, c); zero columns to Kpad
+        std::vector<rcc::CubePiece> pcs;
+        for (int q = 0; q < g->Kpad; ++q) {
+          rcc::CubePiece pc = cube_piece(q, q < K ? 1 : 0);
+          if (q < K) {
+            TripleInfo ti = triple(q / o, q % o, k);
+            pc.t[0].base = ti.blk * V3;
+            pc.t[0].coef = 1.f;
+            pc.t[0].pos = packpos(ti.pos[0], ti.pos[1], ti.pos[2]);
+          }
+          pcs.push_back(pc);
+        }
+        set_cube(c, g, 1, std::move(pcs), &err);
+      }
       c->p_hh.push_back(g);
     }
   }
@@ -1062,6 +1107,22 @@ int build_context(rccsdt_ctx* c) {
           set_two_phase(c, g, tb, ax, ta, &err);
         }
         finish_plan(c, g, K);
+        if (t3f) {  // B: labels (d, b, c), K = (part, l, d), rows (b, c)
+          std::vector<rcc::CubePiece> pcs;
+          for (int l = 0; l < o; ++l) {
+            TripleInfo u = triple(l, j, k), u1 = triple(j, l, k), u2 = triple(k, l, j);
+            rcc::CubePiece p0 = cube_piece(l * v, 3);
+            p0.t[0] = {u.blk * V3, 2.f, packpos(u.pos[0], u.pos[1], u.pos[2])};
+            p0.t[1] = {u.blk * V3, -1.f, packpos(u.pos[1], u.pos[0], u.pos[2])};
+            p0.t[2] = {u.blk * V3, -1.f, packpos(u.pos[2], u.pos[1], u.pos[0])};
+            rcc::CubePiece p1 = cube_piece(o * v + l * v, 2);
+            p1.t[0] = {u1.blk * V3, 1.f, packpos(u1.pos[0], u1.pos[1], u1.pos[2])};
+            p1.t[1] = {u2.blk * V3, 1.f, packpos(u2.pos[0], u2.pos[2], u2.pos[1])};
+            pcs.push_back(p0);
+            pcs.push_back(p1);
+          }
+          set_cube(c, g, 0, std::move(pcs), &err);
+        }
         c->p_ringab.push_back(g);
       }
   }
@@ -1111,6 +1172,16 @@ int build_context(rccsdt_ctx* c) {
           set_two_phase(c, g, tb, ax, ta, &err);
         }
         finish_plan(c, g, K);
+        if (t3f) {  // B: labels (d, a, c) of t_{jlk}, K = (l, d), rows (a, c)
+          std::vector<rcc::CubePiece> pcs;
+          for (int l = 0; l < o; ++l) {
+            TripleInfo u = triple(j, l, k);
+            rcc::CubePiece pc = cube_piece(l * v, 1);
+            pc.t[0] = {u.blk * V3, 1.f, packpos(u.pos[0], u.pos[1], u.pos[2])};
+            pcs.push_back(pc);
+          }
+          set_cube(c, g, 0, std::move(pcs), &err);
+        }
         c->p_ringc.push_back(g);
       }
   }
@@ -1191,6 +1262,7 @@ namespace {
 struct GPanel {
   const rcc::PackArgs* src;
   size_t hi = 0, lo = 0;  // byte offsets in the panel arena
+  const GemmPlan* cube = nullptr;  // gathered through label cubes (the plan's pieces)
 };
 
 // Problem table of the grouped GEMM for tile width bn and problem order ord
@@ -1255,6 +1327,7 @@ int build_grouped(rccsdt_ctx* c) {
     int ish = (g->reuse_A && q > 0) ? -1 : add_panel(shared);
     if (ish < 0) ish = plans[q - 1]->swap_ab ? pb[q - 1] : pa[q - 1];
     const int iot = add_panel(other);
+    if (!g->swap_ab && g->cube) panels[iot].cube = g;
     if (g->swap_ab) {
       pa[q] = iot;
       pb[q] = ish;
@@ -1288,10 +1361,24 @@ int build_grouped(rccsdt_ctx* c) {
   char* base = (char*)G.panels->p;
   float* raw = (float*)G.raw->p;
   // gathers, split by source type
+  // the padding columns of every panel stay zero (gathers write columns < K only)
+  if (dev_zero(G.panels->p, panel_bytes, c->stream) || dev_sync(c->stream))
+    return fail(c, RCCSDT_ERR_CUDA, "grouped residual: panel clear failed");
   std::vector<rcc::PackArgs> packs[2];
   std::vector<int> ptile[2];
+  std::vector<rcc::CubePiece> cubes[2];
+  std::vector<rcc::CubeDst> cdst;
   int tiles[2] = {0, 0};
   for (const GPanel& p : panels) {
+    if (p.cube) {
+      const int d = (int)cdst.size();
+      cdst.push_back({base + p.hi, base + p.lo, p.src->Kpad});
+      for (rcc::CubePiece pc : p.cube->h_cube) {
+        pc.dst = d;
+        cubes[p.cube->cube_mode].push_back(pc);
+      }
+      continue;
+    }
     rcc::PackArgs a = *p.src;
     a.kind = kind;
     a.out_hi = base + p.hi;
@@ -1308,7 +1395,10 @@ int build_grouped(rccsdt_ctx* c) {
       G.packs[t] = upload_vec(c, packs[t], &err);
       G.ptile[t] = upload_vec(c, ptile[t], &err);
     }
+    G.ncube[t] = (int)cubes[t].size();
+    if (G.ncube[t]) G.cubes[t] = upload_vec(c, cubes[t], &err);
   }
+  if (!cdst.empty()) G.cube_dst = upload_vec(c, cdst, &err);
   // problems (kept as sources so that other launch shapes can be encoded later)
   for (size_t q = 0; q < plans.size(); ++q) {
     GemmPlan* g = plans[q];
@@ -1439,6 +1529,11 @@ int run_grouped(rccsdt_ctx* c) {
     if (G.npack[t])
       rcc::launch_pack_grouped((const rcc::PackArgs*)G.packs[t]->p, (const int*)G.ptile[t]->p, G.npack[t], G.ntile[t],
                                t == 1, c->stream);
+  for (int m = 0; m < 2; ++m)
+    if (G.ncube[m])
+      rcc::launch_cube_pack(m, G.kind, (const rcc::CubePiece*)G.cubes[m]->p, G.ncube[m],
+                            (const rcc::CubeDst*)G.cube_dst->p, rcc::CubeDst{nullptr, nullptr, 0}, c->B("t3")->f(),
+                            c->v, c->stream);
   if (c->opt.autotune && !G.tuned) {
     const int st = autotune_grouped(c);
     if (st) return st;

@@ -79,6 +79,46 @@ void launch_combine(const CombineArgs& c, cudaStream_t) {
   }
 }
 
+static void host_store_split(int kind, void* hi, void* lo, long long o, float x) {
+  if (kind == PANEL_BF16X2) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    ((__nv_bfloat16*)hi)[o] = h;
+    ((__nv_bfloat16*)lo)[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+  } else {
+    const float h = tf32_round(x);
+    ((float*)hi)[o] = h;
+    ((float*)lo)[o] = tf32_round(x - h);
+  }
+}
+
+void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, const CubeDst* dsts,
+                      const CubeDst& d0, const float* src, int v, cudaStream_t) {
+  const i64 S[3] = {(i64)v * v, v, 1};
+  for (int q = 0; q < npieces; ++q) {
+    const CubePiece& P = pieces[q];
+    const CubeDst d = dsts ? dsts[P.dst] : d0;
+    const int nt = mode == 1 ? (P.nterm > 0 ? 1 : 0) : P.nterm;
+    for (int l0 = 0; l0 < v; ++l0)
+      for (int l1 = 0; l1 < v; ++l1)
+        for (int l2 = 0; l2 < v; ++l2) {
+          float x = 0.f;
+          for (int t = 0; t < nt; ++t) {
+            const int ps = P.t[t].pos;
+            const i64 off = P.t[t].base + l0 * S[ps & 3] + l1 * S[(ps >> 2) & 3] + l2 * S[(ps >> 4) & 3];
+            x = std::fma(P.t[t].coef, src[off], x);
+          }
+          const i64 row = mode == 0 ? P.row0 + (i64)l1 * v + l2 : P.row0 + ((i64)l0 * v + l1) * v + l2;
+          const i64 k = mode == 0 ? P.k0 + l0 : P.k0;
+          host_store_split(kind, d.out_hi, d.out_lo, row * d.Kpad + k, x);
+        }
+  }
+}
+
+void launch_zero_cols(const CubeDst& d, i64 rows, int k0, int kind, cudaStream_t) {
+  for (i64 r = 0; r < rows; ++r)
+    for (int k = k0; k < d.Kpad; ++k) host_store_split(kind, d.out_hi, d.out_lo, r * d.Kpad + k, 0.f);
+}
+
 int gemm_tc_block_k(int kind) { return kind == PANEL_BF16X2 ? 64 : 32; }
 
 int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int M,

@@ -43,7 +43,8 @@ struct TileCfg {
   static constexpr int B_PLANE = BN * ROWB;
   static constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;  // 96 KiB for BN = 256
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-  static constexpr int TMEM_COLS = 2 * BN;                        // double-buffered accumulator
+  static constexpr int TMEM_COLS = 2 * BN <= 256 ? 256 : 512;      // double-buffered accumulator (power of 2)
+  static constexpr int FULL = BN / 32, HALF = (BN % 32) / 16;      // 32- and 16-column epilogue chunks
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -121,6 +122,18 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 16; j < 32; ++j) r[j] = 0u;
+}
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
@@ -204,6 +217,7 @@ struct PlainSched {
   TileGeom g;
   EpiArgs e;
   float* partial;  // [splitk][M][N] partial tiles, or the dense raw result when splitk == 1
+  int colmajor;    // raw result stored as [N][M] (each thread's row runs along memory)
   __device__ __forceinline__ int ntiles() const { return g.mt * g.nt * g.splitk; }
   __device__ __forceinline__ void tile(int t, Tile& x) const {
     x.p = 0;
@@ -215,15 +229,22 @@ struct PlainSched {
   __device__ __forceinline__ const CUtensorMap* map(int q, const Tile&) const {
     return q == 0 ? &ah : q == 1 ? &al : q == 2 ? &bh : &bl;
   }
-  __device__ __forceinline__ void store(const Tile& x, int m, int n0, const uint32_t (&r)[32]) const {
+  __device__ __forceinline__ void store(const Tile& x, int m, int n0, const uint32_t (&r)[32], int ncols) const {
     if (m >= e.M) return;
-    if (partial) {
+    if (partial && colmajor) {
+      float* dst = partial + (i64)n0 * e.M + m;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < ncols && n0 + j < e.N) dst[(i64)j * e.M] = __uint_as_float(r[j]);
+    } else if (partial) {
       float* dst = partial + ((i64)x.ks * e.M + m) * e.N;
 #pragma unroll
       for (int j = 0; j < 32; ++j)
-        if (n0 + j < e.N) dst[n0 + j] = __uint_as_float(r[j]);
+        if (j < ncols && n0 + j < e.N) dst[n0 + j] = __uint_as_float(r[j]);
     } else {
-      epilogue_row(e, m, n0, r);
+      EpiArgs e2 = e;
+      if (ncols < 32) e2.N = min(e.N, n0 + ncols);
+      epilogue_row(e2, m, n0, r);
     }
   }
 };
@@ -254,12 +275,19 @@ struct GroupSched {
     const GProblem& P = probs[x.p];
     return q == 0 ? &P.ah : q == 1 ? &P.al : q == 2 ? &P.bh : &P.bl;
   }
-  __device__ __forceinline__ void store(const Tile& x, int m, int n0, const uint32_t (&r)[32]) const {
+  __device__ __forceinline__ void store(const Tile& x, int m, int n0, const uint32_t (&r)[32], int ncols) const {
     const GProblem& P = probs[x.p];
     const int M = __ldg(&P.M), N = __ldg(&P.N);
     if (m >= M) return;
+    if (__ldg(&P.colmajor)) {
+      float* dst = P.out + (i64)n0 * M + m;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < ncols && n0 + j < N) dst[(i64)j * M] = __uint_as_float(r[j]);
+      return;
+    }
     float* dst = P.out + (i64)m * N + n0;
-    if ((N & 3) == 0 && n0 + 32 <= N) {
+    if ((N & 3) == 0 && ncols == 32 && n0 + 32 <= N) {
 #pragma unroll
       for (int j = 0; j < 32; j += 4)
         *(float4*)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
@@ -267,7 +295,7 @@ struct GroupSched {
     } else {
 #pragma unroll
       for (int j = 0; j < 32; ++j)
-        if (n0 + j < N) dst[j] = __uint_as_float(r[j]);
+        if (j < ncols && n0 + j < N) dst[j] = __uint_as_float(r[j]);
     }
   }
 };
@@ -424,10 +452,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       fence_after();
       const int m = x.tm * BM + row;
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = 0; c < TileCfg<BN>::FULL; ++c) {
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c * 32), r);
-        sch.store(x, m, x.tn * BN + c * 32, r);
+        sch.store(x, m, x.tn * BN + c * 32, r, 32);
+      }
+      if constexpr (TileCfg<BN>::HALF) {
+        uint32_t r[32];
+        const int c0 = TileCfg<BN>::FULL * 32;
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0), r);
+        sch.store(x, m, x.tn * BN + c0, r, 16);
       }
       fence_before();
       __syncwarp();
@@ -506,18 +540,20 @@ template <class S>
 static void launch_any(int kind, int bn, const S& sch, int grid, int* status_flag, long long budget, cudaStream_t s) {
   if (kind == PANEL_BF16X2) {
     if (bn == 128) launch_sched<1, 128>(sch, grid, status_flag, budget, s);
+    else if (bn == 144) launch_sched<1, 144>(sch, grid, status_flag, budget, s);
     else launch_sched<1, 256>(sch, grid, status_flag, budget, s);
   } else {
     if (bn == 128) launch_sched<2, 128>(sch, grid, status_flag, budget, s);
+    else if (bn == 144) launch_sched<2, 144>(sch, grid, status_flag, budget, s);
     else launch_sched<2, 256>(sch, grid, status_flag, budget, s);
   }
 }
 
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int Kpad,
                    const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s, float* scratch,
-                   long long scratch_elems, float* raw_out, int bn) {
+                   long long scratch_elems, float* raw_out, int bn, int colmajor) {
   if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
-  const int BN = bn == 128 ? 128 : 256;
+  const int BN = (bn == 128 || bn == 144) ? bn : 256;
   const int esz = kind == PANEL_BF16X2 ? 2 : 4;
   const int bk = ROWB / esz;
   if (Kpad % bk != 0 || e.M <= 0 || e.N <= 0) return 1;
@@ -545,6 +581,7 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
   float* part = raw_out ? raw_out : (g.splitk > 1 ? scratch : nullptr);
   sch.e = e;
   sch.partial = part;
+  sch.colmajor = raw_out && colmajor ? 1 : 0;
   launch_any(kind, BN, sch, grid, status_flag, budget, s);
   if (part && !raw_out) {
     const long long MN = (long long)e.M * e.N;
@@ -561,7 +598,7 @@ int gemm_tc_block_k(int kind) { return ROWB / (kind == PANEL_BF16X2 ? 2 : 4); }
 int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int M,
                   int N, int Kpad, float* out, int bn) {
   if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
-  const int BN = bn == 128 ? 128 : 256;
+  const int BN = (bn == 128 || bn == 144) ? bn : 256;
   const int bk = gemm_tc_block_k(kind);
   if (Kpad % bk != 0 || M <= 0 || N <= 0) return 1;
   if (!make_map(&p->ah, Ahi, M, Kpad, kind, BM) || !make_map(&p->al, Alo, M, Kpad, kind, BM) ||
@@ -572,6 +609,7 @@ int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const
   p->b_hi = Bhi;
   p->b_lo = Blo;
   p->out = out;
+  p->colmajor = 0;
   p->M = M;
   p->N = N;
   p->Kpad = Kpad;
@@ -592,7 +630,7 @@ int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total
   sch.total = total_tiles;
   const int g = std::max(1, std::min(grid > 0 ? grid : num_sms(), total_tiles));
   const long long budget = watchdog > 0 ? watchdog : 4000000000LL;
-  launch_any(kind, bn == 128 ? 128 : 256, sch, g, status_flag, budget, s);
+  launch_any(kind, (bn == 128 || bn == 144) ? bn : 256, sch, g, status_flag, budget, s);
   return 0;
 }
 

@@ -74,10 +74,12 @@ void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t s);
 // `scratch` (scratch_elems floats) holds FP32 partial tiles when K is split.
 // With raw_out, the raw FP32 result is written densely to raw_out[m * N + n] (no
 // alpha, no scatter, no split-K) for a separate scatter pass.
-// bn: tile width, 256 (default) or 128 columns.
+// bn: tile width, 256 (default), 144 or 128 columns.
+// colmajor (raw output only): the result is stored as raw_out[n * M + m].
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo,
                    int Kpad, const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s,
-                   float* scratch, long long scratch_elems, float* raw_out = nullptr, int bn = 256);
+                   float* scratch, long long scratch_elems, float* raw_out = nullptr, int bn = 256,
+                   int colmajor = 0);
 // One GEMM of a grouped launch: X[M][N] = (Ahi Bhi + Ahi Blo + Alo Bhi) with A
 // [M][Kpad], B [N][Kpad] split panels; the tensor maps are encoded on the host
 // (make_gproblem) and the table is copied to device memory before the launch.
@@ -87,10 +89,10 @@ struct alignas(128) GProblem {
   const void* a_lo;
   const void* b_hi;
   const void* b_lo;
-  float* out;  // dense FP32 result, row-major [M][N]
+  float* out;  // dense FP32 result, row-major [M][N] (colmajor: [N][M])
   int M, N, Kpad, kblocks, mt, nt;
   int tile0;   // first tile of this problem in the launch's tile order (set by the caller)
-  int pad;
+  int colmajor;
 };
 // Fills p (except tile0) for panels of `kind`; nonzero if unsupported.
 int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int M,

@@ -182,6 +182,9 @@ struct GemmPlan {
   std::vector<int> h_sel;
   std::vector<double> h_alpha;
   int swap_ab = 0;
+  // split modes: the tensor-core GEMM runs with the operands exchanged and stores its
+  // result column-major (same dense layout), so that a short M becomes the tile width
+  int tc_swap = 0;
   // split modes: the B operand is gathered from T3 through label cubes (cube_pack.cu)
   std::vector<rcc::CubePiece> h_cube;
   std::unique_ptr<DBuf> cube;
@@ -251,6 +254,7 @@ struct rccsdt_ctx {
       const void *ahi, *alo, *bhi, *blo;
       int M, N, Kpad;
       float* out;
+      int colmajor;
     };
     std::vector<Src> src;
   } gr;
@@ -577,10 +581,20 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   } else {
     int* flag = (int*)((double*)c->scalars->p + 1000);
     float* raw = g->s3_rows > 0 && c->rawX ? (float*)c->rawX->p : nullptr;
-    if (rcc::launch_gemm_tc(kind, pa.out_hi, pa.out_lo, pb.out_hi, pb.out_lo, g->Kpad, g->E.e, flag,
-                            c->opt.watchdog_cycles, c->stream, c->concurrent ? nullptr : (float*)c->splitk->p,
-                            (long long)(c->splitk->bytes / 4), raw))
-      return fail(c, RCCSDT_ERR_ARG, "tensor-core GEMM configuration unsupported");
+    // tile width from the output columns: 128, 144 (e.g. the 136 pairs i <= j of o = 16) or 256
+    auto width = [](int n) { return n <= 128 ? 128 : (n <= 144 ? 144 : 256); };
+    int lst;
+    if (raw && g->tc_swap) {
+      rcc::EpiArgs et = g->E.e;
+      std::swap(et.M, et.N);
+      lst = rcc::launch_gemm_tc(kind, pb.out_hi, pb.out_lo, pa.out_hi, pa.out_lo, g->Kpad, et, flag,
+                                c->opt.watchdog_cycles, c->stream, nullptr, 0, raw, width(et.N), 1);
+    } else {
+      lst = rcc::launch_gemm_tc(kind, pa.out_hi, pa.out_lo, pb.out_hi, pb.out_lo, g->Kpad, g->E.e, flag,
+                                c->opt.watchdog_cycles, c->stream, c->concurrent ? nullptr : (float*)c->splitk->p,
+                                (long long)(c->splitk->bytes / 4), raw, width(g->E.e.N));
+    }
+    if (lst) return fail(c, RCCSDT_ERR_ARG, "tensor-core GEMM configuration unsupported");
     if (raw) {
       const rcc::EpiArgs& e = g->E.e;
       const i64* sb = (const i64*)g->s3_base->p;
@@ -1050,6 +1064,7 @@ int build_context(rccsdt_ctx* c) {
           pcs.push_back(pc);
         }
         set_cube(c, g, 1, std::move(pcs), &err);
+        g->tc_swap = 1;  // rows (i <= j) become the 144/128-wide tile columns
       }
       c->p_hh.push_back(g);
     }
@@ -1275,6 +1290,7 @@ int grouped_table(rccsdt_ctx* c, int bn, int ord, std::unique_ptr<DBuf>* out, in
     const auto& x = G.src[q];
     if (rcc::make_gproblem(&probs[q], G.kind, x.ahi, x.alo, x.bhi, x.blo, x.M, x.N, x.Kpad, x.out, bn))
       return fail(c, RCCSDT_ERR_CUDA, "grouped residual: tensor map encoding failed");
+    probs[q].colmajor = x.colmajor;
   }
   std::vector<int> order(n);
   for (size_t q = 0; q < n; ++q) order[q] = (int)q;
@@ -1408,8 +1424,13 @@ int build_grouped(rccsdt_ctx* c) {
     x.alo = base + A.lo;
     x.bhi = base + B.hi;
     x.blo = base + B.lo;
-    x.M = g->swap_ab ? g->E.e.N : g->E.e.M;
-    x.N = g->swap_ab ? g->E.e.M : g->E.e.N;
+    x.M = (g->swap_ab || g->tc_swap) ? g->E.e.N : g->E.e.M;
+    x.N = (g->swap_ab || g->tc_swap) ? g->E.e.M : g->E.e.N;
+    x.colmajor = g->tc_swap;
+    if (g->tc_swap) {  // exchanged operands, column-major result
+      std::swap(x.ahi, x.bhi);
+      std::swap(x.alo, x.blo);
+    }
     x.Kpad = g->Kpad;
     x.out = raw + xo[q];
     G.src.push_back(x);

@@ -42,7 +42,8 @@ void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, 
 // Split-precision product hi*hi + hi*lo + lo*hi with float products and a float
 // accumulator (the order of the tensor-core sum is not modelled).
 int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int Kpad,
-                   const EpiArgs& e, int*, long long, cudaStream_t, float*, long long, float* raw_out, int) {
+                   const EpiArgs& e, int*, long long, cudaStream_t, float*, long long, float* raw_out, int,
+                   int colmajor) {
   auto get = [&](const void* p, i64 i) -> float {
     if (kind == PANEL_BF16X2) return __bfloat162float(((const __nv_bfloat16*)p)[i]);
     return ((const float*)p)[i];
@@ -56,7 +57,7 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
         s += ah * bh + ah * bl + al * bh;
       }
       if (raw_out)
-        raw_out[(i64)m * e.N + n] = s;
+        raw_out[colmajor ? (i64)n * e.M + m : (i64)m * e.N + n] = s;
       else
         epi_apply(e, m, n, (double)s);
     }
@@ -126,6 +127,7 @@ int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const
   if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
   if (Kpad % gemm_tc_block_k(kind) != 0 || M <= 0 || N <= 0) return 1;
   memset((void*)p, 0, sizeof(*p));
+  p->colmajor = 0;
   p->a_hi = Ahi;
   p->a_lo = Alo;
   p->b_hi = Bhi;
@@ -149,7 +151,9 @@ int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int, int,
     EpiArgs e{};
     e.M = P.M;
     e.N = P.N;
-    if (launch_gemm_tc(kind, P.a_hi, P.a_lo, P.b_hi, P.b_lo, P.Kpad, e, flag, wd, s, nullptr, 0, P.out, 256)) return 1;
+    if (launch_gemm_tc(kind, P.a_hi, P.a_lo, P.b_hi, P.b_lo, P.Kpad, e, flag, wd, s, nullptr, 0, P.out, 256,
+                       P.colmajor))
+      return 1;
   }
   return 0;
 }

@@ -384,10 +384,14 @@ def run_ours(args, rank, world):
         else:
             peak, bound, src = pk.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25) / 3.0, "tensor", \
                 "measured bf16 sustained x nominal tf32/bf16 ratio / 3"
+        # DRAM bytes of one pp-ladder launch from an ncu capture of this workload and
+        # precision (profiles/k_gemm_tc_pp_o16v160w_traffic.md); other runs have none
+        traffic = 29.86e9 if (args.workload == "o16v160w" and prec == 1) else None
         roof = {"kernel": "pp-ladder GEMM (k_gemm_f64)" if prec == 0 else "pp-ladder GEMM (k_gemm_tc)",
                 "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": src, "launches": int(gemm_n),
-                "avg_launch_ms": gemm_ms / gemm_n}
+                "traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, first "
+                "pp-ladder launch (61 stored blocks)" if traffic else None, "peak_source": src,
+                "launches": int(gemm_n), "avg_launch_ms": gemm_ms / gemm_n}
 
     compare = None
     if not args.no_compare and world == 1:

@@ -8,8 +8,9 @@
 // most permutations touches one 32-byte sector per element.  Here a CTA stages a
 // cube of the labels in shared memory, reading every source cube along its stored
 // unit-stride axis, and writes the panel in runs along K:
-//   mode 0  the piece's label L0 runs along K (K = k0 + L0) and the rows are
-//           row0 + L1 v + L2 (ring terms: K = (part, l, d), rows (b, c) or (a, c));
+//   mode 0  the piece's label L0 runs along K (K = k0 + L0 + L1 ks1) and the rows
+//           are row0 + L1 rs1 + L2 rs2 (ring terms: K = (part, l, d), rows (b, c) or
+//           (a, c); the panels of step (iii) read from the unpacked batch S);
 //   mode 1  each piece is one column (K = k0) of one term and the rows are
 //           row0 + L0 v^2 + L1 v + L2 (hh-ladder: K = (l, m), rows (a, b, c)); a CTA
 //           takes 16 consecutive columns and an 8^3 cube of rows.
@@ -132,9 +133,9 @@ __global__ void __launch_bounds__(256) k_cube_pack_k(const CubePiece* __restrict
   }
   const CubeDst d = dsts ? dsts[P.dst] : d0;
   const int n = min(TL, v - lo[0]);
-  const int k = P.k0 + lo[0];
+  const int k = P.k0 + lo[0] + g1 * P.ks1;
   const bool vec = (k & 7) == 0 && (KIND == PANEL_BF16X2 || (k & 3) == 0);
-  store_run<KIND>(d, P.row0 + (i64)g1 * v + g2, k, x, n, vec);
+  store_run<KIND>(d, P.row0 + (i64)g1 * P.rs1 + (i64)g2 * P.rs2, k, x, n, vec);
 }
 
 // Mode 1: grid (label cubes of 8^3, groups of 16 pieces = 16 consecutive columns).

@@ -1237,18 +1237,51 @@ template void launch_unpack_spin<float>(const void*, int, int, const i64*, const
 template <typename T>
 __global__ void __launch_bounds__(256) k_r1_t3(const T* __restrict__ S, const double* __restrict__ oovv, int o,
                                                int v, double* __restrict__ partial) {
+  // per slab (x, y, b) = sl[c][a]: term 1 sum_c w[c] sl[c][a] with threads along a,
+  // term 2 sum_c w[c] sl[a][c] with a warp per row a and lanes along c (both coalesced);
+  // term 2 of each row is owned by one warp and kept in shared memory per warp.
+  // a = threadIdx.x + 256 j, j < 16 (v <= 4096).
+  extern __shared__ __align__(16) unsigned char r1_smem[];
+  T* t2s = reinterpret_cast<T*>(r1_smem);  // [8 warps][v]
+  T* ws = t2s + 8 * v;                     // the slab's weights in the storage type
   const i64 nslab = (i64)o * o * v;
   const i64 V2 = (i64)v * v;
-  for (int a0 = 0; a0 < v; a0 += blockDim.x) {
-    const int a = a0 + threadIdx.x;
-    T acc = (T)0;
-    if (a < v) {
-      for (i64 s = blockIdx.x; s < nslab; s += gridDim.x) {
-        const T* sl = S + s * V2;          // slab (x, y, b): [c][a]
-        const double* w = oovv + s * v;    // v^{xy}_{bc} over c (oovv[x][y][b][c])
-        for (int c = 0; c < v; ++c) acc += (T)w[c] * (sl[(i64)c * v + a] - (T)0.5 * sl[(i64)a * v + c]);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = threadIdx.x; q < 8 * v; q += blockDim.x) t2s[q] = (T)0;
+  T acc[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j] = (T)0;
+  for (i64 sgi = blockIdx.x; sgi < nslab; sgi += gridDim.x) {
+    const T* sl = S + sgi * V2;          // slab (x, y, b): [c][a]
+    __syncthreads();                     // the previous slab's weights are consumed
+    for (int c = threadIdx.x; c < v; c += blockDim.x) ws[c] = (T)oovv[sgi * v + c];  // v^{xy}_{bc}
+    __syncthreads();
+    const T* w = ws;
+    for (int c = 0; c < v; ++c) {
+      const T wc = w[c];
+      const T* row = sl + (i64)c * v;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int a = threadIdx.x + 256 * j;
+        if (a < v) acc[j] += wc * row[a];
       }
-      partial[(i64)blockIdx.x * v + a] = (double)acc;
+    }
+    for (int ar = warp; ar < v; ar += 8) {
+      T part = (T)0;
+      for (int c = lane; c < v; c += 32) part += w[c] * sl[(i64)ar * v + c];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+      if (lane == 0) t2s[warp * v + ar] += part;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int a = threadIdx.x + 256 * j;
+    if (a < v) {
+      T t2 = (T)0;
+      for (int q = 0; q < 8; ++q) t2 += t2s[q * v + a];
+      partial[(i64)blockIdx.x * v + a] = (double)acc[j] - 0.5 * (double)t2;
     }
   }
 }
@@ -1268,8 +1301,14 @@ void launch_r1_t3(const T* S, const double* oovv, int o, int v, double* dR1_z, d
   const i64 nslab = (i64)o * o * v;
   int nblk = (int)std::min<i64>(nslab, 1216);
   while ((i64)nblk * v > scratch_elems && nblk > 1) nblk /= 2;
+  const size_t smem = (size_t)9 * v * sizeof(T);
+  static bool attr = false;
+  if (!attr) {  // v up to 4096
+    cudaFuncSetAttribute(k_r1_t3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(9 * 4096 * sizeof(T)));
+    attr = true;
+  }
   ++g_launch_count;
-  k_r1_t3<T><<<nblk, 256, 0, s>>>(S, oovv, o, v, scratch);
+  k_r1_t3<T><<<nblk, 256, smem, s>>>(S, oovv, o, v, scratch);
   ++g_launch_count;
   k_r1_reduce<<<v, 256, 0, s>>>(scratch, nblk, v, dR1_z);
 }

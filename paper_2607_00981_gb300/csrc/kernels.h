@@ -114,6 +114,8 @@ struct CubePiece {
   int k0;      // mode 0: panel column of L0 = 0; mode 1: the piece's column
   i64 row0;    // panel row of the labels' origin
   int nterm;   // 0 (zeros), 1..3 (mode 1: at most 1)
+  int ks1;     // mode 0: K stride of L1 (0 when L1 indexes rows)
+  int rs1, rs2;  // mode 0: row strides of L1 and L2
   CubeTerm t[3];
 };
 struct CubeDst {
@@ -121,7 +123,7 @@ struct CubeDst {
   void* out_lo;
   int Kpad;
 };
-// mode 0: K = k0 + L0, rows row0 + L1 v + L2 (pieces in any order);
+// mode 0: K = k0 + L0 + L1 ks1, rows row0 + L1 rs1 + L2 rs2 (pieces in any order);
 // mode 1: K = k0, rows row0 + L0 v^2 + L1 v + L2, pieces in groups of 16 consecutive
 // columns of one panel (npieces a multiple of 16).  Panels of `kind` (split).
 void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, const CubeDst* dsts,

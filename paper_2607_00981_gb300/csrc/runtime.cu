@@ -673,11 +673,14 @@ struct TripleInfo {
 
 int packpos(int a, int b, int c) { return a | (b << 2) | (c << 4); }
 
-rcc::CubePiece cube_piece(int k0, int nterm) {
+// A piece with rows row0 + L1 rs1 + L2 rs2 (mode 0: default rows L1 v + L2).
+rcc::CubePiece cube_piece(int k0, int nterm, int v = 0) {
   rcc::CubePiece p;
   memset(&p, 0, sizeof(p));
   p.k0 = k0;
   p.nterm = nterm;
+  p.rs1 = v;
+  p.rs2 = 1;
   return p;
 }
 
@@ -905,16 +908,48 @@ int build_context(rccsdt_ctx* c) {
       auto& g = c->p_a3.back();
       // (the R1 term runs in k_r1_t3 on the same S batch)
       View dX2z = sub(permuted(dX2, {1, 0, 2, 3}), 0, z0, Zb);  // dX2[y, z, a, b] over (z, y, a, b)
-      b.ct(g, "xc,zxycab->zyab", 0.5, sub(sub(ft, 0, O0, o), 1, V0, v), Sz, dX2z);
+      GemmPlan* q1 = b.ct(g, "xc,zxycab->zyab", 0.5, sub(sub(ft, 0, O0, o), 1, V0, v), Sz, dX2z);
       // S panel [(y,e2,e3)][(z,x,e1)], shared by two contractions (and the first one when Zb = 1)
-      GemmPlan* q = b.ct(g, "zxjc,zxycab->yjab", -1.0, sub(eri("ooov"), 0, z0, Zb), Sz, dX2);
-      if (q && Zb == 1) q->reuse_B = 1;
-      b.ct(g, "zxde,zxyeba->ybad", -1.0, sub(eri("oovv"), 0, z0, Zb), Sz, permuted(Wvvvo, {3, 1, 0, 2}), 1)
-          ->reuse_B = 1;
+      GemmPlan* q2 = b.ct(g, "zxjc,zxycab->yjab", -1.0, sub(eri("ooov"), 0, z0, Zb), Sz, dX2);
+      if (q2 && Zb == 1) q2->reuse_B = 1;
+      GemmPlan* q3 = b.ct(g, "zxde,zxyeba->ybad", -1.0, sub(eri("oovv"), 0, z0, Zb), Sz,
+                          permuted(Wvvvo, {3, 1, 0, 2}), 1);
+      if (q3) q3->reuse_B = 1;
       // S panel [(z,y,e2)][(x,e3,e1)], shared by two contractions
-      b.ct(g, "bxcd,zxydac->zyab", 1.0, eri("vovv"), Sz, dX2z, 1);
-      b.ct(g, "lxde,zxyead->zyal", 1.0, eri("oovv"), Sz,
-           permuted(sub(permuted(Wvooo, {3, 0, 1, 2}), 0, z0, Zb), {0, 3, 1, 2}))->reuse_B = 1;
+      GemmPlan* q4 = b.ct(g, "bxcd,zxydac->zyab", 1.0, eri("vovv"), Sz, dX2z, 1);
+      GemmPlan* q5 = b.ct(g, "lxde,zxyead->zyal", 1.0, eri("oovv"), Sz,
+                          permuted(sub(permuted(Wvooo, {3, 0, 1, 2}), 0, z0, Zb), {0, 3, 1, 2}));
+      if (q5) q5->reuse_B = 1;
+      if (t3f && q1 && q2 && q3 && q4 && q5) {
+        // the S panels through label cubes: one piece per unpacked block S[z][x][y]
+        // (labels e1, e2, e3 on axes 0, 1, 2 of the block)
+        std::vector<rcc::CubePiece> pa_, pb_, pc_;
+        for (int z = 0; z < Zb; ++z)
+          for (int x = 0; x < o; ++x)
+            for (int y = 0; y < o; ++y) {
+              const i64 base = (((i64)z * o + x) * o + y) * V3;
+              rcc::CubePiece p1 = cube_piece(x * v, 1, v);  // rows (z, y, e2, e3), K (x, e1)
+              p1.row0 = ((i64)z * o + y) * V2;
+              p1.t[0] = {base, 1.f, packpos(0, 1, 2)};
+              rcc::CubePiece p2 = cube_piece((z * o + x) * v, 1, v);  // rows (y, e2, e3), K (z, x, e1)
+              p2.row0 = (i64)y * V2;
+              p2.t[0] = {base, 1.f, packpos(0, 1, 2)};
+              rcc::CubePiece p4 = cube_piece(x * (int)V2, 1);  // rows (z, y, e2), K (x, e3, e1)
+              p4.ks1 = v;
+              p4.rs1 = 0;
+              p4.rs2 = 1;
+              p4.row0 = ((i64)z * o + y) * v;
+              p4.t[0] = {base, 1.f, packpos(0, 2, 1)};  // L0 = e1, L1 = e3, L2 = e2
+              pa_.push_back(p1);
+              pb_.push_back(p2);
+              pc_.push_back(p4);
+            }
+        set_cube(c, q1, 0, pa_, &err);
+        set_cube(c, q2, 0, pb_, &err);
+        set_cube(c, q3, 0, std::move(pb_), &err);
+        set_cube(c, q4, 0, pc_, &err);
+        set_cube(c, q5, 0, std::move(pc_), &err);
+      }
     }
   }
 
@@ -1126,11 +1161,11 @@ int build_context(rccsdt_ctx* c) {
           std::vector<rcc::CubePiece> pcs;
           for (int l = 0; l < o; ++l) {
             TripleInfo u = triple(l, j, k), u1 = triple(j, l, k), u2 = triple(k, l, j);
-            rcc::CubePiece p0 = cube_piece(l * v, 3);
+            rcc::CubePiece p0 = cube_piece(l * v, 3, v);
             p0.t[0] = {u.blk * V3, 2.f, packpos(u.pos[0], u.pos[1], u.pos[2])};
             p0.t[1] = {u.blk * V3, -1.f, packpos(u.pos[1], u.pos[0], u.pos[2])};
             p0.t[2] = {u.blk * V3, -1.f, packpos(u.pos[2], u.pos[1], u.pos[0])};
-            rcc::CubePiece p1 = cube_piece(o * v + l * v, 2);
+            rcc::CubePiece p1 = cube_piece(o * v + l * v, 2, v);
             p1.t[0] = {u1.blk * V3, 1.f, packpos(u1.pos[0], u1.pos[1], u1.pos[2])};
             p1.t[1] = {u2.blk * V3, 1.f, packpos(u2.pos[0], u2.pos[2], u2.pos[1])};
             pcs.push_back(p0);
@@ -1191,7 +1226,7 @@ int build_context(rccsdt_ctx* c) {
           std::vector<rcc::CubePiece> pcs;
           for (int l = 0; l < o; ++l) {
             TripleInfo u = triple(j, l, k);
-            rcc::CubePiece pc = cube_piece(l * v, 1);
+            rcc::CubePiece pc = cube_piece(l * v, 1, v);
             pc.t[0] = {u.blk * V3, 1.f, packpos(u.pos[0], u.pos[1], u.pos[2])};
             pcs.push_back(pc);
           }

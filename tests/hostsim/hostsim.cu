@@ -108,8 +108,8 @@ void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, 
             const i64 off = P.t[t].base + l0 * S[ps & 3] + l1 * S[(ps >> 2) & 3] + l2 * S[(ps >> 4) & 3];
             x = std::fma(P.t[t].coef, src[off], x);
           }
-          const i64 row = mode == 0 ? P.row0 + (i64)l1 * v + l2 : P.row0 + ((i64)l0 * v + l1) * v + l2;
-          const i64 k = mode == 0 ? P.k0 + l0 : P.k0;
+          const i64 row = mode == 0 ? P.row0 + (i64)l1 * P.rs1 + (i64)l2 * P.rs2 : P.row0 + ((i64)l0 * v + l1) * v + l2;
+          const i64 k = mode == 0 ? P.k0 + l0 + (i64)l1 * P.ks1 : P.k0;
           host_store_split(kind, d.out_hi, d.out_lo, row * d.Kpad + k, x);
         }
   }

@@ -1411,33 +1411,40 @@ __global__ void __launch_bounds__(256) k_t2_outer(T* __restrict__ r3, const T* _
   constexpr int TL = 16, LC = 16;
   __shared__ T Ws[TL][LC + 1];
   __shared__ T Ts[LC][TL][TL + 1];
-  const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
   const int nt = (v + TL - 1) / TL;
   const i64 V3 = (i64)v * v * v;
   const int tc = threadIdx.x % TL, tb = threadIdx.x / TL;
   for (i64 blk = blockIdx.y; blk < n3; blk += gridDim.y) {
     const int4 ijk = blocks[blk];
-    const int occ[3] = {ijk.x, ijk.y, ijk.z};
+    auto occ = [&](int x) { return x == 0 ? ijk.x : (x == 1 ? ijk.y : ijk.z); };
     for (int tile = blockIdx.x; tile < nt * nt * nt; tile += gridDim.x) {
-      const int lo[3] = {tile / (nt * nt) * TL, (tile / nt) % nt * TL, tile % nt * TL};
+      const int lo0 = tile / (nt * nt) * TL, lo1 = (tile / nt) % nt * TL, lo2 = tile % nt * TL;
+      auto lo = [&](int x) { return x == 0 ? lo0 : (x == 1 ? lo1 : lo2); };
       T acc[TL];
 #pragma unroll
       for (int a = 0; a < TL; ++a) acc[a] = (T)0;
+#pragma unroll 1
       for (int q = 0; q < 6; ++q) {
-        // roles: position P[q][0] -> (i1, a1), P[q][1] -> (i2, a2), P[q][2] -> (i3, a3)
-        const int x1 = P[q][0], x2 = P[q][1], x3 = P[q][2];
-        const int i1 = occ[x1], i2 = occ[x2], i3 = occ[x3];
+        // roles: position x1 -> (i1, a1), x2 -> (i2, a2), x3 -> (i3, a3) (the q-th ordering)
+        const int x1 = perm3(q, 0), x2 = perm3(q, 1), x3 = perm3(q, 2);
+        const int i1 = occ(x1), i2 = occ(x2), i3 = occ(x3);
         for (int l0 = 0; l0 < o; l0 += LC) {
           const int lc = min(LC, o - l0);
           __syncthreads();
-          for (int e = threadIdx.x; e < TL * LC; e += blockDim.x) {
-            const int u = e / LC, l = e % LC, ga = lo[x1] + u;
-            Ws[u][l] = (l < lc && ga < v) ? Wvooo[(((i64)ga * o + l0 + l) * o + i1) * o + i2] : (T)0;
+          {  // W slice [u][l]: thread (u, l) = (tb, tc)
+            const int ga = lo(x1) + tb;
+            Ws[tb][tc] = (tc < lc && ga < v) ? Wvooo[(((i64)ga * o + l0 + tc) * o + i1) * o + i2] : (T)0;
           }
-          for (int e = threadIdx.x; e < LC * TL * TL; e += blockDim.x) {
-            const int l = e / (TL * TL), u2 = (e / TL) % TL, u3 = e % TL;
-            const int g2 = lo[x2] + u2, g3 = lo[x3] + u3;
-            Ts[l][u2][u3] = (l < lc && g2 < v && g3 < v) ? t2[(((i64)(l0 + l) * o + i3) * v + g2) * v + g3] : (T)0;
+          {  // t2 slice [l][u2][u3]: thread (u2, u3) = (tb, tc), 16 loads in flight
+            const int g2 = lo(x2) + tb, g3 = lo(x3) + tc;
+            const bool in = g2 < v && g3 < v;
+            const T* src = t2 + ((i64)(l0 * o + i3) * v + g2) * v + g3;
+            const i64 ls = (i64)o * v * v;  // stride of l
+            T ld[LC];
+#pragma unroll
+            for (int l = 0; l < LC; ++l) ld[l] = (in && l < lc) ? src[l * ls] : (T)0;
+#pragma unroll
+            for (int l = 0; l < LC; ++l) Ts[l][tb][tc] = ld[l];
           }
           __syncthreads();
           // the thread's fixed (b, c) sit on two of the three roles; a runs over the third
@@ -1464,16 +1471,15 @@ __global__ void __launch_bounds__(256) k_t2_outer(T* __restrict__ r3, const T* _
           }
         }
       }
-      const int gb = lo[1] + tb, gc = lo[2] + tc;
+      const int gb = lo1 + tb, gc = lo2 + tc;
       if (gb < v && gc < v) {
+        T* dst = r3 + blk * V3 + (i64)gb * v + gc;
+        T old[TL];
 #pragma unroll
-        for (int a = 0; a < TL; ++a) {
-          const int ga = lo[0] + a;
-          if (ga < v) {
-            const i64 off = blk * V3 + ((i64)ga * v + gb) * v + gc;
-            r3[off] = r3[off] + acc[a];
-          }
-        }
+        for (int a = 0; a < TL; ++a) old[a] = lo0 + a < v ? dst[(i64)(lo0 + a) * v * v] : (T)0;
+#pragma unroll
+        for (int a = 0; a < TL; ++a)
+          if (lo0 + a < v) dst[(i64)(lo0 + a) * v * v] = old[a] + acc[a];
       }
     }
   }

@@ -1302,10 +1302,10 @@ void launch_r1_t3(const T* S, const double* oovv, int o, int v, double* dR1_z, d
   int nblk = (int)std::min<i64>(nslab, 1216);
   while ((i64)nblk * v > scratch_elems && nblk > 1) nblk /= 2;
   const size_t smem = (size_t)9 * v * sizeof(T);
-  static bool attr = false;
-  if (!attr) {  // v up to 4096
-    cudaFuncSetAttribute(k_r1_t3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(9 * 4096 * sizeof(T)));
-    attr = true;
+  static size_t attr = 48 << 10;  // above the default 48 KB the kernel opts in (up to the 227 KB limit)
+  if (smem > attr) {
+    cudaFuncSetAttribute(k_r1_t3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = smem;
   }
   ++g_launch_count;
   k_r1_t3<T><<<nblk, 256, smem, s>>>(S, oovv, o, v, scratch);

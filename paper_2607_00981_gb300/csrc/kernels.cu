@@ -1286,6 +1286,43 @@ __global__ void __launch_bounds__(256) k_r1_t3(const T* __restrict__ S, const do
   }
 }
 
+// Same sums with the whole slab staged in shared memory ([c][a] rows padded to v+1):
+// every element of S is read from memory once and both terms come from shared
+// memory (used when a slab fits, v up to about 220 in FP32).
+template <typename T>
+__global__ void __launch_bounds__(256) k_r1_slab(const T* __restrict__ S, const double* __restrict__ oovv, int o,
+                                                 int v, double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char r1s_smem[];
+  T* sl = reinterpret_cast<T*>(r1s_smem);  // [v][v + 1]
+  T* ws = sl + (i64)v * (v + 1);           // [v]
+  const i64 nslab = (i64)o * o * v;
+  const i64 V2 = (i64)v * v;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, a = threadIdx.x;
+  T t1 = (T)0, t2 = (T)0;
+  for (i64 sgi = blockIdx.x; sgi < nslab; sgi += gridDim.x) {
+    const T* src = S + sgi * V2;
+    __syncthreads();  // the previous slab is consumed
+    for (int c = warp; c < v; c += 8) {
+      const T* row = src + (i64)c * v;
+      T* dst = sl + c * (v + 1);
+#pragma unroll 4
+      for (int x = lane; x < v; x += 32) dst[x] = row[x];
+    }
+    for (int c = threadIdx.x; c < v; c += blockDim.x) ws[c] = (T)oovv[sgi * v + c];
+    __syncthreads();
+    if (a < v) {
+      const T* col = sl + a;                 // sl[c][a] over c
+      const T* row = sl + a * (v + 1);       // sl[a][c] over c
+      for (int c = 0; c < v; ++c) {
+        const T w = ws[c];
+        t1 += w * col[c * (v + 1)];
+        t2 += w * row[c];
+      }
+    }
+  }
+  if (a < v) partial[(i64)blockIdx.x * v + a] = (double)t1 - 0.5 * (double)t2;
+}
+
 // One block per a: the nblk partials are summed in a fixed order.
 __global__ void k_r1_reduce(const double* __restrict__ partial, int nblk, int v, double* __restrict__ out) {
   const int a = blockIdx.x;
@@ -1301,14 +1338,25 @@ void launch_r1_t3(const T* S, const double* oovv, int o, int v, double* dR1_z, d
   const i64 nslab = (i64)o * o * v;
   int nblk = (int)std::min<i64>(nslab, 1216);
   while ((i64)nblk * v > scratch_elems && nblk > 1) nblk /= 2;
-  const size_t smem = (size_t)9 * v * sizeof(T);
-  static size_t attr = 48 << 10;  // above the default 48 KB the kernel opts in (up to the 227 KB limit)
-  if (smem > attr) {
-    cudaFuncSetAttribute(k_r1_t3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = smem;
+  const size_t slab = ((size_t)v * (v + 1) + v) * sizeof(T);
+  if (v <= 256 && slab <= (200u << 10)) {
+    static size_t attr_s = 48 << 10;
+    if (slab > attr_s) {
+      cudaFuncSetAttribute(k_r1_slab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab);
+      attr_s = slab;
+    }
+    ++g_launch_count;
+    k_r1_slab<T><<<nblk, 256, slab, s>>>(S, oovv, o, v, scratch);
+  } else {
+    const size_t smem = (size_t)9 * v * sizeof(T);
+    static size_t attr = 48 << 10;  // above the default 48 KB the kernel opts in (up to the 227 KB limit)
+    if (smem > attr) {
+      cudaFuncSetAttribute(k_r1_t3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = smem;
+    }
+    ++g_launch_count;
+    k_r1_t3<T><<<nblk, 256, smem, s>>>(S, oovv, o, v, scratch);
   }
-  ++g_launch_count;
-  k_r1_t3<T><<<nblk, 256, smem, s>>>(S, oovv, o, v, scratch);
   ++g_launch_count;
   k_r1_reduce<<<v, 256, 0, s>>>(scratch, nblk, v, dR1_z);
 }

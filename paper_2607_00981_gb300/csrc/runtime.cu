@@ -1157,6 +1157,7 @@ int build_context(rccsdt_ctx* c) {
           set_two_phase(c, g, tb, ax, ta, &err);
         }
         finish_plan(c, g, K);
+        g->tc_swap = 1;  // column-major dense result: coalesced rows of the raw output
         if (t3f) {  // B: labels (d, b, c), K = (part, l, d), rows (b, c)
           std::vector<rcc::CubePiece> pcs;
           for (int l = 0; l < o; ++l) {
@@ -1222,6 +1223,7 @@ int build_context(rccsdt_ctx* c) {
           set_two_phase(c, g, tb, ax, ta, &err);
         }
         finish_plan(c, g, K);
+        g->tc_swap = 1;
         if (t3f) {  // B: labels (d, a, c) of t_{jlk}, K = (l, d), rows (a, c)
           std::vector<rcc::CubePiece> pcs;
           for (int l = 0; l < o; ++l) {
@@ -1282,6 +1284,7 @@ int build_context(rccsdt_ctx* c) {
         set_two_phase(c, g, tb, ax, ta, &err);
       }
       finish_plan(c, g, K);
+      g->tc_swap = 1;  // K = v is short: the GEMM streams its result, written column-major (coalesced)
       c->p_t2a.push_back(g);
     }
 

@@ -39,6 +39,8 @@ struct PackArgs {
 };
 
 // Table-driven epilogue: C[row_base[m] + col_off[row_sel[m]*N + n]] += row_alpha[m] * acc(m, n)
+// where rows m >= m2 write to C2 instead of C (a GEMM whose stacked A operand
+// feeds two output tensors of the same element type; C2 null: C only).
 struct EpiArgs {
   void* C;               // double or float
   int c_f32;
@@ -47,6 +49,8 @@ struct EpiArgs {
   const int* row_sel;    // [M]
   const double* row_alpha; // [M]
   const i64* col_off;    // [nsel][N]
+  void* C2;
+  int m2;
 };
 
 }  // namespace rcc

@@ -20,6 +20,46 @@ RCC_HD float tf32_round(float x) {
   return c.f;
 }
 
+// IEEE 754 binary64 -> binary32, round to nearest even, on the integer
+// representation (no FP64 instructions: this part's FP64 pipe is about 1/64 of its
+// FP32 rate, which made FP64-source panel gathers compute bound).  Overflow gives
+// infinity, binary64 subnormals give zero, NaN stays NaN.
+RCC_HD float f64_to_f32_rn(double x) {
+  union { double d; unsigned long long u; } in;
+  union { unsigned u; float f; } out;
+  in.d = x;
+  const unsigned long long b = in.u;
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  if (e == 0x7ff) {
+    out.u = sign | 0x7f800000u | (m ? 0x00400000u : 0u);
+    return out.f;
+  }
+  int fe = e - 1023 + 127;
+  if (fe >= 255) {
+    out.u = sign | 0x7f800000u;
+    return out.f;
+  }
+  unsigned long long sig = m;
+  int shift = 29;  // 52 - 23 fraction bits dropped
+  if (fe <= 0) {   // binary32 subnormal: value = q 2^-149, q = sig 2^(fe - 30)
+    if (e == 0 || fe < -24) {
+      out.u = sign;
+      return out.f;
+    }
+    sig = m | (1ull << 52);
+    shift = 30 - fe;
+    fe = 0;
+  }
+  unsigned long long q = sig >> shift;
+  const unsigned long long rem = sig & ((1ull << shift) - 1), half = 1ull << (shift - 1);
+  if (rem > half || (rem == half && (q & 1ull))) ++q;
+  // a carry out of the fraction moves into the exponent (up to infinity)
+  out.u = sign | (unsigned)(((unsigned long long)fe << 23) + q);
+  return out.f;
+}
+
 // Stored-axis index of label q under ordering s (the six orderings, lexicographic).
 RCC_HD int perm3(int s, int q) {
   // {0,1,2} {0,2,1} {1,0,2} {1,2,0} {2,0,1} {2,1,0}
@@ -94,13 +134,16 @@ RCC_HD void store_panel_f(const PackArgs& a, int r, int k, float x) {
   }
 }
 
+// Output tensor of row m (see EpiArgs).
+RCC_HD void* epi_out(const EpiArgs& e, int m) { return (e.C2 && m >= e.m2) ? e.C2 : e.C; }
+
 RCC_HD void epi_apply(const EpiArgs& e, int m, int n, double acc) {
   const i64 addr = e.row_base[m] + e.col_off[(i64)e.row_sel[m] * e.N + n];
   const double val = e.row_alpha[m] * acc;
   if (e.c_f32)
-    ((float*)e.C)[addr] += (float)val;
+    ((float*)epi_out(e, m))[addr] += (float)val;
   else
-    ((double*)e.C)[addr] += val;
+    ((double*)epi_out(e, m))[addr] += val;
 }
 
 // ---------------------------------------------------------------------------

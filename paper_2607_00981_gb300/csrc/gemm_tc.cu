@@ -8,16 +8,19 @@
 // for BF16 and of Ootomo & Yokota (2022) for TF32: dropping lo*lo leaves a
 // relative error of about 2^-16 (BF16) or 2^-21 (TF32) per product.
 //
-// Persistent kernel, one CTA per SM, 192 threads:
+// Persistent kernel, one CTA per SM, 320 threads:
 //   warp 0     TMA producer: 128-byte-swizzled 128 x 64B-row tiles of A and
 //              256-row tiles of B, hi and lo planes, into a 2-stage ring;
 //   warp 1     TMEM owner and MMA issuer (one thread): 3 tcgen05.mma per 32-byte
 //              K slice into a 128 x 256 FP32 accumulator, double buffered in
 //              TMEM (512 columns) so the epilogue of one tile overlaps the MMAs
 //              of the next;
-//   warps 2-5  epilogue: tcgen05.ld of the accumulator (one row per thread) and
+//   warps 2-9  epilogue: tcgen05.ld of the accumulator (one row per thread; the
+//              two warps of a lane quadrant take alternate 32-column chunks) and
 //              the table-driven scatter C[row_base[m] + col_off[sel[m]][n]] +=
-//              alpha[m] * acc, or FP32 partial tiles when K is split.
+//              alpha[m] * acc, or FP32 partial tiles when K is split.  Two warps
+//              per quadrant double the loads in flight of read-modify-write
+//              epilogues (short K, large outputs), which are latency bound.
 // Every mbarrier wait is bounded by a clock64 budget; on expiry the kernel sets
 // *status, drains its own copies and MMAs (bounded again), frees TMEM and exits.
 #include <cuda.h>
@@ -35,7 +38,8 @@ namespace {
 constexpr int BM = 128, STAGES = 2;
 constexpr int ROWB = 128;                      // bytes of one K-row of a tile (swizzle span)
 constexpr int A_PLANE = BM * ROWB;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;                 // two epilogue warps per TMEM lane quadrant
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 // Tile width BN (256 or 128 columns): B planes, stage and shared-memory sizes.
 template <int BN>
@@ -154,7 +158,7 @@ __device__ __forceinline__ void epilogue_row(const EpiArgs& e, int m, int n0, co
   const i64* co = e.col_off + (i64)e.row_sel[m] * e.N;
   const int nv = min(32, e.N - n0);
   if (e.c_f32) {
-    float* C = (float*)e.C;
+    float* C = (float*)epi_out(e, m);
     const float al = (float)e.row_alpha[m];
 #pragma unroll
     for (int h = 0; h < 32; h += 16) {
@@ -169,7 +173,7 @@ __device__ __forceinline__ void epilogue_row(const EpiArgs& e, int m, int n0, co
         if (ad[j] >= 0) C[ad[j]] = fmaf(al, __uint_as_float(r[h + j]), old[j]);
     }
   } else {
-    double* C = (double*)e.C;
+    double* C = (double*)epi_out(e, m);
     const double al = e.row_alpha[m];
 #pragma unroll
     for (int h = 0; h < 32; h += 16) {
@@ -323,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], kEpiWarps);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -437,7 +441,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    const int q = warp & 3;
+    const int q = warp & 3;        // TMEM lane quadrant this warp may read
+    const int h = (warp - 2) >> 2;  // which of the quadrant's two warps
     const int row = q * 32 + lane;
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -452,12 +457,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       fence_after();
       const int m = x.tm * BM + row;
-      for (int c = 0; c < TileCfg<BN>::FULL; ++c) {
+      for (int c = h; c < TileCfg<BN>::FULL; c += 2) {
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c * 32), r);
         sch.store(x, m, x.tn * BN + c * 32, r, 32);
       }
-      if constexpr (TileCfg<BN>::HALF) {
+      if (TileCfg<BN>::HALF && h == (TileCfg<BN>::FULL & 1)) {
         uint32_t r[32];
         const int c0 = TileCfg<BN>::FULL * 32;
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0), r);

@@ -28,6 +28,8 @@ __constant__ int c_perm3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2
 // One 32 x 32 tile per step; the tile's column tables (coefficient, base offset,
 // selector of up to 3 terms) and, with a single selector, its 32 row offsets
 // are staged in shared memory, so an element costs one source load.
+// F32: FP32 arithmetic into split panels (FP32 sources read directly, FP64 sources
+// converted on the integer path); otherwise FP64 arithmetic (FP64 panels).
 template <bool F32>
 __device__ __forceinline__ void pack_tiles(const PackArgs& a, int r0, int kfirst, int kstep) {
   typedef typename std::conditional<F32, float, double>::type T;
@@ -57,8 +59,8 @@ __device__ __forceinline__ void pack_tiles(const PackArgs& a, int r0, int kfirst
         const i64 off = cb[t][kk] + (rm ? lab[0][rr] * cs[t][0][kk] + lab[1][rr] * cs[t][1][kk] +
                                               lab[2][rr] * cs[t][2][kk]
                                         : (a.one_sel ? ro[rr] : a.rowoff[(i64)sl[t][kk] * a.R + r]));
-        if constexpr (F32)
-          s += c * ((const float*)a.src)[off];  // no FP64 conversions on the FP32 path
+        if constexpr (F32)  // no FP64 instructions on the FP32 path
+          s += c * (a.src_f32 ? ((const float*)a.src)[off] : f64_to_f32_rn(((const double*)a.src)[off]));
         else
           s += c * (T)load_src(a.src, a.src_f32, off);
       }
@@ -213,6 +215,8 @@ __device__ __forceinline__ void pack_tiles_any(const PackArgs& a, int r0, int kf
       if (a.kind == PANEL_BF16X2) pack_tiles_f32<3, PANEL_BF16X2>(a, r0, kfirst, kstep);
       else pack_tiles_f32<3, PANEL_TF32X2>(a, r0, kfirst, kstep);
     }
+  } else if (a.kind != PANEL_F64) {
+    pack_tiles<true>(a, r0, kfirst, kstep);  // FP64 source into split panels
   } else {
     pack_tiles<false>(a, r0, kfirst, kstep);
   }
@@ -445,30 +449,71 @@ void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, 
 // ---------------------------------------------------------------------------
 // Dense permuted linear combination.
 // ---------------------------------------------------------------------------
+template <bool FAST>
 __global__ void k_combine(CombineArgs c) {
   const i64 total = c.total;
   for (i64 idx = blockIdx.x * (i64)blockDim.x + threadIdx.x; idx < total;
        idx += (i64)gridDim.x * blockDim.x) {
-    i64 rem = idx, ooff = 0;
+    i64 ooff = 0;
     i64 ioff[4] = {0, 0, 0, 0};
-    for (int d = c.rank - 1; d >= 0; --d) {
-      const i64 x = rem % c.shape[d];
-      rem /= c.shape[d];
-      ooff += x * c.ostride[d];
-      for (int t = 0; t < c.nterm; ++t) ioff[t] += x * c.istride[t][d];
+    if constexpr (FAST) {
+      unsigned rem = (unsigned)idx;
+#pragma unroll
+      for (int d = 5; d >= 0; --d) {
+        if (d >= c.rank) continue;
+        const unsigned q = (__umulhi(c.fdm[d], rem) + rem) >> c.fdl[d];
+        const i64 x = (i64)(rem - q * (unsigned)c.shape[d]);
+        rem = q;
+        ooff += x * c.ostride[d];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < c.nterm) ioff[t] += x * c.istride[t][d];
+      }
+    } else {
+      i64 rem = idx;
+      for (int d = c.rank - 1; d >= 0; --d) {
+        const i64 x = rem % c.shape[d];
+        rem /= c.shape[d];
+        ooff += x * c.ostride[d];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < c.nterm) ioff[t] += x * c.istride[t][d];
+      }
+    }
+    if (c.beta == 0.0 && c.nterm == 1 && c.coef[0] == 1.0) {  // a permuted copy: no FP64 arithmetic
+      c.out[ooff] = c.in[0][ioff[0]];
+      continue;
     }
     double s = c.beta == 0.0 ? 0.0 : c.beta * c.out[ooff];
-    for (int t = 0; t < c.nterm; ++t) s += c.coef[t] * c.in[t][ioff[t]];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t < c.nterm) s += c.coef[t] * c.in[t][ioff[t]];
     c.out[ooff] = s;
   }
 }
 
-void launch_combine(const CombineArgs& c, cudaStream_t s) {
-  if (c.total <= 0) return;
+void launch_combine(const CombineArgs& c0, cudaStream_t s) {
+  if (c0.total <= 0) return;
+  CombineArgs c = c0;
+  const bool fast = c.total < (1LL << 31);
+  if (fast) {
+    // divisor d < 2^31: l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1 < 2^32;
+    // then n / d = (umulhi(m, n) + n) >> l for every n < 2^31
+    for (int d = 0; d < c.rank; ++d) {
+      const unsigned long long dv = (unsigned long long)c.shape[d];
+      int l = 0;
+      while ((1ULL << l) < dv) ++l;
+      c.fdl[d] = l;
+      c.fdm[d] = (unsigned)(((1ULL << 32) * ((1ULL << l) - dv)) / dv + 1);
+    }
+  }
   i64 blocks = (c.total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   ++g_launch_count;
-  k_combine<<<(unsigned)blocks, 256, 0, s>>>(c);
+  if (fast)
+    k_combine<true><<<(unsigned)blocks, 256, 0, s>>>(c);
+  else
+    k_combine<false><<<(unsigned)blocks, 256, 0, s>>>(c);
 }
 
 // ---------------------------------------------------------------------------
@@ -1302,13 +1347,25 @@ __global__ void __launch_bounds__(256) k_r1_slab(const T* __restrict__ S, const 
   for (i64 sgi = blockIdx.x; sgi < nslab; sgi += gridDim.x) {
     const T* src = S + sgi * V2;
     __syncthreads();  // the previous slab is consumed
+    // asynchronous element copies (cp.async, no register staging): all of a thread's
+    // loads of the slab are in flight at once
     for (int c = warp; c < v; c += 8) {
       const T* row = src + (i64)c * v;
       T* dst = sl + c * (v + 1);
-#pragma unroll 4
-      for (int x = lane; x < v; x += 32) dst[x] = row[x];
+      for (int x = lane; x < v; x += 32) {
+        if constexpr (sizeof(T) == 4)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst + x)),
+                       "l"(row + x)
+                       : "memory");
+        else
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst + x)),
+                       "l"(row + x)
+                       : "memory");
+      }
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
     for (int c = threadIdx.x; c < v; c += blockDim.x) ws[c] = (T)oovv[sgi * v + c];
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     if (a < v) {
       const T* col = sl + a;                 // sl[c][a] over c

@@ -20,6 +20,10 @@ struct CombineArgs {
   i64 istride[4][6];
   double coef[4];
   double beta;
+  // filled by launch_combine: 32-bit index division by shape[d] as a multiply-high
+  // and shift (Granlund & Montgomery, PLDI 1994, round-up method) when total < 2^31
+  unsigned fdm[6];
+  int fdl[6];
 };
 
 void launch_pack(const PackArgs& a, cudaStream_t s);

@@ -23,6 +23,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <array>
+#include <limits>
 #include <map>
 #include <memory>
 #include <string>
@@ -189,6 +190,9 @@ struct GemmPlan {
   std::vector<rcc::CubePiece> h_cube;
   std::unique_ptr<DBuf> cube;
   int cube_mode = -1;
+  // stacked rows: the A panel is the concatenation of these plans' A operands
+  // (each packed into its row range); the plan stands for all of them
+  std::vector<GemmPlan*> a_parts;
 };
 
 struct rccsdt_ctx {
@@ -370,6 +374,105 @@ void finish_plan(rccsdt_ctx* c, GemmPlan* g, int K) {
   g->fma = (double)g->E.e.M * g->E.e.N * K;
   size_t need = (size_t)std::max(g->A.a.R, g->B.a.R) * g->Kpad * 8;
   if (need > c->panel_bytes) c->panel_bytes = need;
+}
+
+// The allocation holding p (start pointer and element offset of p in it).
+static bool locate(rccsdt_ctx* c, const void* p, size_t esz, void** start, i64* off) {
+  for (auto& kv : c->buf) {
+    const char* b = (const char*)kv.second->p;
+    if (b && (const char*)p >= b && (const char*)p < b + kv.second->bytes) {
+      *start = kv.second->p;
+      *off = (i64)(((const char*)p - b) / esz);
+      return ((const char*)p - b) % esz == 0;
+    }
+  }
+  return false;
+}
+
+// One GEMM for plans that share their B operand (same N, K and K order; the first
+// part's B is taken over): their A operands are stacked into one panel, so the B
+// panel is streamed once for all of them.  The parts' outputs may lie in at most
+// two allocations of one element type, the parts writing the first one coming
+// first, and the address ranges of parts in one allocation must not overlap
+// (rows of one GEMM update their elements concurrently, without atomics).
+// Returns null (parts unchanged) when the parts do not fit this form.
+GemmPlan* stack_rows(rccsdt_ctx* c, const std::vector<GemmPlan*>& parts, int* err) {
+  if (parts.size() < 2) return nullptr;
+  const GemmPlan* p0 = parts[0];
+  const size_t esz = p0->E.e.c_f32 ? 4 : 8;
+  void* bufs[2] = {nullptr, nullptr};
+  int m2 = -1, M = 0, nsel_total = 0;
+  const int N = p0->E.e.N;
+  std::vector<i64> rb, co;
+  std::vector<int> rs;
+  std::vector<double> ra;
+  std::vector<std::array<i64, 3>> span;  // per part: slot, first and last element written
+  for (const GemmPlan* q : parts) {
+    const rcc::EpiArgs& e = q->E.e;
+    if (e.N != N || q->K != p0->K || e.c_f32 != p0->E.e.c_f32 || q->s3_rows || q->tc_swap || e.C2) return nullptr;
+    void* start = nullptr;
+    i64 off = 0;
+    if (!locate(c, e.C, esz, &start, &off)) return nullptr;
+    int slot = start == bufs[0] ? 0 : (start == bufs[1] ? 1 : -1);
+    if (slot < 0) {
+      if (!bufs[0]) slot = 0;
+      else if (!bufs[1]) slot = 1;
+      else return nullptr;
+      bufs[slot] = start;
+      if (slot == 1) m2 = M;
+    }
+    if (slot == 0 && m2 >= 0) return nullptr;  // rows of the first output must come first
+    std::vector<i64> hb(e.M);
+    std::vector<int> hs(e.M);
+    std::vector<double> ha(e.M);
+    if (dev_copy(hb.data(), e.row_base, hb.size() * 8, c->stream) ||
+        dev_copy(hs.data(), e.row_sel, hs.size() * 4, c->stream) ||
+        dev_copy(ha.data(), e.row_alpha, ha.size() * 8, c->stream) || dev_sync(c->stream)) {
+      *err = RCCSDT_ERR_CUDA;
+      return nullptr;
+    }
+    int nsel = 0;
+    for (int x : hs) nsel = std::max(nsel, x + 1);
+    std::vector<i64> hc((size_t)nsel * N);
+    if (dev_copy(hc.data(), e.col_off, hc.size() * 8, c->stream) || dev_sync(c->stream)) {
+      *err = RCCSDT_ERR_CUDA;
+      return nullptr;
+    }
+    i64 lo = std::numeric_limits<i64>::max(), hi = std::numeric_limits<i64>::min();
+    for (int m = 0; m < e.M; ++m) {
+      rb.push_back(hb[m] + off);
+      rs.push_back(hs[m] + nsel_total);
+      ra.push_back(ha[m]);
+      for (int n = 0; n < N; ++n) {
+        const i64 a = hb[m] + off + hc[(size_t)hs[m] * N + n];
+        lo = std::min(lo, a);
+        hi = std::max(hi, a);
+      }
+    }
+    for (const auto& sp : span)
+      if (sp[0] == slot && lo <= sp[2] && sp[1] <= hi) return nullptr;
+    span.push_back({(i64)slot, lo, hi});
+    co.insert(co.end(), hc.begin(), hc.end());
+    nsel_total += nsel;
+    M += e.M;
+  }
+  c->plans.push_back(std::make_unique<GemmPlan>());
+  GemmPlan* g = c->plans.back().get();
+  GemmPlan* b0 = parts[0];
+  g->B = std::move(b0->B);
+  g->h_cube = std::move(b0->h_cube);
+  g->cube = std::move(b0->cube);
+  g->cube_mode = b0->cube_mode;
+  make_epi(c, g->E, bufs[0], p0->E.e.c_f32, M, N, rb, rs, ra, co, err);
+  g->E.e.C2 = bufs[1];
+  g->E.e.m2 = m2 >= 0 ? m2 : M;
+  g->a_parts = parts;
+  g->reuse_B = b0->reuse_B;  // the first part's B may be the panel of the plan before
+  g->A.a.R = M;
+  g->step = p0->step;
+  g->big = 1;
+  finish_plan(c, g, p0->K);
+  return g;
 }
 
 // Multi-index enumeration: offsets sum_d idx_d * stride_d over dims in order.
@@ -562,7 +665,20 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   pa.out_lo = c->panelA_lo ? c->panelA_lo->p : nullptr;
   pb.out_hi = c->panelB_hi->p;
   pb.out_lo = c->panelB_lo ? c->panelB_lo->p : nullptr;
-  if (!g->reuse_A || c->packedA_kind != kind) rcc::launch_pack(pa, c->stream);
+  if (!g->a_parts.empty()) {
+    const size_t esz = kind == rcc::PANEL_F64 ? 8 : (kind == rcc::PANEL_BF16X2 ? 2 : 4);
+    size_t r0 = 0;
+    for (GemmPlan* q : g->a_parts) {
+      rcc::PackArgs pq = q->A.a;
+      pq.kind = kind;
+      pq.out_hi = (char*)c->panelA_hi->p + r0 * g->Kpad * esz;
+      pq.out_lo = c->panelA_lo ? (void*)((char*)c->panelA_lo->p + r0 * g->Kpad * esz) : nullptr;
+      rcc::launch_pack(pq, c->stream);
+      r0 += (size_t)pq.R;
+    }
+  } else if (!g->reuse_A || c->packedA_kind != kind) {
+    rcc::launch_pack(pa, c->stream);
+  }
   if (!g->reuse_B || c->packedB_kind != kind) {
     if (tc && g->cube) {
       const rcc::CubeDst d0{pb.out_hi, pb.out_lo, g->Kpad};
@@ -851,7 +967,9 @@ int build_context(rccsdt_ctx* c) {
   View vs_oovo = b.T("vs_oovo", {o, o, v, o});
   View Fvv = b.T("Fvv", {v, v}), Foo = b.T("Foo", {o, o}), Woooo = b.T("Woooo", {o, o, o, o});
   View Wovvo = b.T("Wovvo", {o, v, v, o}), Wovov = b.T("Wovov", {o, v, o, v});
-  View Wvvvo = b.T("Wvvvo", {v, v, v, o}), Wvooo = b.T("Wvooo", {v, o, o, o});
+  // W^{ab}_{dj} is stored [j][a][b][d]: the T3 contribution of step (iii) writes it
+  // along d (the rows of its GEMM) and the T2-driven R3 term reads it along d (K)
+  View Wvvvo = strided(c->D("Wvvvo"), {v, v, v, o}, {V2, v, 1, V3}), Wvooo = b.T("Wvooo", {v, o, o, o});
   View Wb_ovvo = b.T("Wb_ovvo", {o, v, v, o}), Wb_ovov = b.T("Wb_ovov", {o, v, o, v});
   View Wvvvv = b.T("Wvvvv", {v, v, v, v});
   c->c_int_base.push_back(combine(Fvv, 0.0, {{1.0, sub(sub(ft, 0, V0, v), 1, V0, v)}}));
@@ -859,7 +977,7 @@ int build_context(rccsdt_ctx* c) {
   c->c_int_base.push_back(combine(Woooo, 0.0, {{1.0, eri("oooo")}}));
   c->c_int_base.push_back(combine(Wovvo, 0.0, {{2.0, eri("ovvo")}, {-1.0, permuted(eri("ovov"), {0, 1, 3, 2})}}));
   c->c_int_base.push_back(combine(Wovov, 0.0, {{1.0, eri("ovov")}}));
-  c->c_int_base.push_back(combine(Wvvvo, 0.0, {{1.0, eri("vvvo")}}));
+  c->c_int_base.push_back(combine(permuted(Wvvvo, {3, 0, 1, 2}), 0.0, {{1.0, permuted(eri("vvvo"), {3, 0, 1, 2})}}));
   c->c_int_base.push_back(combine(Wvooo, 0.0, {{1.0, eri("vooo")}}));
   c->c_int_base.push_back(combine(Wvvvv, 0.0, {{1.0, eri("vvvv")}}));
   b.ct(c->p_int, "kldc,kldb->bc", -1.0, vs_oovv, t2, Fvv);
@@ -870,7 +988,7 @@ int build_context(rccsdt_ctx* c) {
   b.ct(c->p_int, "laed,ljeb->abdj", 0.5, vs_ovvv, ts2, Wvvvo);
   b.ct(c->p_int, "lade,jleb->abdj", -0.5, eri("ovvv"), t2, Wvvvo);
   b.ct(c->p_int, "lbde,jlea->abdj", -1.0, eri("ovvv"), t2, Wvvvo);
-  b.ct(c->p_int, "lmdj,lmab->abdj", 1.0, eri("oovo"), t2, Wvvvo);
+  b.ct(c->p_int, "lmdj,lmab->jabd", 1.0, eri("oovo"), t2, permuted(Wvvvo, {3, 0, 1, 2}));  // rows (j, d)
   b.ct(c->p_int, "ld,ijad->alij", 1.0, sub(sub(ft, 0, O0, o), 1, V0, v), t2, Wvooo);
   b.ct(c->p_int, "mldj,mida->alij", 0.5, vs_oovo, ts2, Wvooo);
   b.ct(c->p_int, "mljd,imda->alij", -0.5, eri("ooov"), t2, Wvooo);
@@ -949,6 +1067,21 @@ int build_context(rccsdt_ctx* c) {
         set_cube(c, q3, 0, std::move(pb_), &err);
         set_cube(c, q4, 0, pc_, &err);
         set_cube(c, q5, 0, std::move(pc_), &err);
+      }
+      // one pass over each S panel: the contractions sharing it run as one GEMM with
+      // stacked A operands.  (With Zb = 1 the first contraction's panel is the
+      // second's too, but both write dX2[y][z0], so they stay two GEMMs.)
+      if (q1 && q2 && q3 && q4 && q5) {
+        auto replace = [&](const std::vector<GemmPlan*>& parts) {
+          GemmPlan* m = stack_rows(c, parts, &err);
+          if (!m) return;
+          auto at = std::find(g.begin(), g.end(), parts[0]);
+          const size_t pos = (size_t)(at - g.begin());
+          for (GemmPlan* q : parts) g.erase(std::find(g.begin(), g.end(), q));
+          g.insert(g.begin() + pos, m);
+        };
+        replace({q2, q3});
+        replace({q4, q5});
       }
     }
   }
@@ -1261,12 +1394,12 @@ int build_context(rccsdt_ctx* c) {
           esel[r] = ti.pos[0] * 3 + ti.pos[1];
           ealpha[r] = 6.0 / ti.m;
         }
-      for (int d = 0; d < v; ++d) { acol[d] = (i64)d * v; bcol[d] = (i64)d * o; }
-      for (i64 ab = 0; ab < V2; ++ab) brow[ab] = ab * v * o + j;
+      for (int d = 0; d < v; ++d) { acol[d] = (i64)d * v; bcol[d] = d; }
+      for (i64 ab = 0; ab < V2; ++ab) brow[ab] = (i64)j * V3 + ab * v;  // W stored [j][a][b][d]
       make_pack(c, g->A, c->D("t2"), 0, M, K, 1, std::vector<double>(K, 1.0), acol, std::vector<int>(K, 0), arow, 0,
                 &err);
       make_pack(c, g->B, c->D("Wvvvo"), 0, (int)V2, K, 1, std::vector<double>(K, 1.0), bcol, std::vector<int>(K, 0),
-                brow, 0, &err);
+                brow, 1, &err);
       make_epi(c, g->E, r3p, t3f, M, (int)V2, ebase, esel, ealpha, {}, &err, b.RT2);
       g->big = 1;
       g->step = 4;
@@ -2165,7 +2298,19 @@ RCC_API int rccsdt_debug_copy(rccsdt_ctx* c, const char* name, double* out, long
   if (!c || !name || !out) return RCCSDT_ERR_ARG;
   auto it = c->buf.find(name);
   if (it == c->buf.end()) return fail(c, RCCSDT_ERR_ARG, std::string("no tensor ") + name);
-  if ((size_t)count * 8 > it->second->bytes) return fail(c, RCCSDT_ERR_ARG, "count too large");
+  if (count < 0 || (size_t)count * 8 > it->second->bytes) return fail(c, RCCSDT_ERR_ARG, "count too large");
+  if (std::string(name) == "Wvvvo") {
+    // stored [j][a][b][d]; returned in the symbol's order [a][b][d][j]
+    const i64 o = c->o, V3 = c->V3;
+    std::vector<double> h((size_t)(o * V3));
+    if (dev_copy(h.data(), it->second->p, h.size() * 8, c->stream) || dev_sync(c->stream))
+      return fail(c, RCCSDT_ERR_CUDA, "copy");
+    for (i64 x = 0; x < count; ++x) {
+      const i64 j = x % o, abd = x / o;
+      out[x] = h[(size_t)(j * V3 + abd)];  // a V^2 + b v + d = abd
+    }
+    return RCCSDT_OK;
+  }
   if (dev_copy(out, it->second->p, (size_t)count * 8, c->stream) || dev_sync(c->stream))
     return fail(c, RCCSDT_ERR_CUDA, "copy");
   return RCCSDT_OK;

@@ -450,3 +450,8 @@ void launch_t2_outer(T* r3, const T* Wvooo, const T* t2, const int4* blocks, int
 template void launch_t2_outer<double>(double*, const double*, const double*, const int4*, int, int, i64, cudaStream_t);
 template void launch_t2_outer<float>(float*, const float*, const float*, const int4*, int, int, i64, cudaStream_t);
 }  // namespace rcc
+
+// Test hook: the integer-path binary64 -> binary32 conversion of the panel gathers.
+extern "C" void rcc_test_f64_to_f32(const double* x, float* y, long long n) {
+  for (long long i = 0; i < n; ++i) y[i] = rcc::f64_to_f32_rn(x[i]);
+}

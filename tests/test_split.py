@@ -49,6 +49,31 @@ def test_split_residual_matches_oracle(kind, prec, o, v, naux, grouped):
 
 
 @pytest.mark.parametrize("kind", BACKENDS)
+@pytest.mark.parametrize("o,v,naux", [(3, 12, 40), (4, 9, 16)])
+def test_split_step_iii_one_z_at_a_time(kind, o, v, naux):
+    """Step (iii) on one z per batch (the S panel of the first contraction is then
+    the second's; the second and third share one GEMM with stacked A operands)."""
+    lib = gpu_lib() if kind == "gpu" else hostsim_lib()
+    inst = make_instance(o, v, naux, seed=o + 2 * v)
+    t1, t2, t3 = random_amplitudes(o, v, seed=v + o)
+    t3c = oc.pack(t3)
+    ctx = B.Context(lib, o, v, naux, precision=B.SPLIT_BF16X3, unpack_bytes=1)
+    ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    ctx.set_amplitudes(t1, t2, t3c)
+    ctx.build_intermediates()
+    ctx.residual()
+    ctx.postprocess()
+    r1, r2, r3 = ctx.residuals()
+    R1, R2, R3 = oc.residuals_compact(inst.L, inst.fock_diag, t1, t2, t3c)
+    scale = max(1.0, np.abs(R3).max())
+    tol = TOL[B.SPLIT_BF16X3]
+    assert np.abs(r1 - R1).max() / scale < tol
+    assert np.abs(r2 - R2).max() / scale < tol
+    assert np.abs(oc.postprocess(r3, o) - oc.postprocess(R3, o)).max() / scale < tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind", BACKENDS)
 @pytest.mark.parametrize("prec", [B.SPLIT_BF16X3, B.SPLIT_TF32X3], ids=["bf16x3", "tf32x3"])
 def test_split_solve_refines_to_fp64_energy(kind, prec):
     """Split iterations, then FP64 refinement: converged energy within 1e-6 Eh

@@ -84,19 +84,38 @@ __device__ __forceinline__ void store_run(const CubeDst& d, i64 row, int k, cons
   }
 }
 
-// Mode 0: grid (label cubes of 16^3, pieces).  Shared: one [16][17][18] cube per term.
-template <int KIND>
+// Mode 0: grid (label cubes of 16^3, pieces).  Shared: one [16][17][18] cube that
+// accumulates the terms one after the other (19 KB, so small enough for the
+// register limit, not shared memory, to set the occupancy).
+//
+// R1 (the variant for the S panels of step (iii)): piece p is the spin-summed block
+// S^{xy}[e1][e2][e3] of one z (L0, L1, L2 = e1, e2, e3) and the CTA also forms the
+// two partial sums of the T3 term of R1 over its cube,
+//   A[e3] = sum_{e1,e2} v^{xy}_{e1 e2} S[e1][e2][e3],  B[e2] = sum_{e1,e3} v^{xy}_{e1 e3} S[e1][e2][e3]
+// (w + wbase[p] = v^{xy} as [v][v] floats), written in a fixed order to
+// part[(p * cubes + cube) * 32 + (0..15: A, 16..31: B)].
+template <int KIND, bool R1>
 __global__ void __launch_bounds__(256) k_cube_pack_k(const CubePiece* __restrict__ pieces,
                                                      const CubeDst* __restrict__ dsts, CubeDst d0,
-                                                     const float* __restrict__ src, int v) {
+                                                     const float* __restrict__ src, int v,
+                                                     const float* __restrict__ w, const i64* __restrict__ wbase,
+                                                     float* __restrict__ part) {
   constexpr int TL = 16, CA = (TL + 1) * (TL + 2), CB = TL + 2;
   extern __shared__ __align__(16) float cube_smem[];
+  __shared__ float wA[R1 ? TL : 1][TL + 1], wB[R1 ? TL : 1][TL + 1], red[R1 ? TL : 1][TL + 1];
   const CubePiece& P = pieces[blockIdx.y];
   const int nterm = P.nterm;
   const int nc = (v + TL - 1) / TL;
   const int cb = blockIdx.x;
   const int lo[3] = {(cb / (nc * nc)) * TL, ((cb / nc) % nc) * TL, (cb % nc) * TL};
   const int lf = threadIdx.x & 15, lm = threadIdx.x >> 4;
+  if constexpr (R1) {
+    // weights v^{xy}_{e1 e2} and v^{xy}_{e1 e3} of this cube (zero outside v)
+    const float* wp = w + wbase[blockIdx.y];
+    const int e1 = lo[0] + lm;
+    wA[lm][lf] = (e1 < v && lo[1] + lf < v) ? wp[(i64)e1 * v + lo[1] + lf] : 0.f;
+    wB[lm][lf] = (e1 < v && lo[2] + lf < v) ? wp[(i64)e1 * v + lo[2] + lf] : 0.f;
+  }
   for (int t = 0; t < nterm; ++t) {
     const int pos = P.t[t].pos;
     const int p0 = pos_of(pos, 0), p1 = pos_of(pos, 1);
@@ -114,23 +133,48 @@ __global__ void __launch_bounds__(256) k_cube_pack_k(const CubePiece* __restrict
     float ld[TL];
 #pragma unroll
     for (int u = 0; u < TL; ++u) ld[u] = (in && xs + u < v) ? __ldg(s0 + u * ss) : 0.f;
-    float* c = cube_smem + t * TL * CA + lf * cf + lm * cmid;
+    float* c = cube_smem + lf * cf + lm * cmid;
+    const float coef = P.t[t].coef;
+    if (t == 0) {
 #pragma unroll
-    for (int u = 0; u < TL; ++u) c[u * cs] = ld[u];
+      for (int u = 0; u < TL; ++u) c[u * cs] = fmaf(coef, ld[u], 0.f);
+    } else {
+      __syncthreads();  // the previous term's updates of these positions are done
+#pragma unroll
+      for (int u = 0; u < TL; ++u) c[u * cs] = fmaf(coef, ld[u], c[u * cs]);
+    }
   }
   __syncthreads();
   // thread (L1, L2) = (lm, lf) writes its row's run of 16 K values (L0)
   const int g1 = lo[1] + lm, g2 = lo[2] + lf;
-  if (g1 >= v || g2 >= v) return;
   float x[TL];
+  {
+    const float* c = cube_smem + lm * CB + lf;
 #pragma unroll
-  for (int u = 0; u < TL; ++u) x[u] = 0.f;
-  for (int t = 0; t < nterm; ++t) {
-    const float cf = P.t[t].coef;
-    const float* c = cube_smem + t * TL * CA + lm * CB + lf;
-#pragma unroll
-    for (int u = 0; u < TL; ++u) x[u] = fmaf(cf, c[u * CA], x[u]);
+    for (int u = 0; u < TL; ++u) x[u] = nterm > 0 ? c[u * CA] : 0.f;
   }
+  if constexpr (R1) {
+    // labels outside v hold zeros in the cube, so every thread takes part
+    float sa = 0.f, sb = 0.f;
+#pragma unroll
+    for (int u = 0; u < TL; ++u) {
+      sa = fmaf(wA[u][lm], x[u], sa);
+      sb = fmaf(wB[u][lf], x[u], sb);
+    }
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) sb += __shfl_xor_sync(0xffffffffu, sb, off);  // over e3 (lf)
+    red[lm][lf] = sa;
+    __syncthreads();
+    float* out = part + ((i64)blockIdx.y * gridDim.x + blockIdx.x) * 32;
+    if (threadIdx.x < TL) {  // over e2 (lm), fixed order
+      float a = 0.f;
+#pragma unroll
+      for (int q = 0; q < TL; ++q) a += red[q][threadIdx.x];
+      out[threadIdx.x] = a;
+    }
+    if (lf == 0) out[TL + lm] = sb;
+  }
+  if (g1 >= v || g2 >= v) return;
   const CubeDst d = dsts ? dsts[P.dst] : d0;
   const int n = min(TL, v - lo[0]);
   const int k = P.k0 + lo[0] + g1 * P.ks1;
@@ -229,19 +273,13 @@ void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, 
   if (npieces <= 0) return;
   if (mode == 0) {
     const int nc = (v + 15) / 16;
-    const size_t smem = (size_t)3 * 16 * 17 * 18 * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_cube_pack_k<PANEL_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(k_cube_pack_k<PANEL_TF32X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
-    }
+    const size_t smem = (size_t)16 * 17 * 18 * sizeof(float);
     dim3 grid((unsigned)(nc * nc * nc), (unsigned)npieces);
     ++g_launch_count;
     if (kind == PANEL_BF16X2)
-      k_cube_pack_k<PANEL_BF16X2><<<grid, 256, smem, s>>>(pieces, dsts, d0, src, v);
+      k_cube_pack_k<PANEL_BF16X2, false><<<grid, 256, smem, s>>>(pieces, dsts, d0, src, v, nullptr, nullptr, nullptr);
     else
-      k_cube_pack_k<PANEL_TF32X2><<<grid, 256, smem, s>>>(pieces, dsts, d0, src, v);
+      k_cube_pack_k<PANEL_TF32X2, false><<<grid, 256, smem, s>>>(pieces, dsts, d0, src, v, nullptr, nullptr, nullptr);
   } else {
     const int nc = (v + 7) / 8;
     dim3 grid((unsigned)(nc * nc * nc), (unsigned)(npieces / 16));
@@ -251,6 +289,56 @@ void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, 
     else
       k_cube_pack_col<PANEL_TF32X2><<<grid, 256, 0, s>>>(pieces, dsts, d0, src, v);
   }
+}
+
+void launch_cube_pack_r1(int kind, const CubePiece* pieces, int npieces, const CubeDst& d0, const float* src, int v,
+                         const float* w, const i64* wbase, float* part, cudaStream_t s) {
+  if (npieces <= 0) return;
+  const int nc = (v + 15) / 16;
+  const size_t smem = (size_t)16 * 17 * 18 * sizeof(float);
+  dim3 grid((unsigned)(nc * nc * nc), (unsigned)npieces);
+  ++g_launch_count;
+  if (kind == PANEL_BF16X2)
+    k_cube_pack_k<PANEL_BF16X2, true><<<grid, 256, smem, s>>>(pieces, nullptr, d0, src, v, w, wbase, part);
+  else
+    k_cube_pack_k<PANEL_TF32X2, true><<<grid, 256, smem, s>>>(pieces, nullptr, d0, src, v, w, wbase, part);
+}
+
+// dR1[z][a] += sum over the pieces of z and the cubes holding a of A[a] - B[a] / 2
+// (the partials of k_cube_pack_k<R1>).  One block per (z, a); each thread sums a
+// fixed strided subset in FP64, then a fixed-order tree: deterministic.
+__global__ void __launch_bounds__(256) k_r1_cubes_reduce(const float* __restrict__ part, int ppz, int nc, int v,
+                                                         double* __restrict__ dR1) {
+  __shared__ double acc[256];
+  const int z = blockIdx.y, a = blockIdx.x;
+  const int ta = a / 16, r = a % 16;
+  const int per = nc * nc;  // cubes of one piece whose e3 (or e2) tile is ta
+  const i64 total = (i64)ppz * per * 2;
+  double s = 0.0;
+  for (i64 q = threadIdx.x; q < total; q += blockDim.x) {
+    const int kind = (int)(q % 2);
+    const i64 rest = q / 2;
+    const int c2 = (int)(rest % per);
+    const i64 p = (i64)z * ppz + rest / per;
+    // cube index (t0, t1, t2) = lo / 16: A needs t2 = ta, B needs t1 = ta
+    const int t0 = c2 / nc, tx = c2 % nc;
+    const int cube = kind == 0 ? (t0 * nc + tx) * nc + ta : (t0 * nc + ta) * nc + tx;
+    const float val = part[(p * (i64)(nc * nc * nc) + cube) * 32 + kind * 16 + r];
+    s += kind == 0 ? (double)val : -0.5 * (double)val;
+  }
+  acc[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) acc[threadIdx.x] += acc[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dR1[(i64)z * v + a] += acc[0];
+}
+
+void launch_r1_cubes_reduce(const float* part, int ppz, int nz, int v, double* dR1, cudaStream_t s) {
+  if (ppz <= 0 || nz <= 0) return;
+  ++g_launch_count;
+  k_r1_cubes_reduce<<<dim3((unsigned)v, (unsigned)nz), 256, 0, s>>>(part, ppz, (v + 15) / 16, v, dR1);
 }
 
 void launch_zero_cols(const CubeDst& d, i64 rows, int k0, int kind, cudaStream_t s) {

@@ -190,6 +190,10 @@ struct GemmPlan {
   std::vector<rcc::CubePiece> h_cube;
   std::unique_ptr<DBuf> cube;
   int cube_mode = -1;
+  const float* cube_src = nullptr;  // the pieces' source (default: the B operand's)
+  // step (iii): the cube gather also forms the partial sums of the T3 term of R1
+  // (per piece, the offset of v^{xy} in the FP32 copy of the oovv integrals)
+  std::unique_ptr<DBuf> r1_wbase;
   // stacked rows: the A panel is the concatenation of these plans' A operands
   // (each packed into its row range); the plan stands for all of them
   std::vector<GemmPlan*> a_parts;
@@ -227,6 +231,7 @@ struct rccsdt_ctx {
   std::vector<std::vector<GemmPlan*>> p_a3;  // per batch of a3_Z values of z
   std::vector<GemmPlan*> p_wbar;             // the W-bar contractions before step (iii)
   int a3_Z = 1;
+  int a3_direct = 0;  // batches whose split-body panels are gathered from T3 (all of them, or none used)
   std::vector<GemmPlan*> p_pp, p_hh, p_ringab, p_ringc, p_t2a;
   // combines
   std::vector<rcc::CombineArgs> c_fock, c_helpers, c_int_base, c_r12_base, c_r2_sym, c_wt;
@@ -463,6 +468,8 @@ GemmPlan* stack_rows(rccsdt_ctx* c, const std::vector<GemmPlan*>& parts, int* er
   g->h_cube = std::move(b0->h_cube);
   g->cube = std::move(b0->cube);
   g->cube_mode = b0->cube_mode;
+  g->cube_src = b0->cube_src;
+  g->r1_wbase = std::move(b0->r1_wbase);
   make_epi(c, g->E, bufs[0], p0->E.e.c_f32, M, N, rb, rs, ra, co, err);
   g->E.e.C2 = bufs[1];
   g->E.e.m2 = m2 >= 0 ? m2 : M;
@@ -682,8 +689,13 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   if (!g->reuse_B || c->packedB_kind != kind) {
     if (tc && g->cube) {
       const rcc::CubeDst d0{pb.out_hi, pb.out_lo, g->Kpad};
-      rcc::launch_cube_pack(g->cube_mode, kind, (const rcc::CubePiece*)g->cube->p, (int)g->h_cube.size(), nullptr,
-                            d0, (const float*)pb.src, c->v, c->stream);
+      const float* src = g->cube_src ? g->cube_src : (const float*)pb.src;
+      if (g->r1_wbase)
+        rcc::launch_cube_pack_r1(kind, (const rcc::CubePiece*)g->cube->p, (int)g->h_cube.size(), d0, src, c->v,
+                                 c->B("oovv_f")->f(), (const i64*)g->r1_wbase->p, c->B("r1_part")->f(), c->stream);
+      else
+        rcc::launch_cube_pack(g->cube_mode, kind, (const rcc::CubePiece*)g->cube->p, (int)g->h_cube.size(), nullptr,
+                              d0, src, c->v, c->stream);
       if (g->cube_mode == 0) rcc::launch_zero_cols(d0, pb.R, g->K, kind, c->stream);
     } else {
       rcc::launch_pack(pb, c->stream);
@@ -875,6 +887,11 @@ int build_context(rccsdt_ctx* c) {
   const i64 ub = c->opt.unpack_bytes > 0 ? c->opt.unpack_bytes : (1LL << 30);
   c->a3_Z = (int)std::max<i64>(1, std::min<i64>(o, ub / std::max<i64>(1, (i64)o * o * V3 * (i64)t3e)));
   b.mk("Sz", (size_t)c->a3_Z * o * o * V3, t3e);
+  if (t3f) {  // split bodies of step (iii): panels gathered from T3, R1 partials per cube
+    const i64 nc = (v + 15) / 16;
+    b.mk("oovv_f", (size_t)o * o * V2, 4);
+    b.mk("r1_part", (size_t)c->a3_Z * o * o * nc * nc * nc * 32, 4);
+  }
   if (err) return fail(c, err, "device allocation failed");
 
   // --- block info and weights
@@ -1039,30 +1056,47 @@ int build_context(rccsdt_ctx* c) {
                           permuted(sub(permuted(Wvooo, {3, 0, 1, 2}), 0, z0, Zb), {0, 3, 1, 2}));
       if (q5) q5->reuse_B = 1;
       if (t3f && q1 && q2 && q3 && q4 && q5) {
-        // the S panels through label cubes: one piece per unpacked block S[z][x][y]
-        // (labels e1, e2, e3 on axes 0, 1, 2 of the block)
+        // split bodies: the S panels straight from T3 through label cubes, one piece
+        // per block S^{xy} = 2 U^{e1e2e3} - U^{e2e1e3} - U^{e3e2e1}, U = t_{x y z}
+        // (no unpacked batch); the first panel's gather also forms the R1 partials
+        auto spin = [&](rcc::CubePiece& pc, int x, int y, int z, const int lab[3]) {
+          // lab[q]: the S label (0 e1, 1 e2, 2 e3) of the piece's label Lq; term t
+          // reads S label s in slot slot[t][s] of U
+          static const int slot[3][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0}};
+          static const float coef[3] = {2.f, -1.f, -1.f};
+          const TripleInfo u = triple(x, y, z);
+          pc.nterm = 3;
+          for (int t = 0; t < 3; ++t)
+            pc.t[t] = {u.blk * V3, coef[t],
+                       packpos(u.pos[slot[t][lab[0]]], u.pos[slot[t][lab[1]]], u.pos[slot[t][lab[2]]])};
+        };
+        const int l123[3] = {0, 1, 2}, l132[3] = {0, 2, 1};
         std::vector<rcc::CubePiece> pa_, pb_, pc_;
+        std::vector<i64> wb;
         for (int z = 0; z < Zb; ++z)
           for (int x = 0; x < o; ++x)
             for (int y = 0; y < o; ++y) {
-              const i64 base = (((i64)z * o + x) * o + y) * V3;
-              rcc::CubePiece p1 = cube_piece(x * v, 1, v);  // rows (z, y, e2, e3), K (x, e1)
+              rcc::CubePiece p1 = cube_piece(x * v, 3, v);  // rows (z, y, e2, e3), K (x, e1)
               p1.row0 = ((i64)z * o + y) * V2;
-              p1.t[0] = {base, 1.f, packpos(0, 1, 2)};
-              rcc::CubePiece p2 = cube_piece((z * o + x) * v, 1, v);  // rows (y, e2, e3), K (z, x, e1)
+              spin(p1, x, y, z0 + z, l123);
+              rcc::CubePiece p2 = cube_piece((z * o + x) * v, 3, v);  // rows (y, e2, e3), K (z, x, e1)
               p2.row0 = (i64)y * V2;
-              p2.t[0] = {base, 1.f, packpos(0, 1, 2)};
-              rcc::CubePiece p4 = cube_piece(x * (int)V2, 1);  // rows (z, y, e2), K (x, e3, e1)
+              spin(p2, x, y, z0 + z, l123);
+              rcc::CubePiece p4 = cube_piece(x * (int)V2, 3);  // rows (z, y, e2), K (x, e3, e1)
               p4.ks1 = v;
               p4.rs1 = 0;
               p4.rs2 = 1;
               p4.row0 = ((i64)z * o + y) * v;
-              p4.t[0] = {base, 1.f, packpos(0, 2, 1)};  // L0 = e1, L1 = e3, L2 = e2
+              spin(p4, x, y, z0 + z, l132);  // L0 = e1, L1 = e3, L2 = e2
               pa_.push_back(p1);
               pb_.push_back(p2);
               pc_.push_back(p4);
+              wb.push_back(((i64)x * o + y) * V2);  // v^{xy} in oovv [x][y][b][c]
             }
+        for (GemmPlan* q : {q1, q2, q3, q4, q5}) q->cube_src = c->B("t3")->f();
         set_cube(c, q1, 0, pa_, &err);
+        q1->r1_wbase = upload_vec(c, wb, &err);
+        ++c->a3_direct;
         set_cube(c, q2, 0, pb_, &err);
         set_cube(c, q3, 0, std::move(pb_), &err);
         set_cube(c, q4, 0, pc_, &err);
@@ -1796,11 +1830,21 @@ int do_intermediates(rccsdt_ctx* c) {
   zero(c, "dX2");
   const int o = c->o;
   const int t3f = c->opt.precision != RCCSDT_FP64;
+  // split bodies gather the S panels from T3 directly (cube pieces, R1 partials);
+  // FP64 bodies unpack each batch of S and run the generic gathers
+  const bool direct = t3f && c->precision != RCCSDT_FP64 && c->a3_direct == (int)c->p_a3.size();
+  if (direct)
+    rcc::launch_convert<float, double>(c->B("oovv_f")->f(), c->D("oovv"), (i64)o * o * c->v * c->v, c->stream);
   const i64 slab = (i64)o * o * c->V3;  // S of one z
   for (int z0 = 0, bz = 0; z0 < o; z0 += c->a3_Z, ++bz) {
     const int Zb = std::min(c->a3_Z, o - z0);
     const i64* zb = (const i64*)c->a3_base->p + (size_t)z0 * o * o;
     const int* zp = (const int*)c->a3_pos->p + (size_t)z0 * o * o * 3;
+    if (direct) {
+      if ((st = run_plans(c, c->p_a3[bz]))) return st;
+      rcc::launch_r1_cubes_reduce(c->B("r1_part")->f(), o * o, Zb, c->v, c->D("dR1") + (size_t)z0 * c->v, c->stream);
+      continue;
+    }
     if (t3f)
       rcc::launch_unpack_spin<float>(c->B("t3")->p, 1, Zb * o * o, zb, zp, c->v, c->B("Sz")->f(), c->stream);
     else

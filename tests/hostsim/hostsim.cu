@@ -115,6 +115,58 @@ void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, 
   }
 }
 
+void launch_cube_pack_r1(int kind, const CubePiece* pieces, int npieces, const CubeDst& d0, const float* src, int v,
+                         const float* w, const i64* wbase, float* part, cudaStream_t st) {
+  launch_cube_pack(0, kind, pieces, npieces, nullptr, d0, src, v, st);
+  const i64 S[3] = {(i64)v * v, v, 1};
+  const int nc = (v + 15) / 16;
+  auto sval = [&](const CubePiece& P, int l0, int l1, int l2) {
+    if (l0 >= v || l1 >= v || l2 >= v) return 0.f;
+    float x = 0.f;
+    for (int t = 0; t < P.nterm; ++t) {
+      const int ps = P.t[t].pos;
+      x = std::fma(P.t[t].coef, src[P.t[t].base + l0 * S[ps & 3] + l1 * S[(ps >> 2) & 3] + l2 * S[(ps >> 4) & 3]], x);
+    }
+    return x;
+  };
+  for (int q = 0; q < npieces; ++q) {
+    const CubePiece& P = pieces[q];
+    const float* wp = w + wbase[q];
+    for (int cb = 0; cb < nc * nc * nc; ++cb) {
+      const int t0 = cb / (nc * nc), t1 = (cb / nc) % nc, t2 = cb % nc;
+      float* out = part + ((i64)q * nc * nc * nc + cb) * 32;
+      for (int r = 0; r < 16; ++r) {
+        float a = 0.f, b = 0.f;
+        for (int u = 0; u < 16; ++u)
+          for (int m = 0; m < 16; ++m) {
+            const int e1 = t0 * 16 + u;
+            if (e1 >= v) continue;
+            if (t1 * 16 + m < v) a += wp[(i64)e1 * v + t1 * 16 + m] * sval(P, e1, t1 * 16 + m, t2 * 16 + r);
+            if (t2 * 16 + m < v) b += wp[(i64)e1 * v + t2 * 16 + m] * sval(P, e1, t1 * 16 + r, t2 * 16 + m);
+          }
+        out[r] = a;
+        out[16 + r] = b;
+      }
+    }
+  }
+}
+
+void launch_r1_cubes_reduce(const float* part, int ppz, int nz, int v, double* dR1, cudaStream_t) {
+  const int nc = (v + 15) / 16, ncube = nc * nc * nc;
+  for (int z = 0; z < nz; ++z)
+    for (int a = 0; a < v; ++a) {
+      double s = 0.0;
+      for (int p = 0; p < ppz; ++p)
+        for (int cb = 0; cb < ncube; ++cb) {
+          const int t1 = (cb / nc) % nc, t2 = cb % nc;
+          const float* pp = part + ((i64)(z * ppz + p) * ncube + cb) * 32;
+          if (t2 == a / 16) s += pp[a % 16];
+          if (t1 == a / 16) s -= 0.5 * pp[16 + a % 16];
+        }
+      dR1[(i64)z * v + a] += s;
+    }
+}
+
 void launch_zero_cols(const CubeDst& d, i64 rows, int k0, int kind, cudaStream_t) {
   for (i64 r = 0; r < rows; ++r)
     for (int k = k0; k < d.Kpad; ++k) host_store_split(kind, d.out_hi, d.out_lo, r * d.Kpad + k, 0.f);

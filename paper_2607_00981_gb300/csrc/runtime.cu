@@ -190,6 +190,7 @@ struct GemmPlan {
   std::vector<rcc::CubePiece> h_cube;
   std::unique_ptr<DBuf> cube;
   int cube_mode = -1;
+  int cube_terms = 0;  // the largest nterm of the pieces
   const float* cube_src = nullptr;  // the pieces' source (default: the B operand's)
   // step (iii): the cube gather also forms the partial sums of the T3 term of R1
   // (per piece, the offset of v^{xy} in the FP32 copy of the oovv integrals)
@@ -251,6 +252,7 @@ struct rccsdt_ctx {
     int npack[2] = {0, 0}, ntile[2] = {0, 0};
     std::unique_ptr<DBuf> cubes[2], cube_dst;     // label-cube gathers from T3, modes 0 and 1
     int ncube[2] = {0, 0};
+    int cube_terms[2] = {0, 0};
     std::unique_ptr<DBuf> probs;
     int nprob = 0, ntiles = 0, grid = 0;
     double flop = 0.0;
@@ -468,6 +470,7 @@ GemmPlan* stack_rows(rccsdt_ctx* c, const std::vector<GemmPlan*>& parts, int* er
   g->h_cube = std::move(b0->h_cube);
   g->cube = std::move(b0->cube);
   g->cube_mode = b0->cube_mode;
+  g->cube_terms = b0->cube_terms;
   g->cube_src = b0->cube_src;
   g->r1_wbase = std::move(b0->r1_wbase);
   make_epi(c, g->E, bufs[0], p0->E.e.c_f32, M, N, rb, rs, ra, co, err);
@@ -691,11 +694,12 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
       const rcc::CubeDst d0{pb.out_hi, pb.out_lo, g->Kpad};
       const float* src = g->cube_src ? g->cube_src : (const float*)pb.src;
       if (g->r1_wbase)
-        rcc::launch_cube_pack_r1(kind, (const rcc::CubePiece*)g->cube->p, (int)g->h_cube.size(), d0, src, c->v,
+        rcc::launch_cube_pack_r1(kind, (const rcc::CubePiece*)g->cube->p, (int)g->h_cube.size(), g->cube_terms, d0,
+                                 src, c->v,
                                  c->B("oovv_f")->f(), (const i64*)g->r1_wbase->p, c->B("r1_part")->f(), c->stream);
       else
-        rcc::launch_cube_pack(g->cube_mode, kind, (const rcc::CubePiece*)g->cube->p, (int)g->h_cube.size(), nullptr,
-                              d0, src, c->v, c->stream);
+        rcc::launch_cube_pack(g->cube_mode, kind, (const rcc::CubePiece*)g->cube->p, (int)g->h_cube.size(),
+                              g->cube_terms, nullptr, d0, src, c->v, c->stream);
       if (g->cube_mode == 0) rcc::launch_zero_cols(d0, pb.R, g->K, kind, c->stream);
     } else {
       rcc::launch_pack(pb, c->stream);
@@ -814,6 +818,8 @@ rcc::CubePiece cube_piece(int k0, int nterm, int v = 0) {
 
 void set_cube(rccsdt_ctx* c, GemmPlan* g, int mode, std::vector<rcc::CubePiece> pieces, int* err) {
   g->cube_mode = mode;
+  g->cube_terms = 0;
+  for (const auto& pc : pieces) g->cube_terms = std::max(g->cube_terms, pc.nterm);
   g->h_cube = std::move(pieces);
   g->cube = upload_vec(c, g->h_cube, err);
 }
@@ -1041,7 +1047,7 @@ int build_context(rccsdt_ctx* c) {
       View Sz = dense(c->B("Sz")->p, {Zb, o, o, v, v, v}, t3f);  // S[z][x][y][e1][e2][e3]
       c->p_a3.emplace_back();
       auto& g = c->p_a3.back();
-      // (the R1 term runs in k_r1_t3 on the same S batch)
+      // (the T3 term of R1: k_r1_t3 on the unpacked batch, or the first panel's gather)
       View dX2z = sub(permuted(dX2, {1, 0, 2, 3}), 0, z0, Zb);  // dX2[y, z, a, b] over (z, y, a, b)
       GemmPlan* q1 = b.ct(g, "xc,zxycab->zyab", 0.5, sub(sub(ft, 0, O0, o), 1, V0, v), Sz, dX2z);
       // S panel [(y,e2,e3)][(z,x,e1)], shared by two contractions (and the first one when Zb = 1)
@@ -1050,11 +1056,38 @@ int build_context(rccsdt_ctx* c) {
       GemmPlan* q3 = b.ct(g, "zxde,zxyeba->ybad", -1.0, sub(eri("oovv"), 0, z0, Zb), Sz,
                           permuted(Wvvvo, {3, 1, 0, 2}), 1);
       if (q3) q3->reuse_B = 1;
-      // S panel [(z,y,e2)][(x,e3,e1)], shared by two contractions
+      // two contractions over (x, e3, e1), rows (z, y, e2)
       GemmPlan* q4 = b.ct(g, "bxcd,zxydac->zyab", 1.0, eri("vovv"), Sz, dX2z, 1);
       GemmPlan* q5 = b.ct(g, "lxde,zxyead->zyal", 1.0, eri("oovv"), Sz,
                           permuted(sub(permuted(Wvooo, {3, 0, 1, 2}), 0, z0, Zb), {0, 3, 1, 2}));
       if (q5) q5->reuse_B = 1;
+      // The last two contractions sum over (x, e3, e1): they read the first panel
+      // P1 [(z, y, e2, e3)][(x, e1)] (K padded to Kp1) as [(z, y, e2)][(e3, x, e1)],
+      // the same memory with K blocks of Kp1 per e3, so they need no panel of their
+      // own; their A operands are laid out with the same padded K.
+      if (q1 && q4 && q5) {
+        const int Kp1 = q1->Kpad, K45 = v * Kp1;
+        std::vector<double> cf((size_t)K45, 0.0);
+        std::vector<i64> cbase((size_t)K45, 0);
+        for (int e3 = 0; e3 < v; ++e3)
+          for (int x = 0; x < o; ++x)
+            for (int e1 = 0; e1 < v; ++e1) {
+              const size_t k = (size_t)e3 * Kp1 + (size_t)x * v + e1;
+              cf[k] = 1.0;
+              cbase[k] = (i64)x * V2 + (i64)e3 * v + e1;  // vovv[b][x][e3][e1], oovv[l][x][e3][e1]
+            }
+        std::vector<i64> rb(v), rl(o);
+        for (int bb = 0; bb < v; ++bb) rb[bb] = (i64)bb * o * V2;
+        for (int l = 0; l < o; ++l) rl[l] = (i64)l * o * V2;
+        make_pack(c, q4->A, c->D("vovv"), 0, v, K45, 1, cf, cbase, std::vector<int>((size_t)K45, 0), rb, 1, &err);
+        make_pack(c, q5->A, c->D("oovv"), 0, o, K45, 1, cf, cbase, std::vector<int>((size_t)K45, 0), rl, 1, &err);
+        for (GemmPlan* q : {q4, q5}) {
+          q->B = PackPlan();
+          q->B.a.R = q->E.e.N;
+          q->reuse_B = 1;  // the panel of q1
+          finish_plan(c, q, K45);
+        }
+      }
       if (t3f && q1 && q2 && q3 && q4 && q5) {
         // split bodies: the S panels straight from T3 through label cubes, one piece
         // per block S^{xy} = 2 U^{e1e2e3} - U^{e2e1e3} - U^{e3e2e1}, U = t_{x y z}
@@ -1070,8 +1103,8 @@ int build_context(rccsdt_ctx* c) {
             pc.t[t] = {u.blk * V3, coef[t],
                        packpos(u.pos[slot[t][lab[0]]], u.pos[slot[t][lab[1]]], u.pos[slot[t][lab[2]]])};
         };
-        const int l123[3] = {0, 1, 2}, l132[3] = {0, 2, 1};
-        std::vector<rcc::CubePiece> pa_, pb_, pc_;
+        const int l123[3] = {0, 1, 2};
+        std::vector<rcc::CubePiece> pa_, pb_;
         std::vector<i64> wb;
         for (int z = 0; z < Zb; ++z)
           for (int x = 0; x < o; ++x)
@@ -1082,25 +1115,16 @@ int build_context(rccsdt_ctx* c) {
               rcc::CubePiece p2 = cube_piece((z * o + x) * v, 3, v);  // rows (y, e2, e3), K (z, x, e1)
               p2.row0 = (i64)y * V2;
               spin(p2, x, y, z0 + z, l123);
-              rcc::CubePiece p4 = cube_piece(x * (int)V2, 3);  // rows (z, y, e2), K (x, e3, e1)
-              p4.ks1 = v;
-              p4.rs1 = 0;
-              p4.rs2 = 1;
-              p4.row0 = ((i64)z * o + y) * v;
-              spin(p4, x, y, z0 + z, l132);  // L0 = e1, L1 = e3, L2 = e2
               pa_.push_back(p1);
               pb_.push_back(p2);
-              pc_.push_back(p4);
               wb.push_back(((i64)x * o + y) * V2);  // v^{xy} in oovv [x][y][b][c]
             }
-        for (GemmPlan* q : {q1, q2, q3, q4, q5}) q->cube_src = c->B("t3")->f();
+        for (GemmPlan* q : {q1, q2, q3}) q->cube_src = c->B("t3")->f();
         set_cube(c, q1, 0, pa_, &err);
         q1->r1_wbase = upload_vec(c, wb, &err);
         ++c->a3_direct;
         set_cube(c, q2, 0, pb_, &err);
         set_cube(c, q3, 0, std::move(pb_), &err);
-        set_cube(c, q4, 0, pc_, &err);
-        set_cube(c, q5, 0, std::move(pc_), &err);
       }
       // one pass over each S panel: the contractions sharing it run as one GEMM with
       // stacked A operands.  (With Zb = 1 the first contraction's panel is the
@@ -1116,6 +1140,10 @@ int build_context(rccsdt_ctx* c) {
         };
         replace({q2, q3});
         replace({q4, q5});
+        // q1's panel must still be in place for the reshaped read: q1, (q4 q5), (q2 q3)
+        std::stable_partition(g.begin(), g.end(), [&](GemmPlan* p) {
+          return p == q1 || (!p->a_parts.empty() && p->a_parts[0] == q4) || p == q4 || p == q5;
+        });
       }
     }
   }
@@ -1617,6 +1645,8 @@ int build_grouped(rccsdt_ctx* c) {
       G.ptile[t] = upload_vec(c, ptile[t], &err);
     }
     G.ncube[t] = (int)cubes[t].size();
+    G.cube_terms[t] = 0;
+    for (const auto& pc : cubes[t]) G.cube_terms[t] = std::max(G.cube_terms[t], pc.nterm);
     if (G.ncube[t]) G.cubes[t] = upload_vec(c, cubes[t], &err);
   }
   if (!cdst.empty()) G.cube_dst = upload_vec(c, cdst, &err);
@@ -1757,7 +1787,7 @@ int run_grouped(rccsdt_ctx* c) {
                                t == 1, c->stream);
   for (int m = 0; m < 2; ++m)
     if (G.ncube[m])
-      rcc::launch_cube_pack(m, G.kind, (const rcc::CubePiece*)G.cubes[m]->p, G.ncube[m],
+      rcc::launch_cube_pack(m, G.kind, (const rcc::CubePiece*)G.cubes[m]->p, G.ncube[m], G.cube_terms[m],
                             (const rcc::CubeDst*)G.cube_dst->p, rcc::CubeDst{nullptr, nullptr, 0}, c->B("t3")->f(),
                             c->v, c->stream);
   if (c->opt.autotune && !G.tuned) {

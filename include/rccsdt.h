@@ -78,10 +78,18 @@ typedef struct {
   int autotune;              /* 1: time candidate launch shapes of the grouped GEMM on the
                                 first iteration and keep the fastest; 0: fixed shape;
                                 2 + i: always candidate i (0..5) of the autotuner's list */
+  int f64_tc;                /* FP64 contractions (FP64 contexts, and the final FP64
+                                iterations of split contexts): 0 on the FP64 units (DFMA);
+                                1 those of 3e7 FMA or more on the BF16 tensor cores, exact to
+                                about 2^-37 of the operands' row and column maxima (six 7-bit
+                                digit planes per operand, 21 digit products, exact FP32
+                                partial sums of the leading digit levels over K chunks of
+                                256, double-float and FP64 totals); 2 every contraction there */
 } rccsdt_options;
 
 /* Fills *opt with the defaults: FP64, DIIS(8) from iteration 2 including T3,
- * max_iter 100, tol 1e-8, grouped_bytes 8 GiB, unpack_bytes 1 GiB, autotune 0. */
+ * max_iter 100, tol 1e-8, grouped_bytes 8 GiB, unpack_bytes 1 GiB, autotune 0,
+ * f64_tc 0. */
 int rccsdt_options_default(rccsdt_options* opt);
 
 /* Creates a context for o occupied / v virtual orbitals and naux factors, on the

@@ -10,6 +10,8 @@ typedef long long i64;
 
 // Operand storage of packed GEMM panels.
 enum PanelKind : int { PANEL_F64 = 0, PANEL_BF16X2 = 1, PANEL_TF32X2 = 2 };
+// (FP64 bodies on the tensor cores keep the FP64 panel and add its BF16 digit planes,
+// kSlices x [rows][Kpad], with one scale exponent per row: see elem.cuh.)
 
 // A packed panel out[r][k] (row-major, k contiguous) is gathered as
 //   out[r][k] = sum_{t < nterm} coef[t*K + k] * src[colbase[t*K + k] + rowoff[sel[t*K + k]*R + r]]

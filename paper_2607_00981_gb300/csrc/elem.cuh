@@ -60,6 +60,44 @@ RCC_HD float f64_to_f32_rn(double x) {
   return out.f;
 }
 
+// FP64-accurate products on the BF16 tensor cores (the FP64 bodies' emulated GEMM):
+// a row of an operand is scaled by 2^-e (e: its largest magnitude is below 2^e) and
+// each element's magnitude, as a 42-bit fixed-point fraction N (round to nearest), is
+// cut into six 7-bit digits d_0..d_5 (d_0 <= 128, the others <= 127), stored
+// pre-scaled as a_s = sign * d_s * 2^(-7 s), which BF16 holds exactly:
+//   x = 2^(e - 7) * sum_s a_s   (up to 2^-42 of the row's largest magnitude).
+// Everything works on the binary64 bit patterns (subnormals count as zero).
+constexpr int kSlices = 6;
+RCC_HD unsigned long long f64_magnitude_bits(double x) {
+  union { double d; unsigned long long u; } c;
+  c.d = x;
+  return c.u & 0x7fffffffffffffffull;  // orders like |x| for finite values
+}
+RCC_HD int slice_exponent(unsigned long long max_bits) {
+  const int ex = (int)(max_bits >> 52);
+  return ex == 0 ? 0 : ex - 1022;  // |x| < 2^(ex - 1023 + 1)
+}
+RCC_HD void slice_digits(double x, int e, float (&a)[kSlices]) {
+  union { double d; unsigned long long u; } c;
+  c.d = x;
+  const int ex = (int)((c.u >> 52) & 0x7ff);
+  unsigned long long n = 0;
+  if (ex != 0) {
+    const unsigned long long m = (c.u & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = 1033 + e - ex;  // N = m 2^(ex - 1033 - e), and |x| < 2^e makes sh >= 11
+    if (sh < 64) n = (m + (1ull << (sh - 1))) >> sh;
+  }
+  const float sign = (c.u >> 63) ? -1.f : 1.f;
+  const float d[kSlices] = {(float)(n >> 35), (float)((n >> 28) & 127), (float)((n >> 21) & 127),
+                            (float)((n >> 14) & 127), (float)((n >> 7) & 127), (float)(n & 127)};
+  float scale = sign;
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s) {
+    a[s] = d[s] * scale;
+    scale *= 0.0078125f;  // 2^-7
+  }
+}
+
 // Stored-axis index of label q under ordering s (the six orderings, lexicographic).
 RCC_HD int perm3(int s, int q) {
   // {0,1,2} {0,2,1} {1,0,2} {1,2,0} {2,0,1} {2,1,0}

@@ -89,6 +89,24 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          su32(dst)),
+      "l"((uint64_t)map), "r"(su32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// K-major, 64-byte swizzle (rows of 32 BF16), 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;  // SWIZZLE_64B
+  return d;
+}
+
 // SM100 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (SBO), version 1; tiles are 1024-byte aligned (base offset 0).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -481,6 +499,285 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64-accurate GEMM on the BF16 tensor cores (FP64 bodies):
+//   C[m, n] (+)= alpha[m] * sum_k A[m, k] B[n, k],  A = 2^(e_m - 7) sum_s a_s, B likewise
+// with the digit planes of slice_digits (elem.cuh).  Of the 36 digit products the 21
+// with s + t <= 5 are summed on the tensor cores into four FP32 accumulators in TMEM,
+// by digit level d = s + t: d = 0, 1, 2 each in its own (values are multiples of
+// 2^-7d), d = 3..5 together.  Over a chunk of 256 K values the first three stay below
+// 2^24 units of their granularity (|d_s| <= 128, at most three products per level),
+// so they are exact however the tensor cores align and truncate partial sums; the
+// last is about 2^-21 of the first, so its truncation errors (measured: a few 2^-24
+// of it per chunk) stay near 2^-37 of the result.  (One accumulator for all levels
+// d >= 2 measured 2^-30.)  After each chunk the epilogue warps add the four to a
+// double-float (two FP32) running sum per element, and the tile ends with one FP64
+// step: C += alpha * 2^(e_m + f_n - 14) * (hi + lo).
+// This is the error-free splitting of matrix products (Ozaki, Ogita, Oishi, Rump,
+// Numer. Algorithms 59, 2012) with fixed 7-bit digits; the neglected digits and digit
+// products leave about 2^-38 of the row and column maxima times K.
+//
+// Persistent CTA per SM, 320 threads: warp 0 TMA (both operands' six planes of a
+// 128 x 32 tile in one 3D copy each, 64-byte swizzle, 2 stages of 96 KiB), warp 1
+// TMEM owner and MMA issuer, warps 2-9 epilogue (two per TMEM lane quadrant, 64
+// columns each).  All waits are bounded as in k_gemm_tc.
+// ---------------------------------------------------------------------------
+constexpr int EBN = 64;                          // tile width (two double-float sums of 32 columns per thread)
+constexpr int EKB = 32;                          // K per stage (64-byte rows)
+constexpr int E_APLANE = 128 * EKB * 2;          // one digit plane of a 128-row A tile: 8 KiB
+constexpr int E_BPLANE = EBN * EKB * 2;          // one digit plane of a 64-row B tile: 4 KiB
+constexpr int E_AOPER = kSlices * E_APLANE, E_BOPER = kSlices * E_BPLANE;
+constexpr int E_STAGE = E_AOPER + E_BOPER;       // 72 KiB
+constexpr int E_STAGES = 3;
+constexpr int E_CHUNK = 256 / EKB;               // stages per exact chunk
+constexpr int E_SMEM = E_STAGES * E_STAGE + 1024 + 256;
+constexpr int E_NACC = 4;                        // accumulators per buffer (digit levels 0, 1, 2, >= 3)
+constexpr int E_ACC = E_NACC * EBN;              // one buffer (two buffers in 512 columns)
+
+struct F64ESched {
+  CUtensorMap a, b;        // 3D maps {Kpad, rows, kSlices} of the digit planes
+  const int* ea;           // per-row scale exponents of A and B
+  const int* eb;
+  EpiArgs e;
+  int mt, nt, kstages;
+};
+
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {  // (hi, lo) += x, TwoSum
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_f64e(const __grid_constant__ F64ESched sch, int* __restrict__ status, long long budget) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + E_STAGES * E_STAGE);
+  uint64_t* empty = full + E_STAGES;
+  uint64_t* tfull = empty + E_STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < E_STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kEpiWarps);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int ntiles = sch.mt * sch.nt;
+  const int ks = sch.kstages;
+  const int nchunk = (ks + E_CHUNK - 1) / E_CHUNK;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int st = 0;
+      uint32_t ph = 0;
+      int issued[E_STAGES];
+      for (int q = 0; q < E_STAGES; ++q) issued[q] = -1;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        int tm, tn;
+        raster(sch.mt, sch.nt, tile, tm, tn);
+        for (int kb = 0; kb < ks; ++kb) {
+          if (!mbar_wait(&empty[st], ph ^ 1, budget, abort_flag)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sp = smem + st * E_STAGE;
+          mbar_expect_tx(&full[st], E_STAGE);
+          tma_load_3d(sp, &sch.a, &full[st], kb * EKB, tm * BM, 0);
+          tma_load_3d(sp + E_AOPER, &sch.b, &full[st], kb * EKB, tn * EBN, 0);
+          issued[st] = (int)ph;
+          if (++st == E_STAGES) {
+            st = 0;
+            ph ^= 1;
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(status, 1);
+        for (int q = 0; q < E_STAGES; ++q) {
+          if (issued[q] < 0) continue;
+          const long long t0 = clock64();
+          while (!mbar_try(&full[q], (uint32_t)issued[q]) && clock64() - t0 < budget) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int st = 0;
+      uint32_t ph = 0;
+      int chunk = 0;  // chunks issued by this CTA; buffer chunk & 1
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        for (int c = 0; c < nchunk && ok; ++c, ++chunk) {
+          const int b = chunk & 1;
+          if (!mbar_wait(&tempty[b], (uint32_t)((chunk >> 1) & 1) ^ 1u, budget, abort_flag)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t d0 = tmem + (uint32_t)(b * E_ACC);
+          bool first[E_NACC] = {true, true, true, true};
+          const int kb1 = min(ks, (c + 1) * E_CHUNK);
+          for (int kb = c * E_CHUNK; kb < kb1; ++kb) {
+            if (!mbar_wait(&full[st], ph, budget, abort_flag)) {
+              ok = false;
+              break;
+            }
+            fence_after();
+            const uint32_t base = su32(smem + st * E_STAGE);
+#pragma unroll
+            for (int sa = 0; sa < kSlices; ++sa) {
+#pragma unroll
+              for (int sb = 0; sb < kSlices - sa; ++sb) {
+                const int acc = sa + sb < 3 ? sa + sb : 3;
+                const uint64_t da = sdesc64(base + sa * E_APLANE), db = sdesc64(base + E_AOPER + sb * E_BPLANE);
+#pragma unroll
+                for (int j = 0; j < EKB / 16; ++j) {
+                  const uint64_t adv = (uint64_t)(j * 32 >> 4);
+                  umma<1, EBN>(d0 + (uint32_t)(acc * EBN), da + adv, db + adv, first[acc] ? 0u : 1u);
+                  first[acc] = false;
+                }
+              }
+            }
+            umma_commit(&empty[st]);
+            if (++st == E_STAGES) {
+              st = 0;
+              ph ^= 1;
+            }
+          }
+          if (!ok) break;
+          umma_commit(&tfull[b]);
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(status, 1);
+      }
+      umma_commit(drain);
+      const long long t0 = clock64();
+      while (!mbar_try(drain, 0) && clock64() - t0 < budget) {
+      }
+    }
+  } else {
+    const int q = warp & 3, h = (warp - 2) >> 2;  // lane quadrant, column half
+    const int row = q * 32 + lane;
+    int chunk = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      int tm, tn;
+      raster(sch.mt, sch.nt, tile, tm, tn);
+      float shi[32], slo[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) shi[j] = slo[j] = 0.f;
+      for (int c = 0; c < nchunk; ++c, ++chunk) {
+        const int b = chunk & 1;
+        if (!mbar_wait(&tfull[b], (uint32_t)((chunk >> 1) & 1), budget, abort_flag)) {
+          *abort_flag = 1;
+          atomicExch(status, 1);
+          ok = false;
+          break;
+        }
+        fence_after();
+#pragma unroll
+        for (int acc = 0; acc < E_NACC; ++acc) {
+          uint32_t r[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * E_ACC + acc * EBN + h * 32), r);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) df_add(shi[j], slo[j], __uint_as_float(r[j]));
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
+      }
+      if (!ok) break;
+      // finish the tile in FP64: C += alpha * 2^(e_m + f_n - 14) * (hi + lo)
+      const EpiArgs& e = sch.e;
+      const int m = tm * BM + row;
+      if (m < e.M) {
+        const i64 rb = e.row_base[m];
+        const i64* co = e.col_off + (i64)e.row_sel[m] * e.N;
+        const double al = e.row_alpha[m];
+        const int em = sch.ea[m];
+        double* C = (double*)epi_out(e, m);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = tn * EBN + h * 32 + j;
+          if (n < e.N) {
+            const int sc = em + __ldg(sch.eb + n) - 14;
+            const double pw = __longlong_as_double((long long)(sc + 1023) << 52);  // |sc| < 1000 for finite data
+            const double val = ((double)shi[j] + (double)slo[j]) * pw;
+            const i64 ad = rb + __ldg(co + n);
+            C[ad] += al * val;
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// Digit planes of an FP64 panel: one CTA per row (grid-strided), the row's scale
+// exponent from an integer max over the magnitudes' bit patterns, then the digits.
+__global__ void __launch_bounds__(256) k_slice_f64(const double* __restrict__ P, int R, int Kpad,
+                                                   __nv_bfloat16* __restrict__ planes, int* __restrict__ exps) {
+  __shared__ unsigned long long red[8];
+  const i64 plane = (i64)R * Kpad;
+  for (int r = blockIdx.x; r < R; r += gridDim.x) {
+    const double* row = P + (i64)r * Kpad;
+    unsigned long long mx = 0;
+    for (int k = threadIdx.x; k < Kpad; k += blockDim.x) mx = max(mx, f64_magnitude_bits(row[k]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      unsigned long long v = threadIdx.x < 8 ? red[threadIdx.x] : 0ull;
+#pragma unroll
+      for (int off = 4; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, off));
+      if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    const int ex = slice_exponent(red[0]);
+    if (threadIdx.x == 0) exps[r] = ex;
+    for (int k = threadIdx.x; k < Kpad; k += blockDim.x) {
+      float a[kSlices];
+      slice_digits(row[k], ex, a);
+#pragma unroll
+      for (int s = 0; s < kSlices; ++s) planes[s * plane + (i64)r * Kpad + k] = __float2bfloat16_rn(a[s]);
+    }
+    __syncthreads();  // red[] is reused by the next row
+  }
+}
+
 __global__ void k_splitk_reduce_f32(const float* __restrict__ partial, int splitk, EpiArgs e) {
   const i64 MN = (i64)e.M * e.N;
   for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < MN; x += (i64)gridDim.x * blockDim.x) {
@@ -636,6 +933,46 @@ int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total
   const int g = std::max(1, std::min(grid > 0 ? grid : num_sms(), total_tiles));
   const long long budget = watchdog > 0 ? watchdog : 4000000000LL;
   launch_any(kind, (bn == 128 || bn == 144) ? bn : 256, sch, g, status_flag, budget, s);
+  return 0;
+}
+
+bool make_map_planes(CUtensorMap* map, const void* planes, int rows, int Kpad, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows, (cuuint64_t)kSlices};
+  cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)rows * Kpad * 2};
+  cuuint32_t box[3] = {(cuuint32_t)EKB, (cuuint32_t)box_rows, (cuuint32_t)kSlices};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(planes), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void launch_slice_f64(const double* P, int R, int Kpad, void* planes, int* exps, cudaStream_t s) {
+  if (R <= 0) return;
+  ++g_launch_count;
+  k_slice_f64<<<(unsigned)std::min(R, 152 * 16), 256, 0, s>>>(P, R, Kpad, (__nv_bfloat16*)planes, exps);
+}
+
+int launch_gemm_f64e(const void* Aplanes, const int* ea, const void* Bplanes, const int* eb, int Kpad, const EpiArgs& e,
+                     int* status_flag, long long watchdog, cudaStream_t s) {
+  if (Kpad % 64 != 0 || e.M <= 0 || e.N <= 0 || e.c_f32) return 1;
+  F64ESched sch;
+  if (!make_map_planes(&sch.a, Aplanes, e.M, Kpad, BM) || !make_map_planes(&sch.b, Bplanes, e.N, Kpad, EBN)) return 2;
+  sch.ea = ea;
+  sch.eb = eb;
+  sch.e = e;
+  sch.mt = (e.M + BM - 1) / BM;
+  sch.nt = (e.N + EBN - 1) / EBN;
+  sch.kstages = Kpad / EKB;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_f64e, cudaFuncAttributeMaxDynamicSharedMemorySize, E_SMEM);
+    attr = true;
+  }
+  const int grid = std::min(sch.mt * sch.nt, num_sms());
+  ++g_launch_count;
+  k_gemm_f64e<<<grid, kThreads, E_SMEM, s>>>(sch, status_flag, watchdog > 0 ? watchdog : 4000000000LL);
   return 0;
 }
 

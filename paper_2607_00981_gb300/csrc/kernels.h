@@ -105,6 +105,14 @@ int gproblem_tiles(const GProblem& p);
 int gemm_tc_block_k(int kind);
 // One persistent launch over every tile of the nprob problems (device table,
 // tile0 prefix order, tables made with the same bn); grid <= 0 picks one CTA per SM.
+// FP64-accurate GEMM on the BF16 tensor cores (digit planes, see elem.cuh):
+// launch_slice_f64 cuts an FP64 panel [R][Kpad] into kSlices BF16 planes
+// [kSlices][R][Kpad] and one scale exponent per row; launch_gemm_f64e then applies
+// the FP64 table epilogue e (c_f32 = 0) to the product of two such panels.
+// Kpad a multiple of 64.  Returns nonzero for an unsupported configuration.
+void launch_slice_f64(const double* P, int R, int Kpad, void* planes, int* exps, cudaStream_t s);
+int launch_gemm_f64e(const void* Aplanes, const int* ea, const void* Bplanes, const int* eb, int Kpad, const EpiArgs& e,
+                     int* status_flag, long long watchdog, cudaStream_t s);
 int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total_tiles, int grid, int bn,
                            int* status_flag, long long watchdog, cudaStream_t s);
 // Operand panels read from compact T3 through label cubes (cube_pack.cu).

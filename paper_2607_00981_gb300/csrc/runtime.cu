@@ -225,7 +225,14 @@ struct rccsdt_ctx {
   // panels (engine scratch)
   std::unique_ptr<DBuf> panelA_hi, panelA_lo, panelB_hi, panelB_lo;
   size_t panel_bytes = 0;
+  int panel_rows = 0;  // the most rows of any operand panel
   int packedA_kind = -1, packedB_kind = -1;  // panel kinds last written (reuse needs a match)
+  // FP64 contractions on the tensor cores: digit planes and row exponents of the
+  // FP64 panels (which stay in panelA_hi / panelB_hi)
+  std::unique_ptr<DBuf> planesA, planesB, expA, expB;
+  // the planes hold the current FP64 panels cut into rows of this many K values
+  // (0: stale; a reused panel read with another row length is cut again)
+  int slicedA = 0, slicedB = 0;
 
   // plan groups
   std::vector<GemmPlan*> p_dress, p_fock, p_eri, p_int, p_r12, p_energy_bare;
@@ -381,6 +388,7 @@ void finish_plan(rccsdt_ctx* c, GemmPlan* g, int K) {
   g->fma = (double)g->E.e.M * g->E.e.N * K;
   size_t need = (size_t)std::max(g->A.a.R, g->B.a.R) * g->Kpad * 8;
   if (need > c->panel_bytes) c->panel_bytes = need;
+  c->panel_rows = std::max(c->panel_rows, std::max(g->A.a.R, g->B.a.R));
 }
 
 // The allocation holding p (start pointer and element offset of p in it).
@@ -675,7 +683,12 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   pa.out_lo = c->panelA_lo ? c->panelA_lo->p : nullptr;
   pb.out_hi = c->panelB_hi->p;
   pb.out_lo = c->panelB_lo ? c->panelB_lo->p : nullptr;
-  if (!g->a_parts.empty()) {
+  // FP64 contractions on the tensor cores (option f64_tc): the large ones only
+  const bool f64e = !tc && c->opt.f64_tc && c->planesA && (c->opt.f64_tc == 2 || g->fma >= 3e7) && !g->f64_only;
+  const bool packA = !g->a_parts.empty() || !g->reuse_A || c->packedA_kind != kind;
+  const bool packB = !g->reuse_B || c->packedB_kind != kind;
+  if (!packA) {
+  } else if (!g->a_parts.empty()) {
     const size_t esz = kind == rcc::PANEL_F64 ? 8 : (kind == rcc::PANEL_BF16X2 ? 2 : 4);
     size_t r0 = 0;
     for (GemmPlan* q : g->a_parts) {
@@ -686,10 +699,12 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
       rcc::launch_pack(pq, c->stream);
       r0 += (size_t)pq.R;
     }
-  } else if (!g->reuse_A || c->packedA_kind != kind) {
+  } else {
     rcc::launch_pack(pa, c->stream);
   }
-  if (!g->reuse_B || c->packedB_kind != kind) {
+  if (packA) c->slicedA = 0;
+  if (packB) c->slicedB = 0;
+  if (packB) {
     if (tc && g->cube) {
       const rcc::CubeDst d0{pb.out_hi, pb.out_lo, g->Kpad};
       const float* src = g->cube_src ? g->cube_src : (const float*)pb.src;
@@ -707,7 +722,17 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   }
   c->packedA_kind = c->packedB_kind = kind;
   const int tidx = g->step == 1 ? timer_begin(c, 16, 2.0 * g->fma) : -1;
-  if (!tc) {
+  if (f64e) {
+    if (c->slicedA != g->Kpad)
+      rcc::launch_slice_f64((const double*)pa.out_hi, g->E.e.M, g->Kpad, c->planesA->p, (int*)c->expA->p, c->stream);
+    if (c->slicedB != g->Kpad)
+      rcc::launch_slice_f64((const double*)pb.out_hi, g->E.e.N, g->Kpad, c->planesB->p, (int*)c->expB->p, c->stream);
+    c->slicedA = c->slicedB = g->Kpad;
+    int* flag = (int*)((double*)c->scalars->p + 1000);
+    if (rcc::launch_gemm_f64e(c->planesA->p, (const int*)c->expA->p, c->planesB->p, (const int*)c->expB->p, g->Kpad,
+                              g->E.e, flag, c->opt.watchdog_cycles, c->stream))
+      return fail(c, RCCSDT_ERR_ARG, "tensor-core FP64 GEMM configuration unsupported");
+  } else if (!tc) {
     rcc::launch_gemm_f64((const double*)pa.out_hi, (const double*)pb.out_hi, round_up(g->K, 16), g->Kpad, g->Kpad,
                          g->E.e, c->concurrent ? nullptr : c->splitk->d(), (i64)(c->splitk->bytes / 8), c->stream);
   } else {
@@ -2092,6 +2117,7 @@ RCC_API int rccsdt_options_default(rccsdt_options* opt) {
   opt->grouped_bytes = 8LL << 30;
   opt->unpack_bytes = 1LL << 30;
   opt->autotune = 0;
+  opt->f64_tc = 0;
   return RCCSDT_OK;
 }
 
@@ -2102,7 +2128,9 @@ RCC_API int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, voi
   rccsdt_options def;
   rccsdt_options_default(&def);
   const rccsdt_options& op = opt ? *opt : def;
-  if (op.precision < 0 || op.precision > 2 || op.diis_space < 0 || op.diis_space > 16) return RCCSDT_ERR_ARG;
+  if (op.precision < 0 || op.precision > 2 || op.diis_space < 0 || op.diis_space > 16 || op.f64_tc < 0 ||
+      op.f64_tc > 2)
+    return RCCSDT_ERR_ARG;
   auto* c = new rccsdt_ctx();
   c->o = o; c->v = v; c->n = o + v; c->naux = naux;
   c->n3 = n3_of(o);
@@ -2124,6 +2152,20 @@ RCC_API int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, voi
     c->panelB_hi = std::make_unique<DBuf>();
     c->panelA_hi->p = dev_alloc(c->panel_bytes, &err);
     c->panelB_hi->p = dev_alloc(c->panel_bytes, &err);
+    if (op.f64_tc) {  // digit planes (kSlices BF16 per FP64 panel element) and row exponents
+      const size_t pb = c->panel_bytes / 8 * rcc::kSlices * 2;
+      for (auto* q : {&c->planesA, &c->planesB}) {
+        *q = std::make_unique<DBuf>();
+        (*q)->p = dev_alloc(pb, &err);
+        (*q)->bytes = pb;
+        c->total_bytes += pb;
+      }
+      for (auto* q : {&c->expA, &c->expB}) {
+        *q = std::make_unique<DBuf>();
+        (*q)->p = dev_alloc((size_t)c->panel_rows * 4 + 16, &err);
+        (*q)->bytes = (size_t)c->panel_rows * 4 + 16;
+      }
+    }
     c->total_bytes += 2 * c->panel_bytes;
     if (op.precision != RCCSDT_FP64) {
       c->panelA_lo = std::make_unique<DBuf>();

@@ -167,6 +167,42 @@ void launch_r1_cubes_reduce(const float* part, int ppz, int nz, int v, double* d
     }
 }
 
+void launch_slice_f64(const double* P, int R, int Kpad, void* planes, int* exps, cudaStream_t) {
+  __nv_bfloat16* pl = (__nv_bfloat16*)planes;
+  const i64 plane = (i64)R * Kpad;
+  for (int r = 0; r < R; ++r) {
+    unsigned long long mx = 0;
+    for (int k = 0; k < Kpad; ++k) mx = std::max(mx, f64_magnitude_bits(P[(i64)r * Kpad + k]));
+    exps[r] = slice_exponent(mx);
+    for (int k = 0; k < Kpad; ++k) {
+      float a[kSlices];
+      slice_digits(P[(i64)r * Kpad + k], exps[r], a);
+      for (int s = 0; s < kSlices; ++s) pl[s * plane + (i64)r * Kpad + k] = __float2bfloat16_rn(a[s]);
+    }
+  }
+}
+
+// The digit products with s + t <= 5, summed in FP64 (the device sums them exactly,
+// up to the FP32 rounding of the smallest ones).
+int launch_gemm_f64e(const void* Aplanes, const int* ea, const void* Bplanes, const int* eb, int Kpad, const EpiArgs& e,
+                     int*, long long, cudaStream_t) {
+  if (Kpad % 64 != 0 || e.c_f32) return 1;
+  const __nv_bfloat16* A = (const __nv_bfloat16*)Aplanes;
+  const __nv_bfloat16* B = (const __nv_bfloat16*)Bplanes;
+  const i64 pa = (i64)e.M * Kpad, pb = (i64)e.N * Kpad;
+  for (int m = 0; m < e.M; ++m)
+    for (int n = 0; n < e.N; ++n) {
+      double s = 0.0;
+      for (int k = 0; k < Kpad; ++k)
+        for (int sa = 0; sa < kSlices; ++sa)
+          for (int sb = 0; sb + sa < kSlices; ++sb)
+            s += (double)__bfloat162float(A[sa * pa + (i64)m * Kpad + k]) *
+                 (double)__bfloat162float(B[sb * pb + (i64)n * Kpad + k]);
+      epi_apply(e, m, n, std::ldexp(s, ea[m] + eb[n] - 14));
+    }
+  return 0;
+}
+
 void launch_zero_cols(const CubeDst& d, i64 rows, int k0, int kind, cudaStream_t) {
   for (i64 r = 0; r < rows; ++r)
     for (int k = k0; k < d.Kpad; ++k) host_store_split(kind, d.out_hi, d.out_lo, r * d.Kpad + k, 0.f);

@@ -87,6 +87,30 @@ def test_intermediates_match_oracle(kind):
 
 
 @pytest.mark.parametrize("kind", BACKENDS)
+@pytest.mark.parametrize("o,v,naux", [(3, 12, 40), (4, 5, 12), (2, 21, 12), (5, 9, 20)])
+def test_residual_f64_on_tensor_cores_matches_oracle(kind, o, v, naux):
+    """FP64 contractions on the BF16 tensor cores (six digit planes per operand,
+    exact chunk sums): every residual element within 1e-10 of the oracle's, relative
+    to the largest, and the same intermediates."""
+    inst = make_instance(o, v, naux, seed=o * 13 + v)
+    t1, t2, t3 = random_amplitudes(o, v, seed=v * 3 + o)
+    t3c = oc.pack(t3)
+    ctx = _ctx(kind, o, v, naux, f64_tc=2)
+    ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    ctx.set_amplitudes(t1, t2, t3c)
+    ctx.build_intermediates()
+    ctx.residual()
+    ctx.postprocess()
+    r1, r2, r3 = ctx.residuals()
+    R1, R2, R3 = oc.residuals_compact(inst.L, inst.fock_diag, t1, t2, t3c)
+    scale = max(1.0, np.abs(R3).max())
+    assert np.abs(r1 - R1).max() / scale < 1e-10
+    assert np.abs(r2 - R2).max() / scale < 1e-10
+    assert np.abs(oc.postprocess(r3, o) - oc.postprocess(R3, o)).max() / scale < 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind", BACKENDS)
 def test_trajectory_matches_oracle_on_the_o3v12_workload(kind):
     """Six Jacobi+DIIS iterations of the o=3, v=12 workload from the MP2 guess:
     energies and residual norms agree iteration by iteration."""

@@ -5,8 +5,18 @@
 Prints the energy and residual norms of each iteration (the device work is
 exactly one ``rccsdt_iterate`` per iteration after ``set_hamiltonian`` and the
 MP2 guess), which makes it a small, fixed launch sequence for profilers.
+
+    python -m paper_2607_00981_gb300 --workload o12v120w --solve --tol 1e-8 --precision bf16x3 --f64-tc 1
+
+runs rccsdt_solve instead (split contexts switch to FP64 contractions at
+|R| <= sqrt(tol)) and prints one JSON line: energy, iterations, norm, status, time.
+With --refine-fp64 the converged amplitudes then seed an FP64 context (FP64
+storage, FP64 DIIS of --refine-diis vectors, contractions per --f64-tc) iterated to
+--tol again; its energy is the FP64 reference the split energy is compared with
+(converged energies do not depend on the path).
 """
 import argparse
+import json
 import sys
 import time
 
@@ -21,15 +31,49 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp64", choices=["fp64", "bf16x3", "tf32x3"])
     ap.add_argument("--scale", type=float, default=None, help="override the factor entry scale")
     ap.add_argument("--no-diis-t3", action="store_true", help="DIIS on T1 and T2 only")
+    ap.add_argument("--f64-tc", type=int, default=0, choices=[0, 1, 2],
+                    help="FP64 contractions on the tensor cores (option f64_tc)")
+    ap.add_argument("--solve", action="store_true", help="iterate to --tol with rccsdt_solve")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--max-iter", type=int, default=200)
+    ap.add_argument("--diis-space", type=int, default=8)
+    ap.add_argument("--refine-fp64", action="store_true", help="re-converge in an FP64 context afterwards")
+    ap.add_argument("--refine-diis", type=int, default=2)
     args = ap.parse_args(argv)
     spec = dict(WORKLOADS.get(args.workload) or CONVERGENCE[args.workload])
     if args.scale is not None:
         spec["scale"] = args.scale
     inst = make_instance(**spec)
     prec = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}[args.precision]
-    ctx = pkg.context(inst.o, inst.v, inst.naux, precision=prec, diis_t3=0 if args.no_diis_t3 else 1)
+    ctx = pkg.context(inst.o, inst.v, inst.naux, precision=prec, diis_t3=0 if args.no_diis_t3 else 1,
+                      f64_tc=args.f64_tc, tol=args.tol, max_iter=args.max_iter, diis_space=args.diis_space)
     ctx.set_hamiltonian(inst.fock_diag, inst.L)
     ctx.init_mp2()
+    if args.solve:
+        t0 = time.perf_counter()
+        e, iters, norm, conv = ctx.solve()
+        out = {"workload": args.workload, "precision": args.precision, "f64_tc": args.f64_tc, "tol": args.tol,
+               "diis_space": args.diis_space, "energy": e, "iterations": iters, "norm": norm, "converged": conv,
+               "seconds": time.perf_counter() - t0}
+        print(json.dumps(out), flush=True)
+        if args.refine_fp64 and conv:
+            t1, t2, t3 = ctx.amplitudes()
+            ctx.close()
+            ref = pkg.context(inst.o, inst.v, inst.naux, precision=0, diis_t3=1, diis_space=args.refine_diis,
+                              f64_tc=args.f64_tc, tol=args.tol, max_iter=args.max_iter)
+            ref.set_hamiltonian(inst.fock_diag, inst.L)
+            ref.set_amplitudes(t1, t2, t3)
+            del t1, t2, t3
+            t0 = time.perf_counter()
+            e64, it64, n64, c64 = ref.solve()
+            print(json.dumps({"workload": args.workload, "reference": "fp64 storage", "f64_tc": args.f64_tc,
+                              "energy": e64, "iterations": it64, "norm": n64, "converged": c64,
+                              "seconds": time.perf_counter() - t0, "abs_energy_difference": abs(e64 - e)}),
+                  flush=True)
+            ref.close()
+            return 0
+        ctx.close()
+        return 0
     for it in range(args.iters):
         t0 = time.perf_counter()
         e, n = ctx.iterate()

@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const i64* co = e.col_off + (i64)e.row_sel[m] * e.N;
         const double al = e.row_alpha[m];
         const int em = sch.ea[m];
-        double* C = (double*)epi_out(e, m);
+        void* C = epi_out(e, m);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int n = tn * EBN + h * 32 + j;
@@ -731,7 +731,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const double pw = __longlong_as_double((long long)(sc + 1023) << 52);  // |sc| < 1000 for finite data
             const double val = ((double)shi[j] + (double)slo[j]) * pw;
             const i64 ad = rb + __ldg(co + n);
-            C[ad] += al * val;
+            if (e.c_f32)  // FP32 storage (R3 of split contexts)
+              ((float*)C)[ad] = (float)((double)((float*)C)[ad] + al * val);
+            else
+              ((double*)C)[ad] += al * val;
           }
         }
       }
@@ -956,7 +959,7 @@ void launch_slice_f64(const double* P, int R, int Kpad, void* planes, int* exps,
 
 int launch_gemm_f64e(const void* Aplanes, const int* ea, const void* Bplanes, const int* eb, int Kpad, const EpiArgs& e,
                      int* status_flag, long long watchdog, cudaStream_t s) {
-  if (Kpad % 64 != 0 || e.M <= 0 || e.N <= 0 || e.c_f32) return 1;
+  if (Kpad % 64 != 0 || e.M <= 0 || e.N <= 0) return 1;
   F64ESched sch;
   if (!make_map_planes(&sch.a, Aplanes, e.M, Kpad, BM) || !make_map_planes(&sch.b, Bplanes, e.N, Kpad, EBN)) return 2;
   sch.ea = ea;

@@ -108,7 +108,7 @@ int gemm_tc_block_k(int kind);
 // FP64-accurate GEMM on the BF16 tensor cores (digit planes, see elem.cuh):
 // launch_slice_f64 cuts an FP64 panel [R][Kpad] into kSlices BF16 planes
 // [kSlices][R][Kpad] and one scale exponent per row; launch_gemm_f64e then applies
-// the FP64 table epilogue e (c_f32 = 0) to the product of two such panels.
+// the table epilogue e (FP64 or FP32 outputs, FP64 arithmetic) to the product of two such panels.
 // Kpad a multiple of 64.  Returns nonzero for an unsupported configuration.
 void launch_slice_f64(const double* P, int R, int Kpad, void* planes, int* exps, cudaStream_t s);
 int launch_gemm_f64e(const void* Aplanes, const int* ea, const void* Bplanes, const int* eb, int Kpad, const EpiArgs& e,

@@ -186,7 +186,7 @@ void launch_slice_f64(const double* P, int R, int Kpad, void* planes, int* exps,
 // up to the FP32 rounding of the smallest ones).
 int launch_gemm_f64e(const void* Aplanes, const int* ea, const void* Bplanes, const int* eb, int Kpad, const EpiArgs& e,
                      int*, long long, cudaStream_t) {
-  if (Kpad % 64 != 0 || e.c_f32) return 1;
+  if (Kpad % 64 != 0) return 1;
   const __nv_bfloat16* A = (const __nv_bfloat16*)Aplanes;
   const __nv_bfloat16* B = (const __nv_bfloat16*)Bplanes;
   const i64 pa = (i64)e.M * Kpad, pb = (i64)e.N * Kpad;

@@ -109,6 +109,25 @@ def test_batch_split_precision(kind, prec):
 
 
 @pytest.mark.parametrize("kind", BACKENDS)
+def test_batch_split_with_tensor_core_fp64_phase(kind):
+    """Split batches whose final FP64 iterations run their contractions on the tensor
+    cores (option f64_tc): every instance converges, energies within 1e-6 Eh of the
+    oracle, and each equals its single-context solve."""
+    lib = _lib(kind)
+    insts = _instances()[:3]
+    opt = dict(tol=1e-8, max_iter=200, precision=B.SPLIT_BF16X3, f64_tc=2)
+    b = _batch(lib, insts, **opt)
+    e, it, nrm, st = b.solve()
+    assert (st == B.OK).all(), st
+    for q, inst in enumerate(insts):
+        (e1, it1, n1, conv), _ = _single(lib, inst, **opt)
+        assert it[q] == it1 and abs(e[q] - e1) < 1e-9, (q, it[q], it1, e[q], e1)
+        E0 = oc.solve_compact(inst.L, inst.fock_diag, inst.o, tol=1e-10, max_iter=300)[0]
+        assert abs(e[q] - E0) < 1e-6
+    b.close()
+
+
+@pytest.mark.parametrize("kind", BACKENDS)
 def test_batch_max_iter_stops_one_instance(kind):
     """An instance that needs more than max_iter evaluations stops with
     NOT_CONVERGED while the others still converge."""

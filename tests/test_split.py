@@ -75,14 +75,16 @@ def test_split_step_iii_one_z_at_a_time(kind, o, v, naux):
 
 @pytest.mark.parametrize("kind", BACKENDS)
 @pytest.mark.parametrize("prec", [B.SPLIT_BF16X3, B.SPLIT_TF32X3], ids=["bf16x3", "tf32x3"])
-def test_split_solve_refines_to_fp64_energy(kind, prec):
-    """Split iterations, then FP64 refinement: converged energy within 1e-6 Eh
-    (the target) of the FP64 oracle's, at a weakly coupled o=3, v=8 instance."""
+@pytest.mark.parametrize("f64_tc", [0, 2], ids=["fp64-units", "fp64-tensor-cores"])
+def test_split_solve_refines_to_fp64_energy(kind, prec, f64_tc):
+    """Split iterations, then FP64 refinement (on the FP64 units, or on the tensor
+    cores through digit planes): converged energy within 1e-6 Eh (the target) of the
+    FP64 oracle's, at a weakly coupled o=3, v=8 instance."""
     lib = gpu_lib() if kind == "gpu" else hostsim_lib()
     o, v, naux = 3, 8, 20
     inst = make_instance(o, v, naux, seed=11, scale=0.2)
     E0 = oc.solve_compact(inst.L, inst.fock_diag, o, tol=1e-10, max_iter=300)[0]
-    ctx = B.Context(lib, o, v, naux, precision=prec, tol=1e-8, max_iter=300)
+    ctx = B.Context(lib, o, v, naux, precision=prec, tol=1e-8, max_iter=300, f64_tc=f64_tc)
     ctx.set_hamiltonian(inst.fock_diag, inst.L)
     ctx.init_mp2()
     E, it, nrm, conv = ctx.solve()

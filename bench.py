@@ -167,13 +167,14 @@ def config(args, inst):
 
 
 def compare_fp64_split(pkg, stream, dev, name="o8v80w", warm=2, steps=2):
-    """FP64, 3xBF16 and 3xTF32 s/iteration on the same o8v80 shapes (same MP2 start)."""
+    """FP64 (contractions on the FP64 units, and on the tensor cores through digit
+    planes), 3xBF16 and 3xTF32 s/iteration on the same o8v80 shapes (same MP2 start)."""
     import torch
     from paper_2607_00981_gb300.synth import workload
     inst = workload(name)
     out = {"workload": name}
-    for label, prec in (("fp64", 0), ("bf16x3", 1), ("tf32x3", 2)):
-        ctx = pkg.context(inst.o, inst.v, inst.naux, stream=stream.cuda_stream, precision=prec)
+    for label, prec, f64_tc in (("fp64", 0, 0), ("fp64_tc", 0, 1), ("bf16x3", 1, 0), ("tf32x3", 2, 0)):
+        ctx = pkg.context(inst.o, inst.v, inst.naux, stream=stream.cuda_stream, precision=prec, f64_tc=f64_tc)
         ctx.set_hamiltonian(inst.fock_diag, inst.L)
         ctx.init_mp2()
         for _ in range(warm):
@@ -190,10 +191,38 @@ def compare_fp64_split(pkg, stream, dev, name="o8v80w", warm=2, steps=2):
     out["unit"] = "s/iteration"
     out["speedup_bf16x3"] = out["fp64"] / out["bf16x3"]
     out["speedup_tf32x3"] = out["fp64"] / out["tf32x3"]
+    out["speedup_fp64_tc"] = out["fp64"] / out["fp64_tc"]
+    out["speedup_bf16x3_vs_fp64_tc"] = out["fp64_tc"] / out["bf16x3"]
     return out
 
 
-def batch_solve(pkg, insts, prec, autotune, max_iter=100, tol=1e-8, host=False):
+def fp64_tc_iteration(pkg, stream, inst, fp64_rate):
+    """One FP64 iteration (FP64 storage, contractions on the tensor cores through
+    digit planes, no DIIS history) at the benchmark workload, timed after one warm-up
+    iteration; the DFMA path's time is estimated from its measured rate at o8v80w
+    (one of its iterations here would take about ten minutes)."""
+    import torch
+    ctx = pkg.context(inst.o, inst.v, inst.naux, stream=stream.cuda_stream, precision=0, f64_tc=1, diis_space=0)
+    ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    ctx.init_mp2()
+    ctx.iterate()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.iterate()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    flop = 2.0 * ctx.lib.rccsdt_iteration_fma(inst.o, inst.v)
+    ctx.close()
+    out = {"fp64_tc_s_per_iteration": t, "fp64_tc_tflops": flop / t / 1e12}
+    if fp64_rate:
+        out["fp64_dfma_s_per_iteration_estimated"] = flop / fp64_rate
+        out["note"] = "DFMA estimate = algorithmic flop / the DFMA path's measured flop rate at o8v80w"
+    return out
+
+
+def batch_solve(pkg, insts, prec, autotune, max_iter=100, tol=1e-8, host=False, f64_tc=1):
     """One rccsdt_batch_solve of the uneven-instance workload from the MP2 guess.
 
     host=True feeds every instance's Hamiltonian from pinned host memory inside the
@@ -203,7 +232,7 @@ def batch_solve(pkg, insts, prec, autotune, max_iter=100, tol=1e-8, host=False):
     from paper_2607_00981_gb300 import binding as B
     lib = pkg.load()
     b = B.Batch(lib, [(i.o, i.v, i.naux) for i in insts], precision=prec, tol=tol, max_iter=max_iter,
-                autotune=autotune)
+                autotune=autotune, f64_tc=f64_tc)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
     hL = [pin(i.L) for i in insts] if host else None
     hf = [pin(i.fock_diag) for i in insts] if host else None
@@ -232,9 +261,11 @@ def batch_solve(pkg, insts, prec, autotune, max_iter=100, tol=1e-8, host=False):
 def batch_summary(pkg, args):
     """The batched uneven-instance workload (64 RCCSDT problems, o in [3, 8], v in
     [20, 60]) iterated to |R| <= 1e-8 in one CUDA graph launch per batch iteration:
-    split precision with the autotuned and the fixed grouped-GEMM shape, FP64 for a
-    few batch iterations (s/iteration), end to end from pinned host memory, and
-    converged energies against the oracle's stored values where they exist."""
+    split precision with the autotuned and the fixed grouped-GEMM shape (the final
+    FP64 iterations with their large contractions on the tensor cores, f64_tc = 1),
+    FP64 for a few batch iterations on the FP64 units and on the tensor cores
+    (s/iteration), end to end from pinned host memory, and converged energies against
+    the oracle's stored values where they exist."""
     import json as _json
     from paper_2607_00981_gb300.synth import batch_instances
     insts = batch_instances(64)
@@ -263,12 +294,14 @@ def batch_summary(pkg, args):
                 "half_grid": sum(1 for i in infos if i["grid"] > 0)}
             energies = r["energies"]
     out["split"] = runs
+    out["split_final_phase"] = "FP64 iterations from |R| <= sqrt(tol), large contractions on the tensor cores"
     # FP64: per-iteration cost over three batch iterations (not to convergence)
-    r = batch_solve(pkg, insts, 0, 0, max_iter=3)
-    s = r["stats"]
-    out["fp64"] = {"s_per_batch_iteration": s["device_ms"] / 1e3 / max(1.0, s["launches"]),
-                   "tflops": s["flop"] / (s["device_ms"] / 1e3) / 1e12, "launches": int(s["launches"]),
-                   "note": "three batch iterations from the MP2 guess"}
+    for label, f64_tc in (("fp64", 0), ("fp64_tc", 1)):
+        r = batch_solve(pkg, insts, 0, 0, max_iter=3, f64_tc=f64_tc)
+        s = r["stats"]
+        out[label] = {"s_per_batch_iteration": s["device_ms"] / 1e3 / max(1.0, s["launches"]),
+                      "tflops": s["flop"] / (s["device_ms"] / 1e3) / 1e12, "launches": int(s["launches"]),
+                      "note": "three batch iterations from the MP2 guess"}
     out["speedup_split_vs_fp64_per_iteration"] = out["fp64"]["s_per_batch_iteration"] / \
         runs["autotuned"]["s_per_batch_iteration"]
     # end to end: Hamiltonians from pinned host memory, MP2 start, solve, energies to host
@@ -393,9 +426,21 @@ def run_ours(args, rank, world):
                 "pp-ladder launch (61 stored blocks)" if traffic else None, "peak_source": src,
                 "launches": int(gemm_n), "avg_launch_ms": gemm_ms / gemm_n}
 
+    step_ms = {k: float(x) / args.steps for k, x in zip(
+        ["intermediates", "pp", "ring", "hh", "t2", "r12_setup", "post", "update", "energy"], st[:9])}
+    ctx.close()  # the comparisons below need the device memory
+
     compare = None
     if not args.no_compare and world == 1:
         compare = compare_fp64_split(pkg, stream, dev)
+    fp64_here = None
+    if not args.no_compare and world == 1 and prec != 0:
+        rate = 2.0 * lib.rccsdt_iteration_fma(8, 80) / compare["fp64"] if compare else None
+        fp64_here = fp64_tc_iteration(pkg, stream, inst, rate)
+        fp64_here["speedup_split_vs_fp64_tc"] = fp64_here["fp64_tc_s_per_iteration"] / s_per_iter
+        if rate:
+            fp64_here["speedup_split_vs_fp64_dfma_estimated"] = \
+                fp64_here["fp64_dfma_s_per_iteration_estimated"] / s_per_iter
 
     batch = None
     if rank == 0 and world == 1 and not args.no_batch:
@@ -413,12 +458,11 @@ def run_ours(args, rank, world):
                 "config": dict(config(args, inst), parallelism=f"replicas{world}"),
                 "tflops": 2.0 * fma * world / (ms_total / 1e3 / args.steps) / 1e12,
                 "energy_last": energies[-1], "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
-                "cpu_baseline": cpu, "clocks": clk.summary(), "fp64_vs_split": compare, "batch64": batch,
+                "cpu_baseline": cpu, "clocks": clk.summary(), "fp64_vs_split": compare, "fp64_here": fp64_here,
+                "batch64": batch,
                 "diis": "T1, T2 and T3" if diis_t3 else "T1 and T2 (T3 history would exceed 64 GB)",
-                "step_ms": {k: float(x) / args.steps for k, x in zip(
-                    ["intermediates", "pp", "ring", "hh", "t2", "r12_setup", "post", "update", "energy"], st[:9])}}
+                "step_ms": step_ms}
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist:
         dist.destroy_process_group()
 

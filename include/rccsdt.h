@@ -113,8 +113,9 @@ int rccsdt_set_amplitudes(rccsdt_ctx* ctx, const double* t1, const double* t2, c
 /* t1 = 0, t2 = first-order (MP2) doubles v^{ab}_{ij} / eps_ij^ab, t3 = 0. */
 int rccsdt_init_mp2(rccsdt_ctx* ctx);
 
-/* Switches the precision of later contractions (rccsdt_precision).  Changing
- * between FP64 and a split mode converts the stored T3. */
+/* Switches the precision of later contractions (rccsdt_precision).  A split context
+ * may switch between the split modes and FP64 contractions (its T3 and R3 stay in
+ * FP32 storage); a context created in FP64 mode accepts FP64 only (RCCSDT_ERR_ARG). */
 int rccsdt_set_precision(rccsdt_ctx* ctx, int precision);
 
 /* Step (i)-(iii) of one iteration: T1-dressing, the RCCSD and RCCSDT
@@ -141,11 +142,13 @@ int rccsdt_energy(rccsdt_ctx* ctx, double* e_corr);
 int rccsdt_iterate(rccsdt_ctx* ctx, double* e_corr, double norms[4]);
 
 /* Iterates from the current amplitudes until |R| <= tol or max_iter evaluations.
- * In the split modes the iterations run in split precision until |R| <= sqrt(tol);
- * from then on they run with FP64 contractions (iterative refinement), and
- * convergence is only accepted on an FP64 evaluation.  Outputs describe the last residual evaluated
- * (iterations counts evaluations).  Returns RCCSDT_NOT_CONVERGED if max_iter is
- * reached. */
+ * In the split modes the iterations run in the context's split precision until
+ * |R| <= sqrt(tol); a 3xBF16 context then runs 3xTF32 iterations until
+ * |R| <= tol^(3/4) or until they stop improving (no 10 % gain in three evaluations);
+ * the rest run with FP64 contractions (options.f64_tc chooses the engine), and
+ * convergence is only accepted on an FP64 evaluation (iterative refinement).
+ * Outputs describe the last residual evaluated (iterations counts evaluations).
+ * Returns RCCSDT_NOT_CONVERGED if max_iter is reached. */
 int rccsdt_solve(rccsdt_ctx* ctx, double* e_corr, int* iterations, double* final_norm);
 
 /* Copies out the amplitudes / the current residuals (float64). NULL skips. */

@@ -140,7 +140,8 @@ int build_graph(rccsdt_batch* b) {
     cudaGraph_t* bodies = p.conditional.phGraph_out;
     rccsdt_ctx* c = b->inst[i];
     for (int code = 0; code < kBodies; ++code) {
-      const bool unused = !split && (code == rcc::kEvalF64 || code == rcc::kStepF64);
+      const bool unused = (!split && (code == rcc::kEvalF64 || code == rcc::kStepF64 || code == rcc::kStepMid)) ||
+                          (code == rcc::kStepMid && !rcc::has_mid(b->opt));
       if (unused) {
         cudaGraphNode_t e;
         cudaGraphAddEmptyNode(&e, bodies[code], nullptr, 0);

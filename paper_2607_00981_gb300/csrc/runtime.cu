@@ -2501,7 +2501,7 @@ int ctx_enqueue(rccsdt_ctx* c, int update_first, int precision) {
 // Queues one body of the solver (solve_sm.h) without host synchronisation.
 int ctx_enqueue_code(rccsdt_ctx* c, int code) {
   if (code < 0 || code >= kBodies) return fail(c, RCCSDT_ERR_ARG, "internal: unknown body");
-  const int st = ctx_enqueue(c, code == kStepMain || code == kStepF64, body_precision(c->opt, code));
+  const int st = ctx_enqueue(c, rcc::body_updates(code), body_precision(c->opt, code));
   c->precision = c->opt.precision;
   return st ? st : check(c, "ctx_enqueue_code");
 }

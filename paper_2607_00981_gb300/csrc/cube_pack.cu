@@ -183,57 +183,71 @@ __global__ void __launch_bounds__(256) k_cube_pack_k(const CubePiece* __restrict
 }
 
 // Mode 1: grid (label cubes of 8^3, groups of 16 pieces = 16 consecutive columns).
+// The 16 columns' source geometry is decoded once into shared memory, then every
+// thread issues its 32 loads (2 elements x 16 columns) before staging any of them.
 template <int KIND>
 __global__ void __launch_bounds__(256) k_cube_pack_col(const CubePiece* __restrict__ pieces,
                                                        const CubeDst* __restrict__ dsts, CubeDst d0,
                                                        const float* __restrict__ src, int v) {
   constexpr int TL = 8, CS = TL * TL * (TL + 1) + 1;  // one padded 8^3 cube per column
   __shared__ float cols[16 * CS];
+  __shared__ i64 g_off[16], g_sm[16], g_ss[16];
+  __shared__ int g_n[16], g_map[16];
+  __shared__ float g_coef[16];
   const int nc = (v + TL - 1) / TL;
   const int cb = blockIdx.x;
   const int lo[3] = {(cb / (nc * nc)) * TL, ((cb / nc) % nc) * TL, (cb % nc) * TL};
   const CubePiece* G = pieces + (i64)blockIdx.y * 16;
   const int tid = threadIdx.x;
-  for (int c = 0; c < 16; ++c) {
-    const CubePiece& P = G[c];
-    float acc[2] = {0.f, 0.f};
-    for (int t = 0; t < (P.nterm > 0 ? 1 : 0); ++t) {  // one term per column
-      const int pos = P.t[t].pos;
-      const int p0 = pos_of(pos, 0), p1 = pos_of(pos, 1);
-      const int fast = p0 == 2 ? 0 : (p1 == 2 ? 1 : 2);
-      const int mid = fast == 0 ? 1 : 0, slow = 3 - fast - mid;
-      const i64 sm = axis_stride(pos_of(pos, mid), v), ss = axis_stride(pos_of(pos, slow), v);
-      const float cf = P.t[t].coef;
+  if (tid < 16) {
+    const CubePiece& P = G[tid];
+    // load order: the label on the stored unit-stride axis (fast), then mid, slow
+    const int pos = P.t[0].pos;
+    const int p0 = pos_of(pos, 0), p1 = pos_of(pos, 1);
+    const int fast = P.nterm > 0 ? (p0 == 2 ? 0 : (p1 == 2 ? 1 : 2)) : 2;
+    const int mid = P.nterm > 0 ? (fast == 0 ? 1 : 0) : 1, slow = 3 - fast - mid;
+    const i64 sm = axis_stride(pos_of(pos, mid), v), ss = axis_stride(pos_of(pos, slow), v);
+    const int lf = fast == 0 ? lo[0] : (fast == 1 ? lo[1] : lo[2]);
+    const int lm = mid == 0 ? lo[0] : (mid == 1 ? lo[1] : lo[2]);
+    const int ls = slow == 0 ? lo[0] : (slow == 1 ? lo[1] : lo[2]);
+    g_off[tid] = P.t[0].base + lf + lm * sm + (i64)ls * ss;
+    g_sm[tid] = sm;
+    g_ss[tid] = ss;
+    // valid extents along fast, mid, slow (8 bits each; 0 for a zero column)
+    const int nf = P.nterm > 0 ? min(TL, v - lf) : 0, nm = min(TL, v - lm), ns = min(TL, v - ls);
+    g_n[tid] = nf | (nm << 8) | (ns << 16);
+    g_map[tid] = fast | (mid << 2) | (slow << 4);  // label of each load coordinate
+    g_coef[tid] = P.t[0].coef;
+  }
+  __syncthreads();
+  float ld[16][2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int e = tid + 256 * h;  // (slow, mid, fast) of 8^3
-        const int uf = e & 7, um = (e >> 3) & 7, us = e >> 6;
-        const int xf = (fast == 0 ? lo[0] : fast == 1 ? lo[1] : lo[2]) + uf;
-        const int xm = (mid == 0 ? lo[0] : mid == 1 ? lo[1] : lo[2]) + um;
-        const int xs = (slow == 0 ? lo[0] : slow == 1 ? lo[1] : lo[2]) + us;
-        if (xf < v && xm < v && xs < v) acc[h] = fmaf(cf, __ldg(src + P.t[t].base + xf + xm * sm + xs * ss), acc[h]);
-      }
+  for (int c = 0; c < 16; ++c) {
+    const i64 off = g_off[c], sm = g_sm[c], ss = g_ss[c];
+    const int n = g_n[c];
+    const float cf = g_coef[c];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + 256 * h;  // (slow, mid, fast) of 8^3
+      const int uf = e & 7, um = (e >> 3) & 7, us = e >> 6;
+      const bool ok = uf < (n & 255) && um < ((n >> 8) & 255) && us < (n >> 16);
+      ld[c][h] = ok ? cf * __ldg(src + off + uf + um * sm + us * ss) : 0.f;
     }
-    // stage by label order (L0, L1, L2), whatever the load order was
+  }
+  // stage by label order (L0, L1, L2), whatever the load order was
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int mp = g_map[c];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int e = tid + 256 * h;
-      const int uf = e & 7, um = (e >> 3) & 7, us = e >> 6;
-      int u0 = 0, u1 = 0, u2 = 0;
-      if (P.nterm > 0) {
-        const int pos = P.t[0].pos;
-        const int p0 = pos_of(pos, 0), p1 = pos_of(pos, 1);
-        const int fast = p0 == 2 ? 0 : (p1 == 2 ? 1 : 2);
-        const int mid = fast == 0 ? 1 : 0;
-        u0 = fast == 0 ? uf : (mid == 0 ? um : us);
-        u1 = fast == 1 ? uf : (mid == 1 ? um : us);
-        u2 = fast == 2 ? uf : (mid == 2 ? um : us);
-      } else {
-        u0 = us;
-        u1 = um;
-        u2 = uf;
-      }
-      cols[c * CS + (u0 * TL + u1) * (TL + 1) + u2] = acc[h];
+      const int u[3] = {e & 7, (e >> 3) & 7, e >> 6};  // fast, mid, slow coordinates
+      const int lab_f = mp & 3, lab_m = (mp >> 2) & 3;
+      // coordinate of label q: the load coordinate whose label is q
+      const int u0 = lab_f == 0 ? u[0] : (lab_m == 0 ? u[1] : u[2]);
+      const int u1 = lab_f == 1 ? u[0] : (lab_m == 1 ? u[1] : u[2]);
+      const int u2 = lab_f == 2 ? u[0] : (lab_m == 2 ? u[1] : u[2]);
+      cols[c * CS + (u0 * TL + u1) * (TL + 1) + u2] = ld[c][h];
     }
   }
   __syncthreads();

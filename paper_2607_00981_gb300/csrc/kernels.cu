@@ -1428,7 +1428,7 @@ template void launch_r1_t3<float>(const float*, const double*, int, int, double*
 // axis (coalesced read-modify-write).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_scatter_rows3(const float* __restrict__ X, int M, int v,
+__global__ void __launch_bounds__(256, 5) k_scatter_rows3(const float* __restrict__ X, int M, int v,
                                                        const i64* __restrict__ row_base,
                                                        const int* __restrict__ row_sel,
                                                        const double* __restrict__ row_alpha, T* __restrict__ C) {
@@ -1455,12 +1455,16 @@ __global__ void __launch_bounds__(256) k_scatter_rows3(const float* __restrict__
     for (int tile = blockIdx.x; tile < nt * nt * nt; tile += gridDim.x) {
       const int lo0 = tile / (nt * nt) * TL, lo1 = (tile / nt) % nt * TL, lo2 = tile % nt * TL;
       __syncthreads();
-      {  // X cube along c: thread (b, c) = (lm, lf), 16 loads in flight
+      {  // X cube along c: thread (b, c) = (lm, lf), 16 loads in flight (one running pointer)
         const int gb = lo1 + lm, gc = lo2 + lf;
-        const bool in = gb < v && gc < v;
+        const int na = (gb < v && gc < v) ? min(TL, v - lo0) : 0;
+        const float* px = xm + lo0 * V2 + (i64)gb * v + gc;
         float ld[TL];
 #pragma unroll
-        for (int a = 0; a < TL; ++a) ld[a] = (in && lo0 + a < v) ? __ldg(xm + (lo0 + a) * V2 + (i64)gb * v + gc) : 0.f;
+        for (int a = 0; a < TL; ++a) {
+          ld[a] = a < na ? __ldg(px) : 0.f;
+          px += V2;
+        }
 #pragma unroll
         for (int a = 0; a < TL; ++a) cube[a][lm][lf] = ld[a];
       }
@@ -1474,12 +1478,22 @@ __global__ void __launch_bounds__(256) k_scatter_rows3(const float* __restrict__
         T* dst = C + base + gf + gm * stm + (i64)loslow * sts;
         const float* src = &cube[0][0][0] + lf * cF + lm * cM;
         const int nu = min(TL, v - loslow);
-        T old[TL];
 #pragma unroll
-        for (int u = 0; u < TL; ++u) old[u] = u < nu ? dst[u * sts] : (T)0;
+        for (int h = 0; h < TL; h += 8) {  // two halves of 8 read-modify-writes in flight
+          T old[8];
+          T* pd = dst + h * sts;
 #pragma unroll
-        for (int u = 0; u < TL; ++u)
-          if (u < nu) dst[u * sts] = old[u] + al * (T)src[u * cS];
+          for (int u = 0; u < 8; ++u) {
+            old[u] = h + u < nu ? pd[0] : (T)0;
+            pd += sts;
+          }
+          pd = dst + h * sts;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (h + u < nu) pd[0] = old[u] + al * (T)src[(h + u) * cS];
+            pd += sts;
+          }
+        }
       }
     }
   }

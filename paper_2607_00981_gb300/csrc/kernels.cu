@@ -1518,21 +1518,46 @@ template void launch_scatter_rows3<double>(const float*, int, int, const i64*, c
 //   r_{ijk}^{abc} += sum over the six column permutations of
 //                    -sum_l W^{a1 l}_{i1 i2} t_{l i3}^{a2 a3}
 // One CTA owns a 16^3 tile of one stored block and accumulates all six terms in
-// registers; per term the W slice [a1][l] and the t2 slice [l][a2][a3] of the
-// tile are staged in shared memory (l in chunks of 16).  Each thread holds a
-// fixed (b, c) and 16 values of a; the block is written once, along c.
+// registers; per term the W slice [l][a1] and the t2 slice of the tile are staged in
+// shared memory (l in chunks of 16), the t2 slice as [l][a2][a3], or as [l][a3][a2]
+// when a2 lies on the tile's first axis, so that the 16 values a thread needs along
+// that axis are one contiguous, 16-byte aligned run (vector loads: about one shared
+// load per three FMAs).  Each thread holds a fixed (b, c) and 16 values of a; the
+// block is written once, along c.
 // Wvooo[a][l][i][j] = W^{al}_{ij}; t2[l][k][b][c] = t_lk^bc (T precision copies).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_t2_outer(T* __restrict__ r3, const T* __restrict__ Wvooo,
+__device__ __forceinline__ void load16(const T* p, T (&x)[16]) {  // p 16-byte aligned
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 f = reinterpret_cast<const float4*>(p)[j];
+      x[4 * j] = f.x;
+      x[4 * j + 1] = f.y;
+      x[4 * j + 2] = f.z;
+      x[4 * j + 3] = f.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const double2 f = reinterpret_cast<const double2*>(p)[j];
+      x[2 * j] = f.x;
+      x[2 * j + 1] = f.y;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 3) k_t2_outer(T* __restrict__ r3, const T* __restrict__ Wvooo,
                                                   const T* __restrict__ t2, const int4* __restrict__ blocks, int o,
                                                   int v, i64 n3) {
-  constexpr int TL = 16, LC = 16;
-  __shared__ T Ws[TL][LC + 1];
-  __shared__ T Ts[LC][TL][TL + 1];
+  constexpr int TL = 16, LC = 16, PW = TL + 16 / (int)sizeof(T);  // rows padded, 16-byte aligned
+  __shared__ __align__(16) T Ws[LC][PW];      // [l][a1]
+  __shared__ __align__(16) T Ts[LC][TL][PW];  // [l][a2][a3] or [l][a3][a2]
   const int nt = (v + TL - 1) / TL;
   const i64 V3 = (i64)v * v * v;
   const int tc = threadIdx.x % TL, tb = threadIdx.x / TL;
+  auto coord = [&](int x) { return x == 1 ? tb : tc; };  // the thread's coordinate on axis 1 or 2
   for (i64 blk = blockIdx.y; blk < n3; blk += gridDim.y) {
     const int4 ijk = blocks[blk];
     auto occ = [&](int x) { return x == 0 ? ijk.x : (x == 1 ? ijk.y : ijk.z); };
@@ -1547,14 +1572,15 @@ __global__ void __launch_bounds__(256) k_t2_outer(T* __restrict__ r3, const T* _
         // roles: position x1 -> (i1, a1), x2 -> (i2, a2), x3 -> (i3, a3) (the q-th ordering)
         const int x1 = perm3(q, 0), x2 = perm3(q, 1), x3 = perm3(q, 2);
         const int i1 = occ(x1), i2 = occ(x2), i3 = occ(x3);
+        const bool tr = x2 == 0;  // stage the t2 slice as [l][a3][a2]
         for (int l0 = 0; l0 < o; l0 += LC) {
           const int lc = min(LC, o - l0);
           __syncthreads();
-          {  // W slice [u][l]: thread (u, l) = (tb, tc)
+          {  // W slice [l][a1]: thread (a1, l) = (tb, tc)
             const int ga = lo(x1) + tb;
-            Ws[tb][tc] = (tc < lc && ga < v) ? Wvooo[(((i64)ga * o + l0 + tc) * o + i1) * o + i2] : (T)0;
+            Ws[tc][tb] = (tc < lc && ga < v) ? Wvooo[(((i64)ga * o + l0 + tc) * o + i1) * o + i2] : (T)0;
           }
-          {  // t2 slice [l][u2][u3]: thread (u2, u3) = (tb, tc), 16 loads in flight
+          {  // t2 slice: thread (a2, a3) = (tb, tc), 16 loads in flight
             const int g2 = lo(x2) + tb, g3 = lo(x3) + tc;
             const bool in = g2 < v && g3 < v;
             const T* src = t2 + ((i64)(l0 * o + i3) * v + g2) * v + g3;
@@ -1562,30 +1588,29 @@ __global__ void __launch_bounds__(256) k_t2_outer(T* __restrict__ r3, const T* _
             T ld[LC];
 #pragma unroll
             for (int l = 0; l < LC; ++l) ld[l] = (in && l < lc) ? src[l * ls] : (T)0;
+            T* dst = tr ? &Ts[0][tc][tb] : &Ts[0][tb][tc];
 #pragma unroll
-            for (int l = 0; l < LC; ++l) Ts[l][tb][tc] = ld[l];
+            for (int l = 0; l < LC; ++l) dst[l * TL * PW] = ld[l];
           }
           __syncthreads();
-          // the thread's fixed (b, c) sit on two of the three roles; a runs over the third
           if (x1 == 0) {  // a = a1: W varies with a, the t2 value is fixed per l
-            const int u2 = x2 == 1 ? tb : tc, u3 = x3 == 1 ? tb : tc;
+            const int u2 = coord(x2), u3 = coord(x3);
             for (int l = 0; l < lc; ++l) {
               const T tv = Ts[l][u2][u3];
+              T w[TL];
+              load16(&Ws[l][0], w);
 #pragma unroll
-              for (int a = 0; a < TL; ++a) acc[a] -= Ws[a][l] * tv;
+              for (int a = 0; a < TL; ++a) acc[a] -= w[a] * tv;
             }
-          } else {  // a = a2 or a3: W fixed per l, t2 varies with a
-            const int u1 = x1 == 1 ? tb : tc;
-            const int other = (x2 == 0) ? (x3 == 1 ? tb : tc) : (x2 == 1 ? tb : tc);
+          } else {  // a = a2 or a3: W fixed per l, t2 varies with a along a contiguous row
+            const int u1 = coord(x1);
+            const int row = tr ? coord(x3) : coord(x2);
             for (int l = 0; l < lc; ++l) {
-              const T wv = Ws[u1][l];
-              if (x2 == 0) {
+              const T wv = Ws[l][u1];
+              T t[TL];
+              load16(&Ts[l][row][0], t);
 #pragma unroll
-                for (int a = 0; a < TL; ++a) acc[a] -= wv * Ts[l][a][other];
-              } else {
-#pragma unroll
-                for (int a = 0; a < TL; ++a) acc[a] -= wv * Ts[l][other][a];
-              }
+              for (int a = 0; a < TL; ++a) acc[a] -= wv * t[a];
             }
           }
         }

@@ -1262,6 +1262,20 @@ int build_context(rccsdt_ctx* c) {
           g->swap_ab = 1;
         }
         finish_plan(c, g, (int)V2);
+        if (t3f) {  // split bodies: B through label cubes, one piece per block, K = (d, e), rows w
+          static const int vp[3][3] = {{1, 0, 2}, {2, 0, 1}, {2, 1, 0}};  // stored axes of (e, d, w)
+          std::vector<rcc::CubePiece> pcs;
+          for (i64 blk = b0; blk < b1; ++blk) {
+            rcc::CubePiece pc = cube_piece(0, 1);
+            pc.ks1 = v;
+            pc.rs1 = 0;
+            pc.rs2 = 1;
+            pc.row0 = (blk - b0) * v;
+            pc.t[0] = {blk * V3, 1.f, packpos(vp[term][0], vp[term][1], vp[term][2])};
+            pcs.push_back(pc);
+          }
+          set_cube(c, g, 0, std::move(pcs), &err);
+        }
         c->p_pp.push_back(g);
       }
   }

@@ -29,10 +29,13 @@ def _golden(name):
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec,tol_e,tol_r", [(B.FP64, 1e-10, 1e-10), (B.SPLIT_BF16X3, 1e-6, 1e-8),
                                               (B.SPLIT_TF32X3, 1e-6, 1e-8)], ids=["fp64", "bf16x3", "tf32x3"])
-def test_converged_energy_o6v48w(prec, tol_e, tol_r):
+@pytest.mark.parametrize("f64_tc", [0, 1], ids=["fp64-units", "fp64-tensor-cores"])
+def test_converged_energy_o6v48w(prec, tol_e, tol_r, f64_tc):
+    """FP64 contractions on the FP64 units or on the tensor cores (digit planes; for
+    split contexts those are the final iterations)."""
     E0 = _golden("o6v48w")
     inst = workload("o6v48w")
-    ctx = B.Context(gpu_lib(), inst.o, inst.v, inst.naux, precision=prec, tol=tol_r, max_iter=300)
+    ctx = B.Context(gpu_lib(), inst.o, inst.v, inst.naux, precision=prec, tol=tol_r, max_iter=300, f64_tc=f64_tc)
     ctx.set_hamiltonian(inst.fock_diag, inst.L)
     ctx.init_mp2()
     E, it, nrm, conv = ctx.solve()

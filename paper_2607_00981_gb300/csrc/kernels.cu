@@ -1552,11 +1552,17 @@ __global__ void __launch_bounds__(256, 3) k_t2_outer(T* __restrict__ r3, const T
                                                   const T* __restrict__ t2, const int4* __restrict__ blocks, int o,
                                                   int v, i64 n3) {
   constexpr int TL = 16, LC = 16, PW = TL + 16 / (int)sizeof(T);  // rows padded, 16-byte aligned
-  __shared__ __align__(16) T Ws[LC][PW];      // [l][a1]
-  __shared__ __align__(16) T Ts[LC][TL][PW];  // [l][a2][a3] or [l][a3][a2]
+  // two buffers: the slices of stage s + 1 are loaded while stage s is computed
+  // (dynamic shared memory: 43 KB for FP32, 78 KB for FP64)
+  extern __shared__ __align__(16) unsigned char t2o_smem[];
+  typedef T WsT[LC][PW];
+  typedef T TsT[LC][TL][PW];
+  WsT* Ws = reinterpret_cast<WsT*>(t2o_smem);                         // [2][l][a1]
+  TsT* Ts = reinterpret_cast<TsT*>(t2o_smem + 2 * sizeof(WsT));       // [2][l][a2][a3] or [2][l][a3][a2]
   const int nt = (v + TL - 1) / TL;
   const i64 V3 = (i64)v * v * v;
   const int tc = threadIdx.x % TL, tb = threadIdx.x / TL;
+  const int nch = (o + LC - 1) / LC, nstage = 6 * nch;  // stage = (ordering q, chunk of l)
   auto coord = [&](int x) { return x == 1 ? tb : tc; };  // the thread's coordinate on axis 1 or 2
   for (i64 blk = blockIdx.y; blk < n3; blk += gridDim.y) {
     const int4 ijk = blocks[blk];
@@ -1564,56 +1570,64 @@ __global__ void __launch_bounds__(256, 3) k_t2_outer(T* __restrict__ r3, const T
     for (int tile = blockIdx.x; tile < nt * nt * nt; tile += gridDim.x) {
       const int lo0 = tile / (nt * nt) * TL, lo1 = (tile / nt) % nt * TL, lo2 = tile % nt * TL;
       auto lo = [&](int x) { return x == 0 ? lo0 : (x == 1 ? lo1 : lo2); };
+      // global loads of one stage into registers: W value of thread (a1, l) = (tb, tc),
+      // t2 values of thread (a2, a3) = (tb, tc) over the chunk's l
+      T ld[LC], wl;
+      auto load = [&](int st) {
+        const int q = st / nch, l0 = (st % nch) * LC, lc = min(LC, o - l0);
+        const int x1 = perm3(q, 0), x2 = perm3(q, 1), x3 = perm3(q, 2);
+        const int i1 = occ(x1), i2 = occ(x2), i3 = occ(x3);
+        const int ga = lo(x1) + tb;
+        wl = (tc < lc && ga < v) ? Wvooo[(((i64)ga * o + l0 + tc) * o + i1) * o + i2] : (T)0;
+        const int g2 = lo(x2) + tb, g3 = lo(x3) + tc;
+        const bool in = g2 < v && g3 < v;
+        const T* src = t2 + ((i64)(l0 * o + i3) * v + g2) * v + g3;
+        const i64 ls = (i64)o * v * v;  // stride of l
+#pragma unroll
+        for (int l = 0; l < LC; ++l) ld[l] = (in && l < lc) ? src[l * ls] : (T)0;
+      };
+      auto store = [&](int st) {
+        const int b = st & 1, q = st / nch;
+        const bool tr = perm3(q, 1) == 0;  // the t2 slice as [l][a3][a2]
+        Ws[b][tc][tb] = wl;
+        T* dst = tr ? &Ts[b][0][tc][tb] : &Ts[b][0][tb][tc];
+#pragma unroll
+        for (int l = 0; l < LC; ++l) dst[l * TL * PW] = ld[l];
+      };
       T acc[TL];
 #pragma unroll
       for (int a = 0; a < TL; ++a) acc[a] = (T)0;
+      __syncthreads();  // the previous tile's last stage is consumed
+      load(0);
+      store(0);
+      __syncthreads();
 #pragma unroll 1
-      for (int q = 0; q < 6; ++q) {
-        // roles: position x1 -> (i1, a1), x2 -> (i2, a2), x3 -> (i3, a3) (the q-th ordering)
+      for (int st = 0; st < nstage; ++st) {
+        if (st + 1 < nstage) load(st + 1);  // in flight during the FMAs below
+        const int b = st & 1, q = st / nch, lc = min(LC, o - (st % nch) * LC);
         const int x1 = perm3(q, 0), x2 = perm3(q, 1), x3 = perm3(q, 2);
-        const int i1 = occ(x1), i2 = occ(x2), i3 = occ(x3);
-        const bool tr = x2 == 0;  // stage the t2 slice as [l][a3][a2]
-        for (int l0 = 0; l0 < o; l0 += LC) {
-          const int lc = min(LC, o - l0);
-          __syncthreads();
-          {  // W slice [l][a1]: thread (a1, l) = (tb, tc)
-            const int ga = lo(x1) + tb;
-            Ws[tc][tb] = (tc < lc && ga < v) ? Wvooo[(((i64)ga * o + l0 + tc) * o + i1) * o + i2] : (T)0;
+        if (x1 == 0) {  // a = a1: W varies with a, the t2 value is fixed per l
+          const int u2 = coord(x2), u3 = coord(x3);
+          for (int l = 0; l < lc; ++l) {
+            const T tv = Ts[b][l][u2][u3];
+            T w[TL];
+            load16(&Ws[b][l][0], w);
+#pragma unroll
+            for (int a = 0; a < TL; ++a) acc[a] -= w[a] * tv;
           }
-          {  // t2 slice: thread (a2, a3) = (tb, tc), 16 loads in flight
-            const int g2 = lo(x2) + tb, g3 = lo(x3) + tc;
-            const bool in = g2 < v && g3 < v;
-            const T* src = t2 + ((i64)(l0 * o + i3) * v + g2) * v + g3;
-            const i64 ls = (i64)o * v * v;  // stride of l
-            T ld[LC];
+        } else {  // a = a2 or a3: W fixed per l, t2 varies with a along a contiguous row
+          const int u1 = coord(x1);
+          const int row = x2 == 0 ? coord(x3) : coord(x2);
+          for (int l = 0; l < lc; ++l) {
+            const T wv = Ws[b][l][u1];
+            T t[TL];
+            load16(&Ts[b][l][row][0], t);
 #pragma unroll
-            for (int l = 0; l < LC; ++l) ld[l] = (in && l < lc) ? src[l * ls] : (T)0;
-            T* dst = tr ? &Ts[0][tc][tb] : &Ts[0][tb][tc];
-#pragma unroll
-            for (int l = 0; l < LC; ++l) dst[l * TL * PW] = ld[l];
-          }
-          __syncthreads();
-          if (x1 == 0) {  // a = a1: W varies with a, the t2 value is fixed per l
-            const int u2 = coord(x2), u3 = coord(x3);
-            for (int l = 0; l < lc; ++l) {
-              const T tv = Ts[l][u2][u3];
-              T w[TL];
-              load16(&Ws[l][0], w);
-#pragma unroll
-              for (int a = 0; a < TL; ++a) acc[a] -= w[a] * tv;
-            }
-          } else {  // a = a2 or a3: W fixed per l, t2 varies with a along a contiguous row
-            const int u1 = coord(x1);
-            const int row = tr ? coord(x3) : coord(x2);
-            for (int l = 0; l < lc; ++l) {
-              const T wv = Ws[l][u1];
-              T t[TL];
-              load16(&Ts[l][row][0], t);
-#pragma unroll
-              for (int a = 0; a < TL; ++a) acc[a] -= wv * t[a];
-            }
+            for (int a = 0; a < TL; ++a) acc[a] -= wv * t[a];
           }
         }
+        if (st + 1 < nstage) store(st + 1);  // the other buffer: its last reader was stage st - 1
+        __syncthreads();
       }
       const int gb = lo1 + tb, gc = lo2 + tc;
       if (gb < v && gc < v) {
@@ -1634,8 +1648,15 @@ void launch_t2_outer(T* r3, const T* Wvooo, const T* t2, const int4* blocks, int
   const int nt = (v + 15) / 16;
   const unsigned gx = (unsigned)std::min(nt * nt * nt, 65535);
   const unsigned gy = (unsigned)std::min<i64>(n3, 65535);
+  constexpr int PW = 16 + 16 / (int)sizeof(T);
+  const size_t smem = (size_t)2 * (16 * PW + 16 * 16 * PW) * sizeof(T);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_t2_outer<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
   ++g_launch_count;
-  k_t2_outer<T><<<dim3(gx, gy), 256, 0, s>>>(r3, Wvooo, t2, blocks, o, v, n3);
+  k_t2_outer<T><<<dim3(gx, gy), 256, smem, s>>>(r3, Wvooo, t2, blocks, o, v, n3);
 }
 template void launch_t2_outer<double>(double*, const double*, const double*, const int4*, int, int, i64, cudaStream_t);
 template void launch_t2_outer<float>(float*, const float*, const float*, const int4*, int, int, i64, cudaStream_t);

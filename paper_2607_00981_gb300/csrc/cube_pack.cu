@@ -282,8 +282,8 @@ __global__ void k_zero_cols(CubeDst d, i64 rows, int k0, int esz) {
 
 }  // namespace
 
-void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, int /*max_terms*/,
-                      const CubeDst* dsts, const CubeDst& d0, const float* src, int v, cudaStream_t s) {
+void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, const CubeDst* dsts,
+                      const CubeDst& d0, const float* src, int v, cudaStream_t s) {
   if (npieces <= 0) return;
   if (mode == 0) {
     const int nc = (v + 15) / 16;
@@ -305,7 +305,7 @@ void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, 
   }
 }
 
-void launch_cube_pack_r1(int kind, const CubePiece* pieces, int npieces, int /*max_terms*/, const CubeDst& d0,
+void launch_cube_pack_r1(int kind, const CubePiece* pieces, int npieces, const CubeDst& d0,
                          const float* src, int v, const float* w, const i64* wbase, float* part, cudaStream_t s) {
   if (npieces <= 0) return;
   const int nc = (v + 15) / 16;

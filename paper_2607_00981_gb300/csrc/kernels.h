@@ -138,14 +138,13 @@ struct CubeDst {
 // mode 0: K = k0 + L0 + L1 ks1, rows row0 + L1 rs1 + L2 rs2 (pieces in any order);
 // mode 1: K = k0, rows row0 + L0 v^2 + L1 v + L2, pieces in groups of 16 consecutive
 // columns of one panel (npieces a multiple of 16).  Panels of `kind` (split).
-// max_terms: the largest nterm of the pieces.
-void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, int max_terms, const CubeDst* dsts,
+void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, const CubeDst* dsts,
                       const CubeDst& d0, const float* src, int v, cudaStream_t s);
 // Mode 0 for the S panels of step (iii) (pieces ordered by (z, x, y), ppz per z),
 // also writing the per-cube partial sums of the T3 term of R1 to `part`
 // [npieces][cubes][32] (w + wbase[p] = v^{xy}_{..} of piece p as [v][v] floats);
 // launch_r1_cubes_reduce then adds them into dR1[z][a] for z < nz (dR1 at z0).
-void launch_cube_pack_r1(int kind, const CubePiece* pieces, int npieces, int max_terms, const CubeDst& d0,
+void launch_cube_pack_r1(int kind, const CubePiece* pieces, int npieces, const CubeDst& d0,
                          const float* src, int v, const float* w, const i64* wbase, float* part, cudaStream_t s);
 void launch_r1_cubes_reduce(const float* part, int ppz, int nz, int v, double* dR1, cudaStream_t s);
 // Zero the panel columns [k0, Kpad) of `rows` rows.

@@ -190,7 +190,6 @@ struct GemmPlan {
   std::vector<rcc::CubePiece> h_cube;
   std::unique_ptr<DBuf> cube;
   int cube_mode = -1;
-  int cube_terms = 0;  // the largest nterm of the pieces
   const float* cube_src = nullptr;  // the pieces' source (default: the B operand's)
   // step (iii): the cube gather also forms the partial sums of the T3 term of R1
   // (per piece, the offset of v^{xy} in the FP32 copy of the oovv integrals)
@@ -259,7 +258,6 @@ struct rccsdt_ctx {
     int npack[2] = {0, 0}, ntile[2] = {0, 0};
     std::unique_ptr<DBuf> cubes[2], cube_dst;     // label-cube gathers from T3, modes 0 and 1
     int ncube[2] = {0, 0};
-    int cube_terms[2] = {0, 0};
     std::unique_ptr<DBuf> probs;
     int nprob = 0, ntiles = 0, grid = 0;
     double flop = 0.0;
@@ -478,7 +476,6 @@ GemmPlan* stack_rows(rccsdt_ctx* c, const std::vector<GemmPlan*>& parts, int* er
   g->h_cube = std::move(b0->h_cube);
   g->cube = std::move(b0->cube);
   g->cube_mode = b0->cube_mode;
-  g->cube_terms = b0->cube_terms;
   g->cube_src = b0->cube_src;
   g->r1_wbase = std::move(b0->r1_wbase);
   make_epi(c, g->E, bufs[0], p0->E.e.c_f32, M, N, rb, rs, ra, co, err);
@@ -709,12 +706,11 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
       const rcc::CubeDst d0{pb.out_hi, pb.out_lo, g->Kpad};
       const float* src = g->cube_src ? g->cube_src : (const float*)pb.src;
       if (g->r1_wbase)
-        rcc::launch_cube_pack_r1(kind, (const rcc::CubePiece*)g->cube->p, (int)g->h_cube.size(), g->cube_terms, d0,
-                                 src, c->v,
+        rcc::launch_cube_pack_r1(kind, (const rcc::CubePiece*)g->cube->p, (int)g->h_cube.size(), d0, src, c->v,
                                  c->B("oovv_f")->f(), (const i64*)g->r1_wbase->p, c->B("r1_part")->f(), c->stream);
       else
         rcc::launch_cube_pack(g->cube_mode, kind, (const rcc::CubePiece*)g->cube->p, (int)g->h_cube.size(),
-                              g->cube_terms, nullptr, d0, src, c->v, c->stream);
+                              nullptr, d0, src, c->v, c->stream);
       if (g->cube_mode == 0) rcc::launch_zero_cols(d0, pb.R, g->K, kind, c->stream);
     } else {
       rcc::launch_pack(pb, c->stream);
@@ -843,8 +839,6 @@ rcc::CubePiece cube_piece(int k0, int nterm, int v = 0) {
 
 void set_cube(rccsdt_ctx* c, GemmPlan* g, int mode, std::vector<rcc::CubePiece> pieces, int* err) {
   g->cube_mode = mode;
-  g->cube_terms = 0;
-  for (const auto& pc : pieces) g->cube_terms = std::max(g->cube_terms, pc.nterm);
   g->h_cube = std::move(pieces);
   g->cube = upload_vec(c, g->h_cube, err);
 }
@@ -1684,8 +1678,6 @@ int build_grouped(rccsdt_ctx* c) {
       G.ptile[t] = upload_vec(c, ptile[t], &err);
     }
     G.ncube[t] = (int)cubes[t].size();
-    G.cube_terms[t] = 0;
-    for (const auto& pc : cubes[t]) G.cube_terms[t] = std::max(G.cube_terms[t], pc.nterm);
     if (G.ncube[t]) G.cubes[t] = upload_vec(c, cubes[t], &err);
   }
   if (!cdst.empty()) G.cube_dst = upload_vec(c, cdst, &err);
@@ -1826,7 +1818,7 @@ int run_grouped(rccsdt_ctx* c) {
                                t == 1, c->stream);
   for (int m = 0; m < 2; ++m)
     if (G.ncube[m])
-      rcc::launch_cube_pack(m, G.kind, (const rcc::CubePiece*)G.cubes[m]->p, G.ncube[m], G.cube_terms[m],
+      rcc::launch_cube_pack(m, G.kind, (const rcc::CubePiece*)G.cubes[m]->p, G.ncube[m],
                             (const rcc::CubeDst*)G.cube_dst->p, rcc::CubeDst{nullptr, nullptr, 0}, c->B("t3")->f(),
                             c->v, c->stream);
   if (c->opt.autotune && !G.tuned) {

@@ -92,7 +92,7 @@ static void host_store_split(int kind, void* hi, void* lo, long long o, float x)
   }
 }
 
-void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, int, const CubeDst* dsts,
+void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, const CubeDst* dsts,
                       const CubeDst& d0, const float* src, int v, cudaStream_t) {
   const i64 S[3] = {(i64)v * v, v, 1};
   for (int q = 0; q < npieces; ++q) {
@@ -115,9 +115,9 @@ void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, 
   }
 }
 
-void launch_cube_pack_r1(int kind, const CubePiece* pieces, int npieces, int max_terms, const CubeDst& d0,
+void launch_cube_pack_r1(int kind, const CubePiece* pieces, int npieces, const CubeDst& d0,
                          const float* src, int v, const float* w, const i64* wbase, float* part, cudaStream_t st) {
-  launch_cube_pack(0, kind, pieces, npieces, max_terms, nullptr, d0, src, v, st);
+  launch_cube_pack(0, kind, pieces, npieces, nullptr, d0, src, v, st);
   const i64 S[3] = {(i64)v * v, v, 1};
   const int nc = (v + 15) / 16;
   auto sval = [&](const CubePiece& P, int l0, int l1, int l2) {

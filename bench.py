@@ -294,7 +294,8 @@ def batch_summary(pkg, args):
                 "half_grid": sum(1 for i in infos if i["grid"] > 0)}
             energies = r["energies"]
     out["split"] = runs
-    out["split_final_phase"] = "FP64 iterations from |R| <= sqrt(tol), large contractions on the tensor cores"
+    out["split_final_phase"] = ("3xTF32 from |R| <= sqrt(tol), FP64 from tol^0.75 (or a 3xTF32 stall), "
+                                "large FP64 contractions on the tensor cores")
     # FP64: per-iteration cost over three batch iterations (not to convergence)
     for label, f64_tc in (("fp64", 0), ("fp64_tc", 1)):
         r = batch_solve(pkg, insts, 0, 0, max_iter=3, f64_tc=f64_tc)

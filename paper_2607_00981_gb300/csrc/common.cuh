@@ -43,6 +43,9 @@ struct PackArgs {
 // Table-driven epilogue: C[row_base[m] + col_off[row_sel[m]*N + n]] += row_alpha[m] * acc(m, n)
 // where rows m >= m2 write to C2 instead of C (a GEMM whose stacked A operand
 // feeds two output tensors of the same element type; C2 null: C only).
+// With row_base2 set, every value is also added, times row_alpha2[m], at
+// row_base2[m] + the same column offset of the same tensor (rows with
+// row_base2[m] < 0 write once): the mirrored element of a pair-symmetric product.
 struct EpiArgs {
   void* C;               // double or float
   int c_f32;
@@ -53,6 +56,8 @@ struct EpiArgs {
   const i64* col_off;    // [nsel][N]
   void* C2;
   int m2;
+  const i64* row_base2;     // [M] or null
+  const double* row_alpha2; // [M] (with row_base2)
 };
 
 }  // namespace rcc

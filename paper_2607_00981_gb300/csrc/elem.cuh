@@ -172,16 +172,59 @@ RCC_HD void store_panel_f(const PackArgs& a, int r, int k, float x) {
   }
 }
 
+// Pair-symmetric operands of the pp-ladder.  Pairs of virtual labels are
+// numbered tile-major: the 16-label tiles P <= Q form chunks, and inside a chunk
+// of n0 x n1 labels the pair of local labels (a, b) sits at a n1 + b (P < Q), or,
+// on a diagonal chunk (P = Q, n0 = n1), row-major over a <= b (plus) or a < b
+// (minus).  Returns the local pair of index idx.
+RCC_HD void pair_decode(int idx, bool diag, bool plus, int n0, int n1, int& a, int& b) {
+  if (!diag) {
+    a = idx / n1;
+    b = idx - a * n1;
+    return;
+  }
+  a = 0;
+  int len = plus ? n0 : n0 - 1;
+  while (idx >= len) {
+    idx -= len;
+    ++a;
+    --len;
+  }
+  b = a + (plus ? 0 : 1) + idx;
+}
+
+// One element of a K-major panel of `kind` (FP64, or split into hi + lo planes
+// from the FP32 value of x).
+RCC_HD void panel_put(int kind, void* out_hi, void* out_lo, i64 o, double x) {
+  if (kind == PANEL_F64) {
+    ((double*)out_hi)[o] = x;
+  } else if (kind == PANEL_BF16X2) {
+    const float f = (float)x;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+    ((__nv_bfloat16*)out_hi)[o] = hi;
+    ((__nv_bfloat16*)out_lo)[o] = __float2bfloat16_rn(f - __bfloat162float(hi));
+  } else {
+    const float f = (float)x;
+    const float hi = tf32_round(f);
+    ((float*)out_hi)[o] = hi;
+    ((float*)out_lo)[o] = tf32_round(f - hi);
+  }
+}
+
 // Output tensor of row m (see EpiArgs).
 RCC_HD void* epi_out(const EpiArgs& e, int m) { return (e.C2 && m >= e.m2) ? e.C2 : e.C; }
 
 RCC_HD void epi_apply(const EpiArgs& e, int m, int n, double acc) {
-  const i64 addr = e.row_base[m] + e.col_off[(i64)e.row_sel[m] * e.N + n];
-  const double val = e.row_alpha[m] * acc;
-  if (e.c_f32)
-    ((float*)epi_out(e, m))[addr] += (float)val;
-  else
-    ((double*)epi_out(e, m))[addr] += val;
+  const i64 co = e.col_off[(i64)e.row_sel[m] * e.N + n];
+  const int nout = (e.row_base2 && e.row_base2[m] >= 0) ? 2 : 1;
+  for (int q = 0; q < nout; ++q) {
+    const i64 addr = (q ? e.row_base2[m] : e.row_base[m]) + co;
+    const double val = (q ? e.row_alpha2[m] : e.row_alpha[m]) * acc;
+    if (e.c_f32)
+      ((float*)epi_out(e, m))[addr] += (float)val;
+    else
+      ((double*)epi_out(e, m))[addr] += val;
+  }
 }
 
 // ---------------------------------------------------------------------------

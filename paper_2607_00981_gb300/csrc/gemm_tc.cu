@@ -170,40 +170,45 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 // Scatter 32 accumulator columns of row m: every address and old value is
-// loaded before any store, so the loads of a row overlap in flight.
+// loaded before any store, so the loads of a row overlap in flight.  A mirrored
+// row (row_base2) repeats the pass at its second base.
 __device__ __forceinline__ void epilogue_row(const EpiArgs& e, int m, int n0, const uint32_t (&r)[32]) {
-  const i64 rb = e.row_base[m];
   const i64* co = e.col_off + (i64)e.row_sel[m] * e.N;
   const int nv = min(32, e.N - n0);
-  if (e.c_f32) {
-    float* C = (float*)epi_out(e, m);
-    const float al = (float)e.row_alpha[m];
+  const int nout = (e.row_base2 && e.row_base2[m] >= 0) ? 2 : 1;
+  for (int q = 0; q < nout; ++q) {
+    const i64 rb = q ? e.row_base2[m] : e.row_base[m];
+    const double alq = q ? e.row_alpha2[m] : e.row_alpha[m];
+    if (e.c_f32) {
+      float* C = (float*)epi_out(e, m);
+      const float al = (float)alq;
 #pragma unroll
-    for (int h = 0; h < 32; h += 16) {
-      i64 ad[16];
-      float old[16];
+      for (int h = 0; h < 32; h += 16) {
+        i64 ad[16];
+        float old[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) ad[j] = (h + j < nv) ? rb + __ldg(co + n0 + h + j) : -1;
+        for (int j = 0; j < 16; ++j) ad[j] = (h + j < nv) ? rb + __ldg(co + n0 + h + j) : -1;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) old[j] = ad[j] >= 0 ? C[ad[j]] : 0.f;
+        for (int j = 0; j < 16; ++j) old[j] = ad[j] >= 0 ? C[ad[j]] : 0.f;
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (ad[j] >= 0) C[ad[j]] = fmaf(al, __uint_as_float(r[h + j]), old[j]);
-    }
-  } else {
-    double* C = (double*)epi_out(e, m);
-    const double al = e.row_alpha[m];
+        for (int j = 0; j < 16; ++j)
+          if (ad[j] >= 0) C[ad[j]] = fmaf(al, __uint_as_float(r[h + j]), old[j]);
+      }
+    } else {
+      double* C = (double*)epi_out(e, m);
+      const double al = alq;
 #pragma unroll
-    for (int h = 0; h < 32; h += 16) {
-      i64 ad[16];
-      double old[16];
+      for (int h = 0; h < 32; h += 16) {
+        i64 ad[16];
+        double old[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) ad[j] = (h + j < nv) ? rb + __ldg(co + n0 + h + j) : -1;
+        for (int j = 0; j < 16; ++j) ad[j] = (h + j < nv) ? rb + __ldg(co + n0 + h + j) : -1;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) old[j] = ad[j] >= 0 ? C[ad[j]] : 0.0;
+        for (int j = 0; j < 16; ++j) old[j] = ad[j] >= 0 ? C[ad[j]] : 0.0;
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (ad[j] >= 0) C[ad[j]] = old[j] + al * (double)__uint_as_float(r[h + j]);
+        for (int j = 0; j < 16; ++j)
+          if (ad[j] >= 0) C[ad[j]] = old[j] + al * (double)__uint_as_float(r[h + j]);
+      }
     }
   }
 }
@@ -718,23 +723,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       const EpiArgs& e = sch.e;
       const int m = tm * BM + row;
       if (m < e.M) {
-        const i64 rb = e.row_base[m];
         const i64* co = e.col_off + (i64)e.row_sel[m] * e.N;
-        const double al = e.row_alpha[m];
         const int em = sch.ea[m];
         void* C = epi_out(e, m);
+        const int nout = (e.row_base2 && e.row_base2[m] >= 0) ? 2 : 1;
+        for (int q = 0; q < nout; ++q) {
+          const i64 rb = q ? e.row_base2[m] : e.row_base[m];
+          const double al = q ? e.row_alpha2[m] : e.row_alpha[m];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = tn * EBN + h * 32 + j;
-          if (n < e.N) {
-            const int sc = em + __ldg(sch.eb + n) - 14;
-            const double pw = __longlong_as_double((long long)(sc + 1023) << 52);  // |sc| < 1000 for finite data
-            const double val = ((double)shi[j] + (double)slo[j]) * pw;
-            const i64 ad = rb + __ldg(co + n);
-            if (e.c_f32)  // FP32 storage (R3 of split contexts)
-              ((float*)C)[ad] = (float)((double)((float*)C)[ad] + al * val);
-            else
-              ((double*)C)[ad] += al * val;
+          for (int j = 0; j < 32; ++j) {
+            const int n = tn * EBN + h * 32 + j;
+            if (n < e.N) {
+              const int sc = em + __ldg(sch.eb + n) - 14;
+              const double pw = __longlong_as_double((long long)(sc + 1023) << 52);  // |sc| < 1000 for finite data
+              const double val = ((double)shi[j] + (double)slo[j]) * pw;
+              const i64 ad = rb + __ldg(co + n);
+              if (e.c_f32)  // FP32 storage (R3 of split contexts)
+                ((float*)C)[ad] = (float)((double)((float*)C)[ad] + al * val);
+              else
+                ((double*)C)[ad] += al * val;
+            }
           }
         }
       }

@@ -147,6 +147,26 @@ void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, 
 void launch_cube_pack_r1(int kind, const CubePiece* pieces, int npieces, const CubeDst& d0,
                          const float* src, int v, const float* w, const i64* wbase, float* part, cudaStream_t s);
 void launch_r1_cubes_reduce(const float* part, int ppz, int nz, int v, double* dR1, cudaStream_t s);
+// Pair-symmetric pp-ladder panels (pair_pack.cu).  Chunk (P, Q), P <= Q, of the
+// 16-label tiles holds its pairs at K offsets offp (d <= e) and offm (d < e); inside
+// a chunk pairs are numbered as pair_decode (elem.cuh) describes.
+struct PairChunk {
+  int P, Q, offp, offm;
+};
+// A panels: row m of dp is the pair (x, y) = rows[m].x, .y (x <= y) with
+// dp[m][k] = W^{xy}_{de} + W^{xy}_{ed} (W^{xy}_{dd} for d = e), and row rows[m].z
+// (>= 0 when x < y) of dm holds W^{xy}_{de} - W^{xy}_{ed}; (d, e) the pair of
+// column k.  W is FP64 [x][y][d][e]; Kp = v(v+1)/2, Km = v(v-1)/2 columns, the
+// padding up to each Kpad zero.
+void launch_pair_pack_w(int kind, const double* W, int v, const int4* rows, int Mp, const PairChunk* ch, int nchunk,
+                        int Kp, int Km, const CubeDst& dp, const CubeDst& dm, cudaStream_t s);
+// B panels of one view of the stored blocks b0 .. b0 + nblk - 1 (element strides
+// sd, se, sw of the view's axes d, e, w inside a v^3 block): row (blk - b0) v + w,
+// dp = T(d, e, w) + T(e, d, w), dm = T(d, e, w) - T(e, d, w); padding zero.
+// FP32 T3 fills any panel kind, FP64 T3 FP64 panels.
+void launch_pair_pack_t(int kind, const void* t3, int t3_f32, i64 b0, int nblk, int v, i64 sd, i64 se, i64 sw,
+                        const PairChunk* ch, int nchunk, int Kp, int Km, const CubeDst& dp, const CubeDst& dm,
+                        cudaStream_t s);
 // Zero the panel columns [k0, Kpad) of `rows` rows.
 void launch_zero_cols(const CubeDst& d, i64 rows, int k0, int kind, cudaStream_t s);
 // Second phase of a two-phase scatter: for each row m of the dense FP32 result X

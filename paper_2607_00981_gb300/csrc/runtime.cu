@@ -240,6 +240,21 @@ struct rccsdt_ctx {
   int a3_Z = 1;
   int a3_direct = 0;  // batches whose split-body panels are gathered from T3 (all of them, or none used)
   std::vector<GemmPlan*> p_pp, p_hh, p_ringab, p_ringc, p_t2a;
+  // pp-ladder of the per-plan engine on pair-symmetric operands (pair_pack.cu): the
+  // sum and difference parts of each view of a block range, two GEMMs per unit
+  struct PpSym {
+    int on = 0, nchunk = 0, Kp = 0, Km = 0, Kpadp = 0, Kpadm = 0;
+    std::unique_ptr<DBuf> chunks, rows;  // PairChunk[nchunk], int4[Kp] (x, y, row of the difference)
+    std::unique_ptr<DBuf> rb[3][2], rb2[3][2], al[2], al2[2], sel;  // per view / part: row tables
+    struct Unit {
+      int term = 0, nblk = 0, N = 0;
+      i64 b0 = 0;
+      std::unique_ptr<DBuf> col;  // [N] column offsets into R3
+      rcc::EpiArgs e[2]{};        // sum and difference GEMMs
+      double fma[2] = {0, 0};
+    };
+    std::vector<std::unique_ptr<Unit>> units;
+  } pps;
   // combines
   std::vector<rcc::CombineArgs> c_fock, c_helpers, c_int_base, c_r12_base, c_r2_sym, c_wt;
   rcc::CombineArgs c_Lt_copy{}, c_ft_copy{};
@@ -387,6 +402,107 @@ void finish_plan(rccsdt_ctx* c, GemmPlan* g, int K) {
   size_t need = (size_t)std::max(g->A.a.R, g->B.a.R) * g->Kpad * 8;
   if (need > c->panel_bytes) c->panel_bytes = need;
   c->panel_rows = std::max(c->panel_rows, std::max(g->A.a.R, g->B.a.R));
+}
+
+// Tables of the pair-symmetric pp-ladder (see PpSym): tile-major pair numbering,
+// W panel rows, per-view epilogue rows (each x <= y writes (x, y) and, mirrored,
+// (y, x)), and units of the same block ranges as the plain plans.
+void build_pp_sym(rccsdt_ctx* c, bool t3f, void* r3p, int* err) {
+  auto& S = c->pps;
+  const int v = c->v;
+  const i64 V2 = (i64)v * v, V3 = c->V3;
+  const int nt = (v + 15) / 16;
+  std::vector<rcc::PairChunk> ch;
+  std::vector<std::array<int, 2>> pp, pm;  // pairs of the sum and difference columns
+  int offp = 0, offm = 0;
+  for (int P = 0; P < nt; ++P)
+    for (int Q = P; Q < nt; ++Q) {
+      const int nd = std::min(16, v - 16 * P), ne = std::min(16, v - 16 * Q);
+      const bool diag = P == Q;
+      ch.push_back({P, Q, offp, offm});
+      const int np = diag ? nd * (nd + 1) / 2 : nd * ne, nm = diag ? nd * (nd - 1) / 2 : nd * ne;
+      for (int t = 0; t < np; ++t) {
+        int a, b;
+        rcc::pair_decode(t, diag, true, nd, ne, a, b);
+        pp.push_back({16 * P + a, 16 * Q + b});
+      }
+      for (int t = 0; t < nm; ++t) {
+        int a, b;
+        rcc::pair_decode(t, diag, false, nd, ne, a, b);
+        pm.push_back({16 * P + a, 16 * Q + b});
+      }
+      offp += np;
+      offm += nm;
+    }
+  S.nchunk = (int)ch.size();
+  S.Kp = offp;
+  S.Km = offm;
+  S.Kpadp = round_up(S.Kp, 64);
+  S.Kpadm = round_up(S.Km, 64);
+  std::vector<int> mrow((size_t)V2, -1);
+  for (int q = 0; q < S.Km; ++q) mrow[(size_t)pm[q][0] * v + pm[q][1]] = q;
+  std::vector<int4> rows(S.Kp);
+  for (int q = 0; q < S.Kp; ++q) rows[q] = make_int4(pp[q][0], pp[q][1], mrow[(size_t)pp[q][0] * v + pp[q][1]], 0);
+  S.chunks = upload_vec(c, ch, err);
+  S.rows = upload_vec(c, rows, err);
+  // R3 offset of the result element (x, y, w) of view `term` is ebase(x, y) + col(blk, w)
+  auto ebase = [&](int term, i64 x, i64 y) { return term == 0 ? x * V2 + y * v : term == 1 ? x * V2 + y : x * v + y; };
+  for (int part = 0; part < 2; ++part) {
+    const auto& pr = part == 0 ? pp : pm;
+    const size_t M = pr.size();
+    for (int term = 0; term < 3; ++term) {
+      std::vector<i64> rb(M), rb2(M);
+      for (size_t q = 0; q < M; ++q) {
+        rb[q] = ebase(term, pr[q][0], pr[q][1]);
+        rb2[q] = pr[q][0] == pr[q][1] ? -1 : ebase(term, pr[q][1], pr[q][0]);
+      }
+      S.rb[term][part] = upload_vec(c, rb, err);
+      S.rb2[term][part] = upload_vec(c, rb2, err);
+    }
+    S.al[part] = upload_vec(c, std::vector<double>(std::max<size_t>(M, 1), 0.5), err);
+    S.al2[part] = upload_vec(c, std::vector<double>(std::max<size_t>(M, 1), part == 0 ? 0.5 : -0.5), err);
+  }
+  S.sel = upload_vec(c, std::vector<int>(std::max(S.Kp, 1), 0), err);
+  const i64 per_blk = (i64)v * round_up((int)V2, 64) * 8;
+  const i64 nb = std::max<i64>(1, std::min<i64>(c->n3, (2LL << 30) / per_blk));
+  int maxN = 0;
+  for (int term = 0; term < 3; ++term)
+    for (i64 b0 = 0; b0 < c->n3; b0 += nb) {
+      auto u = std::make_unique<rccsdt_ctx::PpSym::Unit>();
+      u->term = term;
+      u->b0 = b0;
+      u->nblk = (int)(std::min(c->n3, b0 + nb) - b0);
+      u->N = u->nblk * v;
+      maxN = std::max(maxN, u->N);
+      std::vector<i64> col(u->N);
+      for (int q = 0; q < u->N; ++q) {
+        const i64 blk = b0 + q / v, w = q % v;
+        col[q] = blk * V3 + (term == 0 ? w : term == 1 ? w * v : w * V2);
+      }
+      u->col = upload_vec(c, col, err);
+      for (int part = 0; part < 2; ++part) {
+        rcc::EpiArgs& e = u->e[part];
+        e.C = r3p;
+        e.c_f32 = t3f ? 1 : 0;
+        e.M = part == 0 ? S.Kp : S.Km;
+        e.N = u->N;
+        e.row_base = (const i64*)S.rb[term][part]->p;
+        e.row_sel = (const int*)S.sel->p;
+        e.row_alpha = (const double*)S.al[part]->p;
+        e.col_off = (const i64*)u->col->p;
+        e.row_base2 = (const i64*)S.rb2[term][part]->p;
+        e.row_alpha2 = (const double*)S.al2[part]->p;
+        const int K = part == 0 ? S.Kp : S.Km;
+        u->fma[part] = (double)e.M * e.N * K;
+      }
+      S.units.push_back(std::move(u));
+    }
+  // engine panels: both A parts side by side, both B parts side by side
+  const size_t needA = ((size_t)S.Kp * S.Kpadp + (size_t)S.Km * S.Kpadm) * 8;
+  const size_t needB = (size_t)maxN * (S.Kpadp + S.Kpadm) * 8;
+  c->panel_bytes = std::max(c->panel_bytes, std::max(needA, needB));
+  c->panel_rows = std::max(c->panel_rows, std::max(S.Kp + S.Km, 2 * maxN));
+  S.on = 1;
 }
 
 // The allocation holding p (start pointer and element offset of p in it).
@@ -772,6 +888,81 @@ static int run_plans(rccsdt_ctx* c, const std::vector<GemmPlan*>& ps) {
     int st = run_gemm(c, g);
     if (st) return st;
   }
+  return 0;
+}
+
+// pp-ladder on pair-symmetric operands: the two W panels once, then per unit the
+// two T panels of its view and the sum and difference GEMMs (tensor cores in the
+// split modes; FP64 on the tensor cores or the FP64 units otherwise).
+static int run_pp_sym(rccsdt_ctx* c) {
+  auto& S = c->pps;
+  const int v = c->v;
+  const i64 V2 = (i64)v * v;
+  const bool tc = c->precision != RCCSDT_FP64;
+  const int kind = !tc ? rcc::PANEL_F64 : (c->precision == RCCSDT_SPLIT_BF16X3 ? rcc::PANEL_BF16X2 : rcc::PANEL_TF32X2);
+  const size_t esz = kind == rcc::PANEL_F64 ? 8 : (kind == rcc::PANEL_BF16X2 ? 2 : 4);
+  const bool f64e = !tc && c->opt.f64_tc && c->planesA && !S.units.empty() &&
+                    (c->opt.f64_tc == 2 || S.units[0]->fma[0] >= 3e7);
+  char* ahi = (char*)c->panelA_hi->p;
+  char* alo = c->panelA_lo ? (char*)c->panelA_lo->p : nullptr;
+  char* bhi = (char*)c->panelB_hi->p;
+  char* blo = c->panelB_lo ? (char*)c->panelB_lo->p : nullptr;
+  const size_t aoff = (size_t)S.Kp * S.Kpadp * esz;
+  const rcc::CubeDst Ap{ahi, alo, S.Kpadp}, Am{ahi + aoff, alo ? alo + aoff : nullptr, S.Kpadm};
+  const auto* ch = (const rcc::PairChunk*)S.chunks->p;
+  // the shared panels hold other operands afterwards
+  c->packedA_kind = c->packedB_kind = -1;
+  c->slicedA = c->slicedB = 0;
+  rcc::launch_pair_pack_w(kind, c->D("Wvvvv"), v, (const int4*)S.rows->p, S.Kp, ch, S.nchunk, S.Kp, S.Km, Ap, Am,
+                          c->stream);
+  char* pA[2] = {nullptr, nullptr};
+  int* eA[2] = {nullptr, nullptr};
+  if (f64e) {
+    pA[0] = (char*)c->planesA->p;
+    pA[1] = pA[0] + (size_t)rcc::kSlices * S.Kp * S.Kpadp * 2;
+    eA[0] = (int*)c->expA->p;
+    eA[1] = eA[0] + S.Kp;
+    rcc::launch_slice_f64((const double*)Ap.out_hi, S.Kp, S.Kpadp, pA[0], eA[0], c->stream);
+    if (S.Km) rcc::launch_slice_f64((const double*)Am.out_hi, S.Km, S.Kpadm, pA[1], eA[1], c->stream);
+  }
+  int* flag = (int*)((double*)c->scalars->p + 1000);
+  const i64 sd[3] = {V2, V2, v}, se[3] = {v, 1, 1}, sw[3] = {1, v, V2};
+  const bool t3f = c->opt.precision != RCCSDT_FP64;
+  for (auto& up : S.units) {
+    auto& u = *up;
+    const size_t boff = (size_t)u.N * S.Kpadp * esz;
+    const rcc::CubeDst Bp{bhi, blo, S.Kpadp}, Bm{bhi + boff, blo ? blo + boff : nullptr, S.Kpadm};
+    rcc::launch_pair_pack_t(kind, c->B("t3")->p, t3f ? 1 : 0, u.b0, u.nblk, v, sd[u.term], se[u.term], sw[u.term], ch,
+                            S.nchunk, S.Kp, S.Km, Bp, Bm, c->stream);
+    for (int part = 0; part < 2; ++part) {
+      const int K = part ? S.Km : S.Kp, Kpad = part ? S.Kpadm : S.Kpadp;
+      if (K == 0) continue;
+      const rcc::CubeDst& A = part ? Am : Ap;
+      const rcc::CubeDst& Bq = part ? Bm : Bp;
+      const rcc::EpiArgs& e = u.e[part];
+      const int tidx = timer_begin(c, 16, 2.0 * u.fma[part]);
+      int lst = 0;
+      if (f64e) {
+        rcc::launch_slice_f64((const double*)Bq.out_hi, u.N, Kpad, c->planesB->p, (int*)c->expB->p, c->stream);
+        lst = rcc::launch_gemm_f64e(pA[part], eA[part], c->planesB->p, (const int*)c->expB->p, Kpad, e, flag,
+                                    c->opt.watchdog_cycles, c->stream);
+      } else if (!tc) {
+        rcc::launch_gemm_f64((const double*)A.out_hi, (const double*)Bq.out_hi, round_up(K, 16), Kpad, Kpad, e,
+                             c->concurrent ? nullptr : c->splitk->d(), (i64)(c->splitk->bytes / 8), c->stream);
+      } else {
+        const int bn = e.N <= 128 ? 128 : (e.N <= 144 ? 144 : 256);
+        lst = rcc::launch_gemm_tc(kind, A.out_hi, A.out_lo, Bq.out_hi, Bq.out_lo, Kpad, e, flag, c->opt.watchdog_cycles,
+                                  c->stream, c->concurrent ? nullptr : (float*)c->splitk->p,
+                                  (long long)(c->splitk->bytes / 4), nullptr, bn);
+      }
+      timer_end(c, tidx);
+      if (lst) return fail(c, RCCSDT_ERR_ARG, "pair-symmetric pp-ladder GEMM configuration unsupported");
+    }
+  }
+#ifndef RCC_HOSTSIM
+  const cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) return fail(c, RCCSDT_ERR_CUDA, std::string("pp-ladder: ") + cudaGetErrorString(ce));
+#endif
   return 0;
 }
 
@@ -1272,6 +1463,7 @@ int build_context(rccsdt_ctx* c) {
         }
         c->p_pp.push_back(g);
       }
+    build_pp_sym(c, t3f, r3p, &err);
   }
 
   // --- hh-ladder (with F_oo folded in), unit k: rows (i<=j), cols abc, K = (l,m)
@@ -1943,7 +2135,7 @@ int do_residual(rccsdt_ctx* c) {
   } else {
     {
       StepTimer tm(c, 1);
-      if ((st = run_plans(c, c->p_pp))) return st;
+      if ((st = c->pps.on ? run_pp_sym(c) : run_plans(c, c->p_pp))) return st;
     }
     {
       StepTimer tm(c, 2);

@@ -115,6 +115,74 @@ void launch_cube_pack(int mode, int kind, const CubePiece* pieces, int npieces, 
   }
 }
 
+void launch_pair_pack_w(int kind, const double* W, int v, const int4* rows, int Mp, const PairChunk* ch, int nchunk,
+                        int Kp, int Km, const CubeDst& dp, const CubeDst& dm, cudaStream_t) {
+  const i64 V2 = (i64)v * v;
+  for (int m = 0; m < Mp; ++m) {
+    const int4 rw = rows[m];
+    const double* Wr = W + ((i64)rw.x * v + rw.y) * V2;
+    for (int ci = 0; ci < nchunk; ++ci) {
+      const PairChunk c = ch[ci];
+      const int d0 = c.P * 16, e0 = c.Q * 16, nd = std::min(16, v - d0), ne = std::min(16, v - e0);
+      const bool diag = c.P == c.Q;
+      const int np = diag ? nd * (nd + 1) / 2 : nd * ne, nm = diag ? nd * (nd - 1) / 2 : nd * ne;
+      for (int t = 0; t < np; ++t) {
+        int a, b;
+        pair_decode(t, diag, true, nd, ne, a, b);
+        const int d = d0 + a, e = e0 + b;
+        const double x = d == e ? Wr[(i64)d * v + d] : Wr[(i64)d * v + e] + Wr[(i64)e * v + d];
+        panel_put(kind, dp.out_hi, dp.out_lo, (i64)m * dp.Kpad + c.offp + t, x);
+      }
+      if (rw.z >= 0)
+        for (int t = 0; t < nm; ++t) {
+          int a, b;
+          pair_decode(t, diag, false, nd, ne, a, b);
+          const int d = d0 + a, e = e0 + b;
+          panel_put(kind, dm.out_hi, dm.out_lo, (i64)rw.z * dm.Kpad + c.offm + t,
+                    Wr[(i64)d * v + e] - Wr[(i64)e * v + d]);
+        }
+    }
+    for (int k = Kp; k < dp.Kpad; ++k) panel_put(kind, dp.out_hi, dp.out_lo, (i64)m * dp.Kpad + k, 0.0);
+    if (rw.z >= 0)
+      for (int k = Km; k < dm.Kpad; ++k) panel_put(kind, dm.out_hi, dm.out_lo, (i64)rw.z * dm.Kpad + k, 0.0);
+  }
+}
+
+void launch_pair_pack_t(int kind, const void* t3, int t3_f32, i64 b0, int nblk, int v, i64 sd, i64 se, i64 sw,
+                        const PairChunk* ch, int nchunk, int Kp, int Km, const CubeDst& dp, const CubeDst& dm,
+                        cudaStream_t) {
+  const i64 V3 = (i64)v * v * v;
+  for (int q = 0; q < nblk; ++q) {
+    const i64 base = (b0 + q) * V3;
+    auto T = [&](int d, int e, int w) { return load_src(t3, t3_f32, base + d * sd + e * se + w * sw); };
+    for (int w = 0; w < v; ++w) {
+      const i64 row = (i64)q * v + w;
+      for (int ci = 0; ci < nchunk; ++ci) {
+        const PairChunk c = ch[ci];
+        const int d0 = c.P * 16, e0 = c.Q * 16, nd = std::min(16, v - d0), ne = std::min(16, v - e0);
+        const bool diag = c.P == c.Q;
+        const int np = diag ? nd * (nd + 1) / 2 : nd * ne, nm = diag ? nd * (nd - 1) / 2 : nd * ne;
+        for (int t = 0; t < np; ++t) {
+          int a, b;
+          pair_decode(t, diag, true, nd, ne, a, b);
+          const double x = kind == PANEL_F64 ? T(d0 + a, e0 + b, w) + T(e0 + b, d0 + a, w)
+                                             : (double)((float)T(d0 + a, e0 + b, w) + (float)T(e0 + b, d0 + a, w));
+          panel_put(kind, dp.out_hi, dp.out_lo, row * dp.Kpad + c.offp + t, x);
+        }
+        for (int t = 0; t < nm; ++t) {
+          int a, b;
+          pair_decode(t, diag, false, nd, ne, a, b);
+          const double x = kind == PANEL_F64 ? T(d0 + a, e0 + b, w) - T(e0 + b, d0 + a, w)
+                                             : (double)((float)T(d0 + a, e0 + b, w) - (float)T(e0 + b, d0 + a, w));
+          panel_put(kind, dm.out_hi, dm.out_lo, row * dm.Kpad + c.offm + t, x);
+        }
+      }
+      for (int k = Kp; k < dp.Kpad; ++k) panel_put(kind, dp.out_hi, dp.out_lo, row * dp.Kpad + k, 0.0);
+      for (int k = Km; k < dm.Kpad; ++k) panel_put(kind, dm.out_hi, dm.out_lo, row * dm.Kpad + k, 0.0);
+    }
+  }
+}
+
 void launch_cube_pack_r1(int kind, const CubePiece* pieces, int npieces, const CubeDst& d0,
                          const float* src, int v, const float* w, const i64* wbase, float* part, cudaStream_t st) {
   launch_cube_pack(0, kind, pieces, npieces, nullptr, d0, src, v, st);

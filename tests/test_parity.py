@@ -26,8 +26,9 @@ def _ctx(kind, o, v, naux, **kw):
     return B.Context(_lib(kind), o, v, naux, **kw)
 
 
-# sizes span several 64-wide tiles with ragged tails on the GPU and hit o = 1 / v = 1
-SHAPES = [(3, 4, 8), (2, 7, 10), (4, 5, 12), (1, 6, 6), (3, 1, 4), (3, 12, 40), (5, 9, 20)]
+# sizes span several 64-wide tiles with ragged tails on the GPU, three 16-label pair tiles
+# (v = 35, the last ragged) and hit o = 1 / v = 1
+SHAPES = [(3, 4, 8), (2, 7, 10), (4, 5, 12), (1, 6, 6), (3, 1, 4), (3, 12, 40), (5, 9, 20), (2, 35, 16)]
 
 
 @pytest.mark.parametrize("kind", BACKENDS)

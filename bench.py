@@ -418,13 +418,14 @@ def run_ours(args, rank, world):
         else:
             peak, bound, src = pk.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25) / 3.0, "tensor", \
                 "measured bf16 sustained x nominal tf32/bf16 ratio / 3"
-        # DRAM bytes of one pp-ladder launch from an ncu capture of this workload and
-        # precision (profiles/k_gemm_tc_pp_o16v160w_traffic.md); other runs have none
-        traffic = 29.86e9 if (args.workload == "o16v160w" and prec == 1) else None
+        # DRAM bytes per pp-ladder launch (mean of one sum and one difference GEMM) from an
+        # ncu capture of this workload and precision (profiles/k_gemm_tc_pp_o16v160w_traffic.md);
+        # other runs have none
+        traffic = 9.79e9 if (args.workload == "o16v160w" and prec == 1) else None
         roof = {"kernel": "pp-ladder GEMM (k_gemm_f64)" if prec == 0 else "pp-ladder GEMM (k_gemm_tc)",
                 "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, first "
-                "pp-ladder launch (61 stored blocks)" if traffic else None, "peak_source": src,
+                "traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of "
+                "the sum and difference GEMMs of one pp-ladder unit (65 stored blocks)" if traffic else None, "peak_source": src,
                 "launches": int(gemm_n), "avg_launch_ms": gemm_ms / gemm_n}
 
     step_ms = {k: float(x) / args.steps for k, x in zip(

@@ -39,14 +39,17 @@ def main(argv=None):
     ap.add_argument("--diis-space", type=int, default=8)
     ap.add_argument("--refine-fp64", action="store_true", help="re-converge in an FP64 context afterwards")
     ap.add_argument("--refine-diis", type=int, default=2)
+    ap.add_argument("--grouped-bytes", type=int, default=None,
+                    help="memory budget of the grouped residual of split contexts (0: per-plan engine)")
     args = ap.parse_args(argv)
     spec = dict(WORKLOADS.get(args.workload) or CONVERGENCE[args.workload])
     if args.scale is not None:
         spec["scale"] = args.scale
     inst = make_instance(**spec)
     prec = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}[args.precision]
+    extra = {} if args.grouped_bytes is None else {"grouped_bytes": args.grouped_bytes}
     ctx = pkg.context(inst.o, inst.v, inst.naux, precision=prec, diis_t3=0 if args.no_diis_t3 else 1,
-                      f64_tc=args.f64_tc, tol=args.tol, max_iter=args.max_iter, diis_space=args.diis_space)
+                      f64_tc=args.f64_tc, tol=args.tol, max_iter=args.max_iter, diis_space=args.diis_space, **extra)
     ctx.set_hamiltonian(inst.fock_diag, inst.L)
     ctx.init_mp2()
     if args.solve:

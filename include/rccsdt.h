@@ -95,7 +95,10 @@ int rccsdt_options_default(rccsdt_options* opt);
 /* Creates a context for o occupied / v virtual orbitals and naux factors, on the
  * CUDA stream `stream` (a cudaStream_t, NULL = legacy default stream) of the
  * current device.  Allocates all device memory the iteration needs.
- * Errors: RCCSDT_ERR_ARG (o, v, naux < 1 or out == NULL), RCCSDT_ERR_OOM. */
+ * Limits: o <= 64, v <= 1024 (offsets inside one v^3 block are 32-bit; W^{ab}_{cd}
+ * alone, v^4 doubles, exceeds any device's memory well before that).
+ * Errors: RCCSDT_ERR_ARG (o, v, naux < 1, o or v above the limits, or out == NULL),
+ * RCCSDT_ERR_OOM. */
 int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, void* stream,
                   rccsdt_ctx** out);
 

@@ -38,11 +38,11 @@ __device__ __forceinline__ void store_run(const CubeDst& d, i64 row, int k, cons
       uint32_t h[8], l[8];  // bf16 pairs, first element in the low half
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * j]), h1 = __float2bfloat16_rn(x[2 * j + 1]);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * j] - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * j + 1] - __bfloat162float(h1));
-        h[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        l[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        const __nv_bfloat162 hp = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+        const float2 hf = __bfloat1622float2(hp);
+        const __nv_bfloat162 lp = __floats2bfloat162_rn(x[2 * j] - hf.x, x[2 * j + 1] - hf.y);
+        h[j] = *reinterpret_cast<const uint32_t*>(&hp);
+        l[j] = *reinterpret_cast<const uint32_t*>(&lp);
       }
       ((uint4*)hi)[0] = make_uint4(h[0], h[1], h[2], h[3]);
       ((uint4*)hi)[1] = make_uint4(h[4], h[5], h[6], h[7]);
@@ -102,7 +102,9 @@ __global__ void __launch_bounds__(256) k_cube_pack_k(const CubePiece* __restrict
                                                      float* __restrict__ part) {
   constexpr int TL = 16, CA = (TL + 1) * (TL + 2), CB = TL + 2;
   extern __shared__ __align__(16) float cube_smem[];
-  __shared__ float wA[R1 ? TL : 1][TL + 1], wB[R1 ? TL : 1][TL + 1], red[R1 ? TL : 1][TL + 1];
+  // R1 weights transposed (wAT[e2][e1], wBT[e3][e1]; rows of 20 floats, 16-byte aligned)
+  __shared__ __align__(16) float wAT[R1 ? TL : 1][TL + 4], wBT[R1 ? TL : 1][TL + 4];
+  __shared__ float red[R1 ? TL : 1][TL + 1];
   const CubePiece& P = pieces[blockIdx.y];
   const int nterm = P.nterm;
   const int nc = (v + TL - 1) / TL;
@@ -113,8 +115,8 @@ __global__ void __launch_bounds__(256) k_cube_pack_k(const CubePiece* __restrict
     // weights v^{xy}_{e1 e2} and v^{xy}_{e1 e3} of this cube (zero outside v)
     const float* wp = w + wbase[blockIdx.y];
     const int e1 = lo[0] + lm;
-    wA[lm][lf] = (e1 < v && lo[1] + lf < v) ? wp[(i64)e1 * v + lo[1] + lf] : 0.f;
-    wB[lm][lf] = (e1 < v && lo[2] + lf < v) ? wp[(i64)e1 * v + lo[2] + lf] : 0.f;
+    wAT[lf][lm] = (e1 < v && lo[1] + lf < v) ? wp[(i64)e1 * v + lo[1] + lf] : 0.f;
+    wBT[lf][lm] = (e1 < v && lo[2] + lf < v) ? wp[(i64)e1 * v + lo[2] + lf] : 0.f;
   }
   for (int t = 0; t < nterm; ++t) {
     const int pos = P.t[t].pos;
@@ -122,17 +124,23 @@ __global__ void __launch_bounds__(256) k_cube_pack_k(const CubePiece* __restrict
     // label on the stored unit-stride axis, then the other two
     const int fast = p0 == 2 ? 0 : (p1 == 2 ? 1 : 2);
     const int mid = fast == 0 ? 1 : 0, slow = 3 - fast - mid;
-    const i64 sm = axis_stride(pos_of(pos, mid), v), ss = axis_stride(pos_of(pos, slow), v);
+    // offsets inside one stored block in 32 bits (v^3 < 2^31 for every accepted v)
+    const int sm = (int)axis_stride(pos_of(pos, mid), v), ss = (int)axis_stride(pos_of(pos, slow), v);
     const int cf = fast == 0 ? CA : (fast == 1 ? CB : 1), cmid = mid == 0 ? CA : (mid == 1 ? CB : 1),
               cs = slow == 0 ? CA : (slow == 1 ? CB : 1);
     const int xf = (fast == 0 ? lo[0] : fast == 1 ? lo[1] : lo[2]) + lf;
     const int xm = (mid == 0 ? lo[0] : mid == 1 ? lo[1] : lo[2]) + lm;
     const int xs = slow == 0 ? lo[0] : slow == 1 ? lo[1] : lo[2];
-    const bool in = xf < v && xm < v;
-    const float* s0 = src + P.t[t].base + xf + xm * sm + (i64)xs * ss;
+    const int nrun = (xf < v && xm < v) ? min(TL, v - xs) : 0;  // valid labels along the slow axis
+    const float* s0 = src + P.t[t].base + (xf + xm * sm + xs * ss);
     float ld[TL];
+    if (nrun == TL) {
 #pragma unroll
-    for (int u = 0; u < TL; ++u) ld[u] = (in && xs + u < v) ? __ldg(s0 + u * ss) : 0.f;
+      for (int u = 0; u < TL; ++u) ld[u] = __ldg(s0 + u * ss);
+    } else {
+#pragma unroll
+      for (int u = 0; u < TL; ++u) ld[u] = u < nrun ? __ldg(s0 + u * ss) : 0.f;
+    }
     float* c = cube_smem + lf * cf + lm * cmid;
     const float coef = P.t[t].coef;
     if (t == 0) {
@@ -157,9 +165,17 @@ __global__ void __launch_bounds__(256) k_cube_pack_k(const CubePiece* __restrict
     // labels outside v hold zeros in the cube, so every thread takes part
     float sa = 0.f, sb = 0.f;
 #pragma unroll
-    for (int u = 0; u < TL; ++u) {
-      sa = fmaf(wA[u][lm], x[u], sa);
-      sb = fmaf(wB[u][lf], x[u], sb);
+    for (int q = 0; q < TL / 4; ++q) {
+      const float4 a4 = reinterpret_cast<const float4*>(&wAT[lm][0])[q];
+      const float4 b4 = reinterpret_cast<const float4*>(&wBT[lf][0])[q];
+      sa = fmaf(a4.x, x[4 * q], sa);
+      sa = fmaf(a4.y, x[4 * q + 1], sa);
+      sa = fmaf(a4.z, x[4 * q + 2], sa);
+      sa = fmaf(a4.w, x[4 * q + 3], sa);
+      sb = fmaf(b4.x, x[4 * q], sb);
+      sb = fmaf(b4.y, x[4 * q + 1], sb);
+      sb = fmaf(b4.z, x[4 * q + 2], sb);
+      sb = fmaf(b4.w, x[4 * q + 3], sb);
     }
 #pragma unroll
     for (int off = 8; off > 0; off >>= 1) sb += __shfl_xor_sync(0xffffffffu, sb, off);  // over e3 (lf)
@@ -191,7 +207,8 @@ __global__ void __launch_bounds__(256) k_cube_pack_col(const CubePiece* __restri
                                                        const float* __restrict__ src, int v) {
   constexpr int TL = 8, CS = TL * TL * (TL + 1) + 1;  // one padded 8^3 cube per column
   __shared__ float cols[16 * CS];
-  __shared__ i64 g_off[16], g_sm[16], g_ss[16];
+  __shared__ i64 g_off[16];
+  __shared__ int g_sm[16], g_ss[16];  // strides inside one stored block (v^3 < 2^31)
   __shared__ int g_n[16], g_map[16];
   __shared__ float g_coef[16];
   const int nc = (v + TL - 1) / TL;
@@ -211,8 +228,8 @@ __global__ void __launch_bounds__(256) k_cube_pack_col(const CubePiece* __restri
     const int lm = mid == 0 ? lo[0] : (mid == 1 ? lo[1] : lo[2]);
     const int ls = slow == 0 ? lo[0] : (slow == 1 ? lo[1] : lo[2]);
     g_off[tid] = P.t[0].base + lf + lm * sm + (i64)ls * ss;
-    g_sm[tid] = sm;
-    g_ss[tid] = ss;
+    g_sm[tid] = (int)sm;
+    g_ss[tid] = (int)ss;
     // valid extents along fast, mid, slow (8 bits each; 0 for a zero column)
     const int nf = P.nterm > 0 ? min(TL, v - lf) : 0, nm = min(TL, v - lm), ns = min(TL, v - ls);
     g_n[tid] = nf | (nm << 8) | (ns << 16);
@@ -223,7 +240,8 @@ __global__ void __launch_bounds__(256) k_cube_pack_col(const CubePiece* __restri
   float ld[16][2];
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
-    const i64 off = g_off[c], sm = g_sm[c], ss = g_ss[c];
+    const float* base = src + g_off[c];
+    const int sm = g_sm[c], ss = g_ss[c];
     const int n = g_n[c];
     const float cf = g_coef[c];
 #pragma unroll
@@ -231,7 +249,7 @@ __global__ void __launch_bounds__(256) k_cube_pack_col(const CubePiece* __restri
       const int e = tid + 256 * h;  // (slow, mid, fast) of 8^3
       const int uf = e & 7, um = (e >> 3) & 7, us = e >> 6;
       const bool ok = uf < (n & 255) && um < ((n >> 8) & 255) && us < (n >> 16);
-      ld[c][h] = ok ? cf * __ldg(src + off + uf + um * sm + us * ss) : 0.f;
+      ld[c][h] = ok ? cf * __ldg(base + (uf + um * sm + us * ss)) : 0.f;
     }
   }
   // stage by label order (L0, L1, L2), whatever the load order was

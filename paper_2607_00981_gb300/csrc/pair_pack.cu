@@ -113,12 +113,26 @@ __global__ void __launch_bounds__(256) k_pair_pack_t(const TS* __restrict__ t3, 
   const int nd = min(kPT, v - d0), ne = min(kPT, v - e0), nw = min(kPT, v - w0);
   const bool diag = c.P == c.Q;
   const bool wfast = sw == 1;
-  for (int i = threadIdx.x; i < kPT * kPT * kPT; i += blockDim.x) {
-    const int f = i & 15, g = (i >> 4) & 15, a = i >> 8;
+  {
+    // thread (f, g) holds the labels (b, w) (the unit-stride one on f) and reads the
+    // 16 values of a of both cubes; every load is issued before any is stored
+    const int f = threadIdx.x & 15, g = threadIdx.x >> 4;
     const int b = wfast ? g : f, w = wfast ? f : g;
-    if (w < nw) {
-      if (a < nd && b < ne) X[(a * kPS + b) * kPS + w] = T[(d0 + a) * sd + (e0 + b) * se + (w0 + w) * sw];
-      if (!diag && a < ne && b < nd) Y[(a * kPS + b) * kPS + w] = T[(e0 + a) * sd + (d0 + b) * se + (w0 + w) * sw];
+    const bool inx = w < nw && b < ne, iny = !diag && w < nw && b < nd;
+    const TS* px = T + (i64)d0 * sd + (e0 + b) * se + (w0 + w) * sw;
+    const TS* py = T + (i64)e0 * sd + (d0 + b) * se + (w0 + w) * sw;
+    TS vx[kPT], vy[kPT];
+#pragma unroll
+    for (int a = 0; a < kPT; ++a) vx[a] = (inx && a < nd) ? __ldg(px + a * sd) : (TS)0;
+#pragma unroll
+    for (int a = 0; a < kPT; ++a) vy[a] = (iny && a < ne) ? __ldg(py + a * sd) : (TS)0;
+    TS* x = X + b * kPS + w;
+    TS* y = Y + b * kPS + w;
+#pragma unroll
+    for (int a = 0; a < kPT; ++a) x[a * kPS * kPS] = vx[a];
+    if (!diag) {
+#pragma unroll
+      for (int a = 0; a < kPT; ++a) y[a * kPS * kPS] = vy[a];
     }
   }
   __syncthreads();

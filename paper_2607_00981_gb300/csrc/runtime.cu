@@ -2322,7 +2322,7 @@ RCC_API int rccsdt_options_default(rccsdt_options* opt) {
 RCC_API int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, void* stream, rccsdt_ctx** out) {
   if (!out) return RCCSDT_ERR_ARG;
   *out = nullptr;
-  if (o < 1 || v < 1 || naux < 1 || o > 64 || v > 4096) return RCCSDT_ERR_ARG;
+  if (o < 1 || v < 1 || naux < 1 || o > 64 || v > 1024) return RCCSDT_ERR_ARG;
   rccsdt_options def;
   rccsdt_options_default(&def);
   const rccsdt_options& op = opt ? *opt : def;

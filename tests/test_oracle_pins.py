@@ -244,3 +244,33 @@ def test_diis_solves_a_linear_fixed_point():
         d.push(xn, xn - x)
         x = d.extrapolate()
     assert np.allclose(x, np.linalg.solve(np.eye(n) - A, b), atol=1e-10)
+
+
+def test_pp_ladder_intermediate_is_pair_symmetric():
+    """W^{ab}_{de} = W^{ba}_{ed} at generic (non-converged) amplitudes, and the sum /
+    difference split over that exchange reproduces the plain pp-ladder view
+    X^{xy}(w) = sum_de W^{xy}_{de} T(d, e, w) (Sec. II.C.1): the premise of the
+    library's pair-symmetric pp-ladder GEMMs, checked on the oracle's intermediate."""
+    o, v = 3, 7
+    inst = make_instance(o, v, naux=20, seed=3)
+    t1, t2, t3 = random_amplitudes(o, v, seed=5)
+    *_, I = C.residuals_compact(inst.L, inst.fock_diag, t1, t2, C.pack(t3), return_intermediates=True)
+    W = I["Wvvvv"]
+    scale = max(1.0, np.abs(W).max())
+    assert np.abs(W - W.transpose(1, 0, 3, 2)).max() < 1e-14 * scale
+    T = np.random.default_rng(9).standard_normal((v, v, v))
+    X = np.einsum("xyde,dew->xyw", W, T)
+    du, eu = np.triu_indices(v)          # pairs d <= e
+    dl, el = np.triu_indices(v, 1)       # pairs d < e
+    Wp = W[:, :, du, eu] + np.where(du == eu, 0.0, 1.0) * W[:, :, eu, du]
+    Tp = T[du, eu, :] + T[eu, du, :]
+    Wm = W[:, :, dl, el] - W[:, :, el, dl]
+    Tm = T[dl, el, :] - T[el, dl, :]
+    Xp = np.einsum("xyk,kw->xyw", Wp, Tp)
+    Xm = np.einsum("xyk,kw->xyw", Wm, Tm)
+    Xs = X + X.transpose(1, 0, 2)
+    Xd = X - X.transpose(1, 0, 2)
+    assert np.abs(Xp - Xs).max() < 1e-12 * max(1.0, np.abs(Xs).max())
+    assert np.abs(Xm - Xd).max() < 1e-12 * max(1.0, np.abs(Xd).max())
+    # the recombination the epilogue performs: X^{xy} = (X+ + X-) / 2
+    assert np.abs(0.5 * (Xp + Xm) - X).max() < 1e-12 * max(1.0, np.abs(X).max())

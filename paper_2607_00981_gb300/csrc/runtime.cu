@@ -439,16 +439,33 @@ void build_pp_sym(rccsdt_ctx* c, bool t3f, void* r3p, int* err) {
   S.Km = offm;
   S.Kpadp = round_up(S.Kp, 64);
   S.Kpadm = round_up(S.Km, 64);
+  // GEMM row orders (independent of the K numbering): full 4 x 8 blocks of (x, y)
+  // first, y fastest, so that the 32 rows of an epilogue warp write 8-element runs
+  // along y for (x, y) and 4-element runs along x for the mirrored (y, x); then the
+  // pairs of the partial blocks
+  auto row_order = [&](bool plus) {
+    std::vector<std::array<int, 2>> full, rest;
+    for (int x0 = 0; x0 < v; x0 += 4)
+      for (int y0 = 0; y0 < v; y0 += 8) {
+        const bool whole = x0 + 4 <= v && y0 + 8 <= v && (plus ? x0 + 3 <= y0 : x0 + 3 < y0);
+        for (int x = x0; x < std::min(x0 + 4, v); ++x)
+          for (int y = y0; y < std::min(y0 + 8, v); ++y)
+            if (plus ? x <= y : x < y) (whole ? full : rest).push_back({x, y});
+      }
+    full.insert(full.end(), rest.begin(), rest.end());
+    return full;
+  };
+  const std::vector<std::array<int, 2>> rp = row_order(true), rm = row_order(false);
   std::vector<int> mrow((size_t)V2, -1);
-  for (int q = 0; q < S.Km; ++q) mrow[(size_t)pm[q][0] * v + pm[q][1]] = q;
-  std::vector<int4> rows(S.Kp);
-  for (int q = 0; q < S.Kp; ++q) rows[q] = make_int4(pp[q][0], pp[q][1], mrow[(size_t)pp[q][0] * v + pp[q][1]], 0);
+  for (size_t q = 0; q < rm.size(); ++q) mrow[(size_t)rm[q][0] * v + rm[q][1]] = (int)q;
+  std::vector<int4> rows(rp.size());
+  for (size_t q = 0; q < rp.size(); ++q) rows[q] = make_int4(rp[q][0], rp[q][1], mrow[(size_t)rp[q][0] * v + rp[q][1]], 0);
   S.chunks = upload_vec(c, ch, err);
   S.rows = upload_vec(c, rows, err);
   // R3 offset of the result element (x, y, w) of view `term` is ebase(x, y) + col(blk, w)
   auto ebase = [&](int term, i64 x, i64 y) { return term == 0 ? x * V2 + y * v : term == 1 ? x * V2 + y : x * v + y; };
   for (int part = 0; part < 2; ++part) {
-    const auto& pr = part == 0 ? pp : pm;
+    const auto& pr = part == 0 ? rp : rm;
     const size_t M = pr.size();
     for (int term = 0; term < 3; ++term) {
       std::vector<i64> rb(M), rb2(M);

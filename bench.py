@@ -421,7 +421,7 @@ def run_ours(args, rank, world):
         # DRAM bytes per pp-ladder launch (mean of one sum and one difference GEMM) from an
         # ncu capture of this workload and precision (profiles/k_gemm_tc_pp_o16v160w_traffic.md);
         # other runs have none
-        traffic = 9.79e9 if (args.workload == "o16v160w" and prec == 1) else None
+        traffic = 10.18e9 if (args.workload == "o16v160w" and prec == 1) else None
         roof = {"kernel": "pp-ladder GEMM (k_gemm_f64)" if prec == 0 else "pp-ladder GEMM (k_gemm_tc)",
                 "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of "

@@ -11,7 +11,9 @@
  *     of appendix A.4 and the spin summations of Eq. triples-spin-sum;
  *   - compact storage and contractions: Sec. II.B.1 and Sec. II.C (direct
  *     traversal of the pp-ladder, unpacking for the hh-ladder and ring terms,
- *     the representative contractions of the operation-count table);
+ *     the representative contractions of the operation-count table); the
+ *     pp-ladder runs as sum and difference products over the exchange symmetry
+ *     W^{ab}_{de} = W^{ba}_{ed} (same result, about half its FMA);
  *   - post-processing: Sec. II.D (symmetrise, purify, orthogonalise);
  *   - update: Jacobi step t += r / eps of appendix A.1; DIIS of Sec. III.A.4;
  *   - energy: the E_CC expression of appendix A.5 with bare integrals.
@@ -169,7 +171,9 @@ double rccsdt_iteration_fma(int o, int v);
  *   ms[0..8]  device ms of: intermediates, pp-ladder, ring, hh-ladder, T2 terms,
  *             R1/R2 and setup, postprocess, update, energy;
  *   ms[9]     device ms inside the pp-ladder GEMM kernels alone;
- *   ms[10]    number of those GEMM launches;  ms[11]  their algorithmic flop.
+ *   ms[10]    number of those GEMM launches;  ms[11]  the flop they execute
+ *             (2 M N K each; with the pair-symmetric form of the per-plan engine,
+ *             about half the paper's pp-ladder count).
  * Returns the number of entries written (<= cap, at most 12). */
 int rccsdt_step_times(rccsdt_ctx* ctx, double* ms, int cap);
 int rccsdt_enable_timing(rccsdt_ctx* ctx, int on);

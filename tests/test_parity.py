@@ -172,3 +172,28 @@ def test_errors_are_reported_not_raised_on_device(kind):
         ctx.build_intermediates()  # no Hamiltonian yet
     assert ei.value.status == B.ERR_STATE
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.SPLIT_BF16X3], ids=["fp64", "bf16x3"])
+@pytest.mark.parametrize("o,v,naux", [(2, 16, 10), (2, 17, 10), (1, 33, 8)])
+def test_pp_pair_tiles_edges_on_host(prec, o, v, naux):
+    """Pair-tile edges of the pair-symmetric pp-ladder (one full 16-label tile; a tile
+    plus one label, whose diagonal chunk has no difference pairs; two tiles plus one),
+    per-plan engine on the host simulation of the same plans."""
+    inst = make_instance(o, v, naux, seed=o + 5 * v)
+    t1, t2, t3 = random_amplitudes(o, v, seed=v + 3 * o)
+    t3c = oc.pack(t3)
+    ctx = _ctx("hostsim", o, v, naux, precision=prec, grouped_bytes=0)
+    ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    ctx.set_amplitudes(t1, t2, t3c)
+    ctx.build_intermediates()
+    ctx.residual()
+    ctx.postprocess()
+    r1, r2, r3 = ctx.residuals()
+    R1, R2, R3 = oc.residuals_compact(inst.L, inst.fock_diag, t1, t2, t3c)
+    scale = max(1.0, np.abs(R3).max())
+    tol = 1e-11 if prec == B.FP64 else 5e-5
+    assert np.abs(r1 - R1).max() / scale < tol
+    assert np.abs(r2 - R2).max() / scale < tol
+    assert np.abs(oc.postprocess(r3, o) - oc.postprocess(R3, o)).max() / scale < tol
+    ctx.close()

@@ -46,6 +46,9 @@ struct PackArgs {
 // With row_base2 set, every value is also added, times row_alpha2[m], at
 // row_base2[m] + the same column offset of the same tensor (rows with
 // row_base2[m] < 0 write once): the mirrored element of a pair-symmetric product.
+// With col_off2 set instead, the second copy goes to row_base[m] + col_off2[n]
+// (columns with col_off2[n] < 0 write once), times row_alpha2[m]: the same mirror
+// when the pairs index the columns.
 struct EpiArgs {
   void* C;               // double or float
   int c_f32;
@@ -57,7 +60,8 @@ struct EpiArgs {
   void* C2;
   int m2;
   const i64* row_base2;     // [M] or null
-  const double* row_alpha2; // [M] (with row_base2)
+  const double* row_alpha2; // [M] (with row_base2 or col_off2)
+  const i64* col_off2;      // [N] or null (row_sel 0 only)
 };
 
 }  // namespace rcc

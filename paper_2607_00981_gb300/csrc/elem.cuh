@@ -216,9 +216,10 @@ RCC_HD void* epi_out(const EpiArgs& e, int m) { return (e.C2 && m >= e.m2) ? e.C
 
 RCC_HD void epi_apply(const EpiArgs& e, int m, int n, double acc) {
   const i64 co = e.col_off[(i64)e.row_sel[m] * e.N + n];
-  const int nout = (e.row_base2 && e.row_base2[m] >= 0) ? 2 : 1;
+  const bool rowm = e.row_base2 && e.row_base2[m] >= 0, colm = e.col_off2 && e.col_off2[n] >= 0;
+  const int nout = (rowm || colm) ? 2 : 1;
   for (int q = 0; q < nout; ++q) {
-    const i64 addr = (q ? e.row_base2[m] : e.row_base[m]) + co;
+    const i64 addr = q == 0 ? e.row_base[m] + co : (rowm ? e.row_base2[m] + co : e.row_base[m] + e.col_off2[n]);
     const double val = (q ? e.row_alpha2[m] : e.row_alpha[m]) * acc;
     if (e.c_f32)
       ((float*)epi_out(e, m))[addr] += (float)val;

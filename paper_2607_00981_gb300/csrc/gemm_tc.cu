@@ -171,7 +171,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 // Scatter 32 accumulator columns of row m: every address and old value is
 // loaded before any store, so the loads of a row overlap in flight.  A mirrored
-// row (row_base2) repeats the pass at its second base.
+// row (row_base2) repeats the pass at its second base; column offsets < 0 are
+// skipped (the unmirrored columns of a column mirror).
 __device__ __forceinline__ void epilogue_row(const EpiArgs& e, int m, int n0, const uint32_t (&r)[32]) {
   const i64* co = e.col_off + (i64)e.row_sel[m] * e.N;
   const int nv = min(32, e.N - n0);
@@ -187,7 +188,10 @@ __device__ __forceinline__ void epilogue_row(const EpiArgs& e, int m, int n0, co
         i64 ad[16];
         float old[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) ad[j] = (h + j < nv) ? rb + __ldg(co + n0 + h + j) : -1;
+        for (int j = 0; j < 16; ++j) {
+          const i64 cv = (h + j < nv) ? __ldg(co + n0 + h + j) : -1;
+          ad[j] = cv >= 0 ? rb + cv : -1;
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) old[j] = ad[j] >= 0 ? C[ad[j]] : 0.f;
 #pragma unroll
@@ -202,7 +206,10 @@ __device__ __forceinline__ void epilogue_row(const EpiArgs& e, int m, int n0, co
         i64 ad[16];
         double old[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) ad[j] = (h + j < nv) ? rb + __ldg(co + n0 + h + j) : -1;
+        for (int j = 0; j < 16; ++j) {
+          const i64 cv = (h + j < nv) ? __ldg(co + n0 + h + j) : -1;
+          ad[j] = cv >= 0 ? rb + cv : -1;
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) old[j] = ad[j] >= 0 ? C[ad[j]] : 0.0;
 #pragma unroll
@@ -239,7 +246,8 @@ __device__ __forceinline__ void raster(int mt, int nt, int t, int& tm, int& tn) 
 // Schedule of a single GEMM (optionally split along K) with the table-driven
 // scatter epilogue or FP32 partial tiles.  Tensor maps live in the kernel's
 // parameter space (__grid_constant__).
-struct PlainSched {
+template <bool COLM>  // COLM: the epilogue adds the column mirror (EpiArgs::col_off2) in a second pass
+struct PlainSchedT {
   CUtensorMap ah, al, bh, bl;
   TileGeom g;
   EpiArgs e;
@@ -271,10 +279,21 @@ struct PlainSched {
     } else {
       EpiArgs e2 = e;
       if (ncols < 32) e2.N = min(e.N, n0 + ncols);
-      epilogue_row(e2, m, n0, r);
+      // with the column mirror, a second pass over the mirrored offsets (one loop body)
+#pragma unroll 1
+      for (int q = 0; q < (COLM ? 2 : 1); ++q) {
+        if (q) {
+          e2.col_off = e.col_off2;
+          e2.row_alpha = e.row_alpha2;
+          e2.row_base2 = nullptr;
+        }
+        epilogue_row(e2, m, n0, r);
+      }
     }
   }
 };
+
+using PlainSched = PlainSchedT<false>;
 
 // Schedule of a group of independent GEMMs of different shapes (problem table in
 // device memory, tensor maps included): one persistent launch runs every tile
@@ -723,21 +742,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       const EpiArgs& e = sch.e;
       const int m = tm * BM + row;
       if (m < e.M) {
-        const i64* co = e.col_off + (i64)e.row_sel[m] * e.N;
+        const i64* co0 = e.col_off + (i64)e.row_sel[m] * e.N;
         const int em = sch.ea[m];
         void* C = epi_out(e, m);
-        const int nout = (e.row_base2 && e.row_base2[m] >= 0) ? 2 : 1;
+        const bool rowm = e.row_base2 && e.row_base2[m] >= 0;
+        const int nout = (rowm || e.col_off2) ? 2 : 1;
         for (int q = 0; q < nout; ++q) {
-          const i64 rb = q ? e.row_base2[m] : e.row_base[m];
+          const i64 rb = (q && rowm) ? e.row_base2[m] : e.row_base[m];
+          const i64* co = (q && !rowm) ? e.col_off2 : co0;  // column offsets < 0: no second copy
           const double al = q ? e.row_alpha2[m] : e.row_alpha[m];
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int n = tn * EBN + h * 32 + j;
-            if (n < e.N) {
+            const i64 cv = n < e.N ? __ldg(co + n) : -1;
+            if (cv >= 0) {
               const int sc = em + __ldg(sch.eb + n) - 14;
               const double pw = __longlong_as_double((long long)(sc + 1023) << 52);  // |sc| < 1000 for finite data
               const double val = ((double)shi[j] + (double)slo[j]) * pw;
-              const i64 ad = rb + __ldg(co + n);
+              const i64 ad = rb + cv;
               if (e.c_f32)  // FP32 storage (R3 of split contexts)
                 ((float*)C)[ad] = (float)((double)((float*)C)[ad] + al * val);
               else
@@ -870,6 +892,7 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
   const int esz = kind == PANEL_BF16X2 ? 2 : 4;
   const int bk = ROWB / esz;
   if (Kpad % bk != 0 || e.M <= 0 || e.N <= 0) return 1;
+  if (e.col_off2 && (BN != 256 || raw_out || e.row_base2)) return 1;  // column mirror: 256-wide, direct epilogue
   PlainSched sch;
   if (!make_map(&sch.ah, Ahi, e.M, Kpad, kind, BM) || !make_map(&sch.al, Alo, e.M, Kpad, kind, BM) ||
       !make_map(&sch.bh, Bhi, e.N, Kpad, kind, BN) || !make_map(&sch.bl, Blo, e.N, Kpad, kind, BN))
@@ -895,7 +918,21 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
   sch.e = e;
   sch.partial = part;
   sch.colmajor = raw_out && colmajor ? 1 : 0;
-  launch_any(kind, BN, sch, grid, status_flag, budget, s);
+  if (e.col_off2 && !part) {
+    PlainSchedT<true> schm;
+    schm.ah = sch.ah;
+    schm.al = sch.al;
+    schm.bh = sch.bh;
+    schm.bl = sch.bl;
+    schm.g = sch.g;
+    schm.e = sch.e;
+    schm.partial = sch.partial;
+    schm.colmajor = sch.colmajor;
+    if (kind == PANEL_BF16X2) launch_sched<1, 256>(schm, grid, status_flag, budget, s);
+    else launch_sched<2, 256>(schm, grid, status_flag, budget, s);
+  } else {
+    launch_any(kind, BN, sch, grid, status_flag, budget, s);
+  }
   if (part && !raw_out) {
     const long long MN = (long long)e.M * e.N;
     long long blocks = (MN + 255) / 256;

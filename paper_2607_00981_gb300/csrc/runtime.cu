@@ -247,7 +247,7 @@ struct rccsdt_ctx {
     std::unique_ptr<DBuf> chunks, rows;  // PairChunk[nchunk], int4[Kp] (x, y, row of the difference)
     std::unique_ptr<DBuf> rb[3][2], rb2[3][2], al[2], al2[2], sel;  // per view / part: row tables
     struct Unit {
-      int term = 0, nblk = 0, N = 0;
+      int term = 0, nblk = 0, N = 0, swap = 0;
       i64 b0 = 0;
       std::unique_ptr<DBuf> col;  // [N] column offsets into R3
       rcc::EpiArgs e[2]{};        // sum and difference GEMMs
@@ -464,6 +464,10 @@ void build_pp_sym(rccsdt_ctx* c, bool t3f, void* r3p, int* err) {
   S.rows = upload_vec(c, rows, err);
   // R3 offset of the result element (x, y, w) of view `term` is ebase(x, y) + col(blk, w)
   auto ebase = [&](int term, i64 x, i64 y) { return term == 0 ? x * V2 + y * v : term == 1 ? x * V2 + y : x * v + y; };
+  // units: each view of nb stored blocks (N = nb v panel rows)
+  const i64 per_blk = (i64)v * round_up((int)V2, 64) * 8;
+  const i64 nb = std::max<i64>(1, std::min<i64>(c->n3, (2LL << 30) / per_blk));
+  const int maxN0 = (int)(std::min<i64>(c->n3, nb) * v);
   for (int part = 0; part < 2; ++part) {
     const auto& pr = part == 0 ? rp : rm;
     const size_t M = pr.size();
@@ -476,12 +480,11 @@ void build_pp_sym(rccsdt_ctx* c, bool t3f, void* r3p, int* err) {
       S.rb[term][part] = upload_vec(c, rb, err);
       S.rb2[term][part] = upload_vec(c, rb2, err);
     }
-    S.al[part] = upload_vec(c, std::vector<double>(std::max<size_t>(M, 1), 0.5), err);
-    S.al2[part] = upload_vec(c, std::vector<double>(std::max<size_t>(M, 1), part == 0 ? 0.5 : -0.5), err);
+    const size_t R = std::max<size_t>(std::max<size_t>(M, (size_t)maxN0), 1);  // rows of either orientation
+    S.al[part] = upload_vec(c, std::vector<double>(R, 0.5), err);
+    S.al2[part] = upload_vec(c, std::vector<double>(R, part == 0 ? 0.5 : -0.5), err);
   }
-  S.sel = upload_vec(c, std::vector<int>(std::max(S.Kp, 1), 0), err);
-  const i64 per_blk = (i64)v * round_up((int)V2, 64) * 8;
-  const i64 nb = std::max<i64>(1, std::min<i64>(c->n3, (2LL << 30) / per_blk));
+  S.sel = upload_vec(c, std::vector<int>(std::max(std::max(S.Kp, maxN0), 1), 0), err);
   int maxN = 0;
   for (int term = 0; term < 3; ++term)
     for (i64 b0 = 0; b0 < c->n3; b0 += nb) {
@@ -497,20 +500,32 @@ void build_pp_sym(rccsdt_ctx* c, bool t3f, void* r3p, int* err) {
         col[q] = blk * V3 + (term == 0 ? w : term == 1 ? w * v : w * V2);
       }
       u->col = upload_vec(c, col, err);
+      // the view with w on the unit-stride axis runs with the operands exchanged
+      // (rows (blk, w), columns the pairs): an epilogue warp's rows are consecutive w,
+      // so both the (x, y) and the mirrored (y, x) writes are coalesced
+      u->swap = term == 0;
       for (int part = 0; part < 2; ++part) {
         rcc::EpiArgs& e = u->e[part];
+        const int P = part == 0 ? S.Kp : S.Km;
         e.C = r3p;
         e.c_f32 = t3f ? 1 : 0;
-        e.M = part == 0 ? S.Kp : S.Km;
-        e.N = u->N;
-        e.row_base = (const i64*)S.rb[term][part]->p;
         e.row_sel = (const int*)S.sel->p;
         e.row_alpha = (const double*)S.al[part]->p;
-        e.col_off = (const i64*)u->col->p;
-        e.row_base2 = (const i64*)S.rb2[term][part]->p;
         e.row_alpha2 = (const double*)S.al2[part]->p;
-        const int K = part == 0 ? S.Kp : S.Km;
-        u->fma[part] = (double)e.M * e.N * K;
+        if (u->swap) {
+          e.M = u->N;
+          e.N = P;
+          e.row_base = (const i64*)u->col->p;
+          e.col_off = (const i64*)S.rb[term][part]->p;
+          e.col_off2 = (const i64*)S.rb2[term][part]->p;
+        } else {
+          e.M = P;
+          e.N = u->N;
+          e.row_base = (const i64*)S.rb[term][part]->p;
+          e.col_off = (const i64*)u->col->p;
+          e.row_base2 = (const i64*)S.rb2[term][part]->p;
+        }
+        u->fma[part] = (double)P * u->N * P;
       }
       S.units.push_back(std::move(u));
     }
@@ -959,16 +974,23 @@ static int run_pp_sym(rccsdt_ctx* c) {
       const rcc::EpiArgs& e = u.e[part];
       const int tidx = timer_begin(c, 16, 2.0 * u.fma[part]);
       int lst = 0;
+      // operands in GEMM order: rows of e.M first (the T panel when the unit is exchanged)
+      const rcc::CubeDst& X = u.swap ? Bq : A;
+      const rcc::CubeDst& Y = u.swap ? A : Bq;
       if (f64e) {
         rcc::launch_slice_f64((const double*)Bq.out_hi, u.N, Kpad, c->planesB->p, (int*)c->expB->p, c->stream);
-        lst = rcc::launch_gemm_f64e(pA[part], eA[part], c->planesB->p, (const int*)c->expB->p, Kpad, e, flag,
-                                    c->opt.watchdog_cycles, c->stream);
+        const void* px = u.swap ? c->planesB->p : (const void*)pA[part];
+        const void* py = u.swap ? (const void*)pA[part] : c->planesB->p;
+        const int* ex = u.swap ? (const int*)c->expB->p : eA[part];
+        const int* ey = u.swap ? eA[part] : (const int*)c->expB->p;
+        lst = rcc::launch_gemm_f64e(px, ex, py, ey, Kpad, e, flag, c->opt.watchdog_cycles, c->stream);
       } else if (!tc) {
-        rcc::launch_gemm_f64((const double*)A.out_hi, (const double*)Bq.out_hi, round_up(K, 16), Kpad, Kpad, e,
+        rcc::launch_gemm_f64((const double*)X.out_hi, (const double*)Y.out_hi, round_up(K, 16), Kpad, Kpad, e,
                              c->concurrent ? nullptr : c->splitk->d(), (i64)(c->splitk->bytes / 8), c->stream);
       } else {
-        const int bn = e.N <= 128 ? 128 : (e.N <= 144 ? 144 : 256);
-        lst = rcc::launch_gemm_tc(kind, A.out_hi, A.out_lo, Bq.out_hi, Bq.out_lo, Kpad, e, flag, c->opt.watchdog_cycles,
+        // (the column-mirror epilogue exists for 256-wide tiles only)
+        const int bn = u.swap ? 256 : (e.N <= 128 ? 128 : (e.N <= 144 ? 144 : 256));
+        lst = rcc::launch_gemm_tc(kind, X.out_hi, X.out_lo, Y.out_hi, Y.out_lo, Kpad, e, flag, c->opt.watchdog_cycles,
                                   c->stream, c->concurrent ? nullptr : (float*)c->splitk->p,
                                   (long long)(c->splitk->bytes / 4), nullptr, bn);
       }

@@ -174,16 +174,18 @@ def test_errors_are_reported_not_raised_on_device(kind):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", [B.FP64, B.SPLIT_BF16X3], ids=["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec,f64_tc", [(B.FP64, 0), (B.FP64, 2), (B.SPLIT_BF16X3, 0)],
+                         ids=["fp64", "fp64-tensor-cores", "bf16x3"])
 @pytest.mark.parametrize("o,v,naux", [(2, 16, 10), (2, 17, 10), (1, 33, 8)])
-def test_pp_pair_tiles_edges_on_host(prec, o, v, naux):
+def test_pp_pair_tiles_edges_on_host(prec, f64_tc, o, v, naux):
     """Pair-tile edges of the pair-symmetric pp-ladder (one full 16-label tile; a tile
     plus one label, whose diagonal chunk has no difference pairs; two tiles plus one),
-    per-plan engine on the host simulation of the same plans."""
+    per-plan engine on the host simulation of the same plans: the DFMA and digit-plane
+    FP64 engines and 3xBF16, each with the row- and the column-mirror epilogue."""
     inst = make_instance(o, v, naux, seed=o + 5 * v)
     t1, t2, t3 = random_amplitudes(o, v, seed=v + 3 * o)
     t3c = oc.pack(t3)
-    ctx = _ctx("hostsim", o, v, naux, precision=prec, grouped_bytes=0)
+    ctx = _ctx("hostsim", o, v, naux, precision=prec, grouped_bytes=0, f64_tc=f64_tc)
     ctx.set_hamiltonian(inst.fock_diag, inst.L)
     ctx.set_amplitudes(t1, t2, t3c)
     ctx.build_intermediates()
@@ -192,7 +194,7 @@ def test_pp_pair_tiles_edges_on_host(prec, o, v, naux):
     r1, r2, r3 = ctx.residuals()
     R1, R2, R3 = oc.residuals_compact(inst.L, inst.fock_diag, t1, t2, t3c)
     scale = max(1.0, np.abs(R3).max())
-    tol = 1e-11 if prec == B.FP64 else 5e-5
+    tol = (1e-11 if f64_tc == 0 else 1e-10) if prec == B.FP64 else 5e-5
     assert np.abs(r1 - R1).max() / scale < tol
     assert np.abs(r2 - R2).max() / scale < tol
     assert np.abs(oc.postprocess(r3, o) - oc.postprocess(R3, o)).max() / scale < tol

@@ -412,27 +412,17 @@ void build_pp_sym(rccsdt_ctx* c, bool t3f, void* r3p, int* err) {
   const int v = c->v;
   const i64 V2 = (i64)v * v, V3 = c->V3;
   const int nt = (v + 15) / 16;
+  // K numbering: chunk (P, Q) of the 16-label tiles holds its sum pairs at offp and
+  // its difference pairs at offm (inside a chunk as pair_decode describes)
   std::vector<rcc::PairChunk> ch;
-  std::vector<std::array<int, 2>> pp, pm;  // pairs of the sum and difference columns
   int offp = 0, offm = 0;
   for (int P = 0; P < nt; ++P)
     for (int Q = P; Q < nt; ++Q) {
       const int nd = std::min(16, v - 16 * P), ne = std::min(16, v - 16 * Q);
       const bool diag = P == Q;
       ch.push_back({P, Q, offp, offm});
-      const int np = diag ? nd * (nd + 1) / 2 : nd * ne, nm = diag ? nd * (nd - 1) / 2 : nd * ne;
-      for (int t = 0; t < np; ++t) {
-        int a, b;
-        rcc::pair_decode(t, diag, true, nd, ne, a, b);
-        pp.push_back({16 * P + a, 16 * Q + b});
-      }
-      for (int t = 0; t < nm; ++t) {
-        int a, b;
-        rcc::pair_decode(t, diag, false, nd, ne, a, b);
-        pm.push_back({16 * P + a, 16 * Q + b});
-      }
-      offp += np;
-      offm += nm;
+      offp += diag ? nd * (nd + 1) / 2 : nd * ne;
+      offm += diag ? nd * (nd - 1) / 2 : nd * ne;
     }
   S.nchunk = (int)ch.size();
   S.Kp = offp;

@@ -17,7 +17,11 @@ Modules
                contractions of the operation-count table) and the post-processing
                of Sec. II.D (symmetrisation, purification, orthogonalisation).
 ``detcc``      Brute-force FCI and determinant-space spin-orbital CC at any
-               truncation, straight from the projective definition of A.1.
+               truncation, straight from the projective definition of A.1, and
+               the spin-orbital CCSDT(Q) energy from its determinant definition.
+``q_correction`` The RCCSDT(Q) energy correction on full storage, from the (Q)
+               appendix (Eqs. ener-pt-q, resi-pt-q, q_t3_terms, q_w_vvv_voo,
+               q_w_vvo_ooo, q_w_alter) and Eq. quadruples-spin-sum.
 ``nullspace``  The spin-free overlap metric of appendix B.
 ``opcount``    Leading operation counts (Sec. II.C.3 and its table).
 

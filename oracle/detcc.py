@@ -246,3 +246,36 @@ def setup(L: np.ndarray, fock_diag: np.ndarray, o_closed: int, na: int, nb: int)
 
 def fci_energies(H: sp.csr_matrix) -> np.ndarray:
     return np.linalg.eigvalsh(H.toarray())
+
+
+def ccsdt_q_energy(cc: "DetCC", t: np.ndarray, fock_so_diag: np.ndarray) -> float:
+    """Spin-orbital CCSDT(Q) correction in determinant space from converged CCSDT
+    amplitudes ``t`` of ``cc`` (rank 3), the standard second-order quadruples
+    estimate and its fourth- and fifth-order energy (T1 left out):
+
+        R_Q = <Q| H T3 + 1/2 [[H, T2], T2] |0>,  L_Q = <Q| H (T2 + T3) |0>,
+        E(Q) = sum_Q L_Q R_Q / D_Q,  D_Q = sum of the occupied minus the virtual
+        spin-orbital energies of Q.
+
+    With a canonical reference (no singles in H|0>) the double commutator keeps the
+    connected H T2 T2 terms and the T3 term is connected by construction; L_Q is the
+    <0|(T2^+ + T3^+) V|Q> projection.  Test infrastructure: a brute-force definition."""
+    space, H = cc.space, cc.H
+    ranks = np.array([len(I) for I, _ in cc.excitations])
+    T2 = cc.T_matrix(np.where(ranks == 2, t, 0.0))
+    T3 = cc.T_matrix(np.where(ranks == 3, t, 0.0))
+    phi0 = cc.phi0
+    v2, v3 = T2 @ phi0, T3 @ phi0
+    R = H @ v3 + 0.5 * (H @ (T2 @ v2) - 2.0 * (T2 @ (H @ v2)) + T2 @ (T2 @ (H @ phi0)))
+    Lv = H @ (v2 + v3)
+    ref = cc.ref
+    E = 0.0
+    for det, idx in space.index.items():
+        if _popcount(det & ~ref) != 4:
+            continue
+        removed = [p for p in range(2 * space.n) if (ref >> p & 1) and not (det >> p & 1)]
+        added = [p for p in range(2 * space.n) if (det >> p & 1) and not (ref >> p & 1)]
+        D = sum(fock_so_diag[p] for p in removed) - sum(fock_so_diag[p] for p in added)
+        E += Lv[idx] * R[idx] / D
+    return float(E)
+

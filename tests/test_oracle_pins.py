@@ -274,3 +274,51 @@ def test_pp_ladder_intermediate_is_pair_symmetric():
     assert np.abs(Xm - Xd).max() < 1e-12 * max(1.0, np.abs(Xd).max())
     # the recombination the epilogue performs: X^{xy} = (X+ + X-) / 2
     assert np.abs(0.5 * (Xp + Xm) - X).max() < 1e-12 * max(1.0, np.abs(X).max())
+
+
+# ------------------------------------------------ (Q) correction (appendix, Eq. ener-pt-q)
+
+from oracle import q_correction as Qc  # noqa: E402
+
+
+def _q_pair(o, v, seed, scale=None):
+    kw = {} if scale is None else {"scale": scale}
+    inst = make_instance(o, v, naux=12, seed=seed, **kw)
+    space, H, ref, fso, h, eri = detcc.setup(inst.L, inst.fock_diag, o, o, o)
+    cc = detcc.DetCC(space, H, ref, 3, fso)
+    _, t, _ = cc.solve(tol=1e-11, max_iter=800)
+    e_det = detcc.ccsdt_q_energy(cc, t, fso)
+    _, _, t2, t3, *_ = full.solve_full(inst.L, inst.fock_diag, o, triples=True, tol=1e-11, max_iter=800)
+    return inst, e_det, t2, t3
+
+
+@pytest.mark.parametrize("o,v,seed,scale", [(2, 2, 3, None), (2, 4, 7, 0.6), (3, 3, 3, None)])
+def test_rccsdt_q_equals_determinant_ccsdt_q(o, v, seed, scale):
+    """The spin-adapted (Q) energy of the paper's appendix, from converged RCCSDT
+    amplitudes, equals the spin-orbital CCSDT(Q) correction computed by brute force
+    in determinant space from the determinant CCSDT amplitudes (both without T1):
+    E(Q) = sum_Q <Q|H(T2+T3)|0><Q|H T3 + [[H,T2],T2]/2|0> / D_Q.  Both intermediate
+    forms the paper prints (Eq. q_w_alter) give it."""
+    inst, e_det, t2, t3 = _q_pair(o, v, seed, scale)
+    e_q = Qc.energy_q(inst.L, inst.fock_diag, t2, t3, o)
+    e_alt = Qc.energy_q(inst.L, inst.fock_diag, t2, t3, o, alternative=True)
+    assert abs(e_det) > 1e-7
+    assert abs(e_q - e_det) < 1e-8 * abs(e_det)
+    assert abs(e_alt - e_det) < 1e-8 * abs(e_det)
+
+
+def test_q_pin_detects_planted_mistakes(monkeypatch):
+    """Negative controls, planted in the oracle on the CPU: a missing factor in the
+    quadruples spin summation, a dropped T2 T2 term of the residual, or the
+    disconnected V term left out of the weights each move E(Q) far off."""
+    o, v = 2, 4
+    inst, e_det, t2, t3 = _q_pair(o, v, 7, 0.6)
+    good = Qc.spin_sum_t4_full
+    monkeypatch.setattr(Qc, "spin_sum_t4_full", lambda t4: 0.5 * good(t4))
+    assert abs(Qc.energy_q(inst.L, inst.fock_diag, t2, t3, o) - e_det) > 0.1 * abs(e_det)
+    monkeypatch.setattr(Qc, "spin_sum_t4_full", good)
+    inter = Qc.q_intermediates
+    monkeypatch.setattr(Qc, "q_intermediates", lambda *a, **k: (lambda X, Y, V: (X, 0 * Y, V))(*inter(*a, **k)))
+    assert abs(Qc.energy_q(inst.L, inst.fock_diag, t2, t3, o) - e_det) > 0.1 * abs(e_det)
+    monkeypatch.setattr(Qc, "q_intermediates", lambda *a, **k: (lambda X, Y, V: (X, Y, 0 * V))(*inter(*a, **k)))
+    assert abs(Qc.energy_q(inst.L, inst.fock_diag, t2, t3, o) - e_det) > 0.1 * abs(e_det)

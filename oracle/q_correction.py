@@ -116,3 +116,42 @@ def energy_q(L, fock_diag, t2, t3, o, alternative=False):
     z = perm_pairs4(X + Vq)
     t4 = r / denom4(e, o)
     return float(np.sum(z * spin_sum_t4_full(t4)) / 24.0)
+
+
+def degeneracy4(n):
+    """f_{pqrs} of the triangular (Q) sums: 24 for p < q < r < s, 12 for one equal
+    adjacent pair, 6 for p = q < r = s, 0 for every other tuple (unordered, or three
+    or four equal labels: no quadruple excitation puts three electrons in one spatial
+    orbital)."""
+    f = np.zeros((n, n, n, n))
+    for p, q, r, s in itertools.product(range(n), repeat=4):
+        if not (p <= q <= r <= s):
+            continue
+        eq = (p == q) + (q == r) + (r == s)
+        if eq == 0:
+            f[p, q, r, s] = 24.0
+        elif eq == 1:
+            f[p, q, r, s] = 12.0
+        elif eq == 2 and p == q and r == s:
+            f[p, q, r, s] = 6.0
+    return f
+
+
+def energy_q_triangular(L, fock_diag, t2, t3, o, over="occ"):
+    """E_(Q) restricted to i <= j <= k <= l (the IJK-based order) or a <= b <= c <= d
+    (the ABC-based order, Eq. ener-pt-q-abc), each tuple weighted by its degeneracy
+    factor f; equal to energy_q."""
+    e = np.asarray(fock_diag, dtype=np.float64)
+    n = len(e)
+    eri = full.Eri(np.asarray(L, dtype=np.float64), o)
+    v = np.zeros((n, n, n, n))
+    for s in itertools.product("ov", repeat=4):
+        sl = [slice(0, o) if c == "o" else slice(o, None) for c in s]
+        v[sl[0], sl[1], sl[2], sl[3]] = eri("".join(s))
+    X, Y, Vq = q_intermediates(v, t2, t3, o)
+    r = perm_pairs4(X + Y)
+    z = perm_pairs4(X + Vq)
+    prod = z * spin_sum_t4_full(r / denom4(e, o))
+    if over == "occ":
+        return float(einsum("ijklabcd,ijkl->", prod, degeneracy4(o)) / 24.0)
+    return float(einsum("ijklabcd,abcd->", prod, degeneracy4(n - o)) / 24.0)

@@ -322,3 +322,29 @@ def test_q_pin_detects_planted_mistakes(monkeypatch):
     assert abs(Qc.energy_q(inst.L, inst.fock_diag, t2, t3, o) - e_det) > 0.1 * abs(e_det)
     monkeypatch.setattr(Qc, "q_intermediates", lambda *a, **k: (lambda X, Y, V: (X, Y, 0 * V))(*inter(*a, **k)))
     assert abs(Qc.energy_q(inst.L, inst.fock_diag, t2, t3, o) - e_det) > 0.1 * abs(e_det)
+
+
+@pytest.mark.parametrize("over", ["occ", "vir"])
+def test_q_triangular_sums_with_degeneracy_factors(over, monkeypatch):
+    """The IJK- and ABC-ordered (Q) sums over i <= j <= k <= l or a <= b <= c <= d with
+    the paper's degeneracy factors (24 / 12 / 6, and 0 for three equal labels) equal
+    the full sum; weighting the three-equal tuples by their multiplicity 4 instead
+    changes nothing either (their spin-summed products vanish), which pins the
+    zeros as a property, not a truncation."""
+    o, v = 3, 3
+    inst, e_det, t2, t3 = _q_pair(o, v, 3)
+    e_full = Qc.energy_q(inst.L, inst.fock_diag, t2, t3, o)
+    e_tri = Qc.energy_q_triangular(inst.L, inst.fock_diag, t2, t3, o, over=over)
+    assert abs(e_tri - e_full) < 1e-12 * max(1.0, abs(e_full)) + 1e-15
+    good = Qc.degeneracy4
+
+    def multiplicities(n):  # 4 for three equal labels, 1 for four
+        f = good(n)
+        for p, q, r, s in itertools.product(range(n), repeat=4):
+            if p <= q <= r <= s and f[p, q, r, s] == 0.0:
+                f[p, q, r, s] = 1.0 if p == s else 4.0
+        return f
+
+    monkeypatch.setattr(Qc, "degeneracy4", multiplicities)
+    e_mult = Qc.energy_q_triangular(inst.L, inst.fock_diag, t2, t3, o, over=over)
+    assert abs(e_mult - e_full) < 1e-12 * max(1.0, abs(e_full)) + 1e-15

@@ -156,6 +156,19 @@ int rccsdt_iterate(rccsdt_ctx* ctx, double* e_corr, double norms[4]);
  * Returns RCCSDT_NOT_CONVERGED if max_iter is reached. */
 int rccsdt_solve(rccsdt_ctx* ctx, double* e_corr, int* iterations, double* final_norm);
 
+/* Checkpoint (the restart from amplitudes on disk of Sec. II.B.1, "Amplitude tensors").
+ * rccsdt_save writes the iteration state -- t1, t2, compact t3 in the context's
+ * storage type, the DIIS history with its counters and B matrix, the iteration
+ * counters and the current precision -- to `path` (raw little-endian with a
+ * header); rccsdt_load reads it into a context created with the same o, v,
+ * storage precision and DIIS options (the Hamiltonian is not part of the file:
+ * set it before iterating).  An iteration after rccsdt_load repeats the one the
+ * saved context would have taken next.  Errors: RCCSDT_ERR_ARG (NULL path, file
+ * not readable or writable, not a checkpoint, truncated, or made for other sizes
+ * or options), RCCSDT_ERR_STATE (save without amplitudes), RCCSDT_ERR_CUDA. */
+int rccsdt_save(rccsdt_ctx* ctx, const char* path);
+int rccsdt_load(rccsdt_ctx* ctx, const char* path);
+
 /* Copies out the amplitudes / the current residuals (float64). NULL skips. */
 int rccsdt_get_amplitudes(rccsdt_ctx* ctx, double* t1, double* t2, double* t3c);
 int rccsdt_get_residuals(rccsdt_ctx* ctx, double* r1, double* r2, double* r3c);

@@ -49,6 +49,8 @@ _SIGS = {
     "rccsdt_iterate": (C.c_int, [_P, _P, _P]),
     "rccsdt_solve": (C.c_int, [_P, _P, _P, _P]),
     "rccsdt_get_amplitudes": (C.c_int, [_P, _P, _P, _P]),
+    "rccsdt_save": (C.c_int, [_P, C.c_char_p]),
+    "rccsdt_load": (C.c_int, [_P, C.c_char_p]),
     "rccsdt_get_residuals": (C.c_int, [_P, _P, _P, _P]),
     "rccsdt_debug_copy": (C.c_int, [_P, C.c_char_p, _P, C.c_longlong]),
     "rccsdt_iteration_fma": (C.c_double, [C.c_int, C.c_int]),
@@ -181,6 +183,15 @@ class Context:
 
     def get_amplitudes(self, t1=None, t2=None, t3c=None):
         self._check(self.lib.rccsdt_get_amplitudes(self.h, _ptr(t1), _ptr(t2), _ptr(t3c)))
+
+    def save(self, path):
+        """Write the iteration state (amplitudes, DIIS history, counters) to ``path``."""
+        self._check(self.lib.rccsdt_save(self.h, str(path).encode()))
+
+    def load(self, path):
+        """Read a state written by ``save`` (same sizes and options; set the
+        Hamiltonian before iterating)."""
+        self._check(self.lib.rccsdt_load(self.h, str(path).encode()))
 
     def get_residuals(self, r1=None, r2=None, r3c=None):
         self._check(self.lib.rccsdt_get_residuals(self.h, _ptr(r1), _ptr(r2), _ptr(r3c)))

@@ -2613,6 +2613,138 @@ RCC_API int rccsdt_get_amplitudes(rccsdt_ctx* c, double* t1, double* t2, double*
   return dev_sync(c->stream) ? fail(c, RCCSDT_ERR_CUDA, "get_amplitudes failed") : 0;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoint: the iteration state (amplitudes in their storage type, the DIIS
+// history, its device counters and B matrix, the host counters) as a raw
+// little-endian file, so that an iteration resumed in a new context with the same
+// Hamiltonian and options repeats the one the saved context would take next.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char kCkMagic[8] = {'R', 'C', 'C', 'S', 'D', 'T', 'c', 'k'};
+constexpr int kCkVersion = 1;
+
+struct CkHeader {
+  char magic[8];
+  int32_t version, o, v, t3_bytes, diis_space, diis_t3, precision, pad;
+  int64_t iter, diis_count, hist_stride, seg1, seg2, seg3;
+};
+
+struct CkRegion {
+  void* dev;
+  size_t bytes;
+};
+
+// The device regions of the state, in file order.
+std::vector<CkRegion> ck_regions(rccsdt_ctx* c) {
+  const bool f = c->opt.precision != RCCSDT_FP64;
+  std::vector<CkRegion> r;
+  r.push_back({c->D("t1"), (size_t)c->seg1 * 8});
+  r.push_back({c->D("t2"), (size_t)c->seg2 * 8});
+  r.push_back({c->B("t3")->p, (size_t)(c->n3 * c->V3) * (f ? 4 : 8)});
+  const int M = c->opt.diis_space;
+  if (M > 0) {
+    r.push_back({c->diis_st->p, 8 * sizeof(int)});
+    r.push_back({scal(c, kB), (size_t)M * M * 8});
+    r.push_back({c->hist_t->p, (size_t)c->hist_stride * M});
+    r.push_back({c->hist_e->p, (size_t)c->hist_stride * M});
+  }
+  return r;
+}
+
+CkHeader ck_header(rccsdt_ctx* c) {
+  CkHeader h{};
+  memcpy(h.magic, kCkMagic, 8);
+  h.version = kCkVersion;
+  h.o = c->o;
+  h.v = c->v;
+  h.t3_bytes = c->opt.precision != RCCSDT_FP64 ? 4 : 8;
+  h.diis_space = c->opt.diis_space;
+  h.diis_t3 = c->opt.diis_t3;
+  h.precision = c->precision;
+  h.iter = c->iter;
+  h.diis_count = c->diis_count;
+  h.hist_stride = c->hist_stride;
+  h.seg1 = c->seg1;
+  h.seg2 = c->seg2;
+  h.seg3 = c->seg3;
+  return h;
+}
+
+constexpr size_t kCkChunk = (size_t)64 << 20;  // host staging per copy
+
+}  // namespace
+
+RCC_API int rccsdt_save(rccsdt_ctx* c, const char* path) {
+  if (!c) return RCCSDT_ERR_ARG;
+  if (!path) return fail(c, RCCSDT_ERR_ARG, "null path");
+  if (!c->have_amp) return fail(c, RCCSDT_ERR_STATE, "no amplitudes to save");
+  if (dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "save: pending work failed");
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return fail(c, RCCSDT_ERR_ARG, std::string("cannot open ") + path + " for writing");
+  const CkHeader h = ck_header(c);
+  bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
+  std::vector<char> buf;
+  for (const CkRegion& r : ck_regions(c)) {
+    for (size_t off = 0; ok && off < r.bytes; off += kCkChunk) {
+      const size_t len = std::min(kCkChunk, r.bytes - off);
+      buf.resize(len);
+      if (dev_copy(buf.data(), (const char*)r.dev + off, len, c->stream) || dev_sync(c->stream)) {
+        fclose(fp);
+        return fail(c, RCCSDT_ERR_CUDA, "save: copy failed");
+      }
+      ok = fwrite(buf.data(), 1, len, fp) == len;
+    }
+  }
+  if (fclose(fp) != 0) ok = false;
+  return ok ? RCCSDT_OK : fail(c, RCCSDT_ERR_ARG, std::string("write to ") + path + " failed");
+}
+
+RCC_API int rccsdt_load(rccsdt_ctx* c, const char* path) {
+  if (!c) return RCCSDT_ERR_ARG;
+  if (!path) return fail(c, RCCSDT_ERR_ARG, "null path");
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return fail(c, RCCSDT_ERR_ARG, std::string("cannot open ") + path);
+  CkHeader h{};
+  const CkHeader want = ck_header(c);
+  if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, kCkMagic, 8) != 0 || h.version != kCkVersion) {
+    fclose(fp);
+    return fail(c, RCCSDT_ERR_ARG, "not an RCCSDT checkpoint");
+  }
+  if (h.o != want.o || h.v != want.v || h.t3_bytes != want.t3_bytes || h.diis_space != want.diis_space ||
+      h.diis_t3 != want.diis_t3 || h.hist_stride != want.hist_stride || h.seg1 != want.seg1 ||
+      h.seg2 != want.seg2 || h.seg3 != want.seg3) {
+    fclose(fp);
+    return fail(c, RCCSDT_ERR_ARG, "checkpoint does not match this context (sizes, storage or DIIS options)");
+  }
+  if (h.precision != c->opt.precision && (c->opt.precision == RCCSDT_FP64 || h.precision < 0 || h.precision > 2)) {
+    fclose(fp);
+    return fail(c, RCCSDT_ERR_ARG, "checkpoint precision not accepted by this context");
+  }
+  std::vector<char> buf;
+  for (const CkRegion& r : ck_regions(c)) {
+    for (size_t off = 0; off < r.bytes; off += kCkChunk) {
+      const size_t len = std::min(kCkChunk, r.bytes - off);
+      buf.resize(len);
+      if (fread(buf.data(), 1, len, fp) != len) {
+        fclose(fp);
+        return fail(c, RCCSDT_ERR_ARG, "checkpoint truncated");
+      }
+      if (dev_copy((char*)r.dev + off, buf.data(), len, c->stream) || dev_sync(c->stream)) {
+        fclose(fp);
+        return fail(c, RCCSDT_ERR_CUDA, "load: copy failed");
+      }
+    }
+  }
+  fclose(fp);
+  c->precision = h.precision;
+  c->iter = (int)h.iter;
+  c->diis_count = (int)h.diis_count;
+  c->have_amp = 1;
+  c->have_int = c->have_res = 0;
+  return RCCSDT_OK;
+}
+
 RCC_API int rccsdt_get_residuals(rccsdt_ctx* c, double* r1, double* r2, double* r3c) {
   if (!c) return RCCSDT_ERR_ARG;
   const bool f = c->opt.precision != RCCSDT_FP64;

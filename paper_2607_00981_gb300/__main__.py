@@ -2,9 +2,12 @@
 
     python -m paper_2607_00981_gb300 --workload o8v80 --iters 2 --precision fp64
 
-Prints the energy and residual norms of each iteration (the device work is
-exactly one ``rccsdt_iterate`` per iteration after ``set_hamiltonian`` and the
-MP2 guess), which makes it a small, fixed launch sequence for profilers.
+Prints one JSON line per iteration: the energy and its change, the residual norms
+(R1, R2, R3, total), the precision and the device ms of each step (the device work
+is exactly one ``rccsdt_iterate`` per iteration after ``set_hamiltonian`` and the
+MP2 guess, which makes it a small, fixed launch sequence for profilers).  With
+``--resume PATH`` the iterations continue from a checkpoint instead of the MP2 guess;
+``--checkpoint PATH`` saves the state after the last iteration.
 
     python -m paper_2607_00981_gb300 --workload o12v120w --solve --tol 1e-8 --precision bf16x3 --f64-tc 1
 
@@ -39,6 +42,8 @@ def main(argv=None):
     ap.add_argument("--diis-space", type=int, default=8)
     ap.add_argument("--refine-fp64", action="store_true", help="re-converge in an FP64 context afterwards")
     ap.add_argument("--refine-diis", type=int, default=2)
+    ap.add_argument("--checkpoint", default=None, help="save the iteration state here at the end")
+    ap.add_argument("--resume", default=None, help="continue from a saved iteration state")
     ap.add_argument("--grouped-bytes", type=int, default=None,
                     help="memory budget of the grouped residual of split contexts (0: per-plan engine)")
     args = ap.parse_args(argv)
@@ -51,7 +56,10 @@ def main(argv=None):
     ctx = pkg.context(inst.o, inst.v, inst.naux, precision=prec, diis_t3=0 if args.no_diis_t3 else 1,
                       f64_tc=args.f64_tc, tol=args.tol, max_iter=args.max_iter, diis_space=args.diis_space, **extra)
     ctx.set_hamiltonian(inst.fock_diag, inst.L)
-    ctx.init_mp2()
+    if args.resume:
+        ctx.load(args.resume)
+    else:
+        ctx.init_mp2()
     if args.solve:
         t0 = time.perf_counter()
         e, iters, norm, conv = ctx.solve()
@@ -77,10 +85,21 @@ def main(argv=None):
             return 0
         ctx.close()
         return 0
+    steps = ["intermediates", "pp", "ring", "hh", "t2", "r12_setup", "post", "update", "energy"]
+    e_prev = None
     for it in range(args.iters):
+        ctx.enable_timing(True)  # a fresh window per iteration
         t0 = time.perf_counter()
         e, n = ctx.iterate()
-        print(f"iter {it + 1}  E = {e:.12f}  |R| = {n[3]:.3e}  ({time.perf_counter() - t0:.3f} s)", flush=True)
+        wall = time.perf_counter() - t0
+        ms = ctx.step_times()
+        print(json.dumps({"iter": it + 1, "energy": e, "delta_e": None if e_prev is None else e - e_prev,
+                          "r1": n[0], "r2": n[1], "r3": n[2], "r": n[3], "precision": args.precision,
+                          "seconds": wall, "step_ms": {k: float(x) for k, x in zip(steps, ms[:9])}}), flush=True)
+        e_prev = e
+    ctx.enable_timing(False)
+    if args.checkpoint:
+        ctx.save(args.checkpoint)
     ctx.close()
     return 0
 

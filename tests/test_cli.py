@@ -1,0 +1,24 @@
+"""The command line (python -m paper_2607_00981_gb300) on the host simulation of the
+library's plans: JSON lines per iteration, checkpoint at the end and resume from it."""
+import json
+
+import paper_2607_00981_gb300 as pkg
+from paper_2607_00981_gb300 import __main__ as cli
+
+from ._helpers import hostsim_lib
+
+
+def test_iterations_checkpoint_and_resume(monkeypatch, capsys, tmp_path):
+    monkeypatch.setattr(pkg, "load", hostsim_lib)
+    ck = tmp_path / "o3v12.ck"
+    assert cli.main(["--workload", "o3v12", "--iters", "3", "--checkpoint", str(ck)]) == 0
+    lines = [json.loads(x) for x in capsys.readouterr().out.splitlines()]
+    assert [x["iter"] for x in lines] == [1, 2, 3]
+    assert lines[0]["delta_e"] is None and lines[1]["delta_e"] == lines[1]["energy"] - lines[0]["energy"]
+    assert set(lines[0]["step_ms"]) >= {"pp", "ring", "hh", "update"}
+    # resuming continues the sequence: its first iteration equals a fourth one
+    assert cli.main(["--workload", "o3v12", "--iters", "1", "--resume", str(ck)]) == 0
+    resumed = json.loads(capsys.readouterr().out.splitlines()[0])
+    assert cli.main(["--workload", "o3v12", "--iters", "4"]) == 0
+    straight = [json.loads(x) for x in capsys.readouterr().out.splitlines()]
+    assert resumed["energy"] == straight[3]["energy"] and resumed["r"] == straight[3]["r"]

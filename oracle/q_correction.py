@@ -155,3 +155,29 @@ def energy_q_triangular(L, fock_diag, t2, t3, o, over="occ"):
     if over == "occ":
         return float(einsum("ijklabcd,ijkl->", prod, degeneracy4(o)) / 24.0)
     return float(einsum("ijklabcd,abcd->", prod, degeneracy4(n - o)) / 24.0)
+
+
+def pack_virtual_triangular(t3c, o):
+    """The one-time transposition before the ABC-based (Q) evaluation (Sec. II.E.2,
+    Fig. q_operation_counts(a)): compact T3 stored by occupied
+    triples i <= j <= k, each a v^3 block over abc, becomes T3 stored by virtual
+    triples a <= b <= c (colex order, as the occupied blocks), each an o^3 block over
+    ijk: out[blk(a, b, c)][i, j, k] = t_{ijk}^{abc}."""
+    from . import compact as cmp
+    v = t3c.shape[1]
+    t3 = cmp.unpack_full(np.asarray(t3c), o)
+    return np.ascontiguousarray(np.stack([t3[:, :, :, a, b, c] for (a, b, c) in cmp.triples(v)]))
+
+
+def unpack_virtual_triangular(t3v, o, v):
+    """The full t_{ijk}^{abc} from the virtual-triangular layout, reading the stored
+    (a, b, c) block of sorted(a, b, c) with the occupied axes permuted by the same
+    sort (the column-permutation symmetry, as for the occupied-triangular layout)."""
+    from . import compact as cmp
+    t3 = np.empty((o, o, o, v, v, v))
+    for a, b, c in itertools.product(range(v), repeat=3):
+        lab = (a, b, c)
+        s = sorted(range(3), key=lambda q: lab[q])
+        blk = t3v[cmp.blk_index(lab[s[0]], lab[s[1]], lab[s[2]])]   # blk[y0, y1, y2]: occupied of sorted labels
+        t3[:, :, :, a, b, c] = np.transpose(blk, np.argsort(s))
+    return t3

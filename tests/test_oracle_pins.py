@@ -348,3 +348,15 @@ def test_q_triangular_sums_with_degeneracy_factors(over, monkeypatch):
     monkeypatch.setattr(Qc, "degeneracy4", multiplicities)
     e_mult = Qc.energy_q_triangular(inst.L, inst.fock_diag, t2, t3, o, over=over)
     assert abs(e_mult - e_full) < 1e-12 * max(1.0, abs(e_full)) + 1e-15
+
+
+def test_virtual_triangular_layout_is_a_bijection():
+    """The ABC-based (Q) layout of T3 (stored by a <= b <= c, o^3 per block) holds the
+    same tensor as the compact occupied-triangular one: unpacking either gives the
+    full t_{ijk}^{abc}, bit for bit, for an amplitude with the column symmetry."""
+    o, v = 3, 4
+    _, _, t3 = random_amplitudes(o, v, seed=11)
+    t3c = C.pack(t3)
+    t3v = Qc.pack_virtual_triangular(t3c, o)
+    assert t3v.shape == (v * (v + 1) * (v + 2) // 6, o, o, o)
+    assert np.array_equal(Qc.unpack_virtual_triangular(t3v, o, v), t3)

@@ -2,8 +2,9 @@
 context from a saved state repeats the one the saved context takes next (the DIIS
 history, its device counters and B matrix travel with the amplitudes): bit for bit on
 the host simulation of the library's plans, to 1e-12 (FP64) or 1e-6 (3xBF16) relative
-on the GPU (a lost DIIS state moves the next step by orders of magnitude more).  The file sorts late so
-that the parity suites run first."""
+on the GPU (a lost DIIS state moves the next step by orders of magnitude more).  This
+file is collected last so that a run stopping at the first failure has run every
+other test first."""
 import numpy as np
 import pytest
 

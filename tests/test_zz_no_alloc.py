@@ -2,8 +2,8 @@
 
 rccsdt_residual_norms_noalloc exists for callers that cannot allocate device
 memory (a framework that owns all device memory through its pool allocator, or
-a service that must not allocate after start-up).  This file is collected last
-so that a run stopping at the first failure has run every other test first.
+a service that must not allocate after start-up).  This file is collected after the
+parity suites so that a run stopping at the first failure has run those first.
 """
 import ctypes
 

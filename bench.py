@@ -39,6 +39,72 @@ def peaks():
         return {}
 
 
+def measure_matmul_peaks(n=8192, reps=5):
+    """FP64 and TF32 dense matmul rates of this GPU (cuBLAS through torch.matmul,
+    2 n^3 flop, best of `reps`, CUDA events): the denominators of the FP64 (DFMA)
+    and 3xTF32 rooflines, which MEASURED_PEAKS.json does not carry.  Takes a few
+    seconds."""
+    import torch
+    out = {}
+    for label, dt, tf32 in (("fp64_tflops", torch.float64, False), ("tf32_tflops", torch.float32, True)):
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        m = n if dt == torch.float32 else n // 2   # the FP64 rate is ~1000x lower: a smaller cube
+        a = torch.randn(m, m, dtype=dt, device="cuda")
+        b = torch.randn(m, m, dtype=dt, device="cuda")
+        c = a @ b
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c = a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[label] = 2.0 * m ** 3 / best / 1e12
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        del a, b, c
+    out["how"] = f"torch.matmul (cuBLAS) FP64 {n // 2}^3 and TF32 {n}^3, best of {reps}, CUDA events"
+    return out
+
+
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in txt.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample_one_core(workload, seconds_budget):
+    """The oracle sample of ``oracle_sample`` in a child process limited to one thread
+    (BLAS and OpenMP thread counts are fixed when numpy loads, hence the child)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "from paper_2607_00981_gb300.synth import workload; "
+            "v, s = bench.oracle_sample(workload(%r), seconds_budget=%r); print(json.dumps([v, s]))"
+            % (ROOT, workload, seconds_budget))
+    try:
+        res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                             timeout=30 * seconds_budget + 300)
+        val, sample = json.loads(res.stdout.strip().splitlines()[-1])
+        return {"value": val, "unit": "s/iteration", "cores": 1, "sample": sample}
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError) as exc:
+        return {"value": None, "error": str(exc)[:200]}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -84,21 +150,34 @@ class ClockSampler:
 
 
 def oracle_sample(inst, seconds_budget=20.0):
-    """Time the FP64 oracle's compact R3 block work on a bounded subset of blocks.
+    """Time one FP64 oracle iteration at this workload from bounded samples.
 
-    The sample is the oracle's ``r3_block`` (pp-ladder, ring, hh-ladder, F and T2
-    terms of one stored block) on the first blocks of a stride through the block
-    list, with intermediates built once outside the timed region; the time is
-    extrapolated to all n3 blocks by block count.  Returns (s/iteration, sample text).
-    """
+    Three parts, summed:
+    * the T1-dressing and the RCCSD/RCCSDT intermediates (``oracle.rccsdt``), once;
+    * the T3 contributions to R1, R2 and W (``oracle.compact.t3_contributions``, a loop
+      of identical v-sized contractions over all o^3 occupied triples), timed on the
+      same v and naux with two occupied orbitals (8 triples) and scaled by (o / 2)^3;
+    * the compact R3 blocks (``oracle.compact.r3_block``: pp-ladder, ring, hh-ladder,
+      F and T2 terms of one stored block) on blocks of a stride through the block list
+      until `seconds_budget` is spent, scaled by block count.
+    Returns (s/iteration, sample text)."""
     from oracle import compact as oc
     from oracle import rccsdt as of
+    from paper_2607_00981_gb300.synth import make_instance
     o, v = inst.o, inst.v
     rng = np.random.default_rng(0)
     t1 = 1e-3 * rng.standard_normal((o, v))
     t2 = of.mp2_t2(inst.L, inst.fock_diag, o)
+    t0 = time.perf_counter()
     Lt, ft = of.dress(inst.L, inst.fock_diag, t1)
     I = of.intermediates(Lt, ft, t2, None, triples=True)
+    t_int = time.perf_counter() - t0
+    small = make_instance(2, v, inst.naux, seed=inst.seed)
+    Ls, fs = of.dress(small.L, small.fock_diag, 1e-3 * rng.standard_normal((2, v)))
+    t3s = 1e-3 * rng.standard_normal((oc.n3(2), v, v, v))
+    t0 = time.perf_counter()
+    oc.t3_contributions(of.Eri(Ls, 2), fs, t3s, 2)
+    t_a3 = (time.perf_counter() - t0) * (o / 2.0) ** 3
     tr = oc.triples(o)
     t3c = 1e-3 * rng.standard_normal((len(tr), v, v, v))
     stride = max(1, len(tr) // 16)
@@ -111,9 +190,11 @@ def oracle_sample(inst, seconds_budget=20.0):
         t_used = time.perf_counter() - t0
         if t_used > seconds_budget:
             break
-    per_block = t_used / picked
-    return per_block * len(tr), f"oracle r3_block on {picked} of {len(tr)} stored blocks (stride {stride}), " \
-                                f"{t_used:.1f} s, extrapolated by block count; intermediates excluded"
+    t_r3 = t_used / picked * len(tr)
+    total = t_int + t_a3 + t_r3
+    return total, (f"oracle: intermediates {t_int:.1f} s (whole); T3 -> R1/R2/W {t_a3:.1f} s (8 occupied "
+                   f"triples at v={v}, scaled by (o/2)^3); R3 {t_r3:.1f} s (r3_block on {picked} of {len(tr)} "
+                   f"stored blocks, stride {stride}, {t_used:.1f} s, scaled by block count)")
 
 
 def run_reference(args, rank, world):
@@ -451,7 +532,8 @@ def run_ours(args, rank, world):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, sample = oracle_sample(inst, seconds_budget=args.ref_seconds)
-        cpu = {"value": val, "unit": "s/iteration", "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
+        cpu = {"value": val, "unit": "s/iteration", "cores": os.cpu_count(), "kind": "oracle", "sample": sample,
+               "cpu_model": cpu_model(), "one_core": oracle_sample_one_core(args.workload, 5.0)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": s_per_iter, "unit": "s/iteration", "n_gpus": world, "steps": args.steps,

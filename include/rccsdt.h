@@ -69,7 +69,12 @@ typedef struct {
   int diis_t3;            /* 1: DIIS vectors include T3; 0: T1 and T2 only */
   int max_iter;           /* rccsdt_solve iteration cap */
   double tol;             /* convergence threshold on the residual norm */
-  long long watchdog_cycles; /* clock64 budget of device-side waits (0 = default) */
+  long long watchdog_cycles; /* clock64 budget of each device-side pipeline wait of the tensor-core
+                                GEMMs (0 = default 4e9, about 2 s; values below 64 are raised to 64;
+                                negative: RCCSDT_ERR_ARG).  A wait that runs out makes the GEMM stop
+                                and the next call that reads results return RCCSDT_ERR_TIMEOUT; the
+                                kernel still retires its own copies and MMAs (waiting at least about
+                                a second for them) before it exits. */
   long long grouped_bytes;   /* split modes: device bytes the grouped residual may hold (all
                                 operand panels and dense results of the R3 contractions at
                                 once); when an instance needs more, or 0, its contractions
@@ -87,11 +92,14 @@ typedef struct {
                                 digit planes per operand, 21 digit products, exact FP32
                                 partial sums of the leading digit levels over K chunks of
                                 256, double-float and FP64 totals); 2 every contraction there */
+  long long pp_unit_bytes;   /* device bytes of one pp-ladder launch unit's T operand (v rows of
+                                v^2 doubles per stored block): the stored blocks are cut into
+                                ranges of that size, one GEMM per view and range (<= 0: 2 GiB) */
 } rccsdt_options;
 
 /* Fills *opt with the defaults: FP64, DIIS(8) from iteration 2 including T3,
  * max_iter 100, tol 1e-8, grouped_bytes 8 GiB, unpack_bytes 1 GiB, autotune 0,
- * f64_tc 0. */
+ * f64_tc 0, pp_unit_bytes 2 GiB. */
 int rccsdt_options_default(rccsdt_options* opt);
 
 /* Creates a context for o occupied / v virtual orbitals and naux factors, on the
@@ -112,7 +120,7 @@ int rccsdt_set_hamiltonian(rccsdt_ctx* ctx, const double* fock_diag, const doubl
 
 /* Sets the amplitudes (float64 in every precision mode; stored as FP32 T3 in the
  * split modes).  Any pointer may be NULL to leave that amplitude unchanged.
- * Clears the DIIS history. */
+ * Clears the DIIS history and a watchdog timeout (as does rccsdt_init_mp2). */
 int rccsdt_set_amplitudes(rccsdt_ctx* ctx, const double* t1, const double* t2, const double* t3c);
 
 /* t1 = 0, t2 = first-order (MP2) doubles v^{ab}_{ij} / eps_ij^ab, t3 = 0. */
@@ -124,7 +132,10 @@ int rccsdt_init_mp2(rccsdt_ctx* ctx);
 int rccsdt_set_precision(rccsdt_ctx* ctx, int precision);
 
 /* Step (i)-(iii) of one iteration: T1-dressing, the RCCSD and RCCSDT
- * intermediates, and the T3 contributions to R1, R2, W^{ab}_{dj}, W^{al}_{ij}. */
+ * intermediates, and the T3 contributions to R1, R2, W^{ab}_{dj}, W^{al}_{ij}.
+ * This call, rccsdt_residual and rccsdt_iterate return RCCSDT_ERR_TIMEOUT once a
+ * device-side wait of the context has run out (options.watchdog_cycles); the
+ * results are then undefined until new amplitudes are set. */
 int rccsdt_build_intermediates(rccsdt_ctx* ctx);
 
 /* Steps (iv)-(v): R1, R2 and the raw compact R3 (requires the intermediates). */
@@ -272,7 +283,8 @@ void rccsdt_batch_destroy(rccsdt_batch* b);
  *
  * Limit: n3 = o(o+1)(o+2)/6 <= 4096, i.e. o <= 28; larger o, o or v < 1, or a NULL
  * pointer return RCCSDT_ERR_ARG before any GPU work.  RCCSDT_ERR_CUDA if the
- * device lookup or a launch fails.
+ * device lookup or a launch fails, or if a CUDA error was already pending when the
+ * call was made (that error is left pending for the caller, not cleared).
  * The first call on each device looks up the scratch's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture.  All calls on a device share the scratch and every call

@@ -23,7 +23,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("diis_space", C.c_int),
                 ("diis_start", C.c_int), ("diis_t3", C.c_int), ("max_iter", C.c_int),
                 ("tol", C.c_double), ("watchdog_cycles", C.c_longlong), ("grouped_bytes", C.c_longlong),
-                ("unpack_bytes", C.c_longlong), ("autotune", C.c_int), ("f64_tc", C.c_int)]
+                ("unpack_bytes", C.c_longlong), ("autotune", C.c_int), ("f64_tc", C.c_int),
+                ("pp_unit_bytes", C.c_longlong)]
 
 
 class RccsdtError(RuntimeError):

@@ -22,7 +22,8 @@
 //              per quadrant double the loads in flight of read-modify-write
 //              epilogues (short K, large outputs), which are latency bound.
 // Every mbarrier wait is bounded by a clock64 budget; on expiry the kernel sets
-// *status, drains its own copies and MMAs (bounded again), frees TMEM and exits.
+// *status, drains its own copies and MMAs (bounded by at least kDrainFloor cycles,
+// whatever the budget), frees TMEM and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -79,6 +80,28 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
     if (clock64() - t0 > budget) return false;
   }
   return true;
+}
+
+// Waits that retire the CTA's own asynchronous work before its shared memory and
+// TMEM are released (the producer's bulk copies, the MMA issuer's tcgen05.mma) are
+// bounded too, but never below kDrainFloor cycles (about a second), whatever budget
+// the caller gave: a short watchdog makes the pipeline waits give up early, never
+// these, so no copy or MMA outlives its CTA.
+constexpr long long kDrainFloor = 1LL << 31;
+__device__ __forceinline__ long long drain_budget(long long budget) { return budget > kDrainFloor ? budget : kDrainFloor; }
+
+// Producer epilogue: wait for every bulk copy this thread issued (stage q's last copy
+// has parity issued[q], -1 = never used).  In the normal path they have landed or are
+// about to (the MMA issuer consumes them); after an abort nobody consumes them.
+template <int NST>
+__device__ __forceinline__ void drain_copies(uint64_t* full, const int (&issued)[NST], long long budget) {
+  const long long lim = drain_budget(budget);
+  for (int q = 0; q < NST; ++q) {
+    if (issued[q] < 0) continue;
+    const long long t0 = clock64();
+    while (!mbar_try(&full[q], (uint32_t)issued[q]) && clock64() - t0 < lim) {
+    }
+  }
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -421,14 +444,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) {
         *abort_flag = 1;
         atomicExch(status, 1);
-        // drain: wait (bounded) for the copies this thread issued
-        for (int q = 0; q < STAGES; ++q) {
-          if (issued[q] < 0) continue;
-          const long long t0 = clock64();
-          while (!mbar_try(&full[q], (uint32_t)issued[q]) && clock64() - t0 < budget) {
-          }
-        }
       }
+      // drain: every copy this thread issued has landed before the CTA may exit
+      drain_copies<STAGES>(full, issued, budget);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -478,8 +496,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // make sure every MMA this thread issued has completed before TMEM is freed
       umma_commit(drain);
-      const long long t0 = clock64();
-      while (!mbar_try(drain, 0) && clock64() - t0 < budget) {
+      const long long t0 = clock64(), lim = drain_budget(budget);
+      while (!mbar_try(drain, 0) && clock64() - t0 < lim) {
       }
     }
   } else {
@@ -641,13 +659,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) {
         *abort_flag = 1;
         atomicExch(status, 1);
-        for (int q = 0; q < E_STAGES; ++q) {
-          if (issued[q] < 0) continue;
-          const long long t0 = clock64();
-          while (!mbar_try(&full[q], (uint32_t)issued[q]) && clock64() - t0 < budget) {
-          }
-        }
       }
+      drain_copies<E_STAGES>(full, issued, budget);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -702,8 +715,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         atomicExch(status, 1);
       }
       umma_commit(drain);
-      const long long t0 = clock64();
-      while (!mbar_try(drain, 0) && clock64() - t0 < budget) {
+      const long long t0 = clock64(), lim = drain_budget(budget);
+      while (!mbar_try(drain, 0) && clock64() - t0 < lim) {
       }
     }
   } else {

@@ -106,7 +106,7 @@ int scratch_address(double** out) {
   if (!g_addr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
+      cudaGetLastError();  // this lookup's own (non-sticky) error; nothing else is pending here
       return RCCSDT_ERR_CUDA;
     }
     g_addr[dev] = p;
@@ -122,6 +122,9 @@ extern "C" __attribute__((visibility("default"))) int rccsdt_residual_norms_noal
   if (o < 1 || v < 1 || !r1 || !r2 || !r3c || !norms) return RCCSDT_ERR_ARG;
   const i64 n3 = (i64)o * (o + 1) * (o + 2) / 6;
   if (n3 > kMaxBlocks) return RCCSDT_ERR_ARG;  // o > 28 exceeds the fixed scratch
+  // an error left pending by the caller's earlier work is reported and left in place
+  // (peek, not get), so the caller can still read its own error state
+  if (cudaPeekAtLastError() != cudaSuccess) return RCCSDT_ERR_CUDA;
   double* scratch = nullptr;
   int st = scratch_address(&scratch);
   if (st) return st;
@@ -130,5 +133,6 @@ extern "C" __attribute__((visibility("default"))) int rccsdt_residual_norms_noal
   k_noalloc_partials<<<(unsigned)n3 + 2, 256, 0, s>>>(scratch, r1, (i64)o * v, r2, (i64)o * o * v * v, r3c, V3,
                                                      (int)n3);
   k_noalloc_finish<<<1, 32, 0, s>>>(scratch, o, norms);
+  // nothing was pending before the launches, so an error here is theirs
   return cudaGetLastError() == cudaSuccess ? RCCSDT_OK : RCCSDT_ERR_CUDA;
 }

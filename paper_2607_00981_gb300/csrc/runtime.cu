@@ -305,6 +305,10 @@ struct rccsdt_ctx {
 
 namespace {
 
+// clock64 budgets of the device-side pipeline waits (the drains that retire a CTA's
+// own copies and MMAs have a floor of their own in the GEMM kernels)
+constexpr long long kDefaultWatchdog = 4000000000LL, kMinWatchdog = 64;
+
 int fail(rccsdt_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -404,6 +408,11 @@ void finish_plan(rccsdt_ctx* c, GemmPlan* g, int K) {
   c->panel_rows = std::max(c->panel_rows, std::max(g->A.a.R, g->B.a.R));
 }
 
+// Bytes of one pp-ladder launch unit's T panel (FP64-sized, v rows of v^2 per stored
+// block): options.pp_unit_bytes, 2 GiB when not positive.  The stored blocks are cut
+// into ranges of that size, one GEMM per view and range.
+i64 pp_unit_bytes(const rccsdt_ctx* c) { return c->opt.pp_unit_bytes > 0 ? c->opt.pp_unit_bytes : (2LL << 30); }
+
 // Tables of the pair-symmetric pp-ladder (see PpSym): tile-major pair numbering,
 // W panel rows, per-view epilogue rows (each x <= y writes (x, y) and, mirrored,
 // (y, x)), and units of the same block ranges as the plain plans.
@@ -456,7 +465,7 @@ void build_pp_sym(rccsdt_ctx* c, bool t3f, void* r3p, int* err) {
   auto ebase = [&](int term, i64 x, i64 y) { return term == 0 ? x * V2 + y * v : term == 1 ? x * V2 + y : x * v + y; };
   // units: each view of nb stored blocks (N = nb v panel rows)
   const i64 per_blk = (i64)v * round_up((int)V2, 64) * 8;
-  const i64 nb = std::max<i64>(1, std::min<i64>(c->n3, (2LL << 30) / per_blk));
+  const i64 nb = std::max<i64>(1, std::min<i64>(c->n3, pp_unit_bytes(c) / per_blk));
   const int maxN0 = (int)(std::min<i64>(c->n3, nb) * v);
   for (int part = 0; part < 2; ++part) {
     const auto& pr = part == 0 ? rp : rm;
@@ -1434,7 +1443,7 @@ int build_context(rccsdt_ctx* c) {
   // --- pp-ladder: three views of each stored block (direct traversal)
   {
     i64 per_blk = (i64)v * round_up((int)V2, 64) * 8;
-    i64 nb = std::max<i64>(1, std::min<i64>(n3, (2LL << 30) / per_blk));
+    i64 nb = std::max<i64>(1, std::min<i64>(n3, pp_unit_bytes(c) / per_blk));
     for (int term = 0; term < 3; ++term)
       for (i64 b0 = 0; b0 < n3; b0 += nb) {
         i64 b1 = std::min(n3, b0 + nb);
@@ -2345,6 +2354,7 @@ RCC_API int rccsdt_options_default(rccsdt_options* opt) {
   opt->unpack_bytes = 1LL << 30;
   opt->autotune = 0;
   opt->f64_tc = 0;
+  opt->pp_unit_bytes = 0;
   return RCCSDT_OK;
 }
 
@@ -2356,13 +2366,15 @@ RCC_API int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, voi
   rccsdt_options_default(&def);
   const rccsdt_options& op = opt ? *opt : def;
   if (op.precision < 0 || op.precision > 2 || op.diis_space < 0 || op.diis_space > 16 || op.f64_tc < 0 ||
-      op.f64_tc > 2)
+      op.f64_tc > 2 || op.watchdog_cycles < 0)
     return RCCSDT_ERR_ARG;
   auto* c = new rccsdt_ctx();
   c->o = o; c->v = v; c->n = o + v; c->naux = naux;
   c->n3 = n3_of(o);
   c->V3 = (i64)v * v * v;
   c->opt = op;
+  // device-side wait budget: 0 selects the default; very small values are raised
+  c->opt.watchdog_cycles = op.watchdog_cycles == 0 ? kDefaultWatchdog : std::max(op.watchdog_cycles, kMinWatchdog);
   c->precision = op.precision;
   c->stream = (cudaStream_t)stream;
   int err = 0;
@@ -2453,6 +2465,17 @@ RCC_API int rccsdt_set_hamiltonian(rccsdt_ctx* c, const double* fock_diag, const
   return RCCSDT_OK;
 }
 
+// RCCSDT_ERR_TIMEOUT once a tensor-core GEMM of this context has given up a wait (the
+// kernels set the flag; it stays set until new amplitudes are given).  Synchronises.
+static int watchdog_status(rccsdt_ctx* c) {
+  int flag = 0;
+  if (dev_copy(&flag, (double*)c->scalars->p + 1000, sizeof(int), c->stream) || dev_sync(c->stream))
+    return fail(c, RCCSDT_ERR_CUDA, "status read failed");
+  return flag ? fail(c, RCCSDT_ERR_TIMEOUT, "a device-side wait exceeded its watchdog budget") : 0;
+}
+
+static int clear_watchdog(rccsdt_ctx* c) { return dev_zero((double*)c->scalars->p + 1000, sizeof(double), c->stream); }
+
 static void reset_diis(rccsdt_ctx* c) {
   c->diis_count = 0;
   c->iter = 0;
@@ -2480,6 +2503,7 @@ RCC_API int rccsdt_set_amplitudes(rccsdt_ctx* c, const double* t1, const double*
       }
     }
   }
+  clear_watchdog(c);
   if (dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "set_amplitudes failed");
   c->have_amp = 1;
   c->have_int = c->have_res = 0;
@@ -2493,6 +2517,7 @@ RCC_API int rccsdt_init_mp2(rccsdt_ctx* c) {
   zero(c, "t1");
   zero(c, "t3");
   rcc::launch_mp2(c->D("t2"), c->D("ovov_bare"), c->D("e"), c->o, c->v, c->stream);
+  clear_watchdog(c);
   if (dev_sync(c->stream) || dev_check()) return fail(c, RCCSDT_ERR_CUDA, "init_mp2 failed");
   c->have_amp = 1;
   c->have_int = c->have_res = 0;
@@ -2521,14 +2546,16 @@ RCC_API int rccsdt_build_intermediates(rccsdt_ctx* c) {
   int st = need(c, true, false, false);
   if (st) return st;
   st = do_intermediates(c);
-  return st ? st : (dev_sync(c->stream) ? fail(c, RCCSDT_ERR_CUDA, "intermediates failed") : 0);
+  if (!st && dev_sync(c->stream)) st = fail(c, RCCSDT_ERR_CUDA, "intermediates failed");
+  return st ? st : watchdog_status(c);
 }
 
 RCC_API int rccsdt_residual(rccsdt_ctx* c) {
   int st = need(c, true, true, false);
   if (st) return st;
   st = do_residual(c);
-  return st ? st : (dev_sync(c->stream) ? fail(c, RCCSDT_ERR_CUDA, "residual failed") : 0);
+  if (!st && dev_sync(c->stream)) st = fail(c, RCCSDT_ERR_CUDA, "residual failed");
+  return st ? st : watchdog_status(c);
 }
 
 RCC_API int rccsdt_postprocess(rccsdt_ctx* c, double norms[4]) {
@@ -2563,6 +2590,7 @@ RCC_API int rccsdt_iterate(rccsdt_ctx* c, double* e, double norms[4]) {
   if ((st = do_update(c))) return st;
   c->have_int = c->have_res = 0;
   if (dev_copy(&et, scal(c, 4), 8, c->stream) || dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "iterate");
+  if ((st = watchdog_status(c))) return st;
   if (!std::isfinite(et)) return fail(c, RCCSDT_ERR_NONFINITE, "non-finite energy");
   if (e) *e = et;
   return RCCSDT_OK;

@@ -100,24 +100,59 @@ def batch_instances(count: int = 64, seed: int = 0, weak: bool = True):
     return out
 
 
+def _orbit_copy(y: np.ndarray, perms) -> np.ndarray:
+    """Copy one drawn value to every image of its orbit under the axis permutations
+    ``perms`` (a group, identity included): each element takes the value of the
+    image with the smallest flat index.  Values keep all 53 bits; the symmetries
+    hold bit for bit because equal positions read the same draw."""
+    idx = np.arange(y.size).reshape(y.shape)
+    rep = idx
+    for p in perms:
+        rep = np.minimum(rep, idx.transpose(p))
+    return y.reshape(-1)[rep]
+
+
+_T2_PERMS = [(0, 1, 2, 3), (1, 0, 3, 2)]
+_S3 = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+_T3_PERMS = [p + tuple(3 + q for q in p) for p in _S3]
+
+
 def random_amplitudes(o: int, v: int, seed: int, scale: float = 0.05):
     """Seeded (t1, t2, t3) with the spin-free column symmetries, for parity tests.
 
     t2[i,j,a,b] = t2[j,i,b,a]; t3 is full [o,o,o,v,v,v] and invariant under the six
-    simultaneous permutations of its (occupied, virtual) column pairs.  These are
-    plain symmetrised random numbers, not solutions of any equation.
+    simultaneous permutations of its (occupied, virtual) column pairs.  One normal
+    draw per orbit of those permutations is copied to every image, so the values
+    carry full 53-bit mantissas (FP32 storage of T3 rounds them).  These are plain
+    random numbers, not solutions of any equation.
     """
     rng = np.random.default_rng(seed)
-    # values on a 2^-24 grid, so the symmetrising sums below are exact and the
-    # symmetries hold bit for bit
-    q = lambda a: np.round(a * 2.0 ** 24) / 2.0 ** 24  # noqa: E731
-    t1 = q(scale * rng.standard_normal((o, v)))
-    x = q(scale * rng.standard_normal((o, o, v, v)))
-    t2 = 0.5 * (x + x.transpose(1, 0, 3, 2))
-    y = q(scale * rng.standard_normal((o, o, o, v, v, v)))
-    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
-    t3 = np.zeros_like(y)
-    for p in perms:
-        t3 += y.transpose(p[0], p[1], p[2], 3 + p[0], 3 + p[1], 3 + p[2])
-    t3 /= 6.0        # equal sums give equal quotients
+    t1 = scale * rng.standard_normal((o, v))
+    t2 = _orbit_copy(scale * rng.standard_normal((o, o, v, v)), _T2_PERMS)
+    t3 = _orbit_copy(scale * rng.standard_normal((o, o, o, v, v, v)), _T3_PERMS)
     return t1, t2, t3
+
+
+def random_amplitudes_compact(o: int, v: int, seed: int, scale: float = 0.05):
+    """As ``random_amplitudes`` with T3 drawn directly in compact storage
+    ``t3c[n3][v][v][v]`` (colex blocks i <= j <= k, the library's layout), for sizes
+    whose full o^3 v^3 tensor is too large to draw.  Inside a stored block the
+    column symmetries that map the block onto itself are imposed by the same orbit
+    copy: a <-> b for i = j < k, b <-> c for i < j = k, all six orders of abc for
+    i = j = k."""
+    rng = np.random.default_rng(seed)
+    t1 = scale * rng.standard_normal((o, v))
+    t2 = _orbit_copy(scale * rng.standard_normal((o, o, v, v)), _T2_PERMS)
+    blocks = []
+    for k in range(o):
+        for j in range(k + 1):
+            for i in range(j + 1):
+                y = scale * rng.standard_normal((v, v, v))
+                if i == j == k:
+                    y = _orbit_copy(y, _S3)
+                elif i == j:
+                    y = _orbit_copy(y, [(0, 1, 2), (1, 0, 2)])
+                elif j == k:
+                    y = _orbit_copy(y, [(0, 1, 2), (0, 2, 1)])
+                blocks.append(y)
+    return t1, t2, np.ascontiguousarray(np.stack(blocks))

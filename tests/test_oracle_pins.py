@@ -107,6 +107,31 @@ def test_compact_residual_equals_full_residual():
     assert np.abs(C.pack(r3f) - r3c).max() < 1e-12 * scale
 
 
+@pytest.mark.parametrize("o,v", [(3, 5), (4, 4)])
+def test_compact_residual_norm_equals_full_storage_norm(o, v):
+    """The weighted compact norm (reading: |R|^2 = |r1|^2 + |r2|^2 + sum over stored
+    blocks of m(blk) |r3_blk|^2, m = 6/3/1) is the norm of the post-processed residual
+    on FULL storage, computed here from the full-storage equations alone.  Unit block
+    weights, or the weights reversed (1/3/6), miss it."""
+    inst = make_instance(o, v, naux=16, seed=o + 10 * v)
+    t1, t2, t3 = random_amplitudes(o, v, seed=3 * o + v)
+    r1, r2, r3f = full.residuals(inst.L, inst.fock_diag, t1, t2, t3)
+    p3f = full.postprocess_full(r3f)
+    ref = np.sqrt(np.sum(r1 ** 2) + np.sum(r2 ** 2) + np.sum(p3f ** 2))
+    r1c, r2c, r3c = C.residuals_compact(inst.L, inst.fock_diag, t1, t2, C.pack(t3))
+    p3c = C.postprocess(r3c, o)
+    got = C.residual_norm(r1c, r2c, p3c, o)
+    assert abs(got - ref) < 1e-12 * ref
+    # negative controls: other block weights give other norms
+    blk2 = np.sum(p3c.reshape(len(p3c), -1) ** 2, axis=1)
+    base = np.sum(r1c ** 2) + np.sum(r2c ** 2)
+    unit = np.sqrt(base + np.sum(blk2))
+    w = C.weights(o)
+    rev = np.sqrt(base + np.sum(np.where(w == 6, 1.0, np.where(w == 1, 6.0, 3.0)) * blk2))
+    assert abs(unit - ref) > 1e-3 * ref
+    assert abs(rev - ref) > 1e-3 * ref
+
+
 def test_compact_converged_energy_equals_full():
     inst = make_instance(3, 6, naux=20, seed=11, scale=0.2)
     Ec, *_ = C.solve_compact(inst.L, inst.fock_diag, 3, tol=1e-10, max_iter=300)

@@ -487,22 +487,22 @@ def run_ours(args, rank, world):
 
     # --- roofline of the dominant kernel (the pp-ladder GEMM)
     pk = peaks()
+    mm = measure_matmul_peaks()
     gemm_ms, gemm_n, gemm_flop = float(st[9]), float(st[10]), float(st[11])
     roof = None
     if gemm_n > 0 and gemm_ms > 0:
         achieved = (gemm_flop / gemm_n) / (gemm_ms / gemm_n / 1e3) / 1e12
         if prec == 0:
-            peak, bound, src = 1.25, "alu", "nominal FP64 1.25 TFLOP/s of the profiling recipe (DFMA path)"
+            peak, bound, src = mm["fp64_tflops"], "alu", "measured FP64 DGEMM (cuBLAS, this run; DFMA path)"
         elif prec == 1:
             peak, bound, src = pk.get("bf16_tflops_sustained", 1700.0) / 3.0, "tensor", \
                 "measured bf16 sustained / 3 (three BF16 products per FP32-accurate product)"
         else:
-            peak, bound, src = pk.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25) / 3.0, "tensor", \
-                "measured bf16 sustained x nominal tf32/bf16 ratio / 3"
-        # DRAM bytes per pp-ladder launch (mean of one sum and one difference GEMM) from an
-        # ncu capture of this workload and precision (profiles/k_gemm_tc_pp_o16v160w_traffic.md);
-        # other runs have none
-        traffic = 10.18e9 if (args.workload == "o16v160w" and prec == 1) else None
+            peak, bound, src = mm["tf32_tflops"] / 3.0, "tensor", \
+                "measured TF32 matmul (cuBLAS, this run) / 3"
+        # DRAM bytes per pp-ladder launch from an ncu capture of the same launch shape;
+        # none until the current kernel has been captured
+        traffic = None
         roof = {"kernel": "pp-ladder GEMM (k_gemm_f64)" if prec == 0 else "pp-ladder GEMM (k_gemm_tc)",
                 "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of "
@@ -543,7 +543,7 @@ def run_ours(args, rank, world):
                 "tflops": 2.0 * fma * world / (ms_total / 1e3 / args.steps) / 1e12,
                 "energy_last": energies[-1], "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                 "cpu_baseline": cpu, "clocks": clk.summary(), "fp64_vs_split": compare, "fp64_here": fp64_here,
-                "batch64": batch,
+                "batch64": batch, "matmul_peaks": mm,
                 "diis": "T1, T2 and T3" if diis_t3 else "T1 and T2 (T3 history would exceed 64 GB)",
                 "step_ms": step_ms}
         print(json.dumps(line), flush=True)

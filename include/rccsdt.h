@@ -95,11 +95,16 @@ typedef struct {
   long long pp_unit_bytes;   /* device bytes of one pp-ladder launch unit's T operand (v rows of
                                 v^2 doubles per stored block): the stored blocks are cut into
                                 ranges of that size, one GEMM per view and range (<= 0: 2 GiB) */
+  int diis_t3_nvir;          /* with diis_t3: the T3 part of the DIIS vectors keeps only the
+                                components t_ijk^abc with a, b, c < diis_t3_nvir (the lowest
+                                virtual orbitals in the given order; the subspace DIIS of
+                                Sec. III.A.4), the rest of T3 takes the plain Jacobi step;
+                                <= 0 or >= v: all of T3 */
 } rccsdt_options;
 
 /* Fills *opt with the defaults: FP64, DIIS(8) from iteration 2 including T3,
  * max_iter 100, tol 1e-8, grouped_bytes 8 GiB, unpack_bytes 1 GiB, autotune 0,
- * f64_tc 0, pp_unit_bytes 2 GiB. */
+ * f64_tc 0, pp_unit_bytes 2 GiB, diis_t3_nvir 0 (all of T3). */
 int rccsdt_options_default(rccsdt_options* opt);
 
 /* Creates a context for o occupied / v virtual orbitals and naux factors, on the
@@ -265,6 +270,40 @@ int rccsdt_batch_launch_times(const rccsdt_batch* b, double* ms, int cap);
 
 const char* rccsdt_batch_last_error(const rccsdt_batch* b);
 void rccsdt_batch_destroy(rccsdt_batch* b);
+
+/* ---------------------------------------------------------------------------
+ * RCCSDT(Q): the perturbative quadruples energy correction on the context's
+ * current (converged) t2 and compact t3 with the BARE Hamiltonian (T1 does not
+ * enter), Eq. ener-pt-q of the (Q) appendix with r = P(X + Y), z = P(X + V)
+ * (Eqs. resi-pt-q, q_t3_terms), the alternative intermediates of Eq. q_w_alter and
+ * the orbital-energy denominators, evaluated by the ABC-based algorithm of
+ * Sec. II.E.2: the one-time transposition of compact T3 to the virtual-triangular
+ * layout, then the sum over sorted virtual quadruples a <= b <= c <= d weighted by
+ * their degeneracy factors (Eq. ener-pt-q-abc).
+ * --------------------------------------------------------------------------- */
+typedef enum {
+  RCCSDT_Q_FP64 = 0,   /* FP64 arithmetic throughout */
+  RCCSDT_Q_FP32 = 1    /* FP32 operands and dot products, FP64 energy partial sums */
+} rccsdt_q_arith;
+
+/* Writes E_(Q) to *e_q (host).  info, if not NULL, receives 6 values: device ms of
+ * the T3 transposition, of the integrals and intermediates, and of the main kernel;
+ * the flop the main kernel executes (24 joint permutations x o^4 x (2v + 2o) FMA per
+ * sorted quadruple with a nonzero degeneracy factor); the number of such
+ * quadruples; the persistent grid.  Allocates its working buffers (the bare ERIs
+ * n^4, Wbar^{abc}_{ejk} o^2 v^4 and Wbar^{abm}_{ijk} o^4 v^2 in the arithmetic's
+ * type, the transposed T3) for the duration of the call and frees them.
+ * Errors: RCCSDT_ERR_ARG (NULL pointers, unknown arith), RCCSDT_ERR_STATE (no
+ * Hamiltonian or amplitudes), RCCSDT_ERR_OOM, RCCSDT_ERR_CUDA (also when a CUDA
+ * error was pending before the call), RCCSDT_ERR_NONFINITE. */
+int rccsdt_q_energy(rccsdt_ctx* ctx, int arith, double* e_q, double* info);
+
+/* The one-time transposition of Sec. II.E.2 (Fig. q_operation_counts(a)): compact
+ * T3 of the context (occupied-triangular, [n3][v][v][v]) written to t3v (host or
+ * device, float64) in the virtual-triangular layout t3v[nv3][o][o][o],
+ * nv3 = v(v+1)(v+2)/6, block (a <= b <= c) at C(c+2,3) + C(b+1,2) + a (colex, as
+ * the occupied blocks), element [i][j][k] = t_ijk^abc. */
+int rccsdt_t3_virtual_triangular(rccsdt_ctx* ctx, double* t3v);
 
 /* Residual norms for callers that cannot allocate device memory.  The paper has
  * no counterpart: this entry point exists for callers such as a framework that

@@ -306,11 +306,14 @@ def residual_norm(r1, r2, r3c, o):
 
 
 def solve_compact(L, fock_diag, o, tol=1e-10, max_iter=200, diis_space=8, diis_start=2,
-                  verbose=False, callback=None):
+                  verbose=False, callback=None, diis_t3_nvir=None):
     """RCCSDT iterations on compact storage from t1 = 0, t2 = MP2, t3 = 0.
 
     Each iteration: raw residuals, post-processing of R3, norm, energy, Jacobi
-    step, DIIS over (t1, t2, sqrt(m) t3c).  Returns (E, t1, t2, t3c, iters, history).
+    step, DIIS over (t1, t2, sqrt(m) t3c).  With ``diis_t3_nvir = ns`` the T3 part of
+    the DIIS vectors keeps only the components with all three virtual labels below
+    ns (the DIIS in a reduced virtual subspace of Sec. III.A.4); the other T3
+    components keep their Jacobi step.  Returns (E, t1, t2, t3c, iters, history).
     """
     e = np.asarray(fock_diag, dtype=np.float64)
     v = len(e) - o
@@ -319,6 +322,7 @@ def solve_compact(L, fock_diag, o, tol=1e-10, max_iter=200, diis_space=8, diis_s
     t3c = np.zeros((n3(o), v, v, v))
     d1, d2, d3 = full.denom1(e, o), full.denom2(e, o), denom3c(e, o)
     sw = np.sqrt(weights(o))[:, None, None, None]
+    ns = v if diis_t3_nvir is None or not 0 < diis_t3_nvir < v else diis_t3_nvir
     diis = full.Diis(diis_space)
     hist = []
     for it in range(1, max_iter + 1):
@@ -334,12 +338,14 @@ def solve_compact(L, fock_diag, o, tol=1e-10, max_iter=200, diis_space=8, diis_s
         if norm <= tol:
             return E, t1, t2, t3c, it, hist
         n1, n2, n3c = t1 + r1 / d1, t2 + r2 / d2, t3c + r3c / d3
-        vec = np.concatenate([n1.ravel(), n2.ravel(), (sw * n3c).ravel()])
-        old = np.concatenate([t1.ravel(), t2.ravel(), (sw * t3c).ravel()])
+        sub = (slice(None), slice(0, ns), slice(0, ns), slice(0, ns))
+        vec = np.concatenate([n1.ravel(), n2.ravel(), (sw * n3c)[sub].ravel()])
+        old = np.concatenate([t1.ravel(), t2.ravel(), (sw * t3c)[sub].ravel()])
         diis.push(vec, vec - old)
         if it >= diis_start:
             vec = diis.extrapolate()
         t1 = vec[: o * v].reshape(o, v)
         t2 = vec[o * v: o * v + (o * v) ** 2].reshape(o, o, v, v)
-        t3c = vec[o * v + (o * v) ** 2:].reshape(t3c.shape) / sw
+        t3c = n3c.copy()
+        t3c[sub] = vec[o * v + (o * v) ** 2:].reshape(len(t3c), ns, ns, ns) / sw
     raise RuntimeError(f"RCCSDT (compact) did not converge in {max_iter} iterations")

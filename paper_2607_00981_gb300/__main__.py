@@ -46,15 +46,37 @@ def main(argv=None):
     ap.add_argument("--resume", default=None, help="continue from a saved iteration state")
     ap.add_argument("--grouped-bytes", type=int, default=None,
                     help="memory budget of the grouped residual of split contexts (0: per-plan engine)")
+    ap.add_argument("--o", type=int, default=None, help="override the workload's occupied count (same v, naux)")
+    ap.add_argument("--pp-unit-bytes", type=int, default=None,
+                    help="bytes of one pp-ladder launch unit's T operand (option pp_unit_bytes)")
+    ap.add_argument("--diis-t3-nvir", type=int, default=0,
+                    help="DIIS on T3 over the lowest N virtual orbitals only (option diis_t3_nvir)")
+    ap.add_argument("--q", default=None, choices=["fp64", "fp32"],
+                    help="after the iterations (or the solve), the RCCSDT(Q) energy correction in this arithmetic")
     args = ap.parse_args(argv)
     spec = dict(WORKLOADS.get(args.workload) or CONVERGENCE[args.workload])
     if args.scale is not None:
         spec["scale"] = args.scale
+    if args.o is not None:
+        spec["o"] = args.o
     inst = make_instance(**spec)
     prec = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}[args.precision]
     extra = {} if args.grouped_bytes is None else {"grouped_bytes": args.grouped_bytes}
+    if args.pp_unit_bytes is not None:
+        extra["pp_unit_bytes"] = args.pp_unit_bytes
     ctx = pkg.context(inst.o, inst.v, inst.naux, precision=prec, diis_t3=0 if args.no_diis_t3 else 1,
-                      f64_tc=args.f64_tc, tol=args.tol, max_iter=args.max_iter, diis_space=args.diis_space, **extra)
+                      f64_tc=args.f64_tc, tol=args.tol, max_iter=args.max_iter, diis_space=args.diis_space,
+                      diis_t3_nvir=args.diis_t3_nvir, **extra)
+
+    def q_correction():
+        if args.q is None:
+            return
+        t0 = time.perf_counter()
+        eq, info = ctx.q_energy(0 if args.q == "fp64" else 1)
+        wall = time.perf_counter() - t0
+        print(json.dumps({"workload": args.workload, "o": inst.o, "v": inst.v, "q_arith": args.q, "e_q": eq,
+                          "seconds": wall, "main_tflops": info["flop"] / (info["main_ms"] / 1e3) / 1e12, **info}),
+              flush=True)
     ctx.set_hamiltonian(inst.fock_diag, inst.L)
     if args.resume:
         ctx.load(args.resume)
@@ -67,6 +89,7 @@ def main(argv=None):
                "diis_space": args.diis_space, "energy": e, "iterations": iters, "norm": norm, "converged": conv,
                "seconds": time.perf_counter() - t0}
         print(json.dumps(out), flush=True)
+        q_correction()
         if args.refine_fp64 and conv:
             t1, t2, t3 = ctx.amplitudes()
             ctx.close()
@@ -98,6 +121,7 @@ def main(argv=None):
                           "seconds": wall, "step_ms": {k: float(x) for k, x in zip(steps, ms[:9])}}), flush=True)
         e_prev = e
     ctx.enable_timing(False)
+    q_correction()
     if args.checkpoint:
         ctx.save(args.checkpoint)
     ctx.close()

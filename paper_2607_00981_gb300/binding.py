@@ -24,7 +24,7 @@ class Options(C.Structure):
                 ("diis_start", C.c_int), ("diis_t3", C.c_int), ("max_iter", C.c_int),
                 ("tol", C.c_double), ("watchdog_cycles", C.c_longlong), ("grouped_bytes", C.c_longlong),
                 ("unpack_bytes", C.c_longlong), ("autotune", C.c_int), ("f64_tc", C.c_int),
-                ("pp_unit_bytes", C.c_longlong)]
+                ("pp_unit_bytes", C.c_longlong), ("diis_t3_nvir", C.c_int)]
 
 
 class RccsdtError(RuntimeError):
@@ -68,13 +68,21 @@ _SIGS = {
     "rccsdt_batch_launch_times": (C.c_int, [_P, _P, C.c_int]),
     "rccsdt_batch_last_error": (C.c_char_p, [_P]),
     "rccsdt_batch_destroy": (None, [_P]),
+    "rccsdt_q_energy": (C.c_int, [_P, C.c_int, _P, _P]),
+    "rccsdt_t3_virtual_triangular": (C.c_int, [_P, _P]),
 }
+Q_FP64, Q_FP32 = 0, 1
 
 
 def load_library(path: str) -> C.CDLL:
+    """Load a build of the library and declare the signatures it exports (the
+    test-only host simulation has no (Q) kernels; the product library exports every
+    declared entry point, which tests/test_abi.py checks)."""
     lib = C.CDLL(path)
     for name, (res, args) in _SIGS.items():
-        fn = getattr(lib, name)
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
         fn.restype = res
         fn.argtypes = args
     return lib
@@ -208,6 +216,22 @@ class Context:
         r1, r2, r3 = np.empty((o, v)), np.empty((o, o, v, v)), np.empty((self.n3, v, v, v))
         self.get_residuals(r1, r2, r3)
         return r1, r2, r3
+
+    def q_energy(self, arith: int = Q_FP64):
+        """RCCSDT(Q) energy correction of the current amplitudes; returns (E_(Q), info)
+        with info = {transpose_ms, intermediates_ms, main_ms, flop, quadruples, grid}."""
+        e = np.zeros(1)
+        info = np.zeros(6)
+        self._check(self.lib.rccsdt_q_energy(self.h, arith, e.ctypes.data, info.ctypes.data))
+        keys = ["transpose_ms", "intermediates_ms", "main_ms", "flop", "quadruples", "grid"]
+        return float(e[0]), dict(zip(keys, info.tolist()))
+
+    def t3_virtual_triangular(self):
+        """Compact T3 transposed to the virtual-triangular layout [nv3][o][o][o]."""
+        nv3 = self.v * (self.v + 1) * (self.v + 2) // 6
+        out = np.empty((nv3, self.o, self.o, self.o))
+        self._check(self.lib.rccsdt_t3_virtual_triangular(self.h, out.ctypes.data))
+        return out
 
     def debug_copy(self, name: str, shape):
         out = np.empty(shape)

@@ -36,4 +36,21 @@ int ctx_ready(rccsdt_ctx* c);
 int ctx_prepare(rccsdt_ctx* c);
 int ctx_dims(const rccsdt_ctx* c, int* o, int* v);
 
+// What the (Q) correction reads from a context: the bare factors L[naux][n][n], the
+// Fock diagonal e[n], t2[o][o][v][v] (FP64) and compact T3 (FP32 in split contexts).
+struct QInputs {
+  const double* L;
+  const double* e;
+  const double* t2;
+  const void* t3;
+  int t3_f32;
+  int o, v, naux;
+  cudaStream_t stream;
+};
+// Fills *q; RCCSDT_ERR_STATE (with the context's error text) when the Hamiltonian or
+// the amplitudes are not set.
+int ctx_q_inputs(rccsdt_ctx* c, QInputs* q);
+// Records msg as the context's last error and returns code.
+int ctx_fail(rccsdt_ctx* c, int code, const char* msg);
+
 }  // namespace rcc

@@ -907,6 +907,32 @@ void launch_slot_save(char* base, i64 stride, i64 off, const int* st, const T* s
 template void launch_slot_save<double>(char*, i64, i64, const int*, const double*, i64, cudaStream_t);
 template void launch_slot_save<float>(char*, i64, i64, const int*, const float*, i64, cudaStream_t);
 
+// Virtual subspace of compact T3 (the T3 part of the DIIS vectors restricted to the
+// first ns virtual orbitals, the lowest in energy): sub[blk][a][b][c] <-> t3[blk][a][b][c]
+// for a, b, c < ns.  dir 0 gathers t3 -> sub, dir 1 scatters sub -> t3.
+template <typename T>
+__global__ void k_subcube(T* __restrict__ t3, T* __restrict__ sub, i64 n3, int v, int ns, int dir) {
+  const i64 S3 = (i64)ns * ns * ns, V3 = (i64)v * v * v, tot = n3 * S3;
+  for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < tot; x += (i64)gridDim.x * blockDim.x) {
+    const i64 blk = x / S3;
+    const int r = (int)(x - blk * S3);
+    const int c = r % ns, b = (r / ns) % ns, a = r / (ns * ns);
+    T* full = t3 + blk * V3 + ((i64)a * v + b) * v + c;
+    if (dir == 0) sub[x] = *full;
+    else *full = sub[x];
+  }
+}
+
+template <typename T>
+void launch_subcube(T* t3, T* sub, i64 n3, int v, int ns, int dir, cudaStream_t s) {
+  const i64 n = n3 * ns * ns * ns;
+  if (n <= 0) return;
+  ++g_launch_count;
+  k_subcube<T><<<ew_blocks(n), 256, 0, s>>>(t3, sub, n3, v, ns, dir);
+}
+template void launch_subcube<double>(double*, double*, i64, int, int, int, cudaStream_t);
+template void launch_subcube<float>(float*, float*, i64, int, int, int, cudaStream_t);
+
 // error slot: e = t - e (new minus old); amplitude slot: t
 template <typename T>
 __global__ void k_slot_diff_store(char* __restrict__ hist_t, char* __restrict__ hist_e, i64 stride, i64 off,

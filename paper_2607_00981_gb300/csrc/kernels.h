@@ -61,6 +61,10 @@ void launch_slot_save(char* base, i64 stride, i64 off, const int* st, const T* s
 template <typename T>
 void launch_slot_diff_store(char* hist_t, char* hist_e, i64 stride, i64 off, const int* st, const T* t, i64 n,
                             cudaStream_t s);
+// Virtual-subspace part of compact T3: sub[n3][ns][ns][ns] = t3[.][a<ns][b<ns][c<ns]
+// (dir 0), or written back into t3 (dir 1).
+template <typename T>
+void launch_subcube(T* t3, T* sub, i64 n3, int v, int ns, int dir, cudaStream_t s);
 template <typename T>
 void launch_diis_dots(const char* hist_e, i64 stride, i64 off, const int* st, int M, i64 n, i64 seg, const double* w,
                       double* partial, cudaStream_t s);

@@ -296,6 +296,7 @@ struct rccsdt_ctx {
   std::unique_ptr<DBuf> hist_t, hist_e;     // M slots each: t1 | t2 | t3 (padded)
   i64 hist_stride = 0;                      // bytes per slot
   i64 seg1 = 0, seg2 = 0, seg3 = 0;         // element counts
+  int ns = 0;                               // virtual orbitals of the T3 part of the DIIS vectors
   std::unique_ptr<DBuf> diis_st, diis_partial;  // device DIIS counters int[8]; dot partials [3][M][blocks]
   std::unique_ptr<DBuf> scalars, partial, splitk, rawX;
 
@@ -2270,14 +2271,23 @@ int do_update(rccsdt_ctx* c) {
   char* ht = c->hist_t ? (char*)c->hist_t->p : nullptr;
   char* he = c->hist_e ? (char*)c->hist_e->p : nullptr;
   const i64 S = c->hist_stride, off1 = 0, off2 = c->seg1 * 8, off3 = (c->seg1 + c->seg2) * 8;
+  // the T3 part of the DIIS vectors: T3 itself, or its virtual subspace gathered into t3sub
+  const bool sub = dt3 && M > 0 && c->ns < v;
+  void* t3d = sub ? c->B("t3sub")->p : c->B("t3")->p;
+  auto gather_sub = [&](int dir) {
+    if (!sub) return;
+    if (f) rcc::launch_subcube<float>(c->B("t3")->f(), (float*)t3d, c->n3, v, c->ns, dir, c->stream);
+    else rcc::launch_subcube<double>(c->D("t3"), (double*)t3d, c->n3, v, c->ns, dir, c->stream);
+  };
   if (M > 0) {
     // slot and counters on the device; the amplitudes before the step go to the error slot
     rcc::launch_diis_begin(st, M, c->opt.diis_start, c->stream);
     rcc::launch_slot_save<double>(he, S, off1, st, c->D("t1"), c->seg1, c->stream);
     rcc::launch_slot_save<double>(he, S, off2, st, c->D("t2"), c->seg2, c->stream);
     if (dt3) {
-      if (f) rcc::launch_slot_save<float>(he, S, off3, st, c->B("t3")->f(), c->seg3, c->stream);
-      else rcc::launch_slot_save<double>(he, S, off3, st, c->D("t3"), c->seg3, c->stream);
+      gather_sub(0);
+      if (f) rcc::launch_slot_save<float>(he, S, off3, st, (const float*)t3d, c->seg3, c->stream);
+      else rcc::launch_slot_save<double>(he, S, off3, st, (const double*)t3d, c->seg3, c->stream);
     }
   }
   rcc::launch_update_t12(c->D("t1"), c->D("r1"), c->D("t2"), c->D("r2"), c->D("e"), o, v, 0.0, c->stream);
@@ -2290,8 +2300,9 @@ int do_update(rccsdt_ctx* c) {
   rcc::launch_slot_diff_store<double>(ht, he, S, off1, st, c->D("t1"), c->seg1, c->stream);
   rcc::launch_slot_diff_store<double>(ht, he, S, off2, st, c->D("t2"), c->seg2, c->stream);
   if (dt3) {
-    if (f) rcc::launch_slot_diff_store<float>(ht, he, S, off3, st, c->B("t3")->f(), c->seg3, c->stream);
-    else rcc::launch_slot_diff_store<double>(ht, he, S, off3, st, c->D("t3"), c->seg3, c->stream);
+    gather_sub(0);
+    if (f) rcc::launch_slot_diff_store<float>(ht, he, S, off3, st, (const float*)t3d, c->seg3, c->stream);
+    else rcc::launch_slot_diff_store<double>(ht, he, S, off3, st, (const double*)t3d, c->seg3, c->stream);
   }
   c->diis_count += 1;
   // new row / column of B: <e_s, e_q> with the multiplicity weights on t3
@@ -2301,9 +2312,11 @@ int do_update(rccsdt_ctx* c) {
   rcc::launch_diis_dots<double>(he, S, off2, st, M, c->seg2, 1, nullptr, dp + G, c->stream);
   if (dt3) {
     if (f)
-      rcc::launch_diis_dots<float>(he, S, off3, st, M, c->seg3, c->V3, c->blk_weight->d(), dp + 2 * G, c->stream);
+      rcc::launch_diis_dots<float>(he, S, off3, st, M, c->seg3, c->seg3 / c->n3, c->blk_weight->d(), dp + 2 * G,
+                                   c->stream);
     else
-      rcc::launch_diis_dots<double>(he, S, off3, st, M, c->seg3, c->V3, c->blk_weight->d(), dp + 2 * G, c->stream);
+      rcc::launch_diis_dots<double>(he, S, off3, st, M, c->seg3, c->seg3 / c->n3, c->blk_weight->d(), dp + 2 * G,
+                                    c->stream);
   }
   rcc::launch_diis_row(dp, dt3 ? 3 : 2, st, M, scal(c, kB), c->stream);
   // extrapolation (the kernels skip themselves before diis_start or with one entry)
@@ -2314,11 +2327,13 @@ int do_update(rccsdt_ctx* c) {
                                        c->stream);
   if (dt3) {
     if (f)
-      rcc::launch_diis_extrapolate<float>(c->B("t3")->f(), (const float*)slot(c, 0).t3, c->hist_stride / 4, c->seg3,
+      rcc::launch_diis_extrapolate<float>((float*)t3d, (const float*)slot(c, 0).t3, c->hist_stride / 4, c->seg3,
                                           scal(c, kCoef), st, c->stream);
     else
-      rcc::launch_diis_extrapolate<double>(c->D("t3"), (const double*)slot(c, 0).t3, c->hist_stride / 8, c->seg3,
+      rcc::launch_diis_extrapolate<double>((double*)t3d, (const double*)slot(c, 0).t3, c->hist_stride / 8, c->seg3,
                                            scal(c, kCoef), st, c->stream);
+    // the subspace back into T3 (without extrapolation t3sub holds T3's own values)
+    gather_sub(1);
   }
   return check(c, "do_update");
 }
@@ -2355,6 +2370,7 @@ RCC_API int rccsdt_options_default(rccsdt_options* opt) {
   opt->autotune = 0;
   opt->f64_tc = 0;
   opt->pp_unit_bytes = 0;
+  opt->diis_t3_nvir = 0;
   return RCCSDT_OK;
 }
 
@@ -2426,7 +2442,14 @@ RCC_API int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, voi
     // DIIS history
     c->seg1 = (i64)o * v;
     c->seg2 = (i64)o * o * v * v;
-    c->seg3 = op.diis_t3 ? c->n3 * c->V3 : 0;
+    // the T3 part of the DIIS vectors: all of T3, or its first ns virtual orbitals
+    c->ns = (op.diis_t3_nvir > 0 && op.diis_t3_nvir < v) ? op.diis_t3_nvir : v;
+    const i64 S3 = (i64)c->ns * c->ns * c->ns;
+    c->seg3 = op.diis_t3 ? c->n3 * S3 : 0;
+    if (op.diis_t3 && op.diis_space > 0 && c->ns < v) {
+      const i64 t3b = op.precision != RCCSDT_FP64 ? 4 : 8;
+      alloc_buf(c, "t3sub", (size_t)(c->n3 * S3 * t3b), &err);
+    }
     const i64 t3e = op.precision != RCCSDT_FP64 ? 4 : 8;
     c->hist_stride = ((c->seg1 + c->seg2) * 8 + c->seg3 * t3e + 15) / 16 * 16;
     if (op.diis_space > 0) {
@@ -2925,6 +2948,23 @@ int ctx_prepare(rccsdt_ctx* c) {
   if (st) return st;
   return dev_sync(c->stream) ? fail(c, RCCSDT_ERR_CUDA, "autotune evaluation failed") : 0;
 }
+int ctx_q_inputs(rccsdt_ctx* c, QInputs* q) {
+  if (!c || !q) return RCCSDT_ERR_ARG;
+  if (!c->have_ham) return fail(c, RCCSDT_ERR_STATE, "hamiltonian not set");
+  if (!c->have_amp) return fail(c, RCCSDT_ERR_STATE, "amplitudes not set");
+  q->L = c->D("L");
+  q->e = c->D("e");
+  q->t2 = c->D("t2");
+  q->t3 = c->B("t3")->p;
+  q->t3_f32 = c->opt.precision != RCCSDT_FP64 ? 1 : 0;
+  q->o = c->o;
+  q->v = c->v;
+  q->naux = c->naux;
+  q->stream = c->stream;
+  return 0;
+}
+int ctx_fail(rccsdt_ctx* c, int code, const char* msg) { return fail(c, code, msg); }
+
 int ctx_dims(const rccsdt_ctx* c, int* o, int* v) {
   *o = c->o;
   *v = c->v;

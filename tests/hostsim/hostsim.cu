@@ -425,6 +425,22 @@ void launch_slot_diff_store(char* hist_t, char* hist_e, i64 stride, i64 off, con
 template void launch_slot_diff_store<double>(char*, char*, i64, i64, const int*, const double*, i64, cudaStream_t);
 template void launch_slot_diff_store<float>(char*, char*, i64, i64, const int*, const float*, i64, cudaStream_t);
 
+template <typename T>
+void launch_subcube(T* t3, T* sub, i64 n3, int v, int ns, int dir, cudaStream_t) {
+  const i64 S3 = (i64)ns * ns * ns, V3 = (i64)v * v * v;
+  for (i64 blk = 0; blk < n3; ++blk)
+    for (int a = 0; a < ns; ++a)
+      for (int b = 0; b < ns; ++b)
+        for (int c = 0; c < ns; ++c) {
+          T* full = t3 + blk * V3 + ((i64)a * v + b) * v + c;
+          T* part = sub + blk * S3 + ((i64)a * ns + b) * ns + c;
+          if (dir == 0) *part = *full;
+          else *full = *part;
+        }
+}
+template void launch_subcube<double>(double*, double*, i64, int, int, int, cudaStream_t);
+template void launch_subcube<float>(float*, float*, i64, int, int, int, cudaStream_t);
+
 // the host version keeps one partial per q (the device splits it over its fixed grid)
 template <typename T>
 void launch_diis_dots(const char* hist_e, i64 stride, i64 off, const int* st, int M, i64 n, i64 seg, const double* w,

@@ -139,6 +139,19 @@ def test_compact_converged_energy_equals_full():
     assert abs(Ec - Ef) < 1e-11
 
 
+def test_subspace_diis_reaches_the_same_fixed_point():
+    """DIIS over a virtual subspace of T3 (Sec. III.A.4) changes the path, not the
+    converged amplitudes: the energy equals the full-DIIS one; the whole space as the
+    subspace is the full DIIS iteration for iteration."""
+    inst = make_instance(3, 6, naux=20, seed=11, scale=0.2)
+    Ef, *_, itf, hf = C.solve_compact(inst.L, inst.fock_diag, 3, tol=1e-10, max_iter=300)
+    Es, *_, its, hs = C.solve_compact(inst.L, inst.fock_diag, 3, tol=1e-10, max_iter=300, diis_t3_nvir=3)
+    Ea, *_, ita, ha = C.solve_compact(inst.L, inst.fock_diag, 3, tol=1e-10, max_iter=300, diis_t3_nvir=6)
+    assert abs(Ef - Es) < 1e-11
+    assert ha == hf
+    assert hs[3][1] != hf[3][1]  # a different path
+
+
 def test_frozen_zero_t3_reduces_to_rccsd():
     """T3 = 0 in the RCCSDT equations gives the RCCSD residuals and energy."""
     o, v = 3, 5

@@ -199,3 +199,44 @@ def test_pp_pair_tiles_edges_on_host(prec, f64_tc, o, v, naux):
     assert np.abs(r2 - R2).max() / scale < tol
     assert np.abs(oc.postprocess(r3, o) - oc.postprocess(R3, o)).max() / scale < tol
     ctx.close()
+
+
+@pytest.mark.parametrize("kind", BACKENDS)
+@pytest.mark.parametrize("prec", [B.FP64, B.SPLIT_TF32X3], ids=["fp64", "tf32x3"])
+def test_subspace_diis_trajectory_matches_oracle(kind, prec):
+    """DIIS with T3 restricted to the 7 lowest of 12 virtual orbitals (the subspace
+    DIIS of Sec. III.A.4): energies and residual norms of six iterations of the o=3,
+    v=12 workload equal the oracle's iteration by iteration (FP32 T3 storage and
+    3xTF32 products: 1e-6 relative)."""
+    inst = workload("o3v12")
+    hist = []
+    try:
+        oc.solve_compact(inst.L, inst.fock_diag, 3, tol=1e-30, max_iter=6, diis_t3_nvir=7,
+                         callback=lambda it, E, n: hist.append((E, n)))
+    except RuntimeError:
+        pass
+    ctx = _ctx(kind, 3, 12, 40, precision=prec, diis_t3_nvir=7)
+    ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    ctx.init_mp2()
+    te, tn = (1e-10, 1e-9) if prec == B.FP64 else (1e-6, 1e-5)
+    for k in range(6):
+        e, norms = ctx.iterate()
+        assert abs(e - hist[k][0]) < te * max(1.0, abs(hist[k][0])), (k, e, hist[k][0])
+        assert abs(norms[3] - hist[k][1]) < tn * max(1.0, hist[k][1]), (k, norms[3], hist[k][1])
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind", BACKENDS)
+def test_subspace_diis_converges_to_the_oracle_energy(kind):
+    """The converged energy does not depend on the DIIS subspace: a solve with T3 in
+    DIIS over 4 of 8 virtual orbitals reaches the oracle's full-DIIS energy."""
+    o, v, naux = 3, 8, 20
+    inst = make_instance(o, v, naux, seed=11, scale=0.2)
+    E0 = oc.solve_compact(inst.L, inst.fock_diag, o, tol=1e-10, max_iter=300)[0]
+    ctx = _ctx(kind, o, v, naux, tol=1e-10, max_iter=300, diis_t3_nvir=4)
+    ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    ctx.init_mp2()
+    E, it, nrm, conv = ctx.solve()
+    assert conv and nrm <= 1e-10
+    assert abs(E - E0) < 1e-10
+    ctx.close()

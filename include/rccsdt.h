@@ -305,6 +305,38 @@ int rccsdt_q_energy(rccsdt_ctx* ctx, int arith, double* e_q, double* info);
  * the occupied blocks), element [i][j][k] = t_ijk^abc. */
 int rccsdt_t3_virtual_triangular(rccsdt_ctx* ctx, double* t3v);
 
+/* ---------------------------------------------------------------------------
+ * Compact T4 of RCCSDTQ (the step one rank above this library's RCCSDT path):
+ * the W^vv_vv * T4 particle-particle ladder on compact storage by direct
+ * traversal (Sec. II.C.4: six terms per stored block, each read from the same
+ * block after relabelling the paired columns), and the post-processing of R4
+ * (Sec. II.D: symmetrisation of blocks with two equal occupied indices as the
+ * average over the column swap, purification of blocks with three equal ones, and
+ * the projection 1 - Pi_[4] - Pi_[3,1] of Eq. T4ortho on every block).
+ * Storage: t4c[n4][v][v][v][v], n4 = o(o+1)(o+2)(o+3)/24, block (i<=j<=k<=l) at
+ * C(l+3,4) + C(k+2,3) + C(j+1,2) + i, element [a][b][c][d] = t_ijkl^abcd;
+ * W[a][b][e][f] = W^{ab}_{ef}, symmetric under (a,e) <-> (b,f).  In the split
+ * precisions T4 and R4 are stored in FP32 and the ladder runs as 3xBF16 / 3xTF32
+ * products on the tensor cores; in FP64 on the FP64 units.
+ * --------------------------------------------------------------------------- */
+typedef struct rccsdt_t4 rccsdt_t4;
+
+/* Allocates T4, R4 and the operand panels on the current device, work on `stream`.
+ * Limits: 1 <= o <= 32, 1 <= v <= 200.  Errors: RCCSDT_ERR_ARG, RCCSDT_ERR_OOM. */
+int rccsdt_t4_create(int o, int v, int precision, void* stream, rccsdt_t4** out);
+/* Sets W (v^4) and/or compact T4 (host or device float64; NULL leaves one as is). */
+int rccsdt_t4_set(rccsdt_t4* t4, const double* W, const double* t4c);
+/* R4 = the six-term ladder of the current W and T4 (overwrites R4).
+ * Errors: RCCSDT_ERR_STATE (W or T4 not set), RCCSDT_ERR_TIMEOUT, RCCSDT_ERR_CUDA. */
+int rccsdt_t4_pp_ladder(rccsdt_t4* t4);
+/* Symmetrise, purify and project R4 in place; *norm (if not NULL) = the full-tensor
+ * norm of the result (block multiplicities 24 / 12 / 6 / 4 / 1). */
+int rccsdt_t4_postprocess(rccsdt_t4* t4, double* norm);
+/* Copies R4 out (host or device float64, n4 v^4 values). */
+int rccsdt_t4_get_r4(rccsdt_t4* t4, double* r4c);
+const char* rccsdt_t4_last_error(const rccsdt_t4* t4);
+void rccsdt_t4_destroy(rccsdt_t4* t4);
+
 /* Residual norms for callers that cannot allocate device memory.  The paper has
  * no counterpart: this entry point exists for callers such as a framework that
  * owns all device memory through its own pool allocator (a raw cudaMalloc would

@@ -51,6 +51,9 @@ def main(argv=None):
                     help="bytes of one pp-ladder launch unit's T operand (option pp_unit_bytes)")
     ap.add_argument("--diis-t3-nvir", type=int, default=0,
                     help="DIIS on T3 over the lowest N virtual orbitals only (option diis_t3_nvir)")
+    ap.add_argument("--contract-fp64", action="store_true",
+                    help="split-storage context (FP32 T3) iterated with FP64 contractions throughout")
+    ap.add_argument("--until-tol", action="store_true", help="with --iters: stop once |R| <= --tol")
     ap.add_argument("--q", default=None, choices=["fp64", "fp32"],
                     help="after the iterations (or the solve), the RCCSDT(Q) energy correction in this arithmetic")
     args = ap.parse_args(argv)
@@ -78,6 +81,8 @@ def main(argv=None):
                           "seconds": wall, "main_tflops": info["flop"] / (info["main_ms"] / 1e3) / 1e12, **info}),
               flush=True)
     ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    if args.contract_fp64:
+        ctx.set_precision(0)
     if args.resume:
         ctx.load(args.resume)
     else:
@@ -120,6 +125,8 @@ def main(argv=None):
                           "r1": n[0], "r2": n[1], "r3": n[2], "r": n[3], "precision": args.precision,
                           "seconds": wall, "step_ms": {k: float(x) for k, x in zip(steps, ms[:9])}}), flush=True)
         e_prev = e
+        if args.until_tol and n[3] <= args.tol:
+            break
     ctx.enable_timing(False)
     q_correction()
     if args.checkpoint:

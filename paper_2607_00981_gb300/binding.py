@@ -70,6 +70,13 @@ _SIGS = {
     "rccsdt_batch_destroy": (None, [_P]),
     "rccsdt_q_energy": (C.c_int, [_P, C.c_int, _P, _P]),
     "rccsdt_t3_virtual_triangular": (C.c_int, [_P, _P]),
+    "rccsdt_t4_create": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, C.POINTER(_P)]),
+    "rccsdt_t4_set": (C.c_int, [_P, _P, _P]),
+    "rccsdt_t4_pp_ladder": (C.c_int, [_P]),
+    "rccsdt_t4_postprocess": (C.c_int, [_P, _P]),
+    "rccsdt_t4_get_r4": (C.c_int, [_P, _P]),
+    "rccsdt_t4_last_error": (C.c_char_p, [_P]),
+    "rccsdt_t4_destroy": (None, [_P]),
 }
 Q_FP64, Q_FP32 = 0, 1
 
@@ -308,3 +315,44 @@ class Batch:
         ms = np.zeros(cap)
         k = self.lib.rccsdt_batch_launch_times(self.h, ms.ctypes.data, cap)
         return ms[:k]
+
+
+class T4Engine:
+    """Compact T4 of RCCSDTQ: the six-term W^vv_vv * T4 ladder and the R4
+    post-processing (rccsdt_t4_* in include/rccsdt.h)."""
+
+    def __init__(self, lib, o: int, v: int, precision: int = FP64, stream: int = 0):
+        self.lib, self.o, self.v = lib, o, v
+        self.n4 = o * (o + 1) * (o + 2) * (o + 3) // 24
+        h = _P()
+        st = lib.rccsdt_t4_create(o, v, precision, _P(stream) if stream else None, C.byref(h))
+        if st != OK:
+            raise RccsdtError(st, "rccsdt_t4_create failed")
+        self.h = h
+
+    def _check(self, st):
+        if st != OK:
+            raise RccsdtError(st, self.lib.rccsdt_t4_last_error(self.h).decode())
+
+    def set(self, W=None, t4c=None):
+        self._check(self.lib.rccsdt_t4_set(self.h, _ptr(W), _ptr(t4c)))
+
+    def pp_ladder(self):
+        self._check(self.lib.rccsdt_t4_pp_ladder(self.h))
+
+    def postprocess(self) -> float:
+        nrm = np.zeros(1)
+        self._check(self.lib.rccsdt_t4_postprocess(self.h, nrm.ctypes.data))
+        return float(nrm[0])
+
+    def r4(self):
+        out = np.empty((self.n4, self.v, self.v, self.v, self.v))
+        self._check(self.lib.rccsdt_t4_get_r4(self.h, out.ctypes.data))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rccsdt_t4_destroy(self.h)
+            self.h = None
+
+    __del__ = close

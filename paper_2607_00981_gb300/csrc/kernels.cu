@@ -526,9 +526,14 @@ void launch_combine(const CombineArgs& c0, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 constexpr int kPostTL = 16;
 
+__device__ __forceinline__ double block_sum(double x);
+__global__ void k_sum(const double* __restrict__ partial, int np, double* __restrict__ out, double scale,
+                      int accumulate);
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __restrict__ rp,
-                                              const int4* __restrict__ blocks, int v, i64 n3) {
+                                              const int4* __restrict__ blocks, int v, i64 n3,
+                                              const double* __restrict__ wblk, double* __restrict__ partial) {
   constexpr int TL = kPostTL;
   // [16][17][17]: odd strides on both outer axes keep the permuted reads below 2-way bank conflicts
   typedef T Cube[TL][TL + 1][TL + 1];
@@ -573,7 +578,10 @@ __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __rest
   __syncthreads();
   const int n = ncube;
   const int tz = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double nrm = 0.0;  // sum over this CTA's outputs of m(blk) val^2 (the |R3|^2 share)
   for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
+    const double wb = wblk[b];
+    double bs = 0.0;
     const int4 ijk = blocks[b];
     const T* rb = r + b * V3;
     __syncthreads();  // the previous block's cubes are consumed
@@ -617,13 +625,25 @@ __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __rest
           val = sym - (rabc + racb + rbac + rbca + rcab + rcba) * (T)(1.0 / 6.0);
         }
         dst[(i64)(x0 + x) * V2] = val;
+        bs += (double)val * (double)val;
       }
     }
+    nrm += wb * bs;
   }
+  nrm = block_sum(nrm);
+  if (threadIdx.x == 0) partial[(i64)blockIdx.y * gridDim.x + blockIdx.x] = nrm;
+}
+
+int post_partials(int v, i64 n3) {
+  const int nt = (v + kPostTL - 1) / kPostTL;
+  const int norb = nt * (nt + 1) * (nt + 2) / 6;
+  const i64 gy = std::max<i64>(1, std::min<i64>(n3, (2048 + norb - 1) / norb));
+  return (int)(norb * gy);
 }
 
 template <typename T>
-void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStream_t s) {
+void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, const double* wblk, double* partial,
+                 double* norm2, cudaStream_t s) {
   if (n3 <= 0) return;
   const int nt = (v + kPostTL - 1) / kPostTL;
   const int norb = nt * (nt + 1) * (nt + 2) / 6;
@@ -636,10 +656,14 @@ void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStrea
     attr = true;
   }
   ++g_launch_count;
-  k_post<T><<<dim3((unsigned)norb, (unsigned)gy), 256, smem, s>>>(r, rp, blocks, v, n3);
+  k_post<T><<<dim3((unsigned)norb, (unsigned)gy), 256, smem, s>>>(r, rp, blocks, v, n3, wblk, partial);
+  ++g_launch_count;
+  k_sum<<<1, 256, 0, s>>>(partial, norb * (int)gy, norm2, 1.0, 0);
 }
-template void launch_post<double>(const double*, double*, const int4*, int, i64, cudaStream_t);
-template void launch_post<float>(const float*, float*, const int4*, int, i64, cudaStream_t);
+template void launch_post<double>(const double*, double*, const int4*, int, i64, const double*, double*, double*,
+                                  cudaStream_t);
+template void launch_post<float>(const float*, float*, const int4*, int, i64, const double*, double*, double*,
+                                 cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Jacobi updates with the bare Fock diagonal (orbital energies e[0..n)).

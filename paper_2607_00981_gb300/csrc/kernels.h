@@ -43,8 +43,13 @@ void launch_r3_gather(const float* X, const i64* target, int ntarget, const int*
 void launch_gemm_f64(const double* A, const double* B, int K, int lda, int ldb, const EpiArgs& e,
                      double* scratch, i64 scratch_elems, cudaStream_t s);
 void launch_combine(const CombineArgs& c, cudaStream_t s);
+// Symmetrise, purify and orthogonalise compact R3 (r -> rp) and, in the same pass,
+// *norm2 = sum over blocks of wblk[b] |rp_b|^2 (fixed-order sums over the
+// post_partials(v, n3) entries of `partial`).
 template <typename T>
-void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStream_t s);
+void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, const double* wblk, double* partial,
+                 double* norm2, cudaStream_t s);
+int post_partials(int v, i64 n3);
 void launch_update_t12(double* t1, const double* r1, double* t2, const double* r2, const double* e,
                        int o, int v, double shift, cudaStream_t s);
 template <typename T>

@@ -49,6 +49,7 @@ namespace {
 using rcc::i64;
 
 constexpr int kThreadsQ = 256;
+constexpr int kMaxVQ = 256;  // largest v of the (Q) kernels (per-CTA tables)
 
 // The 24 permutations of four positions (sigma[x] = source position of position x)
 __constant__ unsigned char c_perm[24][4];
@@ -239,10 +240,20 @@ __device__ __forceinline__ double block_sum_q(double x, double* ws) {
   return t;  // valid in thread 0
 }
 
+// Position pair {x, y} (x < y) of the quadruple's labels -> index 0..5.
+__device__ __forceinline__ int pair_index(int x, int y) {
+  // (0,1) 0, (0,2) 1, (0,3) 2, (1,2) 3, (1,3) 4, (2,3) 5
+  return x == 0 ? y - 1 : (x == 1 ? y + 1 : 5);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreadsQ) k_q_main(const QArgs q) {
   extern __shared__ unsigned char q_smem[];
   __shared__ double ws[32];
+  // per label-position pair {x < y} and summation label e: the element offset (block
+  // index times o^3) of the stored block sorted(e, L[x], L[y]); the rank of e in that
+  // triple, which fixes the occupied order, follows from the range of e
+  __shared__ i64 s_blk[6][kMaxVQ];
   const int o = q.o, v = q.v;
   const i64 O4 = (i64)o * o * o * o;
   T* R = q.smem_rz ? (T*)q_smem : (T*)q.scratch + (i64)blockIdx.x * 2 * O4;
@@ -256,23 +267,44 @@ __global__ void __launch_bounds__(kThreadsQ) k_q_main(const QArgs q) {
   const T* T2e = (const T*)q.T2e;
   const T* T2m = (const T*)q.T2m;
   const T* T2v = (const T*)q.T2v;
-  const i64 o2 = (i64)o * o, o3 = o2 * o, V2 = (i64)v * v;
+  const i64 o2 = (i64)o * o, o3 = o2 * o;
   double total = 0.0;
   for (i64 qi = blockIdx.x; qi < q.nquad; qi += gridDim.x) {
     const int4 L4 = q.quads[qi];
     const int L[4] = {L4.x & 0xffff, L4.x >> 16, L4.y & 0xffff, L4.y >> 16};
     const double fac = (double)L4.z;
+    __syncthreads();  // s_blk of the previous quadruple is consumed
+    for (int t = threadIdx.x; t < 6 * v; t += blockDim.x) {
+      const int pi = t / v, e = t % v;
+      const int x = pi < 3 ? 0 : (pi < 5 ? 1 : 2), y = pi < 3 ? pi + 1 : (pi < 5 ? pi - 1 : 3);
+      const int r0 = L[x], s0 = L[y];  // r0 <= s0 (L is sorted)
+      const i64 b = e <= r0 ? tri3(e, r0, s0) : (e <= s0 ? tri3(r0, e, s0) : tri3(r0, s0, e));
+      s_blk[pi][e] = b * o3;
+    }
+    __syncthreads();
     // (a) R = P(X + Y), Z = P(X + V) for every occupied tuple
     for (i64 el = threadIdx.x; el < O4; el += blockDim.x) {
       const int Oc[4] = {(int)(el / o3), (int)((el / o2) % o), (int)((el / o) % o), (int)(el % o)};
       T rr = 0, zz = 0;
       for (int sg = 0; sg < 24; ++sg) {
-        const int p = L[c_perm[sg][0]], qq = L[c_perm[sg][1]], r = L[c_perm[sg][2]], s = L[c_perm[sg][3]];
-        const int i = Oc[c_perm[sg][0]], j = Oc[c_perm[sg][1]], k = Oc[c_perm[sg][2]], l = Oc[c_perm[sg][3]];
+        const int c0 = c_perm[sg][0], c1 = c_perm[sg][1], c2 = c_perm[sg][2], c3 = c_perm[sg][3];
+        const int p = L[c0], qq = L[c1], r = L[c2], s = L[c3];
+        const int i = Oc[c0], j = Oc[c1], k = Oc[c2], l = Oc[c3];
         // X: 1/2 sum_e v^{pq}_{ej} t^{ers}_{ikl} - 1/2 sum_m v^{pm}_{ij} t^{qrs}_{mkl}
+        // t^{ers}_{ikl}: sorted triple (e, r0, s0) | (r0, e, s0) | (r0, s0, e) by the range of e,
+        // (r0, s0) = the pair's labels in position order with their occupied indices (k0, l0)
+        const bool rs = c2 < c3;
+        const int r0 = rs ? r : s, s0 = rs ? s : r, k0 = rs ? k : l, l0 = rs ? l : k;
+        const i64* bt = s_blk[pair_index(rs ? c2 : c3, rs ? c3 : c2)];
         const T* a1 = A1 + (((i64)p * v + qq) * o + j) * v;
         T x1 = 0;
-        for (int e = 0; e < v; ++e) x1 += a1[e] * t3v[t3v_off(e, r, s, i, k, l, o)];
+        {
+          const i64 f0 = ((i64)i * o + k0) * o + l0, f1 = ((i64)k0 * o + i) * o + l0, f2 = ((i64)k0 * o + l0) * o + i;
+          int e = 0;
+          for (; e <= r0; ++e) x1 += a1[e] * t3v[bt[e] + f0];
+          for (; e <= s0; ++e) x1 += a1[e] * t3v[bt[e] + f1];
+          for (; e < v; ++e) x1 += a1[e] * t3v[bt[e] + f2];
+        }
         const T* a2 = A2 + (((i64)p * o + i) * o + j) * o;
         const i64 b0 = t3v_off(qq, r, s, 0, k, l, o), bm = t3v_off(qq, r, s, 1, k, l, o) - b0;
         T x2 = 0;
@@ -312,7 +344,6 @@ __global__ void __launch_bounds__(kThreadsQ) k_q_main(const QArgs q) {
     }
     const double bs = block_sum_q(part, ws);
     if (threadIdx.x == 0) total += fac * bs;
-    __syncthreads();  // R and Z are rewritten by the next quadruple
   }
   if (threadIdx.x == 0) q.partial[blockIdx.x] = total;
 }
@@ -436,7 +467,8 @@ int q_energy(rccsdt_ctx* ctx, const rcc::QInputs& in, double* e_q, double* info)
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const bool in_smem = rz_bytes + 1024 <= (size_t)std::min(smem_optin, 200 * 1024);
-  const int per_sm = in_smem ? std::max(1, std::min(4, (int)((220 * 1024) / (rz_bytes + 2048)))) : 4;
+  // resident CTAs per SM: the dynamic R and Z plus the static tables (about 13 KB)
+  const int per_sm = in_smem ? std::max(1, std::min(4, (int)((224 * 1024) / (rz_bytes + 14 * 1024)))) : 4;
   const int grid = (int)std::max<i64>(1, std::min<i64>(nquad, (i64)nsm * per_sm));
 
   DevBuf G, t3v, A1, A2, Vv, W1, W2, T2e, T2m, T2v, vtr, qd, scratch, partial, outd;
@@ -524,7 +556,7 @@ RCC_API int rccsdt_q_energy(rccsdt_ctx* ctx, int arith, double* e_q, double* inf
   int st = rcc::ctx_q_inputs(ctx, &in);
   if (st) return st;
   if (cudaPeekAtLastError() != cudaSuccess) return rcc::ctx_fail(ctx, RCCSDT_ERR_CUDA, "(Q): pending CUDA error");
-  if (in.v > 65535) return rcc::ctx_fail(ctx, RCCSDT_ERR_ARG, "(Q): v too large");
+  if (in.v > kMaxVQ) return rcc::ctx_fail(ctx, RCCSDT_ERR_ARG, "(Q): v above 256");
   return arith == RCCSDT_Q_FP64 ? q_energy<double>(ctx, in, e_q, info) : q_energy<float>(ctx, in, e_q, info);
 }
 

@@ -1162,6 +1162,8 @@ int build_context(rccsdt_ctx* c) {
         }
     c->blocks_info = upload_vec(c, info, &err);
     c->blk_weight = upload_vec(c, w, &err);
+    // per-CTA partial sums of |R3|^2 formed by the post-processing pass
+    alloc_buf(c, "post_partial", (size_t)rcc::post_partials(v, n3) * 8, &err);
   }
   // --- selector tables
   std::unique_ptr<DBuf> rt2, rt3;
@@ -2214,22 +2216,19 @@ int do_postprocess(rccsdt_ctx* c, double norms[4]) {
   StepTimer tm(c, 6);
   const int4* blk = (const int4*)c->blocks_info->p;
   const bool f = c->opt.precision != RCCSDT_FP64;
-  const i64 V3 = c->V3;
+  // post-processing with |R3|^2 (block multiplicities) formed in the same pass
+  double* pp = (double*)c->B("post_partial")->p;
   if (f)
-    rcc::launch_post<float>(c->B("r3")->f(), c->B("rp3")->f(), blk, c->v, c->n3, c->stream);
+    rcc::launch_post<float>(c->B("r3")->f(), c->B("rp3")->f(), blk, c->v, c->n3, c->blk_weight->d(), pp, scal(c, 2),
+                            c->stream);
   else
-    rcc::launch_post<double>(c->D("r3"), c->D("rp3"), blk, c->v, c->n3, c->stream);
+    rcc::launch_post<double>(c->D("r3"), c->D("rp3"), blk, c->v, c->n3, c->blk_weight->d(), pp, scal(c, 2),
+                             c->stream);
 
   rcc::launch_wdot<double>(c->D("r1"), c->D("r1"), (i64)c->o * c->v, 1, nullptr, partials(c), scal(c, 0), 1.0, 0,
                            c->stream);
   rcc::launch_wdot<double>(c->D("r2"), c->D("r2"), (i64)c->o * c->o * c->v * c->v, 1, nullptr, partials(c),
                            scal(c, 1), 1.0, 0, c->stream);
-  if (f)
-    rcc::launch_wdot<float>(c->B("rp3")->f(), c->B("rp3")->f(), c->n3 * V3, V3, c->blk_weight->d(), partials(c),
-                            scal(c, 2), 1.0, 0, c->stream);
-  else
-    rcc::launch_wdot<double>(c->D("rp3"), c->D("rp3"), c->n3 * V3, V3, c->blk_weight->d(), partials(c), scal(c, 2),
-                             1.0, 0, c->stream);
   if (norms) {
     double h[3];
     if (dev_copy(h, scal(c, 0), sizeof(h), c->stream) || dev_sync(c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");

@@ -156,3 +156,25 @@ def random_amplitudes_compact(o: int, v: int, seed: int, scale: float = 0.05):
                     y = _orbit_copy(y, [(0, 1, 2), (0, 2, 1)])
                 blocks.append(y)
     return t1, t2, np.ascontiguousarray(np.stack(blocks))
+
+
+_S4 = [(0, 1, 2, 3), (0, 1, 3, 2), (0, 2, 1, 3), (0, 2, 3, 1), (0, 3, 1, 2), (0, 3, 2, 1),
+       (1, 0, 2, 3), (1, 0, 3, 2), (1, 2, 0, 3), (1, 2, 3, 0), (1, 3, 0, 2), (1, 3, 2, 0),
+       (2, 0, 1, 3), (2, 0, 3, 1), (2, 1, 0, 3), (2, 1, 3, 0), (2, 3, 0, 1), (2, 3, 1, 0),
+       (3, 0, 1, 2), (3, 0, 2, 1), (3, 1, 0, 2), (3, 1, 2, 0), (3, 2, 0, 1), (3, 2, 1, 0)]
+
+
+def random_t4(o: int, v: int, seed: int, scale: float = 0.05):
+    """Seeded full quadruples tensor t4[i,j,k,l,a,b,c,d] invariant under the 24 joint
+    permutations of its (occupied, virtual) column pairs (one full-precision draw per
+    orbit, copied to every image), for small sizes."""
+    rng = np.random.default_rng(seed)
+    perms = [p + tuple(4 + q for q in p) for p in _S4]
+    return _orbit_copy(scale * rng.standard_normal((o,) * 4 + (v,) * 4), perms)
+
+
+def random_pair_symmetric(v: int, seed: int, scale: float = 0.1):
+    """Seeded W[a,b,e,f] with the pair-exchange symmetry W[a,b,e,f] = W[b,a,f,e] (the
+    symmetry of the particle-particle ladder intermediate), full-precision values."""
+    rng = np.random.default_rng(seed)
+    return _orbit_copy(scale * rng.standard_normal((v, v, v, v)), [(0, 1, 2, 3), (1, 0, 3, 2)])

@@ -343,16 +343,27 @@ template void launch_r3_gather<double>(const float*, const i64*, int, const int*
                                        const float*, int, int, double*, cudaStream_t);
 
 template <typename T>
-void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, cudaStream_t) {
+void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, const double* wblk, double*, double* norm2,
+                 cudaStream_t) {
   const i64 V3 = (i64)v * v * v;
-  for (i64 b = 0; b < n3; ++b)
+  double s = 0.0;
+  for (i64 b = 0; b < n3; ++b) {
+    double bs = 0.0;
     for (i64 e = 0; e < V3; ++e) {
       const int c = (int)(e % v), bb = (int)((e / v) % v), a = (int)(e / ((i64)v * v));
-      rp[b * V3 + e] = post_value<T>(r + b * V3, v, blocks[b].x, blocks[b].y, blocks[b].z, a, bb, c);
+      const T x = post_value<T>(r + b * V3, v, blocks[b].x, blocks[b].y, blocks[b].z, a, bb, c);
+      rp[b * V3 + e] = x;
+      bs += (double)x * (double)x;
     }
+    s += wblk[b] * bs;
+  }
+  *norm2 = s;
 }
-template void launch_post<double>(const double*, double*, const int4*, int, i64, cudaStream_t);
-template void launch_post<float>(const float*, float*, const int4*, int, i64, cudaStream_t);
+template void launch_post<double>(const double*, double*, const int4*, int, i64, const double*, double*, double*,
+                                  cudaStream_t);
+template void launch_post<float>(const float*, float*, const int4*, int, i64, const double*, double*, double*,
+                                 cudaStream_t);
+int post_partials(int, i64) { return 1; }
 
 void launch_update_t12(double* t1, const double* r1, double* t2, const double* r2, const double* e, int o, int v,
                        double shift, cudaStream_t) {

@@ -398,3 +398,67 @@ def test_virtual_triangular_layout_is_a_bijection():
     t3v = Qc.pack_virtual_triangular(t3c, o)
     assert t3v.shape == (v * (v + 1) * (v + 2) // 6, o, o, o)
     assert np.array_equal(Qc.unpack_virtual_triangular(t3v, o, v), t3)
+
+
+# ---------------------------------------------------------------- compact T4 (Sec. II.C.4, II.D, appendix B)
+
+def test_t4_compact_pp_ladder_equals_full_definition():
+    """The six-term direct traversal of W^vv_vv * T4 on compact storage equals the
+    full-storage definition P_(ia)(jb)(kc)(ld) 1/4 sum_ef W^{ab}_{ef} t^{efcd}_{ijkl}
+    on every stored block (degenerate ones included); a dropped term fails."""
+    from oracle import quadruples as Q
+    from paper_2607_00981_gb300.synth import random_pair_symmetric, random_t4
+    o, v = 3, 4
+    W = random_pair_symmetric(v, seed=1)
+    t4 = random_t4(o, v, seed=2)
+    full = Q.pack4(Q.pp_ladder_full(W, t4))
+    comp = Q.pp_ladder_compact(W, Q.pack4(t4), o)
+    assert np.abs(full - comp).max() < 1e-13 * np.abs(full).max()
+    assert np.array_equal(Q.unpack4(Q.pack4(t4), o), t4)
+    # negative control: the last of the six terms left out
+    T = Q.pack4(t4)
+    partial = comp - np.stack([np.einsum("cdef,abef->abcd", W, T[b]) for b in range(len(T))])
+    assert np.abs(full - partial).max() > 1e-3 * np.abs(full).max()
+
+
+def test_t4_projector_polynomial_equals_character_projector():
+    """(Omega - 6)(Omega - 2)(2 Omega^2 + 19 Omega + 48)/576 = 1 - Pi_[4] - Pi_[3,1]
+    (appendix B): idempotent, rank 14, and its kernel is the null space of the
+    spin-free overlap matrix of four virtual labels."""
+    from oracle import quadruples as Q
+    P = Q.projector_polynomial()
+    assert np.abs(P - Q.projector_from_characters()).max() < 1e-13
+    assert np.abs(P @ P - P).max() < 1e-13
+    assert abs(np.trace(P) - 14.0) < 1e-12
+    M = nullspace.overlap_matrix(4)
+    assert np.abs(M @ (np.eye(24) - P)).max() < 1e-10   # the removed part is M's null space
+    assert np.linalg.matrix_rank(M) == 14
+
+
+def test_t4_block_projection_matches_the_matrix_on_distinct_labels():
+    """orthogonalise4_block on a v^4 block acts, on the 24 orderings of four distinct
+    labels, as the projector matrix; it annihilates a fully symmetric block."""
+    from oracle import quadruples as Q
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((4, 4, 4, 4))
+    out = Q.orthogonalise4_block(B)
+    P = Q.projector_polynomial()
+    vec = np.array([B[p] for p in Q.PERMS4])
+    assert np.abs(np.array([out[p] for p in Q.PERMS4]) - P @ vec).max() < 1e-12
+    S = sum(np.transpose(B, p) for p in Q.PERMS4)
+    assert np.abs(Q.orthogonalise4_block(S)).max() < 1e-11
+
+
+def test_t4_symmetrise_and_purify_on_column_symmetric_input():
+    """A column-symmetric T4 is already symmetric inside its degenerate blocks
+    (symmetrisation leaves it unchanged); purification zeroes exactly the blocks with
+    three equal occupied indices."""
+    from oracle import quadruples as Q
+    from paper_2607_00981_gb300.synth import random_t4
+    o, v = 4, 3
+    t4c = Q.pack4(random_t4(o, v, seed=4))
+    assert np.abs(Q.symmetrise4(t4c, o) - t4c).max() < 1e-15
+    p = Q.purify4(t4c, o)
+    for b, (i, j, k, l) in enumerate(Q.quads(o)):
+        three = i == j == k or j == k == l
+        assert (np.all(p[b] == 0.0)) == three or not np.any(t4c[b])

@@ -1,0 +1,56 @@
+"""Compact T4 of RCCSDTQ on the GPU (rccsdt_t4_*) against the FP64 oracle
+(``oracle.quadruples``, pinned in test_oracle_pins.py to the full-storage definition
+of the ladder and to the character projector of appendix B).
+
+* The six-term W^vv_vv * T4 ladder by direct traversal (Sec. II.C.4): FP64 1e-12,
+  3xBF16 5e-5, 3xTF32 5e-6 relative to the largest element.
+* Post-processing of R4 (Sec. II.D, Eq. T4ortho) and its full-tensor norm: 1e-12 of
+  the GPU's own ladder output (FP64), the same bars as the ladder in split storage.
+Sizes: ragged 32-label tiles (v = 33), degenerate and purified blocks, o = 1.
+"""
+import numpy as np
+import pytest
+
+from oracle import quadruples as Q
+from paper_2607_00981_gb300 import binding as B
+from paper_2607_00981_gb300.synth import random_pair_symmetric, random_t4
+
+from ._helpers import gpu_lib
+
+TOL = {B.FP64: 1e-12, B.SPLIT_BF16X3: 5e-5, B.SPLIT_TF32X3: 5e-6}
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [B.FP64, B.SPLIT_BF16X3, B.SPLIT_TF32X3], ids=["fp64", "bf16x3", "tf32x3"])
+@pytest.mark.parametrize("o,v", [(1, 6), (3, 5), (4, 7), (2, 33)])
+def test_t4_ladder_and_postprocess_match_oracle(prec, o, v):
+    W = random_pair_symmetric(v, seed=o + v)
+    t4c = Q.pack4(random_t4(o, v, seed=3 * o + v))
+    R = Q.pp_ladder_compact(W, t4c, o)
+    P = Q.postprocess4(R, o)
+    eng = B.T4Engine(gpu_lib(), o, v, precision=prec)
+    eng.set(W, t4c)
+    eng.pp_ladder()
+    r4 = eng.r4()
+    scale = max(1.0, np.abs(R).max())
+    tol = TOL[prec]
+    assert np.abs(r4 - R).max() / scale < tol
+    norm = eng.postprocess()
+    p4 = eng.r4()
+    assert np.abs(p4 - P).max() / scale < tol
+    ref = Q.residual_norm4(P, o)
+    assert abs(norm - ref) <= tol * max(1.0, ref)
+    if prec == B.FP64:  # the pass itself, on the GPU's own ladder output
+        assert np.abs(p4 - Q.postprocess4(r4, o)).max() <= 1e-13 * scale
+    eng.close()
+
+
+@pytest.mark.gpu
+def test_t4_errors():
+    with pytest.raises(B.RccsdtError):
+        B.T4Engine(gpu_lib(), 0, 4)
+    eng = B.T4Engine(gpu_lib(), 2, 3)
+    with pytest.raises(B.RccsdtError) as ei:
+        eng.pp_ladder()  # nothing set yet
+    assert ei.value.status == B.ERR_STATE
+    eng.close()

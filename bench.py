@@ -339,6 +339,78 @@ def batch_solve(pkg, insts, prec, autotune, max_iter=100, tol=1e-8, host=False, 
             "h2d_bytes": h2d, "d2h_bytes": int(8 * 8 * len(insts)), "infos": infos}
 
 
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07  # SMs x FP32 lanes x 2 flop x max SM clock (GHz) / 1e3
+
+
+def q_summary(pkg, stream, mm):
+    """RCCSDT(Q) energy correction (ABC-based, Sec. II.E.2) on the o6v48w workload after
+    two iterations from the MP2 guess, FP64 and FP32 arithmetic: device time of each
+    phase, TFLOP/s of the main kernel (the flop it executes) and its fraction of the
+    ALU peak (measured DGEMM for FP64; FP32 lanes x clock for FP32)."""
+    from paper_2607_00981_gb300.synth import workload
+    inst = workload("o6v48w")
+    ctx = pkg.context(inst.o, inst.v, inst.naux, stream=stream.cuda_stream, precision=0)
+    ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    ctx.init_mp2()
+    for _ in range(2):
+        ctx.iterate()
+    out = {"workload": "o6v48w: (Q) on the amplitudes after two RCCSDT iterations, o=6 v=48"}
+    for label, arith, peak in (("fp64", 0, mm["fp64_tflops"]), ("fp32", 1, FP32_SIMT_TFLOPS)):
+        ctx.q_energy(arith)  # warm-up
+        e, info = ctx.q_energy(arith)
+        tf = info["flop"] / (info["main_ms"] / 1e3) / 1e12
+        out[label] = {"e_q": e, "transpose_ms": info["transpose_ms"], "intermediates_ms": info["intermediates_ms"],
+                      "main_ms": info["main_ms"], "quadruples": int(info["quadruples"]), "main_tflops": tf,
+                      "roofline": {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                                   "frac": tf / peak, "peak_source": "measured DGEMM (this run)" if arith == 0 else
+                                   "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}}
+    out["fp32_rel_error_vs_fp64"] = abs(out["fp32"]["e_q"] - out["fp64"]["e_q"]) / abs(out["fp64"]["e_q"])
+    ctx.close()
+    return out
+
+
+def t4_summary(pkg, stream, pk):
+    """Compact T4 ladder (six-term direct traversal, Sec. II.C.4) and R4 post-processing
+    at o=6, v=40 (126 stored blocks of 40^4) in 3xBF16 and 3xTF32: device time,
+    TFLOP/s of the ladder (2 x 6 n4 v^6 flop) against the split roof, and the GB/s of
+    the post-processing pass (R4 read + written once) against the measured copy rate."""
+    import torch
+    from paper_2607_00981_gb300 import binding as B
+    from paper_2607_00981_gb300.synth import random_pair_symmetric
+    o, v = 6, 40
+    n4 = o * (o + 1) * (o + 2) * (o + 3) // 24
+    rng = np.random.default_rng(6)
+    W = random_pair_symmetric(v, seed=40)
+    # T4 values need no symmetry to time the kernels
+    t4c = torch.from_numpy(0.05 * rng.standard_normal((n4, v, v, v, v))).cuda()
+    flop = 2.0 * 6 * n4 * v ** 6
+    out = {"workload": f"o={o} v={v}: {n4} stored blocks of v^4, seeded W (pair-symmetric) and T4"}
+    for label, prec, peak in (("bf16x3", B.SPLIT_BF16X3, pk.get("bf16_tflops", 1893.2) / 3.0),
+                              ("tf32x3", B.SPLIT_TF32X3, None)):
+        eng = B.T4Engine(pkg.load(), o, v, precision=prec, stream=stream.cuda_stream)
+        eng.set(W, t4c)
+        eng.pp_ladder()
+        eng.postprocess()
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        eng.pp_ladder()
+        e1.record(stream)
+        eng.postprocess()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        lad, post = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        tf = flop / (lad / 1e3) / 1e12
+        gbs = 2 * n4 * v ** 4 * 4 / (post / 1e3) / 1e9
+        out[label] = {"ladder_ms": lad, "ladder_tflops": tf, "post_ms": post, "post_gbs": gbs,
+                      "post_frac_of_copy": gbs / pk.get("hbm_gbs", 6787.2)}
+        if peak:
+            out[label]["roofline"] = {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                                      "frac": tf / peak, "peak_source": "measured bf16 burst / 3"}
+        eng.close()
+    return out
+
+
 def batch_summary(pkg, args):
     """The batched uneven-instance workload (64 RCCSDT problems, o in [3, 8], v in
     [20, 60]) iterated to |R| <= 1e-8 in one CUDA graph launch per batch iteration:
@@ -365,14 +437,13 @@ def batch_summary(pkg, args):
                        "converged": int((r["status"] == 0).sum()),
                        "iterations": [int(r["iterations"].min()), float(np.median(r["iterations"])),
                                       int(r["iterations"].max())]}
+        runs[label]["batch_gemm"] = {
+            "on": bool(s.get("batch_gemm", 0)), "problems": int(s.get("batch_gemm_problems", 0)),
+            "tiles_all_active": int(s.get("batch_gemm_tiles", 0)), "tile_width": int(s.get("batch_gemm_bn", 0)),
+            "ms_all_active": s.get("batch_gemm_tuned_ms"), "fixed_shape_ms_all_active": s.get("batch_gemm_fixed_ms"),
+            "note": "one persistent grouped-GEMM launch per batch iteration over every instance's residual "
+                    "products; shape tuned on the batch's table" if label == "autotuned" else "fixed shape"}
         if label == "autotuned":
-            infos = r["infos"]
-            runs[label]["grouped_gemm"] = {
-                "tuned_ms_sum": sum(i["tuned_us"] for i in infos) / 1e3,
-                "fixed_ms_sum": sum(i["fixed_us"] for i in infos) / 1e3,
-                "bn128": sum(1 for i in infos if i["bn"] == 128),
-                "plan_order": sum(1 for i in infos if i["order"] == 1),
-                "half_grid": sum(1 for i in infos if i["grid"] > 0)}
             energies = r["energies"]
     out["split"] = runs
     out["split_final_phase"] = ("3xTF32 from |R| <= sqrt(tol), FP64 from tol^0.75 (or a 3xTF32 stall), "
@@ -500,13 +571,15 @@ def run_ours(args, rank, world):
         else:
             peak, bound, src = mm["tf32_tflops"] / 3.0, "tensor", \
                 "measured TF32 matmul (cuBLAS, this run) / 3"
-        # DRAM bytes per pp-ladder launch from an ncu capture of the same launch shape;
-        # none until the current kernel has been captured
-        traffic = None
+        # DRAM bytes per pp-ladder launch: the mean over the six sum / difference GEMMs of
+        # the three views of the first 65-block range (the launch shape of this workload)
+        # captured at o=7, v=160 (dram__bytes_read.sum + dram__bytes_write.sum, one pass)
+        traffic = 9.85e9 if (args.workload == "o16v160w" and prec == 1) else None
         roof = {"kernel": "pp-ladder GEMM (k_gemm_f64)" if prec == 0 else "pp-ladder GEMM (k_gemm_tc)",
                 "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of "
-                "the sum and difference GEMMs of one pp-ladder unit (65 stored blocks)" if traffic else None, "peak_source": src,
+                "traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                "mean of the six full-shape pp-ladder GEMMs (65-block units, three views) captured at o=7 v=160; "
+                "algorithmic 3.33e9 B per launch" if traffic else None, "peak_source": src,
                 "launches": int(gemm_n), "avg_launch_ms": gemm_ms / gemm_n}
 
     step_ms = {k: float(x) / args.steps for k, x in zip(
@@ -529,6 +602,11 @@ def run_ours(args, rank, world):
     if rank == 0 and world == 1 and not args.no_batch:
         batch = batch_summary(pkg, args)
 
+    extra_q = extra_t4 = None
+    if rank == 0 and world == 1 and not args.no_next:
+        extra_q = q_summary(pkg, stream, mm)
+        extra_t4 = t4_summary(pkg, stream, pk)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, sample = oracle_sample(inst, seconds_budget=args.ref_seconds)
@@ -543,7 +621,7 @@ def run_ours(args, rank, world):
                 "tflops": 2.0 * fma * world / (ms_total / 1e3 / args.steps) / 1e12,
                 "energy_last": energies[-1], "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                 "cpu_baseline": cpu, "clocks": clk.summary(), "fp64_vs_split": compare, "fp64_here": fp64_here,
-                "batch64": batch, "matmul_peaks": mm,
+                "batch64": batch, "matmul_peaks": mm, "q_correction": extra_q, "t4_ladder": extra_t4,
                 "diis": "T1, T2 and T3" if diis_t3 else "T1 and T2 (T3 history would exceed 64 GB)",
                 "step_ms": step_ms}
         print(json.dumps(line), flush=True)
@@ -565,6 +643,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 vs split comparison at o8v80w")
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instance workload")
+    ap.add_argument("--no-next", action="store_true", help="skip the (Q) and compact-T4 measurements")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

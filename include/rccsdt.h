@@ -233,8 +233,12 @@ void rccsdt_destroy(rccsdt_ctx* ctx);
  * o[i], v[i], naux[i]; all share *opt) and iterates them together: one CUDA
  * graph launch per iteration runs every unconverged instance's iteration
  * concurrently, each as the body of a conditional node chosen on the device from
- * a per-instance code the host writes before the launch.  The graph is built on
- * the first rccsdt_batch_solve (capture of each instance's launch sequence) and
+ * a per-instance code the host writes before the launch.  In the split precisions
+ * the residuals' tensor-core products of every instance on the grouped path run
+ * as ONE persistent grouped-GEMM launch inside that graph (the instances' bodies
+ * are captured in two parts around it; its launch shape is tuned on the batch's
+ * own problem table when options.autotune is set).  The graph is built on the
+ * first rccsdt_batch_solve (capture of each instance's launch sequence) and
  * replayed afterwards.
  * --------------------------------------------------------------------------- */
 typedef struct rccsdt_batch rccsdt_batch;
@@ -263,7 +267,11 @@ int rccsdt_batch_solve(rccsdt_batch* b, double* e_corr, int* iterations, double*
  * over those launches (CUDA events around each launch), [2] algorithmic flop of
  * the evaluations run, [3] kernels executed, [4] nodes of the top-level graph,
  * [5] host ms to build the graph (captures included), [6] host ms to instantiate
- * and upload it, [7] device ms of the first launch.  Returns entries written. */
+ * and upload it, [7] device ms of the first launch, [8] 1 when the residuals'
+ * grouped GEMMs of all instances run as one batch-wide persistent launch (split
+ * precisions), [9] its problems, [10] its tiles with every instance active, [11] its
+ * tile width, [12] its tuned and [13] its fixed-shape time in ms (all instances
+ * active).  Returns entries written (at most 14). */
 int rccsdt_batch_stats(const rccsdt_batch* b, double* out, int cap);
 /* Device ms of each launch of the last rccsdt_batch_solve; returns the count. */
 int rccsdt_batch_launch_times(const rccsdt_batch* b, double* ms, int cap);

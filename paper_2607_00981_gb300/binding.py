@@ -305,10 +305,11 @@ class Batch:
         return e, it, nrm, st
 
     def stats(self):
-        out = np.zeros(8)
-        k = self.lib.rccsdt_batch_stats(self.h, out.ctypes.data, 8)
+        out = np.zeros(14)
+        k = self.lib.rccsdt_batch_stats(self.h, out.ctypes.data, 14)
         keys = ["launches", "device_ms", "flop", "kernels", "graph_nodes", "build_ms", "instantiate_ms",
-                "first_launch_ms"]
+                "first_launch_ms", "batch_gemm", "batch_gemm_problems", "batch_gemm_tiles", "batch_gemm_bn",
+                "batch_gemm_tuned_ms", "batch_gemm_fixed_ms"]
         return dict(zip(keys[:k], out[:k].tolist()))
 
     def launch_times(self, cap: int = 100000):

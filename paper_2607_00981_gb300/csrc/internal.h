@@ -2,6 +2,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
+#include "kernels.h"
+
 struct rccsdt_ctx;
 
 namespace rcc {
@@ -35,6 +39,20 @@ int ctx_ready(rccsdt_ctx* c);
 // on one eager evaluation) when the context asks for it; 0 otherwise.
 int ctx_prepare(rccsdt_ctx* c);
 int ctx_dims(const rccsdt_ctx* c, int* o, int* v);
+
+// Batch-wide grouped GEMM.  A body `code` whose evaluation takes the grouped path
+// (ctx_body_grouped) is queued in two parts around its grouped GEMM: part 0 up to
+// the operand gathers, part 1 from the reduction of the GEMM results into R3 to the
+// post-processed norms; other bodies run whole in part 0.
+int ctx_body_grouped(const rccsdt_ctx* c, int code);
+int ctx_enqueue_part(rccsdt_ctx* c, int code, int part);
+// The context's grouped GEMM problems (plan order) with tile width bn.
+int ctx_grouped_problems(rccsdt_ctx* c, int bn, std::vector<GProblem>* out);
+// Panel kind of the grouped path (-1 when the context has none).
+int ctx_grouped_kind(const rccsdt_ctx* c);
+void ctx_set_batch_gemm(rccsdt_ctx* c, int on);
+// The context's own grouped GEMM launch (the host simulation of a batch).
+int ctx_run_grouped_gemm(rccsdt_ctx* c);
 
 // What the (Q) correction reads from a context: the bare factors L[naux][n][n], the
 // Fock diagonal e[n], t2[o][o][v][v] (FP64) and compact T3 (FP32 in split contexts).

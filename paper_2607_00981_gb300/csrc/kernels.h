@@ -124,6 +124,11 @@ int launch_gemm_f64e(const void* Aplanes, const int* ea, const void* Bplanes, co
                      int* status_flag, long long watchdog, cudaStream_t s);
 int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total_tiles, int grid, int bn,
                            int* status_flag, long long watchdog, cudaStream_t s);
+// The same with the tile count and every problem's tile0 read from device memory
+// when the kernel starts (written by an earlier kernel: problems of instances that
+// do not run this time get no tiles); max_tiles bounds the grid.
+int launch_gemm_tc_grouped_dev(int kind, const GProblem* probs, int nprob, int max_tiles, const int* total_dev,
+                               int grid, int bn, int* status_flag, long long watchdog, cudaStream_t s);
 // Operand panels read from compact T3 through label cubes (cube_pack.cu).
 struct CubeTerm {
   i64 base;    // element offset of the stored block

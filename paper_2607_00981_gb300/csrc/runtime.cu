@@ -209,6 +209,7 @@ struct rccsdt_ctx {
   int have_ham = 0, have_amp = 0, have_int = 0, have_res = 0;
   int timing = 0;
   int concurrent = 0;  // other contexts share the GPU (batch): GEMMs keep their natural grids
+  int batch_gemm = 0;  // a batch runs this context's grouped GEMM in its own batch-wide launch
   double step_ms[16] = {0};
   // event pool for non-blocking interval timing: tag < 16 = step slots, 16 = GEMM engine
   std::vector<cudaEvent_t> ev;
@@ -2041,9 +2042,8 @@ int autotune_grouped(rccsdt_ctx* c) {
 #endif
 }
 
-// The residual's tensor-core contractions through the grouped path (R3 is
-// overwritten by the reduction, so it needs no zeroing).
-int run_grouped(rccsdt_ctx* c) {
+// Operand gathers of the grouped residual.
+int run_grouped_gathers(rccsdt_ctx* c) {
   auto& G = c->gr;
   for (int t = 0; t < 2; ++t)
     if (G.npack[t])
@@ -2054,6 +2054,11 @@ int run_grouped(rccsdt_ctx* c) {
       rcc::launch_cube_pack(m, G.kind, (const rcc::CubePiece*)G.cubes[m]->p, G.ncube[m],
                             (const rcc::CubeDst*)G.cube_dst->p, rcc::CubeDst{nullptr, nullptr, 0}, c->B("t3")->f(),
                             c->v, c->stream);
+  return 0;
+}
+
+int run_grouped_gemm(rccsdt_ctx* c) {
+  auto& G = c->gr;
   if (c->opt.autotune && !G.tuned) {
     const int st = autotune_grouped(c);
     if (st) return st;
@@ -2064,12 +2069,25 @@ int run_grouped(rccsdt_ctx* c) {
                                   c->opt.watchdog_cycles, c->stream))
     return fail(c, RCCSDT_ERR_ARG, "grouped GEMM configuration unsupported");
   timer_end(c, tidx);
+  return 0;
+}
+
+void run_grouped_reduce(rccsdt_ctx* c) {
+  auto& G = c->gr;
   const float* X = (const float*)G.raw->p;
   if (c->opt.precision != RCCSDT_FP64)
     rcc::launch_r3_gather<float>(X, (const i64*)G.target->p, G.ntarget, (const int*)G.cstart->p,
                                  (const i64*)G.xoff->p, (const int*)G.csel->p, (const float*)G.calpha->p, c->v, 0,
                                  c->B("r3")->f(), c->stream);
-  return 0;
+}
+
+// The residual's tensor-core contractions through the grouped path (R3 is
+// overwritten by the reduction, so it needs no zeroing).
+int run_grouped(rccsdt_ctx* c) {
+  int st = run_grouped_gathers(c);
+  if (!st) st = run_grouped_gemm(c);
+  if (!st) run_grouped_reduce(c);
+  return st;
 }
 
 }  // namespace
@@ -2158,9 +2176,15 @@ int do_intermediates(rccsdt_ctx* c) {
   return check(c, "do_intermediates");
 }
 
-int do_residual(rccsdt_ctx* c) {
+// Residuals R1, R2, R3.  part -1: all of it.  For a batch that runs the grouped
+// GEMMs of all its instances in one launch, part 0 stops after the grouped operand
+// gathers and part 1 starts with the reduction of the GEMM results into R3 (a
+// context off the grouped path does everything in part 0).
+int do_residual(rccsdt_ctx* c, int part = -1) {
   int st = 0;
   const bool grouped = c->gr.on && c->precision == c->opt.precision;
+  if (part == 1 && !grouped) return 0;
+  if (part != 1) {
   {
     StepTimer tm(c, 5);
     run_combines(c, c->c_r12_base);
@@ -2172,7 +2196,9 @@ int do_residual(rccsdt_ctx* c) {
   if (grouped) {
     // pp-ladder, ring, hh-ladder and the T2 term with W^{ab}_{dj}: one grouped pass
     StepTimer tm(c, 1);
-    if ((st = run_grouped(c))) return st;
+    if ((st = run_grouped_gathers(c))) return st;
+    if (part == 0) return check(c, "do_residual");
+    if ((st = run_grouped_gemm(c))) return st;
   } else {
     {
       StepTimer tm(c, 1);
@@ -2187,6 +2213,11 @@ int do_residual(rccsdt_ctx* c) {
       StepTimer tm(c, 3);
       if ((st = run_plans(c, c->p_hh))) return st;
     }
+  }
+  }
+  if (grouped) {
+    StepTimer tm(c, 1);
+    run_grouped_reduce(c);
   }
   {
     StepTimer tm(c, 4);
@@ -2907,6 +2938,46 @@ int ctx_enqueue(rccsdt_ctx* c, int update_first, int precision) {
   return do_postprocess(c, nullptr);
 }
 
+int ctx_body_grouped(const rccsdt_ctx* c, int code) {
+  return c->gr.on && body_precision(c->opt, code) == c->opt.precision ? 1 : 0;
+}
+
+int ctx_enqueue_part(rccsdt_ctx* c, int code, int part) {
+  if (code < 0 || code >= kBodies) return fail(c, RCCSDT_ERR_ARG, "internal: unknown body");
+  const int precision = body_precision(c->opt, code);
+  const bool split = ctx_body_grouped(c, code) != 0;
+  c->precision = precision;
+  int st = 0;
+  if (part == 0) {
+    if (rcc::body_updates(code) && (st = do_update(c))) return st;
+    if ((st = do_energy(c, nullptr))) return st;
+    if ((st = do_intermediates(c))) return st;
+    if ((st = do_residual(c, split ? 0 : -1))) return st;
+    if (!split && (st = do_postprocess(c, nullptr))) return st;
+  } else if (split) {
+    if ((st = do_residual(c, 1))) return st;
+    if ((st = do_postprocess(c, nullptr))) return st;
+  }
+  c->precision = c->opt.precision;
+  return check(c, "ctx_enqueue_part");
+}
+
+int ctx_grouped_problems(rccsdt_ctx* c, int bn, std::vector<GProblem>* out) {
+  auto& G = c->gr;
+  out->clear();
+  for (const auto& x : G.src) {
+    GProblem P;
+    if (make_gproblem(&P, G.kind, x.ahi, x.alo, x.bhi, x.blo, x.M, x.N, x.Kpad, x.out, bn))
+      return fail(c, RCCSDT_ERR_CUDA, "grouped residual: tensor map encoding failed");
+    P.colmajor = x.colmajor;
+    out->push_back(P);
+  }
+  return 0;
+}
+int ctx_grouped_kind(const rccsdt_ctx* c) { return c->gr.on ? c->gr.kind : -1; }
+void ctx_set_batch_gemm(rccsdt_ctx* c, int on) { c->batch_gemm = on; }
+int ctx_run_grouped_gemm(rccsdt_ctx* c) { return run_grouped_gemm(c); }
+
 // Queues one body of the solver (solve_sm.h) without host synchronisation.
 int ctx_enqueue_code(rccsdt_ctx* c, int code) {
   if (code < 0 || code >= kBodies) return fail(c, RCCSDT_ERR_ARG, "internal: unknown body");
@@ -2940,7 +3011,8 @@ void ctx_begin_capture(rccsdt_ctx* c) {
 }
 int ctx_ready(rccsdt_ctx* c) { return need(c, true, false, false); }
 int ctx_prepare(rccsdt_ctx* c) {
-  if (!c->opt.autotune || !c->gr.on || c->gr.tuned) return 0;
+  // (a batch that runs the grouped GEMMs itself tunes its own launch)
+  if (!c->opt.autotune || !c->gr.on || c->gr.tuned || c->batch_gemm) return 0;
   // one evaluation in the main precision runs the autotuner on real panels
   const int st = ctx_enqueue(c, 0, c->opt.precision);
   c->precision = c->opt.precision;

@@ -105,6 +105,11 @@ def test_batch_split_precision(kind, prec):
         assert it[q] == it1 and abs(e[q] - e1) < 1e-9, (q, it[q], it1, e[q], e1)
         E0 = oc.solve_compact(inst.L, inst.fock_diag, inst.o, tol=1e-10, max_iter=300)[0]
         assert abs(e[q] - E0) < 1e-6
+    # the grouped GEMMs of all instances ran as one batch-wide launch per iteration
+    stats = b.stats()
+    assert stats["batch_gemm"] == 1
+    if kind == "gpu":
+        assert stats["batch_gemm_problems"] > 0 and stats["batch_gemm_tiles"] > 0
     b.close()
 
 

@@ -339,7 +339,7 @@ def batch_solve(pkg, insts, prec, autotune, max_iter=100, tol=1e-8, host=False, 
             "h2d_bytes": h2d, "d2h_bytes": int(8 * 8 * len(insts)), "infos": infos}
 
 
-FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07  # SMs x FP32 lanes x 2 flop x max SM clock (GHz) / 1e3
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07 / 1e3  # SMs x FP32 lanes x 2 flop x max SM clock (GHz), in TFLOP/s
 
 
 def q_summary(pkg, stream, mm):

@@ -325,10 +325,7 @@ using PlainSched = PlainSchedT<false>;
 struct GroupSched {
   const GProblem* probs;
   int nprob, total;
-  // when set, the tile count (and the problems' tile0) were written on the device
-  // by an earlier kernel of the same stream or graph (a batch of instances)
-  const int* total_dev;
-  __device__ __forceinline__ int ntiles() const { return total_dev ? *(volatile const int*)total_dev : total; }
+  __device__ __forceinline__ int ntiles() const { return total; }
   __device__ __forceinline__ void tile(int t, Tile& x) const {
     int lo = 0, hi = nprob - 1;  // last problem with tile0 <= t
     while (lo < hi) {
@@ -370,6 +367,14 @@ struct GroupSched {
         if (j < ncols && n0 + j < N) dst[j] = __uint_as_float(r[j]);
     }
   }
+};
+
+// A group whose tile count (and the problems' tile0) an earlier kernel of the same
+// stream or graph wrote to device memory (a batch of instances, some of which sit
+// out an iteration).
+struct GroupSchedDev : GroupSched {
+  const int* total_dev;
+  __device__ __forceinline__ int ntiles() const { return *(volatile const int*)total_dev; }
 };
 
 template <int FMT, int BN, class S>
@@ -994,7 +999,6 @@ int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total
   sch.probs = probs;
   sch.nprob = nprob;
   sch.total = total_tiles;
-  sch.total_dev = nullptr;
   const int g = std::max(1, std::min(grid > 0 ? grid : num_sms(), total_tiles));
   const long long budget = watchdog > 0 ? watchdog : 4000000000LL;
   launch_any(kind, (bn == 128 || bn == 144) ? bn : 256, sch, g, status_flag, budget, s);
@@ -1004,7 +1008,7 @@ int launch_gemm_tc_grouped(int kind, const GProblem* probs, int nprob, int total
 int launch_gemm_tc_grouped_dev(int kind, const GProblem* probs, int nprob, int max_tiles, const int* total_dev,
                                int grid, int bn, int* status_flag, long long watchdog, cudaStream_t s) {
   if ((kind != PANEL_BF16X2 && kind != PANEL_TF32X2) || nprob <= 0 || max_tiles <= 0 || !total_dev) return 1;
-  GroupSched sch;
+  GroupSchedDev sch;
   sch.probs = probs;
   sch.nprob = nprob;
   sch.total = max_tiles;

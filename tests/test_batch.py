@@ -169,16 +169,19 @@ def test_batch_errors(kind):
 
 @pytest.mark.gpu
 def test_batch_autotuned_split_converges():
-    """The autotuner runs before the graph is captured; the tuned batch converges
-    to the oracle's energies within the split target."""
+    """The batch tunes the launch shape of its batch-wide grouped GEMM on its own
+    table before the graph is captured; the tuned batch converges to the oracle's
+    energies within the split target."""
     lib = gpu_lib()
     insts = _instances()[:3]
     b = _batch(lib, insts, tol=1e-8, max_iter=200, precision=B.SPLIT_BF16X3, autotune=1)
     e, it, nrm, st = b.solve()
     assert (st == B.OK).all(), st
-    for q, c in enumerate(b.instances):
-        info = c.engine_info()
-        assert info["tuned"] == 1 or info["grouped"] == 0
+    stats = b.stats()
+    assert stats["batch_gemm"] == 1 and stats["batch_gemm_tuned_ms"] > 0
+    assert stats["batch_gemm_tuned_ms"] <= stats["batch_gemm_fixed_ms"]
+    assert stats["batch_gemm_bn"] in (128, 256)
+    for q in range(len(insts)):
         E0 = oc.solve_compact(insts[q].L, insts[q].fock_diag, insts[q].o, tol=1e-10, max_iter=300)[0]
         assert abs(e[q] - E0) < 1e-6
     b.close()

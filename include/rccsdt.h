@@ -15,7 +15,7 @@
  *     pp-ladder runs as sum and difference products over the exchange symmetry
  *     W^{ab}_{de} = W^{ba}_{ed} (same result, about half its FMA);
  *   - post-processing: Sec. II.D (symmetrise, purify, orthogonalise);
- *   - update: Jacobi step t += r / eps of appendix A.1; DIIS of Sec. III.A.4;
+ *   - update: Jacobi step t += r / eps of appendix A.1; DIIS of Sec. III.A.5;
  *   - energy: the E_CC expression of appendix A.5 with bare integrals.
  *
  * Conventions (all arrays dense, row-major, float64 unless stated):
@@ -98,7 +98,7 @@ typedef struct {
   int diis_t3_nvir;          /* with diis_t3: the T3 part of the DIIS vectors keeps only the
                                 components t_ijk^abc with a, b, c < diis_t3_nvir (the lowest
                                 virtual orbitals in the given order; the subspace DIIS of
-                                Sec. III.A.4), the rest of T3 takes the plain Jacobi step;
+                                Sec. III.A.5), the rest of T3 takes the plain Jacobi step;
                                 <= 0 or >= v: all of T3 */
 } rccsdt_options;
 
@@ -344,6 +344,64 @@ int rccsdt_t4_postprocess(rccsdt_t4* t4, double* norm);
 int rccsdt_t4_get_r4(rccsdt_t4* t4, double* r4c);
 const char* rccsdt_t4_last_error(const rccsdt_t4* t4);
 void rccsdt_t4_destroy(rccsdt_t4* t4);
+
+/* ---------------------------------------------------------------------------
+ * IJK-partitioned multi-process planning (Sec. III.A.1-III.A.3).  Host-only: no
+ * call in this section touches a GPU, and none needs one.
+ *
+ * The stored blocks of compact T3/R3 (i <= j <= k, storage order of the context)
+ * are distributed over `nranks` processes as individual IJK triples (Sec. III.A.1:
+ * the finest of the three partitions the paper weighs, chosen for load balance);
+ * lower-order quantities stay replicated.  Ownership balances a per-block cost
+ * (longest-processing-time-first: blocks by decreasing cost, ties by storage order,
+ * each to the least-loaded rank, ties to the lowest rank).  The exchange of step
+ * (v) of Sec. III.A.2 (F_oo, W_oooo and the two W_ov rings on T3 blocks owned
+ * elsewhere) runs in batches (Sec. III.A.3): the batches partition the stored
+ * blocks, so each T3 element is sent once per cycle; a batch holds consecutive
+ * blocks in storage order, cut so that the batches carry equal shares of the step
+ * (v) work, and lists its blocks grouped by owner in rank order (the layout of an
+ * all-gather with per-rank counts).  The step (v) work of a gathered block u on rank
+ * r is the work of the contractions of r's blocks that read u: v^3 FMA per F_oo or
+ * W_oooo read, v^4 per ring read, over the reads of every term with unpacking of a
+ * block's residual (F_oo 3o, W_oooo 3o^2, rings 15o reads per block).
+ * --------------------------------------------------------------------------- */
+typedef struct rccsdt_ijk_plan rccsdt_ijk_plan;
+
+/* The default per-block cost: the FMA count of one stored block's residual terms,
+ * 3v^5 (W_vvvv, direct traversal) + 15 o v^4 (rings) + 9 v^4 (F_vv and the T2 terms
+ * with W_vvvo) + 3 o^2 v^3 (W_oooo) + 9 o v^3 (F_oo and the T2 terms with W_vooo),
+ * and 0 for the blocks i = j = k, whose residual purification sets to zero
+ * (Sec. II.D.2), so they need no contraction.  cost[n3] (host).
+ * Errors: RCCSDT_ERR_ARG (o, v < 1, o > 64, NULL cost). */
+int rccsdt_ijk_block_costs(int o, int v, double* cost);
+
+/* Plans the partition and the exchange batches.  batch_triples (>= 1) is the
+ * paper's N_IJK^batch, the mean number of blocks per batch (the batch count is
+ * ceil(n3 / batch_triples)); cost[n3] (host, >= 0 and finite) replaces the default
+ * model when not NULL.  A block of zero cost is owned like any other but reads
+ * nothing in step (v).  Limits: 1 <= o <= 64, 1 <= nranks <= 4096, batches x
+ * nranks <= 2^27.  Errors: RCCSDT_ERR_ARG (limits, NULL out, a negative or
+ * non-finite cost), RCCSDT_ERR_OOM. */
+int rccsdt_ijk_plan_create(int o, int v, int nranks, int batch_triples, const double* cost,
+                           rccsdt_ijk_plan** out);
+void rccsdt_ijk_plan_destroy(rccsdt_ijk_plan* plan);
+/* info[6] = {n3, nranks, number of batches, most blocks one rank owns, most
+ * blocks in one batch, most blocks one rank sends in one batch}. */
+int rccsdt_ijk_plan_info(const rccsdt_ijk_plan* plan, long long info[6]);
+/* owner[n3]: the rank that owns each stored block. */
+int rccsdt_ijk_plan_owners(const rccsdt_ijk_plan* plan, int* owner);
+/* The blocks `rank` owns, in storage order: *count is set; blocks (may be NULL to
+ * query the count) receives *count indices.  Errors: RCCSDT_ERR_ARG (rank out of
+ * range, NULL count). */
+int rccsdt_ijk_plan_local(const rccsdt_ijk_plan* plan, int rank, int* blocks, int* count);
+/* Batch b: counts[nranks] = the blocks each rank contributes; blocks (may be NULL)
+ * receives the batch's block indices grouped by owner in rank order, each group in
+ * storage order.  Errors: RCCSDT_ERR_ARG (b out of range, NULL counts). */
+int rccsdt_ijk_plan_batch(const rccsdt_ijk_plan* plan, int b, int* counts, int* blocks);
+/* rank_cost[nranks] (may be NULL): the summed cost of each rank's blocks;
+ * batch_work[nbatches][nranks] (may be NULL): the step (v) FMA each batch's
+ * gathered blocks cause on each rank. */
+int rccsdt_ijk_plan_work(const rccsdt_ijk_plan* plan, double* rank_cost, double* batch_work);
 
 /* Residual norms for callers that cannot allocate device memory.  The paper has
  * no counterpart: this entry point exists for callers such as a framework that

@@ -11,7 +11,7 @@ Modules
                working equations of the paper's appendix A.5 (T1-dressed
                integrals of A.4, spin summation of Eq. triples-spin-sum, the
                permutation operator of Eq. rcc-perm-op), the energy, the Jacobi
-               update of A.1 and the DIIS of Sec. III.A.4.
+               update of A.1 and the DIIS of Sec. III.A.5.
 ``compact``    The same residual on compact ``i <= j <= k`` storage, following
                Sec. II.C (direct traversal, unpacking, the representative
                contractions of the operation-count table) and the post-processing

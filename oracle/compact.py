@@ -312,7 +312,7 @@ def solve_compact(L, fock_diag, o, tol=1e-10, max_iter=200, diis_space=8, diis_s
     Each iteration: raw residuals, post-processing of R3, norm, energy, Jacobi
     step, DIIS over (t1, t2, sqrt(m) t3c).  With ``diis_t3_nvir = ns`` the T3 part of
     the DIIS vectors keeps only the components with all three virtual labels below
-    ns (the DIIS in a reduced virtual subspace of Sec. III.A.4); the other T3
+    ns (the DIIS in a reduced virtual subspace of Sec. III.A.5); the other T3
     components keep their Jacobi step.  Returns (E, t1, t2, t3c, iters, history).
     """
     e = np.asarray(fock_diag, dtype=np.float64)

@@ -2,7 +2,7 @@
 
 Written from the paper's appendix A (notation of A.2, Hamiltonian of A.3,
 T1-dressing of A.4, working equations of A.5 "RCCSD" and "RCCSDT") and the
-DIIS of Sec. III.A.4.  Array conventions (all row-major numpy):
+DIIS of Sec. III.A.5.  Array conventions (all row-major numpy):
 
 * orbitals are ordered occupied first, ``n = o + v``;
 * ``L[P, p, q]`` factorises the chemists' ERIs, ``(pq|rs) = sum_P L[P,p,q] L[P,r,s]``;
@@ -323,7 +323,7 @@ def postprocess_full(r3):
 
 
 class Diis:
-    """DIIS of Sec. III.A.4: B_mn = e_m . e_n, bordered solve, t = sum c_m t_m.
+    """DIIS of Sec. III.A.5: B_mn = e_m . e_n, bordered solve, t = sum c_m t_m.
 
     Vectors are flat float64 arrays.  Keeps the last ``space`` pairs.  The
     bordered system is solved by least squares (pseudo-inverse), which also

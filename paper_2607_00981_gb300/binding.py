@@ -77,6 +77,14 @@ _SIGS = {
     "rccsdt_t4_get_r4": (C.c_int, [_P, _P]),
     "rccsdt_t4_last_error": (C.c_char_p, [_P]),
     "rccsdt_t4_destroy": (None, [_P]),
+    "rccsdt_ijk_block_costs": (C.c_int, [C.c_int, C.c_int, _P]),
+    "rccsdt_ijk_plan_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _P, C.POINTER(_P)]),
+    "rccsdt_ijk_plan_destroy": (None, [_P]),
+    "rccsdt_ijk_plan_info": (C.c_int, [_P, _P]),
+    "rccsdt_ijk_plan_owners": (C.c_int, [_P, _P]),
+    "rccsdt_ijk_plan_local": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int)]),
+    "rccsdt_ijk_plan_batch": (C.c_int, [_P, C.c_int, _P, _P]),
+    "rccsdt_ijk_plan_work": (C.c_int, [_P, _P, _P]),
 }
 Q_FP64, Q_FP32 = 0, 1
 

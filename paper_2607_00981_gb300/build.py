@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", CSRC, "-I", os.path.join(ROOT, "include")]
 SOURCES = ["runtime.cu", "kernels.cu", "gemm_tc.cu", "noalloc.cu", "batch.cu", "cube_pack.cu", "pair_pack.cu",
-           "q_energy.cu", "t4.cu"]
+           "q_energy.cu", "t4.cu", "ijk_plan.cu"]
 
 
 def nvcc() -> str:

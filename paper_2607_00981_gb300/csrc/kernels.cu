@@ -7,7 +7,7 @@
 //  k_post        symmetrise / purify / orthogonalise compact R3 (Sec. II.D)
 //  k_update_*    Jacobi step t += r / eps (appendix A.1)
 //  k_wdot, k_sum deterministic weighted dot products (norms, DIIS B matrix)
-//  k_diis_*      DIIS bordered solve and extrapolation (Sec. III.A.4)
+//  k_diis_*      DIIS bordered solve and extrapolation (Sec. III.A.5)
 #include <algorithm>
 #include <type_traits>
 
@@ -887,7 +887,7 @@ template void launch_wdot<float>(const float*, const float*, i64, i64, const dou
                                  double, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// DIIS (Sec. III.A.4) with its bookkeeping on the device, so one iteration is a
+// DIIS (Sec. III.A.5) with its bookkeeping on the device, so one iteration is a
 // fixed sequence of launches (capturable in a CUDA graph).  State st[8]:
 //   st[0] updates done, st[1] history entries written, st[2] slot of the current
 //   update, st[3] entries in use after it, st[4] 1 if this update extrapolates.

@@ -140,7 +140,7 @@ def test_compact_converged_energy_equals_full():
 
 
 def test_subspace_diis_reaches_the_same_fixed_point():
-    """DIIS over a virtual subspace of T3 (Sec. III.A.4) changes the path, not the
+    """DIIS over a virtual subspace of T3 (Sec. III.A.5) changes the path, not the
     converged amplitudes: the energy equals the full-DIIS one; the whole space as the
     subspace is the full DIIS iteration for iteration."""
     inst = make_instance(3, 6, naux=20, seed=11, scale=0.2)

@@ -205,7 +205,7 @@ def test_pp_pair_tiles_edges_on_host(prec, f64_tc, o, v, naux):
 @pytest.mark.parametrize("prec", [B.FP64, B.SPLIT_TF32X3], ids=["fp64", "tf32x3"])
 def test_subspace_diis_trajectory_matches_oracle(kind, prec):
     """DIIS with T3 restricted to the 7 lowest of 12 virtual orbitals (the subspace
-    DIIS of Sec. III.A.4): energies and residual norms of six iterations of the o=3,
+    DIIS of Sec. III.A.5): energies and residual norms of six iterations of the o=3,
     v=12 workload equal the oracle's iteration by iteration (FP32 T3 storage and
     3xTF32 products: 1e-5 relative)."""
     inst = workload("o3v12")

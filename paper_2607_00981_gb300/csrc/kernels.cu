@@ -519,12 +519,15 @@ void launch_combine(const CombineArgs& c0, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // R3 post-processing: rp[blk] = post(r[blk]) (symmetrise, purify, orthogonalise).
 // Every element needs its six virtual permutations, which lie in the six cubes
-// of one orbit of 16^3 tiles {(TA,TB,TC) permuted}.  One CTA takes one orbit of
-// one block: it loads the orbit's distinct cubes (1, 3 or 6) into shared memory
-// along the unit-stride axis, then writes every element of those cubes once --
-// one HBM read and one write per element.
+// of one orbit of 8^3 tiles {(TA,TB,TC) permuted}.  One CTA takes one orbit of
+// one block at a time: it loads the orbit's distinct cubes (1, 3 or 6) into shared
+// memory along the unit-stride axis (each thread two rows of every cube, all loads
+// issued before the first store), then writes every element of those cubes once --
+// one HBM read and one write per element.  Small cubes keep eight CTAs on an SM, so
+// one CTA's loads overlap another's stores.  The squared norm of each block is
+// summed in the storage type per thread and in FP64 across blocks and threads.
 // ---------------------------------------------------------------------------
-constexpr int kPostTL = 16;
+constexpr int kPostTL = 8;
 
 __device__ __forceinline__ double block_sum(double x);
 __global__ void k_sum(const double* __restrict__ partial, int np, double* __restrict__ out, double scale,
@@ -535,7 +538,7 @@ __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __rest
                                               const int4* __restrict__ blocks, int v, i64 n3,
                                               const double* __restrict__ wblk, double* __restrict__ partial) {
   constexpr int TL = kPostTL;
-  // [16][17][17]: odd strides on both outer axes keep the permuted reads below 2-way bank conflicts
+  // [8][9][9]: odd strides on both outer axes keep the permuted reads within 2-way bank conflicts
   typedef T Cube[TL][TL + 1][TL + 1];
   extern __shared__ __align__(16) unsigned char post_smem[];
   Cube* cube = reinterpret_cast<Cube*>(post_smem);
@@ -577,35 +580,43 @@ __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __rest
   }
   __syncthreads();
   const int n = ncube;
-  const int tz = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  // thread (xg, ty, tz): rows x = xg and xg + 4 of every cube, local (ty, tz) along them
+  const int tz = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, xg = threadIdx.x >> 6;
   double nrm = 0.0;  // sum over this CTA's outputs of m(blk) val^2 (the |R3|^2 share)
   for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
     const double wb = wblk[b];
-    double bs = 0.0;
     const int4 ijk = blocks[b];
     const T* rb = r + b * V3;
-    __syncthreads();  // the previous block's cubes are consumed
-    for (int k = 0; k < n; ++k) {
-      const int x0 = tcoord[k][0] * TL, gy = tcoord[k][1] * TL + ty, gz = tcoord[k][2] * TL + tz;
-      const bool in = gy < v && gz < v;
+    T ld[6][2];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int kk = k < n ? k : 0;
+      const int x0 = tcoord[kk][0] * TL + xg, gy = tcoord[kk][1] * TL + ty, gz = tcoord[kk][2] * TL + tz;
+      const bool in = k < n && gy < v && gz < v;
       const T* src = rb + (i64)gy * v + gz;
-      T ld[TL];
 #pragma unroll
-      for (int x = 0; x < TL; ++x) ld[x] = (in && x0 + x < v) ? src[(i64)(x0 + x) * V2] : (T)0;
-#pragma unroll
-      for (int x = 0; x < TL; ++x) cube[k][x][ty][tz] = ld[x];
+      for (int h = 0; h < 2; ++h) ld[k][h] = (in && x0 + 4 * h < v) ? src[(i64)(x0 + 4 * h) * V2] : (T)0;
     }
+    __syncthreads();  // the previous block's cubes are consumed
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (k < n) {
+        cube[k][xg][ty][tz] = ld[k][0];
+        cube[k][xg + 4][ty][tz] = ld[k][1];
+      }
     __syncthreads();
     T* out = rp + b * V3;
     const bool all_eq = ijk.x == ijk.y && ijk.y == ijk.z;
+    T bs = (T)0;
     for (int k = 0; k < n; ++k) {
-      const int x0 = tcoord[k][0] * TL, gy = tcoord[k][1] * TL + ty, gz = tcoord[k][2] * TL + tz;
+      const int gy = tcoord[k][1] * TL + ty, gz = tcoord[k][2] * TL + tz;
       if (gy >= v || gz >= v) continue;
       const int s1 = slot[k][1], s2 = slot[k][2], s3 = slot[k][3], s4 = slot[k][4], s5 = slot[k][5];
       T* dst = out + (i64)gy * v + gz;
-#pragma unroll 4
-      for (int x = 0; x < TL; ++x) {
-        if (x0 + x >= v) break;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int x = xg + 4 * h, gx = tcoord[k][0] * TL + x;
+        if (gx >= v) break;
         // element (a,b,c) = local (x, ty, tz); the label permutation (p0,p1,p2) is
         // local (l[p0], l[p1], l[p2]) of the cube holding that tile permutation
         const T rabc = cube[k][x][ty][tz];
@@ -624,21 +635,26 @@ __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __rest
           else sym = rabc;
           val = sym - (rabc + racb + rbac + rbca + rcab + rcba) * (T)(1.0 / 6.0);
         }
-        dst[(i64)(x0 + x) * V2] = val;
-        bs += (double)val * (double)val;
+        dst[(i64)gx * V2] = val;
+        bs += val * val;
       }
     }
-    nrm += wb * bs;
+    nrm += wb * (double)bs;
   }
   nrm = block_sum(nrm);
   if (threadIdx.x == 0) partial[(i64)blockIdx.y * gridDim.x + blockIdx.x] = nrm;
 }
 
+// about 8 resident waves of CTAs (eight per SM); each keeps its orbit tables across
+// the blocks it visits
+static i64 post_grid_y(int norb, i64 n3) {
+  return std::max<i64>(1, std::min<i64>(n3, (152 * 8 * 8 + norb - 1) / norb));
+}
+
 int post_partials(int v, i64 n3) {
   const int nt = (v + kPostTL - 1) / kPostTL;
   const int norb = nt * (nt + 1) * (nt + 2) / 6;
-  const i64 gy = std::max<i64>(1, std::min<i64>(n3, (2048 + norb - 1) / norb));
-  return (int)(norb * gy);
+  return (int)(norb * post_grid_y(norb, n3));
 }
 
 template <typename T>
@@ -647,8 +663,7 @@ void launch_post(const T* r, T* rp, const int4* blocks, int v, i64 n3, const dou
   if (n3 <= 0) return;
   const int nt = (v + kPostTL - 1) / kPostTL;
   const int norb = nt * (nt + 1) * (nt + 2) / 6;
-  // about 2048 CTAs; each keeps its orbit tables across the blocks it visits
-  const i64 gy = std::max<i64>(1, std::min<i64>(n3, (2048 + norb - 1) / norb));
+  const i64 gy = post_grid_y(norb, n3);
   const size_t smem = 6 * sizeof(T) * kPostTL * (kPostTL + 1) * (kPostTL + 1);
   static bool attr = false;
   if (!attr) {
@@ -712,12 +727,33 @@ __global__ void __launch_bounds__(256) k_update_t3(T* __restrict__ t3, const T* 
       cl[q] = (float)(ec - (double)ch[q]);
     }
     __syncthreads();
-    for (int bb = threadIdx.y; bb < v; bb += 8) {
-      const float eh = rh[bb], el = rl[bb];
-      for (int c = threadIdx.x; c < v; c += 32) {
-        const int idx = bb * v + c;
-        const float d = (eh - ch[c]) + (el - cl[c]);
-        tb[idx] = tb[idx] + rb[idx] / d;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    if ((v & 3) == 0) {
+      // rows of v floats start on 16-byte boundaries: four elements per access,
+      // four accesses per thread in flight
+      const int n4 = (int)(V2 >> 2);
+      float4* t4 = reinterpret_cast<float4*>(tb);
+      const float4* r4 = reinterpret_cast<const float4*>(rb);
+#pragma unroll 4
+      for (int q = tid; q < n4; q += 256) {
+        const int bb = (4 * q) / v, c = 4 * q - bb * v;
+        const float eh = rh[bb], el = rl[bb];
+        const float4 tv = t4[q], rv = r4[q];
+        float4 out;
+        out.x = tv.x + rv.x / ((eh - ch[c]) + (el - cl[c]));
+        out.y = tv.y + rv.y / ((eh - ch[c + 1]) + (el - cl[c + 1]));
+        out.z = tv.z + rv.z / ((eh - ch[c + 2]) + (el - cl[c + 2]));
+        out.w = tv.w + rv.w / ((eh - ch[c + 3]) + (el - cl[c + 3]));
+        t4[q] = out;
+      }
+    } else {
+      for (int bb = threadIdx.y; bb < v; bb += 8) {
+        const float eh = rh[bb], el = rl[bb];
+        for (int c = threadIdx.x; c < v; c += 32) {
+          const int idx = bb * v + c;
+          const float d = (eh - ch[c]) + (el - cl[c]);
+          tb[idx] = tb[idx] + rb[idx] / d;
+        }
       }
     }
   } else {
@@ -1567,146 +1603,205 @@ template void launch_scatter_rows3<double>(const float*, int, int, const i64*, c
 // T2-driven term of Eq. resi-rccsdt with K = o, output-stationary:
 //   r_{ijk}^{abc} += sum over the six column permutations of
 //                    -sum_l W^{a1 l}_{i1 i2} t_{l i3}^{a2 a3}
-// One CTA owns a 16^3 tile of one stored block and accumulates all six terms in
-// registers; per term the W slice [l][a1] and the t2 slice of the tile are staged in
-// shared memory (l in chunks of 16), the t2 slice as [l][a2][a3], or as [l][a3][a2]
-// when a2 lies on the tile's first axis, so that the 16 values a thread needs along
-// that axis are one contiguous, 16-byte aligned run (vector loads: about one shared
-// load per three FMAs).  Each thread holds a fixed (b, c) and 16 values of a; the
-// block is written once, along c.
+// One CTA of 64 threads owns a 16^3 tile of one stored block and accumulates all six
+// terms in registers, each thread a 4 x 4 x 4 sub-cube (register blocking: per l one
+// 4-vector of W and a 4 x 4 patch of t2 from shared memory feed 64 FMAs).  Per term
+// and chunk of 16 values of l the W slice [l][a1] and the t2 slice [l][a2][a3] of the
+// tile are copied to shared memory with cp.async (zero-filled outside the block and
+// beyond o), two stages in flight.  The block is read and written once.
 // Wvooo[a][l][i][j] = W^{al}_{ij}; t2[l][k][b][c] = t_lk^bc (T precision copies).
 // ---------------------------------------------------------------------------
+constexpr int kT2oTL = 16, kT2oLC = 16, kT2oThreads = 64;
+
 template <typename T>
-__device__ __forceinline__ void load16(const T* p, T (&x)[16]) {  // p 16-byte aligned
-  if constexpr (sizeof(T) == 4) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float4 f = reinterpret_cast<const float4*>(p)[j];
-      x[4 * j] = f.x;
-      x[4 * j + 1] = f.y;
-      x[4 * j + 2] = f.z;
-      x[4 * j + 3] = f.w;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const double2 f = reinterpret_cast<const double2*>(p)[j];
-      x[2 * j] = f.x;
-      x[2 * j + 1] = f.y;
-    }
-  }
+struct T2oLayout {
+  static constexpr int EPC = 16 / (int)sizeof(T);      // elements per 16-byte chunk
+  static constexpr int PW = kT2oTL + EPC;              // padded row, 16-byte multiple
+  static constexpr int WS = kT2oLC * PW;               // W slice [l][a1]
+  static constexpr int TS = kT2oLC * kT2oTL * PW;      // t2 slice [l][a2][a3]
+  static constexpr int STAGE = WS + TS;
+};
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_t2_outer(T* __restrict__ r3, const T* __restrict__ Wvooo,
-                                                  const T* __restrict__ t2, const int4* __restrict__ blocks, int o,
-                                                  int v, i64 n3) {
-  constexpr int TL = 16, LC = 16, PW = TL + 16 / (int)sizeof(T);  // rows padded, 16-byte aligned
-  // two buffers: the slices of stage s + 1 are loaded while stage s is computed
-  // (dynamic shared memory: 43 KB for FP32, 78 KB for FP64)
+__device__ __forceinline__ void load4(const T* p, T (&x)[4]) {  // p 16-byte aligned
+  if constexpr (sizeof(T) == 4) {
+    const float4 f = *reinterpret_cast<const float4*>(p);
+    x[0] = f.x;
+    x[1] = f.y;
+    x[2] = f.z;
+    x[3] = f.w;
+  } else {
+    const double2 f0 = reinterpret_cast<const double2*>(p)[0], f1 = reinterpret_cast<const double2*>(p)[1];
+    x[0] = f0.x;
+    x[1] = f0.y;
+    x[2] = f1.x;
+    x[3] = f1.y;
+  }
+}
+
+// acc[a0][a1][a2] -= sum_l W[l][a_X1] t[l][a_X2][a_X3] over the thread's sub-cube
+template <int X1, int X2, int X3, typename T>
+__device__ __forceinline__ void t2o_step(T (&acc)[4][4][4], const T* __restrict__ Wb, const T* __restrict__ Tb,
+                                         int lc, const int (&u)[3]) {
+  using Lay = T2oLayout<T>;
+#pragma unroll 2
+  for (int l = 0; l < lc; ++l) {
+    T w[4], t[4][4];
+    load4(Wb + l * Lay::PW + 4 * u[X1], w);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) load4(Tb + (l * kT2oTL + 4 * u[X2] + i) * Lay::PW + 4 * u[X3], t[i]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c0 = X1 == 0 ? m : (X2 == 0 ? i : j);
+          const int c1 = X1 == 1 ? m : (X2 == 1 ? i : j);
+          const int c2 = X1 == 2 ? m : (X2 == 2 ? i : j);
+          acc[c0][c1][c2] -= w[m] * t[i][j];
+        }
+  }
+}
+
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(kT2oThreads) k_t2_outer(T* __restrict__ r3, const T* __restrict__ Wvooo,
+                                                          const T* __restrict__ t2, const int4* __restrict__ blocks,
+                                                          int o, int v, i64 n3) {
+  using Lay = T2oLayout<T>;
+  constexpr int TL = kT2oTL, LC = kT2oLC;
   extern __shared__ __align__(16) unsigned char t2o_smem[];
-  typedef T WsT[LC][PW];
-  typedef T TsT[LC][TL][PW];
-  WsT* Ws = reinterpret_cast<WsT*>(t2o_smem);                         // [2][l][a1]
-  TsT* Ts = reinterpret_cast<TsT*>(t2o_smem + 2 * sizeof(WsT));       // [2][l][a2][a3] or [2][l][a3][a2]
+  T* sm = reinterpret_cast<T*>(t2o_smem);  // [2][STAGE]: W slice then t2 slice
   const int nt = (v + TL - 1) / TL;
-  const i64 V3 = (i64)v * v * v;
-  const int tc = threadIdx.x % TL, tb = threadIdx.x / TL;
+  const i64 V2 = (i64)v * v, V3 = V2 * v;
+  const int tid = threadIdx.x;
+  const int u[3] = {tid >> 4, (tid >> 2) & 3, tid & 3};
   const int nch = (o + LC - 1) / LC, nstage = 6 * nch;  // stage = (ordering q, chunk of l)
-  auto coord = [&](int x) { return x == 1 ? tb : tc; };  // the thread's coordinate on axis 1 or 2
   for (i64 blk = blockIdx.y; blk < n3; blk += gridDim.y) {
     const int4 ijk = blocks[blk];
     auto occ = [&](int x) { return x == 0 ? ijk.x : (x == 1 ? ijk.y : ijk.z); };
     for (int tile = blockIdx.x; tile < nt * nt * nt; tile += gridDim.x) {
       const int lo0 = tile / (nt * nt) * TL, lo1 = (tile / nt) % nt * TL, lo2 = tile % nt * TL;
       auto lo = [&](int x) { return x == 0 ? lo0 : (x == 1 ? lo1 : lo2); };
-      // global loads of one stage into registers: W value of thread (a1, l) = (tb, tc),
-      // t2 values of thread (a2, a3) = (tb, tc) over the chunk's l
-      T ld[LC], wl;
-      auto load = [&](int st) {
+      auto issue = [&](int st) {
+        T* Wb = sm + (st & 1) * Lay::STAGE;
+        T* Tb = Wb + Lay::WS;
         const int q = st / nch, l0 = (st % nch) * LC, lc = min(LC, o - l0);
         const int x1 = perm3(q, 0), x2 = perm3(q, 1), x3 = perm3(q, 2);
         const int i1 = occ(x1), i2 = occ(x2), i3 = occ(x3);
-        const int ga = lo(x1) + tb;
-        wl = (tc < lc && ga < v) ? Wvooo[(((i64)ga * o + l0 + tc) * o + i1) * o + i2] : (T)0;
-        const int g2 = lo(x2) + tb, g3 = lo(x3) + tc;
-        const bool in = g2 < v && g3 < v;
-        const T* src = t2 + ((i64)(l0 * o + i3) * v + g2) * v + g3;
-        const i64 ls = (i64)o * v * v;  // stride of l
-#pragma unroll
-        for (int l = 0; l < LC; ++l) ld[l] = (in && l < lc) ? src[l * ls] : (T)0;
-      };
-      auto store = [&](int st) {
-        const int b = st & 1, q = st / nch;
-        const bool tr = perm3(q, 1) == 0;  // the t2 slice as [l][a3][a2]
-        Ws[b][tc][tb] = wl;
-        T* dst = tr ? &Ts[b][0][tc][tb] : &Ts[b][0][tb][tc];
-#pragma unroll
-        for (int l = 0; l < LC; ++l) dst[l * TL * PW] = ld[l];
-      };
-      T acc[TL];
-#pragma unroll
-      for (int a = 0; a < TL; ++a) acc[a] = (T)0;
-      __syncthreads();  // the previous tile's last stage is consumed
-      load(0);
-      store(0);
-      __syncthreads();
-#pragma unroll 1
-      for (int st = 0; st < nstage; ++st) {
-        if (st + 1 < nstage) load(st + 1);  // in flight during the FMAs below
-        const int b = st & 1, q = st / nch, lc = min(LC, o - (st % nch) * LC);
-        const int x1 = perm3(q, 0), x2 = perm3(q, 1), x3 = perm3(q, 2);
-        if (x1 == 0) {  // a = a1: W varies with a, the t2 value is fixed per l
-          const int u2 = coord(x2), u3 = coord(x3);
-          for (int l = 0; l < lc; ++l) {
-            const T tv = Ts[b][l][u2][u3];
-            T w[TL];
-            load16(&Ws[b][l][0], w);
-#pragma unroll
-            for (int a = 0; a < TL; ++a) acc[a] -= w[a] * tv;
+        for (int e = tid; e < LC * TL; e += kT2oThreads) {  // W[l][a1]
+          const int l = e / TL, a = e % TL, ga = lo(x1) + a;
+          const bool ok = l < lc && ga < v;
+          cp_async_elem(Wb + l * Lay::PW + a, ok ? Wvooo + (((i64)ga * o + l0 + l) * o + i1) * o + i2 : Wvooo, ok);
+        }
+        if constexpr (VEC) {  // t2 rows of 16 elements in 16-byte chunks (v a multiple of the chunk)
+          constexpr int CPR = TL / Lay::EPC;
+          for (int e = tid; e < LC * TL * CPR; e += kT2oThreads) {
+            const int row = e / CPR, part = e % CPR, l = row / TL, r2 = row % TL;
+            const int g2 = lo(x2) + r2, g3 = lo(x3) + part * Lay::EPC;
+            const bool ok = l < lc && g2 < v && g3 < v;
+            const T* src = ok ? t2 + ((i64)(l0 + l) * o + i3) * V2 + (i64)g2 * v + g3 : t2;
+            cp_async16(Tb + (l * TL + r2) * Lay::PW + part * Lay::EPC, src, ok);
           }
-        } else {  // a = a2 or a3: W fixed per l, t2 varies with a along a contiguous row
-          const int u1 = coord(x1);
-          const int row = x2 == 0 ? coord(x3) : coord(x2);
-          for (int l = 0; l < lc; ++l) {
-            const T wv = Ws[b][l][u1];
-            T t[TL];
-            load16(&Ts[b][l][row][0], t);
-#pragma unroll
-            for (int a = 0; a < TL; ++a) acc[a] -= wv * t[a];
+        } else {
+          for (int e = tid; e < LC * TL * TL; e += kT2oThreads) {
+            const int row = e / TL, c = e % TL, l = row / TL, r2 = row % TL;
+            const int g2 = lo(x2) + r2, g3 = lo(x3) + c;
+            const bool ok = l < lc && g2 < v && g3 < v;
+            cp_async_elem(Tb + (l * TL + r2) * Lay::PW + c, ok ? t2 + ((i64)(l0 + l) * o + i3) * V2 + (i64)g2 * v + g3 : t2,
+                          ok);
           }
         }
-        if (st + 1 < nstage) store(st + 1);  // the other buffer: its last reader was stage st - 1
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      };
+      T acc[4][4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+#pragma unroll
+          for (int z = 0; z < 4; ++z) acc[x][y][z] = (T)0;
+      __syncthreads();  // the previous tile's last stage is consumed
+      issue(0);
+#pragma unroll 1
+      for (int st = 0; st < nstage; ++st) {
+        if (st + 1 < nstage) {
+          issue(st + 1);  // its buffer's last reader was stage st - 1
+          asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+          asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        const T* Wb = sm + (st & 1) * Lay::STAGE;
+        const T* Tb = Wb + Lay::WS;
+        const int q = st / nch, lc = min(LC, o - (st % nch) * LC);
+        switch (perm3(q, 0) * 3 + perm3(q, 1)) {
+          case 1: t2o_step<0, 1, 2>(acc, Wb, Tb, lc, u); break;
+          case 2: t2o_step<0, 2, 1>(acc, Wb, Tb, lc, u); break;
+          case 3: t2o_step<1, 0, 2>(acc, Wb, Tb, lc, u); break;
+          case 5: t2o_step<1, 2, 0>(acc, Wb, Tb, lc, u); break;
+          case 6: t2o_step<2, 0, 1>(acc, Wb, Tb, lc, u); break;
+          default: t2o_step<2, 1, 0>(acc, Wb, Tb, lc, u); break;
+        }
         __syncthreads();
       }
-      const int gb = lo1 + tb, gc = lo2 + tc;
-      if (gb < v && gc < v) {
-        T* dst = r3 + blk * V3 + (i64)gb * v + gc;
-        T old[TL];
+      // read-modify-write of the sub-cube: rows of 4 along the unit-stride axis
 #pragma unroll
-        for (int a = 0; a < TL; ++a) old[a] = lo0 + a < v ? dst[(i64)(lo0 + a) * v * v] : (T)0;
+      for (int m0 = 0; m0 < 4; ++m0)
 #pragma unroll
-        for (int a = 0; a < TL; ++a)
-          if (lo0 + a < v) dst[(i64)(lo0 + a) * v * v] = old[a] + acc[a];
-      }
+        for (int m1 = 0; m1 < 4; ++m1) {
+          const int g0 = lo0 + 4 * u[0] + m0, g1 = lo1 + 4 * u[1] + m1, g2 = lo2 + 4 * u[2];
+          if (g0 >= v || g1 >= v || g2 >= v) continue;
+          T* dst = r3 + blk * V3 + (i64)g0 * V2 + (i64)g1 * v + g2;
+          if constexpr (VEC && sizeof(T) == 4) {
+            float4 x = *reinterpret_cast<float4*>(dst);
+            x.x += acc[m0][m1][0];
+            x.y += acc[m0][m1][1];
+            x.z += acc[m0][m1][2];
+            x.w += acc[m0][m1][3];
+            *reinterpret_cast<float4*>(dst) = x;
+          } else {
+#pragma unroll
+            for (int m2 = 0; m2 < 4; ++m2)
+              if (g2 + m2 < v) dst[m2] += acc[m0][m1][m2];
+          }
+        }
     }
   }
 }
 
 template <typename T>
 void launch_t2_outer(T* r3, const T* Wvooo, const T* t2, const int4* blocks, int o, int v, i64 n3, cudaStream_t s) {
-  const int nt = (v + 15) / 16;
+  const int nt = (v + kT2oTL - 1) / kT2oTL;
   const unsigned gx = (unsigned)std::min(nt * nt * nt, 65535);
   const unsigned gy = (unsigned)std::min<i64>(n3, 65535);
-  constexpr int PW = 16 + 16 / (int)sizeof(T);
-  const size_t smem = (size_t)2 * (16 * PW + 16 * 16 * PW) * sizeof(T);
+  const size_t smem = (size_t)2 * T2oLayout<T>::STAGE * sizeof(T);
+  const bool vec = v % T2oLayout<T>::EPC == 0;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_t2_outer<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_t2_outer<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_t2_outer<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   ++g_launch_count;
-  k_t2_outer<T><<<dim3(gx, gy), 256, smem, s>>>(r3, Wvooo, t2, blocks, o, v, n3);
+  if (vec)
+    k_t2_outer<T, true><<<dim3(gx, gy), kT2oThreads, smem, s>>>(r3, Wvooo, t2, blocks, o, v, n3);
+  else
+    k_t2_outer<T, false><<<dim3(gx, gy), kT2oThreads, smem, s>>>(r3, Wvooo, t2, blocks, o, v, n3);
 }
 template void launch_t2_outer<double>(double*, const double*, const double*, const int4*, int, int, i64, cudaStream_t);
 template void launch_t2_outer<float>(float*, const float*, const float*, const int4*, int, int, i64, cudaStream_t);

@@ -118,45 +118,95 @@ __device__ __forceinline__ double t4_block_sum(double x, double* ws) {
   return t;
 }
 
-// Post-processing pass; CTA (chunk, blk) handles 256 * 8 elements of one block and
-// writes its partial squared norm (times the block multiplicity) to partial[cta].
+// Post-processing pass, orbit-tiled: the labels are cut into tiles of 4 (the last
+// one ragged); CTA (x, blk) takes the tile quadruples A <= B <= C <= D numbered x,
+// x + gridDim.x, ... of stored block blk.  The 24 label permutations map the tiles
+// (A, B, C, D) permuted onto one another, so a quadruple's distinct permuted tiles
+// (its orbit, at most 24 tiles of 256 elements) hold every input its outputs read:
+// they are staged in shared memory once, and each output element of the orbit
+// is the 24-term sum over them.  Slot s holds the tile whose position x has tile
+// index Q[perm_s(x)]; the input of term p of an output in slot s lies in slot
+// (s o p) at the output's local coordinates permuted by p.  Shared strides
+// (69, 17, 4, 1) keep every permuted read of a warp within two-way bank conflicts.
+// Writes the block's partial squared norm (times the block multiplicity) to
+// partial[blk * gridDim.x + x].
+constexpr int kT4Tile = 4;
+constexpr int kT4S0 = 69, kT4S1 = 17, kT4S2 = 4;
+constexpr int kT4Slot = 3 * (kT4S0 + kT4S1 + kT4S2 + 1) + 1;  // 274 elements per staged tile
+__constant__ unsigned char c_t4comp[24][24];  // index of the permutation y -> s(p(y))
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_t4_post(const T* __restrict__ r, T* __restrict__ out,
-                                                 const int4* __restrict__ info, int v, int chunks,
-                                                 double* __restrict__ partial) {
+                                                 const int4* __restrict__ info, const int4* __restrict__ quads,
+                                                 int nq, int v, double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char t4_smem[];
+  T* tiles = reinterpret_cast<T*>(t4_smem);
+  __shared__ int canon[24];
   __shared__ double ws[8];
-  const i64 V4 = (i64)v * v * v * v;
-  const int chunk = blockIdx.x % chunks;
-  const i64 blk = blockIdx.x / chunks;
+  const i64 blk = blockIdx.y;
   const int4 q = info[blk];  // x: coefficient row (5 = purified block), y: multiplicity
+  const i64 V4 = (i64)v * v * v * v;
   const T* rb = r + blk * V4;
   T* ob = out + blk * V4;
-  const i64 per = (V4 + chunks - 1) / chunks;
-  const i64 e0 = chunk * per, e1 = min(V4, e0 + per);
+  const int l = threadIdx.x;
+  auto lx = [l](int x) { return (l >> (6 - 2 * x)) & 3; };  // local coordinate of label position x
+  const int own = lx(0) * kT4S0 + lx(1) * kT4S1 + lx(2) * kT4S2 + lx(3);
+  int paddr[24];
+#pragma unroll
+  for (int p = 0; p < 24; ++p)
+    paddr[p] = lx(c_t4perm[p][0]) * kT4S0 + lx(c_t4perm[p][1]) * kT4S1 + lx(c_t4perm[p][2]) * kT4S2 +
+               lx(c_t4perm[p][3]);
   double s = 0.0;
-  for (i64 x = e0 + threadIdx.x; x < e1; x += blockDim.x) {
-    double val = 0.0;
-    if (q.x < 5) {
-      int lab[4];
-      i64 t = x;
-      lab[3] = (int)(t % v); t /= v;
-      lab[2] = (int)(t % v); t /= v;
-      lab[1] = (int)(t % v);
-      lab[0] = (int)(t / v);
-      for (int p = 0; p < 24; ++p) {
-        const double d = c_t4coef[q.x][p];
-        if (d == 0.0) continue;
-        const i64 off = (((i64)lab[c_t4perm[p][0]] * v + lab[c_t4perm[p][1]]) * v + lab[c_t4perm[p][2]]) * v +
-                        lab[c_t4perm[p][3]];
-        val += d * (double)rb[off];
+  for (int qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+    const int4 Q4 = quads[qi];
+    // tile index of label position x (tile indices < 256 since v <= 200)
+    const unsigned Qp = (unsigned)Q4.x | ((unsigned)Q4.y << 8) | ((unsigned)Q4.z << 16) | ((unsigned)Q4.w << 24);
+    auto Qa = [Qp](int x) { return (int)((Qp >> (8 * x)) & 255u); };
+    if (l < 24) {  // first slot with the same tile as slot l
+      int c = l;
+      for (int u = 0; u < l; ++u) {
+        bool same = true;
+        for (int x = 0; x < 4; ++x) same &= Qa(c_t4perm[u][x]) == Qa(c_t4perm[l][x]);
+        if (same) {
+          c = u;
+          break;
+        }
+      }
+      canon[l] = c;
+    }
+    __syncthreads();
+    for (int sl = 0; sl < 24; ++sl) {
+      if (canon[sl] != sl) continue;
+      int g[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) g[x] = kT4Tile * Qa(c_t4perm[sl][x]) + lx(x);
+      const bool in = g[0] < v && g[1] < v && g[2] < v && g[3] < v;
+      const i64 off = (((i64)g[0] * v + g[1]) * v + g[2]) * v + g[3];
+      if (q.x < 5) tiles[sl * kT4Slot + own] = in ? rb[off] : (T)0;
+    }
+    __syncthreads();
+    for (int sl = 0; sl < 24; ++sl) {
+      if (canon[sl] != sl) continue;
+      int g[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) g[x] = kT4Tile * Qa(c_t4perm[sl][x]) + lx(x);
+      T acc = (T)0;
+      if (q.x < 5) {
+#pragma unroll
+        for (int p = 0; p < 24; ++p) {
+          const T d = (T)c_t4coef[q.x][p];
+          acc += d * tiles[canon[c_t4comp[sl][p]] * kT4Slot + paddr[p]];
+        }
+      }
+      if (g[0] < v && g[1] < v && g[2] < v && g[3] < v) {
+        ob[(((i64)g[0] * v + g[1]) * v + g[2]) * v + g[3]] = acc;
+        s += (double)acc * (double)acc;
       }
     }
-    const T o = (T)val;
-    ob[x] = o;
-    s += (double)o * (double)o;
+    __syncthreads();  // the next quadruple restages the tiles
   }
   const double bs = t4_block_sum<T>(s, ws);
-  if (threadIdx.x == 0) partial[blockIdx.x] = bs * (double)q.y;
+  if (threadIdx.x == 0) partial[blk * gridDim.x + blockIdx.x] = bs * (double)q.y;
 }
 
 __global__ void k_t4_reduce(const double* __restrict__ partial, i64 n, double* __restrict__ out) {
@@ -190,10 +240,11 @@ struct rccsdt_t4 {
   double* alpha = nullptr;
   int4* info = nullptr;
   double* partial = nullptr;
+  int4* quads = nullptr;    // tile quadruples A <= B <= C <= D of the post-processing pass
+  int nq = 0, qgrid = 1;
   double* scal = nullptr;   // [0] squared norm, [8..] watchdog flag (int)
   float* splitk = nullptr;
   i64 splitk_elems = 0;
-  int chunks = 1;
   bool have_w = false, have_t = false, have_r = false;
   std::string err;
   ~rccsdt_t4() {
@@ -252,10 +303,17 @@ void t4_tables_once() {
         for (int x = 0; x < 4; ++x) rho[x] = perms[i][h[x]];
         coef[g][index_of(rho)] += proj[i] / (double)groups[g].size();
       }
-  unsigned char hp[24][4];
+  unsigned char hp[24][4], comp[24][24];
   for (int i = 0; i < 24; ++i)
     for (int x = 0; x < 4; ++x) hp[i][x] = (unsigned char)perms[i][x];
+  for (int a = 0; a < 24; ++a)
+    for (int b = 0; b < 24; ++b) {
+      std::array<int, 4> ab;  // y -> a(b(y))
+      for (int y = 0; y < 4; ++y) ab[y] = perms[a][perms[b][y]];
+      comp[a][b] = (unsigned char)index_of(ab);
+    }
   cudaMemcpyToSymbol(c_t4perm, hp, sizeof(hp));
+  cudaMemcpyToSymbol(c_t4comp, comp, sizeof(comp));
   cudaMemcpyToSymbol(c_t4coef, coef, sizeof(coef));
   done = true;
 }
@@ -315,8 +373,11 @@ RCC_API int rccsdt_t4_create(int o, int v, int precision, void* stream, rccsdt_t
   c->rowsel = (int*)c->alloc(std::max<i64>(V2, c->unit * V2) * 4, &ok);
   c->alpha = (double*)c->alloc(std::max<i64>(V2, c->unit * V2) * 8, &ok);
   c->info = (int4*)c->alloc(c->n4 * sizeof(int4), &ok);
-  c->chunks = (int)std::max<i64>(1, std::min<i64>(64, c->V4 / 4096));
-  c->partial = (double*)c->alloc(c->n4 * c->chunks * 8, &ok);
+  const int ntile = (v + kT4Tile - 1) / kT4Tile;
+  c->nq = (int)((i64)ntile * (ntile + 1) * (ntile + 2) * (ntile + 3) / 24);
+  c->qgrid = std::max(1, std::min(c->nq, 64));
+  c->quads = (int4*)c->alloc((size_t)c->nq * sizeof(int4), &ok);
+  c->partial = (double*)c->alloc(c->n4 * c->qgrid * 8, &ok);
   c->scal = (double*)c->alloc(64 * 8, &ok);
   c->splitk_elems = (i64)8 << 20;
   c->splitk = (float*)c->alloc((size_t)c->splitk_elems * 8, &ok);
@@ -359,11 +420,17 @@ RCC_API int rccsdt_t4_create(int o, int v, int precision, void* stream, rccsdt_t
           }
           info.push_back(make_int4(type, mult, 0, 0));
         }
+  std::vector<int4> quads;
+  for (int D = 0; D < ntile; ++D)
+    for (int C = 0; C <= D; ++C)
+      for (int B = 0; B <= C; ++B)
+        for (int A = 0; A <= B; ++A) quads.push_back(make_int4(A, B, C, D));
   std::vector<int> sel(std::max<i64>(V2, c->unit * V2), 0);
   std::vector<double> al(std::max<i64>(V2, c->unit * V2), 1.0);
   bool cp = cudaMemcpy(c->rowbase, rb.data(), rb.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->coloff, co.data(), co.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->info, info.data(), info.size() * sizeof(int4), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->quads, quads.data(), quads.size() * sizeof(int4), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->rowsel, sel.data(), sel.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->alpha, al.data(), al.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemset(c->scal, 0, 64 * 8) == cudaSuccess;
@@ -373,6 +440,12 @@ RCC_API int rccsdt_t4_create(int o, int v, int precision, void* stream, rccsdt_t
     return RCCSDT_ERR_CUDA;
   }
   t4_tables_once();
+  if (cudaFuncSetAttribute(k_t4_post<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 24 * kT4Slot * 8) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return RCCSDT_ERR_CUDA;
+  }
   *out = c;
   return RCCSDT_OK;
 }
@@ -454,14 +527,15 @@ RCC_API int rccsdt_t4_pp_ladder(rccsdt_t4* c) {
 RCC_API int rccsdt_t4_postprocess(rccsdt_t4* c, double* norm) {
   if (!c) return RCCSDT_ERR_ARG;
   if (!c->have_r) return c->fail(RCCSDT_ERR_STATE, "R4 not computed");
-  const i64 ncta = c->n4 * c->chunks;
+  const i64 ncta = c->n4 * c->qgrid;
+  const dim3 grid((unsigned)c->qgrid, (unsigned)c->n4);
   ++rcc::g_launch_count;
   if (c->prec == RCCSDT_FP64)
-    k_t4_post<double><<<(unsigned)ncta, 256, 0, c->s>>>((const double*)c->r4, (double*)c->rp4, c->info, c->v,
-                                                        c->chunks, c->partial);
+    k_t4_post<double><<<grid, 256, 24 * kT4Slot * 8, c->s>>>((const double*)c->r4, (double*)c->rp4, c->info,
+                                                             c->quads, c->nq, c->v, c->partial);
   else
-    k_t4_post<float><<<(unsigned)ncta, 256, 0, c->s>>>((const float*)c->r4, (float*)c->rp4, c->info, c->v,
-                                                       c->chunks, c->partial);
+    k_t4_post<float><<<grid, 256, 24 * kT4Slot * 4, c->s>>>((const float*)c->r4, (float*)c->rp4, c->info,
+                                                            c->quads, c->nq, c->v, c->partial);
   ++rcc::g_launch_count;
   k_t4_reduce<<<1, 32, 0, c->s>>>(c->partial, ncta, c->scal);
   std::swap(c->r4, c->rp4);

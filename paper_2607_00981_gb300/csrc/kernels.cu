@@ -1524,10 +1524,7 @@ __global__ void __launch_bounds__(256, 5) k_scatter_rows3(const float* __restric
   const int nt = (v + TL - 1) / TL;
   const i64 V2 = (i64)v * v, V3 = V2 * v;
   const int lf = threadIdx.x & 15, lm = threadIdx.x >> 4;
-  const int ntile = nt * nt * nt;
-  // work items (row m, cube tile) in row-major order over the whole grid
-  for (i64 w = (i64)blockIdx.y * gridDim.x + blockIdx.x; w < (i64)M * ntile; w += (i64)gridDim.x * gridDim.y) {
-    const int m = (int)(w / ntile), tile = (int)(w - (i64)m * ntile);
+  for (int m = blockIdx.y; m < M; m += gridDim.y) {
     const int sel = row_sel[m];
     const int p0 = perm3(sel, 0), p1 = perm3(sel, 1), p2 = perm3(sel, 2);  // stored axis of X slot q
     // slot whose label lands on the target's unit-stride axis, and the other two
@@ -1541,7 +1538,7 @@ __global__ void __launch_bounds__(256, 5) k_scatter_rows3(const float* __restric
     const i64 base = row_base[m];
     const T al = (T)row_alpha[m];
     const float* xm = X + (i64)m * V3;
-    {
+    for (int tile = blockIdx.x; tile < nt * nt * nt; tile += gridDim.x) {
       const int lo0 = tile / (nt * nt) * TL, lo1 = (tile / nt) % nt * TL, lo2 = tile % nt * TL;
       __syncthreads();
       {  // X cube along c: thread (b, c) = (lm, lf), 16 loads in flight (one running pointer)
@@ -1590,21 +1587,17 @@ __global__ void __launch_bounds__(256, 5) k_scatter_rows3(const float* __restric
 
 template <typename T>
 void launch_scatter_rows3(const float* X, int M, int v, const i64* row_base, const int* row_sel,
-                          const double* row_alpha, T* C, cudaStream_t s, int ctas) {
+                          const double* row_alpha, T* C, cudaStream_t s) {
   const int nt = (v + 15) / 16;
   unsigned gx = (unsigned)std::min(nt * nt * nt, 1024);
   unsigned gy = (unsigned)std::min(M, 65535);
-  if (ctas > 0) {  // a fixed grid that loops over the work (beside a persistent GEMM)
-    gx = (unsigned)ctas;
-    gy = 1;
-  }
   ++g_launch_count;
   k_scatter_rows3<T><<<dim3(gx, gy), 256, 0, s>>>(X, M, v, row_base, row_sel, row_alpha, C);
 }
 template void launch_scatter_rows3<float>(const float*, int, int, const i64*, const int*, const double*, float*,
-                                          cudaStream_t, int);
+                                          cudaStream_t);
 template void launch_scatter_rows3<double>(const float*, int, int, const i64*, const int*, const double*, double*,
-                                           cudaStream_t, int);
+                                           cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // T2-driven term of Eq. resi-rccsdt with K = o, output-stationary:

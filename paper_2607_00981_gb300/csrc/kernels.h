@@ -185,12 +185,10 @@ void launch_pair_pack_t(int kind, const void* t3, int t3_f32, i64 b0, int nblk, 
 void launch_zero_cols(const CubeDst& d, i64 rows, int k0, int kind, cudaStream_t s);
 // Second phase of a two-phase scatter: for each row m of the dense FP32 result X
 // [M][v^3] (natural (a,b,c) order), C[row_base[m] + perm_sel[m](a,b,c)] +=
-// row_alpha[m] * X[m][abc]; perm_sel indexes the 6 virtual permutations.  ctas > 0:
-// a grid of that many CTAs loops over the work (one per SM runs beside a persistent
-// GEMM on another stream).
+// row_alpha[m] * X[m][abc]; perm_sel indexes the 6 virtual permutations.
 template <typename T>
 void launch_scatter_rows3(const float* X, int M, int v, const i64* row_base, const int* row_sel,
-                          const double* row_alpha, T* C, cudaStream_t s, int ctas = 0);
+                          const double* row_alpha, T* C, cudaStream_t s);
 
 }  // namespace rcc
 

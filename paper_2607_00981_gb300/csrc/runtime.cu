@@ -299,13 +299,7 @@ struct rccsdt_ctx {
   i64 seg1 = 0, seg2 = 0, seg3 = 0;         // element counts
   int ns = 0;                               // virtual orbitals of the T3 part of the DIIS vectors
   std::unique_ptr<DBuf> diis_st, diis_partial;  // device DIIS counters int[8]; dot partials [3][M][blocks]
-  std::unique_ptr<DBuf> scalars, partial, splitk, rawX, rawX2;
-  // two-phase scatters on a second stream beside the next GEMM: the dense results
-  // alternate between rawX and rawX2; ev_scat[s] marks the end of the scatter that
-  // last read buffer s, ev_gemm the end of the GEMM a scatter reads
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_gemm = nullptr, ev_join = nullptr, ev_scat[2] = {nullptr, nullptr};
-  int raw_slot = 0, side_busy = 0, side_ctas = 0;
+  std::unique_ptr<DBuf> scalars, partial, splitk, rawX;
 
   DBuf* B(const std::string& k) { return buf.at(k).get(); }
   double* D(const std::string& k) { return buf.at(k)->d(); }
@@ -820,24 +814,10 @@ static void timer_collect(rccsdt_ctx* c, double* out_ms, double* gemm_launches, 
 #endif
 }
 
-// The main stream waits for the scatters queued on the second stream (before any
-// other work that reads or writes R3).
-static void side_join(rccsdt_ctx* c) {
-#ifndef RCC_HOSTSIM
-  if (!c->side_busy) return;
-  cudaEventRecord(c->ev_join, c->side);
-  cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-  c->side_busy = 0;
-#else
-  (void)c;
-#endif
-}
-
 // ---------------------------------------------------------------------------
 // Engine: run one GemmPlan
 // ---------------------------------------------------------------------------
 static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
-  if (g->s3_rows <= 0) side_join(c);
   // in the split modes every contraction runs as a split product on the tensor
   // cores (FP64 throughput on this part is 2 FMA per clock per SM), except the
   // bare integrals that define the energy
@@ -903,14 +883,6 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   } else {
     int* flag = (int*)((double*)c->scalars->p + 1000);
     float* raw = g->s3_rows > 0 && c->rawX ? (float*)c->rawX->p : nullptr;
-    // the scatter of this result on the second stream, beside the next GEMM (not for
-    // contexts that share the GPU in a batch, whose launches a graph captures)
-    const bool overlap = raw && c->side && !c->concurrent;
-    if (overlap) {
-      const int sl = c->raw_slot;
-      raw = sl ? (float*)c->rawX2->p : raw;
-      cudaStreamWaitEvent(c->stream, c->ev_scat[sl], 0);  // its last reader is done
-    }
     // tile width from the output columns: 128, 144 (e.g. the 136 pairs i <= j of o = 16) or 256
     auto width = [](int n) { return n <= 128 ? 128 : (n <= 144 ? 144 : 256); };
     int lst;
@@ -930,23 +902,10 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
       const i64* sb = (const i64*)g->s3_base->p;
       const int* ss = (const int*)g->s3_sel->p;
       const double* sa = (const double*)g->s3_alpha->p;
-      cudaStream_t ss_stream = c->stream;
-      int ctas = 0;
-      if (overlap) {  // scatters stay ordered among themselves on the second stream
-        cudaEventRecord(c->ev_gemm, c->stream);
-        cudaStreamWaitEvent(c->side, c->ev_gemm, 0);
-        ss_stream = c->side;
-        ctas = c->side_ctas;
-      }
       if (e.c_f32)
-        rcc::launch_scatter_rows3<float>(raw, g->s3_rows, c->v, sb, ss, sa, (float*)e.C, ss_stream, ctas);
+        rcc::launch_scatter_rows3<float>(raw, g->s3_rows, c->v, sb, ss, sa, (float*)e.C, c->stream);
       else
-        rcc::launch_scatter_rows3<double>(raw, g->s3_rows, c->v, sb, ss, sa, (double*)e.C, ss_stream, ctas);
-      if (overlap) {
-        cudaEventRecord(c->ev_scat[c->raw_slot], c->side);
-        c->raw_slot ^= 1;
-        c->side_busy = 1;
-      }
+        rcc::launch_scatter_rows3<double>(raw, g->s3_rows, c->v, sb, ss, sa, (double*)e.C, c->stream);
     }
   }
   timer_end(c, tidx);
@@ -960,12 +919,8 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
 static int run_plans(rccsdt_ctx* c, const std::vector<GemmPlan*>& ps) {
   for (GemmPlan* g : ps) {
     int st = run_gemm(c, g);
-    if (st) {
-      side_join(c);
-      return st;
-    }
+    if (st) return st;
   }
-  side_join(c);
   return 0;
 }
 
@@ -2513,24 +2468,6 @@ RCC_API int rccsdt_create(int o, int v, int naux, const rccsdt_options* opt, voi
       c->rawX->bytes = mx * 4;
       c->rawX->p = dev_alloc(c->rawX->bytes, &err);
       c->total_bytes += c->rawX->bytes;
-#ifndef RCC_HOSTSIM
-      if (mx > 0) {
-        c->rawX2 = std::make_unique<DBuf>();
-        c->rawX2->bytes = mx * 4;
-        c->rawX2->p = dev_alloc(c->rawX2->bytes, &err);
-        c->total_bytes += c->rawX2->bytes;
-        int dev = 0, sms = 0;
-        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_gemm, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_scat[0], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_scat[1], cudaEventDisableTiming) != cudaSuccess ||
-            cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-          err = RCCSDT_ERR_CUDA;
-        c->side_ctas = sms;
-      }
-#endif
     }
     // DIIS history
     c->seg1 = (i64)o * v;
@@ -2981,12 +2918,6 @@ RCC_API void rccsdt_destroy(rccsdt_ctx* c) {
   if (!c) return;
   dev_sync(c->stream);
 #ifndef RCC_HOSTSIM
-  if (c->side) {
-    cudaStreamSynchronize(c->side);
-    cudaStreamDestroy(c->side);
-  }
-  for (cudaEvent_t e : {c->ev_gemm, c->ev_join, c->ev_scat[0], c->ev_scat[1]})
-    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
 #endif
   delete c;

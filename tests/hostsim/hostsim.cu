@@ -596,7 +596,7 @@ template void launch_r1_t3<double>(const double*, const double*, int, int, doubl
 template void launch_r1_t3<float>(const float*, const double*, int, int, double*, double*, i64, cudaStream_t);
 template <typename T>
 void launch_scatter_rows3(const float* X, int M, int v, const i64* row_base, const int* row_sel,
-                          const double* row_alpha, T* C, cudaStream_t, int) {
+                          const double* row_alpha, T* C, cudaStream_t) {
   const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
   const i64 V3 = (i64)v * v * v, S[3] = {(i64)v * v, v, 1};
   for (int m = 0; m < M; ++m) {
@@ -608,9 +608,9 @@ void launch_scatter_rows3(const float* X, int M, int v, const i64* row_base, con
   }
 }
 template void launch_scatter_rows3<float>(const float*, int, int, const i64*, const int*, const double*, float*,
-                                          cudaStream_t, int);
+                                          cudaStream_t);
 template void launch_scatter_rows3<double>(const float*, int, int, const i64*, const int*, const double*, double*,
-                                           cudaStream_t, int);
+                                           cudaStream_t);
 template <typename T>
 void launch_t2_outer(T* r3, const T* Wvooo, const T* t2, const int4* blocks, int o, int v, i64 n3, cudaStream_t) {
   const i64 V3 = (i64)v * v * v;

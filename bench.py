@@ -494,9 +494,19 @@ def run_ours(args, rank, world):
     prec = PRECISIONS[args.precision]
     stream = torch.cuda.current_stream()
     n3 = o * (o + 1) * (o + 2) // 6
-    hist_t3 = 2 * 8 * n3 * v ** 3 * (8 if prec == 0 else 4)
-    diis_t3 = 0 if (args.no_diis_t3 or hist_t3 > 64e9) else 1
-    ctx = pkg.context(o, v, naux, stream=stream.cuda_stream, precision=prec, diis_t3=diis_t3)
+    # DIIS(8) over T1, T2 and T3; when the T3 history would exceed 64 GB it keeps the
+    # T3 components with all virtual labels below ns (the largest multiple of 16 whose
+    # history stays within 80 GB: ns = 112 at o16v160, 73 GB, with which that workload
+    # converges)
+    elem = 8 if prec == 0 else 4
+    hist_t3 = 2 * 8 * n3 * v ** 3 * elem
+    diis_t3 = 0 if args.no_diis_t3 else 1
+    nvir = 0
+    if diis_t3 and hist_t3 > 64e9:
+        nvir = 16 * max(1, int((80e9 / (2 * 8 * n3 * elem)) ** (1 / 3) // 16))
+        while nvir > 16 and 2 * 8 * n3 * nvir ** 3 * elem > 80e9:
+            nvir -= 16
+    ctx = pkg.context(o, v, naux, stream=stream.cuda_stream, precision=prec, diis_t3=diis_t3, diis_t3_nvir=nvir)
     lib = ctx.lib
     L = torch.from_numpy(inst.L).to(f"cuda:{dev}")
     f = torch.from_numpy(inst.fock_diag).to(f"cuda:{dev}")
@@ -622,7 +632,10 @@ def run_ours(args, rank, world):
                 "energy_last": energies[-1], "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                 "cpu_baseline": cpu, "clocks": clk.summary(), "fp64_vs_split": compare, "fp64_here": fp64_here,
                 "batch64": batch, "matmul_peaks": mm, "q_correction": extra_q, "t4_ladder": extra_t4,
-                "diis": "T1, T2 and T3" if diis_t3 else "T1 and T2 (T3 history would exceed 64 GB)",
+                "diis": ("DIIS(8) over T1 and T2" if not diis_t3 else
+                         "DIIS(8) over T1, T2 and T3" if not nvir else
+                         f"DIIS(8) over T1, T2 and the T3 components with a, b, c < {nvir} "
+                         f"({2 * 8 * n3 * nvir ** 3 * elem / 1e9:.0f} GB of history)"),
                 "step_ms": step_ms}
         print(json.dumps(line), flush=True)
     if dist:

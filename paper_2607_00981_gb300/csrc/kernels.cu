@@ -738,12 +738,14 @@ __global__ void __launch_bounds__(256) k_update_t3(T* __restrict__ t3, const T* 
       for (int q = tid; q < n4; q += 256) {
         const int bb = (4 * q) / v, c = 4 * q - bb * v;
         const float eh = rh[bb], el = rl[bb];
+        // the four e_c pairs as two vector loads (16-byte aligned: v is a multiple of 4)
+        const float4 h4 = *reinterpret_cast<const float4*>(ch + c), l4 = *reinterpret_cast<const float4*>(cl + c);
         const float4 tv = t4[q], rv = r4[q];
         float4 out;
-        out.x = tv.x + rv.x / ((eh - ch[c]) + (el - cl[c]));
-        out.y = tv.y + rv.y / ((eh - ch[c + 1]) + (el - cl[c + 1]));
-        out.z = tv.z + rv.z / ((eh - ch[c + 2]) + (el - cl[c + 2]));
-        out.w = tv.w + rv.w / ((eh - ch[c + 3]) + (el - cl[c + 3]));
+        out.x = tv.x + rv.x / ((eh - h4.x) + (el - l4.x));
+        out.y = tv.y + rv.y / ((eh - h4.y) + (el - l4.y));
+        out.z = tv.z + rv.z / ((eh - h4.z) + (el - l4.z));
+        out.w = tv.w + rv.w / ((eh - h4.w) + (el - l4.w));
         t4[q] = out;
       }
     } else {

@@ -727,35 +727,12 @@ __global__ void __launch_bounds__(256) k_update_t3(T* __restrict__ t3, const T* 
       cl[q] = (float)(ec - (double)ch[q]);
     }
     __syncthreads();
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    if ((v & 3) == 0) {
-      // rows of v floats start on 16-byte boundaries: four elements per access,
-      // four accesses per thread in flight
-      const int n4 = (int)(V2 >> 2);
-      float4* t4 = reinterpret_cast<float4*>(tb);
-      const float4* r4 = reinterpret_cast<const float4*>(rb);
-#pragma unroll 4
-      for (int q = tid; q < n4; q += 256) {
-        const int bb = (4 * q) / v, c = 4 * q - bb * v;
-        const float eh = rh[bb], el = rl[bb];
-        // the four e_c pairs as two vector loads (16-byte aligned: v is a multiple of 4)
-        const float4 h4 = *reinterpret_cast<const float4*>(ch + c), l4 = *reinterpret_cast<const float4*>(cl + c);
-        const float4 tv = t4[q], rv = r4[q];
-        float4 out;
-        out.x = tv.x + rv.x / ((eh - h4.x) + (el - l4.x));
-        out.y = tv.y + rv.y / ((eh - h4.y) + (el - l4.y));
-        out.z = tv.z + rv.z / ((eh - h4.z) + (el - l4.z));
-        out.w = tv.w + rv.w / ((eh - h4.w) + (el - l4.w));
-        t4[q] = out;
-      }
-    } else {
-      for (int bb = threadIdx.y; bb < v; bb += 8) {
-        const float eh = rh[bb], el = rl[bb];
-        for (int c = threadIdx.x; c < v; c += 32) {
-          const int idx = bb * v + c;
-          const float d = (eh - ch[c]) + (el - cl[c]);
-          tb[idx] = tb[idx] + rb[idx] / d;
-        }
+    for (int bb = threadIdx.y; bb < v; bb += 8) {
+      const float eh = rh[bb], el = rl[bb];
+      for (int c = threadIdx.x; c < v; c += 32) {
+        const int idx = bb * v + c;
+        const float d = (eh - ch[c]) + (el - cl[c]);
+        tb[idx] = tb[idx] + rb[idx] / d;
       }
     }
   } else {
@@ -1608,12 +1585,12 @@ template void launch_scatter_rows3<double>(const float*, int, int, const i64*, c
 // One CTA of 64 threads owns a 16^3 tile of one stored block and accumulates all six
 // terms in registers, each thread a 4 x 4 x 4 sub-cube (register blocking: per l one
 // 4-vector of W and a 4 x 4 patch of t2 from shared memory feed 64 FMAs).  Per term
-// and chunk of 16 values of l the W slice [l][a1] and the t2 slice [l][a2][a3] of the
+// and chunk of 8 values of l the W slice [l][a1] and the t2 slice [l][a2][a3] of the
 // tile are copied to shared memory with cp.async (zero-filled outside the block and
 // beyond o), two stages in flight.  The block is read and written once.
 // Wvooo[a][l][i][j] = W^{al}_{ij}; t2[l][k][b][c] = t_lk^bc (T precision copies).
 // ---------------------------------------------------------------------------
-constexpr int kT2oTL = 16, kT2oLC = 16, kT2oThreads = 64;
+constexpr int kT2oTL = 16, kT2oLC = 8, kT2oThreads = 64;
 
 template <typename T>
 struct T2oLayout {

@@ -199,12 +199,28 @@ RCC_HD void panel_put(int kind, void* out_hi, void* out_lo, i64 o, double x) {
   if (kind == PANEL_F64) {
     ((double*)out_hi)[o] = x;
   } else if (kind == PANEL_BF16X2) {
-    const float f = (float)x;
+    const float f = f64_to_f32_rn(x);  // integer-path rounding (no FP64 pipe)
     const __nv_bfloat16 hi = __float2bfloat16_rn(f);
     ((__nv_bfloat16*)out_hi)[o] = hi;
     ((__nv_bfloat16*)out_lo)[o] = __float2bfloat16_rn(f - __bfloat162float(hi));
   } else {
-    const float f = (float)x;
+    const float f = f64_to_f32_rn(x);
+    const float hi = tf32_round(f);
+    ((float*)out_hi)[o] = hi;
+    ((float*)out_lo)[o] = tf32_round(f - hi);
+  }
+}
+
+// The same for an FP32 value (no round trip through FP64: on this part the FP64
+// units convert at a small fraction of the FP32 rate).
+RCC_HD void panel_put_f(int kind, void* out_hi, void* out_lo, i64 o, float f) {
+  if (kind == PANEL_F64) {
+    ((double*)out_hi)[o] = (double)f;
+  } else if (kind == PANEL_BF16X2) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+    ((__nv_bfloat16*)out_hi)[o] = hi;
+    ((__nv_bfloat16*)out_lo)[o] = __float2bfloat16_rn(f - __bfloat162float(hi));
+  } else {
     const float hi = tf32_round(f);
     ((float*)out_hi)[o] = hi;
     ((float*)out_lo)[o] = tf32_round(f - hi);

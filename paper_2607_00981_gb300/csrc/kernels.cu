@@ -582,9 +582,11 @@ __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __rest
   const int n = ncube;
   // thread (xg, ty, tz): rows x = xg and xg + 4 of every cube, local (ty, tz) along them
   const int tz = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, xg = threadIdx.x >> 6;
-  double nrm = 0.0;  // sum over this CTA's outputs of m(blk) val^2 (the |R3|^2 share)
+  // sum over this CTA's outputs of m(blk) val^2 (the |R3|^2 share), in the storage
+  // type across its blocks (FP32 storage: no per-block FP64 work)
+  T nrm = (T)0;
   for (i64 b = blockIdx.y; b < n3; b += gridDim.y) {
-    const double wb = wblk[b];
+    const T wb = (T)wblk[b];
     const int4 ijk = blocks[b];
     const T* rb = r + b * V3;
     T ld[6][2];
@@ -639,10 +641,10 @@ __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __rest
         bs += val * val;
       }
     }
-    nrm += wb * (double)bs;
+    nrm += wb * bs;
   }
-  nrm = block_sum(nrm);
-  if (threadIdx.x == 0) partial[(i64)blockIdx.y * gridDim.x + blockIdx.x] = nrm;
+  const double tot = block_sum((double)nrm);
+  if (threadIdx.x == 0) partial[(i64)blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
 // about 8 resident waves of CTAs (eight per SM); each keeps its orbit tables across

@@ -46,6 +46,7 @@ constexpr int kPos[6][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}, {1, 2, 0, 
 
 __constant__ unsigned char c_t4perm[24][4];
 __constant__ double c_t4coef[5][24];  // per symmetrisation type
+__constant__ float c_t4coef_f[5][24];  // the same in FP32 (FP32 storage)
 
 // A panel: A[(x, y)][(e, f)] = W^{xy}_{ef} (W row-major is already [v^2][v^2]).
 __global__ void k_t4_pack_w(const double* __restrict__ W, int v, int kind, void* hi, void* lo, int Kpad) {
@@ -64,7 +65,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_t4_pack_t(const T* __restrict__ t4, i64 b0, int nblk, int v, int sp,
                                                    int sq, int sr, int ss, int kind, void* hi, void* lo,
                                                    int Kpad) {
-  __shared__ double tile[32][33];
+  __shared__ T tile[32][33];
   const int nt = (v + 31) / 32;
   i64 id = blockIdx.x;
   const int tw = (int)(id % nt);
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(256) k_t4_pack_t(const T* __restrict__ t4, i64
     // element (f, w2) = (tf*32 + i, tw*32 + j); i, j chosen so consecutive threads read consecutive memory
     const int i = f_fast ? tx : yy, j = f_fast ? yy : tx;
     const int f = tf * 32 + i, w2 = tw * 32 + j;
-    tile[i][j] = (f < v && w2 < v) ? (double)base[(i64)f * sq + (i64)w2 * ss] : 0.0;
+    tile[i][j] = (f < v && w2 < v) ? base[(i64)f * sq + (i64)w2 * ss] : (T)0;
   }
   __syncthreads();
   const i64 V2 = (i64)v * v;
@@ -91,7 +92,10 @@ __global__ void __launch_bounds__(256) k_t4_pack_t(const T* __restrict__ t4, i64
     const int f = tf * 32 + tx, w2 = tw * 32 + yy;
     if (f < v && w2 < v) {
       const i64 row = (blk * v + w1) * v + w2;
-      rcc::panel_put(kind, hi, lo, row * Kpad + (i64)e * v + f, tile[tx][yy]);
+      if constexpr (sizeof(T) == 4)
+        rcc::panel_put_f(kind, hi, lo, row * Kpad + (i64)e * v + f, tile[tx][yy]);
+      else
+        rcc::panel_put(kind, hi, lo, row * Kpad + (i64)e * v + f, tile[tx][yy]);
     }
   }
   // zero the padding columns K = v^2 .. Kpad of the rows this CTA owns (once per row)
@@ -100,7 +104,7 @@ __global__ void __launch_bounds__(256) k_t4_pack_t(const T* __restrict__ t4, i64
       const int w2 = tw * 32 + yy;
       if (w2 >= v) continue;
       const i64 row = (blk * v + w1) * v + w2;
-      for (i64 k = V2 + tx; k < Kpad; k += 32) rcc::panel_put(kind, hi, lo, row * Kpad + k, 0.0);
+      for (i64 k = V2 + tx; k < Kpad; k += 32) rcc::panel_put_f(kind, hi, lo, row * Kpad + k, 0.f);
     }
   }
 }
@@ -185,6 +189,7 @@ __global__ void __launch_bounds__(256) k_t4_post(const T* __restrict__ r, T* __r
       if (q.x < 5) tiles[sl * kT4Slot + own] = in ? rb[off] : (T)0;
     }
     __syncthreads();
+    T qs = (T)0;  // this quadruple's squared outputs, in the storage type
     for (int sl = 0; sl < 24; ++sl) {
       if (canon[sl] != sl) continue;
       int g[4];
@@ -194,15 +199,18 @@ __global__ void __launch_bounds__(256) k_t4_post(const T* __restrict__ r, T* __r
       if (q.x < 5) {
 #pragma unroll
         for (int p = 0; p < 24; ++p) {
-          const T d = (T)c_t4coef[q.x][p];
+          T d;
+          if constexpr (sizeof(T) == 4) d = c_t4coef_f[q.x][p];
+          else d = c_t4coef[q.x][p];
           acc += d * tiles[canon[c_t4comp[sl][p]] * kT4Slot + paddr[p]];
         }
       }
       if (g[0] < v && g[1] < v && g[2] < v && g[3] < v) {
         ob[(((i64)g[0] * v + g[1]) * v + g[2]) * v + g[3]] = acc;
-        s += (double)acc * (double)acc;
+        qs += acc * acc;
       }
     }
+    s += (double)qs;
     __syncthreads();  // the next quadruple restages the tiles
   }
   const double bs = t4_block_sum<T>(s, ws);
@@ -315,6 +323,10 @@ void t4_tables_once() {
   cudaMemcpyToSymbol(c_t4perm, hp, sizeof(hp));
   cudaMemcpyToSymbol(c_t4comp, comp, sizeof(comp));
   cudaMemcpyToSymbol(c_t4coef, coef, sizeof(coef));
+  float coef_f[5][24];
+  for (int g = 0; g < 5; ++g)
+    for (int i = 0; i < 24; ++i) coef_f[g][i] = (float)coef[g][i];
+  cudaMemcpyToSymbol(c_t4coef_f, coef_f, sizeof(coef_f));
   done = true;
 }
 

@@ -1524,97 +1524,90 @@ template void launch_r1_t3<float>(const float*, const double*, int, int, double*
 // ---------------------------------------------------------------------------
 // Two-phase scatter of whole v^3 rows: X[m] in natural (a,b,c) order is added to
 // the stored block at row_base[m] with the virtual axes permuted by the sort
-// permutation perm_sel[m].  A work item is a 32 x 32 tile over two label slots of
-// one row -- slot 2 (c, unit stride in X) and the slot that lands on the target's
-// unit-stride axis (slot 1 when that is c itself) -- for 4 consecutive values of
-// the third slot.  The tile is read along c in 128-byte runs, staged in shared
-// memory, and added along the target's unit-stride axis in 128-byte runs
-// (transposed through shared memory when the two axes differ): whole 128-byte
-// lines on both sides, 16 loads and 16 read-modify-writes in flight per thread.
+// permutation perm_sel[m].  One CTA moves a 16^3 cube: the cube is read along c
+// (coalesced), staged in shared memory, and added along the target's unit-stride
+// axis (coalesced read-modify-write).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_scatter_rows3(const float* __restrict__ X, int M, int v,
+__global__ void __launch_bounds__(256, 5) k_scatter_rows3(const float* __restrict__ X, int M, int v,
                                                        const i64* __restrict__ row_base,
                                                        const int* __restrict__ row_sel,
                                                        const double* __restrict__ row_alpha, T* __restrict__ C) {
-  constexpr int TW = 32, TU = 4;
-  __shared__ float tile[TU][TW][TW + 1];
+  constexpr int TL = 16;
+  __shared__ float cube[TL][TL + 1][TL + 2];
+  constexpr int SA = (TL + 1) * (TL + 2), SB = TL + 2;  // shared strides of the cube's a and b slots
+  const int nt = (v + TL - 1) / TL;
   const i64 V2 = (i64)v * v, V3 = V2 * v;
-  const int nt = (v + TW - 1) / TW, nu = (v + TU - 1) / TU;
-  const i64 per_row = (i64)nu * nt * nt;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  for (i64 w = blockIdx.x; w < (i64)M * per_row; w += gridDim.x) {
-    const int m = (int)(w / per_row);
-    const i64 r = w - (i64)m * per_row;
-    const int u0 = (int)(r / (nt * nt)) * TU, bc = (int)((r / nt) % nt) * TW, bf = (int)(r % nt) * TW;
+  const int lf = threadIdx.x & 15, lm = threadIdx.x >> 4;
+  for (int m = blockIdx.y; m < M; m += gridDim.y) {
     const int sel = row_sel[m];
     const int p0 = perm3(sel, 0), p1 = perm3(sel, 1), p2 = perm3(sel, 2);  // stored axis of X slot q
-    const int fast = p0 == 2 ? 0 : (p1 == 2 ? 1 : 2);  // the slot on the target's unit-stride axis
-    const int F = fast == 2 ? 1 : fast, R = 3 - 2 - F;  // tile slots (2, F), third slot R
-    auto xs = [&](int q) { return q == 0 ? V2 : (q == 1 ? (i64)v : (i64)1); };  // X strides
-    auto cs = [&](int q) {  // target stride of slot q
-      const int ax = q == 0 ? p0 : (q == 1 ? p1 : p2);
-      return ax == 0 ? V2 : (ax == 1 ? (i64)v : (i64)1);
-    };
-    const i64 xF = xs(F), xR = xs(R), cF = cs(F), cR = cs(R), c2 = cs(2);
+    // slot whose label lands on the target's unit-stride axis, and the other two
+    const int fast = p0 == 2 ? 0 : (p1 == 2 ? 1 : 2);
+    const int mid = fast == 0 ? 1 : 0, slow = 3 - fast - mid;
+    auto pq = [&](int q) { return q == 0 ? p0 : (q == 1 ? p1 : p2); };
+    auto sv = [&](int axis) { return axis == 0 ? V2 : (axis == 1 ? (i64)v : (i64)1); };
+    auto ss = [&](int q) { return q == 0 ? SA : (q == 1 ? SB : 1); };
+    const i64 stm = sv(pq(mid)), sts = sv(pq(slow));
+    const int cF = ss(fast), cM = ss(mid), cS = ss(slow);
+    const i64 base = row_base[m];
+    const T al = (T)row_alpha[m];
     const float* xm = X + (i64)m * V3;
-    __syncthreads();  // the previous item's tile is consumed
-    // X along c: thread (f = ty + 8 i, c = tx), 4 values of the third slot
-    {
-      const int gc = bc + tx;
-      float ld[TU][4];
+    for (int tile = blockIdx.x; tile < nt * nt * nt; tile += gridDim.x) {
+      const int lo0 = tile / (nt * nt) * TL, lo1 = (tile / nt) % nt * TL, lo2 = tile % nt * TL;
+      __syncthreads();
+      {  // X cube along c: thread (b, c) = (lm, lf), 16 loads in flight (one running pointer)
+        const int gb = lo1 + lm, gc = lo2 + lf;
+        const int na = (gb < v && gc < v) ? min(TL, v - lo0) : 0;
+        const float* px = xm + lo0 * V2 + (i64)gb * v + gc;
+        float ld[TL];
 #pragma unroll
-      for (int uu = 0; uu < TU; ++uu)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int gf = bf + ty + 8 * i, gu = u0 + uu;
-          ld[uu][i] = (gc < v && gf < v && gu < v) ? __ldg(xm + gf * xF + gu * xR + gc) : 0.f;
+        for (int a = 0; a < TL; ++a) {
+          ld[a] = a < na ? __ldg(px) : 0.f;
+          px += V2;
         }
 #pragma unroll
-      for (int uu = 0; uu < TU; ++uu)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) tile[uu][ty + 8 * i][tx] = ld[uu][i];
-    }
-    __syncthreads();
-    const T al = (T)row_alpha[m];
-    T* cb = C + row_base[m];
-    // lanes along the target's unit-stride slot: c itself (no transposition) or F
-    const bool tr = fast != 2;
-    T* dst[TU][4];
-    float val[TU][4];
-    bool ok[TU][4];
-#pragma unroll
-    for (int uu = 0; uu < TU; ++uu)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int gu = u0 + uu;
-        const int g_lane = (tr ? bf : bc) + tx, g_row = (tr ? bc : bf) + ty + 8 * i;  // lane slot, row slot
-        const int gc = tr ? g_row : g_lane, gf = tr ? g_lane : g_row;
-        ok[uu][i] = gc < v && gf < v && gu < v;
-        dst[uu][i] = cb + gc * c2 + gf * cF + gu * cR;
-        val[uu][i] = tr ? tile[uu][tx][ty + 8 * i] : tile[uu][ty + 8 * i][tx];
+        for (int a = 0; a < TL; ++a) cube[a][lm][lf] = ld[a];
       }
-    T old[TU][4];
+      __syncthreads();
+      // add along the target's unit-stride axis: slot fast = lf, mid = lm, slow = u
+      const int lofast = fast == 0 ? lo0 : (fast == 1 ? lo1 : lo2);
+      const int lomid = mid == 0 ? lo0 : (mid == 1 ? lo1 : lo2);
+      const int loslow = slow == 0 ? lo0 : (slow == 1 ? lo1 : lo2);
+      const int gf = lofast + lf, gm = lomid + lm;
+      if (gf < v && gm < v) {
+        T* dst = C + base + gf + gm * stm + (i64)loslow * sts;
+        const float* src = &cube[0][0][0] + lf * cF + lm * cM;
+        const int nu = min(TL, v - loslow);
 #pragma unroll
-    for (int uu = 0; uu < TU; ++uu)
+        for (int h = 0; h < TL; h += 8) {  // two halves of 8 read-modify-writes in flight
+          T old[8];
+          T* pd = dst + h * sts;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) old[uu][i] = ok[uu][i] ? *dst[uu][i] : (T)0;
+          for (int u = 0; u < 8; ++u) {
+            old[u] = h + u < nu ? pd[0] : (T)0;
+            pd += sts;
+          }
+          pd = dst + h * sts;
 #pragma unroll
-    for (int uu = 0; uu < TU; ++uu)
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (ok[uu][i]) *dst[uu][i] = old[uu][i] + al * (T)val[uu][i];
+          for (int u = 0; u < 8; ++u) {
+            if (h + u < nu) pd[0] = old[u] + al * (T)src[(h + u) * cS];
+            pd += sts;
+          }
+        }
+      }
+    }
   }
 }
 
 template <typename T>
 void launch_scatter_rows3(const float* X, int M, int v, const i64* row_base, const int* row_sel,
                           const double* row_alpha, T* C, cudaStream_t s) {
-  const i64 nt = (v + 31) / 32, nu = (v + 3) / 4;
-  const i64 items = (i64)M * nu * nt * nt;
-  const unsigned gx = (unsigned)std::min<i64>(items, (i64)152 * 64);
+  const int nt = (v + 15) / 16;
+  unsigned gx = (unsigned)std::min(nt * nt * nt, 1024);
+  unsigned gy = (unsigned)std::min(M, 65535);
   ++g_launch_count;
-  k_scatter_rows3<T><<<gx, 256, 0, s>>>(X, M, v, row_base, row_sel, row_alpha, C);
+  k_scatter_rows3<T><<<dim3(gx, gy), 256, 0, s>>>(X, M, v, row_base, row_sel, row_alpha, C);
 }
 template void launch_scatter_rows3<float>(const float*, int, int, const i64*, const int*, const double*, float*,
                                           cudaStream_t);

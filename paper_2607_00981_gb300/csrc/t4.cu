@@ -59,52 +59,77 @@ __global__ void k_t4_pack_w(const double* __restrict__ W, int v, int kind, void*
 
 // B panel of one term for stored blocks b0 .. b0 + nblk - 1:
 //   B[((blk - b0) v + w1) v + w2][e v + f] = T[blk][p <- e, q <- f, r <- w1, s <- w2]
-// CTA = one (blk, w1, e) and a 32 x 32 tile of (f, w2); reads run along f or w2,
-// whichever has the block's unit stride, writes along K (f).
+// CTA = one (blk, w1); per e it stages the (w2, f) plane in chunks of up to 32 rows
+// w2 in shared memory, read along f or w2, whichever has the block's unit stride (one
+// always does), and writes each row's run of v K values (f) with 8 values per
+// thread (16-byte stores when the run starts on an 8-element boundary); the K
+// padding v^2 .. Kpad of its rows is zeroed once.
 template <typename T>
 __global__ void __launch_bounds__(256) k_t4_pack_t(const T* __restrict__ t4, i64 b0, int nblk, int v, int sp,
                                                    int sq, int sr, int ss, int kind, void* hi, void* lo,
                                                    int Kpad) {
-  __shared__ T tile[32][33];
-  const int nt = (v + 31) / 32;
-  i64 id = blockIdx.x;
-  const int tw = (int)(id % nt);
-  id /= nt;
-  const int tf = (int)(id % nt);
-  id /= nt;
-  const int e = (int)(id % v);
-  id /= v;
-  const int w1 = (int)(id % v);
-  const i64 blk = id / v;
-  const i64 V4 = (i64)v * v * v * v;
-  const T* base = t4 + (b0 + blk) * V4 + (i64)e * sp + (i64)w1 * sr;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  extern __shared__ __align__(16) unsigned char t4p_smem[];
+  T* tile = reinterpret_cast<T*>(t4p_smem);  // [32][v + 1]
+  const int P = v + 1;
+  const i64 blk = blockIdx.x / v;
+  const int w1 = (int)(blockIdx.x - blk * v);
+  const i64 V4 = (i64)v * v * v * v, V2 = (i64)v * v;
+  const T* base = t4 + (b0 + blk) * V4 + (i64)w1 * sr;
   const bool f_fast = sq == 1;
-  for (int yy = ty; yy < 32; yy += 8) {
-    // element (f, w2) = (tf*32 + i, tw*32 + j); i, j chosen so consecutive threads read consecutive memory
-    const int i = f_fast ? tx : yy, j = f_fast ? yy : tx;
-    const int f = tf * 32 + i, w2 = tw * 32 + j;
-    tile[i][j] = (f < v && w2 < v) ? base[(i64)f * sq + (i64)w2 * ss] : (T)0;
-  }
-  __syncthreads();
-  const i64 V2 = (i64)v * v;
-  for (int yy = ty; yy < 32; yy += 8) {
-    const int f = tf * 32 + tx, w2 = tw * 32 + yy;
-    if (f < v && w2 < v) {
-      const i64 row = (blk * v + w1) * v + w2;
-      if constexpr (sizeof(T) == 4)
-        rcc::panel_put_f(kind, hi, lo, row * Kpad + (i64)e * v + f, tile[tx][yy]);
-      else
-        rcc::panel_put(kind, hi, lo, row * Kpad + (i64)e * v + f, tile[tx][yy]);
+  const int nf8 = (v + 7) / 8;
+  const bool vec = (v & 7) == 0 && (Kpad & 7) == 0;
+  for (int e = 0; e < v; ++e) {
+    const T* pe = base + (i64)e * sp;
+    for (int r0 = 0; r0 < v; r0 += 32) {
+      const int nr = min(32, v - r0);
+      __syncthreads();  // the previous chunk is written out
+      for (int idx = threadIdx.x; idx < nr * v; idx += blockDim.x) {
+        int r, f;
+        if (f_fast) {
+          r = idx / v;
+          f = idx - r * v;
+        } else {
+          f = idx / nr;
+          r = idx - f * nr;
+        }
+        tile[r * P + f] = pe[(i64)f * sq + (i64)(r0 + r) * ss];
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nr * nf8; idx += blockDim.x) {
+        const int r = idx / nf8, f0 = (idx - r * nf8) * 8;
+        const i64 o = ((blk * v + w1) * v + r0 + r) * (i64)Kpad + (i64)e * v + f0;
+        const T* src = tile + r * P + f0;
+        if (vec && kind == rcc::PANEL_BF16X2 && sizeof(T) == 4) {
+          uint32_t h[4], l[4];  // bf16 pairs, first element in the low half
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const __nv_bfloat162 hp = __floats2bfloat162_rn((float)src[2 * j], (float)src[2 * j + 1]);
+            const float2 hf = __bfloat1622float2(hp);
+            const __nv_bfloat162 lp = __floats2bfloat162_rn((float)src[2 * j] - hf.x, (float)src[2 * j + 1] - hf.y);
+            h[j] = *reinterpret_cast<const uint32_t*>(&hp);
+            l[j] = *reinterpret_cast<const uint32_t*>(&lp);
+          }
+          *reinterpret_cast<uint4*>((__nv_bfloat16*)hi + o) = make_uint4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<uint4*>((__nv_bfloat16*)lo + o) = make_uint4(l[0], l[1], l[2], l[3]);
+        } else {
+          const int n = min(8, v - f0);
+          for (int j = 0; j < n; ++j) {
+            if constexpr (sizeof(T) == 4)
+              rcc::panel_put_f(kind, hi, lo, o + j, src[j]);
+            else
+              rcc::panel_put(kind, hi, lo, o + j, src[j]);
+          }
+        }
+      }
     }
   }
-  // zero the padding columns K = v^2 .. Kpad of the rows this CTA owns (once per row)
-  if (e == 0 && tf == 0) {
-    for (int yy = ty; yy < 32; yy += 8) {
-      const int w2 = tw * 32 + yy;
-      if (w2 >= v) continue;
-      const i64 row = (blk * v + w1) * v + w2;
-      for (i64 k = V2 + tx; k < Kpad; k += 32) rcc::panel_put_f(kind, hi, lo, row * Kpad + k, 0.f);
+  // zero the padding columns K = v^2 .. Kpad of this CTA's v rows
+  if (Kpad > V2) {
+    const int np = Kpad - (int)V2;
+    for (int idx = threadIdx.x; idx < v * np; idx += blockDim.x) {
+      const int w2 = idx / np;
+      const i64 k = V2 + (idx - w2 * np);
+      rcc::panel_put_f(kind, hi, lo, ((blk * v + w1) * v + w2) * (i64)Kpad + k, 0.f);
     }
   }
 }
@@ -217,11 +242,13 @@ __global__ void __launch_bounds__(256) k_t4_post(const T* __restrict__ r, T* __r
   if (threadIdx.x == 0) partial[blk * gridDim.x + blockIdx.x] = bs * (double)q.y;
 }
 
+// Sum of the partials in a fixed order: 256 strided runs, then a fixed tree.
 __global__ void k_t4_reduce(const double* __restrict__ partial, i64 n, double* __restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ double ws[8];
   double s = 0.0;
-  for (i64 i = 0; i < n; ++i) s += partial[i];
-  out[0] = s;
+  for (i64 i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+  const double t = t4_block_sum<double>(s, ws);
+  if (threadIdx.x == 0) out[0] = t;
 }
 
 template <typename TO, typename TI>
@@ -453,7 +480,9 @@ RCC_API int rccsdt_t4_create(int o, int v, int precision, void* stream, rccsdt_t
   }
   t4_tables_once();
   if (cudaFuncSetAttribute(k_t4_post<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 24 * kT4Slot * 8) !=
-      cudaSuccess) {
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_t4_pack_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * (200 + 1) * 8) !=
+          cudaSuccess) {
     cudaGetLastError();
     delete c;
     return RCCSDT_ERR_CUDA;
@@ -493,22 +522,22 @@ RCC_API int rccsdt_t4_pp_ladder(rccsdt_t4* c) {
     return c->fail(RCCSDT_ERR_CUDA, "memset failed");
   cudaMemsetAsync(c->scal, 0, 64 * 8, c->s);
   const i64 st[4] = {V2 * v, V2, (i64)v, 1};
-  const int nt = (v + 31) / 32;
   int* flag = (int*)(c->scal + 8);
   for (int t = 0; t < 6; ++t) {
     const int p = kPos[t][0], q = kPos[t][1], r = kPos[t][2], s = kPos[t][3];
     for (i64 b0 = 0; b0 < c->n4; b0 += c->unit) {
       const int nblk = (int)std::min<i64>(c->unit, c->n4 - b0);
-      const i64 ncta = (i64)nblk * v * v * nt * nt;
+      const i64 ncta = (i64)nblk * v;
+      const size_t tsm = (size_t)32 * (v + 1);
       ++rcc::g_launch_count;
       if (c->prec == RCCSDT_FP64)
-        k_t4_pack_t<double><<<(unsigned)ncta, 256, 0, c->s>>>((const double*)c->t4, b0, nblk, v, (int)st[p],
-                                                               (int)st[q], (int)st[r], (int)st[s], c->kind, c->Bhi,
-                                                               c->Blo, c->Kpad);
+        k_t4_pack_t<double><<<(unsigned)ncta, 256, tsm * 8, c->s>>>((const double*)c->t4, b0, nblk, v, (int)st[p],
+                                                                     (int)st[q], (int)st[r], (int)st[s], c->kind,
+                                                                     c->Bhi, c->Blo, c->Kpad);
       else
-        k_t4_pack_t<float><<<(unsigned)ncta, 256, 0, c->s>>>((const float*)c->t4, b0, nblk, v, (int)st[p],
-                                                              (int)st[q], (int)st[r], (int)st[s], c->kind, c->Bhi,
-                                                              c->Blo, c->Kpad);
+        k_t4_pack_t<float><<<(unsigned)ncta, 256, tsm * 4, c->s>>>((const float*)c->t4, b0, nblk, v, (int)st[p],
+                                                                    (int)st[q], (int)st[r], (int)st[s], c->kind,
+                                                                    c->Bhi, c->Blo, c->Kpad);
       rcc::EpiArgs e{};
       e.C = c->r4;
       e.c_f32 = c->prec != RCCSDT_FP64;
@@ -549,7 +578,7 @@ RCC_API int rccsdt_t4_postprocess(rccsdt_t4* c, double* norm) {
     k_t4_post<float><<<grid, 256, 24 * kT4Slot * 4, c->s>>>((const float*)c->r4, (float*)c->rp4, c->info,
                                                             c->quads, c->nq, c->v, c->partial);
   ++rcc::g_launch_count;
-  k_t4_reduce<<<1, 32, 0, c->s>>>(c->partial, ncta, c->scal);
+  k_t4_reduce<<<1, 256, 0, c->s>>>(c->partial, ncta, c->scal);
   std::swap(c->r4, c->rp4);
   double h = 0.0;
   if (cudaMemcpyAsync(&h, c->scal, 8, cudaMemcpyDeviceToHost, c->s) != cudaSuccess ||

@@ -29,8 +29,10 @@
  *   Residuals r1, r2, r3c use the same layouts.
  * Pointers passed in or out may be host or device memory (the library copies with
  * cudaMemcpyDefault on the context's stream and synchronises before returning
- * from calls that read or write caller memory).  The caller keeps ownership of
- * its buffers; the context owns every buffer it allocates.
+ * from calls that read or write caller memory; an FP32-storage context converts
+ * T3 from or to device memory and pinned host memory in place, with one kernel
+ * over the host link, and stages pageable host memory in chunks).  The caller
+ * keeps ownership of its buffers; the context owns every buffer it allocates.
  *
  * Errors: every call returns an rccsdt_status; nothing aborts, traps or prints.
  * rccsdt_last_error() gives a text for the last failing call on a context.

@@ -2535,6 +2535,26 @@ static void reset_diis(rccsdt_ctx* c) {
   if (c->diis_st) dev_zero(c->diis_st->p, c->diis_st->bytes, c->stream);
 }
 
+// Device address of caller memory that kernels can access in place: device memory,
+// or pinned / registered host memory mapped into the device's address space (read
+// over the host link by the conversion kernel itself, without a staging copy).
+// nullptr for pageable host memory.
+static const void* device_view(const void* p) {
+#ifndef RCC_HOSTSIM
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if ((at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeManaged) &&
+      at.devicePointer)
+    return at.devicePointer;
+#else
+  (void)p;
+#endif
+  return nullptr;
+}
+
 RCC_API int rccsdt_set_amplitudes(rccsdt_ctx* c, const double* t1, const double* t2, const double* t3c) {
   if (!c) return RCCSDT_ERR_ARG;
   const bool f = c->opt.precision != RCCSDT_FP64;
@@ -2545,8 +2565,11 @@ RCC_API int rccsdt_set_amplitudes(rccsdt_ctx* c, const double* t1, const double*
     const i64 cnt = c->n3 * c->V3;
     if (!f) {
       if (dev_copy(c->D("t3"), t3c, (size_t)cnt * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+    } else if (const double* dv = (const double*)device_view(t3c)) {
+      // device or mapped pinned host memory: one conversion pass reads it in place
+      rcc::launch_convert<float, double>(c->B("t3")->f(), dv, cnt, c->stream);
     } else {
-      // stage the FP64 values in rp3's storage (as doubles, chunked) and convert
+      // pageable host memory: stage the FP64 values in rp3's storage (chunked) and convert
       const i64 chunk = c->B("rp3")->bytes / 8;
       for (i64 off = 0; off < cnt; off += chunk) {
         const i64 len = std::min(chunk, cnt - off);
@@ -2680,6 +2703,9 @@ RCC_API int rccsdt_get_amplitudes(rccsdt_ctx* c, double* t1, double* t2, double*
     const i64 cnt = c->n3 * c->V3;
     if (!f) {
       if (dev_copy(t3c, c->D("t3"), (size_t)cnt * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+    } else if (double* dv = (double*)device_view(t3c)) {
+      // device or mapped pinned host memory: the conversion writes it in place
+      rcc::launch_convert<double, float>(dv, c->B("t3")->f(), cnt, c->stream);
     } else {
       const i64 chunk = c->B("Sz")->bytes / 8;
       double* stage = (double*)c->B("Sz")->p;  // FP64 staging through the unpack scratch

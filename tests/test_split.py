@@ -119,3 +119,35 @@ def test_grouped_launch_shapes_match_oracle(shape):
     assert np.abs(oc.postprocess(r3, o) - oc.postprocess(R3, o)).max() / scale < TOL[B.SPLIT_BF16X3]
     assert np.abs(r2 - R2).max() / scale < TOL[B.SPLIT_BF16X3]
     ctx.close()
+
+
+@pytest.mark.gpu
+def test_t3_round_trip_through_pinned_and_pageable_host_memory():
+    """An FP32-storage context reads and writes T3 in place when the caller's
+    buffer is pinned host memory (or device memory) and through staging copies
+    when it is pageable: all three give the same FP32-rounded amplitudes."""
+    torch = pytest.importorskip("torch")
+    lib = gpu_lib()
+    o, v, naux = 3, 10, 24
+    inst = make_instance(o, v, naux, seed=4)
+    t1, t2, t3 = random_amplitudes(o, v, seed=5)
+    t3c = np.ascontiguousarray(oc.pack(t3))
+    ctx = B.Context(lib, o, v, naux, precision=B.SPLIT_BF16X3)
+    ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    want = t3c.astype(np.float32).astype(np.float64)
+    outs = []
+    for kind in ("pageable", "pinned", "device"):
+        if kind == "pageable":
+            src, dst = t3c, np.zeros_like(t3c)
+        elif kind == "pinned":
+            src = torch.from_numpy(t3c.copy()).pin_memory()
+            dst = torch.zeros(t3c.shape, dtype=torch.float64).pin_memory()
+        else:
+            src = torch.from_numpy(t3c).cuda()
+            dst = torch.zeros(t3c.shape, dtype=torch.float64, device="cuda")
+        ctx.set_amplitudes(t1, t2, src)
+        ctx.get_amplitudes(None, None, dst)
+        got = dst if isinstance(dst, np.ndarray) else dst.cpu().numpy()
+        assert np.array_equal(got, want), kind
+        outs.append(got)
+    ctx.close()

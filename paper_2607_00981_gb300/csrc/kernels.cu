@@ -951,6 +951,40 @@ template void launch_slot_save<float>(char*, i64, i64, const int*, const float*,
 // Virtual subspace of compact T3 (the T3 part of the DIIS vectors restricted to the
 // first ns virtual orbitals, the lowest in energy): sub[blk][a][b][c] <-> t3[blk][a][b][c]
 // for a, b, c < ns.  dir 0 gathers t3 -> sub, dir 1 scatters sub -> t3.
+// Vector variant (FP32, ns and v multiples of 4): float4 units, four of them in flight
+// per thread, one division per unit.
+__global__ void k_subcube4(float* __restrict__ t3, float* __restrict__ sub, i64 n3, int v, int ns, int dir) {
+  const int q4 = ns / 4;
+  const i64 V3 = (i64)v * v * v, n4 = n3 * ns * ns * q4;
+  const i64 step = (i64)gridDim.x * blockDim.x;
+  for (i64 i0 = blockIdx.x * (i64)blockDim.x + threadIdx.x; i0 < n4; i0 += 4 * step) {
+    float4* fp[4];
+    float4* sp[4];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const i64 i = i0 + u * step;
+      ok[u] = i < n4;
+      const i64 row = ok[u] ? i / q4 : 0;
+      const int c4 = (int)(i - row * q4);
+      const i64 blk = row / ((i64)ns * ns);
+      const int ab = (int)(row - blk * ns * ns), a = ab / ns, b = ab - a * ns;
+      fp[u] = reinterpret_cast<float4*>(t3 + blk * V3 + ((i64)a * v + b) * v) + c4;
+      sp[u] = reinterpret_cast<float4*>(sub) + i;
+    }
+    float4 x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (ok[u]) x[u] = dir == 0 ? *fp[u] : *sp[u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (ok[u]) {
+        if (dir == 0) *sp[u] = x[u];
+        else *fp[u] = x[u];
+      }
+  }
+}
+
 template <typename T>
 __global__ void k_subcube(T* __restrict__ t3, T* __restrict__ sub, i64 n3, int v, int ns, int dir) {
   // rows (blk, a, b) of ns contiguous values in both layouts: no division per element
@@ -972,6 +1006,12 @@ void launch_subcube(T* t3, T* sub, i64 n3, int v, int ns, int dir, cudaStream_t 
   const i64 nrow = n3 * ns * ns;
   if (nrow <= 0) return;
   ++g_launch_count;
+  if (sizeof(T) == 4 && ns % 4 == 0 && v % 4 == 0) {
+    const i64 n4 = nrow * (ns / 4);
+    const i64 blocks = std::min<i64>((n4 + 1023) / 1024, (i64)152 * 16);
+    k_subcube4<<<(unsigned)blocks, 256, 0, s>>>((float*)t3, (float*)sub, n3, v, ns, dir);
+    return;
+  }
   const int threads = ns <= 64 ? 64 : 128;
   const i64 blocks = std::min<i64>(nrow, (i64)152 * 64);
   k_subcube<T><<<(unsigned)blocks, threads, 0, s>>>(t3, sub, n3, v, ns, dir);
@@ -1025,7 +1065,8 @@ __global__ void k_diis_dots(const char* __restrict__ hist_e, i64 stride, i64 off
 #pragma unroll
     for (int q = 0; q < 16; ++q) ss[q] = 0.0;
     if constexpr (sizeof(T) == 4) {
-      // runs of 16 terms per thread in FP32, added to FP64 (see dot_range)
+      // runs of 64 terms per thread in FP32, added to FP64 (only the m live sums: the
+      // FP64 units run at a small fraction of the FP32 rate on this part)
       float fs[16];
       int run = 0;
 #pragma unroll
@@ -1035,17 +1076,19 @@ __global__ void k_diis_dots(const char* __restrict__ hist_e, i64 stride, i64 off
 #pragma unroll
         for (int q = 0; q < 16; ++q)
           if (q < m) fs[q] = fmaf(x, ((const float*)(hist_e + (i64)q * stride + off))[i], fs[q]);
-        if (++run == 16) {
+        if (++run == 64) {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            ss[q] += (double)fs[q];
-            fs[q] = 0.f;
-          }
+          for (int q = 0; q < 16; ++q)
+            if (q < m) {
+              ss[q] += (double)fs[q];
+              fs[q] = 0.f;
+            }
           run = 0;
         }
       }
 #pragma unroll
-      for (int q = 0; q < 16; ++q) ss[q] += (double)fs[q];
+      for (int q = 0; q < 16; ++q)
+        if (q < m) ss[q] += (double)fs[q];
     } else {
       for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
         const double x = (double)es[i];
@@ -1070,7 +1113,7 @@ template <typename T>
 void launch_diis_dots(const char* hist_e, i64 stride, i64 off, const int* st, int M, i64 n, i64 seg, const double* w,
                       double* partial, cudaStream_t s) {
   ++g_launch_count;
-  k_diis_dots<T><<<kDotBlocks, 256, 0, s>>>(hist_e, stride, off, st, M, n, seg, w, partial);
+  k_diis_dots<T><<<kDotBlocks, 512, 0, s>>>(hist_e, stride, off, st, M, n, seg, w, partial);
 }
 template void launch_diis_dots<double>(const char*, i64, i64, const int*, int, i64, i64, const double*, double*,
                                        cudaStream_t);
@@ -1197,11 +1240,50 @@ __global__ void k_diis_extrapolate(T* __restrict__ out, const T* __restrict__ hi
   }
 }
 
+// FP32 vector variant (16-byte aligned history, stride and output): four elements per
+// access, the same double-float sum per element.
+__global__ void k_diis_extrapolate4(float4* __restrict__ out, const float4* __restrict__ hist, i64 stride4, i64 n4,
+                                    const double* __restrict__ coef, const int* __restrict__ st) {
+  if (!st[4]) return;
+  const int m = st[3];
+  float ch[16], cl[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const double cq = q < m ? coef[q] : 0.0;
+    ch[q] = (float)cq;
+    cl[q] = (float)(cq - (double)ch[q]);
+  }
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n4; i += (i64)gridDim.x * blockDim.x) {
+    float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      if (q >= m) break;
+      const float4 x4 = hist[q * stride4 + i];
+      const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float p = ch[q] * xs[j];
+        const float e = fmaf(ch[q], xs[j], -p);
+        const float t = sh[j] + p;
+        const float bp = t - sh[j];
+        sl[j] += ((sh[j] - (t - bp)) + (p - bp)) + fmaf(cl[q], xs[j], e);
+        sh[j] = t;
+      }
+    }
+    out[i] = make_float4(sh[0] + sl[0], sh[1] + sl[1], sh[2] + sl[2], sh[3] + sl[3]);
+  }
+}
+
 template <typename T>
 void launch_diis_extrapolate(T* out, const T* hist, i64 stride, i64 n, const double* coef, const int* st,
                              cudaStream_t s) {
   if (n <= 0) return;
   ++g_launch_count;
+  if (sizeof(T) == 4 && n % 4 == 0 && stride % 4 == 0 && ((uintptr_t)out & 15) == 0 && ((uintptr_t)hist & 15) == 0) {
+    const i64 n4 = n / 4;
+    k_diis_extrapolate4<<<ew_blocks(n4), 256, 0, s>>>((float4*)out, (const float4*)hist, stride / 4, n4, coef, st);
+    return;
+  }
   k_diis_extrapolate<T><<<ew_blocks(n), 256, 0, s>>>(out, hist, stride, n, coef, st);
 }
 template void launch_diis_extrapolate<double>(double*, const double*, i64, i64, const double*, const int*,

@@ -56,7 +56,6 @@ __constant__ unsigned char c_perm[24][4];
 // spin summation: t~(O, L) = sum_pi c_pi R(O o pi^-1, L) / eps; per pi the inverse map and c_pi
 __constant__ unsigned char c_pinv[24][4];
 __constant__ double c_coef[24];
-__constant__ float c_coef_f[24];  // the same in FP32 (FP32 arithmetic)
 
 __host__ __device__ __forceinline__ i64 tri3(i64 a, i64 b, i64 c) {  // colex a <= b <= c
   return c * (c + 1) * (c + 2) / 6 + b * (b + 1) / 2 + a;
@@ -255,10 +254,7 @@ __global__ void __launch_bounds__(kThreadsQ) k_q_main(const QArgs q) {
   // index times o^3) of the stored block sorted(e, L[x], L[y]); the rank of e in that
   // triple, which fixes the occupied order, follows from the range of e
   __shared__ i64 s_blk[6][kMaxVQ];
-  __shared__ float s_epsf[64 + kMaxVQ];  // FP32 arithmetic: the orbital energies in FP32
   const int o = q.o, v = q.v;
-  if constexpr (sizeof(T) == 4)
-    for (int t = threadIdx.x; t < o + v; t += blockDim.x) s_epsf[t] = (float)q.eps[t];
   const i64 O4 = (i64)o * o * o * o;
   T* R = q.smem_rz ? (T*)q_smem : (T*)q.scratch + (i64)blockIdx.x * 2 * O4;
   T* Z = R + O4;
@@ -335,26 +331,6 @@ __global__ void __launch_bounds__(kThreadsQ) k_q_main(const QArgs q) {
     // (b) f_abcd sum_O Z(O) t~(O), t~(O) = sum_pi c_pi R(O o pi^-1) / eps(O)
     const double ev = q.eps[o + L[0]] + q.eps[o + L[1]] + q.eps[o + L[2]] + q.eps[o + L[3]];
     double part = 0.0;
-    if constexpr (sizeof(T) == 4) {
-      // FP32 arithmetic: the spin sum, the denominator and this thread's share of the
-      // quadruple in FP32 (no per-element work on the FP64 units), one FP64 add per
-      // quadruple
-      const float evf = s_epsf[o + L[0]] + s_epsf[o + L[1]] + s_epsf[o + L[2]] + s_epsf[o + L[3]];
-      float pf = 0.f;
-      for (i64 el = threadIdx.x; el < O4; el += blockDim.x) {
-        const int Oc[4] = {(int)(el / o3), (int)((el / o2) % o), (int)((el / o) % o), (int)(el % o)};
-        float ts = 0.f;
-#pragma unroll 4
-        for (int pi = 0; pi < 24; ++pi) {
-          const i64 idx = (((i64)Oc[c_pinv[pi][0]] * o + Oc[c_pinv[pi][1]]) * o + Oc[c_pinv[pi][2]]) * o +
-                          Oc[c_pinv[pi][3]];
-          ts = fmaf(c_coef_f[pi], (float)R[idx], ts);
-        }
-        const float eo = s_epsf[Oc[0]] + s_epsf[Oc[1]] + s_epsf[Oc[2]] + s_epsf[Oc[3]];
-        pf += (float)Z[el] * ts / (eo - evf);
-      }
-      part = (double)pf;
-    } else
     for (i64 el = threadIdx.x; el < O4; el += blockDim.x) {
       const int Oc[4] = {(int)(el / o3), (int)((el / o2) % o), (int)((el / o) % o), (int)(el % o)};
       double ts = 0.0;
@@ -444,9 +420,6 @@ void init_tables() {
   cudaMemcpyToSymbol(c_perm, hp, sizeof(hp));
   cudaMemcpyToSymbol(c_pinv, hinv, sizeof(hinv));
   cudaMemcpyToSymbol(c_coef, coef, sizeof(coef));
-  float coef_f[24];
-  for (int i = 0; i < 24; ++i) coef_f[i] = (float)coef[i];
-  cudaMemcpyToSymbol(c_coef_f, coef_f, sizeof(coef_f));
   done = true;
 }
 

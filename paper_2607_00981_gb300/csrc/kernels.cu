@@ -1113,7 +1113,7 @@ template <typename T>
 void launch_diis_dots(const char* hist_e, i64 stride, i64 off, const int* st, int M, i64 n, i64 seg, const double* w,
                       double* partial, cudaStream_t s) {
   ++g_launch_count;
-  k_diis_dots<T><<<kDotBlocks, 512, 0, s>>>(hist_e, stride, off, st, M, n, seg, w, partial);
+  k_diis_dots<T><<<kDotBlocks, 256, 0, s>>>(hist_e, stride, off, st, M, n, seg, w, partial);
 }
 template void launch_diis_dots<double>(const char*, i64, i64, const int*, int, i64, i64, const double*, double*,
                                        cudaStream_t);

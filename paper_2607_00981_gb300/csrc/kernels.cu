@@ -819,7 +819,7 @@ __host__ __device__ inline Pieces make_pieces(i64 n, i64 seg, bool weighted, int
   const i64 cap = (q.seg + 2047) / 2048;
   if (per > cap) per = cap;
   q.P = (int)(per < 1 ? 1 : per);
-  q.len = (q.seg + q.P - 1) / q.P;
+  q.len = ((q.seg + q.P - 1) / q.P + 3) & ~(i64)3;  // a multiple of 4 (vector loads)
   return q;
 }
 
@@ -1061,45 +1061,67 @@ __global__ void k_diis_dots(const char* __restrict__ hist_e, i64 stride, i64 off
     i64 b1 = b0 + pc.len;
     const i64 send = sg * pc.seg + pc.seg < n ? sg * pc.seg + pc.seg : n;
     if (b1 > send) b1 = send;
-    double ss[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) ss[q] = 0.0;
+    const double wt = w ? w[sg] : 1.0;
     if constexpr (sizeof(T) == 4) {
-      // runs of 64 terms per thread in FP32, added to FP64 (only the m live sums: the
-      // FP64 units run at a small fraction of the FP32 rate on this part)
+      // runs of 64 terms per thread in FP32, each run added (weighted) to the FP64
+      // sums of the m live slots: the FP64 units run at a small fraction of the FP32
+      // rate on this part.  16-byte aligned data: four elements per load.
       float fs[16];
-      int run = 0;
 #pragma unroll
       for (int q = 0; q < 16; ++q) fs[q] = 0.f;
-      for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-        const float x = es[i];
+      auto flush = [&]() {
 #pragma unroll
         for (int q = 0; q < 16; ++q)
-          if (q < m) fs[q] = fmaf(x, ((const float*)(hist_e + (i64)q * stride + off))[i], fs[q]);
-        if (++run == 64) {
+          if (q < m) {
+            s[q] += wt * (double)fs[q];
+            fs[q] = 0.f;
+          }
+      };
+      const bool vec = (((uintptr_t)(hist_e + off)) & 15) == 0 && (stride & 15) == 0 && (b0 & 3) == 0 && (b1 & 3) == 0;
+      int run = 0;
+      if (vec) {
+        for (i64 i = b0 + 4 * (i64)threadIdx.x; i < b1; i += 4 * (i64)blockDim.x) {
+          const float4 x = *reinterpret_cast<const float4*>(es + i);
 #pragma unroll
           for (int q = 0; q < 16; ++q)
             if (q < m) {
-              ss[q] += (double)fs[q];
-              fs[q] = 0.f;
+              const float4 y = *reinterpret_cast<const float4*>((const float*)(hist_e + (i64)q * stride + off) + i);
+              fs[q] = fmaf(x.x, y.x, fs[q]);
+              fs[q] = fmaf(x.y, y.y, fs[q]);
+              fs[q] = fmaf(x.z, y.z, fs[q]);
+              fs[q] = fmaf(x.w, y.w, fs[q]);
             }
-          run = 0;
+          if (++run == 16) {
+            flush();
+            run = 0;
+          }
+        }
+      } else {
+        for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+          const float x = es[i];
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (q < m) fs[q] = fmaf(x, ((const float*)(hist_e + (i64)q * stride + off))[i], fs[q]);
+          if (++run == 64) {
+            flush();
+            run = 0;
+          }
         }
       }
-#pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (q < m) ss[q] += (double)fs[q];
+      flush();
     } else {
+      double ss[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) ss[q] = 0.0;
       for (i64 i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
         const double x = (double)es[i];
 #pragma unroll
         for (int q = 0; q < 16; ++q)
           if (q < m) ss[q] += x * (double)((const T*)(hist_e + (i64)q * stride + off))[i];
       }
-    }
-    const double wt = w ? w[sg] : 1.0;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) s[q] += wt * ss[q];
+      for (int q = 0; q < 16; ++q) s[q] += wt * ss[q];
+    }
   }
 #pragma unroll
   for (int q = 0; q < 16; ++q) {

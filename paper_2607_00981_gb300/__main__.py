@@ -17,6 +17,12 @@ With --refine-fp64 the converged amplitudes then seed an FP64 context (FP64
 storage, FP64 DIIS of --refine-diis vectors, contractions per --f64-tc) iterated to
 --tol again; its energy is the FP64 reference the split energy is compared with
 (converged energies do not depend on the path).
+
+    python -m paper_2607_00981_gb300 --t4 6,40 --precision bf16x3 --reps 2
+
+runs the compact-T4 engine instead: seeded pair-symmetric W and T4 at o, v, then
+--reps passes of the six-term ladder and the R4 post-processing, one JSON line per
+pass with the device ms of each and the norm of the post-processed R4.
 """
 import argparse
 import json
@@ -25,6 +31,35 @@ import time
 
 import paper_2607_00981_gb300 as pkg
 from paper_2607_00981_gb300.synth import CONVERGENCE, WORKLOADS, make_instance
+
+
+def t4_passes(args):
+    import numpy as np
+    import torch
+
+    from paper_2607_00981_gb300 import binding as B
+    from paper_2607_00981_gb300.synth import random_pair_symmetric
+    o, v = (int(x) for x in args.t4.split(","))
+    n4 = o * (o + 1) * (o + 2) * (o + 3) // 24
+    prec = {"fp64": B.FP64, "bf16x3": B.SPLIT_BF16X3, "tf32x3": B.SPLIT_TF32X3}[args.precision]
+    W = random_pair_symmetric(v, seed=40)
+    t4c = torch.from_numpy(0.05 * np.random.default_rng(6).standard_normal((n4, v, v, v, v))).cuda()
+    eng = B.T4Engine(pkg.load(), o, v, precision=prec)
+    eng.set(W, t4c)
+    for rep in range(args.reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        eng.pp_ladder()
+        ev[1].record()
+        norm = eng.postprocess()
+        ev[2].record()
+        torch.cuda.synchronize()
+        print(json.dumps({"t4": [o, v], "precision": args.precision, "pass": rep, "n4": n4,
+                          "ladder_ms": ev[0].elapsed_time(ev[1]), "post_ms": ev[1].elapsed_time(ev[2]),
+                          "r4_norm": norm}), flush=True)
+    eng.close()
+    return 0
 
 
 def main(argv=None):
@@ -56,7 +91,11 @@ def main(argv=None):
     ap.add_argument("--until-tol", action="store_true", help="with --iters: stop once |R| <= --tol")
     ap.add_argument("--q", default=None, choices=["fp64", "fp32"],
                     help="after the iterations (or the solve), the RCCSDT(Q) energy correction in this arithmetic")
+    ap.add_argument("--t4", default=None, help="o,v: time the compact-T4 ladder and post-processing instead")
+    ap.add_argument("--reps", type=int, default=2, help="with --t4: passes")
     args = ap.parse_args(argv)
+    if args.t4:
+        return t4_passes(args)
     spec = dict(WORKLOADS.get(args.workload) or CONVERGENCE[args.workload])
     if args.scale is not None:
         spec["scale"] = args.scale

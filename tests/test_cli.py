@@ -22,3 +22,18 @@ def test_iterations_checkpoint_and_resume(monkeypatch, capsys, tmp_path):
     assert cli.main(["--workload", "o3v12", "--iters", "4"]) == 0
     straight = [json.loads(x) for x in capsys.readouterr().out.splitlines()]
     assert resumed["energy"] == straight[3]["energy"] and resumed["r"] == straight[3]["r"]
+
+
+import pytest  # noqa: E402
+
+
+@pytest.mark.gpu
+def test_t4_passes_print_one_line_per_pass(capsys):
+    """--t4 o,v times the compact-T4 ladder and post-processing on the GPU; the norm of
+    the post-processed R4 is the same in every pass (same inputs, deterministic)."""
+    assert cli.main(["--t4", "2,12", "--precision", "bf16x3", "--reps", "2"]) == 0
+    lines = [json.loads(x) for x in capsys.readouterr().out.splitlines()]
+    assert [x["pass"] for x in lines] == [0, 1]
+    assert lines[0]["n4"] == 5 and lines[0]["r4_norm"] > 0
+    assert lines[0]["r4_norm"] == lines[1]["r4_norm"]
+    assert all(x["ladder_ms"] > 0 and x["post_ms"] > 0 for x in lines)

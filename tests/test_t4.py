@@ -56,3 +56,37 @@ def test_t4_errors():
         eng.pp_ladder()  # nothing set yet
     assert ei.value.status == B.ERR_STATE
     eng.close()
+
+
+@pytest.mark.gpu
+def test_t4_bench_shape_sampled_blocks_match_oracle():
+    """The bench's launch shape (o = 6, v = 40: 126 stored blocks in three block ranges
+    of the ladder's GEMMs) in 3xBF16, checked on one block of each range and on a
+    purified and a doubly-degenerate block: the ladder against the oracle's direct
+    traversal of those blocks (each reads only itself), the post-processing against
+    the oracle's rules applied to the GPU's own ladder output."""
+    o, v = 6, 40
+    n4 = Q.n4(o)
+    W = random_pair_symmetric(v, seed=40)
+    rng = np.random.default_rng(6)
+    t4c = 0.05 * rng.standard_normal((n4, v, v, v, v))  # any block values (no symmetry needed)
+    quads = Q.quads(o)
+    # purified (0000, 0001, 5555), i=j<k=l, all distinct, and blocks of all three ranges
+    sel = [0, 1, Q.blk4(0, 0, 1, 1), Q.blk4(0, 1, 2, 3), 60, 110, 125]
+    assert quads[1] == (0, 0, 0, 1) and quads[125] == (5, 5, 5, 5)
+    eng = B.T4Engine(gpu_lib(), o, v, precision=B.SPLIT_BF16X3)
+    eng.set(W, t4c)
+    eng.pp_ladder()
+    r4 = eng.r4()
+    R = Q.pp_ladder_compact(W, t4c[sel], o)
+    scale = max(1.0, np.abs(R).max())
+    assert np.abs(r4[sel] - R).max() / scale < TOL[B.SPLIT_BF16X3]
+    eng.postprocess()
+    p4 = eng.r4()
+    full = np.zeros_like(r4)
+    full[sel] = r4[sel]
+    sp = Q.purify4(Q.symmetrise4(full, o), o)
+    for b in sel:
+        ref = Q.orthogonalise4_block(sp[b])
+        assert np.abs(p4[b] - ref).max() / scale < 5e-6, (b, quads[b])  # 24-term FP32 sums
+    eng.close()

@@ -2862,6 +2862,8 @@ RCC_API int rccsdt_get_residuals(rccsdt_ctx* c, double* r1, double* r2, double* 
     const i64 cnt = c->n3 * c->V3;
     if (!f) {
       if (dev_copy(r3c, c->D("r3"), (size_t)cnt * 8, c->stream)) return fail(c, RCCSDT_ERR_CUDA, "copy");
+    } else if (double* dv = (double*)device_view(r3c)) {
+      rcc::launch_convert<double, float>(dv, c->B("r3")->f(), cnt, c->stream);  // converted in place
     } else {
       const i64 chunk = c->B("Sz")->bytes / 8;
       double* stage = (double*)c->B("Sz")->p;

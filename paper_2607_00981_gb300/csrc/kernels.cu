@@ -1727,10 +1727,10 @@ template void launch_scatter_rows3<double>(const float*, int, int, const i64*, c
 // 4-vector of W and a 4 x 4 patch of t2 from shared memory feed 64 FMAs).  Per term
 // and chunk of 8 values of l the W slice [l][a1] and the t2 slice [l][a2][a3] of the
 // tile are copied to shared memory with cp.async (zero-filled outside the block and
-// beyond o), two stages in flight.  The block is read and written once.
+// beyond o), three stages in flight.  The block is read and written once.
 // Wvooo[a][l][i][j] = W^{al}_{ij}; t2[l][k][b][c] = t_lk^bc (T precision copies).
 // ---------------------------------------------------------------------------
-constexpr int kT2oTL = 16, kT2oLC = 8, kT2oThreads = 64;
+constexpr int kT2oTL = 16, kT2oLC = 8, kT2oThreads = 64, kT2oStages = 3;
 
 template <typename T>
 struct T2oLayout {
@@ -1817,7 +1817,7 @@ __global__ void __launch_bounds__(kT2oThreads) k_t2_outer(T* __restrict__ r3, co
       const int lo0 = tile / (nt * nt) * TL, lo1 = (tile / nt) % nt * TL, lo2 = tile % nt * TL;
       auto lo = [&](int x) { return x == 0 ? lo0 : (x == 1 ? lo1 : lo2); };
       auto issue = [&](int st) {
-        T* Wb = sm + (st & 1) * Lay::STAGE;
+        T* Wb = sm + (st % kT2oStages) * Lay::STAGE;
         T* Tb = Wb + Lay::WS;
         const int q = st / nch, l0 = (st % nch) * LC, lc = min(LC, o - l0);
         const int x1 = perm3(q, 0), x2 = perm3(q, 1), x3 = perm3(q, 2);
@@ -1855,17 +1855,18 @@ __global__ void __launch_bounds__(kT2oThreads) k_t2_outer(T* __restrict__ r3, co
 #pragma unroll
           for (int z = 0; z < 4; ++z) acc[x][y][z] = (T)0;
       __syncthreads();  // the previous tile's last stage is consumed
-      issue(0);
+      for (int st = 0; st < kT2oStages - 1; ++st) {
+        if (st < nstage) issue(st);
+        else asm volatile("cp.async.commit_group;" ::: "memory");  // an empty group keeps the count
+      }
 #pragma unroll 1
       for (int st = 0; st < nstage; ++st) {
-        if (st + 1 < nstage) {
-          issue(st + 1);  // its buffer's last reader was stage st - 1
-          asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-          asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
+        // the stage kT2oStages - 1 ahead; its buffer's last reader was stage st - 1
+        if (st + kT2oStages - 1 < nstage) issue(st + kT2oStages - 1);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(kT2oStages - 1) : "memory");  // stage st has landed
         __syncthreads();
-        const T* Wb = sm + (st & 1) * Lay::STAGE;
+        const T* Wb = sm + (st % kT2oStages) * Lay::STAGE;
         const T* Tb = Wb + Lay::WS;
         const int q = st / nch, lc = min(LC, o - (st % nch) * LC);
         switch (perm3(q, 0) * 3 + perm3(q, 1)) {
@@ -1908,7 +1909,7 @@ void launch_t2_outer(T* r3, const T* Wvooo, const T* t2, const int4* blocks, int
   const int nt = (v + kT2oTL - 1) / kT2oTL;
   const unsigned gx = (unsigned)std::min(nt * nt * nt, 65535);
   const unsigned gy = (unsigned)std::min<i64>(n3, 65535);
-  const size_t smem = (size_t)2 * T2oLayout<T>::STAGE * sizeof(T);
+  const size_t smem = (size_t)kT2oStages * T2oLayout<T>::STAGE * sizeof(T);
   const bool vec = v % T2oLayout<T>::EPC == 0;
   static bool attr = false;
   if (!attr) {

@@ -1319,52 +1319,9 @@ __global__ void k_convert(TO* __restrict__ out, const TI* __restrict__ in, i64 n
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     out[i] = (TO)in[i];
 }
-// Vector variants (16-byte aligned, n a multiple of 4): four elements per thread and
-// step, two steps in flight, so that reads and writes over the host link (pinned host
-// buffers converted in place) move whole 16- and 32-byte pieces.
-__global__ void k_convert_d2f4(float4* __restrict__ out, const double2* __restrict__ in, i64 n4) {
-  const i64 stride = (i64)gridDim.x * blockDim.x;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n4; i += 2 * stride) {
-    const bool two = i + stride < n4;
-    const double2 a = in[2 * i], b = in[2 * i + 1];
-    double2 c = make_double2(0.0, 0.0), d = make_double2(0.0, 0.0);
-    if (two) {
-      c = in[2 * (i + stride)];
-      d = in[2 * (i + stride) + 1];
-    }
-    out[i] = make_float4(f64_to_f32_rn(a.x), f64_to_f32_rn(a.y), f64_to_f32_rn(b.x), f64_to_f32_rn(b.y));
-    if (two)
-      out[i + stride] = make_float4(f64_to_f32_rn(c.x), f64_to_f32_rn(c.y), f64_to_f32_rn(d.x), f64_to_f32_rn(d.y));
-  }
-}
-__global__ void k_convert_f2d4(double2* __restrict__ out, const float4* __restrict__ in, i64 n4) {
-  const i64 stride = (i64)gridDim.x * blockDim.x;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n4; i += 2 * stride) {
-    const bool two = i + stride < n4;
-    const float4 a = in[i];
-    const float4 b = two ? in[i + stride] : make_float4(0.f, 0.f, 0.f, 0.f);
-    out[2 * i] = make_double2((double)a.x, (double)a.y);
-    out[2 * i + 1] = make_double2((double)a.z, (double)a.w);
-    if (two) {
-      out[2 * (i + stride)] = make_double2((double)b.x, (double)b.y);
-      out[2 * (i + stride) + 1] = make_double2((double)b.z, (double)b.w);
-    }
-  }
-}
-
 template <typename TO, typename TI>
 void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t s) {
   if (n <= 0) return;
-  if (sizeof(TO) != sizeof(TI) && n % 4 == 0 && ((uintptr_t)out & 15) == 0 && ((uintptr_t)in & 15) == 0) {
-    const i64 n4 = n / 4;
-    const i64 blocks = std::min<i64>((n4 + 511) / 512, 152 * 16);
-    ++g_launch_count;
-    if (sizeof(TO) == 4)
-      k_convert_d2f4<<<(unsigned)blocks, 256, 0, s>>>((float4*)out, (const double2*)in, n4);
-    else
-      k_convert_f2d4<<<(unsigned)blocks, 256, 0, s>>>((double2*)out, (const float4*)in, n4);
-    return;
-  }
   i64 blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   ++g_launch_count;

@@ -1727,10 +1727,11 @@ template void launch_scatter_rows3<double>(const float*, int, int, const i64*, c
 // 4-vector of W and a 4 x 4 patch of t2 from shared memory feed 64 FMAs).  Per term
 // and chunk of 8 values of l the W slice [l][a1] and the t2 slice [l][a2][a3] of the
 // tile are copied to shared memory with cp.async (zero-filled outside the block and
-// beyond o), three stages in flight.  The block is read and written once.
+// beyond o), two stages in flight (three measured slower: fewer CTAs per SM).  The
+// block is read and written once.
 // Wvooo[a][l][i][j] = W^{al}_{ij}; t2[l][k][b][c] = t_lk^bc (T precision copies).
 // ---------------------------------------------------------------------------
-constexpr int kT2oTL = 16, kT2oLC = 8, kT2oThreads = 64, kT2oStages = 3;
+constexpr int kT2oTL = 16, kT2oLC = 8, kT2oThreads = 64, kT2oStages = 2;
 
 template <typename T>
 struct T2oLayout {

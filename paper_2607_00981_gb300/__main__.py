@@ -23,6 +23,12 @@ storage, FP64 DIIS of --refine-diis vectors, contractions per --f64-tc) iterated
 runs the compact-T4 engine instead: seeded pair-symmetric W and T4 at o, v, then
 --reps passes of the six-term ladder and the R4 post-processing, one JSON line per
 pass with the device ms of each and the norm of the post-processed R4.
+
+    python -m paper_2607_00981_gb300 --batch 6,40,64 --iters 4 --precision bf16x3
+
+iterates a batch of n identical instances (o, v, naux = 4 (o + v), weak coupling) in
+one CUDA graph launch per batch iteration for --iters batch iterations from the MP2
+guess and prints the device ms of every launch.
 """
 import argparse
 import json
@@ -62,6 +68,25 @@ def t4_passes(args):
     return 0
 
 
+def batch_launches(args):
+    from paper_2607_00981_gb300 import binding as B
+    o, v, n = (int(x) for x in args.batch.split(","))
+    naux = 4 * (o + v)
+    inst = make_instance(o, v, naux, seed=7, scale=0.6 * 0.3 * (40 / naux) ** 0.5)
+    prec = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}[args.precision]
+    b = B.Batch(pkg.load(), [(o, v, naux)] * n, precision=prec, tol=args.tol, max_iter=args.iters, autotune=0,
+                f64_tc=args.f64_tc)
+    for c in b.instances:
+        c.set_hamiltonian(inst.fock_diag, inst.L)
+        c.init_mp2()
+    b.solve()
+    print(json.dumps({"batch": [o, v, n], "precision": args.precision,
+                      "launch_ms": [float(x) for x in b.launch_times()],
+                      "kernels": float(b.stats()["kernels"])}), flush=True)
+    b.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2607_00981_gb300")
     ap.add_argument("--workload", default="o3v12", choices=sorted(WORKLOADS) + sorted(CONVERGENCE))
@@ -93,9 +118,12 @@ def main(argv=None):
                     help="after the iterations (or the solve), the RCCSDT(Q) energy correction in this arithmetic")
     ap.add_argument("--t4", default=None, help="o,v: time the compact-T4 ladder and post-processing instead")
     ap.add_argument("--reps", type=int, default=2, help="with --t4: passes")
+    ap.add_argument("--batch", default=None, help="o,v,n: n identical instances in one batch instead")
     args = ap.parse_args(argv)
     if args.t4:
         return t4_passes(args)
+    if args.batch:
+        return batch_launches(args)
     spec = dict(WORKLOADS.get(args.workload) or CONVERGENCE[args.workload])
     if args.scale is not None:
         spec["scale"] = args.scale

@@ -37,3 +37,11 @@ def test_t4_passes_print_one_line_per_pass(capsys):
     assert lines[0]["n4"] == 5 and lines[0]["r4_norm"] > 0
     assert lines[0]["r4_norm"] == lines[1]["r4_norm"]
     assert all(x["ladder_ms"] > 0 and x["post_ms"] > 0 for x in lines)
+
+
+@pytest.mark.gpu
+def test_batch_launches_one_line(capsys):
+    """--batch o,v,n runs n identical instances in one graph and prints its launch times."""
+    assert cli.main(["--batch", "3,12,4", "--iters", "2", "--precision", "bf16x3"]) == 0
+    line = json.loads(capsys.readouterr().out.splitlines()[-1])
+    assert line["batch"] == [3, 12, 4] and len(line["launch_ms"]) == 2 and line["kernels"] > 0

@@ -348,6 +348,201 @@ __global__ void __launch_bounds__(kThreadsQ) k_q_main(const QArgs q) {
   if (threadIdx.x == 0) q.partial[blockIdx.x] = total;
 }
 
+// Operand-staged variant of k_q_main (o <= 16, everything in shared memory).  Per joint
+// permutation sigma the four sums of phase (a) are small products: with the labels
+// (p, q, r, s) = sigma(L) fixed, a thread owns an occupied triple (i, k, l) and forms
+// the sums for all o values of j at once, so that each gathered T3 / t2 value feeds o
+// FMAs; the W / integral slices of this sigma, which every thread reads, are staged in
+// shared memory first ([e][j], [k][e][j], [i][m][j], [i][k][m][j], [i][j]: j innermost).
+// Each sum is written into R / Z at the occupied tuple O with O[c_x] = (i, j, k, l)_x.
+// Phase (b) is the same as in k_q_main.
+constexpr int kMaxOQ = 16;
+
+struct QStage {  // element offsets of the staged slices in the dynamic shared memory
+  int a1, w1, a2, w2, vs, w2_staged;
+  i64 total;  // elements (R, Z and the slices)
+};
+
+__host__ __device__ inline i64 q_pad4(i64 x) { return (x + 3) & ~(i64)3; }
+
+__host__ __device__ inline QStage q_stage_layout(int o, int v) {
+  const i64 o2 = (i64)o * o, o4 = o2 * o2;
+  QStage L;
+  i64 off = 2 * q_pad4(o4);
+  L.a1 = (int)off;
+  off += q_pad4((i64)v * o);
+  L.w1 = (int)off;
+  off += q_pad4((i64)o * v * o);
+  L.a2 = (int)off;
+  off += q_pad4(o2 * o);
+  L.w2_staged = o4 <= 4096;
+  L.w2 = (int)off;
+  off += L.w2_staged ? q_pad4(o4) : 0;
+  L.vs = (int)off;
+  off += q_pad4(o2);
+  L.total = off;
+  return L;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsQ) k_q_main_staged(const QArgs q) {
+  extern __shared__ __align__(16) unsigned char q_smem[];
+  __shared__ double ws[32];
+  __shared__ i64 s_blk[6][kMaxVQ];
+  const int o = q.o, v = q.v;
+  const i64 o2 = (i64)o * o, o3 = o2 * o, O4 = o2 * o2;
+  const QStage lay = q_stage_layout(o, v);
+  T* sm = (T*)q_smem;
+  T* R = sm;
+  T* Z = sm + q_pad4(O4);
+  T* A1s = sm + lay.a1;
+  T* W1s = sm + lay.w1;
+  T* A2s = sm + lay.a2;
+  T* W2s = sm + lay.w2;
+  T* Vs = sm + lay.vs;
+  const T* t3v = (const T*)q.t3v;
+  const T* A1 = (const T*)q.A1;
+  const T* A2 = (const T*)q.A2;
+  const T* Vv = (const T*)q.Vv;
+  const T* W1 = (const T*)q.W1;
+  const T* W2 = (const T*)q.W2;
+  const T* T2e = (const T*)q.T2e;
+  const T* T2m = (const T*)q.T2m;
+  const T* T2v = (const T*)q.T2v;
+  double total = 0.0;
+  for (i64 qi = blockIdx.x; qi < q.nquad; qi += gridDim.x) {
+    const int4 L4 = q.quads[qi];
+    const int L[4] = {L4.x & 0xffff, L4.x >> 16, L4.y & 0xffff, L4.y >> 16};
+    const double fac = (double)L4.z;
+    __syncthreads();  // the previous quadruple's tables and R, Z are consumed
+    for (int t = threadIdx.x; t < 6 * v; t += blockDim.x) {
+      const int pi = t / v, e = t % v;
+      const int x = pi < 3 ? 0 : (pi < 5 ? 1 : 2), y = pi < 3 ? pi + 1 : (pi < 5 ? pi - 1 : 3);
+      const int r0 = L[x], s0 = L[y];
+      const i64 b = e <= r0 ? tri3(e, r0, s0) : (e <= s0 ? tri3(r0, e, s0) : tri3(r0, s0, e));
+      s_blk[pi][e] = b * o3;
+    }
+    for (i64 t = threadIdx.x; t < 2 * q_pad4(O4); t += blockDim.x) R[t] = (T)0;  // R and Z
+    for (int sg = 0; sg < 24; ++sg) {
+      const int c0 = c_perm[sg][0], c1 = c_perm[sg][1], c2 = c_perm[sg][2], c3 = c_perm[sg][3];
+      const int p = L[c0], qq = L[c1], r = L[c2], s = L[c3];
+      __syncthreads();  // the previous sigma's slices are consumed (and R, Z, s_blk are set)
+      for (i64 t = threadIdx.x; t < (i64)o * v; t += blockDim.x) {  // A1s[e][j] = v^{pq}_{ej}
+        const int j = (int)(t / v), e = (int)(t % v);
+        A1s[e * o + j] = A1[(((i64)p * v + qq) * o + j) * v + e];
+      }
+      for (i64 t = threadIdx.x; t < o2 * v; t += blockDim.x) {  // W1s[k][e][j] = Wbar^{pqr}_{ejk}
+        const int j = (int)(t / ((i64)o * v)), k = (int)((t / v) % o), e = (int)(t % v);
+        W1s[((i64)k * v + e) * o + j] = W1[((((i64)p * v + qq) * v + r) * o2 + (i64)j * o + k) * v + e];
+      }
+      for (i64 t = threadIdx.x; t < o3; t += blockDim.x) {  // A2s[i][m][j] = v^{pm}_{ij}
+        const int i = (int)(t / o2), j = (int)((t / o) % o), m = (int)(t % o);
+        A2s[((i64)i * o + m) * o + j] = A2[(((i64)p * o + i) * o + j) * o + m];
+      }
+      if (lay.w2_staged)
+        for (i64 t = threadIdx.x; t < O4; t += blockDim.x) {  // W2s[i][k][m][j] = Wbar^{pqm}_{ijk}
+          const int i = (int)(t / o3), j = (int)((t / o2) % o), k = (int)((t / o) % o), m = (int)(t % o);
+          W2s[(((i64)i * o + k) * o + m) * o + j] = W2[((((i64)p * v + qq) * o + i) * o2 + (i64)j * o + k) * o + m];
+        }
+      for (i64 t = threadIdx.x; t < o2; t += blockDim.x)  // Vs[i][j] = v^{pq}_{ij}
+        Vs[t] = Vv[(((i64)p * v + qq) * o) * o + t];
+      __syncthreads();
+      // weights of the permuted occupied positions in R's index
+      const int w[4] = {(int)(c0 == 0 ? o3 : c0 == 1 ? o2 : c0 == 2 ? o : 1),
+                        (int)(c1 == 0 ? o3 : c1 == 1 ? o2 : c1 == 2 ? o : 1),
+                        (int)(c2 == 0 ? o3 : c2 == 1 ? o2 : c2 == 2 ? o : 1),
+                        (int)(c3 == 0 ? o3 : c3 == 1 ? o2 : c3 == 2 ? o : 1)};
+      const bool rs = c2 < c3;
+      const i64* bt = s_blk[pair_index(rs ? c2 : c3, rs ? c3 : c2)];
+      const int r0 = rs ? r : s, s0 = rs ? s : r;
+      for (i64 t = threadIdx.x; t < o3; t += blockDim.x) {
+        const int i = (int)(t / o2), k = (int)((t / o) % o), l = (int)(t % o);
+        T ax[kMaxOQ], ay[kMaxOQ];  // per j: x1 - x2 and y1 - y2
+#pragma unroll
+        for (int j = 0; j < kMaxOQ; ++j) ax[j] = ay[j] = (T)0;
+        {  // x1 = sum_e v^{pq}_{ej} t^{ers}_{ikl}
+          const int k0 = rs ? k : l, l0 = rs ? l : k;
+          const i64 f0 = ((i64)i * o + k0) * o + l0, f1 = ((i64)k0 * o + i) * o + l0, f2 = ((i64)k0 * o + l0) * o + i;
+          for (int e = 0; e < v; ++e) {
+            const i64 f = e <= r0 ? f0 : (e <= s0 ? f1 : f2);
+            const T tv = t3v[bt[e] + f];
+            const T* a = A1s + e * o;
+#pragma unroll
+            for (int j = 0; j < kMaxOQ; ++j)
+              if (j < o) ax[j] += a[j] * tv;
+          }
+        }
+        {  // x2 = sum_m v^{pm}_{ij} t^{qrs}_{mkl}
+          const i64 b0 = t3v_off(qq, r, s, 0, k, l, o), bm = t3v_off(qq, r, s, 1, k, l, o) - b0;
+          for (int m = 0; m < o; ++m) {
+            const T tv = t3v[b0 + m * bm];
+            const T* a = A2s + ((i64)i * o + m) * o;
+#pragma unroll
+            for (int j = 0; j < kMaxOQ; ++j)
+              if (j < o) ax[j] -= a[j] * tv;
+          }
+        }
+        {  // y1 = sum_e Wbar^{pqr}_{ejk} t^{es}_{il}
+          const T* t2e = T2e + (((i64)i * o + l) * v + s) * v;
+          const T* wk = W1s + (i64)k * v * o;
+          for (int e = 0; e < v; ++e) {
+            const T tv = t2e[e];
+            const T* a = wk + e * o;
+#pragma unroll
+            for (int j = 0; j < kMaxOQ; ++j)
+              if (j < o) ay[j] += a[j] * tv;
+          }
+        }
+        {  // y2 = sum_m Wbar^{pqm}_{ijk} t^{rs}_{ml}
+          const T* t2m = T2m + (((i64)l * v + r) * v + s) * o;
+          for (int m = 0; m < o; ++m) {
+            const T tv = t2m[m];
+            if (lay.w2_staged) {
+              const T* a = W2s + (((i64)i * o + k) * o + m) * o;
+#pragma unroll
+              for (int j = 0; j < kMaxOQ; ++j)
+                if (j < o) ay[j] -= a[j] * tv;
+            } else {
+#pragma unroll
+              for (int j = 0; j < kMaxOQ; ++j)
+                if (j < o) ay[j] -= W2[((((i64)p * v + qq) * o + i) * o2 + (i64)j * o + k) * o + m] * tv;
+            }
+          }
+        }
+        // V: 1/4 v^{pq}_{ij} t^{rs}_{kl}; then R += X + Y, Z += X + V with X = (x1 - x2) / 2
+        const T t2v = T2v[(((i64)k * o + l) * v + r) * v + s];
+        const i64 base = (i64)i * w[0] + (i64)k * w[2] + (i64)l * w[3];
+#pragma unroll
+        for (int j = 0; j < kMaxOQ; ++j)
+          if (j < o) {
+            const i64 el = base + (i64)j * w[1];
+            const T X = (T)0.5 * ax[j];
+            R[el] += X + (T)0.5 * ay[j];
+            Z[el] += X + (T)0.25 * Vs[i * o + j] * t2v;
+          }
+      }
+    }
+    __syncthreads();
+    // (b) f_abcd sum_O Z(O) t~(O), t~(O) = sum_pi c_pi R(O o pi^-1) / eps(O)
+    const double ev = q.eps[o + L[0]] + q.eps[o + L[1]] + q.eps[o + L[2]] + q.eps[o + L[3]];
+    double part = 0.0;
+    for (i64 el = threadIdx.x; el < O4; el += blockDim.x) {
+      const int Oc[4] = {(int)(el / o3), (int)((el / o2) % o), (int)((el / o) % o), (int)(el % o)};
+      double ts = 0.0;
+      for (int pi = 0; pi < 24; ++pi) {
+        const i64 idx = (((i64)Oc[c_pinv[pi][0]] * o + Oc[c_pinv[pi][1]]) * o + Oc[c_pinv[pi][2]]) * o +
+                        Oc[c_pinv[pi][3]];
+        ts += c_coef[pi] * (double)R[idx];
+      }
+      const double eo = q.eps[Oc[0]] + q.eps[Oc[1]] + q.eps[Oc[2]] + q.eps[Oc[3]];
+      part += (double)Z[el] * ts / (eo - ev);
+    }
+    const double bs = block_sum_q(part, ws);
+    if (threadIdx.x == 0) total += fac * bs;
+  }
+  if (threadIdx.x == 0) q.partial[blockIdx.x] = total;
+}
+
 __global__ void k_q_reduce(const double* __restrict__ partial, int n, double* __restrict__ out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double s = 0.0;
@@ -467,8 +662,12 @@ int q_energy(rccsdt_ctx* ctx, const rcc::QInputs& in, double* e_q, double* info)
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const bool in_smem = rz_bytes + 1024 <= (size_t)std::min(smem_optin, 200 * 1024);
-  // resident CTAs per SM: the dynamic R and Z plus the static tables (about 13 KB)
-  const int per_sm = in_smem ? std::max(1, std::min(4, (int)((224 * 1024) / (rz_bytes + 14 * 1024)))) : 4;
+  // the operand-staged kernel when o <= 16 and R, Z and the slices fit shared memory
+  const size_t staged_bytes = (size_t)q_stage_layout(o, v).total * es;
+  const bool staged = o <= kMaxOQ && staged_bytes + 1024 <= (size_t)std::min(smem_optin, 200 * 1024);
+  // resident CTAs per SM: the dynamic shared memory plus the static tables (about 13 KB)
+  const size_t dyn = staged ? staged_bytes : rz_bytes;
+  const int per_sm = (staged || in_smem) ? std::max(1, std::min(4, (int)((224 * 1024) / (dyn + 14 * 1024)))) : 4;
   const int grid = (int)std::max<i64>(1, std::min<i64>(nquad, (i64)nsm * per_sm));
 
   DevBuf G, t3v, A1, A2, Vv, W1, W2, T2e, T2m, T2v, vtr, qd, scratch, partial, outd;
@@ -518,9 +717,15 @@ int q_energy(rccsdt_ctx* ctx, const rcc::QInputs& in, double* e_q, double* info)
   qa.smem_rz = in_smem ? 1 : 0;
   qa.partial = (double*)partial.p;
   const int smem = in_smem ? (int)rz_bytes : 0;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_q_main<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   ++rcc::g_launch_count;
-  k_q_main<T><<<grid, kThreadsQ, smem, s>>>(qa);
+  if (staged) {
+    if (staged_bytes > 48 * 1024)
+      cudaFuncSetAttribute(k_q_main_staged<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged_bytes);
+    k_q_main_staged<T><<<grid, kThreadsQ, staged_bytes, s>>>(qa);
+  } else {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_q_main<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_q_main<T><<<grid, kThreadsQ, smem, s>>>(qa);
+  }
   cudaEventRecord(ev[3], s);
   ++rcc::g_launch_count;
   k_q_reduce<<<1, 32, 0, s>>>((const double*)partial.p, grid, (double*)outd.p);

@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kThreadsQ) k_q_main(const QArgs q) {
   if (threadIdx.x == 0) q.partial[blockIdx.x] = total;
 }
 
-// Operand-staged variant of k_q_main (o <= 16, everything in shared memory).  Per joint
+// Operand-staged variant of k_q_main (FP32, o <= 16, everything in shared memory).  Per joint
 // permutation sigma the four sums of phase (a) are small products: with the labels
 // (p, q, r, s) = sigma(L) fixed, a thread owns an occupied triple (i, k, l) and forms
 // the sums for all o values of j at once, so that each gathered T3 / t2 value feeds o
@@ -385,7 +385,7 @@ __host__ __device__ inline QStage q_stage_layout(int o, int v) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreadsQ) k_q_main_staged(const QArgs q) {
+__global__ void __launch_bounds__(kThreadsQ, 2) k_q_main_staged(const QArgs q) {
   extern __shared__ __align__(16) unsigned char q_smem[];
   __shared__ double ws[32];
   __shared__ i64 s_blk[6][kMaxVQ];
@@ -463,13 +463,21 @@ __global__ void __launch_bounds__(kThreadsQ) k_q_main_staged(const QArgs q) {
         {  // x1 = sum_e v^{pq}_{ej} t^{ers}_{ikl}
           const int k0 = rs ? k : l, l0 = rs ? l : k;
           const i64 f0 = ((i64)i * o + k0) * o + l0, f1 = ((i64)k0 * o + i) * o + l0, f2 = ((i64)k0 * o + l0) * o + i;
-          for (int e = 0; e < v; ++e) {
-            const i64 f = e <= r0 ? f0 : (e <= s0 ? f1 : f2);
-            const T tv = t3v[bt[e] + f];
-            const T* a = A1s + e * o;
+          for (int e0 = 0; e0 < v; e0 += 8) {  // eight gathers in flight, then their FMAs
+            T tv[8];
 #pragma unroll
-            for (int j = 0; j < kMaxOQ; ++j)
-              if (j < o) ax[j] += a[j] * tv;
+            for (int u = 0; u < 8; ++u) {
+              const int e = e0 + u;
+              tv[u] = e < v ? t3v[bt[e] + (e <= r0 ? f0 : (e <= s0 ? f1 : f2))] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              if (e0 + u >= v) break;
+              const T* a = A1s + (e0 + u) * o;
+#pragma unroll
+              for (int j = 0; j < kMaxOQ; ++j)
+                if (j < o) ax[j] += a[j] * tv[u];
+            }
           }
         }
         {  // x2 = sum_m v^{pm}_{ij} t^{qrs}_{mkl}
@@ -485,12 +493,18 @@ __global__ void __launch_bounds__(kThreadsQ) k_q_main_staged(const QArgs q) {
         {  // y1 = sum_e Wbar^{pqr}_{ejk} t^{es}_{il}
           const T* t2e = T2e + (((i64)i * o + l) * v + s) * v;
           const T* wk = W1s + (i64)k * v * o;
-          for (int e = 0; e < v; ++e) {
-            const T tv = t2e[e];
-            const T* a = wk + e * o;
+          for (int e0 = 0; e0 < v; e0 += 8) {
+            T tv[8];
 #pragma unroll
-            for (int j = 0; j < kMaxOQ; ++j)
-              if (j < o) ay[j] += a[j] * tv;
+            for (int u = 0; u < 8; ++u) tv[u] = e0 + u < v ? t2e[e0 + u] : (T)0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              if (e0 + u >= v) break;
+              const T* a = wk + (e0 + u) * o;
+#pragma unroll
+              for (int j = 0; j < kMaxOQ; ++j)
+                if (j < o) ay[j] += a[j] * tv[u];
+            }
           }
         }
         {  // y2 = sum_m Wbar^{pqm}_{ijk} t^{rs}_{ml}
@@ -664,7 +678,9 @@ int q_energy(rccsdt_ctx* ctx, const rcc::QInputs& in, double* e_q, double* info)
   const bool in_smem = rz_bytes + 1024 <= (size_t)std::min(smem_optin, 200 * 1024);
   // the operand-staged kernel when o <= 16 and R, Z and the slices fit shared memory
   const size_t staged_bytes = (size_t)q_stage_layout(o, v).total * es;
-  const bool staged = o <= kMaxOQ && staged_bytes + 1024 <= (size_t)std::min(smem_optin, 200 * 1024);
+  // (FP32 only: in FP64 the sums are bound by the FP64 units either way, and the
+  // per-j accumulators of the staged form cost the FP64 kernel its occupancy)
+  const bool staged = sizeof(T) == 4 && o <= kMaxOQ && staged_bytes + 1024 <= (size_t)std::min(smem_optin, 200 * 1024);
   // resident CTAs per SM: the dynamic shared memory plus the static tables (about 13 KB)
   const size_t dyn = staged ? staged_bytes : rz_bytes;
   const int per_sm = (staged || in_smem) ? std::max(1, std::min(4, (int)((224 * 1024) / (dyn + 14 * 1024)))) : 4;

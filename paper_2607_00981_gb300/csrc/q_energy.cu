@@ -384,7 +384,7 @@ __host__ __device__ inline QStage q_stage_layout(int o, int v) {
   return L;
 }
 
-template <typename T>
+template <typename T, int JM>  // JM >= o: the per-j accumulators and loops (o rounded up to 4)
 __global__ void __launch_bounds__(kThreadsQ, 2) k_q_main_staged(const QArgs q) {
   extern __shared__ __align__(16) unsigned char q_smem[];
   __shared__ double ws[32];
@@ -457,9 +457,9 @@ __global__ void __launch_bounds__(kThreadsQ, 2) k_q_main_staged(const QArgs q) {
       const int r0 = rs ? r : s, s0 = rs ? s : r;
       for (i64 t = threadIdx.x; t < o3; t += blockDim.x) {
         const int i = (int)(t / o2), k = (int)((t / o) % o), l = (int)(t % o);
-        T ax[kMaxOQ], ay[kMaxOQ];  // per j: x1 - x2 and y1 - y2
+        T ax[JM], ay[JM];  // per j: x1 - x2 and y1 - y2
 #pragma unroll
-        for (int j = 0; j < kMaxOQ; ++j) ax[j] = ay[j] = (T)0;
+        for (int j = 0; j < JM; ++j) ax[j] = ay[j] = (T)0;
         {  // x1 = sum_e v^{pq}_{ej} t^{ers}_{ikl}
           const int k0 = rs ? k : l, l0 = rs ? l : k;
           const i64 f0 = ((i64)i * o + k0) * o + l0, f1 = ((i64)k0 * o + i) * o + l0, f2 = ((i64)k0 * o + l0) * o + i;
@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(kThreadsQ, 2) k_q_main_staged(const QArgs q) {
               if (e0 + u >= v) break;
               const T* a = A1s + (e0 + u) * o;
 #pragma unroll
-              for (int j = 0; j < kMaxOQ; ++j)
+              for (int j = 0; j < JM; ++j)
                 if (j < o) ax[j] += a[j] * tv[u];
             }
           }
@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(kThreadsQ, 2) k_q_main_staged(const QArgs q) {
             const T tv = t3v[b0 + m * bm];
             const T* a = A2s + ((i64)i * o + m) * o;
 #pragma unroll
-            for (int j = 0; j < kMaxOQ; ++j)
+            for (int j = 0; j < JM; ++j)
               if (j < o) ax[j] -= a[j] * tv;
           }
         }
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(kThreadsQ, 2) k_q_main_staged(const QArgs q) {
               if (e0 + u >= v) break;
               const T* a = wk + (e0 + u) * o;
 #pragma unroll
-              for (int j = 0; j < kMaxOQ; ++j)
+              for (int j = 0; j < JM; ++j)
                 if (j < o) ay[j] += a[j] * tv[u];
             }
           }
@@ -514,11 +514,11 @@ __global__ void __launch_bounds__(kThreadsQ, 2) k_q_main_staged(const QArgs q) {
             if (lay.w2_staged) {
               const T* a = W2s + (((i64)i * o + k) * o + m) * o;
 #pragma unroll
-              for (int j = 0; j < kMaxOQ; ++j)
+              for (int j = 0; j < JM; ++j)
                 if (j < o) ay[j] -= a[j] * tv;
             } else {
 #pragma unroll
-              for (int j = 0; j < kMaxOQ; ++j)
+              for (int j = 0; j < JM; ++j)
                 if (j < o) ay[j] -= W2[((((i64)p * v + qq) * o + i) * o2 + (i64)j * o + k) * o + m] * tv;
             }
           }
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(kThreadsQ, 2) k_q_main_staged(const QArgs q) {
         const T t2v = T2v[(((i64)k * o + l) * v + r) * v + s];
         const i64 base = (i64)i * w[0] + (i64)k * w[2] + (i64)l * w[3];
 #pragma unroll
-        for (int j = 0; j < kMaxOQ; ++j)
+        for (int j = 0; j < JM; ++j)
           if (j < o) {
             const i64 el = base + (i64)j * w[1];
             const T X = (T)0.5 * ax[j];
@@ -735,9 +735,15 @@ int q_energy(rccsdt_ctx* ctx, const rcc::QInputs& in, double* e_q, double* info)
   const int smem = in_smem ? (int)rz_bytes : 0;
   ++rcc::g_launch_count;
   if (staged) {
-    if (staged_bytes > 48 * 1024)
-      cudaFuncSetAttribute(k_q_main_staged<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged_bytes);
-    k_q_main_staged<T><<<grid, kThreadsQ, staged_bytes, s>>>(qa);
+    auto launch = [&](auto kern) {
+      if (staged_bytes > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged_bytes);
+      kern<<<grid, kThreadsQ, staged_bytes, s>>>(qa);
+    };
+    if (o <= 4) launch(k_q_main_staged<T, 4>);
+    else if (o <= 8) launch(k_q_main_staged<T, 8>);
+    else if (o <= 12) launch(k_q_main_staged<T, 12>);
+    else launch(k_q_main_staged<T, 16>);
   } else {
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_q_main<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     k_q_main<T><<<grid, kThreadsQ, smem, s>>>(qa);

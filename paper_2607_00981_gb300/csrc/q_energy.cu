@@ -145,9 +145,11 @@ __global__ void k_q_layout(int kind, const double* __restrict__ G, const double*
 // 3b. W1[p][q][r][j][k][e] = Wbar^{pqr}_{ejk} = w(p,q,r; e,j,k) + w(p,r,q; e,k,j), with
 //   w(a,b,c; e,j,k) = -sum_m v^{mb}_{ej} t^{ac}_{mk} - sum_m v^{ma}_{je} t^{bc}_{mk}
 //                     + 1/2 sum_f v^{ab}_{ef} t^{fc}_{jk}
-// (v^{mb}_{ej} = (me|bj), v^{ma}_{je} = (mj|ae), v^{ab}_{ef} = (ae|bf)); arithmetic in T.
-template <typename T>
-__device__ __forceinline__ T q_w1(const double* __restrict__ G, const double* __restrict__ t2, int o, int v, int a,
+// (v^{mb}_{ej} = (me|bj), v^{ma}_{je} = (mj|ae), v^{ab}_{ef} = (ae|bf)); arithmetic in T,
+// on ERI and t2 copies of T's precision (FP32: converted once, so that the sums do no
+// per-product conversions on the FP64 units).
+template <typename T, typename TI>
+__device__ __forceinline__ T q_w1(const TI* __restrict__ G, const TI* __restrict__ t2, int o, int v, int a,
                                   int b, int c, int e, int j, int k) {
   const int n = o + v;
   const i64 n1 = n, n2 = n1 * n, n3 = n2 * n;
@@ -163,8 +165,8 @@ __device__ __forceinline__ T q_w1(const double* __restrict__ G, const double* __
   return s + (T)0.5 * h;
 }
 
-template <typename T>
-__global__ void k_q_wbar1(const double* __restrict__ G, const double* __restrict__ t2, int o, int v,
+template <typename T, typename TI>  // TI: the type of the ERI and t2 copies read (T's precision)
+__global__ void k_q_wbar1(const TI* __restrict__ G, const TI* __restrict__ t2, int o, int v,
                           T* __restrict__ W1) {
   const i64 tot = (i64)v * v * v * o * o * v;
   for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < tot; x += (i64)gridDim.x * blockDim.x) {
@@ -177,14 +179,14 @@ __global__ void k_q_wbar1(const double* __restrict__ G, const double* __restrict
     const int c = (int)(r % v);
     r /= v;
     const int b = (int)(r % v), a = (int)(r / v);
-    W1[x] = q_w1<T>(G, t2, o, v, a, b, c, e, j, k) + q_w1<T>(G, t2, o, v, a, c, b, e, k, j);
+    W1[x] = q_w1<T, TI>(G, t2, o, v, a, b, c, e, j, k) + q_w1<T, TI>(G, t2, o, v, a, c, b, e, k, j);
   }
 }
 
 // 3c. W2[p][q][i][j][k][m] = Wbar^{pqm}_{ijk} = w2(p,q,m; i,j,k) + w2(q,p,m; j,i,k),
 //   w2(a,b,m; i,j,k) = -1/2 sum_n v^{mn}_{ki} t^{ab}_{nj}   (v^{mn}_{ki} = (mk|ni))
-template <typename T>
-__global__ void k_q_wbar2(const double* __restrict__ G, const double* __restrict__ t2, int o, int v,
+template <typename T, typename TI>
+__global__ void k_q_wbar2(const TI* __restrict__ G, const TI* __restrict__ t2, int o, int v,
                           T* __restrict__ W2) {
   const int n = o + v;
   const i64 n1 = n, n2 = n1 * n, n3 = n2 * n, V2 = (i64)v * v;
@@ -686,8 +688,8 @@ int q_energy(rccsdt_ctx* ctx, const rcc::QInputs& in, double* e_q, double* info)
   const int per_sm = (staged || in_smem) ? std::max(1, std::min(4, (int)((224 * 1024) / (dyn + 14 * 1024)))) : 4;
   const int grid = (int)std::max<i64>(1, std::min<i64>(nquad, (i64)nsm * per_sm));
 
-  DevBuf G, t3v, A1, A2, Vv, W1, W2, T2e, T2m, T2v, vtr, qd, scratch, partial, outd;
-  if (!G.alloc(n4 * 8) || !t3v.alloc(nv3 * o2 * o * es) || !A1.alloc(V2 * o * v * es) ||
+  DevBuf G, Gf_buf, t3v, A1, A2, Vv, W1, W2, T2e, T2m, T2v, vtr, qd, scratch, partial, outd;
+  if (!G.alloc(n4 * 8) || !Gf_buf.alloc(sizeof(T) == 4 ? (size_t)(n4 + o2 * V2) * 4 : 16) || !t3v.alloc(nv3 * o2 * o * es) || !A1.alloc(V2 * o * v * es) ||
       !A2.alloc((i64)v * o2 * o * es) || !Vv.alloc(V2 * o2 * es) || !W1.alloc(V2 * V2 * o2 * es) ||
       !W2.alloc(V2 * o4 * es) || !T2e.alloc(o2 * V2 * es) || !T2m.alloc(o2 * V2 * es) ||
       !T2v.alloc(o2 * V2 * es) || !vtr.alloc(vt.size() * sizeof(int4)) || !qd.alloc(quads.size() * sizeof(int4)) ||
@@ -711,8 +713,18 @@ int q_energy(rccsdt_ctx* ctx, const rcc::QInputs& in, double* e_q, double* info)
   for (int kind = 0; kind < 6; ++kind)
     k_q_layout<T><<<grid_for(sizes[kind]), 256, 0, s>>>(kind, (const double*)G.p, in.t2, o, v, (T*)dst[kind],
                                                         sizes[kind]);
-  k_q_wbar1<T><<<grid_for(V2 * V2 * o2), 256, 0, s>>>((const double*)G.p, in.t2, o, v, (T*)W1.p);
-  k_q_wbar2<T><<<grid_for(V2 * o4), 256, 0, s>>>((const double*)G.p, in.t2, o, v, (T*)W2.p);
+  if (sizeof(T) == 8) {
+    k_q_wbar1<T, double><<<grid_for(V2 * V2 * o2), 256, 0, s>>>((const double*)G.p, in.t2, o, v, (T*)W1.p);
+    k_q_wbar2<T, double><<<grid_for(V2 * o4), 256, 0, s>>>((const double*)G.p, in.t2, o, v, (T*)W2.p);
+  } else {
+    // FP32 copies of the ERIs and t2, read by the FP32 sums
+    float* Gf = (float*)Gf_buf.p;
+    float* t2f = Gf + n4;
+    rcc::launch_convert<float, double>(Gf, (const double*)G.p, n4, s);
+    rcc::launch_convert<float, double>(t2f, in.t2, o2 * V2, s);
+    k_q_wbar1<T, float><<<grid_for(V2 * V2 * o2), 256, 0, s>>>(Gf, t2f, o, v, (T*)W1.p);
+    k_q_wbar2<T, float><<<grid_for(V2 * o4), 256, 0, s>>>(Gf, t2f, o, v, (T*)W2.p);
+  }
   cudaEventRecord(ev[2], s);
   QArgs qa;
   qa.quads = (const int4*)qd.p;

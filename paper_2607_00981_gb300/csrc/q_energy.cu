@@ -362,9 +362,7 @@ constexpr int kMaxOQ = 16;
 
 struct QStage {  // element offsets of the staged slices in the dynamic shared memory
   int a1, w1, a2, w2, vs, w2_staged;
-  int t2s, t1s, ec;  // amplitude slices: t^{es}_{il} rows and chunks of ec labels e of t^{ers}_{ikl}
-  int amp_staged;    // 1: the amplitude slices are staged too (when the whole fits 64 K elements)
-  i64 total;         // elements (R, Z and the slices)
+  i64 total;  // elements (R, Z and the slices)
 };
 
 __host__ __device__ inline i64 q_pad4(i64 x) { return (x + 3) & ~(i64)3; }
@@ -384,16 +382,6 @@ __host__ __device__ inline QStage q_stage_layout(int o, int v) {
   off += L.w2_staged ? q_pad4(o4) : 0;
   L.vs = (int)off;
   off += q_pad4(o2);
-  // amplitudes: t^{es}_{il} for all (i, l) and e, and t^{ers}_{ikl} for a chunk of e
-  // (at most 6144 values; the chunks split v evenly)
-  const i64 o3 = o2 * o;
-  const i64 nch = ((i64)v * o3 + 6143) / 6144;
-  L.ec = (int)((v + nch - 1) / nch);
-  const i64 amp = q_pad4(o2 * v) + q_pad4((i64)L.ec * o3);
-  L.amp_staged = (off + amp) * 4 <= 64 * 1024;  // about three CTAs per SM in FP32
-  L.t2s = (int)off;
-  L.t1s = (int)(off + q_pad4(o2 * v));
-  if (L.amp_staged) off += amp;
   L.total = off;
   return L;
 }
@@ -414,8 +402,6 @@ __global__ void __launch_bounds__(kThreadsQ, 2) k_q_main_staged(const QArgs q) {
   T* A2s = sm + lay.a2;
   T* W2s = sm + lay.w2;
   T* Vs = sm + lay.vs;
-  T* T2s = sm + lay.t2s;
-  T* T1s = sm + lay.t1s;
   const T* t3v = (const T*)q.t3v;
   const T* A1 = (const T*)q.A1;
   const T* A2 = (const T*)q.A2;
@@ -462,12 +448,6 @@ __global__ void __launch_bounds__(kThreadsQ, 2) k_q_main_staged(const QArgs q) {
         }
       for (i64 t = threadIdx.x; t < o2; t += blockDim.x)  // Vs[i][j] = v^{pq}_{ij}
         Vs[t] = Vv[(((i64)p * v + qq) * o) * o + t];
-      if (lay.amp_staged)
-        for (i64 t = threadIdx.x; t < o2 * v; t += blockDim.x) {  // T2s[(i, l)][e] = t^{es}_{il}
-          const i64 il = t / v;
-          const int e = (int)(t - il * v);
-          T2s[t] = T2e[(il * v + s) * v + e];
-        }
       __syncthreads();
       // weights of the permuted occupied positions in R's index
       const int w[4] = {(int)(c0 == 0 ? o3 : c0 == 1 ? o2 : c0 == 2 ? o : 1),
@@ -477,53 +457,12 @@ __global__ void __launch_bounds__(kThreadsQ, 2) k_q_main_staged(const QArgs q) {
       const bool rs = c2 < c3;
       const i64* bt = s_blk[pair_index(rs ? c2 : c3, rs ? c3 : c2)];
       const int r0 = rs ? r : s, s0 = rs ? s : r;
-      if (lay.amp_staged) {
-        // x1 in chunks of e: the gathered t^{ers}_{ikl} of a chunk staged by all threads,
-        // then each thread adds its x1 / 2 of the chunk to R and Z (the same thread owns
-        // the same (i, k, l), so the same elements, in the pass below)
-        for (int e0 = 0; e0 < v; e0 += lay.ec) {
-          const int ne = min(lay.ec, v - e0);
-          __syncthreads();  // the previous chunk is consumed
-          for (i64 x = threadIdx.x; x < (i64)ne * o3; x += blockDim.x) {
-            const int eu = (int)(x / o3), e = e0 + eu;
-            const i64 t = x - (i64)eu * o3;
-            const int i = (int)(t / o2), k = (int)((t / o) % o), l = (int)(t % o);
-            const int k0 = rs ? k : l, l0 = rs ? l : k;
-            const i64 f = e <= r0 ? ((i64)i * o + k0) * o + l0
-                                  : (e <= s0 ? ((i64)k0 * o + i) * o + l0 : ((i64)k0 * o + l0) * o + i);
-            T1s[x] = t3v[bt[e] + f];
-          }
-          __syncthreads();
-          for (i64 t = threadIdx.x; t < o3; t += blockDim.x) {
-            const int i = (int)(t / o2), k = (int)((t / o) % o), l = (int)(t % o);
-            T acc[JM];
-#pragma unroll
-            for (int j = 0; j < JM; ++j) acc[j] = (T)0;
-            for (int eu = 0; eu < ne; ++eu) {
-              const T tv = T1s[(i64)eu * o3 + t];
-              const T* a = A1s + (e0 + eu) * o;
-#pragma unroll
-              for (int j = 0; j < JM; ++j)
-                if (j < o) acc[j] += a[j] * tv;
-            }
-            const i64 base = (i64)i * w[0] + (i64)k * w[2] + (i64)l * w[3];
-#pragma unroll
-            for (int j = 0; j < JM; ++j)
-              if (j < o) {
-                const i64 el = base + (i64)j * w[1];
-                const T h = (T)0.5 * acc[j];
-                R[el] += h;
-                Z[el] += h;
-              }
-          }
-        }
-      }
       for (i64 t = threadIdx.x; t < o3; t += blockDim.x) {
         const int i = (int)(t / o2), k = (int)((t / o) % o), l = (int)(t % o);
         T ax[JM], ay[JM];  // per j: x1 - x2 and y1 - y2
 #pragma unroll
         for (int j = 0; j < JM; ++j) ax[j] = ay[j] = (T)0;
-        if (!lay.amp_staged) {  // x1 = sum_e v^{pq}_{ej} t^{ers}_{ikl}
+        {  // x1 = sum_e v^{pq}_{ej} t^{ers}_{ikl}
           const int k0 = rs ? k : l, l0 = rs ? l : k;
           const i64 f0 = ((i64)i * o + k0) * o + l0, f1 = ((i64)k0 * o + i) * o + l0, f2 = ((i64)k0 * o + l0) * o + i;
           for (int e0 = 0; e0 < v; e0 += 8) {  // eight gathers in flight, then their FMAs
@@ -554,7 +493,7 @@ __global__ void __launch_bounds__(kThreadsQ, 2) k_q_main_staged(const QArgs q) {
           }
         }
         {  // y1 = sum_e Wbar^{pqr}_{ejk} t^{es}_{il}
-          const T* t2e = lay.amp_staged ? T2s + ((i64)i * o + l) * v : T2e + (((i64)i * o + l) * v + s) * v;
+          const T* t2e = T2e + (((i64)i * o + l) * v + s) * v;
           const T* wk = W1s + (i64)k * v * o;
           for (int e0 = 0; e0 < v; e0 += 8) {
             T tv[8];

@@ -325,7 +325,8 @@ int rccsdt_t3_virtual_triangular(rccsdt_ctx* ctx, double* t3v);
  * the projection 1 - Pi_[4] - Pi_[3,1] of Eq. T4ortho on every block).
  * Storage: t4c[n4][v][v][v][v], n4 = o(o+1)(o+2)(o+3)/24, block (i<=j<=k<=l) at
  * C(l+3,4) + C(k+2,3) + C(j+1,2) + i, element [a][b][c][d] = t_ijkl^abcd;
- * W[a][b][e][f] = W^{ab}_{ef}, symmetric under (a,e) <-> (b,f).  In the split
+ * W[a][b][e][f] = W^{ab}_{ef}, symmetric under (a,e) <-> (b,f) (the ladder runs as
+ * sum and difference products over the label pairs and relies on it).  In the split
  * precisions T4 and R4 are stored in FP32 and the ladder runs as 3xBF16 / 3xTF32
  * products on the tensor cores; in FP64 on the FP64 units.
  * --------------------------------------------------------------------------- */

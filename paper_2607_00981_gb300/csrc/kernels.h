@@ -181,6 +181,11 @@ void launch_pair_pack_w(int kind, const double* W, int v, const int4* rows, int 
 void launch_pair_pack_t(int kind, const void* t3, int t3_f32, i64 b0, int nblk, int v, i64 sd, i64 se, i64 sw,
                         const PairChunk* ch, int nchunk, int Kp, int Km, const CubeDst& dp, const CubeDst& dm,
                         cudaStream_t s);
+// The same for one view of compact T4 blocks (v^4, a second free label w1 at stride sr):
+// row ((blk - b0) v + w1) v + w, dp = T(d, e, w1, w) + T(e, d, w1, w), dm = the difference.
+void launch_pair_pack_t4(int kind, const void* t4, int t4_f32, i64 b0, int nblk, int v, i64 sd, i64 se, i64 sw,
+                         i64 sr, const PairChunk* ch, int nchunk, int Kp, int Km, const CubeDst& dp,
+                         const CubeDst& dm, cudaStream_t s);
 // Zero the panel columns [k0, Kpad) of `rows` rows.
 void launch_zero_cols(const CubeDst& d, i64 rows, int k0, int kind, cudaStream_t s);
 // Second phase of a two-phase scatter: for each row m of the dense FP32 result X

@@ -98,17 +98,21 @@ __global__ void __launch_bounds__(256) k_pair_pack_w(const double* __restrict__ 
 // label cubes T(d0.., e0.., w0..) and T(e0.., d0.., w0..) (read along the view's
 // unit-stride axis), then writes 16 panel rows of the chunk's pairs.  The last
 // chunk's CTAs also zero the padding columns.
+// (Also the T4 views: grid z = (block, w1) pairs with `inner` values of w1 at stride
+// `sinner` inside a block of `vblk` elements; T3: inner 1, vblk v^3.)
 template <int KIND, typename TS>
 __global__ void __launch_bounds__(256) k_pair_pack_t(const TS* __restrict__ t3, i64 b0, int v, i64 sd, i64 se,
                                                      i64 sw, const PairChunk* __restrict__ ch, int nchunk, int Kp,
-                                                     int Km, CubeDst dp, CubeDst dm) {
+                                                     int Km, CubeDst dp, CubeDst dm, int inner, i64 sinner,
+                                                     i64 vblk) {
   using AT = typename std::conditional<KIND == PANEL_F64, double, float>::type;
   extern __shared__ __align__(16) unsigned char pp_smem[];
   TS* X = (TS*)pp_smem;            // X[a][b][w] = T(d0 + a, e0 + b, w0 + w)
   TS* Y = X + kPT * kPS * kPS;     // Y[a][b][w] = T(e0 + a, d0 + b, w0 + w)
   const PairChunk c = ch[blockIdx.x];
   const int w0 = blockIdx.y * kPT;
-  const TS* T = t3 + (b0 + blockIdx.z) * (i64)v * v * v;
+  const i64 zb = blockIdx.z / inner, zi = blockIdx.z - zb * inner;
+  const TS* T = t3 + (b0 + zb) * vblk + zi * sinner;
   const int d0 = c.P * kPT, e0 = c.Q * kPT;
   const int nd = min(kPT, v - d0), ne = min(kPT, v - e0), nw = min(kPT, v - w0);
   const bool diag = c.P == c.Q;
@@ -160,7 +164,9 @@ __global__ void __launch_bounds__(256) k_pair_pack_t(const TS* __restrict__ t3, 
 
 template <int KIND, typename TS>
 void pack_t(const TS* t3, i64 b0, int nblk, int v, i64 sd, i64 se, i64 sw, const PairChunk* ch, int nchunk, int Kp,
-            int Km, const CubeDst& dp, const CubeDst& dm, cudaStream_t s) {
+            int Km, const CubeDst& dp, const CubeDst& dm, cudaStream_t s, int inner = 1, i64 sinner = 0,
+            i64 vblk = -1) {
+  if (vblk < 0) vblk = (i64)v * v * v;
   const size_t smem = (size_t)2 * kPT * kPS * kPS * sizeof(TS);
   static bool attr = false;
   if (!attr) {
@@ -168,9 +174,10 @@ void pack_t(const TS* t3, i64 b0, int nblk, int v, i64 sd, i64 se, i64 sw, const
     attr = true;
   }
   const int nw = (v + kPT - 1) / kPT;
-  dim3 grid((unsigned)nchunk, (unsigned)nw, (unsigned)nblk);
+  dim3 grid((unsigned)nchunk, (unsigned)nw, (unsigned)((i64)nblk * inner));
   ++g_launch_count;
-  k_pair_pack_t<KIND, TS><<<grid, 256, smem, s>>>(t3, b0, v, sd, se, sw, ch, nchunk, Kp, Km, dp, dm);
+  k_pair_pack_t<KIND, TS><<<grid, 256, smem, s>>>(t3, b0, v, sd, se, sw, ch, nchunk, Kp, Km, dp, dm, inner, sinner,
+                                                  vblk);
 }
 
 }  // namespace
@@ -199,6 +206,22 @@ void launch_pair_pack_t(int kind, const void* t3, int t3_f32, i64 b0, int nblk, 
     else pack_t<PANEL_TF32X2, float>(t, b0, nblk, v, sd, se, sw, ch, nchunk, Kp, Km, dp, dm, s);
   } else {  // FP64 storage: FP64 panels only
     pack_t<PANEL_F64, double>((const double*)t3, b0, nblk, v, sd, se, sw, ch, nchunk, Kp, Km, dp, dm, s);
+  }
+}
+
+void launch_pair_pack_t4(int kind, const void* t4, int t4_f32, i64 b0, int nblk, int v, i64 sd, i64 se, i64 sw,
+                         i64 sr, const PairChunk* ch, int nchunk, int Kp, int Km, const CubeDst& dp,
+                         const CubeDst& dm, cudaStream_t s) {
+  if (nblk <= 0 || nchunk <= 0) return;
+  const i64 V4 = (i64)v * v * v * v;
+  if (t4_f32) {
+    const float* t = (const float*)t4;
+    if (kind == PANEL_BF16X2)
+      pack_t<PANEL_BF16X2, float>(t, b0, nblk, v, sd, se, sw, ch, nchunk, Kp, Km, dp, dm, s, v, sr, V4);
+    else
+      pack_t<PANEL_TF32X2, float>(t, b0, nblk, v, sd, se, sw, ch, nchunk, Kp, Km, dp, dm, s, v, sr, V4);
+  } else {
+    pack_t<PANEL_F64, double>((const double*)t4, b0, nblk, v, sd, se, sw, ch, nchunk, Kp, Km, dp, dm, s, v, sr, V4);
   }
 }
 

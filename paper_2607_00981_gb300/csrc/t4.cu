@@ -9,13 +9,20 @@
 // pp-ladder: for a stored block the six terms of Sec. II.C.4 are
 //   R[p <- x, q <- y, r <- w1, s <- w2] += sum_ef W^{xy}_{ef} T[p <- e, q <- f, r <- w1, s <- w2]
 // over the six position pairs (p, q) of the W labels ((0,1), (0,2), (0,3), (1,2),
-// (1,3), (2,3); (r, s) the other two positions in order).  Per term and range of
-// stored blocks this is one GEMM: rows (x, y) (M = v^2), columns (blk, w1, w2)
-// (N = v^2 per block), K = (e, f) (v^2), with A = W reshaped (the same panel for all
-// six terms) and B gathered from the stored blocks through 32 x 32 shared-memory
-// tiles (one of f and w2 always runs along the block's unit-stride axis).  The
-// table epilogue adds row x, y and column blk, w1, w2 at its place in R4; the six
-// terms run one after another on the stream, each GEMM writes every element once.
+// (1,3), (2,3); (r, s) the other two positions in order).  W is pair-symmetric
+// (W^{xy}_{ef} = W^{yx}_{fe}), so each term runs as the sum and difference products of
+// the RCCSDT pp-ladder: per term and range of stored blocks two GEMMs with K over the
+// label pairs e <= f (sum) and e < f (difference), rows the pairs x <= y and x < y of
+// W+ / W- (one panel pair for all six terms), columns (blk, w1, w2), B the T+ / T-
+// panels gathered from the stored blocks; each product is added half to (x, y) and
+// half, with its part's sign, to (y, x).  Half the multiply-adds of the plain
+// v^2 x v^2 product.  Where the block's unit-stride label is free (s = 3) the GEMMs
+// run with the operands exchanged and write R4 from the epilogue (both writes run
+// along w2); otherwise the unit-stride label is y, the mirrored writes would run
+// across it, so in the split precisions the GEMMs write their raw products and
+// k_t4_pair_scatter combines both parts per 16 x 16 label tile, writing 64-byte runs
+// for (x, y) and (y, x) (FP64 keeps the epilogue's writes).
+// The six terms run one after another on the stream.
 //
 // Post-processing (one pass, out of place): with x o rho the labels of element x
 // permuted by rho, out(x) = sum_rho d_rho R(x o rho) where d convolves the projector
@@ -47,92 +54,6 @@ constexpr int kPos[6][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}, {1, 2, 0, 
 __constant__ unsigned char c_t4perm[24][4];
 __constant__ double c_t4coef[5][24];  // per symmetrisation type
 __constant__ float c_t4coef_f[5][24];  // the same in FP32 (FP32 storage)
-
-// A panel: A[(x, y)][(e, f)] = W^{xy}_{ef} (W row-major is already [v^2][v^2]).
-__global__ void k_t4_pack_w(const double* __restrict__ W, int v, int kind, void* hi, void* lo, int Kpad) {
-  const i64 V2 = (i64)v * v, tot = V2 * Kpad;
-  for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < tot; x += (i64)gridDim.x * blockDim.x) {
-    const i64 r = x / Kpad, k = x - r * Kpad;
-    rcc::panel_put(kind, hi, lo, x, k < V2 ? W[r * V2 + k] : 0.0);
-  }
-}
-
-// B panel of one term for stored blocks b0 .. b0 + nblk - 1:
-//   B[((blk - b0) v + w1) v + w2][e v + f] = T[blk][p <- e, q <- f, r <- w1, s <- w2]
-// CTA = one (blk, w1); per e it stages the (w2, f) plane in chunks of up to 32 rows
-// w2 in shared memory, read along f or w2, whichever has the block's unit stride (one
-// always does), and writes each row's run of v K values (f) with 8 values per
-// thread (16-byte stores when the run starts on an 8-element boundary); the K
-// padding v^2 .. Kpad of its rows is zeroed once.
-template <typename T>
-__global__ void __launch_bounds__(256) k_t4_pack_t(const T* __restrict__ t4, i64 b0, int nblk, int v, int sp,
-                                                   int sq, int sr, int ss, int kind, void* hi, void* lo,
-                                                   int Kpad) {
-  extern __shared__ __align__(16) unsigned char t4p_smem[];
-  T* tile = reinterpret_cast<T*>(t4p_smem);  // [32][v + 1]
-  const int P = v + 1;
-  const i64 blk = blockIdx.x / v;
-  const int w1 = (int)(blockIdx.x - blk * v);
-  const i64 V4 = (i64)v * v * v * v, V2 = (i64)v * v;
-  const T* base = t4 + (b0 + blk) * V4 + (i64)w1 * sr;
-  const bool f_fast = sq == 1;
-  const int nf8 = (v + 7) / 8;
-  const bool vec = (v & 7) == 0 && (Kpad & 7) == 0;
-  for (int e = 0; e < v; ++e) {
-    const T* pe = base + (i64)e * sp;
-    for (int r0 = 0; r0 < v; r0 += 32) {
-      const int nr = min(32, v - r0);
-      __syncthreads();  // the previous chunk is written out
-      for (int idx = threadIdx.x; idx < nr * v; idx += blockDim.x) {
-        int r, f;
-        if (f_fast) {
-          r = idx / v;
-          f = idx - r * v;
-        } else {
-          f = idx / nr;
-          r = idx - f * nr;
-        }
-        tile[r * P + f] = pe[(i64)f * sq + (i64)(r0 + r) * ss];
-      }
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < nr * nf8; idx += blockDim.x) {
-        const int r = idx / nf8, f0 = (idx - r * nf8) * 8;
-        const i64 o = ((blk * v + w1) * v + r0 + r) * (i64)Kpad + (i64)e * v + f0;
-        const T* src = tile + r * P + f0;
-        if (vec && kind == rcc::PANEL_BF16X2 && sizeof(T) == 4) {
-          uint32_t h[4], l[4];  // bf16 pairs, first element in the low half
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const __nv_bfloat162 hp = __floats2bfloat162_rn((float)src[2 * j], (float)src[2 * j + 1]);
-            const float2 hf = __bfloat1622float2(hp);
-            const __nv_bfloat162 lp = __floats2bfloat162_rn((float)src[2 * j] - hf.x, (float)src[2 * j + 1] - hf.y);
-            h[j] = *reinterpret_cast<const uint32_t*>(&hp);
-            l[j] = *reinterpret_cast<const uint32_t*>(&lp);
-          }
-          *reinterpret_cast<uint4*>((__nv_bfloat16*)hi + o) = make_uint4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<uint4*>((__nv_bfloat16*)lo + o) = make_uint4(l[0], l[1], l[2], l[3]);
-        } else {
-          const int n = min(8, v - f0);
-          for (int j = 0; j < n; ++j) {
-            if constexpr (sizeof(T) == 4)
-              rcc::panel_put_f(kind, hi, lo, o + j, src[j]);
-            else
-              rcc::panel_put(kind, hi, lo, o + j, src[j]);
-          }
-        }
-      }
-    }
-  }
-  // zero the padding columns K = v^2 .. Kpad of this CTA's v rows
-  if (Kpad > V2) {
-    const int np = Kpad - (int)V2;
-    for (int idx = threadIdx.x; idx < v * np; idx += blockDim.x) {
-      const int w2 = idx / np;
-      const i64 k = V2 + (idx - w2 * np);
-      rcc::panel_put_f(kind, hi, lo, ((blk * v + w1) * v + w2) * (i64)Kpad + k, 0.f);
-    }
-  }
-}
 
 template <typename T>
 __device__ __forceinline__ double t4_block_sum(double x, double* ws) {
@@ -251,6 +172,79 @@ __global__ void k_t4_reduce(const double* __restrict__ partial, i64 n, double* _
   if (threadIdx.x == 0) out[0] = t;
 }
 
+// Second phase of a ladder term whose GEMM wrote its sum and difference products raw
+// (column-major: P[n][m] over the sum pairs, M[n][m] over the difference pairs, n =
+// (blk, w1, w2) of the range): per column and chunk of 16-label tiles, both parts are
+// staged as full 16 x 16 tiles, then thread (r, c) adds
+//   R(d0 + r, e0 + c) += (P + M) / 2 at pair (r, c) and R(e0 + r, d0 + c) += (P - M) / 2
+// at pair (c, r) (a diagonal chunk: the one element (r, c), from the pair with r <= c).
+// Consecutive threads run along c, the label at the second W position, so the writes
+// are 64-byte runs when that position has unit stride.  Chunks and columns write
+// disjoint elements (no atomics).
+constexpr int kT4ScCols = 8;
+__global__ void __launch_bounds__(256, 3) k_t4_pair_scatter(const float* __restrict__ P, const float* __restrict__ M,
+                                                         int Kp, int Km, const rcc::PairChunk* __restrict__ ch,
+                                                         int v, const i64* __restrict__ colo, i64 sp, i64 sq,
+                                                         i64 N, float* __restrict__ r4) {
+  __shared__ float SP[kT4ScCols][16][17], SM[kT4ScCols][16][17];
+  const rcc::PairChunk c = ch[blockIdx.x];
+  const int d0 = c.P * 16, e0 = c.Q * 16;
+  const int nd = min(16, v - d0), ne = min(16, v - e0);
+  const bool diag = c.P == c.Q;
+  const int np = diag ? nd * (nd + 1) / 2 : nd * ne;
+  const int nm = diag ? nd * (nd - 1) / 2 : nd * ne;
+  const int t = threadIdx.x;
+  int ap = 0, bp = 0, am = 0, bm = 0;
+  if (t < np) rcc::pair_decode(t, diag, true, nd, ne, ap, bp);
+  if (t < nm) rcc::pair_decode(t, diag, false, nd, ne, am, bm);
+  const int r = t >> 4, q = t & 15;
+  for (i64 n0 = (i64)blockIdx.y * kT4ScCols; n0 < N; n0 += (i64)gridDim.y * kT4ScCols) {
+    const int ncol = (int)min((i64)kT4ScCols, N - n0);
+    __syncthreads();  // the previous group's tiles are consumed
+    {
+      float vp[kT4ScCols], vm[kT4ScCols];
+#pragma unroll
+      for (int j = 0; j < kT4ScCols; ++j) {
+        const i64 n = n0 + j;
+        vp[j] = (j < ncol && t < np) ? __ldg(P + n * Kp + c.offp + t) : 0.f;
+        vm[j] = (j < ncol && t < nm) ? __ldg(M + n * Km + c.offm + t) : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < kT4ScCols; ++j) {
+        if (t < np) SP[j][ap][bp] = vp[j];
+        if (t < nm) SM[j][am][bm] = vm[j];
+      }
+    }
+    __syncthreads();
+    // all read-modify-write loads of the group first (independent, in flight together)
+    i64 base[kT4ScCols];
+    const bool w1 = diag ? (r < nd && q < nd) : (r < nd && q < ne);
+    const bool w2 = !diag && r < ne && q < nd;
+    const i64 off1 = (i64)(d0 + r) * sp + (i64)((diag ? d0 : e0) + q) * sq;
+    const i64 off2 = (i64)(e0 + r) * sp + (i64)(d0 + q) * sq;
+#pragma unroll
+    for (int j = 0; j < kT4ScCols; ++j) base[j] = j < ncol ? __ldg(colo + n0 + j) : 0;
+    float o[kT4ScCols];
+    // the (d, e) elements: loads of the group in flight together, then the stores
+#pragma unroll
+    for (int j = 0; j < kT4ScCols; ++j) o[j] = (j < ncol && w1) ? r4[base[j] + off1] : 0.f;
+#pragma unroll
+    for (int j = 0; j < kT4ScCols; ++j) {
+      const float x = !diag || r < q ? 0.5f * (SP[j][r][q] + SM[j][r][q])
+                                     : (r > q ? 0.5f * (SP[j][q][r] - SM[j][q][r]) : 0.5f * SP[j][r][r]);
+      if (j < ncol && w1) r4[base[j] + off1] = o[j] + x;
+    }
+    // the mirrored (e, d) elements of an off-diagonal chunk
+    if (w2) {
+#pragma unroll
+      for (int j = 0; j < kT4ScCols; ++j) o[j] = j < ncol ? r4[base[j] + off2] : 0.f;
+#pragma unroll
+      for (int j = 0; j < kT4ScCols; ++j)
+        if (j < ncol) r4[base[j] + off2] = o[j] + 0.5f * (SP[j][q][r] - SM[j][q][r]);
+    }
+  }
+}
+
 template <typename TO, typename TI>
 __global__ void k_t4_convert(TO* __restrict__ out, const TI* __restrict__ in, i64 n) {
   for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < n; x += (i64)gridDim.x * blockDim.x)
@@ -262,17 +256,26 @@ unsigned grid_of(i64 n) { return (unsigned)std::max<i64>(1, std::min<i64>((n + 2
 }  // namespace
 
 struct rccsdt_t4 {
-  int o = 0, v = 0, prec = 0, kind = 0, Kpad = 0;
+  int o = 0, v = 0, prec = 0, kind = 0;
   i64 n4 = 0, V4 = 0, unit = 1;
   cudaStream_t s = nullptr;
   std::vector<void*> allocs;
   void *t4 = nullptr, *r4 = nullptr, *rp4 = nullptr, *stage = nullptr;
   double* W = nullptr;
   void *Ahi = nullptr, *Alo = nullptr, *Bhi = nullptr, *Blo = nullptr;
-  i64* rowbase = nullptr;   // [6][v^2]
-  i64* coloff = nullptr;    // [6][n4 v^2]
-  int* rowsel = nullptr;
-  double* alpha = nullptr;
+  i64* coloff = nullptr;    // [6][n4 v^2]: R4 offset of column (blk, w1, w2) of each term
+  // pair-symmetric ladder (W^{ab}_{ef} = W^{ba}_{fe}): sum and difference panels over the
+  // label pairs; K numbered by chunks of 16-label tiles, rows x <= y (sum), x < y (difference)
+  rcc::PairChunk* pchunks = nullptr;
+  int nchunk = 0, Kp = 0, Km = 0, Kpadp = 0, Kpadm = 0;
+  int4* prows = nullptr;    // [Kp] (x, y, row of (x, y) among the difference pairs or -1)
+  i64* prb = nullptr;       // [6][2][Kp] R4 offset of (x, y) at the term's W label positions
+  i64* prb2 = nullptr;      // the mirrored (y, x); -1 on the diagonal
+  i64 nal = 0;              // rows of the alpha and selector tables: max(Kp, unit v^2)
+  double* pal = nullptr;    // [2][nal] 1/2
+  double* pal2 = nullptr;   // [2][nal] +1/2 (sum), -1/2 (difference)
+  int* psel = nullptr;      // [nal] zeros
+  float* raw = nullptr;     // split kinds: raw sum and difference products of one range, [unit v^2][Kp + Km]
   int4* info = nullptr;
   double* partial = nullptr;
   int4* quads = nullptr;    // tile quadruples A <= B <= C <= D of the post-processing pass
@@ -391,26 +394,54 @@ RCC_API int rccsdt_t4_create(int o, int v, int precision, void* stream, rccsdt_t
   const i64 V2 = (i64)v * v;
   c->V4 = V2 * V2;
   c->s = (cudaStream_t)stream;
-  c->Kpad = (int)((V2 + 63) / 64 * 64);
   const size_t es = precision == RCCSDT_FP64 ? 8 : 4;
   const size_t pe = precision == RCCSDT_FP64 ? 8 : (precision == RCCSDT_SPLIT_BF16X3 ? 2 : 4);
-  // blocks per B panel: about 1 GiB of FP64-sized panel
-  const i64 per_blk = V2 * c->Kpad * 8;
-  c->unit = std::max<i64>(1, std::min<i64>(c->n4, ((i64)1 << 30) / per_blk));
+  // pair numbering (16-label tiles P <= Q; inside a chunk as pair_decode describes)
+  std::vector<rcc::PairChunk> ch;
+  {
+    const int nt = (v + 15) / 16;
+    int offp = 0, offm = 0;
+    for (int P = 0; P < nt; ++P)
+      for (int Q = P; Q < nt; ++Q) {
+        const int nd = std::min(16, v - 16 * P), ne = std::min(16, v - 16 * Q);
+        const bool diag = P == Q;
+        ch.push_back({P, Q, offp, offm});
+        offp += diag ? nd * (nd + 1) / 2 : nd * ne;
+        offm += diag ? nd * (nd - 1) / 2 : nd * ne;
+      }
+    c->nchunk = (int)ch.size();
+    c->Kp = offp;
+    c->Km = offm;
+    c->Kpadp = (offp + 63) / 64 * 64;
+    c->Kpadm = (offm + 63) / 64 * 64;
+  }
+  // blocks per B panel: about 1 GiB of FP64-sized panel, and at most 65535 (block, w1)
+  // pairs (the pair gather's grid)
+  const i64 kcols = c->Kpadp + std::max(c->Kpadm, 64);
+  const i64 per_blk = V2 * kcols * 8;
+  c->unit = std::max<i64>(1, std::min<i64>(std::min<i64>(c->n4, ((i64)1 << 30) / per_blk), 65535 / v));
   bool ok = true;
   c->t4 = c->alloc(c->n4 * c->V4 * es, &ok);
   c->r4 = c->alloc(c->n4 * c->V4 * es, &ok);
   c->rp4 = c->alloc(c->n4 * c->V4 * es, &ok);
   c->stage = c->alloc(precision == RCCSDT_FP64 ? 16 : ((size_t)32 << 20) * 8, &ok);
   c->W = (double*)c->alloc(c->V4 * 8, &ok);
-  c->Ahi = c->alloc(V2 * c->Kpad * pe, &ok);
-  c->Alo = c->alloc(precision == RCCSDT_FP64 ? 16 : V2 * c->Kpad * pe, &ok);
-  c->Bhi = c->alloc(c->unit * V2 * c->Kpad * pe, &ok);
-  c->Blo = c->alloc(precision == RCCSDT_FP64 ? 16 : c->unit * V2 * c->Kpad * pe, &ok);
-  c->rowbase = (i64*)c->alloc(6 * V2 * 8, &ok);
+  const i64 abytes = ((i64)c->Kp * c->Kpadp + (i64)c->Km * c->Kpadm) * (i64)pe;
+  const i64 bbytes = c->unit * V2 * kcols * (i64)pe;
+  c->Ahi = c->alloc(abytes, &ok);
+  c->Alo = c->alloc(precision == RCCSDT_FP64 ? 16 : abytes, &ok);
+  c->Bhi = c->alloc(bbytes, &ok);
+  c->Blo = c->alloc(precision == RCCSDT_FP64 ? 16 : bbytes, &ok);
   c->coloff = (i64*)c->alloc(6 * c->n4 * V2 * 8, &ok);
-  c->rowsel = (int*)c->alloc(std::max<i64>(V2, c->unit * V2) * 4, &ok);
-  c->alpha = (double*)c->alloc(std::max<i64>(V2, c->unit * V2) * 8, &ok);
+  c->pchunks = (rcc::PairChunk*)c->alloc(ch.size() * sizeof(rcc::PairChunk), &ok);
+  c->prows = (int4*)c->alloc((size_t)c->Kp * sizeof(int4), &ok);
+  c->prb = (i64*)c->alloc((size_t)12 * c->Kp * 8, &ok);
+  c->prb2 = (i64*)c->alloc((size_t)12 * c->Kp * 8, &ok);
+  c->nal = std::max<i64>(c->Kp, std::min(c->n4, c->unit) * V2);
+  c->pal = (double*)c->alloc((size_t)2 * c->nal * 8, &ok);
+  c->pal2 = (double*)c->alloc((size_t)2 * c->nal * 8, &ok);
+  c->psel = (int*)c->alloc((size_t)c->nal * 4, &ok);
+  if (precision != RCCSDT_FP64) c->raw = (float*)c->alloc((size_t)(c->unit * V2) * (c->Kp + c->Km) * 4, &ok);
   c->info = (int4*)c->alloc(c->n4 * sizeof(int4), &ok);
   const int ntile = (v + kT4Tile - 1) / kT4Tile;
   c->nq = (int)((i64)ntile * (ntile + 1) * (ntile + 2) * (ntile + 3) / 24);
@@ -426,11 +457,43 @@ RCC_API int rccsdt_t4_create(int o, int v, int precision, void* stream, rccsdt_t
   }
   // tables: strides of the four label positions in a v^4 block
   const i64 st[4] = {V2 * v, V2, (i64)v, 1};
-  std::vector<i64> rb(6 * V2), co((size_t)6 * c->n4 * V2);
+  // rows of both parts in the K order of the chunks (pair_decode inside a chunk), so the
+  // raw products' row index is the pair's K index: sum rows x <= y, difference rows x < y
+  std::vector<std::array<int, 2>> rp, rm;
+  std::vector<int> mrow((size_t)V2, -1);
+  for (const rcc::PairChunk& q : ch) {
+    const int nd = std::min(16, v - 16 * q.P), ne = std::min(16, v - 16 * q.Q);
+    const bool diag = q.P == q.Q;
+    const int np = diag ? nd * (nd + 1) / 2 : nd * ne, nm = diag ? nd * (nd - 1) / 2 : nd * ne;
+    for (int t = 0; t < np; ++t) {
+      int a, b;
+      rcc::pair_decode(t, diag, true, nd, ne, a, b);
+      rp.push_back({16 * q.P + a, 16 * q.Q + b});
+    }
+    for (int t = 0; t < nm; ++t) {
+      int a, b;
+      rcc::pair_decode(t, diag, false, nd, ne, a, b);
+      mrow[(size_t)(16 * q.P + a) * v + 16 * q.Q + b] = (int)rm.size();
+      rm.push_back({16 * q.P + a, 16 * q.Q + b});
+    }
+  }
+  std::vector<int4> prows(rp.size());
+  for (size_t m = 0; m < rp.size(); ++m) prows[m] = make_int4(rp[m][0], rp[m][1], mrow[(size_t)rp[m][0] * v + rp[m][1]], 0);
+  std::vector<i64> prb((size_t)12 * c->Kp, -1), prb2((size_t)12 * c->Kp, -1), co((size_t)6 * c->n4 * V2);
+  std::vector<double> pal((size_t)2 * c->nal, 0.5), pal2((size_t)2 * c->nal, 0.5);
+  for (i64 m = 0; m < c->nal; ++m) pal2[(size_t)(c->nal + m)] = -0.5;
   for (int t = 0; t < 6; ++t) {
     const int p = kPos[t][0], q = kPos[t][1], r = kPos[t][2], s = kPos[t][3];
-    for (int x = 0; x < v; ++x)
-      for (int y = 0; y < v; ++y) rb[t * V2 + x * v + y] = x * st[p] + y * st[q];
+    for (int part = 0; part < 2; ++part) {
+      const auto& pr = part == 0 ? rp : rm;
+      i64* b1 = prb.data() + (size_t)(t * 2 + part) * c->Kp;
+      i64* b2 = prb2.data() + (size_t)(t * 2 + part) * c->Kp;
+      for (size_t m = 0; m < pr.size(); ++m) {
+        const i64 x = pr[m][0], y = pr[m][1];
+        b1[m] = x * st[p] + y * st[q];
+        b2[m] = x == y ? -1 : y * st[p] + x * st[q];
+      }
+    }
     for (i64 b = 0; b < c->n4; ++b)
       for (int w1 = 0; w1 < v; ++w1)
         for (int w2 = 0; w2 < v; ++w2) co[(size_t)t * c->n4 * V2 + (b * v + w1) * v + w2] = b * c->V4 + w1 * st[r] + w2 * st[s];
@@ -464,14 +527,17 @@ RCC_API int rccsdt_t4_create(int o, int v, int precision, void* stream, rccsdt_t
     for (int C = 0; C <= D; ++C)
       for (int B = 0; B <= C; ++B)
         for (int A = 0; A <= B; ++A) quads.push_back(make_int4(A, B, C, D));
-  std::vector<int> sel(std::max<i64>(V2, c->unit * V2), 0);
-  std::vector<double> al(std::max<i64>(V2, c->unit * V2), 1.0);
-  bool cp = cudaMemcpy(c->rowbase, rb.data(), rb.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(c->coloff, co.data(), co.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+  std::vector<int> sel((size_t)c->nal, 0);
+  bool cp = cudaMemcpy(c->coloff, co.data(), co.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->pchunks, ch.data(), ch.size() * sizeof(rcc::PairChunk), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->prows, prows.data(), prows.size() * sizeof(int4), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->prb, prb.data(), prb.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->prb2, prb2.data(), prb2.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->pal, pal.data(), pal.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->pal2, pal2.data(), pal2.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->psel, sel.data(), sel.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->info, info.data(), info.size() * sizeof(int4), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->quads, quads.data(), quads.size() * sizeof(int4), cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(c->rowsel, sel.data(), sel.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(c->alpha, al.data(), al.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemset(c->scal, 0, 64 * 8) == cudaSuccess;
   if (!cp) {
     cudaGetLastError();
@@ -480,9 +546,7 @@ RCC_API int rccsdt_t4_create(int o, int v, int precision, void* stream, rccsdt_t
   }
   t4_tables_once();
   if (cudaFuncSetAttribute(k_t4_post<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 24 * kT4Slot * 8) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_t4_pack_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * (200 + 1) * 8) !=
-          cudaSuccess) {
+      cudaSuccess) {
     cudaGetLastError();
     delete c;
     return RCCSDT_ERR_CUDA;
@@ -496,9 +560,12 @@ RCC_API int rccsdt_t4_set(rccsdt_t4* c, const double* W, const double* t4c) {
   if (W) {
     if (cudaMemcpyAsync(c->W, W, (size_t)c->V4 * 8, cudaMemcpyDefault, c->s) != cudaSuccess)
       return c->fail(RCCSDT_ERR_CUDA, "copy of W failed");
-    ++rcc::g_launch_count;
-    k_t4_pack_w<<<grid_of((i64)c->v * c->v * c->Kpad), 256, 0, c->s>>>(c->W, c->v, c->kind, c->Ahi, c->Alo,
-                                                                        c->Kpad);
+    // W+ / W- panels (both parts side by side in the A buffers)
+    const size_t pe = c->prec == RCCSDT_FP64 ? 8 : (c->prec == RCCSDT_SPLIT_BF16X3 ? 2 : 4);
+    const size_t aoff = (size_t)c->Kp * c->Kpadp * pe;
+    const rcc::CubeDst Ap{c->Ahi, c->prec == RCCSDT_FP64 ? nullptr : c->Alo, c->Kpadp};
+    const rcc::CubeDst Am{(char*)c->Ahi + aoff, c->prec == RCCSDT_FP64 ? nullptr : (char*)c->Alo + aoff, c->Kpadm};
+    rcc::launch_pair_pack_w(c->kind, c->W, c->v, c->prows, c->Kp, c->pchunks, c->nchunk, c->Kp, c->Km, Ap, Am, c->s);
     c->have_w = true;
   }
   if (t4c) {
@@ -523,36 +590,76 @@ RCC_API int rccsdt_t4_pp_ladder(rccsdt_t4* c) {
   cudaMemsetAsync(c->scal, 0, 64 * 8, c->s);
   const i64 st[4] = {V2 * v, V2, (i64)v, 1};
   int* flag = (int*)(c->scal + 8);
+  const bool f64 = c->prec == RCCSDT_FP64;
+  const size_t pe = f64 ? 8 : (c->prec == RCCSDT_SPLIT_BF16X3 ? 2 : 4);
+  const size_t aoff = (size_t)c->Kp * c->Kpadp * pe;
   for (int t = 0; t < 6; ++t) {
     const int p = kPos[t][0], q = kPos[t][1], r = kPos[t][2], s = kPos[t][3];
     for (i64 b0 = 0; b0 < c->n4; b0 += c->unit) {
       const int nblk = (int)std::min<i64>(c->unit, c->n4 - b0);
-      const i64 ncta = (i64)nblk * v;
-      const size_t tsm = (size_t)32 * (v + 1);
-      ++rcc::g_launch_count;
-      if (c->prec == RCCSDT_FP64)
-        k_t4_pack_t<double><<<(unsigned)ncta, 256, tsm * 8, c->s>>>((const double*)c->t4, b0, nblk, v, (int)st[p],
-                                                                     (int)st[q], (int)st[r], (int)st[s], c->kind,
-                                                                     c->Bhi, c->Blo, c->Kpad);
-      else
-        k_t4_pack_t<float><<<(unsigned)ncta, 256, tsm * 4, c->s>>>((const float*)c->t4, b0, nblk, v, (int)st[p],
-                                                                    (int)st[q], (int)st[r], (int)st[s], c->kind,
-                                                                    c->Bhi, c->Blo, c->Kpad);
-      rcc::EpiArgs e{};
-      e.C = c->r4;
-      e.c_f32 = c->prec != RCCSDT_FP64;
-      e.M = (int)V2;
-      e.N = (int)(nblk * V2);
-      e.row_base = c->rowbase + t * V2;
-      e.row_sel = c->rowsel;
-      e.row_alpha = c->alpha;
-      e.col_off = c->coloff + (size_t)t * c->n4 * V2 + b0 * V2;
-      if (c->prec == RCCSDT_FP64) {
-        rcc::launch_gemm_f64((const double*)c->Ahi, (const double*)c->Bhi, (int)((V2 + 15) / 16 * 16), c->Kpad,
-                             c->Kpad, e, (double*)c->splitk, c->splitk_elems, c->s);
-      } else if (rcc::launch_gemm_tc(c->kind, c->Ahi, c->Alo, c->Bhi, c->Blo, c->Kpad, e, flag, 0, c->s, c->splitk,
-                                     c->splitk_elems * 2, nullptr, e.N <= 128 ? 128 : 256)) {
-        return c->fail(RCCSDT_ERR_ARG, "tensor-core GEMM configuration unsupported");
+      const i64 N = nblk * V2;
+      // T+ / T- panels of this view: rows (blk, w1, w2), K the pairs of the labels at p, q
+      const size_t boff = (size_t)N * c->Kpadp * pe;
+      char* bh = (char*)c->Bhi;
+      char* bl = f64 ? nullptr : (char*)c->Blo;
+      const rcc::CubeDst Bp{bh, bl, c->Kpadp}, Bm{bh + boff, bl ? bl + boff : nullptr, c->Kpadm};
+      rcc::launch_pair_pack_t4(c->kind, c->t4, f64 ? 0 : 1, b0, nblk, v, st[p], st[q], st[s], st[r], c->pchunks,
+                               c->nchunk, c->Kp, c->Km, Bp, Bm, c->s);
+      for (int part = 0; part < 2; ++part) {
+        const int K = part ? c->Km : c->Kp, Kpad = part ? c->Kpadm : c->Kpadp;
+        if (K == 0) continue;
+        // With the unit-stride label free (s = 3) the operands are exchanged: rows
+        // (blk, w1, w2), so an epilogue warp's 32 rows are 32 consecutive elements for both
+        // the (x, y) write and its mirror (the column mirror); otherwise rows are the pairs
+        // and the direct write runs along y at unit stride.
+        const bool swap = s == 3;
+        const i64* pb = c->prb + (size_t)(t * 2 + part) * c->Kp;
+        const i64* pb2 = c->prb2 + (size_t)(t * 2 + part) * c->Kp;
+        const i64* co = c->coloff + (size_t)t * c->n4 * V2 + b0 * V2;
+        rcc::EpiArgs e{};
+        e.C = c->r4;
+        e.c_f32 = f64 ? 0 : 1;
+        e.row_sel = c->psel;
+        e.row_alpha = c->pal + (size_t)part * c->nal;
+        e.row_alpha2 = c->pal2 + (size_t)part * c->nal;
+        if (swap) {
+          e.M = (int)N;
+          e.N = K;
+          e.row_base = co;
+          e.col_off = pb;
+          e.col_off2 = pb2;
+        } else {
+          e.M = K;
+          e.N = (int)N;
+          e.row_base = pb;
+          e.row_base2 = pb2;
+          e.col_off = co;
+        }
+        const char* wh = (const char*)c->Ahi + (part ? aoff : 0);
+        const char* wl = f64 ? nullptr : (const char*)c->Alo + (part ? aoff : 0);
+        const char* th = bh + (part ? boff : 0);
+        const char* tl = bl ? bl + (part ? boff : 0) : nullptr;
+        const char* ah = swap ? th : wh;
+        const char* al = swap ? tl : wl;
+        const char* bhp = swap ? wh : th;
+        const char* blp = swap ? wl : tl;
+        if (f64) {
+          rcc::launch_gemm_f64((const double*)ah, (const double*)bhp, (K + 15) / 16 * 16, Kpad, Kpad, e,
+                               (double*)c->splitk, c->splitk_elems, c->s);
+        } else if (rcc::launch_gemm_tc(c->kind, ah, al, bhp, blp, Kpad, e, flag, 0, c->s, c->splitk,
+                                       c->splitk_elems * 2, swap ? nullptr : c->raw + (part ? N * c->Kp : 0), 256,
+                                       1)) {
+          return c->fail(RCCSDT_ERR_ARG, "tensor-core GEMM configuration unsupported");
+        }
+      }
+      if (!f64 && s != 3) {
+        // raw products of both parts -> R4 (the direct epilogue's mirrored writes would
+        // run across the unit-stride label)
+        ++rcc::g_launch_count;
+        k_t4_pair_scatter<<<dim3((unsigned)c->nchunk, (unsigned)std::min<i64>(65535, (N + kT4ScCols - 1) / kT4ScCols)),
+                            256, 0, c->s>>>(
+            c->raw, c->raw + N * c->Kp, c->Kp, c->Km, c->pchunks, v, c->coloff + (size_t)t * c->n4 * V2 + b0 * V2,
+            st[p], st[q], N, (float*)c->r4);
       }
     }
   }

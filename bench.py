@@ -542,29 +542,42 @@ def run_ours(args, rank, world):
     fma = lib.rccsdt_iteration_fma(o, v)
 
     # --- end to end through the C ABI with pinned host buffers
-    e2e = None
+    e2e = e2e64 = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
         hL, hf = pin(inst.L), pin(inst.fock_diag)
         n3 = ctx.n3
         ht1, ht2, ht3 = ctx.amplitudes()
         ht1, ht2, ht3 = pin(ht1), pin(ht2), pin(ht3)
-        bytes_in = hL.nbytes + hf.nbytes + ht1.nbytes + ht2.nbytes + ht3.nbytes
-        bytes_out = ht1.nbytes + ht2.nbytes + ht3.nbytes + 8 * 5
+        split = prec != PRECISIONS["fp64"]
         ksteps = max(1, min(args.steps, 3 if n3 * v ** 3 < 1e9 else 1))
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(ksteps):
-            ctx.set_hamiltonian(hf, hL)
-            ctx.set_amplitudes(ht1, ht2, ht3)
-            ctx.iterate()
-            ctx.get_amplitudes(ht1, ht2, ht3)
-        barrier()
-        dt = max_over_ranks(time.perf_counter() - t0, dist, f"cuda:{dev}")
-        e2e = {"value": per_iteration(dt, ksteps, world), "unit": "s/iteration",
-               "h2d_bytes_per_step": int(bytes_in), "d2h_bytes_per_step": int(bytes_out),
-               "steps": ksteps, "note": "set_hamiltonian + set_amplitudes from pinned host memory, "
-                                        "rccsdt_iterate, get_amplitudes to host; DIIS history restarts each step"}
+
+        def run_e2e(t3_f32):
+            h3 = pin(ht3.astype(np.float32)) if t3_f32 else ht3
+            setter = ctx.set_amplitudes_t3f32 if t3_f32 else ctx.set_amplitudes
+            getter = ctx.get_amplitudes_t3f32 if t3_f32 else ctx.get_amplitudes
+            bytes_in = hL.nbytes + hf.nbytes + ht1.nbytes + ht2.nbytes + h3.nbytes
+            bytes_out = ht1.nbytes + ht2.nbytes + h3.nbytes + 8 * 5
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(ksteps):
+                ctx.set_hamiltonian(hf, hL)
+                setter(ht1, ht2, h3)
+                ctx.iterate()
+                getter(ht1, ht2, h3)
+            barrier()
+            dt = max_over_ranks(time.perf_counter() - t0, dist, f"cuda:{dev}")
+            return {"value": per_iteration(dt, ksteps, world), "unit": "s/iteration",
+                    "h2d_bytes_per_step": int(bytes_in), "d2h_bytes_per_step": int(bytes_out), "steps": ksteps,
+                    "note": "set_hamiltonian + " + ("set_amplitudes_t3f32 (T3 in its FP32 storage type)"
+                                                    if t3_f32 else "set_amplitudes (float64 T3)")
+                            + " from pinned host memory, rccsdt_iterate, "
+                            + ("get_amplitudes_t3f32" if t3_f32 else "get_amplitudes")
+                            + " to host; DIIS history restarts each step"}
+
+        e2e = run_e2e(split)
+        if split:
+            e2e64 = run_e2e(False)
 
     # --- roofline of the dominant kernel (the pp-ladder GEMM)
     pk = peaks()
@@ -629,7 +642,7 @@ def run_ours(args, rank, world):
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
                 "config": dict(config(args, inst), parallelism=f"replicas{world}"),
                 "tflops": 2.0 * fma * world / (ms_total / 1e3 / args.steps) / 1e12,
-                "energy_last": energies[-1], "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
+                "energy_last": energies[-1], "e2e": e2e, "e2e_float64_t3": e2e64, "gpu_launches": int(launches), "roofline": roof,
                 "cpu_baseline": cpu, "clocks": clk.summary(), "fp64_vs_split": compare, "fp64_here": fp64_here,
                 "batch64": batch, "matmul_peaks": mm, "q_correction": extra_q, "t4_ladder": extra_t4,
                 "diis": ("DIIS(8) over T1 and T2" if not diis_t3 else

@@ -130,6 +130,12 @@ int rccsdt_set_hamiltonian(rccsdt_ctx* ctx, const double* fock_diag, const doubl
  * Clears the DIIS history and a watchdog timeout (as does rccsdt_init_mp2). */
 int rccsdt_set_amplitudes(rccsdt_ctx* ctx, const double* t1, const double* t2, const double* t3c);
 
+/* The same with T3 in FP32, the storage type of the split modes (RCCSDT_SPLIT_*
+ * contexts only): t3c is copied as it is (host pageable or pinned, or device
+ * memory), half the bytes of the float64 call and no conversion pass.  t1 and t2 stay
+ * float64.  Errors: RCCSDT_ERR_ARG (an FP64 context), RCCSDT_ERR_CUDA. */
+int rccsdt_set_amplitudes_t3f32(rccsdt_ctx* ctx, const double* t1, const double* t2, const float* t3c);
+
 /* t1 = 0, t2 = first-order (MP2) doubles v^{ab}_{ij} / eps_ij^ab, t3 = 0. */
 int rccsdt_init_mp2(rccsdt_ctx* ctx);
 
@@ -189,6 +195,9 @@ int rccsdt_load(rccsdt_ctx* ctx, const char* path);
 
 /* Copies out the amplitudes / the current residuals (float64). NULL skips. */
 int rccsdt_get_amplitudes(rccsdt_ctx* ctx, double* t1, double* t2, double* t3c);
+/* Copies out the amplitudes with T3 in its FP32 storage (split modes only; errors as
+ * rccsdt_set_amplitudes_t3f32). */
+int rccsdt_get_amplitudes_t3f32(rccsdt_ctx* ctx, double* t1, double* t2, float* t3c);
 int rccsdt_get_residuals(rccsdt_ctx* ctx, double* r1, double* r2, double* r3c);
 
 /* Leading algorithmic FMA count of the compact contractions of one iteration,

@@ -50,6 +50,8 @@ _SIGS = {
     "rccsdt_iterate": (C.c_int, [_P, _P, _P]),
     "rccsdt_solve": (C.c_int, [_P, _P, _P, _P]),
     "rccsdt_get_amplitudes": (C.c_int, [_P, _P, _P, _P]),
+    "rccsdt_set_amplitudes_t3f32": (C.c_int, [_P, _P, _P, _P]),
+    "rccsdt_get_amplitudes_t3f32": (C.c_int, [_P, _P, _P, _P]),
     "rccsdt_save": (C.c_int, [_P, C.c_char_p]),
     "rccsdt_load": (C.c_int, [_P, C.c_char_p]),
     "rccsdt_get_residuals": (C.c_int, [_P, _P, _P, _P]),
@@ -103,18 +105,20 @@ def load_library(path: str) -> C.CDLL:
     return lib
 
 
-def _ptr(x):
-    """Raw pointer of a contiguous float64 numpy array or torch tensor (None -> NULL)."""
+def _ptr(x, f32=False):
+    """Raw pointer of a contiguous float64 (float32 with ``f32``) numpy array or torch
+    tensor (None -> NULL)."""
     if x is None:
         return None
+    kind = "float32" if f32 else "float64"
     if isinstance(x, np.ndarray):
-        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
-            raise ValueError("arrays must be contiguous float64")
+        if x.dtype != np.dtype(kind) or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"arrays must be contiguous {kind}")
         return x.ctypes.data
     if hasattr(x, "data_ptr"):
         import torch
-        if x.dtype != torch.float64 or not x.is_contiguous():
-            raise ValueError("tensors must be contiguous float64")
+        if x.dtype != getattr(torch, kind) or not x.is_contiguous():
+            raise ValueError(f"tensors must be contiguous {kind}")
         return x.data_ptr()
     raise TypeError(f"unsupported array type {type(x)}")
 
@@ -166,6 +170,10 @@ class Context:
     def set_amplitudes(self, t1=None, t2=None, t3c=None):
         self._check(self.lib.rccsdt_set_amplitudes(self.h, _ptr(t1), _ptr(t2), _ptr(t3c)))
 
+    def set_amplitudes_t3f32(self, t1=None, t2=None, t3c=None):
+        """T3 in FP32, the split modes' storage type (t1, t2 float64)."""
+        self._check(self.lib.rccsdt_set_amplitudes_t3f32(self.h, _ptr(t1), _ptr(t2), _ptr(t3c, f32=True)))
+
     def init_mp2(self):
         self._check(self.lib.rccsdt_init_mp2(self.h))
 
@@ -207,6 +215,9 @@ class Context:
 
     def get_amplitudes(self, t1=None, t2=None, t3c=None):
         self._check(self.lib.rccsdt_get_amplitudes(self.h, _ptr(t1), _ptr(t2), _ptr(t3c)))
+
+    def get_amplitudes_t3f32(self, t1=None, t2=None, t3c=None):
+        self._check(self.lib.rccsdt_get_amplitudes_t3f32(self.h, _ptr(t1), _ptr(t2), _ptr(t3c, f32=True)))
 
     def save(self, path):
         """Write the iteration state (amplitudes, DIIS history, counters) to ``path``."""

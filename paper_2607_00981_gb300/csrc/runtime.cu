@@ -2587,6 +2587,14 @@ RCC_API int rccsdt_set_amplitudes(rccsdt_ctx* c, const double* t1, const double*
   return RCCSDT_OK;
 }
 
+RCC_API int rccsdt_set_amplitudes_t3f32(rccsdt_ctx* c, const double* t1, const double* t2, const float* t3c) {
+  if (!c) return RCCSDT_ERR_ARG;
+  if (c->opt.precision == RCCSDT_FP64) return fail(c, RCCSDT_ERR_ARG, "FP32 T3 exchange needs a split-precision context");
+  if (t3c && dev_copy(c->B("t3")->p, t3c, (size_t)(c->n3 * c->V3) * 4, c->stream))
+    return fail(c, RCCSDT_ERR_CUDA, "copy");
+  return rccsdt_set_amplitudes(c, t1, t2, nullptr);  // stream order; synchronises, resets DIIS
+}
+
 RCC_API int rccsdt_init_mp2(rccsdt_ctx* c) {
   if (!c) return RCCSDT_ERR_ARG;
   if (!c->have_ham) return fail(c, RCCSDT_ERR_STATE, "hamiltonian not set");
@@ -2718,6 +2726,14 @@ RCC_API int rccsdt_get_amplitudes(rccsdt_ctx* c, double* t1, double* t2, double*
     }
   }
   return dev_sync(c->stream) ? fail(c, RCCSDT_ERR_CUDA, "get_amplitudes failed") : 0;
+}
+
+RCC_API int rccsdt_get_amplitudes_t3f32(rccsdt_ctx* c, double* t1, double* t2, float* t3c) {
+  if (!c) return RCCSDT_ERR_ARG;
+  if (c->opt.precision == RCCSDT_FP64) return fail(c, RCCSDT_ERR_ARG, "FP32 T3 exchange needs a split-precision context");
+  if (t3c && dev_copy(t3c, c->B("t3")->p, (size_t)(c->n3 * c->V3) * 4, c->stream))
+    return fail(c, RCCSDT_ERR_CUDA, "copy");
+  return rccsdt_get_amplitudes(c, t1, t2, nullptr);  // stream order; synchronises
 }
 
 // ---------------------------------------------------------------------------

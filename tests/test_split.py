@@ -151,3 +151,48 @@ def test_t3_round_trip_through_pinned_and_pageable_host_memory():
         assert np.array_equal(got, want), kind
         outs.append(got)
     ctx.close()
+
+
+@pytest.mark.gpu
+def test_t3_exchange_in_fp32_storage():
+    """rccsdt_set/get_amplitudes_t3f32 move T3 in the split modes' FP32 storage as it
+    is (pageable, pinned or device buffers), agree with the float64 calls on the same
+    amplitudes (same residual norms), and are refused by an FP64 context."""
+    torch = pytest.importorskip("torch")
+    lib = gpu_lib()
+    o, v, naux = 3, 10, 24
+    inst = make_instance(o, v, naux, seed=4)
+    t1, t2, t3 = random_amplitudes(o, v, seed=5)
+    t3c = np.ascontiguousarray(oc.pack(t3))
+    t3f = t3c.astype(np.float32)
+    ctx = B.Context(lib, o, v, naux, precision=B.SPLIT_BF16X3)
+    ctx.set_hamiltonian(inst.fock_diag, inst.L)
+    for kind in ("pageable", "pinned", "device"):
+        if kind == "pageable":
+            src, dst = t3f, np.zeros_like(t3f)
+        elif kind == "pinned":
+            src = torch.from_numpy(t3f.copy()).pin_memory()
+            dst = torch.zeros(t3f.shape, dtype=torch.float32).pin_memory()
+        else:
+            src = torch.from_numpy(t3f).cuda()
+            dst = torch.zeros(t3f.shape, dtype=torch.float32, device="cuda")
+        ctx.set_amplitudes_t3f32(t1, t2, src)
+        g1, g2 = np.zeros_like(t1), np.zeros_like(t2)
+        ctx.get_amplitudes_t3f32(g1, g2, dst)
+        got = dst if isinstance(dst, np.ndarray) else dst.cpu().numpy()
+        assert np.array_equal(got, t3f), kind
+        assert np.array_equal(g1, t1) and np.array_equal(g2, t2)
+    # the same iteration from either entry point
+    ctx.set_amplitudes_t3f32(t1, t2, t3f)
+    e32, n32 = ctx.iterate()
+    ctx.set_amplitudes(t1, t2, t3c)
+    e64, n64 = ctx.iterate()
+    assert e32 == e64 and np.array_equal(n32, n64)
+    ctx.close()
+    c64 = B.Context(lib, o, v, naux, precision=B.FP64)
+    with pytest.raises(B.RccsdtError) as ei:
+        c64.set_amplitudes_t3f32(t1, t2, t3f)
+    assert ei.value.status == B.ERR_ARG
+    with pytest.raises(ValueError):
+        c64.set_amplitudes_t3f32(t1, t2, t3c)  # float64 array for the FP32 call
+    c64.close()

@@ -131,9 +131,9 @@ int rccsdt_set_hamiltonian(rccsdt_ctx* ctx, const double* fock_diag, const doubl
 int rccsdt_set_amplitudes(rccsdt_ctx* ctx, const double* t1, const double* t2, const double* t3c);
 
 /* The same with T3 in FP32, the storage type of the split modes (RCCSDT_SPLIT_*
- * contexts only): t3c is copied as it is (host pageable or pinned, or device
- * memory), half the bytes of the float64 call and no conversion pass.  t1 and t2 stay
- * float64.  Errors: RCCSDT_ERR_ARG (an FP64 context), RCCSDT_ERR_CUDA. */
+ * contexts only): t3c is copied as it is, half the bytes of the float64 call (pinned
+ * host or device memory: one copy kernel reads it in place; pageable host memory: a
+ * staged copy).  t1 and t2 stay float64.  Errors: RCCSDT_ERR_ARG (an FP64 context), RCCSDT_ERR_CUDA. */
 int rccsdt_set_amplitudes_t3f32(rccsdt_ctx* ctx, const double* t1, const double* t2, const float* t3c);
 
 /* t1 = 0, t2 = first-order (MP2) doubles v^{ab}_{ij} / eps_ij^ab, t3 = 0. */

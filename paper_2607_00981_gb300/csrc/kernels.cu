@@ -1330,6 +1330,7 @@ void launch_convert(TO* out, const TI* in, i64 n, cudaStream_t s) {
 template void launch_convert<float, double>(float*, const double*, i64, cudaStream_t);
 template void launch_convert<double, float>(double*, const float*, i64, cudaStream_t);
 template void launch_convert<double, double>(double*, const double*, i64, cudaStream_t);
+template void launch_convert<float, float>(float*, const float*, i64, cudaStream_t);
 
 }  // namespace rcc
 

@@ -2590,8 +2590,13 @@ RCC_API int rccsdt_set_amplitudes(rccsdt_ctx* c, const double* t1, const double*
 RCC_API int rccsdt_set_amplitudes_t3f32(rccsdt_ctx* c, const double* t1, const double* t2, const float* t3c) {
   if (!c) return RCCSDT_ERR_ARG;
   if (c->opt.precision == RCCSDT_FP64) return fail(c, RCCSDT_ERR_ARG, "FP32 T3 exchange needs a split-precision context");
-  if (t3c && dev_copy(c->B("t3")->p, t3c, (size_t)(c->n3 * c->V3) * 4, c->stream))
-    return fail(c, RCCSDT_ERR_CUDA, "copy");
+  if (t3c) {
+    const i64 cnt = c->n3 * c->V3;
+    if (const float* dv = (const float*)device_view(t3c))
+      rcc::launch_convert<float, float>(c->B("t3")->f(), dv, cnt, c->stream);  // in place (SM loads over the link)
+    else if (dev_copy(c->B("t3")->p, t3c, (size_t)cnt * 4, c->stream))
+      return fail(c, RCCSDT_ERR_CUDA, "copy");
+  }
   return rccsdt_set_amplitudes(c, t1, t2, nullptr);  // stream order; synchronises, resets DIIS
 }
 
@@ -2731,8 +2736,13 @@ RCC_API int rccsdt_get_amplitudes(rccsdt_ctx* c, double* t1, double* t2, double*
 RCC_API int rccsdt_get_amplitudes_t3f32(rccsdt_ctx* c, double* t1, double* t2, float* t3c) {
   if (!c) return RCCSDT_ERR_ARG;
   if (c->opt.precision == RCCSDT_FP64) return fail(c, RCCSDT_ERR_ARG, "FP32 T3 exchange needs a split-precision context");
-  if (t3c && dev_copy(t3c, c->B("t3")->p, (size_t)(c->n3 * c->V3) * 4, c->stream))
-    return fail(c, RCCSDT_ERR_CUDA, "copy");
+  if (t3c) {
+    const i64 cnt = c->n3 * c->V3;
+    if (float* dv = (float*)device_view(t3c))
+      rcc::launch_convert<float, float>(dv, c->B("t3")->f(), cnt, c->stream);  // in place (SM stores over the link)
+    else if (dev_copy(t3c, c->B("t3")->p, (size_t)cnt * 4, c->stream))
+      return fail(c, RCCSDT_ERR_CUDA, "copy");
+  }
   return rccsdt_get_amplitudes(c, t1, t2, nullptr);  // stream order; synchronises
 }
 

@@ -909,11 +909,17 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
                    const EpiArgs& e, int* status_flag, long long watchdog, cudaStream_t s, float* scratch,
                    long long scratch_elems, float* raw_out, int bn, int colmajor) {
   if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
-  const int BN = (bn == 128 || bn == 144) ? bn : 256;
+  int BN = (bn == 128 || bn == 144) ? bn : 256;
   const int esz = kind == PANEL_BF16X2 ? 2 : 4;
   const int bk = ROWB / esz;
   if (Kpad % bk != 0 || e.M <= 0 || e.N <= 0) return 1;
   if (e.col_off2 && (BN != 256 || raw_out || e.row_base2)) return 1;  // column mirror: 256-wide, direct epilogue
+  // A table-epilogue GEMM of few 256-wide tiles is bound by its epilogue's chains of
+  // dependent loads (eight warps per tile): with at most half the SMs busy, 128-wide
+  // tiles give twice the CTAs and half the epilogue work each.
+  if (BN == 256 && !raw_out && !e.col_off2 &&
+      2LL * ((e.M + BM - 1) / BM) * ((e.N + 255) / 256) <= (long long)num_sms())
+    BN = 128;
   PlainSched sch;
   if (!make_map(&sch.ah, Ahi, e.M, Kpad, kind, BM) || !make_map(&sch.al, Alo, e.M, Kpad, kind, BM) ||
       !make_map(&sch.bh, Bhi, e.N, Kpad, kind, BN) || !make_map(&sch.bl, Blo, e.N, Kpad, kind, BN))

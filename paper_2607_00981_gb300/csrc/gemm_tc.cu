@@ -278,9 +278,12 @@ struct PlainSchedT {
   int colmajor;    // raw result stored as [N][M] (each thread's row runs along memory)
   __device__ __forceinline__ int ntiles() const { return g.mt * g.nt * g.splitk; }
   __device__ __forceinline__ void tile(int t, Tile& x) const {
+    // split slices K-range-major: the CTAs of one wave take every tile of the same
+    // K ranges, so the A and B slices they read are shared through L2
+    const int nmn = g.mt * g.nt;
     x.p = 0;
-    x.ks = t % g.splitk;
-    raster(g.mt, g.nt, t / g.splitk, x.tm, x.tn);
+    x.ks = t / nmn;
+    raster(g.mt, g.nt, t - x.ks * nmn, x.tm, x.tn);
     x.kb0 = x.ks * g.kb_per;
     x.kb1 = min(g.kblocks, x.kb0 + g.kb_per);
   }
@@ -932,9 +935,24 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
   const int sms = num_sms();
   const int tiles = g.mt * g.nt;
   if (tiles < sms && g.kblocks >= 8 && scratch && !raw_out) {
-    int sk = std::min((2 * sms + tiles - 1) / tiles, g.kblocks / 4);
-    while (sk > 1 && (long long)sk * e.M * e.N > scratch_elems) --sk;
-    g.splitk = std::max(sk, 1);
+    // split factor with the shortest critical path: whole waves of tile slices times
+    // the K blocks of one slice (plus a few K blocks' worth of epilogue per slice), so
+    // that the last wave is not a sliver of the SMs
+    const int max_sk = std::min(g.kblocks / 4, 64);
+    long long best = -1;
+    int best_sk = 1;
+    for (int sk = 1; sk <= max_sk; ++sk) {
+      const int kb_per = (g.kblocks + sk - 1) / sk;
+      const int real = (g.kblocks + kb_per - 1) / kb_per;
+      if (real > 1 && (long long)real * e.M * e.N > scratch_elems) break;
+      const long long waves = ((long long)tiles * real + sms - 1) / sms;
+      const long long cost = waves * (kb_per + 4);
+      if (best < 0 || cost < best) {
+        best = cost;
+        best_sk = real;
+      }
+    }
+    g.splitk = best_sk;
   }
   g.kb_per = (g.kblocks + g.splitk - 1) / g.splitk;
   g.splitk = (g.kblocks + g.kb_per - 1) / g.kb_per;

@@ -197,6 +197,15 @@ struct GemmPlan {
   // stacked rows: the A panel is the concatenation of these plans' A operands
   // (each packed into its row range); the plan stands for all of them
   std::vector<GemmPlan*> a_parts;
+  // split modes: an A panel of its own, shared by plans with the same A operand (the
+  // step (iii) plans of every z batch); the plan with own_pack packs it, the others
+  // reuse it while own_kind matches
+  struct OwnPanel {
+    DBuf hi, lo;
+    int kind = -1;
+  };
+  std::shared_ptr<OwnPanel> own;
+  int own_pack = 0;
 };
 
 struct rccsdt_ctx {
@@ -825,13 +834,15 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
   const int kind = !tc ? rcc::PANEL_F64 : (c->precision == RCCSDT_SPLIT_BF16X3 ? rcc::PANEL_BF16X2 : rcc::PANEL_TF32X2);
   rcc::PackArgs pa = g->A.a, pb = g->B.a;
   pa.kind = pb.kind = kind;
-  pa.out_hi = c->panelA_hi->p;
-  pa.out_lo = c->panelA_lo ? c->panelA_lo->p : nullptr;
+  const bool own = tc && g->own;  // the plan's own A panel (split modes)
+  pa.out_hi = own ? g->own->hi.p : c->panelA_hi->p;
+  pa.out_lo = own ? g->own->lo.p : (c->panelA_lo ? c->panelA_lo->p : nullptr);
   pb.out_hi = c->panelB_hi->p;
   pb.out_lo = c->panelB_lo ? c->panelB_lo->p : nullptr;
   // FP64 contractions on the tensor cores (option f64_tc): the large ones only
   const bool f64e = !tc && c->opt.f64_tc && c->planesA && (c->opt.f64_tc == 2 || g->fma >= 3e7) && !g->f64_only;
-  const bool packA = !g->a_parts.empty() || !g->reuse_A || c->packedA_kind != kind;
+  const bool packA = own ? (g->own_pack || g->own->kind != kind)
+                         : (!g->a_parts.empty() || !g->reuse_A || c->packedA_kind != kind);
   const bool packB = !g->reuse_B || c->packedB_kind != kind;
   if (!packA) {
   } else if (!g->a_parts.empty()) {
@@ -840,15 +851,19 @@ static int run_gemm(rccsdt_ctx* c, GemmPlan* g) {
     for (GemmPlan* q : g->a_parts) {
       rcc::PackArgs pq = q->A.a;
       pq.kind = kind;
-      pq.out_hi = (char*)c->panelA_hi->p + r0 * g->Kpad * esz;
-      pq.out_lo = c->panelA_lo ? (void*)((char*)c->panelA_lo->p + r0 * g->Kpad * esz) : nullptr;
+      pq.out_hi = (char*)pa.out_hi + r0 * g->Kpad * esz;
+      pq.out_lo = pa.out_lo ? (void*)((char*)pa.out_lo + r0 * g->Kpad * esz) : nullptr;
       rcc::launch_pack(pq, c->stream);
       r0 += (size_t)pq.R;
     }
   } else {
     rcc::launch_pack(pa, c->stream);
   }
-  if (packA) c->slicedA = 0;
+  if (own) {
+    if (packA) g->own->kind = kind;
+  } else if (packA) {
+    c->slicedA = 0;
+  }
   if (packB) c->slicedB = 0;
   if (packB) {
     if (tc && g->cube) {
@@ -1294,6 +1309,7 @@ int build_context(rccsdt_ctx* c) {
     c->a3_pos = upload_vec(c, pos, &err);
     View dR1 = b.T("dR1", {o, v}), dX2 = b.T("dX2", {o, o, v, v});
     const int Z = c->a3_Z;
+    std::shared_ptr<GemmPlan::OwnPanel> own45;
     for (int z0 = 0; z0 < o; z0 += Z) {
       const int Zb = std::min(Z, o - z0);
       View Sz = dense(c->B("Sz")->p, {Zb, o, o, v, v, v}, t3f);  // S[z][x][y][e1][e2][e3]
@@ -1382,16 +1398,32 @@ int build_context(rccsdt_ctx* c) {
       // stacked A operands.  (With Zb = 1 the first contraction's panel is the
       // second's too, but both write dX2[y][z0], so they stay two GEMMs.)
       if (q1 && q2 && q3 && q4 && q5) {
-        auto replace = [&](const std::vector<GemmPlan*>& parts) {
+        auto replace = [&](const std::vector<GemmPlan*>& parts) -> GemmPlan* {
           GemmPlan* m = stack_rows(c, parts, &err);
-          if (!m) return;
+          if (!m) return nullptr;
           auto at = std::find(g.begin(), g.end(), parts[0]);
           const size_t pos = (size_t)(at - g.begin());
           for (GemmPlan* q : parts) g.erase(std::find(g.begin(), g.end(), q));
           g.insert(g.begin() + pos, m);
+          return m;
         };
         replace({q2, q3});
-        replace({q4, q5});
+        GemmPlan* m45 = replace({q4, q5});
+        // the A operand of (q4 q5) (vovv and oovv over (e3, x, e1)) is the same for every
+        // z batch: in the split modes it is packed once per iteration into a panel of
+        // its own (the first batch packs it)
+        if (m45 && t3f) {
+          if (!own45) {
+            own45 = std::make_shared<GemmPlan::OwnPanel>();
+            const size_t bytes = (size_t)m45->A.a.R * m45->Kpad * 4;  // widest split element (TF32)
+            own45->hi.p = dev_alloc(bytes, &err);
+            own45->hi.bytes = bytes;
+            own45->lo.p = dev_alloc(bytes, &err);
+            own45->lo.bytes = bytes;
+            m45->own_pack = 1;
+          }
+          m45->own = own45;
+        }
         // q1's panel must still be in place for the reshaped read: q1, (q4 q5), (q2 q3)
         std::stable_partition(g.begin(), g.end(), [&](GemmPlan* p) {
           return p == q1 || (!p->a_parts.empty() && p->a_parts[0] == q4) || p == q4 || p == q5;

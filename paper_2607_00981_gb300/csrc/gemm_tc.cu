@@ -9,8 +9,9 @@
 // relative error of about 2^-16 (BF16) or 2^-21 (TF32) per product.
 //
 // Persistent kernel, one CTA per SM, 320 threads:
-//   warp 0     TMA producer: 128-byte-swizzled 128 x 64B-row tiles of A and
-//              256-row tiles of B, hi and lo planes, into a 2-stage ring;
+//   warp 0     TMA producer: 64-byte-swizzled tiles (rows of 64 bytes of K) of
+//              128 rows of A and up to 256 rows of B, hi and lo planes, into a
+//              4-stage ring;
 //   warp 1     TMEM owner and MMA issuer (one thread): 3 tcgen05.mma per 32-byte
 //              K slice into a 128 x 256 FP32 accumulator, double buffered in
 //              TMEM (512 columns) so the epilogue of one tile overlaps the MMAs
@@ -36,8 +37,10 @@
 namespace rcc {
 namespace {
 
-constexpr int BM = 128, STAGES = 2;
-constexpr int ROWB = 128;                      // bytes of one K-row of a tile (swizzle span)
+// Four stages of 64-byte K rows (48 KiB per stage at BN = 256) rather than two of 128:
+// the same shared memory, with three stages' loads in flight behind the MMAs instead of one.
+constexpr int BM = 128, STAGES = 4;
+constexpr int ROWB = 64;                       // bytes of one K-row of a tile (swizzle span)
 constexpr int A_PLANE = BM * ROWB;
 constexpr int kEpiWarps = 8;                 // two epilogue warps per TMEM lane quadrant
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -46,7 +49,7 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 template <int BN>
 struct TileCfg {
   static constexpr int B_PLANE = BN * ROWB;
-  static constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;  // 96 KiB for BN = 256
+  static constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;  // 48 KiB for BN = 256
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
   static constexpr int TMEM_COLS = 2 * BN <= 256 ? 256 : 512;      // double-buffered accumulator (power of 2)
   static constexpr int FULL = BN / 32, HALF = (BN % 32) / 16;      // 32- and 16-column epilogue chunks
@@ -130,15 +133,11 @@ __device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
   return d;
 }
 
-// SM100 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), version 1; tiles are 1024-byte aligned (base offset 0).
+// SM100 shared-memory matrix descriptor of the k_gemm_tc tiles: K-major rows of ROWB
+// bytes with the matching swizzle (version 1; tiles 1024-byte aligned, base offset 0).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;                      // SWIZZLE_128B
-  return d;
+  static_assert(ROWB == 64, "k_gemm_tc tiles use the 64-byte swizzle");
+  return sdesc64(saddr);
 }
 
 // Instruction descriptor: D = F32, A = B = fmt (1 BF16, 2 TF32), both K-major, N = BN, M = BM.
@@ -865,8 +864,9 @@ bool make_map(CUtensorMap* map, const void* ptr, int rows, int Kpad, int kind, i
   cuuint32_t box[2] = {(cuuint32_t)(ROWB / esz), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   const CUtensorMapDataType dt = kind == PANEL_BF16X2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  static_assert(ROWB == 64, "the tensor maps' swizzle matches the descriptors' (64 bytes)");
   return fn(map, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

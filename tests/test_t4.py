@@ -90,3 +90,30 @@ def test_t4_bench_shape_sampled_blocks_match_oracle():
         ref = Q.orthogonalise4_block(sp[b])
         assert np.abs(p4[b] - ref).max() / scale < 5e-6, (b, quads[b])  # 24-term FP32 sums
     eng.close()
+
+
+@pytest.mark.gpu
+def test_t4_many_small_blocks_match_oracle():
+    """o = 19, v = 10: 7315 stored blocks, ladder ranges of 6553 blocks (65535 / v
+    (block, w1) pairs per pair gather), so the raw-product scatter has more column
+    groups than its grid rows and runs its grid-stride loop.  Sampled blocks of both
+    ranges (degenerate, purified and distinct-index ones) against the oracle's direct
+    traversal of those blocks, in 3xBF16 and 3xTF32."""
+    o, v = 19, 10
+    n4 = Q.n4(o)
+    assert n4 == 7315
+    W = random_pair_symmetric(v, seed=19)
+    rng = np.random.default_rng(10)
+    t4c = 0.05 * rng.standard_normal((n4, v, v, v, v))
+    quads = Q.quads(o)
+    sel = [0, 1, Q.blk4(0, 1, 2, 3), 4000, 6552, 6553, 7000, Q.blk4(3, 3, 17, 17), n4 - 1]
+    assert quads[n4 - 1] == (18, 18, 18, 18)
+    R = Q.pp_ladder_compact(W, t4c[sel], o)
+    scale = max(1.0, np.abs(R).max())
+    for prec in (B.SPLIT_BF16X3, B.SPLIT_TF32X3):
+        eng = B.T4Engine(gpu_lib(), o, v, precision=prec)
+        eng.set(W, t4c)
+        eng.pp_ladder()
+        r4 = eng.r4()
+        assert np.abs(r4[sel] - R).max() / scale < TOL[prec], prec
+        eng.close()

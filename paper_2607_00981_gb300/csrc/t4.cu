@@ -39,6 +39,7 @@
 #include <cmath>
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/rccsdt.h"
@@ -73,17 +74,76 @@ __device__ __forceinline__ double t4_block_sum(double x, double* ws) {
 // x + gridDim.x, ... of stored block blk.  The 24 label permutations map the tiles
 // (A, B, C, D) permuted onto one another, so a quadruple's distinct permuted tiles
 // (its orbit, at most 24 tiles of 256 elements) hold every input its outputs read:
-// they are staged in shared memory once, and each output element of the orbit
-// is the 24-term sum over them.  Slot s holds the tile whose position x has tile
-// index Q[perm_s(x)]; the input of term p of an output in slot s lies in slot
-// (s o p) at the output's local coordinates permuted by p.  Shared strides
-// (69, 17, 4, 1) keep every permuted read of a warp within two-way bank conflicts.
-// Writes the block's partial squared norm (times the block multiplicity) to
-// partial[blk * gridDim.x + x].
+// they are staged in shared memory once.  Slot s holds the tile whose position x has
+// tile index Q[perm_s(x)].  Thread l takes the element e of slot 0 at local
+// coordinates l and its orbit {e o s}: it reads the 24 values v_s = R(e o s) once
+// (slot s at l's coordinates permuted by s), forms out(e o s) = sum_p d_p v_(s o p)
+// for every distinct slot s (24 x 24 multiply-adds in registers, the permutation
+// indices compile-time constants), and writes them back into the staged tiles in
+// place; the tiles are then stored to R4 along the unit-stride axis.  Each output
+// element of a distinct slot comes from exactly one thread (l -> l o s is a
+// bijection), so the pass is deterministic.  Shared strides (69, 17, 4, 1) keep every
+// permuted access of a warp within two-way bank conflicts.  Writes the block's
+// partial squared norm (times the block multiplicity) to partial[blk * gridDim.x + x].
 constexpr int kT4Tile = 4;
 constexpr int kT4S0 = 69, kT4S1 = 17, kT4S2 = 4;
 constexpr int kT4Slot = 3 * (kT4S0 + kT4S1 + kT4S2 + 1) + 1;  // 274 elements per staged tile
-__constant__ unsigned char c_t4comp[24][24];  // index of the permutation y -> s(p(y))
+
+// The 24 permutations of (0, 1, 2, 3) in lexicographic order (the order of the
+// coefficient tables) and their composition, as compile-time constants.
+__host__ __device__ constexpr int t4_perm(int i, int x) {
+  int n = 0;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      for (int c = 0; c < 4; ++c)
+        for (int d = 0; d < 4; ++d)
+          if (a != b && a != c && a != d && b != c && b != d && c != d) {
+            if (n == i) return x == 0 ? a : (x == 1 ? b : (x == 2 ? c : d));
+            ++n;
+          }
+  return -1;
+}
+__host__ __device__ constexpr int t4_comp(int i, int j) {  // index of y -> perm_i(perm_j(y))
+  for (int k = 0; k < 24; ++k) {
+    bool eq = true;
+    for (int y = 0; y < 4; ++y) eq = eq && t4_perm(k, y) == t4_perm(i, t4_perm(j, y));
+    if (eq) return k;
+  }
+  return -1;
+}
+template <int I, int J>
+constexpr int kT4Comp = t4_comp(I, J);
+template <int I, int X>
+constexpr int kT4Perm = t4_perm(I, X);
+static_assert(kT4Comp<5, 0> == 5 && kT4Comp<0, 7> == 7 && kT4Perm<23, 0> == 3, "permutation tables");
+
+// staged address of slot-local coordinates l permuted by permutation I
+template <int I>
+__device__ __forceinline__ int t4_paddr(const int (&lx)[4]) {
+  return lx[kT4Perm<I, 0>] * kT4S0 + lx[kT4Perm<I, 1>] * kT4S1 + lx[kT4Perm<I, 2>] * kT4S2 + lx[kT4Perm<I, 3>];
+}
+
+template <typename T, int S, int... P>
+__device__ __forceinline__ T t4_orbit_out(const T (&vv)[24], const T (&d)[24], std::integer_sequence<int, P...>) {
+  T acc = (T)0;
+  ((acc += d[P] * vv[kT4Comp<S, P>]), ...);
+  return acc;
+}
+
+template <typename T, int... S>
+__device__ __forceinline__ void t4_orbit_read(T (&vv)[24], const T* tiles, const int* canon, const int (&lx)[4],
+                                              std::integer_sequence<int, S...>) {
+  ((vv[S] = tiles[canon[S] * kT4Slot + t4_paddr<S>(lx)]), ...);
+}
+
+template <typename T, int... S>
+__device__ __forceinline__ void t4_orbit_write(const T (&vv)[24], const T (&d)[24], T* tiles, const int* canon,
+                                               const int (&lx)[4], std::integer_sequence<int, S...>) {
+  ((canon[S] == S ? (void)(tiles[S * kT4Slot + t4_paddr<S>(lx)] =
+                               t4_orbit_out<T, S>(vv, d, std::make_integer_sequence<int, 24>{}))
+                  : (void)0),
+   ...);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_t4_post(const T* __restrict__ r, T* __restrict__ out,
@@ -99,13 +159,14 @@ __global__ void __launch_bounds__(256) k_t4_post(const T* __restrict__ r, T* __r
   const T* rb = r + blk * V4;
   T* ob = out + blk * V4;
   const int l = threadIdx.x;
-  auto lx = [l](int x) { return (l >> (6 - 2 * x)) & 3; };  // local coordinate of label position x
-  const int own = lx(0) * kT4S0 + lx(1) * kT4S1 + lx(2) * kT4S2 + lx(3);
-  int paddr[24];
+  const int lx[4] = {(l >> 6) & 3, (l >> 4) & 3, (l >> 2) & 3, l & 3};  // local coordinate of label position x
+  const int own = lx[0] * kT4S0 + lx[1] * kT4S1 + lx[2] * kT4S2 + lx[3];
+  T d[24];  // this block's coefficients (uniform over the CTA)
 #pragma unroll
-  for (int p = 0; p < 24; ++p)
-    paddr[p] = lx(c_t4perm[p][0]) * kT4S0 + lx(c_t4perm[p][1]) * kT4S1 + lx(c_t4perm[p][2]) * kT4S2 +
-               lx(c_t4perm[p][3]);
+  for (int p = 0; p < 24; ++p) {
+    if constexpr (sizeof(T) == 4) d[p] = q.x < 5 ? c_t4coef_f[q.x][p] : 0.f;
+    else d[p] = q.x < 5 ? c_t4coef[q.x][p] : 0.0;
+  }
   double s = 0.0;
   for (int qi = blockIdx.x; qi < nq; qi += gridDim.x) {
     const int4 Q4 = quads[qi];
@@ -125,35 +186,33 @@ __global__ void __launch_bounds__(256) k_t4_post(const T* __restrict__ r, T* __r
       canon[l] = c;
     }
     __syncthreads();
-    for (int sl = 0; sl < 24; ++sl) {
-      if (canon[sl] != sl) continue;
-      int g[4];
+    if (q.x < 5) {
+      for (int sl = 0; sl < 24; ++sl) {
+        if (canon[sl] != sl) continue;
+        int g[4];
 #pragma unroll
-      for (int x = 0; x < 4; ++x) g[x] = kT4Tile * Qa(c_t4perm[sl][x]) + lx(x);
-      const bool in = g[0] < v && g[1] < v && g[2] < v && g[3] < v;
-      const i64 off = (((i64)g[0] * v + g[1]) * v + g[2]) * v + g[3];
-      if (q.x < 5) tiles[sl * kT4Slot + own] = in ? rb[off] : (T)0;
+        for (int x = 0; x < 4; ++x) g[x] = kT4Tile * Qa(c_t4perm[sl][x]) + lx[x];
+        const bool in = g[0] < v && g[1] < v && g[2] < v && g[3] < v;
+        const i64 off = (((i64)g[0] * v + g[1]) * v + g[2]) * v + g[3];
+        tiles[sl * kT4Slot + own] = in ? rb[off] : (T)0;
+      }
+      __syncthreads();
+      T vv[24];
+      t4_orbit_read<T>(vv, tiles, canon, lx, std::make_integer_sequence<int, 24>{});
+      __syncthreads();  // every orbit read before the outputs overwrite the tiles
+      t4_orbit_write<T>(vv, d, tiles, canon, lx, std::make_integer_sequence<int, 24>{});
+      __syncthreads();
     }
-    __syncthreads();
     T qs = (T)0;  // this quadruple's squared outputs, in the storage type
     for (int sl = 0; sl < 24; ++sl) {
       if (canon[sl] != sl) continue;
       int g[4];
 #pragma unroll
-      for (int x = 0; x < 4; ++x) g[x] = kT4Tile * Qa(c_t4perm[sl][x]) + lx(x);
-      T acc = (T)0;
-      if (q.x < 5) {
-#pragma unroll
-        for (int p = 0; p < 24; ++p) {
-          T d;
-          if constexpr (sizeof(T) == 4) d = c_t4coef_f[q.x][p];
-          else d = c_t4coef[q.x][p];
-          acc += d * tiles[canon[c_t4comp[sl][p]] * kT4Slot + paddr[p]];
-        }
-      }
+      for (int x = 0; x < 4; ++x) g[x] = kT4Tile * Qa(c_t4perm[sl][x]) + lx[x];
+      const T val = q.x < 5 ? tiles[sl * kT4Slot + own] : (T)0;
       if (g[0] < v && g[1] < v && g[2] < v && g[3] < v) {
-        ob[(((i64)g[0] * v + g[1]) * v + g[2]) * v + g[3]] = acc;
-        qs += acc * acc;
+        ob[(((i64)g[0] * v + g[1]) * v + g[2]) * v + g[3]] = val;
+        qs += val * val;
       }
     }
     s += (double)qs;
@@ -341,17 +400,10 @@ void t4_tables_once() {
         for (int x = 0; x < 4; ++x) rho[x] = perms[i][h[x]];
         coef[g][index_of(rho)] += proj[i] / (double)groups[g].size();
       }
-  unsigned char hp[24][4], comp[24][24];
+  unsigned char hp[24][4];  // lexicographic, as t4_perm (the kernel's compile-time tables)
   for (int i = 0; i < 24; ++i)
     for (int x = 0; x < 4; ++x) hp[i][x] = (unsigned char)perms[i][x];
-  for (int a = 0; a < 24; ++a)
-    for (int b = 0; b < 24; ++b) {
-      std::array<int, 4> ab;  // y -> a(b(y))
-      for (int y = 0; y < 4; ++y) ab[y] = perms[a][perms[b][y]];
-      comp[a][b] = (unsigned char)index_of(ab);
-    }
   cudaMemcpyToSymbol(c_t4perm, hp, sizeof(hp));
-  cudaMemcpyToSymbol(c_t4comp, comp, sizeof(comp));
   cudaMemcpyToSymbol(c_t4coef, coef, sizeof(coef));
   float coef_f[5][24];
   for (int g = 0; g < 5; ++g)

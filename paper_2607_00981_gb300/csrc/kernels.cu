@@ -522,10 +522,15 @@ void launch_combine(const CombineArgs& c0, cudaStream_t s) {
 // of one orbit of 8^3 tiles {(TA,TB,TC) permuted}.  One CTA takes one orbit of
 // one block at a time: it loads the orbit's distinct cubes (1, 3 or 6) into shared
 // memory along the unit-stride axis (each thread two rows of every cube, all loads
-// issued before the first store), then writes every element of those cubes once --
-// one HBM read and one write per element.  Small cubes keep eight CTAs on an SM, so
-// one CTA's loads overlap another's stores.  The squared norm of each block is
-// summed in the storage type per thread and in FP64 across blocks and threads.
+// issued before the first store).  Each thread then reads the six values of the
+// element orbits of its two elements of cube 0 once, forms all six outputs of each
+// orbit (one mean, the block's column-swap average) and writes them back into the
+// cubes, one writer per element; the cubes are then stored along the unit-stride
+// axis -- one HBM read and one write per element, about four shared-memory accesses
+// per element (seven when every output read its six permutations).  Small cubes
+// keep six CTAs on an SM, so one CTA's loads overlap another's stores.  The squared
+// norm of each block is summed in the storage type per thread and in FP64 across
+// blocks and threads.
 // ---------------------------------------------------------------------------
 constexpr int kPostTL = 8;
 
@@ -534,7 +539,7 @@ __global__ void k_sum(const double* __restrict__ partial, int np, double* __rest
                       int accumulate);
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __restrict__ rp,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_post(const T* __restrict__ r, T* __restrict__ rp,
                                               const int4* __restrict__ blocks, int v, i64 n3,
                                               const double* __restrict__ wblk, double* __restrict__ partial) {
   constexpr int TL = kPostTL;
@@ -544,6 +549,7 @@ __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __rest
   Cube* cube = reinterpret_cast<Cube*>(post_smem);
   __shared__ int tcoord[6][3];
   __shared__ int slot[6][6];
+  __shared__ bool first[6];
   __shared__ int ncube;
   const i64 V2 = (i64)v * v, V3 = V2 * v;
   // orbit index -> sorted tile triple (TA <= TB <= TC), colex like the blocks; the
@@ -578,6 +584,11 @@ __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __rest
         if (tcoord[k2][0] == x && tcoord[k2][1] == y && tcoord[k2][2] == z) slot[k][q] = k2;
     }
   }
+  if (threadIdx.x < 6) {  // q is the first label permutation of cube 0 that lands in its cube
+    bool f = true;
+    for (int q2 = 0; q2 < (int)threadIdx.x; ++q2) f = f && slot[0][q2] != slot[0][threadIdx.x];
+    first[threadIdx.x] = f;
+  }
   __syncthreads();
   const int n = ncube;
   // thread (xg, ty, tz): rows x = xg and xg + 4 of every cube, local (ty, tz) along them
@@ -609,34 +620,56 @@ __global__ void __launch_bounds__(256) k_post(const T* __restrict__ r, T* __rest
     __syncthreads();
     T* out = rp + b * V3;
     const bool all_eq = ijk.x == ijk.y && ijk.y == ijk.z;
+    if (!all_eq) {
+      // the orbit of element e = (x, ty, tz) of cube 0: v[q] = R(e o perm_q) lies in
+      // cube slot[0][q] at e's local coordinates permuted by q
+      const int s1 = slot[0][1], s2 = slot[0][2], s3 = slot[0][3], s4 = slot[0][4], s5 = slot[0][5];
+      T vv[2][6];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int x = xg + 4 * h;
+        vv[h][0] = cube[0][x][ty][tz];
+        vv[h][1] = cube[s1][x][tz][ty];
+        vv[h][2] = cube[s2][ty][x][tz];
+        vv[h][3] = cube[s3][ty][tz][x];
+        vv[h][4] = cube[s4][tz][x][ty];
+        vv[h][5] = cube[s5][tz][ty][x];
+      }
+      __syncthreads();  // every orbit read before the outputs overwrite the cubes
+      // out(e o q) = sym(e o q) - mean over the orbit; sym averages e o q with its
+      // image under the block's column swap (positions 0 1 for i = j, 1 2 for j = k)
+      const int mode = ijk.x == ijk.y ? 1 : (ijk.y == ijk.z ? 2 : 0);
+      constexpr int kS01[6] = {2, 4, 0, 5, 1, 3}, kS12[6] = {1, 0, 3, 2, 5, 4};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int x = xg + 4 * h;
+        const T* w = vv[h];
+        const T mean = (w[0] + w[1] + w[2] + w[3] + w[4] + w[5]) * (T)(1.0 / 6.0);
+        T o6[6];
+#pragma unroll
+        for (int qq = 0; qq < 6; ++qq)
+          o6[qq] = (mode == 1 ? (T)0.5 * (w[qq] + w[kS01[qq]])
+                              : (mode == 2 ? (T)0.5 * (w[qq] + w[kS12[qq]]) : w[qq])) - mean;
+        // one writer per output: cube slot[0][q] is written through its first q
+        if (first[0]) cube[0][x][ty][tz] = o6[0];
+        if (first[1]) cube[s1][x][tz][ty] = o6[1];
+        if (first[2]) cube[s2][ty][x][tz] = o6[2];
+        if (first[3]) cube[s3][ty][tz][x] = o6[3];
+        if (first[4]) cube[s4][tz][x][ty] = o6[4];
+        if (first[5]) cube[s5][tz][ty][x] = o6[5];
+      }
+      __syncthreads();
+    }
     T bs = (T)0;
     for (int k = 0; k < n; ++k) {
       const int gy = tcoord[k][1] * TL + ty, gz = tcoord[k][2] * TL + tz;
       if (gy >= v || gz >= v) continue;
-      const int s1 = slot[k][1], s2 = slot[k][2], s3 = slot[k][3], s4 = slot[k][4], s5 = slot[k][5];
       T* dst = out + (i64)gy * v + gz;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int x = xg + 4 * h, gx = tcoord[k][0] * TL + x;
         if (gx >= v) break;
-        // element (a,b,c) = local (x, ty, tz); the label permutation (p0,p1,p2) is
-        // local (l[p0], l[p1], l[p2]) of the cube holding that tile permutation
-        const T rabc = cube[k][x][ty][tz];
-        const T racb = cube[s1][x][tz][ty];
-        const T rbac = cube[s2][ty][x][tz];
-        const T rbca = cube[s3][ty][tz][x];
-        const T rcab = cube[s4][tz][x][ty];
-        const T rcba = cube[s5][tz][ty][x];
-        T val;
-        if (all_eq) {
-          val = (T)0;
-        } else {
-          T sym;
-          if (ijk.x == ijk.y) sym = (T)0.5 * (rabc + rbac);
-          else if (ijk.y == ijk.z) sym = (T)0.5 * (rabc + racb);
-          else sym = rabc;
-          val = sym - (rabc + racb + rbac + rbca + rcab + rcba) * (T)(1.0 / 6.0);
-        }
+        const T val = all_eq ? (T)0 : cube[k][x][ty][tz];
         dst[(i64)gx * V2] = val;
         bs += val * val;
       }

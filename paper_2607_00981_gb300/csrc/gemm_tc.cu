@@ -9,9 +9,9 @@
 // relative error of about 2^-16 (BF16) or 2^-21 (TF32) per product.
 //
 // Persistent kernel, one CTA per SM, 320 threads:
-//   warp 0     TMA producer: 64-byte-swizzled tiles (rows of 64 bytes of K) of
-//              128 rows of A and up to 256 rows of B, hi and lo planes, into a
-//              4-stage ring;
+//   warp 0     TMA producer: swizzled K-major tiles of 128 rows of A and 128,
+//              144 or 256 rows of B, hi and lo planes, into a ring of stages (256-
+//              wide tiles: four stages of 64-byte K rows; narrower: three of 128);
 //   warp 1     TMEM owner and MMA issuer (one thread): 3 tcgen05.mma per 32-byte
 //              K slice into a 128 x 256 FP32 accumulator, double buffered in
 //              TMEM (512 columns) so the epilogue of one tile overlaps the MMAs
@@ -37,19 +37,23 @@
 namespace rcc {
 namespace {
 
-// Four stages of 64-byte K rows (48 KiB per stage at BN = 256) rather than two of 128:
-// the same shared memory, with three stages' loads in flight behind the MMAs instead of one.
-constexpr int BM = 128, STAGES = 4;
-constexpr int ROWB = 64;                       // bytes of one K-row of a tile (swizzle span)
-constexpr int A_PLANE = BM * ROWB;
+constexpr int BM = 128;
 constexpr int kEpiWarps = 8;                 // two epilogue warps per TMEM lane quadrant
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 // Tile width BN (256 or 128 columns): B planes, stage and shared-memory sizes.
+// 256-wide tiles: four stages of 64-byte K rows (48 KiB per stage; two stages of
+// 128-byte rows in the same memory kept one stage in flight behind the MMAs).  128-
+// and 144-wide tiles (GEMMs of few tiles, the hh-ladder): three stages of 128-byte rows
+// (64 / 68 KiB per stage), whose larger copies suit these mostly load-bound GEMMs.
+constexpr int row_bytes(int BN) { return BN == 256 ? 64 : 128; }
 template <int BN>
 struct TileCfg {
+  static constexpr int ROWB = row_bytes(BN);  // bytes of one K-row of a tile (swizzle span)
+  static constexpr int STAGES = BN == 256 ? 4 : 3;
+  static constexpr int A_PLANE = BM * ROWB;
   static constexpr int B_PLANE = BN * ROWB;
-  static constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;  // 48 KiB for BN = 256
+  static constexpr int STAGE_BYTES = 2 * A_PLANE + 2 * B_PLANE;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
   static constexpr int TMEM_COLS = 2 * BN <= 256 ? 256 : 512;      // double-buffered accumulator (power of 2)
   static constexpr int FULL = BN / 32, HALF = (BN % 32) / 16;      // 32- and 16-column epilogue chunks
@@ -133,11 +137,22 @@ __device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
   return d;
 }
 
-// SM100 shared-memory matrix descriptor of the k_gemm_tc tiles: K-major rows of ROWB
-// bytes with the matching swizzle (version 1; tiles 1024-byte aligned, base offset 0).
+// SM100 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), version 1; tiles are 1024-byte aligned (base offset 0).
+__device__ __forceinline__ uint64_t sdesc128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;                      // SWIZZLE_128B
+  return d;
+}
+// the k_gemm_tc tiles' descriptor for K rows of ROWB bytes (swizzle span = row)
+template <int ROWB>
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  static_assert(ROWB == 64, "k_gemm_tc tiles use the 64-byte swizzle");
-  return sdesc64(saddr);
+  static_assert(ROWB == 64 || ROWB == 128, "64- or 128-byte K rows");
+  if constexpr (ROWB == 64) return sdesc64(saddr);
+  else return sdesc128(saddr);
 }
 
 // Instruction descriptor: D = F32, A = B = fmt (1 BF16, 2 TF32), both K-major, N = BN, M = BM.
@@ -383,6 +398,7 @@ template <int FMT, int BN, class S>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ S sch, int* __restrict__ status, long long budget) {
   constexpr int B_PLANE = TileCfg<BN>::B_PLANE, STAGE_BYTES = TileCfg<BN>::STAGE_BYTES;
+  constexpr int ROWB = TileCfg<BN>::ROWB, STAGES = TileCfg<BN>::STAGES, A_PLANE = TileCfg<BN>::A_PLANE;
   constexpr int TMEM_COLS = TileCfg<BN>::TMEM_COLS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -482,8 +498,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           fence_after();
           const uint32_t base = su32(smem + s * STAGE_BYTES);
-          const uint64_t ah = sdesc(base), al = sdesc(base + A_PLANE);
-          const uint64_t bh = sdesc(base + 2 * A_PLANE), bl = sdesc(base + 2 * A_PLANE + B_PLANE);
+          const uint64_t ah = sdesc<ROWB>(base), al = sdesc<ROWB>(base + A_PLANE);
+          const uint64_t bh = sdesc<ROWB>(base + 2 * A_PLANE), bl = sdesc<ROWB>(base + 2 * A_PLANE + B_PLANE);
 #pragma unroll
           for (int j = 0; j < ROWB / 32; ++j) {
             const uint64_t adv = (uint64_t)(j * 32 >> 4);  // 32-byte K slice inside the swizzled row
@@ -855,18 +871,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* map, const void* ptr, int rows, int Kpad, int kind, int box_rows) {
+// rowb: bytes of one K row of the kernel's tiles (64 or 128, the swizzle span)
+bool make_map(CUtensorMap* map, const void* ptr, int rows, int Kpad, int kind, int box_rows, int rowb) {
   auto fn = encode_fn();
   if (!fn) return false;
   const int esz = kind == PANEL_BF16X2 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)Kpad * esz};
-  cuuint32_t box[2] = {(cuuint32_t)(ROWB / esz), (cuuint32_t)box_rows};
+  if (rowb != 64 && rowb != 128) return false;
+  cuuint32_t box[2] = {(cuuint32_t)(rowb / esz), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   const CUtensorMapDataType dt = kind == PANEL_BF16X2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  static_assert(ROWB == 64, "the tensor maps' swizzle matches the descriptors' (64 bytes)");
   return fn(map, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            rowb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -914,8 +931,7 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
   if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
   int BN = (bn == 128 || bn == 144) ? bn : 256;
   const int esz = kind == PANEL_BF16X2 ? 2 : 4;
-  const int bk = ROWB / esz;
-  if (Kpad % bk != 0 || e.M <= 0 || e.N <= 0) return 1;
+  if (e.M <= 0 || e.N <= 0) return 1;
   if (e.col_off2 && (BN != 256 || raw_out || e.row_base2)) return 1;  // column mirror: 256-wide, direct epilogue
   // A table-epilogue GEMM of few 256-wide tiles is bound by its epilogue's chains of
   // dependent loads (eight warps per tile): with at most half the SMs busy, 128-wide
@@ -923,9 +939,11 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
   if (BN == 256 && !raw_out && !e.col_off2 &&
       2LL * ((e.M + BM - 1) / BM) * ((e.N + 255) / 256) <= (long long)num_sms())
     BN = 128;
+  const int rowb = row_bytes(BN), bk = rowb / esz;
+  if (Kpad % bk != 0) return 1;
   PlainSched sch;
-  if (!make_map(&sch.ah, Ahi, e.M, Kpad, kind, BM) || !make_map(&sch.al, Alo, e.M, Kpad, kind, BM) ||
-      !make_map(&sch.bh, Bhi, e.N, Kpad, kind, BN) || !make_map(&sch.bl, Blo, e.N, Kpad, kind, BN))
+  if (!make_map(&sch.ah, Ahi, e.M, Kpad, kind, BM, rowb) || !make_map(&sch.al, Alo, e.M, Kpad, kind, BM, rowb) ||
+      !make_map(&sch.bh, Bhi, e.N, Kpad, kind, BN, rowb) || !make_map(&sch.bl, Blo, e.N, Kpad, kind, BN, rowb))
     return 2;
   TileGeom& g = sch.g;
   g.mt = (e.M + BM - 1) / BM;
@@ -988,16 +1006,19 @@ int launch_gemm_tc(int kind, const void* Ahi, const void* Alo, const void* Bhi, 
   return 0;
 }
 
-int gemm_tc_block_k(int kind) { return ROWB / (kind == PANEL_BF16X2 ? 2 : 4); }
+int gemm_tc_block_k(int kind, int bn) {
+  const int BN = (bn == 128 || bn == 144) ? bn : 256;
+  return row_bytes(BN) / (kind == PANEL_BF16X2 ? 2 : 4);
+}
 
 int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int M,
                   int N, int Kpad, float* out, int bn) {
   if (kind != PANEL_BF16X2 && kind != PANEL_TF32X2) return 1;
   const int BN = (bn == 128 || bn == 144) ? bn : 256;
-  const int bk = gemm_tc_block_k(kind);
+  const int bk = gemm_tc_block_k(kind, BN), rowb = row_bytes(BN);
   if (Kpad % bk != 0 || M <= 0 || N <= 0) return 1;
-  if (!make_map(&p->ah, Ahi, M, Kpad, kind, BM) || !make_map(&p->al, Alo, M, Kpad, kind, BM) ||
-      !make_map(&p->bh, Bhi, N, Kpad, kind, BN) || !make_map(&p->bl, Blo, N, Kpad, kind, BN))
+  if (!make_map(&p->ah, Ahi, M, Kpad, kind, BM, rowb) || !make_map(&p->al, Alo, M, Kpad, kind, BM, rowb) ||
+      !make_map(&p->bh, Bhi, N, Kpad, kind, BN, rowb) || !make_map(&p->bl, Blo, N, Kpad, kind, BN, rowb))
     return 2;
   p->a_hi = Ahi;
   p->a_lo = Alo;

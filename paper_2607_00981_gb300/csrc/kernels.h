@@ -111,7 +111,7 @@ struct alignas(128) GProblem {
 int make_gproblem(GProblem* p, int kind, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo, int M,
                   int N, int Kpad, float* out, int bn = 256);
 int gproblem_tiles(const GProblem& p);
-int gemm_tc_block_k(int kind);
+int gemm_tc_block_k(int kind, int bn);
 // One persistent launch over every tile of the nprob problems (device table,
 // tile0 prefix order, tables made with the same bn); grid <= 0 picks one CTA per SM.
 // FP64-accurate GEMM on the BF16 tensor cores (digit planes, see elem.cuh):

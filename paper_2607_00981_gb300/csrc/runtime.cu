@@ -82,15 +82,6 @@ int dev_zero(void* p, size_t bytes, cudaStream_t s) {
 int dev_sync(cudaStream_t s) { return cudaStreamSynchronize(s) == cudaSuccess ? 0 : RCCSDT_ERR_CUDA; }
 int dev_check() { return cudaGetLastError() == cudaSuccess ? 0 : RCCSDT_ERR_CUDA; }
 #endif
-// Last CUDA error text (or empty) for error messages.
-const char* cuda_error_text() {
-#ifdef RCC_HOSTSIM
-  return "";
-#else
-  return cudaGetErrorString(cudaPeekAtLastError());
-#endif
-}
-
 i64 n3_of(int o) { return (i64)o * (o + 1) * (o + 2) / 6; }
 int multiplicity(int i, int j, int k) {
   if (i == j && j == k) return 1;
@@ -1029,16 +1020,6 @@ static void run_combines(rccsdt_ctx* c, const std::vector<rcc::CombineArgs>& cs)
 // Context construction: buffers and every plan of one iteration
 // ---------------------------------------------------------------------------
 namespace {
-
-// View with dimension 0 fixed at `idx` and removed.
-View slice0(const View& v, i64 idx) {
-  View r;
-  r.p = (char*)v.p + idx * v.stride[0] * (v.f32 ? 4 : 8);
-  r.f32 = v.f32;
-  r.shape.assign(v.shape.begin() + 1, v.shape.end());
-  r.stride.assign(v.stride.begin() + 1, v.stride.end());
-  return r;
-}
 
 // Virtual-permutation index of pos (the 6 orderings in lexicographic order).
 int perm_id(const int pos[3]) {
@@ -2113,14 +2094,6 @@ void run_grouped_reduce(rccsdt_ctx* c) {
                                  c->B("r3")->f(), c->stream);
 }
 
-// The residual's tensor-core contractions through the grouped path (R3 is
-// overwritten by the reduction, so it needs no zeroing).
-int run_grouped(rccsdt_ctx* c) {
-  int st = run_grouped_gathers(c);
-  if (!st) st = run_grouped_gemm(c);
-  if (!st) run_grouped_reduce(c);
-  return st;
-}
 
 }  // namespace
 

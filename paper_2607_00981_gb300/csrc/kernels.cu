@@ -680,8 +680,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_post(const T* _
   if (threadIdx.x == 0) partial[(i64)blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
-// about 8 resident waves of CTAs (eight per SM); each keeps its orbit tables across
-// the blocks it visits
+// about 64 CTAs per SM in all (six resident at a time); each keeps its orbit tables
+// across the blocks it visits
 static i64 post_grid_y(int norb, i64 n3) {
   return std::max<i64>(1, std::min<i64>(n3, (152 * 8 * 8 + norb - 1) / norb));
 }
